@@ -10,10 +10,16 @@ pseudo-inverse of the connectivity matrix:  q~^a = -(P^a)^+ z^a
 Sec. 4.2: if ||g*||_2^2 >= delta after the update, the positions and
 orientations are corrected by increments (dq_p, dtheta_p) minimising ||g||^2
 subject to ||dtheta_p||^2 = 1 (Eq. min_probl_a/b, residual Eq. residual),
-with the exact Jacobian (App. B).  The paper uses SciPy's least squares; this
-oracle uses Gauss-Newton with minimum-norm least-squares steps on the
-residual [g; ||dtheta_p||^2 - 1], from dq = 0, dtheta = [1, 0, 0, 0], until
-the squared residual norm is below delta^2.
+with the exact Jacobian (App. B).  The paper uses SciPy's trust-region least
+squares; this oracle takes Levenberg-Marquardt steps on the residual
+r = [g; ||dtheta_p||^2 - 1] from dq = 0, dtheta = [1, 0, 0, 0]:
+    (J^T J + mu I) step = -J^T r,   mu = 1e-10 max diag(J^T J),
+until ||r||^2 < delta^2.  Fixed damping rather than undamped minimum-norm
+Gauss-Newton steps: link sets such as two links on a common axis leave
+near-free directions (rotation about that axis) with singular values of J
+down to ~1e-8, along which undamped steps move by orders of magnitude more
+than the constraint violation; the damped step is the small correction, of
+the size of the violation, that Sec. 4.2 describes.
 
 Sec. 4.3 (explicit Euler with reconstruction and correction):
   U = solve(t_k); u_COM^a = mean_p u_p; q_COM* = q_COM + dt u_COM;
@@ -149,7 +155,9 @@ def correct(q, theta, dl_p, dl_q, assembly, bp, bq, delta, max_iter=20):
             if r @ r < delta * delta or it >= max_iter:
                 break
             J = correction_jacobian(x, lt_p, lt_q, lbp, lbq, col)
-            step, *_ = np.linalg.lstsq(J, -r, rcond=1e-12)
+            N = J.T @ J
+            mu = 1e-10 * np.diag(N).max()
+            step = np.linalg.solve(N + mu * np.eye(len(N)), -J.T @ r)
             x = x + step
             it += 1
         iters[a_] = it
