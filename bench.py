@@ -1,0 +1,339 @@
+"""Benchmark of the constrained mobility solve: one time step of the diatom
+colony above a no-slip wall (32 rods x 80 blobs = 2,560 blobs, 62 sliding
+links, dt = 1e-3, plain FP64, GMRES to relative residual 1e-8).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one am_solve_step: pose, preconditioner build, warm-started GMRES
+solve, Euler update, reconstruction and correction.  The headline metric is
+blob-pair interactions of the mobility products per second over the whole
+step (pairs evaluated / step time).  Prints one JSON line (rank 0).
+
+With N > 1 (torchrun) every rank runs its own colony (seed 1 + rank): the
+suspensions are independent, so there is no exchange and scaling is weak.
+--impl reference times the FP64 CPU oracle on the same workload (a bounded
+sample of mobility rows per step), rank 0 only.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RPY pair-interactions/s"
+UNIT = "pairs/s"
+DT = 1e-3
+TOL = 1e-8
+WORKLOAD = ("diatom colony above a no-slip wall: 32 rods of 2x40 blobs (2,560 blobs, a=0.1), "
+            "62 sliding links, dt=1e-3, FP64, GMRES relative residual 1e-8")
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % self.gpu)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            return None
+    return None
+
+
+def oracle_sample(w, t, seconds=10.0):
+    """The oracle's mobility rows on a bounded sample of target blobs of the
+    workload: returns (pairs/s, pairs, rows, elapsed)."""
+    from oracle.system import System
+    from oracle import mobility as om
+    S = System(w, t=t)
+    lam = np.random.default_rng(0).standard_normal((S.Nb, 3))
+    rng = np.random.default_rng(1)
+    rows = rng.choice(S.Nb, 16, replace=False)
+    t0 = time.perf_counter()
+    om.mobility_rows(S.r, lam, rows, S.a, S.eta, S.wall)
+    per_row = (time.perf_counter() - t0) / len(rows)
+    nrows = int(min(S.Nb, max(16, seconds / max(per_row, 1e-6))))
+    rows = rng.choice(S.Nb, nrows, replace=False)
+    t0 = time.perf_counter()
+    om.mobility_rows(S.r, lam, rows, S.a, S.eta, S.wall)
+    el = time.perf_counter() - t0
+    pairs = nrows * S.Nb
+    return pairs / el, pairs, nrows, el
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2107_10800_gb300 import workloads as W
+    w = W.diatom_colony(1)
+    nb = W.counts(w)[0]
+    for _ in range(args.warmup):
+        oracle_sample(w, 0.0, seconds=0.5)
+    times, pairs_tot = [], 0
+    per_step = max(1.0, min(10.0, 120.0 / max(args.steps, 1)))
+    for k in range(args.steps):
+        rate, pairs, nrows, el = oracle_sample(w, k * DT, seconds=per_step)
+        times.append(el)
+        pairs_tot += pairs
+    value = pairs_tot / sum(times)
+    sample = "oracle mobility rows of the colony, %d-%d target rows x %d sources per step" % (
+        16, nb, nb)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "blobs": nb},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2107_10800_gb300 import build as _b
+    from paper_2107_10800_gb300 import binding, workloads as W
+    if rank == 0 or world == 1:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    _b.build()
+    L = binding.lib()
+    w = W.diatom_colony(1 + rank)
+    nb, M, P, n = W.counts(w)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    solver = binding.Solver.from_workload(w, t=0.0, tol=TOL, precision=args.precision,
+                                          stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def do_step(k, outputs):
+        t = k * DT
+        dlp, dlq, dlpd, dlqd = w["dl"](t)
+        solver.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd)
+        nxt = w["dl"](t + DT)[:2]
+        if outputs:
+            return solver.step(t, DT, dl_next=nxt)
+        st = binding.StepStats()
+        import ctypes
+        a1 = np.ascontiguousarray(nxt[0]).ravel()
+        a2 = np.ascontiguousarray(nxt[1]).ravel()
+        rc = L.am_solve_step(solver.h, t, DT, a1.ctypes.data_as(binding._dp),
+                             a2.ctypes.data_as(binding._dp), ctypes.byref(st), None, None, None)
+        if rc not in (0, binding.AM_ERR_NOT_CONVERGED):
+            raise binding.AmError(rc, L.am_last_error(solver.h).decode())
+        return None, None, None, st.as_dict()
+
+    k = 0
+    for _ in range(args.warmup):
+        do_step(k, False)
+        k += 1
+    # peaks for the roofline of the all-pairs kernel (ALU bound)
+    fp64_peak = binding.alu_peak(True)
+    fp32_peak = binding.alu_peak(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms, pairs, iters, resid = [], 0, [], []
+    launches0 = binding.kernel_launches()
+    solver.mobility_timing(True)
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            _, _, _, st = do_step(k, False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            pairs += st["pairs"]
+            iters.append(st["iterations"])
+            resid.append(st["rel_residual"])
+            k += 1
+        t_wall = time.perf_counter() - t_wall0
+    mob_ms, mob_launches = solver.mobility_timing(False)
+    launches = binding.kernel_launches() - launches0
+    total_s = sum(step_ms) * 1e-3
+    local_rate = pairs / total_s
+    # end to end: host link schedule in, solution out, every step
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        U, phi, lam, st = do_step(k, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        k += 1
+    e2e_rate = st["pairs"] / (statistics.mean(e2e_ms) * 1e-3)
+
+    # aggregate over ranks: max time, summed pairs
+    if world > 1:
+        tt = torch.tensor([total_s, float(pairs), statistics.mean(e2e_ms)], dtype=torch.float64,
+                          device="cuda")
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = tt.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        total_s_all = float(tmax[0])
+        pairs_all = float(tsum[1])
+        e2e_rate = float(tsum[1]) / args.steps / (float(tmax[2]) * 1e-3)
+    else:
+        total_s_all = total_s
+        pairs_all = float(pairs)
+    value = pairs_all / total_s_all
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return
+
+    fpp = binding.flops_per_pair(1)
+    avg_launch_s = (mob_ms * 1e-3) / max(mob_launches, 1)
+    achieved = nb * nb * fpp / avg_launch_s
+    peak = fp64_peak if args.precision == "fp64" else fp32_peak
+    clocks = clk.summary()
+    roofline = {"bound": "alu", "achieved": achieved / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "rpy_partial_%s<wall>" % ("f64" if args.precision == "fp64" else "mixed"),
+                "flop_per_pair": fpp, "pairs_per_launch": nb * nb,
+                "launch_ms": avg_launch_s * 1e3, "launches": mob_launches,
+                "peak_source": "measured %s FMA streams (am_alu_peak) on this GPU" %
+                               ("DFMA" if args.precision == "fp64" else "FFMA"),
+                "fp32_fma_peak_tflops": fp32_peak / 1e12, "fp64_fma_peak_tflops": fp64_peak / 1e12}
+    cpu = None
+    if world == 1:
+        rate, cp, nrows, el = oracle_sample(w, 0.0, seconds=12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "oracle mobility rows: %d of %d target blobs x %d sources (%.1f s)"
+                         % (nrows, nb, nb, el)}
+    h2d = 6 * 3 * P * 8
+    d2h = (6 * M + 3 * P + 3 * nb) * 8
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32-pairs/f64-sums",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "blobs": nb, "bodies": M, "links": P, "unknowns": n,
+                       "precision": args.precision, "tol": TOL,
+                       "l2": "512 MB buffer written between timed steps (inputs smaller than L2)",
+                       "parallelism": "independent suspension per GPU" if world > 1 else "1 GPU"},
+            "solve_ms_per_step": 1e3 * total_s_all / args.steps,
+            "gmres_iterations_per_step": statistics.mean(iters),
+            "max_rel_residual": max(resid),
+            "wall_s_timed_region": t_wall,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

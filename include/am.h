@@ -1,0 +1,247 @@
+/*
+ * am.h -- C ABI of the GB300 articulated-body Stokes solver (libam.so).
+ *
+ * The library solves, for suspensions of rigid bodies linked by joints in a
+ * viscous (Stokes) fluid, the constrained mobility problem of Sec. 2.3,
+ * Eq. linear_system:
+ *
+ *     [ M    -K   0  ] [lambda]   [ u_s ]
+ *     [-K^T   0   C^T] [  U   ] = [ -F  ]
+ *     [ 0     C   0  ] [ phi  ]   [  B  ]
+ *
+ * lambda: forces on the blobs that discretise each body (3 per blob);
+ * U = (u_p, omega_p): body velocities (6 per body);
+ * phi: Lagrange multipliers of the link constraints (3 per link);
+ * M: the Rotne-Prager-Yamakawa blob mobility (Eq. RPY), in free space or
+ *    above a no-slip wall at z = 0;
+ * K: rigid-body map, (K U)_i = u_p + omega_p x (r_i - q_p) (Eq. no-slip);
+ * C: constraint Jacobian of the links (Eq. dg_compact, App. A);
+ * B: active-link term (Eq. dg).
+ * It is solved by right-preconditioned GMRES with the block-diagonal
+ * preconditioner of Sec. 3.1, and am_solve_step advances the bodies by one
+ * explicit Euler step with the reconstruction and nonlinear correction of
+ * Sec. 4.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (AM_OK) on success or a negative AM_ERR_* code; the handle's
+ *    message is then available from am_last_error(handle) (or
+ *    am_last_error(NULL) for the stateless calls).
+ *  - Host pointers are caller-owned, read or written during the call only,
+ *    never retained.  Arrays are dense, row-major, FP64 unless stated; "3N"
+ *    means N consecutive (x, y, z) triples.
+ *  - Device pointers (only in am_rpy_matvec) are caller-owned device memory
+ *    of the current CUDA device.
+ *  - The library owns all device memory of a handle; a handle is not
+ *    thread-safe.  All work of a handle runs on its stream.
+ */
+#ifndef AM_H
+#define AM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define AM_API __attribute__((visibility("default")))
+#else
+#define AM_API
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define AM_OK                    0
+#define AM_ERR_ARG              -1  /* bad argument, size or call order      */
+#define AM_ERR_CUDA             -2  /* a CUDA call failed                     */
+#define AM_ERR_NOT_CONVERGED    -3  /* GMRES hit max_iter; outputs written    */
+#define AM_ERR_WALL_PENETRATION -4  /* a blob centre at or below height a     */
+#define AM_ERR_NONUNIT_QUAT     -5  /* | |theta| - 1 | > 1e-8 on input        */
+#define AM_ERR_SINGULAR         -6  /* a body's blob mobility block is not SPD */
+
+/* ---- precision of the blob mobility product --------------------------- */
+#define AM_FP64  0   /* every operation in FP64                              */
+#define AM_MIXED 1   /* pair terms in FP32, per-target sums in FP64; outer
+                        residual, Arnoldi and constraint algebra in FP64     */
+
+typedef struct am_handle am_handle;
+
+typedef struct {
+    double eta;          /* fluid viscosity (> 0)                           */
+    double blob_radius;  /* a (> 0), the same for every blob                */
+    int    wall;         /* 0: free space; 1: no-slip wall at z = 0         */
+    int    precision;    /* AM_FP64 or AM_MIXED                             */
+    int    n_systems;    /* independent suspensions in the handle (1)       */
+    double tol;          /* GMRES stop: ||b - A y||_2 <= tol ||b||_2        */
+    int    restart;      /* GMRES restart length m (1..200); 0 -> 50        */
+    int    max_iter;     /* total GMRES iterations cap; 0 -> 500            */
+    double corr_tol;     /* delta of Sec. 4.3; correction runs when
+                            ||g*||_2^2 >= delta; 0 -> 1e-10                 */
+    int    corr_max_iter;/* Gauss-Newton iteration cap; 0 -> 20             */
+    void*  cuda_stream;  /* cudaStream_t to run on; NULL -> library stream  */
+} am_config;
+
+typedef struct {
+    int    status;          /* return code of the call                       */
+    int    iterations;      /* GMRES iterations (Arnoldi steps)              */
+    int    restarts;        /* GMRES cycles started                          */
+    double rel_residual;    /* true ||b - A y||_2 / ||b||_2 at exit          */
+    double constraint_residual; /* max_n |(C U - B)_n| at exit               */
+    double g2_before;       /* ||g*||_2^2 after reconstruction (Sec. 4.3)    */
+    double g2_after;        /* ||g||_2^2 at the end of the step              */
+    int    corr_iterations; /* max Gauss-Newton iterations over assemblies   */
+    long long pairs;        /* blob pairs evaluated by mobility products     */
+    int    kernel_launches; /* kernels launched by the call                  */
+    double ms_precond;      /* device time: preconditioner build             */
+    double ms_gmres;        /* device time: GMRES                            */
+    double ms_update;       /* device time: Euler update, reconstruction,
+                               correction                                    */
+} am_step_stats;
+
+/* Create a solver handle.  cfg is copied.  Errors: AM_ERR_ARG for eta <= 0,
+ * blob_radius <= 0, wall not 0/1, unknown precision, n_systems != 1,
+ * tol <= 0 or restart/max_iter out of range; AM_ERR_CUDA. */
+AM_API int am_create(const am_config* cfg, am_handle** out);
+
+/* Set the bodies of system `system` (0 <= system < n_systems) at the
+ * current time (Sec. 2.1, 2.3).
+ *   n_bodies         M > 0
+ *   q                3M   tracking points q_p (lab frame)
+ *   theta            4M   unit quaternions [s, p] of the orientations
+ *   blob_offset      M+1  int, CSR offsets: body p owns blobs
+ *                         blob_offset[p] .. blob_offset[p+1]-1; [0] = 0,
+ *                         every body has at least one blob
+ *   blob_body_pos    3Nb  body-frame blob positions relative to q_p, so that
+ *                         r_i = q_p + R(theta_p) blob_body_pos_i
+ *   force_torque     6M   F_p = (f_p, tau_p) (tau about q_p)
+ *   slip             3Nb  slip velocities u_s of Eq. linear_system, or NULL
+ *   assembly_of_body M    int, articulated-body index of each body, in
+ *                         0 .. n_assemblies-1, every index used
+ * Replaces any earlier bodies (and drops links and the warm start).
+ * Errors: AM_ERR_ARG, AM_ERR_NONUNIT_QUAT, AM_ERR_WALL_PENETRATION (wall and
+ * some r_i,z <= a), AM_ERR_CUDA. */
+AM_API int am_set_bodies(am_handle* h, int system, int n_bodies,
+                         const double* q, const double* theta,
+                         const int* blob_offset, const double* blob_body_pos,
+                         const double* force_torque, const double* slip,
+                         const int* assembly_of_body);
+
+/* Set the links of system `system` (Eq. constraint):
+ *   g_n = q_p + R(theta_p) dl_p[n] - q_q - R(theta_q) dl_q[n] = 0.
+ *   n_links          P >= 0
+ *   body_p, body_q   P    int, distinct bodies of the same articulated body
+ *   dl_p, dl_q       3P   body-frame link vectors at the current time
+ *   dl_p_dot, dl_q_dot 3P their time derivatives (active links, Eq. dg), or
+ *                    both NULL for passive links (B = 0)
+ * May be called before every step to move active links; the connectivity
+ * (body_p, body_q) may change too.  Needs am_set_bodies first.
+ * Errors: AM_ERR_ARG (bad index, p == q, cross-assembly link, articulated
+ * body not connected by its links), AM_ERR_CUDA. */
+AM_API int am_set_constraints(am_handle* h, int system, int n_links,
+                              const int* body_p, const int* body_q,
+                              const double* dl_p, const double* dl_q,
+                              const double* dl_p_dot, const double* dl_q_dot);
+
+/* Passive links given by their joint points in the lab frame at the current
+ * pose: dl_p[n] = R(theta_p)^T (joint_n - q_p), dl_q[n] likewise, so that
+ * g = 0 now.  joint: 3P.  Otherwise as am_set_constraints. */
+AM_API int am_set_joints(am_handle* h, int system, int n_links,
+                         const int* body_p, const int* body_q,
+                         const double* joint);
+
+/* Solve Eq. linear_system at the current pose (no time step).  Outputs (any
+ * may be NULL): U 6M, phi 3P, lambda 3Nb.  With a rank-deficient C, phi is
+ * determined up to null(C^T); lambda, U and C^T phi are unique.
+ * Errors: AM_ERR_ARG (no bodies), AM_ERR_NOT_CONVERGED (outputs written),
+ * AM_ERR_CUDA. */
+AM_API int am_solve(am_handle* h, am_step_stats* stats,
+                    double* U_out, double* phi_out, double* lambda_out);
+
+/* One explicit Euler step of Sec. 4.3 from t to t + dt: solve Eq.
+ * linear_system at t (warm-started from the previous step's solution),
+ * move each articulated body's centre by dt times its mean body velocity
+ * (Eq. ucom) and each orientation by theta_{omega dt} . theta, rebuild the
+ * positions with the pseudo-inverse of the connectivity (Eq. pseudo-inv-sol,
+ * reconst-up-COM) using the link vectors at t + dt, and run the nonlinear
+ * correction (Eq. min_probl_a/b) when ||g*||^2 >= corr_tol.
+ *   dl_p_next, dl_q_next  3P each: body-frame link vectors at t + dt, or
+ *                         NULL to keep the current ones (passive links).
+ * The link derivatives for t + dt must be set by am_set_constraints before
+ * the next step.  Outputs as am_solve (values at t).
+ * Errors: as am_solve, and AM_ERR_ARG if an articulated body of several
+ * bodies is not connected by links. */
+AM_API int am_solve_step(am_handle* h, double t, double dt,
+                         const double* dl_p_next, const double* dl_q_next,
+                         am_step_stats* stats,
+                         double* U_out, double* phi_out, double* lambda_out);
+
+/* Current bodies (after the last step): q 3M, theta 4M; either may be NULL. */
+AM_API int am_get_bodies(am_handle* h, int system, double* q, double* theta);
+
+/* Current lab-frame blob positions r_i (3Nb). */
+AM_API int am_get_blobs(am_handle* h, int system, double* r);
+
+/* One blob mobility product u = M lambda at the current pose (Eq. RPY),
+ * host arrays of 3Nb.  For checking and benchmarking the hot kernel. */
+AM_API int am_apply_mobility(am_handle* h, const double* lambda, double* u);
+
+/* y -> A y for the full operator of Eq. linear_system at the current pose
+ * (y and Ay: 3Nb + 6M + 3P, ordered (lambda, U, phi)). */
+AM_API int am_apply_operator(am_handle* h, const double* y, double* Ay);
+
+/* r -> z solving the block-diagonal approximate problem (Eq. precond) at
+ * the current pose, with G~ a generalised inverse when C is
+ * rank-deficient (Eq. block_diag_const_res).  Same layout as
+ * am_apply_operator. */
+AM_API int am_apply_precond(am_handle* h, const double* r, double* z);
+
+/* Stateless blob mobility product on device memory of the current device,
+ * u = M(r) lambda (Eq. RPY), free space (wall = 0) or above a no-slip wall
+ * at z = 0 (wall = 1; every r_z must exceed a, not checked here).
+ *   d_r        3n doubles, blob centres
+ *   d_lambda   3n doubles, blob forces
+ *   d_u        3n doubles, output velocities (overwritten)
+ *   precision  AM_FP64 or AM_MIXED
+ *   d_work     scratch of at least am_rpy_matvec_workspace(n, precision)
+ *              bytes, 256-byte aligned; contents are overwritten
+ *   stream     cudaStream_t or NULL (legacy default stream)
+ * Asynchronous on `stream`.  Errors: AM_ERR_ARG (n < 0, eta or a <= 0, NULL
+ * pointer with n > 0, workspace too small or misaligned), AM_ERR_CUDA. */
+AM_API int am_rpy_matvec(const double* d_r, const double* d_lambda,
+                         double* d_u, int n, double eta, double a, int wall,
+                         int precision, void* d_work, size_t work_bytes,
+                         void* stream);
+AM_API size_t am_rpy_matvec_workspace(int n, int precision);
+
+/* Pair arithmetic of the mobility kernels, counted with FMA = 2 flops, for
+ * roofline figures: per pair of the free-space tensor and per pair of the
+ * wall tensor (free part plus image part). */
+AM_API int am_flops_per_pair(int wall);
+
+/* Device time of the all-pairs mobility kernel inside the calls of h,
+ * measured with CUDA events on the handle's stream around every launch.
+ * enable != 0 clears earlier records and starts recording; enable == 0
+ * stops recording and keeps the records.  *ms and *launches (either may be
+ * NULL) receive the total time and the number of launches recorded so far
+ * (this synchronises the stream).  Not in the paper: a measurement aid. */
+AM_API int am_mobility_timing(am_handle* h, int enable, double* ms, long long* launches);
+
+/* Throughput of independent FMA streams on the current device, the
+ * denominator of the roofline of ALU-bound kernels: fp64 = 1 measures DFMA,
+ * 0 FFMA; *flops receives FLOP/s (FMA = 2).  Takes about 0.1 s.  Not in the
+ * paper: a measurement aid. */
+AM_API int am_alu_peak(int fp64, double* flops);
+
+/* Kernels launched by this library in this process so far. */
+AM_API long long am_kernel_launches(void);
+
+/* Destroy a handle and free its device memory (NULL is a no-op). */
+AM_API void am_destroy(am_handle* h);
+
+/* Message of the last error of h, or of the calling thread's last stateless
+ * call when h is NULL; never NULL. */
+AM_API const char* am_last_error(const am_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AM_H */

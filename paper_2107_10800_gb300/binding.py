@@ -1,0 +1,289 @@
+"""ctypes binding of libam.so (include/am.h).  Argument marshalling only:
+every step of the solve runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+AM_OK = 0
+AM_ERR_ARG = -1
+AM_ERR_CUDA = -2
+AM_ERR_NOT_CONVERGED = -3
+AM_ERR_WALL_PENETRATION = -4
+AM_ERR_NONUNIT_QUAT = -5
+AM_ERR_SINGULAR = -6
+AM_FP64 = 0
+AM_MIXED = 1
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libam.so")
+
+# Every function the header declares, with its ctypes signature.
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("blob_radius", ctypes.c_double),
+                ("wall", ctypes.c_int), ("precision", ctypes.c_int),
+                ("n_systems", ctypes.c_int), ("tol", ctypes.c_double),
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("corr_tol", ctypes.c_double), ("corr_max_iter", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("constraint_residual", ctypes.c_double),
+                ("g2_before", ctypes.c_double), ("g2_after", ctypes.c_double),
+                ("corr_iterations", ctypes.c_int), ("pairs", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_int), ("ms_precond", ctypes.c_double),
+                ("ms_gmres", ctypes.c_double), ("ms_update", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SIGNATURES = {
+    "am_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(_vp)]),
+    "am_set_bodies": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _dp, _dp, _ip, _dp, _dp, _dp, _ip]),
+    "am_set_constraints": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, _dp, _dp, _dp]),
+    "am_set_joints": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip, _dp]),
+    "am_solve": (ctypes.c_int, [_vp, ctypes.POINTER(StepStats), _dp, _dp, _dp]),
+    "am_solve_step": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                                     ctypes.POINTER(StepStats), _dp, _dp, _dp]),
+    "am_get_bodies": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
+    "am_get_blobs": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "am_apply_mobility": (ctypes.c_int, [_vp, _dp, _dp]),
+    "am_apply_operator": (ctypes.c_int, [_vp, _dp, _dp]),
+    "am_apply_precond": (ctypes.c_int, [_vp, _dp, _dp]),
+    "am_rpy_matvec": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp,
+                                     ctypes.c_size_t, _vp]),
+    "am_rpy_matvec_workspace": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "am_flops_per_pair": (ctypes.c_int, [ctypes.c_int]),
+    "am_kernel_launches": (ctypes.c_longlong, []),
+    "am_mobility_timing": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "am_alu_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
+    "am_destroy": (None, [_vp]),
+    "am_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load libam.so once; raise if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libam.so is not built (call paper_2107_10800_gb300.build.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class AmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libam error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _d(a, n=None):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    if n is not None and arr.size != n:
+        raise ValueError("expected %d values, got %d" % (n, arr.size))
+    return arr, arr.ctypes.data_as(_dp)
+
+
+def _i(a):
+    arr = np.ascontiguousarray(a, dtype=np.int32).ravel()
+    return arr, arr.ctypes.data_as(_ip)
+
+
+def _out(n):
+    arr = np.empty(n, dtype=np.float64)
+    return arr, arr.ctypes.data_as(_dp)
+
+
+class Solver:
+    """One handle of the library (am_create ... am_destroy)."""
+
+    def __init__(self, eta=1.0, a=0.1, wall=0, precision="fp64", tol=1e-10, restart=50,
+                 max_iter=500, corr_tol=1e-10, corr_max_iter=20, stream=None):
+        L = lib()
+        prec = {"fp64": AM_FP64, "mixed": AM_MIXED}[precision]
+        cfg = Config(eta, a, wall, prec, 1, tol, restart, max_iter, corr_tol, corr_max_iter,
+                     stream)
+        h = _vp()
+        rc = L.am_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != AM_OK:
+            raise AmError(rc, "am_create failed (" + L.am_last_error(None).decode() + ")")
+        self.h = h
+        self.M = self.Nb = self.P = 0
+
+    def _check(self, rc, allow_nc=False):
+        if rc == AM_OK or (allow_nc and rc == AM_ERR_NOT_CONVERGED):
+            return rc
+        raise AmError(rc, lib().am_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            lib().am_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_bodies(self, q, theta, blob_offset, rho, F, assembly, slip=None):
+        M = len(np.asarray(theta).reshape(-1, 4))
+        off, off_p = _i(blob_offset)
+        Nb = int(off[-1])
+        qa, qp = _d(q, 3 * M)
+        ta, tp = _d(theta, 4 * M)
+        ra, rp = _d(rho, 3 * Nb)
+        fa, fp = _d(F, 6 * M)
+        sa, sp = _d(slip, 3 * Nb)
+        aa, ap = _i(assembly)
+        self._check(lib().am_set_bodies(self.h, 0, M, qp, tp, off_p, rp, fp, sp, ap))
+        self.M, self.Nb, self.P = M, Nb, 0
+
+    def set_constraints(self, body_p, body_q, dl_p, dl_q, dl_p_dot=None, dl_q_dot=None):
+        bp, bpp = _i(body_p)
+        bq, bqp = _i(body_q)
+        P = len(bp)
+        a1, p1 = _d(dl_p, 3 * P)
+        a2, p2 = _d(dl_q, 3 * P)
+        a3, p3 = _d(dl_p_dot, 3 * P)
+        a4, p4 = _d(dl_q_dot, 3 * P)
+        self._check(lib().am_set_constraints(self.h, 0, P, bpp, bqp, p1, p2, p3, p4))
+        self.P = P
+
+    def set_joints(self, body_p, body_q, joints):
+        bp, bpp = _i(body_p)
+        bq, bqp = _i(body_q)
+        P = len(bp)
+        ja, jp = _d(joints, 3 * P)
+        self._check(lib().am_set_joints(self.h, 0, P, bpp, bqp, jp))
+        self.P = P
+
+    @property
+    def n(self):
+        return 3 * self.Nb + 6 * self.M + 3 * self.P
+
+    def solve(self):
+        st = StepStats()
+        U, Up = _out(6 * self.M)
+        phi, pp = _out(3 * self.P)
+        lam, lp = _out(3 * self.Nb)
+        self._check(lib().am_solve(self.h, ctypes.byref(st), Up, pp, lp), allow_nc=True)
+        return U.reshape(-1, 6), phi.reshape(-1, 3), lam.reshape(-1, 3), st.as_dict()
+
+    def step(self, t, dt, dl_next=None):
+        st = StepStats()
+        U, Up = _out(6 * self.M)
+        phi, pp = _out(3 * self.P)
+        lam, lp = _out(3 * self.Nb)
+        if dl_next is None:
+            a1 = a2 = None
+            p1 = p2 = None
+        else:
+            a1, p1 = _d(dl_next[0], 3 * self.P)
+            a2, p2 = _d(dl_next[1], 3 * self.P)
+        self._check(lib().am_solve_step(self.h, t, dt, p1, p2, ctypes.byref(st), Up, pp, lp),
+                    allow_nc=True)
+        return U.reshape(-1, 6), phi.reshape(-1, 3), lam.reshape(-1, 3), st.as_dict()
+
+    def bodies(self):
+        q, qp = _out(3 * self.M)
+        th, tp = _out(4 * self.M)
+        self._check(lib().am_get_bodies(self.h, 0, qp, tp))
+        return q.reshape(-1, 3), th.reshape(-1, 4)
+
+    def blobs(self):
+        r, rp = _out(3 * self.Nb)
+        self._check(lib().am_get_blobs(self.h, 0, rp))
+        return r.reshape(-1, 3)
+
+    def apply_mobility(self, lam):
+        la, lp = _d(lam, 3 * self.Nb)
+        u, up = _out(3 * self.Nb)
+        self._check(lib().am_apply_mobility(self.h, lp, up))
+        return u.reshape(-1, 3)
+
+    def apply_operator(self, y):
+        ya, yp = _d(y, self.n)
+        o, op = _out(self.n)
+        self._check(lib().am_apply_operator(self.h, yp, op))
+        return o
+
+    def apply_precond(self, r):
+        ra, rp = _d(r, self.n)
+        o, op = _out(self.n)
+        self._check(lib().am_apply_precond(self.h, rp, op))
+        return o
+
+    def mobility_timing(self, enable):
+        """(total ms, launches) of the all-pairs kernel recorded so far;
+        enable=True clears and starts recording, False stops."""
+        ms = ctypes.c_double()
+        k = ctypes.c_longlong()
+        self._check(lib().am_mobility_timing(self.h, 1 if enable else 0, ctypes.byref(ms),
+                                             ctypes.byref(k)))
+        return ms.value, k.value
+
+    @classmethod
+    def from_workload(cls, w, t=0.0, **kw):
+        """A solver holding a workload dict of paper_2107_10800_gb300.workloads."""
+        s = cls(eta=w["eta"], a=w["a"], wall=w["wall"], **kw)
+        s.set_bodies(w["q"], w["theta"], w["blob_offset"], w["rho"], w["F"], w["assembly"])
+        if len(w["body_p"]):
+            if w.get("dl") is not None:
+                dlp, dlq, dlpd, dlqd = w["dl"](t)
+                s.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd)
+            else:
+                s.set_joints(w["body_p"], w["body_q"], w["joints"])
+        return s
+
+
+def rpy_matvec_ptr(d_r, d_lam, d_u, n, eta, a, wall, precision, d_work, work_bytes, stream=None):
+    """am_rpy_matvec on raw device pointers (ints)."""
+    prec = {"fp64": AM_FP64, "mixed": AM_MIXED}.get(precision, precision)
+    rc = lib().am_rpy_matvec(d_r, d_lam, d_u, n, eta, a, wall, prec, d_work, work_bytes, stream)
+    if rc != AM_OK:
+        raise AmError(rc, lib().am_last_error(None).decode())
+
+
+def rpy_matvec_workspace(n, precision):
+    prec = {"fp64": AM_FP64, "mixed": AM_MIXED}.get(precision, precision)
+    return int(lib().am_rpy_matvec_workspace(n, prec))
+
+
+def flops_per_pair(wall):
+    return int(lib().am_flops_per_pair(wall))
+
+
+def alu_peak(fp64):
+    """Measured FMA throughput (FLOP/s) of the current device."""
+    f = ctypes.c_double()
+    rc = lib().am_alu_peak(1 if fp64 else 0, ctypes.byref(f))
+    if rc != AM_OK:
+        raise AmError(rc, "am_alu_peak failed")
+    return f.value
+
+
+def kernel_launches():
+    return int(lib().am_kernel_launches())

@@ -1,0 +1,174 @@
+// Internal declarations of libam: handle layout, device helpers, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "am.h"
+
+namespace am {
+
+constexpr int kTile = 128;        // sources per shared-memory tile
+constexpr int kThreads = 128;     // threads per block of the pair kernels
+constexpr double kPi = 3.14159265358979323846;
+
+extern std::atomic<long long> g_launches;
+inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int num_sms();
+
+// Constants of the RPY pair tensors (free space and wall image part).
+struct RpyParams {
+    double a, a2, four_a2;
+    double inv8pieta;     // 1 / (8 pi eta)
+    double k_far2;        // inv8pieta * 2 a^2 / 3
+    double k_far3;        // inv8pieta * 2 a^2
+    double mu0;           // 1 / (6 pi eta a)
+    double k_near1;       // 9 / (32 a)
+    double k_near2;       // mu0 * 3 / (32 a)
+};
+RpyParams make_params(double eta, double a);
+
+// Source splitting of the all-pairs product: grid (target blocks, splits).
+struct Split { int splits; int chunk; };
+Split choose_split(int n, int precision);
+
+// ---- mobility product launchers (rpy.cu) ------------------------------
+// FP64: r4 = (x, y, z, 0) per blob.  Mixed: hi/lo float4 positions.
+// Writes partial sums part[s][3n] for s < splits.
+void launch_rpy_partial_f64(const double4_32a* r4, const double* lam, double* part,
+                            int n, const Split& sp, const RpyParams& prm, int wall,
+                            cudaStream_t st);
+void launch_rpy_partial_mixed(const float4* hi, const float4* lo, const double* lam,
+                              double* part, int n, const Split& sp,
+                              const RpyParams& prm, int wall, cudaStream_t st);
+void launch_pack_positions(const double* r3, double4_32a* r4, float4* hi, float4* lo,
+                           int n, cudaStream_t st);
+void launch_sum_partials(const double* part, double* u, int n, int splits,
+                         cudaStream_t st);
+
+// ---- device helpers -----------------------------------------------------
+// R(theta) v = 2 [ p (p.v) + s (p x v) + (s^2 - 1/2) v ]   (App. B, Eq. rot_mat)
+__device__ __forceinline__ void quat_rotate(double s, double px, double py, double pz,
+                                            double vx, double vy, double vz,
+                                            double& ox, double& oy, double& oz) {
+    double pv = px * vx + py * vy + pz * vz;
+    double cx = py * vz - pz * vy, cy = pz * vx - px * vz, cz = px * vy - py * vx;
+    double c = s * s - 0.5;
+    ox = 2.0 * (px * pv + s * cx + c * vx);
+    oy = 2.0 * (py * pv + s * cy + c * vy);
+    oz = 2.0 * (pz * pv + s * cz + c * vz);
+}
+// R(theta)^T v (the inverse rotation: p -> -p)
+__device__ __forceinline__ void quat_rotate_inv(double s, double px, double py, double pz,
+                                                double vx, double vy, double vz,
+                                                double& ox, double& oy, double& oz) {
+    quat_rotate(s, -px, -py, -pz, vx, vy, vz, ox, oy, oz);
+}
+// theta_2 . theta_1 (Eq. quaternion_mult)
+__device__ __forceinline__ void quat_mul(const double* t2, const double* t1, double* o) {
+    double s2 = t2[0], s1 = t1[0];
+    o[0] = s2 * s1 - (t2[1] * t1[1] + t2[2] * t1[2] + t2[3] * t1[3]);
+    o[1] = s2 * t1[1] + s1 * t2[1] + (t2[2] * t1[3] - t2[3] * t1[2]);
+    o[2] = s2 * t1[2] + s1 * t2[2] + (t2[3] * t1[1] - t2[1] * t1[3]);
+    o[3] = s2 * t1[3] + s1 * t2[3] + (t2[1] * t1[2] - t2[2] * t1[1]);
+}
+// theta_gamma = [cos(g/2), sin(g/2) gamma / g]  (Sec. 2.1)
+__device__ __forceinline__ void quat_from_rotvec(double gx, double gy, double gz, double* o) {
+    double g = sqrt(gx * gx + gy * gy + gz * gz);
+    double sg, cg;
+    sincos(0.5 * g, &sg, &cg);
+    double f = (g > 1e-8) ? sg / g : 0.5 - g * g / 48.0;
+    o[0] = cg; o[1] = f * gx; o[2] = f * gy; o[3] = f * gz;
+}
+
+}  // namespace am
+
+// ---- the handle -----------------------------------------------------------
+struct am_handle {
+    am_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    am::RpyParams prm{};
+
+    // sizes
+    int M = 0, Nb = 0, P = 0, NA = 0, n = 0;
+    bool have_bodies = false;
+
+    // host structure
+    std::vector<int> blob_off, asm_of_body, bp, bq;
+    std::vector<int> asm_body_off, asm_body_idx, asm_link_off, asm_link_idx;
+    std::vector<long long> minv_off, G_off, pplus_off, corr_off;
+    std::vector<int> G_dim;
+    long long minv_total = 0, G_total = 0, pplus_total = 0, corr_total = 0;
+    int max_body_blobs = 0;
+    bool active_links = false;
+    bool links_connected = true;
+
+    // device: bodies
+    double *d_q = nullptr, *d_theta = nullptr, *d_rho = nullptr, *d_F = nullptr,
+           *d_slip = nullptr;
+    int *d_blob_off = nullptr, *d_body_of_blob = nullptr, *d_asm_of_body = nullptr;
+    int *d_asm_body_off = nullptr, *d_asm_body_idx = nullptr;
+    double4_32a *d_r4 = nullptr, *d_d4 = nullptr;   // lab positions, R(theta) rho
+    float4 *d_rhi = nullptr, *d_rlo = nullptr;  // mixed-precision positions
+    double* d_r3 = nullptr;                     // lab positions, 3Nb (get_blobs)
+
+    // device: links
+    int *d_bp = nullptr, *d_bq = nullptr;
+    double *d_dlp = nullptr, *d_dlq = nullptr, *d_dlpd = nullptr, *d_dlqd = nullptr;
+    double *d_dlp1 = nullptr, *d_dlq1 = nullptr;     // link vectors at t + dt
+    double *d_lp = nullptr, *d_lq = nullptr, *d_B = nullptr;
+    int *d_body_link_off = nullptr, *d_body_link_idx = nullptr;
+    int *d_asm_link_off = nullptr, *d_asm_link_idx = nullptr, *d_link_local = nullptr;
+    double* d_pplus = nullptr; long long* d_pplus_off = nullptr;
+    int* d_body_local = nullptr;
+
+    // device: preconditioner
+    double *d_minv = nullptr, *d_pcwork = nullptr, *d_Y = nullptr, *d_Nt = nullptr;
+    long long* d_minv_off = nullptr;
+    double* d_G = nullptr; double* d_Gwork = nullptr;
+    long long* d_G_off = nullptr; int* d_G_rank = nullptr;
+    int* d_perm = nullptr; long long* d_perm_off = nullptr;
+    double *d_pc_w = nullptr, *d_pc_Uhat = nullptr;
+    bool pc_valid = false;
+
+    // device: solver vectors
+    double *d_b = nullptr, *d_x = nullptr, *d_xprev = nullptr, *d_t = nullptr,
+           *d_z = nullptr, *d_w = nullptr, *d_V = nullptr;
+    double *d_Hm = nullptr, *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr,
+           *d_coef = nullptr, *d_part = nullptr, *d_scal = nullptr, *d_xi = nullptr,
+           *d_npart = nullptr, *d_rir = nullptr, *d_dx = nullptr;
+    int restart = 50;
+    int ldv = 0;
+    long long pairs = 0;
+    bool have_warm = false;
+
+    // device: mobility partial sums
+    double* d_mv = nullptr;
+    am::Split split{1, 0};
+
+    // device: step
+    double *d_qnew = nullptr, *d_thnew = nullptr, *d_corr = nullptr, *d_red = nullptr;
+    double *d_zbuf = nullptr, *d_cbuf = nullptr;
+    long long* d_corr_off = nullptr;
+    int* d_iters = nullptr;
+    int* d_flags = nullptr;
+
+    // host staging (pinned)
+    double* h_scal = nullptr;
+    int* h_flags = nullptr;
+    int* h_iters = nullptr;
+
+    cudaEvent_t ev[8] = {};
+    bool geometry_valid = false;
+
+    // per-launch timing of the all-pairs kernel (am_mobility_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;   // start/stop pairs
+    size_t tev_used = 0;
+};

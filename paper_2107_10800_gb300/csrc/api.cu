@@ -1,0 +1,751 @@
+// C ABI of libam (declared in include/am.h): argument checks, device memory,
+// set-up precomputation and the call sequence of a solve and of a step.
+#include "am_internal.cuh"
+#include "ops.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+namespace am {
+const char* thread_error();
+}
+
+namespace {
+
+int set_err(am_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return set_err(h, AM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+template <class T>
+void dfree(T** p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+template <class T>
+cudaError_t h2d(T* d, const T* hsrc, size_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    return cudaMemcpyAsync(d, hsrc, count * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+template <class T>
+cudaError_t d2h(T* hdst, const T* d, size_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    return cudaMemcpyAsync(hdst, d, count * sizeof(T), cudaMemcpyDeviceToHost, s);
+}
+
+// Host rotation R(theta) v (App. B, Eq. rot_mat), for set-up only.
+void host_rotate(const double* th, const double* v, double* o, bool transpose) {
+    const double s = th[0];
+    const double sg = transpose ? -1.0 : 1.0;
+    const double p[3] = {sg * th[1], sg * th[2], sg * th[3]};
+    const double pv = p[0] * v[0] + p[1] * v[1] + p[2] * v[2];
+    const double c[3] = {p[1] * v[2] - p[2] * v[1], p[2] * v[0] - p[0] * v[2], p[0] * v[1] - p[1] * v[0]};
+    const double k = s * s - 0.5;
+    for (int a = 0; a < 3; ++a) o[a] = 2.0 * (p[a] * pv + s * c[a] + k * v[a]);
+}
+
+// Inverse of a small dense n x n matrix by Gauss-Jordan with partial
+// pivoting; false if singular.
+bool host_inverse(std::vector<double>& A, int n) {
+    std::vector<double> I(static_cast<size_t>(n) * n, 0.0);
+    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+        if (!(std::fabs(A[(size_t)piv * n + c]) > 1e-300)) return false;
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(A[(size_t)piv * n + k], A[(size_t)c * n + k]);
+                std::swap(I[(size_t)piv * n + k], I[(size_t)c * n + k]);
+            }
+        const double d = 1.0 / A[(size_t)c * n + c];
+        for (int k = 0; k < n; ++k) { A[(size_t)c * n + k] *= d; I[(size_t)c * n + k] *= d; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[(size_t)r * n + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+                I[(size_t)r * n + k] -= f * I[(size_t)c * n + k];
+            }
+        }
+    }
+    A.swap(I);
+    return true;
+}
+
+void free_links(am_handle* h) {
+    dfree(&h->d_bp); dfree(&h->d_bq); dfree(&h->d_dlp); dfree(&h->d_dlq);
+    dfree(&h->d_dlpd); dfree(&h->d_dlqd); dfree(&h->d_dlp1); dfree(&h->d_dlq1);
+    dfree(&h->d_lp); dfree(&h->d_lq); dfree(&h->d_B);
+    dfree(&h->d_body_link_off); dfree(&h->d_body_link_idx);
+    dfree(&h->d_asm_link_off); dfree(&h->d_asm_link_idx); dfree(&h->d_link_local);
+    dfree(&h->d_pplus); dfree(&h->d_pplus_off);
+    dfree(&h->d_G); dfree(&h->d_Gwork); dfree(&h->d_G_off); dfree(&h->d_G_rank);
+    dfree(&h->d_perm); dfree(&h->d_perm_off);
+    dfree(&h->d_corr); dfree(&h->d_corr_off); dfree(&h->d_zbuf); dfree(&h->d_cbuf);
+}
+
+void free_bodies(am_handle* h) {
+    dfree(&h->d_q); dfree(&h->d_theta); dfree(&h->d_rho); dfree(&h->d_F); dfree(&h->d_slip);
+    dfree(&h->d_blob_off); dfree(&h->d_body_of_blob); dfree(&h->d_asm_of_body);
+    dfree(&h->d_asm_body_off); dfree(&h->d_asm_body_idx); dfree(&h->d_body_local);
+    dfree(&h->d_r4); dfree(&h->d_d4); dfree(&h->d_rhi); dfree(&h->d_rlo); dfree(&h->d_r3);
+    dfree(&h->d_minv); dfree(&h->d_pcwork); dfree(&h->d_Y); dfree(&h->d_Nt); dfree(&h->d_minv_off);
+    dfree(&h->d_pc_w); dfree(&h->d_pc_Uhat); dfree(&h->d_mv);
+    dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters);
+}
+
+void free_solver(am_handle* h) {
+    dfree(&h->d_b); dfree(&h->d_x); dfree(&h->d_xprev); dfree(&h->d_t); dfree(&h->d_z);
+    dfree(&h->d_w); dfree(&h->d_V); dfree(&h->d_rir); dfree(&h->d_dx);
+    dfree(&h->d_Hm); dfree(&h->d_cs); dfree(&h->d_sn); dfree(&h->d_g); dfree(&h->d_coef);
+    dfree(&h->d_xi); dfree(&h->d_part); dfree(&h->d_npart);
+}
+
+int alloc_solver(am_handle* h) {
+    const int n = h->n;
+    const int m = h->restart;
+    h->ldv = (n + 31) & ~31;
+    CK(dalloc(&h->d_b, n)); CK(dalloc(&h->d_x, n)); CK(dalloc(&h->d_xprev, n));
+    CK(dalloc(&h->d_t, n)); CK(dalloc(&h->d_z, n)); CK(dalloc(&h->d_w, n));
+    CK(dalloc(&h->d_rir, n)); CK(dalloc(&h->d_dx, n));
+    CK(dalloc(&h->d_V, (size_t)h->ldv * (m + 1)));
+    CK(dalloc(&h->d_Hm, (size_t)(m + 1) * m)); CK(dalloc(&h->d_cs, m)); CK(dalloc(&h->d_sn, m));
+    CK(dalloc(&h->d_g, m + 1)); CK(dalloc(&h->d_coef, m + 1)); CK(dalloc(&h->d_xi, m + 1));
+    CK(dalloc(&h->d_part, (size_t)(m + 1) * 64)); CK(dalloc(&h->d_npart, 4 * am::num_sms() + 64));
+    h->have_warm = false;
+    return AM_OK;
+}
+
+// Links and everything that depends on them.  Empty (P = 0) is valid.
+int build_links(am_handle* h, int P, const int* bp, const int* bq) {
+    const int M = h->M, NA = h->NA;
+    free_links(h);
+    h->P = P;
+    h->bp.assign(bp, bp + P);
+    h->bq.assign(bq, bq + P);
+    // body -> link CSR (code = 2 n + side, side 1 = the link's body q)
+    std::vector<int> bl_off(M + 1, 0), bl_idx(2 * (size_t)P);
+    for (int n = 0; n < P; ++n) { bl_off[bp[n] + 1]++; bl_off[bq[n] + 1]++; }
+    for (int p = 0; p < M; ++p) bl_off[p + 1] += bl_off[p];
+    {
+        std::vector<int> fill(bl_off.begin(), bl_off.end() - 1);
+        for (int n = 0; n < P; ++n) {
+            bl_idx[fill[bp[n]]++] = 2 * n;
+            bl_idx[fill[bq[n]]++] = 2 * n + 1;
+        }
+    }
+    // assembly -> link CSR, link position within its assembly
+    std::vector<int> al_off(NA + 1, 0), al_idx(P), link_local(P);
+    for (int n = 0; n < P; ++n) al_off[h->asm_of_body[bp[n]] + 1]++;
+    for (int a = 0; a < NA; ++a) al_off[a + 1] += al_off[a];
+    {
+        std::vector<int> fill(al_off.begin(), al_off.end() - 1);
+        for (int n = 0; n < P; ++n) {
+            const int a = h->asm_of_body[bp[n]];
+            link_local[n] = fill[a] - al_off[a];
+            al_idx[fill[a]++] = n;
+        }
+    }
+    h->asm_link_off = al_off;
+    h->asm_link_idx = al_idx;
+    // connectivity: bodies of every articulated body joined by its links
+    std::vector<int> parent(M);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int x) {
+        while (parent[x] != x) x = parent[x] = parent[parent[x]];
+        return x;
+    };
+    for (int n = 0; n < P; ++n) parent[find(bp[n])] = find(bq[n]);
+    h->links_connected = true;
+    for (int a = 0; a < NA; ++a) {
+        const int b0 = h->asm_body_idx[h->asm_body_off[a]];
+        for (int k = h->asm_body_off[a]; k < h->asm_body_off[a + 1]; ++k)
+            if (find(h->asm_body_idx[k]) != find(b0)) {
+                h->links_connected = false;
+                if (P > 0)
+                    return set_err(h, AM_ERR_ARG, "am_set_constraints: articulated body " + std::to_string(a) +
+                                                      " is not connected by its links");
+            }
+    }
+    // (P^a)^+ = L^+ (P^a)^T with L = (P^a)^T P^a the graph Laplacian of the
+    // articulated body and L^+ = (L + J/M_a)^-1 - J/M_a (J all ones) for a
+    // connected graph (Sec. 4.1, Eq. pseudo-inv-sol).  Rows follow the
+    // assembly's body order, columns its link order.
+    std::vector<long long> poff(NA + 1, 0);
+    for (int a = 0; a < NA; ++a) {
+        const long long Ma = h->asm_body_off[a + 1] - h->asm_body_off[a];
+        const long long Pa = al_off[a + 1] - al_off[a];
+        poff[a + 1] = poff[a] + Ma * Pa;
+    }
+    std::vector<double> pplus(std::max<long long>(poff[NA], 1), 0.0);
+    std::vector<int> local(M);
+    for (int a = 0; a < NA; ++a)
+        for (int k = h->asm_body_off[a]; k < h->asm_body_off[a + 1]; ++k)
+            local[h->asm_body_idx[k]] = k - h->asm_body_off[a];
+    for (int a = 0; a < NA; ++a) {
+        const int Ma = h->asm_body_off[a + 1] - h->asm_body_off[a];
+        const int Pa = al_off[a + 1] - al_off[a];
+        if (Pa == 0) continue;
+        std::vector<double> Ps((size_t)Pa * Ma, 0.0);
+        for (int k = 0; k < Pa; ++k) {
+            const int n = al_idx[al_off[a] + k];
+            Ps[(size_t)k * Ma + local[bp[n]]] += 1.0;
+            Ps[(size_t)k * Ma + local[bq[n]]] -= 1.0;
+        }
+        std::vector<double> L((size_t)Ma * Ma, 0.0);
+        for (int i = 0; i < Ma; ++i)
+            for (int j = 0; j < Ma; ++j) {
+                double s = 1.0 / Ma;
+                for (int k = 0; k < Pa; ++k) s += Ps[(size_t)k * Ma + i] * Ps[(size_t)k * Ma + j];
+                L[(size_t)i * Ma + j] = s;
+            }
+        if (!host_inverse(L, Ma)) return set_err(h, AM_ERR_ARG, "am_set_constraints: singular connectivity");
+        for (int i = 0; i < Ma; ++i)
+            for (int k = 0; k < Pa; ++k) {
+                double s = 0.0;
+                for (int j = 0; j < Ma; ++j) s += (L[(size_t)i * Ma + j] - 1.0 / Ma) * Ps[(size_t)k * Ma + j];
+                pplus[poff[a] + (size_t)i * Pa + k] = s;
+            }
+    }
+    // sizes of the per-assembly preconditioner and correction workspaces
+    std::vector<long long> goff(NA + 1, 0), permoff(NA + 1, 0), coff(NA + 1, 0);
+    for (int a = 0; a < NA; ++a) {
+        const long long m = 3LL * (al_off[a + 1] - al_off[a]);
+        const long long Ma = h->asm_body_off[a + 1] - h->asm_body_off[a];
+        const long long nd = 7 * Ma;
+        goff[a + 1] = goff[a] + m * m;
+        permoff[a + 1] = permoff[a] + m;
+        coff[a + 1] = coff[a] + (m ? nd * nd + 3 * nd + 3 * m : 0);
+    }
+    cudaStream_t s = h->stream;
+    CK(dalloc(&h->d_bp, P)); CK(dalloc(&h->d_bq, P));
+    CK(dalloc(&h->d_dlp, 3 * (size_t)P)); CK(dalloc(&h->d_dlq, 3 * (size_t)P));
+    CK(dalloc(&h->d_dlpd, 3 * (size_t)P)); CK(dalloc(&h->d_dlqd, 3 * (size_t)P));
+    CK(dalloc(&h->d_dlp1, 3 * (size_t)P)); CK(dalloc(&h->d_dlq1, 3 * (size_t)P));
+    CK(dalloc(&h->d_lp, 3 * (size_t)P)); CK(dalloc(&h->d_lq, 3 * (size_t)P));
+    CK(dalloc(&h->d_B, 3 * (size_t)P));
+    CK(dalloc(&h->d_body_link_off, M + 1)); CK(dalloc(&h->d_body_link_idx, 2 * (size_t)P));
+    CK(dalloc(&h->d_asm_link_off, NA + 1)); CK(dalloc(&h->d_asm_link_idx, P));
+    CK(dalloc(&h->d_link_local, P));
+    CK(dalloc(&h->d_pplus, pplus.size())); CK(dalloc(&h->d_pplus_off, NA + 1));
+    CK(dalloc(&h->d_G, goff[NA])); CK(dalloc(&h->d_Gwork, 2 * goff[NA]));
+    CK(dalloc(&h->d_G_off, NA + 1)); CK(dalloc(&h->d_G_rank, NA));
+    CK(dalloc(&h->d_perm, permoff[NA])); CK(dalloc(&h->d_perm_off, NA + 1));
+    CK(dalloc(&h->d_corr, coff[NA])); CK(dalloc(&h->d_corr_off, NA + 1));
+    CK(dalloc(&h->d_zbuf, 3 * (size_t)P)); CK(dalloc(&h->d_cbuf, 3 * (size_t)P));
+    CK(h2d(h->d_bp, bp, P, s)); CK(h2d(h->d_bq, bq, P, s));
+    CK(h2d(h->d_body_link_off, bl_off.data(), M + 1, s));
+    CK(h2d(h->d_body_link_idx, bl_idx.data(), bl_idx.size(), s));
+    CK(h2d(h->d_asm_link_off, al_off.data(), NA + 1, s));
+    CK(h2d(h->d_asm_link_idx, al_idx.data(), P, s));
+    CK(h2d(h->d_link_local, link_local.data(), P, s));
+    CK(h2d(h->d_pplus, pplus.data(), pplus.size(), s));
+    CK(h2d(h->d_pplus_off, poff.data(), NA + 1, s));
+    CK(h2d(h->d_G_off, goff.data(), NA + 1, s));
+    CK(h2d(h->d_perm_off, permoff.data(), NA + 1, s));
+    CK(h2d(h->d_corr_off, coff.data(), NA + 1, s));
+    CK(cudaStreamSynchronize(s));
+    h->n = 3 * h->Nb + 6 * h->M + 3 * P;
+    h->pc_valid = false;
+    return alloc_solver(h);
+}
+
+int check_quats(am_handle* h, int M, const double* theta, const char* who) {
+    for (int p = 0; p < M; ++p) {
+        const double* t = theta + 4 * (size_t)p;
+        const double nn = std::sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
+        if (!(std::fabs(nn - 1.0) <= 1e-8))
+            return set_err(h, AM_ERR_NONUNIT_QUAT, std::string(who) + ": quaternion of body " +
+                                                       std::to_string(p) + " is not unit");
+    }
+    return AM_OK;
+}
+
+int device_flags_to_status(am_handle* h, const char* who) {
+    const int f = am::take_flags(h);
+    if (f & am::kFlagWall)
+        return set_err(h, AM_ERR_WALL_PENETRATION, std::string(who) + ": a blob centre is at or below height a");
+    if (f & am::kFlagSingular)
+        return set_err(h, AM_ERR_SINGULAR, std::string(who) +
+                                               ": a body's blob mobility or body mobility is not positive definite "
+                                               "(bodies need at least three non-collinear blobs)");
+    if (f & am::kFlagCorrection)
+        return set_err(h, AM_ERR_SINGULAR, std::string(who) + ": correction normal equations not positive definite");
+    return AM_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+// pose, preconditioner and initial guess at the current configuration
+int prepare(am_handle* h, const char* who, bool warm, am_step_stats* st) {
+    cudaStream_t s = h->stream;
+    am::launch_geometry(h);
+    CK(cudaEventRecord(h->ev[0], s));
+    am::pc_build(h);
+    CK(cudaEventRecord(h->ev[1], s));
+    CK(cudaGetLastError());
+    int rc = device_flags_to_status(h, who);
+    if (rc) return rc;
+    if (warm && h->have_warm) {
+        CK(cudaMemcpyAsync(h->d_x, h->d_xprev, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        am::project_constraints(h, h->d_x);
+    } else {
+        am::pc_apply(h, h->d_b, h->d_x);
+    }
+    CK(cudaGetLastError());
+    if (st) st->ms_precond = elapsed(h->ev[0], h->ev[1]);
+    return AM_OK;
+}
+
+int copy_outputs(am_handle* h, double* U, double* phi, double* lam) {
+    cudaStream_t s = h->stream;
+    if (lam) CK(d2h(lam, h->d_x, 3 * (size_t)h->Nb, s));
+    if (U) CK(d2h(U, h->d_x + 3 * (size_t)h->Nb, 6 * (size_t)h->M, s));
+    if (phi) CK(d2h(phi, h->d_x + 3 * (size_t)h->Nb + 6 * (size_t)h->M, 3 * (size_t)h->P, s));
+    CK(cudaStreamSynchronize(s));
+    return AM_OK;
+}
+
+int check_handle(am_handle* h, const char* who, bool need_bodies) {
+    if (!h) { return AM_ERR_ARG; }
+    if (need_bodies && !h->have_bodies) return set_err(h, AM_ERR_ARG, std::string(who) + ": no bodies set");
+    return AM_OK;
+}
+
+}  // namespace
+
+extern "C" AM_API int am_create(const am_config* cfg, am_handle** out) {
+    if (!cfg || !out) return AM_ERR_ARG;
+    *out = nullptr;
+    am_config c = *cfg;
+    if (c.restart == 0) c.restart = 50;
+    if (c.max_iter == 0) c.max_iter = 500;
+    if (c.corr_tol == 0.0) c.corr_tol = 1e-10;
+    if (c.corr_max_iter == 0) c.corr_max_iter = 20;
+    if (c.n_systems == 0) c.n_systems = 1;
+    if (!(c.eta > 0.0) || !(c.blob_radius > 0.0) || (c.wall != 0 && c.wall != 1) ||
+        (c.precision != AM_FP64 && c.precision != AM_MIXED) || c.n_systems != 1 || !(c.tol > 0.0) ||
+        c.restart < 1 || c.restart > 200 || c.max_iter < 1 || !(c.corr_tol > 0.0) || c.corr_max_iter < 1)
+        return AM_ERR_ARG;
+    am_handle* h = new am_handle();
+    h->cfg = c;
+    h->restart = c.restart;
+    h->prm = am::make_params(c.eta, c.blob_radius);
+    if (c.cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(c.cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return AM_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    bool ok = cudaMallocHost(reinterpret_cast<void**>(&h->h_scal), 16 * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(reinterpret_cast<void**>(&h->h_flags), sizeof(int)) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&h->d_scal), 16 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&h->d_flags), sizeof(int)) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&h->d_red), 4 * sizeof(double)) == cudaSuccess &&
+              cudaMemset(h->d_flags, 0, sizeof(int)) == cudaSuccess;
+    for (int k = 0; k < 8 && ok; ++k) ok = cudaEventCreate(&h->ev[k]) == cudaSuccess;
+    if (!ok) {
+        am_destroy(h);
+        return AM_ERR_CUDA;
+    }
+    *out = h;
+    return AM_OK;
+}
+
+extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const double* q, const double* theta,
+                                    const int* blob_offset, const double* rho, const double* F,
+                                    const double* slip, const int* asm_of_body) {
+    if (!h) return AM_ERR_ARG;
+    const char* who = "am_set_bodies";
+    if (system != 0) return set_err(h, AM_ERR_ARG, "am_set_bodies: system out of range");
+    if (M <= 0 || !q || !theta || !blob_offset || !rho || !F || !asm_of_body)
+        return set_err(h, AM_ERR_ARG, "am_set_bodies: n_bodies <= 0 or NULL array");
+    if (blob_offset[0] != 0) return set_err(h, AM_ERR_ARG, "am_set_bodies: blob_offset[0] != 0");
+    int maxb = 0;
+    for (int p = 0; p < M; ++p) {
+        const int c = blob_offset[p + 1] - blob_offset[p];
+        if (c < 1) return set_err(h, AM_ERR_ARG, "am_set_bodies: body without blobs");
+        maxb = std::max(maxb, c);
+    }
+    const long long Nb = blob_offset[M];
+    if (Nb > (1LL << 28)) return set_err(h, AM_ERR_ARG, "am_set_bodies: too many blobs");
+    int NA = 0;
+    for (int p = 0; p < M; ++p) {
+        if (asm_of_body[p] < 0 || asm_of_body[p] >= M)
+            return set_err(h, AM_ERR_ARG, "am_set_bodies: assembly index out of range");
+        NA = std::max(NA, asm_of_body[p] + 1);
+    }
+    std::vector<int> cnt(NA, 0);
+    for (int p = 0; p < M; ++p) cnt[asm_of_body[p]]++;
+    for (int a = 0; a < NA; ++a)
+        if (!cnt[a]) return set_err(h, AM_ERR_ARG, "am_set_bodies: unused assembly index");
+    int rc = check_quats(h, M, theta, who);
+    if (rc) return rc;
+
+    free_links(h);
+    free_bodies(h);
+    free_solver(h);
+    h->have_bodies = false;
+    h->M = M;
+    h->Nb = (int)Nb;
+    h->NA = NA;
+    h->P = 0;
+    h->max_body_blobs = maxb;
+    h->blob_off.assign(blob_offset, blob_offset + M + 1);
+    h->asm_of_body.assign(asm_of_body, asm_of_body + M);
+    h->asm_body_off.assign(NA + 1, 0);
+    for (int a = 0; a < NA; ++a) h->asm_body_off[a + 1] = h->asm_body_off[a] + cnt[a];
+    h->asm_body_idx.assign(M, 0);
+    std::vector<int> body_local(M);
+    {
+        std::vector<int> fill(h->asm_body_off.begin(), h->asm_body_off.end() - 1);
+        for (int p = 0; p < M; ++p) {
+            const int a = asm_of_body[p];
+            body_local[p] = fill[a] - h->asm_body_off[a];
+            h->asm_body_idx[fill[a]++] = p;
+        }
+    }
+    std::vector<int> body_of_blob(Nb);
+    std::vector<long long> moff(M + 1, 0);
+    for (int p = 0; p < M; ++p) {
+        for (int i = blob_offset[p]; i < blob_offset[p + 1]; ++i) body_of_blob[i] = p;
+        const long long m = 3LL * (blob_offset[p + 1] - blob_offset[p]);
+        moff[p + 1] = moff[p] + m * m;
+    }
+    h->minv_total = moff[M];
+    h->split = am::choose_split((int)Nb, h->cfg.precision);
+    cudaStream_t s = h->stream;
+    CK(dalloc(&h->d_q, 3 * (size_t)M)); CK(dalloc(&h->d_theta, 4 * (size_t)M));
+    CK(dalloc(&h->d_rho, 3 * (size_t)Nb)); CK(dalloc(&h->d_F, 6 * (size_t)M));
+    if (slip) CK(dalloc(&h->d_slip, 3 * (size_t)Nb));
+    CK(dalloc(&h->d_blob_off, M + 1)); CK(dalloc(&h->d_body_of_blob, Nb));
+    CK(dalloc(&h->d_asm_of_body, M)); CK(dalloc(&h->d_asm_body_off, NA + 1));
+    CK(dalloc(&h->d_asm_body_idx, M)); CK(dalloc(&h->d_body_local, M));
+    CK(dalloc(&h->d_r4, Nb)); CK(dalloc(&h->d_d4, Nb)); CK(dalloc(&h->d_rhi, Nb));
+    CK(dalloc(&h->d_rlo, Nb)); CK(dalloc(&h->d_r3, 3 * (size_t)Nb));
+    CK(dalloc(&h->d_minv, h->minv_total)); CK(dalloc(&h->d_pcwork, 2 * h->minv_total));
+    CK(dalloc(&h->d_Y, 18 * (size_t)Nb)); CK(dalloc(&h->d_Nt, 36 * (size_t)M));
+    CK(dalloc(&h->d_minv_off, M + 1)); CK(dalloc(&h->d_pc_w, 3 * (size_t)Nb));
+    CK(dalloc(&h->d_pc_Uhat, 6 * (size_t)M));
+    CK(dalloc(&h->d_mv, (size_t)h->split.splits * 3 * Nb));
+    CK(dalloc(&h->d_qnew, 3 * (size_t)M)); CK(dalloc(&h->d_thnew, 4 * (size_t)M));
+    CK(dalloc(&h->d_iters, NA));
+    if (h->h_iters) cudaFreeHost(h->h_iters);
+    h->h_iters = nullptr;
+    CK(cudaMallocHost(reinterpret_cast<void**>(&h->h_iters), std::max(NA, 1) * sizeof(int)));
+    CK(h2d(h->d_q, q, 3 * (size_t)M, s)); CK(h2d(h->d_theta, theta, 4 * (size_t)M, s));
+    CK(h2d(h->d_rho, rho, 3 * (size_t)Nb, s)); CK(h2d(h->d_F, F, 6 * (size_t)M, s));
+    if (slip) CK(h2d(h->d_slip, slip, 3 * (size_t)Nb, s));
+    CK(h2d(h->d_blob_off, blob_offset, M + 1, s));
+    CK(h2d(h->d_body_of_blob, body_of_blob.data(), Nb, s));
+    CK(h2d(h->d_asm_of_body, asm_of_body, M, s));
+    CK(h2d(h->d_asm_body_off, h->asm_body_off.data(), NA + 1, s));
+    CK(h2d(h->d_asm_body_idx, h->asm_body_idx.data(), M, s));
+    CK(h2d(h->d_body_local, body_local.data(), M, s));
+    CK(h2d(h->d_minv_off, moff.data(), M + 1, s));
+    CK(cudaStreamSynchronize(s));
+    rc = build_links(h, 0, nullptr, nullptr);
+    if (rc) return rc;
+    h->have_bodies = true;
+    am::launch_geometry(h);
+    CK(cudaGetLastError());
+    rc = device_flags_to_status(h, who);
+    if (rc) {
+        h->have_bodies = false;
+        return rc;
+    }
+    return AM_OK;
+}
+
+extern "C" AM_API int am_set_constraints(am_handle* h, int system, int P, const int* bp, const int* bq,
+                                         const double* dlp, const double* dlq, const double* dlpd,
+                                         const double* dlqd) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_set_constraints", true);
+    if (rc) return rc;
+    if (system != 0) return set_err(h, AM_ERR_ARG, "am_set_constraints: system out of range");
+    if (P < 0 || (P > 0 && (!bp || !bq || !dlp || !dlq)))
+        return set_err(h, AM_ERR_ARG, "am_set_constraints: n_links < 0 or NULL array");
+    if ((dlpd == nullptr) != (dlqd == nullptr))
+        return set_err(h, AM_ERR_ARG, "am_set_constraints: give both link derivatives or neither");
+    for (int n = 0; n < P; ++n) {
+        if (bp[n] < 0 || bp[n] >= h->M || bq[n] < 0 || bq[n] >= h->M)
+            return set_err(h, AM_ERR_ARG, "am_set_constraints: body index out of range");
+        if (bp[n] == bq[n]) return set_err(h, AM_ERR_ARG, "am_set_constraints: link joins a body to itself");
+        if (h->asm_of_body[bp[n]] != h->asm_of_body[bq[n]])
+            return set_err(h, AM_ERR_ARG, "am_set_constraints: link joins two articulated bodies");
+    }
+    const bool same = (P == h->P) && std::equal(bp, bp + P, h->bp.begin()) &&
+                      std::equal(bq, bq + P, h->bq.begin());
+    if (!same) {
+        rc = build_links(h, P, bp, bq);
+        if (rc) return rc;
+    }
+    cudaStream_t s = h->stream;
+    CK(h2d(h->d_dlp, dlp, 3 * (size_t)P, s));
+    CK(h2d(h->d_dlq, dlq, 3 * (size_t)P, s));
+    h->active_links = dlpd != nullptr;
+    if (dlpd) {
+        CK(h2d(h->d_dlpd, dlpd, 3 * (size_t)P, s));
+        CK(h2d(h->d_dlqd, dlqd, 3 * (size_t)P, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    h->pc_valid = false;
+    return AM_OK;
+}
+
+extern "C" AM_API int am_set_joints(am_handle* h, int system, int P, const int* bp, const int* bq,
+                                    const double* joint) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_set_joints", true);
+    if (rc) return rc;
+    if (P < 0 || (P > 0 && (!bp || !bq || !joint)))
+        return set_err(h, AM_ERR_ARG, "am_set_joints: n_links < 0 or NULL array");
+    std::vector<double> q(3 * (size_t)h->M), th(4 * (size_t)h->M);
+    cudaStream_t s = h->stream;
+    CK(d2h(q.data(), h->d_q, q.size(), s));
+    CK(d2h(th.data(), h->d_theta, th.size(), s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> dlp(3 * (size_t)P), dlq(3 * (size_t)P);
+    for (int n = 0; n < P; ++n) {
+        if (bp[n] < 0 || bp[n] >= h->M || bq[n] < 0 || bq[n] >= h->M)
+            return set_err(h, AM_ERR_ARG, "am_set_joints: body index out of range");
+        double v[3];
+        for (int a = 0; a < 3; ++a) v[a] = joint[3 * n + a] - q[3 * bp[n] + a];
+        host_rotate(&th[4 * bp[n]], v, &dlp[3 * n], true);
+        for (int a = 0; a < 3; ++a) v[a] = joint[3 * n + a] - q[3 * bq[n] + a];
+        host_rotate(&th[4 * bq[n]], v, &dlq[3 * n], true);
+    }
+    return am_set_constraints(h, system, P, bp, bq, dlp.data(), dlq.data(), nullptr, nullptr);
+}
+
+extern "C" AM_API int am_solve(am_handle* h, am_step_stats* stats, double* U, double* phi, double* lam) {
+    if (!h) return AM_ERR_ARG;
+    am_step_stats st{};
+    int rc = check_handle(h, "am_solve", true);
+    if (rc) return rc;
+    const long long l0 = am::g_launches.load();
+    h->pairs = 0;
+    rc = prepare(h, "am_solve", false, &st);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev[2], h->stream));
+    rc = am::solve(h, &st);
+    CK(cudaEventRecord(h->ev[3], h->stream));
+    CK(cudaGetLastError());
+    int rc2 = copy_outputs(h, U, phi, lam);
+    if (rc2) return rc2;
+    st.ms_gmres = elapsed(h->ev[2], h->ev[3]);
+    st.pairs = h->pairs;
+    st.kernel_launches = (int)(am::g_launches.load() - l0);
+    st.status = rc;
+    if (stats) *stats = st;
+    if (rc == AM_ERR_NOT_CONVERGED) set_err(h, rc, "am_solve: GMRES did not reach the tolerance");
+    return rc;
+}
+
+extern "C" AM_API int am_solve_step(am_handle* h, double t, double dt, const double* dlp_next,
+                                    const double* dlq_next, am_step_stats* stats, double* U, double* phi,
+                                    double* lam) {
+    if (!h) return AM_ERR_ARG;
+    (void)t;
+    am_step_stats st{};
+    int rc = check_handle(h, "am_solve_step", true);
+    if (rc) return rc;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(h, AM_ERR_ARG, "am_solve_step: dt must be > 0");
+    if ((dlp_next == nullptr) != (dlq_next == nullptr))
+        return set_err(h, AM_ERR_ARG, "am_solve_step: give both next link vectors or neither");
+    if (!h->links_connected)
+        return set_err(h, AM_ERR_ARG, "am_solve_step: an articulated body of several bodies has no links "
+                                      "joining them (set them with am_set_constraints)");
+    const long long l0 = am::g_launches.load();
+    h->pairs = 0;
+    cudaStream_t s = h->stream;
+    rc = prepare(h, "am_solve_step", true, &st);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev[2], s));
+    int rs = am::solve(h, &st);
+    CK(cudaEventRecord(h->ev[3], s));
+    CK(cudaGetLastError());
+    rc = copy_outputs(h, U, phi, lam);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->d_xprev, h->d_x, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    h->have_warm = true;
+    if (h->P) {
+        if (dlp_next) {
+            CK(h2d(h->d_dlp1, dlp_next, 3 * (size_t)h->P, s));
+            CK(h2d(h->d_dlq1, dlq_next, 3 * (size_t)h->P, s));
+        } else {
+            CK(cudaMemcpyAsync(h->d_dlp1, h->d_dlp, 3 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(h->d_dlq1, h->d_dlq, 3 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    CK(cudaEventRecord(h->ev[4], s));
+    rc = am::advance(h, dt, &st);
+    CK(cudaEventRecord(h->ev[5], s));
+    CK(cudaGetLastError());
+    if (rc) return rc;
+    rc = device_flags_to_status(h, "am_solve_step");
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    st.ms_gmres = elapsed(h->ev[2], h->ev[3]);
+    st.ms_update = elapsed(h->ev[4], h->ev[5]);
+    st.pairs = h->pairs;
+    st.kernel_launches = (int)(am::g_launches.load() - l0);
+    st.status = rs;
+    h->pc_valid = false;
+    if (stats) *stats = st;
+    if (rs == AM_ERR_NOT_CONVERGED) set_err(h, rs, "am_solve_step: GMRES did not reach the tolerance");
+    return rs;
+}
+
+extern "C" AM_API int am_get_bodies(am_handle* h, int system, double* q, double* theta) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_get_bodies", true);
+    if (rc) return rc;
+    if (system != 0) return set_err(h, AM_ERR_ARG, "am_get_bodies: system out of range");
+    cudaStream_t s = h->stream;
+    if (q) CK(d2h(q, h->d_q, 3 * (size_t)h->M, s));
+    if (theta) CK(d2h(theta, h->d_theta, 4 * (size_t)h->M, s));
+    CK(cudaStreamSynchronize(s));
+    return AM_OK;
+}
+
+extern "C" AM_API int am_get_blobs(am_handle* h, int system, double* r) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_get_blobs", true);
+    if (rc) return rc;
+    if (system != 0 || !r) return set_err(h, AM_ERR_ARG, "am_get_blobs: bad argument");
+    am::launch_geometry(h);
+    CK(cudaGetLastError());
+    am::take_flags(h);
+    CK(d2h(r, h->d_r3, 3 * (size_t)h->Nb, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return AM_OK;
+}
+
+extern "C" AM_API int am_apply_mobility(am_handle* h, const double* lam, double* u) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_apply_mobility", true);
+    if (rc) return rc;
+    if (!lam || !u) return set_err(h, AM_ERR_ARG, "am_apply_mobility: NULL array");
+    cudaStream_t s = h->stream;
+    am::launch_geometry(h);
+    rc = device_flags_to_status(h, "am_apply_mobility");
+    if (rc) return rc;
+    CK(h2d(h->d_t, lam, 3 * (size_t)h->Nb, s));
+    am::mobility_apply(h, h->d_t, h->d_w, false);
+    CK(cudaGetLastError());
+    CK(d2h(u, h->d_w, 3 * (size_t)h->Nb, s));
+    CK(cudaStreamSynchronize(s));
+    return AM_OK;
+}
+
+extern "C" AM_API int am_apply_operator(am_handle* h, const double* y, double* Ay) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_apply_operator", true);
+    if (rc) return rc;
+    if (!y || !Ay) return set_err(h, AM_ERR_ARG, "am_apply_operator: NULL array");
+    cudaStream_t s = h->stream;
+    am::launch_geometry(h);
+    rc = device_flags_to_status(h, "am_apply_operator");
+    if (rc) return rc;
+    CK(h2d(h->d_t, y, h->n, s));
+    am::op_apply(h, h->d_t, h->d_w, false);
+    CK(cudaGetLastError());
+    CK(d2h(Ay, h->d_w, h->n, s));
+    CK(cudaStreamSynchronize(s));
+    return AM_OK;
+}
+
+extern "C" AM_API int am_apply_precond(am_handle* h, const double* r, double* z) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_apply_precond", true);
+    if (rc) return rc;
+    if (!r || !z) return set_err(h, AM_ERR_ARG, "am_apply_precond: NULL array");
+    cudaStream_t s = h->stream;
+    am::launch_geometry(h);
+    am::pc_build(h);
+    CK(cudaGetLastError());
+    rc = device_flags_to_status(h, "am_apply_precond");
+    if (rc) return rc;
+    CK(h2d(h->d_t, r, h->n, s));
+    am::pc_apply(h, h->d_t, h->d_z);
+    CK(cudaGetLastError());
+    CK(d2h(z, h->d_z, h->n, s));
+    CK(cudaStreamSynchronize(s));
+    return AM_OK;
+}
+
+extern "C" AM_API int am_mobility_timing(am_handle* h, int enable, double* ms, long long* launches) {
+    if (!h) return AM_ERR_ARG;
+    if (enable) {
+        CK(cudaStreamSynchronize(h->stream));
+        h->tev_used = 0;
+        h->timing = true;
+    } else {
+        h->timing = false;
+    }
+    if (ms || launches) {
+        CK(cudaStreamSynchronize(h->stream));
+        double tot = 0.0;
+        const size_t pairs = h->tev_used / 2;
+        for (size_t k = 0; k < pairs; ++k) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, h->tev[2 * k], h->tev[2 * k + 1]));
+            tot += t;
+        }
+        if (ms) *ms = tot;
+        if (launches) *launches = (long long)pairs;
+    }
+    return AM_OK;
+}
+
+extern "C" AM_API void am_destroy(am_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_links(h);
+    free_bodies(h);
+    free_solver(h);
+    dfree(&h->d_scal); dfree(&h->d_flags); dfree(&h->d_red);
+    if (h->h_scal) cudaFreeHost(h->h_scal);
+    if (h->h_flags) cudaFreeHost(h->h_flags);
+    if (h->h_iters) cudaFreeHost(h->h_iters);
+    for (int k = 0; k < 8; ++k)
+        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+extern "C" AM_API const char* am_last_error(const am_handle* h) {
+    if (!h) return am::thread_error();
+    return h->err.c_str();
+}

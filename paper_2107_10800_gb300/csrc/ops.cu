@@ -1,0 +1,1384 @@
+// O(N) kernels of the solve: pose, links, the fused part of the operator
+// apply, the block-diagonal preconditioner (build and apply), GMRES vector
+// kernels, and the Euler update with reconstruction and correction.
+#include "am_internal.cuh"
+#include "ops.cuh"
+#include "rpy_pair.cuh"
+
+#include <algorithm>
+
+namespace am {
+
+// ------------------------------------------------------------ helpers ---
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; every thread gets the result.  sh: >= 33 doubles.
+__device__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double r = (lane < (int)((blockDim.x + 31) >> 5)) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+        if (lane == 0) sh[32] = r;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// In-place lower Cholesky factor of the m x m matrix A (row-major, full
+// storage), cooperative over the block.  Returns false (to every thread) if
+// a pivot is not positive.
+__device__ bool block_cholesky(double* A, int m, double* sh) {
+    for (int k = 0; k < m; ++k) {
+        if (threadIdx.x == 0) {
+            double d = A[(size_t)k * m + k];
+            sh[0] = d;
+            if (d > 0.0) {
+                d = sqrt(d);
+                A[(size_t)k * m + k] = d;
+                sh[1] = 1.0 / d;
+            }
+        }
+        __syncthreads();
+        if (!(sh[0] > 0.0)) return false;
+        const double inv = sh[1];
+        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * m + k] *= inv;
+        __syncthreads();
+        const int len = m - k - 1;
+        for (int idx = threadIdx.x; idx < len * len; idx += blockDim.x) {
+            const int i = k + 1 + idx / len, j = k + 1 + idx % len;
+            if (j <= i) A[(size_t)i * m + j] -= A[(size_t)i * m + k] * A[(size_t)j * m + k];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// X = L^{-1} for the lower-triangular m x m L (both row-major), one column
+// per thread by forward substitution; X's upper triangle is left unset.
+__device__ void block_lower_inverse(const double* L, double* X, int m) {
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        X[(size_t)j * m + j] = 1.0 / L[(size_t)j * m + j];
+        for (int i = j + 1; i < m; ++i) {
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s = fma(L[(size_t)i * m + k], X[(size_t)k * m + j], s);
+            X[(size_t)i * m + j] = -s / L[(size_t)i * m + i];
+        }
+    }
+    __syncthreads();
+}
+
+// O = X^T X restricted to the leading r x r block of the m x m lower X.
+__device__ void block_xtx(const double* X, int m, int r, double* O, int ldo) {
+    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+        const int i = idx / r, j = idx % r;
+        const int k0 = i > j ? i : j;
+        double s = 0.0;
+        for (int k = k0; k < r; ++k) s = fma(X[(size_t)k * m + i], X[(size_t)k * m + j], s);
+        O[(size_t)i * ldo + j] = s;
+    }
+    __syncthreads();
+}
+
+// 6 x 6 symmetric positive definite inverse in one thread (Cholesky).
+__device__ bool spd6_inverse(const double* S, double* Out) {
+    double L[36];
+    for (int i = 0; i < 36; ++i) L[i] = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        double d = 0.5 * (S[j * 6 + j] + S[j * 6 + j]);
+        for (int k = 0; k < j; ++k) d -= L[j * 6 + k] * L[j * 6 + k];
+        if (!(d > 0.0)) return false;
+        d = sqrt(d);
+        L[j * 6 + j] = d;
+        for (int i = j + 1; i < 6; ++i) {
+            double s = 0.5 * (S[i * 6 + j] + S[j * 6 + i]);
+            for (int k = 0; k < j; ++k) s -= L[i * 6 + k] * L[j * 6 + k];
+            L[i * 6 + j] = s / d;
+        }
+    }
+    // columns of the inverse: solve L L^T x = e_c
+    for (int c = 0; c < 6; ++c) {
+        double y[6];
+        for (int i = 0; i < 6; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L[i * 6 + k] * y[k];
+            y[i] = s / L[i * 6 + i];
+        }
+        for (int i = 5; i >= 0; --i) {
+            double s = y[i];
+            for (int k = i + 1; k < 6; ++k) s -= L[k * 6 + i] * y[k];
+            y[i] = s / L[i * 6 + i];
+        }
+        for (int i = 0; i < 6; ++i) Out[i * 6 + c] = y[i];
+    }
+    return true;
+}
+
+// ------------------------------------------------------- pose, links ---
+// r_i = q_p + R(theta_p) rho_i  (Sec. 2.3)
+__global__ void k_pose(int Nb, const int* __restrict__ body_of_blob, const double* __restrict__ q,
+                       const double* __restrict__ th, const double* __restrict__ rho,
+                       double4_32a* __restrict__ r4, double4_32a* __restrict__ d4,
+                       float4* __restrict__ hi, float4* __restrict__ lo, double* __restrict__ r3,
+                       double a, int wall, int* flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nb) return;
+    const int p = body_of_blob[i];
+    double dx, dy, dz;
+    quat_rotate(th[4 * p], th[4 * p + 1], th[4 * p + 2], th[4 * p + 3],
+                rho[3 * (size_t)i], rho[3 * (size_t)i + 1], rho[3 * (size_t)i + 2], dx, dy, dz);
+    const double x = q[3 * p] + dx, y = q[3 * p + 1] + dy, z = q[3 * p + 2] + dz;
+    r4[i] = make_double4_32a(x, y, z, 0.0);
+    d4[i] = make_double4_32a(dx, dy, dz, 0.0);
+    r3[3 * (size_t)i] = x; r3[3 * (size_t)i + 1] = y; r3[3 * (size_t)i + 2] = z;
+    const float hx = (float)x, hy = (float)y, hz = (float)z;
+    hi[i] = make_float4(hx, hy, hz, 0.f);
+    lo[i] = make_float4((float)(x - hx), (float)(y - hy), (float)(z - hz), 0.f);
+    if (wall && !(z > a)) atomicOr(flags, kFlagWall);
+}
+
+// l_np = R_p dl_np, l_nq = R_q dl_nq; B_n = R_q d(dl_nq)/dt - R_p d(dl_np)/dt (Eq. dg)
+__global__ void k_links(int P, const int* __restrict__ bp, const int* __restrict__ bq,
+                        const double* __restrict__ th, const double* __restrict__ dlp,
+                        const double* __restrict__ dlq, const double* __restrict__ dlpd,
+                        const double* __restrict__ dlqd, double* __restrict__ lp,
+                        double* __restrict__ lq, double* __restrict__ B) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= P) return;
+    const int p = bp[n], q = bq[n];
+    const double* tp = th + 4 * p;
+    const double* tq = th + 4 * q;
+    double x, y, z;
+    quat_rotate(tp[0], tp[1], tp[2], tp[3], dlp[3 * n], dlp[3 * n + 1], dlp[3 * n + 2], x, y, z);
+    lp[3 * n] = x; lp[3 * n + 1] = y; lp[3 * n + 2] = z;
+    quat_rotate(tq[0], tq[1], tq[2], tq[3], dlq[3 * n], dlq[3 * n + 1], dlq[3 * n + 2], x, y, z);
+    lq[3 * n] = x; lq[3 * n + 1] = y; lq[3 * n + 2] = z;
+    double bx = 0.0, by = 0.0, bz = 0.0;
+    if (dlpd) {
+        double ax, ay, az;
+        quat_rotate(tq[0], tq[1], tq[2], tq[3], dlqd[3 * n], dlqd[3 * n + 1], dlqd[3 * n + 2], bx, by, bz);
+        quat_rotate(tp[0], tp[1], tp[2], tp[3], dlpd[3 * n], dlpd[3 * n + 1], dlpd[3 * n + 2], ax, ay, az);
+        bx -= ax; by -= ay; bz -= az;
+    }
+    B[3 * n] = bx; B[3 * n + 1] = by; B[3 * n + 2] = bz;
+}
+
+// b = (u_s, -F, B)  (Eq. linear_system)
+__global__ void k_rhs(int Nb, int M, int P, const double* __restrict__ slip,
+                      const double* __restrict__ F, const double* __restrict__ B,
+                      double* __restrict__ b) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nl = 3 * Nb, nu = 6 * M;
+    if (k < nl) b[k] = slip ? slip[k] : 0.0;
+    else if (k < nl + nu) b[k] = -F[k - nl];
+    else if (k < nl + nu + 3 * P) b[k] = B[k - nl - nu];
+}
+
+// --------------------------------------------------- operator epilogue ---
+// out_lambda = M lambda - K U   (sum of the mobility partials, minus the
+//                                 rigid velocity u_p + omega_p x (r_i - q_p))
+// out_U      = -K^T lambda + C^T phi
+// out_phi    = C U   (per link: u_p + omega_p x l_np - u_q - omega_q x l_nq)
+__global__ void k_op_epilogue(int Nb, int M, int P, int nblob_blocks, int nbody_blocks,
+                              const double* __restrict__ part, int splits,
+                              const double* __restrict__ y, double* __restrict__ out,
+                              const int* __restrict__ body_of_blob, const int* __restrict__ blob_off,
+                              const double4_32a* __restrict__ d4, const int* __restrict__ bl_off,
+                              const int* __restrict__ bl_idx, const double* __restrict__ lp,
+                              const double* __restrict__ lq, const int* __restrict__ bp,
+                              const int* __restrict__ bq) {
+    const double* lam = y;
+    const double* U = y + 3 * (size_t)Nb;
+    const double* phi = U + 6 * (size_t)M;
+    double* oU = out + 3 * (size_t)Nb;
+    double* of = oU + 6 * (size_t)M;
+    const int b = blockIdx.x;
+    if (b < nblob_blocks) {
+        const int i = b * blockDim.x + threadIdx.x;
+        if (i >= Nb) return;
+        const size_t n3 = 3 * (size_t)Nb;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int t = 0; t < splits; ++t) {
+            const double* pp = part + t * n3 + 3 * (size_t)i;
+            s0 += pp[0]; s1 += pp[1]; s2 += pp[2];
+        }
+        const int p = body_of_blob[i];
+        const double4_32a d = d4[i];
+        const double* u = U + 6 * p;
+        // u + omega x d
+        const double k0 = u[0] + (u[4] * d.z - u[5] * d.y);
+        const double k1 = u[1] + (u[5] * d.x - u[3] * d.z);
+        const double k2 = u[2] + (u[3] * d.y - u[4] * d.x);
+        out[3 * (size_t)i] = s0 - k0;
+        out[3 * (size_t)i + 1] = s1 - k1;
+        out[3 * (size_t)i + 2] = s2 - k2;
+    } else if (b < nblob_blocks + nbody_blocks) {
+        const int wpb = blockDim.x >> 5;
+        const int p = (b - nblob_blocks) * wpb + (threadIdx.x >> 5);
+        const int lane = threadIdx.x & 31;
+        if (p >= M) return;
+        double f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
+        for (int i = blob_off[p] + lane; i < blob_off[p + 1]; i += 32) {
+            const double4_32a d = d4[i];
+            const double l0 = lam[3 * (size_t)i], l1 = lam[3 * (size_t)i + 1], l2 = lam[3 * (size_t)i + 2];
+            f0 += l0; f1 += l1; f2 += l2;
+            t0 += d.y * l2 - d.z * l1;
+            t1 += d.z * l0 - d.x * l2;
+            t2 += d.x * l1 - d.y * l0;
+        }
+        f0 = warp_sum(f0); f1 = warp_sum(f1); f2 = warp_sum(f2);
+        t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2);
+        if (lane == 0) {
+            double c[6] = {0, 0, 0, 0, 0, 0};
+            for (int k = bl_off[p]; k < bl_off[p + 1]; ++k) {
+                const int e = bl_idx[k];
+                const int n = e >> 1;
+                const double sg = (e & 1) ? -1.0 : 1.0;
+                const double* l = (e & 1) ? lq + 3 * n : lp + 3 * n;
+                const double* ph = phi + 3 * n;
+                double tq[3];
+                cross3(l, ph, tq);
+                for (int a = 0; a < 3; ++a) { c[a] += sg * ph[a]; c[3 + a] += sg * tq[a]; }
+            }
+            double* o = oU + 6 * p;
+            o[0] = c[0] - f0; o[1] = c[1] - f1; o[2] = c[2] - f2;
+            o[3] = c[3] - t0; o[4] = c[4] - t1; o[5] = c[5] - t2;
+        }
+    } else {
+        const int n = (b - nblob_blocks - nbody_blocks) * blockDim.x + threadIdx.x;
+        if (n >= P) return;
+        const double* up = U + 6 * bp[n];
+        const double* uq = U + 6 * bq[n];
+        double wp[3], wq[3];
+        cross3(up + 3, lp + 3 * n, wp);
+        cross3(uq + 3, lq + 3 * n, wq);
+        for (int a = 0; a < 3; ++a) of[3 * n + a] = up[a] + wp[a] - uq[a] - wq[a];
+    }
+}
+
+// ------------------------------------------------- preconditioner build ---
+// Per body p (one block): M_pp (same-body blobs only), its Cholesky factor,
+// the explicit inverse, Y_p = M_pp^-1 K_p, S_p = K_p^T Y_p and
+// N~_p = S_p^-1 (Sec. 3.1, the body mobility of the non-interacting body).
+__global__ void __launch_bounds__(256)
+k_pc_body_build(const int* __restrict__ blob_off, const double4_32a* __restrict__ r4,
+                const double4_32a* __restrict__ d4, const long long* __restrict__ moff,
+                double* __restrict__ minv, double* __restrict__ work, double* __restrict__ Y,
+                double* __restrict__ Nt, RpyParamsDev prm, int wall, int* flags) {
+    __shared__ double sh[64];
+    const int b = blockIdx.x;
+    const int i0 = blob_off[b];
+    const int nbl = blob_off[b + 1] - i0;
+    const int m = 3 * nbl;
+    double* A = minv + moff[b];
+    double* L = work + 2 * moff[b];
+    double* X = L + (size_t)m * m;
+    for (int idx = threadIdx.x; idx < nbl * nbl; idx += blockDim.x) {
+        const int ti = idx / nbl, sj = idx % nbl;
+        double T[9];
+        pair_tensor_f64(r4[i0 + ti], r4[i0 + sj], prm, wall, T);
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) L[(size_t)(3 * ti + a) * m + 3 * sj + c] = T[3 * a + c];
+    }
+    __syncthreads();
+    if (!block_cholesky(L, m, sh)) {
+        if (threadIdx.x == 0) atomicOr(flags, kFlagSingular);
+        return;
+    }
+    block_lower_inverse(L, X, m);
+    block_xtx(X, m, m, A, m);
+    double* Yb = Y + 18 * (size_t)i0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double y[6] = {0, 0, 0, 0, 0, 0};
+        for (int bb = 0; bb < nbl; ++bb) {
+            // row i of M^-1 = column i (symmetric)
+            const double v[3] = {A[(size_t)(3 * bb) * m + i], A[(size_t)(3 * bb + 1) * m + i],
+                                 A[(size_t)(3 * bb + 2) * m + i]};
+            const double4_32a dd = d4[i0 + bb];
+            const double d[3] = {dd.x, dd.y, dd.z};
+            double c[3];
+            cross3(d, v, c);
+            for (int a = 0; a < 3; ++a) { y[a] += v[a]; y[3 + a] += c[a]; }
+        }
+        for (int a = 0; a < 6; ++a) Yb[6 * (size_t)i + a] = y[a];
+    }
+    __syncthreads();
+    if (threadIdx.x < 36) {
+        const int c = threadIdx.x / 6, e = threadIdx.x % 6;
+        double s = 0.0;
+        for (int bb = 0; bb < nbl; ++bb) {
+            if (c < 3) {
+                s += Yb[6 * (size_t)(3 * bb + c) + e];
+            } else {
+                const double v[3] = {Yb[6 * (size_t)(3 * bb) + e], Yb[6 * (size_t)(3 * bb + 1) + e],
+                                     Yb[6 * (size_t)(3 * bb + 2) + e]};
+                const double4_32a dd = d4[i0 + bb];
+                const double d[3] = {dd.x, dd.y, dd.z};
+                double cr[3];
+                cross3(d, v, cr);
+                s += cr[c - 3];
+            }
+        }
+        sh[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S[36];
+        for (int k = 0; k < 36; ++k) S[k] = sh[k];
+        if (!spd6_inverse(S, Nt + 36 * (size_t)b)) atomicOr(flags, kFlagSingular);
+    }
+}
+
+// 3x6 block of C for link n on one of its bodies: sigma [I, -l^x]
+// (sigma = +1, l = l_np on body p; sigma = -1, l = l_nq on body q), App. A.
+// W = E N~ (3x6).
+__device__ __forceinline__ void e_times_n(double sg, const double* l, const double* N, double* W) {
+    for (int c = 0; c < 6; ++c) {
+        // (l^x N[3:6, c]) = l x N[3:6, c]
+        const double v[3] = {N[3 * 6 + c], N[4 * 6 + c], N[5 * 6 + c]};
+        double cr[3];
+        cross3(l, v, cr);
+        for (int a = 0; a < 3; ++a) W[a * 6 + c] = sg * (N[a * 6 + c] - cr[a]);
+    }
+}
+
+// Per articulated body (one block): H_a = C_a N~_a C_a^T and the generalised
+// inverse G~_a (Eq. block_diag_const_res).  Symmetric pivoted Cholesky with
+// a relative threshold gives H(perm) ~ L L^T with L of rank r, and
+// G~ = perm [ (L11 L11^T)^-1 0 ; 0 0 ] perm^T, which solves H phi = c
+// exactly for every c in range(H) = range(C_a) (the pseudo-inverse of
+// Sec. 3.1 differs from it only in null(C_a^T), which C^T phi does not see).
+__global__ void __launch_bounds__(256)
+k_pc_asm_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
+               const int* __restrict__ bp, const int* __restrict__ bq,
+               const double* __restrict__ lp, const double* __restrict__ lq,
+               const double* __restrict__ Nt, const long long* __restrict__ goff,
+               double* __restrict__ G, double* __restrict__ gwork, int* __restrict__ perm_all,
+               const long long* __restrict__ poff, int* __restrict__ rank_out, double tol) {
+    __shared__ double shv[256];
+    __shared__ int shi[256];
+    __shared__ double sh[64];
+    __shared__ int s_rank;
+    const int a = blockIdx.x;
+    const int L0 = asm_link_off[a];
+    const int Pa = asm_link_off[a + 1] - L0;
+    const int m = 3 * Pa;
+    if (m == 0) return;
+    double* H = gwork + 2 * goff[a];
+    double* X = H + (size_t)m * m;
+    double* Ga = G + goff[a];
+    int* perm = perm_all + poff[a];
+    for (int idx = threadIdx.x; idx < Pa * Pa; idx += blockDim.x) {
+        const int r = idx / Pa, c = idx % Pa;
+        const int ln = asm_link_idx[L0 + r], lk = asm_link_idx[L0 + c];
+        double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int sn = 0; sn < 2; ++sn) {
+            const int bn = sn ? bq[ln] : bp[ln];
+            for (int sk = 0; sk < 2; ++sk) {
+                const int bk = sk ? bq[lk] : bp[lk];
+                if (bn != bk) continue;
+                double W[18];
+                e_times_n(sn ? -1.0 : 1.0, sn ? lq + 3 * ln : lp + 3 * ln, Nt + 36 * (size_t)bn, W);
+                const double* l = sk ? lq + 3 * lk : lp + 3 * lk;
+                const double sg = sk ? -1.0 : 1.0;
+                // (W E_k^T)[x][y] = sg (W[x][y] + sum_d W[x][3+d] (l^x)[d][y])
+                for (int x = 0; x < 3; ++x) {
+                    const double w3[3] = {W[x * 6 + 3], W[x * 6 + 4], W[x * 6 + 5]};
+                    // sum_d w3[d] (l^x)[d][y] = (w3^T l^x)_y = (l x w3)_y ... with sign:
+                    // (l^x)[d][y] = eps_{d k y} l_k, so sum_d w3_d eps_{dky} l_k = (w3 x l)_y
+                    double cr[3];
+                    cross3(w3, l, cr);
+                    for (int yy = 0; yy < 3; ++yy) blk[x * 3 + yy] += sg * (W[x * 6 + yy] + cr[yy]);
+                }
+            }
+        }
+        for (int x = 0; x < 3; ++x)
+            for (int yy = 0; yy < 3; ++yy) H[(size_t)(3 * r + x) * m + 3 * c + yy] = blk[x * 3 + yy];
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
+    if (threadIdx.x == 0) s_rank = m;
+    __syncthreads();
+    double d0 = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+            const double v = H[(size_t)i * m + i];
+            if (v > best) { best = v; bi = i; }
+        }
+        shv[threadIdx.x] = best;
+        shi[threadIdx.x] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double o = shv[threadIdx.x + s];
+                const int oi = shi[threadIdx.x + s];
+                if (o > shv[threadIdx.x] || (o == shv[threadIdx.x] && oi < shi[threadIdx.x])) {
+                    shv[threadIdx.x] = o;
+                    shi[threadIdx.x] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        const double dmax = shv[0];
+        if (k == 0) d0 = dmax;
+        if (!(dmax > tol * d0) || !(dmax > 0.0)) {
+            if (threadIdx.x == 0) s_rank = k;
+            __syncthreads();
+            break;
+        }
+        const int j = shi[0];
+        __syncthreads();
+        if (j != k) {
+            for (int c = threadIdx.x; c < m; c += blockDim.x) {
+                const double t = H[(size_t)k * m + c];
+                H[(size_t)k * m + c] = H[(size_t)j * m + c];
+                H[(size_t)j * m + c] = t;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < m; r += blockDim.x) {
+                const double t = H[(size_t)r * m + k];
+                H[(size_t)r * m + k] = H[(size_t)r * m + j];
+                H[(size_t)r * m + j] = t;
+            }
+            if (threadIdx.x == 0) {
+                const int t = perm[k];
+                perm[k] = perm[j];
+                perm[j] = t;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double d = sqrt(H[(size_t)k * m + k]);
+            H[(size_t)k * m + k] = d;
+            sh[0] = 1.0 / d;
+        }
+        __syncthreads();
+        const double inv = sh[0];
+        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) H[(size_t)i * m + k] *= inv;
+        __syncthreads();
+        const int len = m - k - 1;
+        for (int idx = threadIdx.x; idx < len * len; idx += blockDim.x) {
+            const int i = k + 1 + idx / len, jj = k + 1 + idx % len;
+            H[(size_t)i * m + jj] -= H[(size_t)i * m + k] * H[(size_t)jj * m + k];
+        }
+        __syncthreads();
+    }
+    const int r = s_rank;
+    if (threadIdx.x == 0) rank_out[a] = r;
+    // X = L11^-1 (leading r x r of H, leading dimension m)
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        X[(size_t)j * m + j] = 1.0 / H[(size_t)j * m + j];
+        for (int i = j + 1; i < r; ++i) {
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s = fma(H[(size_t)i * m + k], X[(size_t)k * m + j], s);
+            X[(size_t)i * m + j] = -s / H[(size_t)i * m + i];
+        }
+    }
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Ga[idx] = 0.0;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+        const int i = idx / r, j = idx % r;
+        const int k0 = i > j ? i : j;
+        double s = 0.0;
+        for (int k = k0; k < r; ++k) s = fma(X[(size_t)k * m + i], X[(size_t)k * m + j], s);
+        Ga[(size_t)perm[i] * m + perm[j]] = s;
+    }
+}
+
+// ------------------------------------------------- preconditioner apply ---
+// Solves the block-diagonal problem of Eq. precond for r = (r1, r2, r3):
+//   w = M~^-1 r1;  U^ = N~ (-r2 - K^T w)  (K^T w = Y^T r1)      [apply1]
+//   phi = G~ (r3 - C U^)                                       [apply2]
+//   U = U^ + N~ C^T phi;  lambda = w + Y U  (= M~^-1 (r1 + K U)) [apply3]
+__global__ void __launch_bounds__(128)
+k_pc_apply1(int Nb, const int* __restrict__ blob_off, const double* __restrict__ minv,
+            const long long* __restrict__ moff, const double* __restrict__ Y,
+            const double* __restrict__ Nt, const double* __restrict__ r,
+            double* __restrict__ w, double* __restrict__ Uhat) {
+    __shared__ double sh[64];
+    const int b = blockIdx.x;
+    const int i0 = blob_off[b];
+    const int m = 3 * (blob_off[b + 1] - i0);
+    const double* A = minv + moff[b];
+    const double* r1 = r + 3 * (size_t)i0;
+    const double* Yb = Y + 18 * (size_t)i0;
+    double yt[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s = fma(A[(size_t)k * m + i], r1[k], s);
+        w[3 * (size_t)i0 + i] = s;
+        const double ri = r1[i];
+        for (int c = 0; c < 6; ++c) yt[c] = fma(Yb[6 * (size_t)i + c], ri, yt[c]);
+    }
+    double tot[6];
+    for (int c = 0; c < 6; ++c) tot[c] = block_sum(yt[c], sh);
+    if (threadIdx.x == 0) {
+        const double* r2 = r + 3 * (size_t)Nb + 6 * (size_t)b;
+        const double* N = Nt + 36 * (size_t)b;
+        double v[6];
+        for (int c = 0; c < 6; ++c) v[c] = -r2[c] - tot[c];
+        for (int a = 0; a < 6; ++a) {
+            double s = 0.0;
+            for (int c = 0; c < 6; ++c) s += N[a * 6 + c] * v[c];
+            Uhat[6 * (size_t)b + a] = s;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128)
+k_pc_apply2(int Nb, int M, const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
+            const int* __restrict__ bp, const int* __restrict__ bq, const double* __restrict__ lp,
+            const double* __restrict__ lq, const double* __restrict__ Uhat,
+            const double* __restrict__ G, const long long* __restrict__ goff,
+            const double* __restrict__ r, double* __restrict__ z, double* __restrict__ cbuf) {
+    const int a = blockIdx.x;
+    const int L0 = asm_link_off[a];
+    const int Pa = asm_link_off[a + 1] - L0;
+    const int m = 3 * Pa;
+    if (m == 0) return;
+    const double* r3 = r + 3 * (size_t)Nb + 6 * (size_t)M;
+    double* c = cbuf + 3 * (size_t)L0;
+    for (int k = threadIdx.x; k < Pa; k += blockDim.x) {
+        const int n = asm_link_idx[L0 + k];
+        const double* up = Uhat + 6 * bp[n];
+        const double* uq = Uhat + 6 * bq[n];
+        double wp[3], wq[3];
+        cross3(up + 3, lp + 3 * n, wp);
+        cross3(uq + 3, lq + 3 * n, wq);
+        for (int x = 0; x < 3; ++x) c[3 * k + x] = r3[3 * n + x] - (up[x] + wp[x] - uq[x] - wq[x]);
+    }
+    __syncthreads();
+    const double* Ga = G + goff[a];
+    double* zf = z + 3 * (size_t)Nb + 6 * (size_t)M;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s = fma(Ga[(size_t)k * m + i], c[k], s);
+        const int n = asm_link_idx[L0 + i / 3];
+        zf[3 * n + i % 3] = s;
+    }
+}
+
+__global__ void __launch_bounds__(128)
+k_pc_apply3(int Nb, int M, const int* __restrict__ blob_off, const double* __restrict__ Y,
+            const double* __restrict__ Nt, const double* __restrict__ w,
+            const double* __restrict__ Uhat, const int* __restrict__ bl_off,
+            const int* __restrict__ bl_idx, const double* __restrict__ lp,
+            const double* __restrict__ lq, double* __restrict__ z) {
+    __shared__ double sU[6];
+    const int b = blockIdx.x;
+    const double* phi = z + 3 * (size_t)Nb + 6 * (size_t)M;
+    if (threadIdx.x == 0) {
+        double f[6] = {0, 0, 0, 0, 0, 0};
+        for (int k = bl_off[b]; k < bl_off[b + 1]; ++k) {
+            const int e = bl_idx[k];
+            const int n = e >> 1;
+            const double sg = (e & 1) ? -1.0 : 1.0;
+            const double* l = (e & 1) ? lq + 3 * n : lp + 3 * n;
+            const double* ph = phi + 3 * n;
+            double t[3];
+            cross3(l, ph, t);
+            for (int x = 0; x < 3; ++x) { f[x] += sg * ph[x]; f[3 + x] += sg * t[x]; }
+        }
+        const double* N = Nt + 36 * (size_t)b;
+        double* zU = z + 3 * (size_t)Nb + 6 * (size_t)b;
+        for (int x = 0; x < 6; ++x) {
+            double s = Uhat[6 * (size_t)b + x];
+            for (int c = 0; c < 6; ++c) s += N[x * 6 + c] * f[c];
+            sU[x] = s;
+            zU[x] = s;
+        }
+    }
+    __syncthreads();
+    const int i0 = blob_off[b];
+    const int m = 3 * (blob_off[b + 1] - i0);
+    const double* Yb = Y + 18 * (size_t)i0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double s = w[3 * (size_t)i0 + i];
+        for (int c = 0; c < 6; ++c) s = fma(Yb[6 * (size_t)i + c], sU[c], s);
+        z[3 * (size_t)i0 + i] = s;
+    }
+}
+
+// --------------------------------------------------------- GMRES kernels ---
+// part[k * nch + c] = <V_k, w> over chunk c (k < jp1)
+__global__ void __launch_bounds__(256)
+k_dots(const double* __restrict__ V, size_t ldv, const double* __restrict__ w, int n,
+       int chunk, double* __restrict__ part, int nch) {
+    __shared__ double sh[64];
+    const int c = blockIdx.x, k = blockIdx.y;
+    const int i0 = c * chunk, i1 = min(n, i0 + chunk);
+    const double* v = V + (size_t)k * ldv;
+    double s = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(v[i], w[i], s);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[(size_t)k * nch + c] = s;
+}
+
+// w -= sum_k h_k V_k with h_k = sum_c part[k][c]; hcol = h (or += h);
+// optional per-block partial sums of |w|^2 after the update.
+__global__ void __launch_bounds__(256)
+k_orth(const double* __restrict__ V, size_t ldv, double* __restrict__ w, int n,
+       const double* __restrict__ part, int nch, int jp1, double* __restrict__ hcol,
+       int accumulate, double* __restrict__ npart) {
+    extern __shared__ double coef[];
+    __shared__ double sh[64];
+    for (int k = threadIdx.x; k < jp1; k += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nch; ++c) s += part[(size_t)k * nch + c];
+        coef[k] = s;
+        if (blockIdx.x == 0) hcol[k] = accumulate ? hcol[k] + s : s;
+    }
+    __syncthreads();
+    double nn = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v = w[i];
+        for (int k = 0; k < jp1; ++k) v = fma(-coef[k], V[(size_t)k * ldv + i], v);
+        w[i] = v;
+        nn = fma(v, v, nn);
+    }
+    if (npart) {
+        nn = block_sum(nn, sh);
+        if (threadIdx.x == 0) npart[blockIdx.x] = nn;
+    }
+}
+
+// |w|^2 partial sums (no orthogonalisation)
+__global__ void __launch_bounds__(256)
+k_norm_part(const double* __restrict__ w, int n, double* __restrict__ npart) {
+    __shared__ double sh[64];
+    double nn = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        nn = fma(w[i], w[i], nn);
+    nn = block_sum(nn, sh);
+    if (threadIdx.x == 0) npart[blockIdx.x] = nn;
+}
+
+// r = b - Ax and per-block |r|^2
+__global__ void __launch_bounds__(256)
+k_residual(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
+           int n, double* __restrict__ npart) {
+    __shared__ double sh[64];
+    double nn = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = b[i] - Ax[i];
+        r[i] = v;
+        nn = fma(v, v, nn);
+    }
+    nn = block_sum(nn, sh);
+    if (threadIdx.x == 0) npart[blockIdx.x] = nn;
+}
+
+// scal[slot] = sqrt(sum npart); scal[slot+1] = 1/that (0 if zero)
+__global__ void k_norm_finish(const double* __restrict__ npart, int nb, double* __restrict__ scal,
+                              int slot) {
+    __shared__ double sh[64];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += npart[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        const double nrm = sqrt(s);
+        scal[slot] = nrm;
+        scal[slot + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    }
+}
+
+// Arnoldi column j: H[0..j][j] = hcol, H[j+1][j] = |w|; apply the previous
+// Givens rotations, form the new one and update g.  scal[0] = |g[j+1]|
+// (residual estimate), scal[1] = |w|, scal[2] = 1/|w|.
+__global__ void k_arnoldi_finish(int j, const double* __restrict__ hcol,
+                                 const double* __restrict__ npart, int nb, double* __restrict__ H,
+                                 int ldh, double* __restrict__ cs, double* __restrict__ sn,
+                                 double* __restrict__ g, double* __restrict__ scal) {
+    __shared__ double sh[64];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += npart[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x != 0) return;
+    const double nrm = sqrt(s);
+    double* h = H + (size_t)j * ldh;
+    for (int i = 0; i <= j; ++i) h[i] = hcol[i];
+    h[j + 1] = nrm;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    const double d = hypot(h[j], h[j + 1]);
+    double c = 1.0, sg = 0.0;
+    if (d > 0.0) { c = h[j] / d; sg = h[j + 1] / d; }
+    cs[j] = c; sn[j] = sg;
+    h[j] = d;
+    h[j + 1] = 0.0;
+    g[j + 1] = -sg * g[j];
+    g[j] = c * g[j];
+    scal[0] = fabs(g[j + 1]);
+    scal[1] = nrm;
+    scal[2] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+}
+
+// xi = H(0:k,0:k)^-1 g(0:k)  (upper triangular back substitution)
+__global__ void k_hessenberg_solve(int k, const double* __restrict__ H, int ldh,
+                                   const double* __restrict__ g, double* __restrict__ xi) {
+    if (threadIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int c = i + 1; c < k; ++c) s -= H[(size_t)c * ldh + i] * xi[c];
+        const double d = H[(size_t)i * ldh + i];
+        xi[i] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+// t = sum_{k<kk} xi_k V_k
+__global__ void k_combine(const double* __restrict__ V, size_t ldv, const double* __restrict__ xi,
+                          int kk, int n, double* __restrict__ t) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < kk; ++k) s = fma(xi[k], V[(size_t)k * ldv + i], s);
+        t[i] = s;
+    }
+}
+
+// y = a * x (a read from device memory), and optional g[0] = |.|
+__global__ void k_scale(const double* __restrict__ x, double* __restrict__ y, int n,
+                        const double* __restrict__ a) {
+    const double s = *a;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = s * x[i];
+}
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int n, double a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = fma(a, x[i], y[i]);
+}
+
+__global__ void k_init_g(double* __restrict__ g, int len, const double* __restrict__ scal, int slot) {
+    for (int i = threadIdx.x; i < len; i += blockDim.x) g[i] = (i == 0) ? scal[slot] : 0.0;
+}
+
+// zero the lambda and U blocks and put B - C U0 in the phi block: the
+// right-hand side whose preconditioned solution projects U0 onto C U = B.
+__global__ void k_proj_rhs(int Nb, int M, int P, const int* __restrict__ bp,
+                           const int* __restrict__ bq, const double* __restrict__ lp,
+                           const double* __restrict__ lq, const double* __restrict__ B,
+                           const double* __restrict__ x, double* __restrict__ t) {
+    const int nl = 3 * Nb, nu = 6 * M;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nl + nu) { t[k] = 0.0; return; }
+    const int n = k - nl - nu;
+    if (n >= P) return;
+    const double* U = x + nl;
+    const double* up = U + 6 * bp[n];
+    const double* uq = U + 6 * bq[n];
+    double wp[3], wq[3];
+    cross3(up + 3, lp + 3 * n, wp);
+    cross3(uq + 3, lq + 3 * n, wq);
+    for (int a = 0; a < 3; ++a) t[nl + nu + 3 * n + a] = B[3 * n + a] - (up[a] + wp[a] - uq[a] - wq[a]);
+}
+
+// max_n |(C U - B)_n| into scal[slot] (single block)
+__global__ void k_constraint_residual(int Nb, int M, int P, const int* __restrict__ bp,
+                                      const int* __restrict__ bq, const double* __restrict__ lp,
+                                      const double* __restrict__ lq, const double* __restrict__ B,
+                                      const double* __restrict__ x, double* __restrict__ scal,
+                                      int slot) {
+    __shared__ double sh[256];
+    const double* U = x + 3 * (size_t)Nb;
+    double mx = 0.0;
+    for (int n = threadIdx.x; n < P; n += blockDim.x) {
+        const double* up = U + 6 * bp[n];
+        const double* uq = U + 6 * bq[n];
+        double wp[3], wq[3];
+        cross3(up + 3, lp + 3 * n, wp);
+        cross3(uq + 3, lq + 3 * n, wq);
+        for (int a = 0; a < 3; ++a) mx = fmax(mx, fabs(up[a] + wp[a] - uq[a] - wq[a] - B[3 * n + a]));
+    }
+    sh[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scal[slot] = sh[0];
+}
+
+// ------------------------------------------------ Euler + reconstruction ---
+// Per articulated body a (one block), Sec. 4.3 steps 2-5:
+//   u_COM = mean_p u_p; q_COM* = mean_p q_p + dt u_COM;
+//   theta*_p = theta_{omega_p dt} . theta_p;
+//   z_n = R(theta*_p) dl_np(t+dt) - R(theta*_q) dl_nq(t+dt);
+//   q*_p = -((P^a)^+ z)_p + q_COM*;  g2 += |g_n(q*, theta*)|^2.
+__global__ void __launch_bounds__(128)
+k_euler_reconstruct(const int* __restrict__ asm_body_off, const int* __restrict__ asm_body_idx,
+                    const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
+                    const int* __restrict__ bp, const int* __restrict__ bq,
+                    const double* __restrict__ U, const double* __restrict__ q,
+                    const double* __restrict__ th, const double* __restrict__ dlp1,
+                    const double* __restrict__ dlq1, const double* __restrict__ pplus,
+                    const long long* __restrict__ pplus_off, double dt,
+                    double* __restrict__ qnew, double* __restrict__ thnew,
+                    double* __restrict__ zbuf, double* __restrict__ g2acc) {
+    __shared__ double sh[64];
+    const int a = blockIdx.x;
+    const int B0 = asm_body_off[a], Ma = asm_body_off[a + 1] - B0;
+    const int L0 = asm_link_off[a], Pa = asm_link_off[a + 1] - L0;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < Ma; k += blockDim.x) {
+        const int p = asm_body_idx[B0 + k];
+        for (int x = 0; x < 3; ++x) { acc[x] += U[6 * (size_t)p + x]; acc[3 + x] += q[3 * p + x]; }
+        double gq[4];
+        quat_from_rotvec(U[6 * (size_t)p + 3] * dt, U[6 * (size_t)p + 4] * dt, U[6 * (size_t)p + 5] * dt, gq);
+        quat_mul(gq, th + 4 * p, thnew + 4 * p);
+    }
+    double com[3];
+    for (int x = 0; x < 3; ++x) {
+        const double su = block_sum(acc[x], sh);
+        const double sq = block_sum(acc[3 + x], sh);
+        com[x] = sq / Ma + dt * (su / Ma);
+    }
+    // block_sum synchronises, so thnew is visible to the whole block here
+    double* z = zbuf + 3 * (size_t)L0;
+    for (int k = threadIdx.x; k < Pa; k += blockDim.x) {
+        const int n = asm_link_idx[L0 + k];
+        const double* tp = thnew + 4 * bp[n];
+        const double* tq = thnew + 4 * bq[n];
+        double ax, ay, az, bx, by, bz;
+        quat_rotate(tp[0], tp[1], tp[2], tp[3], dlp1[3 * n], dlp1[3 * n + 1], dlp1[3 * n + 2], ax, ay, az);
+        quat_rotate(tq[0], tq[1], tq[2], tq[3], dlq1[3 * n], dlq1[3 * n + 1], dlq1[3 * n + 2], bx, by, bz);
+        z[3 * k] = ax - bx; z[3 * k + 1] = ay - by; z[3 * k + 2] = az - bz;
+    }
+    __syncthreads();
+    const double* Pp = pplus + pplus_off[a];
+    for (int k = threadIdx.x; k < Ma; k += blockDim.x) {
+        const int p = asm_body_idx[B0 + k];
+        double s[3] = {0, 0, 0};
+        for (int l = 0; l < Pa; ++l) {
+            const double c = Pp[(size_t)k * Pa + l];
+            for (int x = 0; x < 3; ++x) s[x] = fma(c, z[3 * l + x], s[x]);
+        }
+        for (int x = 0; x < 3; ++x) qnew[3 * p + x] = com[x] - s[x];
+    }
+    __syncthreads();
+    double gg = 0.0;
+    for (int k = threadIdx.x; k < Pa; k += blockDim.x) {
+        const int n = asm_link_idx[L0 + k];
+        for (int x = 0; x < 3; ++x) {
+            const double gx = qnew[3 * bp[n] + x] - qnew[3 * bq[n] + x] + z[3 * k + x];
+            gg = fma(gx, gx, gg);
+        }
+    }
+    gg = block_sum(gg, sh);
+    if (threadIdx.x == 0 && Pa > 0) atomicAdd(g2acc, gg);
+}
+
+// d/d(dth) of R(dth) v, dth = [s, p] (from Eq. rot_mat):
+//   column s:   4 s v + 2 p x v
+//   column p_l: 2 delta_il (p.v) + 2 p_i v_l + 2 s eps_ilk v_k
+__device__ __forceinline__ void d_rot_apply(const double* dth, const double* v, double* D /*3x4*/) {
+    const double s = dth[0];
+    const double p[3] = {dth[1], dth[2], dth[3]};
+    double pxv[3];
+    cross3(p, v, pxv);
+    const double pv = p[0] * v[0] + p[1] * v[1] + p[2] * v[2];
+    for (int i = 0; i < 3; ++i) D[i * 4] = 4.0 * s * v[i] + 2.0 * pxv[i];
+    // eps_ilk v_k as a matrix E[i][l]: E = -[v]^x
+    const double E[9] = {0.0, v[2], -v[1], -v[2], 0.0, v[0], v[1], -v[0], 0.0};
+    for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l)
+            D[i * 4 + 1 + l] = 2.0 * ((i == l) ? pv : 0.0) + 2.0 * p[i] * v[l] + 2.0 * s * E[i * 3 + l];
+}
+
+// Correction (Sec. 4.2): per articulated body, Gauss-Newton on the residual
+// [g_n(dq, dth) (Eq. residual); |dth_p|^2 - 1] from dq = 0, dth = [1,0,0,0],
+// until its squared norm is below delta^2.  Each step solves the normal
+// equations (J^T J + mu I) step = -J^T r with mu = 1e-10 max diag(J^T J),
+// which gives the minimum-norm least-squares step to high relative accuracy
+// (the residual is invariant under rigid motions of the whole articulated
+// body, so J^T J is singular).  Runs only if the global ||g*||^2 >= delta.
+__global__ void __launch_bounds__(256)
+k_correct(const int* __restrict__ asm_body_off, const int* __restrict__ asm_body_idx,
+          const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
+          const int* __restrict__ bp, const int* __restrict__ bq, const int* __restrict__ body_local,
+          const int* __restrict__ link_local, const int* __restrict__ bl_off,
+          const int* __restrict__ bl_idx,
+          const double* __restrict__ dlp1, const double* __restrict__ dlq1,
+          double* __restrict__ qnew, double* __restrict__ thnew, const double* __restrict__ g2acc,
+          double delta, int max_iter, double* __restrict__ ws, const long long* __restrict__ ws_off,
+          int* __restrict__ iters_out, int* flags) {
+    __shared__ double sh[64];
+    __shared__ double smax[8];
+    const int a = blockIdx.x;
+    const int B0 = asm_body_off[a], Ma = asm_body_off[a + 1] - B0;
+    const int L0 = asm_link_off[a], Pa = asm_link_off[a + 1] - L0;
+    if (threadIdx.x == 0) iters_out[a] = 0;
+    if (Pa == 0 || !(*g2acc >= delta)) return;
+    const int nd = 7 * Ma;
+    double* x = ws + ws_off[a];
+    double* N = x + nd;
+    double* rhs = N + (size_t)nd * nd;
+    double* ltp = rhs + nd;
+    double* ltq = ltp + 3 * Pa;
+    double* g = ltq + 3 * Pa;
+    double* yv = g + 3 * Pa;
+    for (int k = threadIdx.x; k < Pa; k += blockDim.x) {
+        const int n = asm_link_idx[L0 + k];
+        const double* tp = thnew + 4 * bp[n];
+        const double* tq = thnew + 4 * bq[n];
+        quat_rotate(tp[0], tp[1], tp[2], tp[3], dlp1[3 * n], dlp1[3 * n + 1], dlp1[3 * n + 2],
+                    ltp[3 * k], ltp[3 * k + 1], ltp[3 * k + 2]);
+        quat_rotate(tq[0], tq[1], tq[2], tq[3], dlq1[3 * n], dlq1[3 * n + 1], dlq1[3 * n + 2],
+                    ltq[3 * k], ltq[3 * k + 1], ltq[3 * k + 2]);
+    }
+    for (int k = threadIdx.x; k < nd; k += blockDim.x) x[k] = ((k % 7) == 3) ? 1.0 : 0.0;
+    __syncthreads();
+    int it = 0;
+    while (true) {
+        // residual
+        double rr = 0.0;
+        for (int k = threadIdx.x; k < Pa; k += blockDim.x) {
+            const int n = asm_link_idx[L0 + k];
+            const int lp_ = body_local[bp[n]], lq_ = body_local[bq[n]];
+            const double* xp = x + 7 * lp_;
+            const double* xq = x + 7 * lq_;
+            double ap[3], aq[3];
+            quat_rotate(xp[3], xp[4], xp[5], xp[6], ltp[3 * k], ltp[3 * k + 1], ltp[3 * k + 2], ap[0], ap[1], ap[2]);
+            quat_rotate(xq[3], xq[4], xq[5], xq[6], ltq[3 * k], ltq[3 * k + 1], ltq[3 * k + 2], aq[0], aq[1], aq[2]);
+            for (int c = 0; c < 3; ++c) {
+                const double v = qnew[3 * bp[n] + c] + xp[c] + ap[c] - qnew[3 * bq[n] + c] - xq[c] - aq[c];
+                g[3 * k + c] = v;
+                rr = fma(v, v, rr);
+            }
+        }
+        for (int k = threadIdx.x; k < Ma; k += blockDim.x) {
+            const double* xb = x + 7 * k;
+            const double u = xb[3] * xb[3] + xb[4] * xb[4] + xb[5] * xb[5] + xb[6] * xb[6] - 1.0;
+            rr = fma(u, u, rr);
+        }
+        rr = block_sum(rr, sh);
+        if (rr < delta * delta || it >= max_iter) break;
+        // normal equations, one block row per body (deterministic)
+        for (int k = threadIdx.x; k < Ma; k += blockDim.x) {
+            const int p = asm_body_idx[B0 + k];
+            double* Nrow = N + (size_t)(7 * k) * nd;
+            for (int e = 0; e < 7 * nd; ++e) Nrow[e] = 0.0;
+            double rh[7] = {0, 0, 0, 0, 0, 0, 0};
+            const double* xb = x + 7 * k;
+            for (int e = bl_off[p]; e < bl_off[p + 1]; ++e) {
+                const int code = bl_idx[e];
+                const int n = code >> 1;
+                const int side = code & 1;
+                const int loc = link_local[n];  // position of link n in its assembly
+                const double sg = side ? -1.0 : 1.0;
+                const int other = body_local[side ? bp[n] : bq[n]];
+                const double* xo = x + 7 * other;
+                double Dm[12], Do[12];
+                d_rot_apply(xb + 3, side ? ltq + 3 * loc : ltp + 3 * loc, Dm);
+                d_rot_apply(xo + 3, side ? ltp + 3 * loc : ltq + 3 * loc, Do);
+                // J rows of link n: this body sg [I, Dm], other body -sg [I, Do]
+                double Jm[21], Jo[21];
+                for (int r = 0; r < 3; ++r) {
+                    for (int c = 0; c < 3; ++c) {
+                        Jm[r * 7 + c] = sg * (r == c ? 1.0 : 0.0);
+                        Jo[r * 7 + c] = -sg * (r == c ? 1.0 : 0.0);
+                    }
+                    for (int c = 0; c < 4; ++c) {
+                        Jm[r * 7 + 3 + c] = sg * Dm[r * 4 + c];
+                        Jo[r * 7 + 3 + c] = -sg * Do[r * 4 + c];
+                    }
+                }
+                for (int i = 0; i < 7; ++i) {
+                    for (int j = 0; j < 7; ++j) {
+                        double smm = 0.0, smo = 0.0;
+                        for (int r = 0; r < 3; ++r) {
+                            smm += Jm[r * 7 + i] * Jm[r * 7 + j];
+                            smo += Jm[r * 7 + i] * Jo[r * 7 + j];
+                        }
+                        Nrow[(size_t)i * nd + 7 * k + j] += smm;
+                        Nrow[(size_t)i * nd + 7 * other + j] += smo;
+                    }
+                    double sr = 0.0;
+                    for (int r = 0; r < 3; ++r) sr += Jm[r * 7 + i] * g[3 * loc + r];
+                    rh[i] += sr;
+                }
+            }
+            // unit-norm row: 2 dth^T on the quaternion columns
+            const double u = xb[3] * xb[3] + xb[4] * xb[4] + xb[5] * xb[5] + xb[6] * xb[6] - 1.0;
+            for (int i = 0; i < 4; ++i) {
+                for (int j = 0; j < 4; ++j) Nrow[(size_t)(3 + i) * nd + 7 * k + 3 + j] += 4.0 * xb[3 + i] * xb[3 + j];
+                rh[3 + i] += 2.0 * xb[3 + i] * u;
+            }
+            for (int i = 0; i < 7; ++i) rhs[7 * k + i] = -rh[i];
+        }
+        __syncthreads();
+        double dm = 0.0;
+        for (int k = threadIdx.x; k < nd; k += blockDim.x) dm = fmax(dm, N[(size_t)k * nd + k]);
+        // max over the block
+        {
+            double v = dm;
+            for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double mm = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, smax[w]);
+                sh[48] = mm;
+            }
+            __syncthreads();
+        }
+        const double mu = 1e-10 * sh[48];
+        for (int k = threadIdx.x; k < nd; k += blockDim.x) N[(size_t)k * nd + k] += mu;
+        __syncthreads();
+        if (!block_cholesky(N, nd, sh)) {
+            if (threadIdx.x == 0) atomicOr(flags, kFlagCorrection);
+            break;
+        }
+        // solve L L^T step = rhs (one warp, row by row)
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            for (int i = 0; i < nd; ++i) {
+                double s = 0.0;
+                for (int k = lane; k < i; k += 32) s = fma(N[(size_t)i * nd + k], yv[k], s);
+                s = warp_sum(s);
+                if (lane == 0) yv[i] = (rhs[i] - s) / N[(size_t)i * nd + i];
+                __syncwarp();
+            }
+            for (int i = nd - 1; i >= 0; --i) {
+                double s = 0.0;
+                for (int k = i + 1 + lane; k < nd; k += 32) s = fma(N[(size_t)k * nd + i], yv[k], s);
+                s = warp_sum(s);
+                if (lane == 0) yv[i] = (yv[i] - s) / N[(size_t)i * nd + i];
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < nd; k += blockDim.x) x[k] += yv[k];
+        __syncthreads();
+        ++it;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < Ma; k += blockDim.x) {
+        const int p = asm_body_idx[B0 + k];
+        const double* xb = x + 7 * k;
+        for (int c = 0; c < 3; ++c) qnew[3 * p + c] += xb[c];
+        double o[4];
+        quat_mul(xb + 3, thnew + 4 * p, o);
+        for (int c = 0; c < 4; ++c) thnew[4 * p + c] = o[c];
+    }
+    if (threadIdx.x == 0) iters_out[a] = it;
+}
+
+// |g|^2 over all links (global accumulator), after the step
+__global__ void k_g2(int P, const int* __restrict__ bp, const int* __restrict__ bq,
+                     const double* __restrict__ q, const double* __restrict__ th,
+                     const double* __restrict__ dlp, const double* __restrict__ dlq,
+                     double* __restrict__ acc) {
+    __shared__ double sh[64];
+    double gg = 0.0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < P; n += gridDim.x * blockDim.x) {
+        const int p = bp[n], qq = bq[n];
+        const double* tp = th + 4 * p;
+        const double* tq = th + 4 * qq;
+        double ax, ay, az, bx, by, bz;
+        quat_rotate(tp[0], tp[1], tp[2], tp[3], dlp[3 * n], dlp[3 * n + 1], dlp[3 * n + 2], ax, ay, az);
+        quat_rotate(tq[0], tq[1], tq[2], tq[3], dlq[3 * n], dlq[3 * n + 1], dlq[3 * n + 2], bx, by, bz);
+        const double g0 = q[3 * p] + ax - q[3 * qq] - bx;
+        const double g1 = q[3 * p + 1] + ay - q[3 * qq + 1] - by;
+        const double g2 = q[3 * p + 2] + az - q[3 * qq + 2] - bz;
+        gg += g0 * g0 + g1 * g1 + g2 * g2;
+    }
+    gg = block_sum(gg, sh);
+    if (threadIdx.x == 0) atomicAdd(acc, gg);
+}
+
+}  // namespace am
+
+// =============================================================== host ===
+namespace am {
+
+static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+int take_flags(am_handle* h) {
+    int f = 0;
+    cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
+    cudaStreamSynchronize(h->stream);
+    f = *h->h_flags;
+    return f;
+}
+
+void launch_geometry(am_handle* h) {
+    cudaStream_t s = h->stream;
+    if (h->Nb) {
+        k_pose<<<nblk(h->Nb, 256), 256, 0, s>>>(h->Nb, h->d_body_of_blob, h->d_q, h->d_theta, h->d_rho,
+                                                 h->d_r4, h->d_d4, h->d_rhi, h->d_rlo, h->d_r3,
+                                                 h->cfg.blob_radius, h->cfg.wall, h->d_flags);
+        count_launch();
+    }
+    if (h->P) {
+        k_links<<<nblk(h->P, 256), 256, 0, s>>>(h->P, h->d_bp, h->d_bq, h->d_theta, h->d_dlp, h->d_dlq,
+                                                 h->active_links ? h->d_dlpd : nullptr,
+                                                 h->active_links ? h->d_dlqd : nullptr,
+                                                 h->d_lp, h->d_lq, h->d_B);
+        count_launch();
+    }
+    k_rhs<<<nblk(h->n, 256), 256, 0, s>>>(h->Nb, h->M, h->P, h->d_slip, h->d_F, h->d_B, h->d_b);
+    count_launch();
+}
+
+static void timing_mark(am_handle* h) {
+    if (!h->timing) return;
+    if (h->tev_used == h->tev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        h->tev.push_back(e);
+    }
+    cudaEventRecord(h->tev[h->tev_used++], h->stream);
+}
+
+static void mobility_partial(am_handle* h, const double* lam, bool fp64) {
+    timing_mark(h);
+    if (fp64 || h->cfg.precision == AM_FP64)
+        launch_rpy_partial_f64(h->d_r4, lam, h->d_mv, h->Nb, h->split, h->prm, h->cfg.wall, h->stream);
+    else
+        launch_rpy_partial_mixed(h->d_rhi, h->d_rlo, lam, h->d_mv, h->Nb, h->split, h->prm,
+                                 h->cfg.wall, h->stream);
+    timing_mark(h);
+    h->pairs += (long long)h->Nb * h->Nb;
+}
+
+void mobility_apply(am_handle* h, const double* lam, double* u, bool fp64) {
+    mobility_partial(h, lam, fp64);
+    launch_sum_partials(h->d_mv, u, h->Nb, h->split.splits, h->stream);
+}
+
+void op_apply(am_handle* h, const double* y, double* out, bool fp64) {
+    mobility_partial(h, y, fp64);
+    const int nbb = nblk(h->Nb, 128), nbody = nblk(h->M, 4), nlink = nblk(h->P, 128);
+    k_op_epilogue<<<nbb + nbody + nlink, 128, 0, h->stream>>>(
+        h->Nb, h->M, h->P, nbb, nbody, h->d_mv, h->split.splits, y, out, h->d_body_of_blob,
+        h->d_blob_off, h->d_d4, h->d_body_link_off, h->d_body_link_idx, h->d_lp, h->d_lq, h->d_bp,
+        h->d_bq);
+    count_launch();
+}
+
+void pc_build(am_handle* h) {
+    cudaStream_t s = h->stream;
+    k_pc_body_build<<<h->M, 256, 0, s>>>(h->d_blob_off, h->d_r4, h->d_d4, h->d_minv_off, h->d_minv,
+                                          h->d_pcwork, h->d_Y, h->d_Nt, dev_params(h->prm),
+                                          h->cfg.wall, h->d_flags);
+    count_launch();
+    if (h->P) {
+        k_pc_asm_build<<<h->NA, 256, 0, s>>>(h->d_asm_link_off, h->d_asm_link_idx, h->d_bp, h->d_bq,
+                                              h->d_lp, h->d_lq, h->d_Nt, h->d_G_off, h->d_G,
+                                              h->d_Gwork, h->d_perm, h->d_perm_off, h->d_G_rank,
+                                              1e-11);
+        count_launch();
+    }
+    h->pc_valid = true;
+}
+
+void pc_apply(am_handle* h, const double* r, double* z) {
+    cudaStream_t s = h->stream;
+    k_pc_apply1<<<h->M, 128, 0, s>>>(h->Nb, h->d_blob_off, h->d_minv, h->d_minv_off, h->d_Y, h->d_Nt,
+                                      r, h->d_pc_w, h->d_pc_Uhat);
+    count_launch();
+    if (h->P) {
+        k_pc_apply2<<<h->NA, 128, 0, s>>>(h->Nb, h->M, h->d_asm_link_off, h->d_asm_link_idx, h->d_bp,
+                                           h->d_bq, h->d_lp, h->d_lq, h->d_pc_Uhat, h->d_G, h->d_G_off,
+                                           r, z, h->d_cbuf);
+        count_launch();
+    }
+    k_pc_apply3<<<h->M, 128, 0, s>>>(h->Nb, h->M, h->d_blob_off, h->d_Y, h->d_Nt, h->d_pc_w,
+                                      h->d_pc_Uhat, h->d_body_link_off, h->d_body_link_idx, h->d_lp,
+                                      h->d_lq, z);
+    count_launch();
+}
+
+void project_constraints(am_handle* h, double* x) {
+    if (!h->P) return;
+    cudaStream_t s = h->stream;
+    k_proj_rhs<<<nblk(h->n, 256), 256, 0, s>>>(h->Nb, h->M, h->P, h->d_bp, h->d_bq, h->d_lp, h->d_lq,
+                                                h->d_B, x, h->d_t);
+    count_launch();
+    pc_apply(h, h->d_t, h->d_z);
+    k_axpy<<<nblk(h->n, 256), 256, 0, s>>>(x, h->d_z, h->n, 1.0);
+    count_launch();
+}
+
+static int red_blocks(int n) { return std::min(nblk(n, 256), 2 * num_sms()); }
+
+static double read_scal(am_handle* h, int count) {
+    cudaMemcpyAsync(h->h_scal, h->d_scal, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaStreamSynchronize(h->stream);
+    return h->h_scal[0];
+}
+
+// ||v||_2 into h_scal[0] (synchronous)
+static double norm2(am_handle* h, const double* v) {
+    const int nb = red_blocks(h->n);
+    k_norm_part<<<nb, 256, 0, h->stream>>>(v, h->n, h->d_npart);
+    k_norm_finish<<<1, 256, 0, h->stream>>>(h->d_npart, nb, h->d_scal, 0);
+    count_launch(2);
+    return read_scal(h, 2);
+}
+
+// GMRES(m), right preconditioned, CGS2, on A x = rhs with the operator in
+// FP64 (fp64) or in the handle's precision.  Stops when the true relative
+// residual (same operator) is <= tol or after `budget` iterations.
+// Returns the number of iterations; *rel = final true relative residual.
+static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp64, int budget,
+                 double* rel, int* cycles) {
+    cudaStream_t s = h->stream;
+    const int n = h->n;
+    const int m = h->restart;
+    const size_t ldv = (size_t)h->ldv;
+    const int nb = red_blocks(n);
+    const int nch = std::max(1, std::min(64, nblk(n, 4096)));
+    const int chunk = nblk(n, nch);
+    const double bnorm = norm2(h, rhs);
+    *rel = 0.0;
+    if (bnorm == 0.0) {
+        cudaMemsetAsync(x, 0, n * sizeof(double), s);
+        return 0;
+    }
+    int it = 0;
+    while (true) {
+        double* V0 = h->d_V;
+        op_apply(h, x, h->d_w, fp64);
+        k_residual<<<nb, 256, 0, s>>>(rhs, h->d_w, V0, n, h->d_npart);
+        k_norm_finish<<<1, 256, 0, s>>>(h->d_npart, nb, h->d_scal, 4);
+        count_launch(2);
+        read_scal(h, 6);
+        const double beta = h->h_scal[4];
+        *rel = beta / bnorm;
+        if (*rel <= tol || it >= budget || !(beta == beta)) break;
+        ++*cycles;
+        k_scale<<<nb, 256, 0, s>>>(V0, V0, n, h->d_scal + 5);
+        k_init_g<<<1, 64, 0, s>>>(h->d_g, m + 1, h->d_scal, 4);
+        count_launch(2);
+        int kdone = 0;
+        for (int j = 0; j < m; ++j) {
+            const double* vj = h->d_V + j * ldv;
+            pc_apply(h, vj, h->d_z);
+            op_apply(h, h->d_z, h->d_w, fp64);
+            const int jp1 = j + 1;
+            for (int pass = 0; pass < 2; ++pass) {
+                k_dots<<<dim3(nch, jp1), 256, 0, s>>>(h->d_V, ldv, h->d_w, n, chunk, h->d_part, nch);
+                k_orth<<<nb, 256, jp1 * sizeof(double), s>>>(h->d_V, ldv, h->d_w, n, h->d_part, nch, jp1,
+                                                            h->d_coef, pass, pass ? h->d_npart : nullptr);
+                count_launch(2);
+            }
+            k_arnoldi_finish<<<1, 256, 0, s>>>(j, h->d_coef, h->d_npart, nb, h->d_Hm, m + 1, h->d_cs,
+                                                h->d_sn, h->d_g, h->d_scal);
+            k_scale<<<nb, 256, 0, s>>>(h->d_w, h->d_V + (j + 1) * ldv, n, h->d_scal + 2);
+            count_launch(2);
+            read_scal(h, 3);
+            ++it;
+            kdone = j + 1;
+            const double est = h->h_scal[0] / bnorm;
+            if (est <= tol || it >= budget || h->h_scal[1] == 0.0 || !(est == est)) break;
+        }
+        k_hessenberg_solve<<<1, 32, 0, s>>>(kdone, h->d_Hm, m + 1, h->d_g, h->d_xi);
+        k_combine<<<nb, 256, 0, s>>>(h->d_V, ldv, h->d_xi, kdone, n, h->d_t);
+        count_launch(2);
+        pc_apply(h, h->d_t, h->d_z);
+        k_axpy<<<nb, 256, 0, s>>>(x, h->d_z, n, 1.0);
+        count_launch();
+    }
+    return it;
+}
+
+int solve(am_handle* h, am_step_stats* st) {
+    const double tol = h->cfg.tol;
+    const int budget = h->cfg.max_iter;
+    int cycles = 0, it = 0;
+    double rel = 0.0;
+    if (h->cfg.precision == AM_FP64) {
+        it = gmres(h, h->d_b, h->d_x, tol, true, budget, &rel, &cycles);
+    } else {
+        // Iterative refinement: FP64 residual outside, mixed-precision
+        // GMRES for the correction inside.
+        cudaStream_t s = h->stream;
+        const int nb = red_blocks(h->n);
+        const double bnorm = norm2(h, h->d_b);
+        for (int outer = 0; outer < 20; ++outer) {
+            op_apply(h, h->d_x, h->d_w, true);
+            k_residual<<<nb, 256, 0, s>>>(h->d_b, h->d_w, h->d_rir, h->n, h->d_npart);
+            k_norm_finish<<<1, 256, 0, s>>>(h->d_npart, nb, h->d_scal, 4);
+            count_launch(2);
+            read_scal(h, 6);
+            rel = bnorm > 0.0 ? h->h_scal[4] / bnorm : 0.0;
+            if (rel <= tol || it >= budget || !(rel == rel)) break;
+            const double tin = std::max(1e-6, 0.3 * tol / rel);
+            cudaMemsetAsync(h->d_dx, 0, h->n * sizeof(double), s);
+            double rin = 0.0;
+            it += gmres(h, h->d_rir, h->d_dx, tin, false, budget - it, &rin, &cycles);
+            k_axpy<<<nb, 256, 0, s>>>(h->d_x, h->d_dx, h->n, 1.0);
+            count_launch();
+        }
+    }
+    if (h->P) {
+        k_constraint_residual<<<1, 256, 0, h->stream>>>(h->Nb, h->M, h->P, h->d_bp, h->d_bq, h->d_lp,
+                                                        h->d_lq, h->d_B, h->d_x, h->d_scal, 6);
+        count_launch();
+        read_scal(h, 7);
+        st->constraint_residual = h->h_scal[6];
+    } else {
+        st->constraint_residual = 0.0;
+    }
+    st->iterations = it;
+    st->restarts = cycles;
+    st->rel_residual = rel;
+    return (rel <= tol) ? AM_OK : AM_ERR_NOT_CONVERGED;
+}
+
+int advance(am_handle* h, double dt, am_step_stats* st) {
+    cudaStream_t s = h->stream;
+    cudaMemsetAsync(h->d_red, 0, 2 * sizeof(double), s);
+    k_euler_reconstruct<<<h->NA, 128, 0, s>>>(h->d_asm_body_off, h->d_asm_body_idx, h->d_asm_link_off,
+                                               h->d_asm_link_idx, h->d_bp, h->d_bq,
+                                               h->d_x + 3 * (size_t)h->Nb, h->d_q, h->d_theta,
+                                               h->d_dlp1, h->d_dlq1, h->d_pplus, h->d_pplus_off, dt,
+                                               h->d_qnew, h->d_thnew, h->d_zbuf, h->d_red);
+    count_launch();
+    if (h->P) {
+        k_correct<<<h->NA, 256, 0, s>>>(h->d_asm_body_off, h->d_asm_body_idx, h->d_asm_link_off,
+                                         h->d_asm_link_idx, h->d_bp, h->d_bq, h->d_body_local,
+                                         h->d_link_local, h->d_body_link_off, h->d_body_link_idx,
+                                         h->d_dlp1, h->d_dlq1, h->d_qnew, h->d_thnew, h->d_red,
+                                         h->cfg.corr_tol, h->cfg.corr_max_iter, h->d_corr,
+                                         h->d_corr_off, h->d_iters, h->d_flags);
+        k_g2<<<std::max(1, std::min(nblk(h->P, 256), 64)), 256, 0, s>>>(
+            h->P, h->d_bp, h->d_bq, h->d_qnew, h->d_thnew, h->d_dlp1, h->d_dlq1, h->d_red + 1);
+        count_launch(2);
+    }
+    cudaMemcpyAsync(h->d_q, h->d_qnew, 3 * h->M * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(h->d_theta, h->d_thnew, 4 * h->M * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (h->P) {
+        cudaMemcpyAsync(h->d_dlp, h->d_dlp1, 3 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(h->d_dlq, h->d_dlq1, 3 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    }
+    cudaMemcpyAsync(h->h_scal, h->d_red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h->h_iters, h->d_iters, h->NA * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    st->g2_before = h->h_scal[0];
+    st->g2_after = h->P ? h->h_scal[1] : 0.0;
+    int mx = 0;
+    for (int a = 0; a < h->NA; ++a) mx = std::max(mx, h->h_iters[a]);
+    st->corr_iterations = mx;
+    return AM_OK;
+}
+
+}  // namespace am

@@ -1,0 +1,33 @@
+// Host-side entry points of ops.cu (kernel orchestration for one handle).
+#pragma once
+#include "am_internal.cuh"
+
+namespace am {
+
+// device error flags (h->d_flags[0])
+constexpr int kFlagWall = 1;        // a blob centre at or below height a
+constexpr int kFlagSingular = 2;    // a body block of M or N~ not SPD
+constexpr int kFlagCorrection = 4;  // correction normal equations not SPD
+
+// Geometry of the current pose: blob positions, lab link vectors, B, b.
+void launch_geometry(am_handle* h);
+// out = A y (Eq. linear_system) with the handle's mobility precision or FP64.
+void op_apply(am_handle* h, const double* y, double* out, bool fp64);
+// Blob mobility product only: u = M lambda (3Nb).
+void mobility_apply(am_handle* h, const double* lam, double* u, bool fp64);
+// Block-diagonal preconditioner (Sec. 3.1): build at the current pose, apply.
+void pc_build(am_handle* h);
+void pc_apply(am_handle* h, const double* r, double* z);
+// Project the U block of x onto C U = B with the preconditioner
+// (x += P~^-1 (0, 0, B - C U)).
+void project_constraints(am_handle* h, double* x);
+// Solve A x = b (d_b, d_x in the handle; d_x holds the initial guess).
+// Returns AM_OK or AM_ERR_NOT_CONVERGED; fills iteration fields of st.
+int solve(am_handle* h, am_step_stats* st);
+// Euler update + reconstruction + correction (Sec. 4.3) from the solution
+// in d_x; writes the new q, theta into the handle.
+int advance(am_handle* h, double dt, am_step_stats* st);
+// Read and clear the device error flags.
+int take_flags(am_handle* h);
+
+}  // namespace am

@@ -1,0 +1,294 @@
+// All-pairs blob mobility product u = M lambda (Sec. 2.3, Eq. RPY).
+//
+// Free space, equal radii a, d = r_i - r_j, r = |d|, A1 = 1/(8 pi eta),
+// mu0 = 1/(6 pi eta a):
+//   r >= 2a:  M = A1/r [(1 + 2a^2/(3r^2)) I + (1 - 2a^2/r^2) dhat dhat]
+//   r <  2a:  M = mu0 [(1 - 9r/(32a)) I + (3r/(32a)) dhat dhat],  M_ii = mu0 I.
+// No-slip wall at z = 0: add the image part, the double surface average of
+// the image terms of Blake's Green's function.  Written in the basis
+// {delta_ij, Rh_i Rh_j, Rh_i e3_j, e3_i Rh_j, e3_i e3_j} with R = x - y*,
+// y* = (y1, y2, -y3), s = 1/|R|, Rh = R s, h = y3 (source height),
+// x3 = target height, ez = R3 s, A = a^2 s^2:
+//   M_img = A1 s [ cI delta + cRR Rh Rh + cRz Rh e3 + czR e3 Rh + czz e3 e3 ]
+//   cI  = -1 - 2 h x3 s^2 + A (2 ez^2 - 2/3) + A^2 (2/3 - 10/3 ez^2)
+//   cRR = -1 + 6 h x3 s^2 + A (2 - 10 ez^2) + A^2 (70/3 ez^2 - 10/3)
+//   cRz = 2 h s + ez [ -12 h x3 s^2 + A (20 ez^2 - 4) + A^2 (40/3 - 140/3 ez^2) ]
+//   czR = 2 h s - 20/3 A^2 ez
+//   czz = -4 h^2 s^2 + A (-4 ez^2) + A^2 (20 ez^2 - 8/3)
+// (derived from Blake's image system by applying (1 + a^2/6 lap_x)
+// (1 + a^2/6 lap_y), which is exact for blobs whose centres are above a).
+//
+// Layout: one thread per target blob, 128 targets per block; sources are
+// staged through shared memory 128 at a time; the sources are split into
+// `splits` contiguous chunks (grid.y) so that small systems still fill the
+// 152 SMs; each (target block, chunk) writes its partial sums, and a second
+// kernel adds the chunks.
+#include "am_internal.cuh"
+#include "rpy_pair.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+namespace am {
+
+std::atomic<long long> g_launches{0};
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    return sms;
+}
+
+RpyParams make_params(double eta, double a) {
+    RpyParams p;
+    p.a = a;
+    p.a2 = a * a;
+    p.four_a2 = 4.0 * a * a;
+    p.inv8pieta = 1.0 / (8.0 * kPi * eta);
+    p.k_far2 = p.inv8pieta * 2.0 * a * a / 3.0;
+    p.k_far3 = p.inv8pieta * 2.0 * a * a;
+    p.mu0 = 1.0 / (6.0 * kPi * eta * a);
+    p.k_near1 = 9.0 / (32.0 * a);
+    p.k_near2 = p.mu0 * 3.0 / (32.0 * a);
+    return p;
+}
+
+Split choose_split(int n, int precision) {
+    Split s{1, std::max(n, 1)};
+    if (n <= 0) return s;
+    int tiles = (n + kTile - 1) / kTile;
+    int tblocks = (n + kThreads - 1) / kThreads;
+    int want = 4 * num_sms();              // blocks to fill the GPU
+    int splits = std::max(1, std::min(tiles, (want + tblocks - 1) / tblocks));
+    int per = (tiles + splits - 1) / splits;  // tiles per chunk
+    s.chunk = per * kTile;
+    s.splits = (n + s.chunk - 1) / s.chunk;
+    (void)precision;
+    return s;
+}
+
+template <bool WALL>
+__global__ void __launch_bounds__(kThreads)
+rpy_partial_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam,
+                double* __restrict__ part, int n, int chunk, RpyParamsDev p) {
+    __shared__ double4_32a sr[kTile];
+    __shared__ double sl[3 * kTile];
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    const int j0 = blockIdx.y * chunk;
+    const int j1 = min(n, j0 + chunk);
+    double4_32a ri = (i < n) ? r4[i] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int jt = j0; jt < j1; jt += kTile) {
+        const int cnt = min(kTile, j1 - jt);
+        __syncthreads();
+        if (threadIdx.x < cnt) sr[threadIdx.x] = r4[jt + threadIdx.x];
+        for (int k = threadIdx.x; k < 3 * cnt; k += kThreads) sl[k] = lam[3 * (size_t)jt + k];
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < cnt; ++k) {
+            const double4_32a rj = sr[k];
+            const double lx = sl[3 * k], ly = sl[3 * k + 1], lz = sl[3 * k + 2];
+            pair_free_f64(ri.x - rj.x, ri.y - rj.y, ri.z - rj.z, lx, ly, lz, p, ux, uy, uz);
+            if (WALL)
+                pair_image_f64(ri.x - rj.x, ri.y - rj.y, ri.z + rj.z, ri.z, rj.z, lx, ly, lz, p,
+                               ux, uy, uz);
+        }
+    }
+    if (i < n) {
+        double* o = part + (size_t)blockIdx.y * 3 * n + 3 * (size_t)i;
+        o[0] = ux; o[1] = uy; o[2] = uz;
+    }
+}
+
+// Positions as hi + lo float pairs: differences of nearby blobs are formed
+// from the exact hi difference plus the lo difference, so they keep FP32
+// relative accuracy even far from the origin.  Pair terms and the sum over
+// one tile are FP32; tile sums are added in FP64.
+template <bool WALL>
+__global__ void __launch_bounds__(kThreads)
+rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
+                  const double* __restrict__ lam, double* __restrict__ part, int n,
+                  int chunk, RpyParamsF p) {
+    __shared__ float4 sh[kTile];
+    __shared__ float4 so[kTile];
+    __shared__ float sl[3 * kTile];
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    const int j0 = blockIdx.y * chunk;
+    const int j1 = min(n, j0 + chunk);
+    float4 hi_i = (i < n) ? hi[i] : make_float4(0.f, 0.f, 1.f, 0.f);
+    float4 lo_i = (i < n) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    double Ux = 0.0, Uy = 0.0, Uz = 0.0;
+    for (int jt = j0; jt < j1; jt += kTile) {
+        const int cnt = min(kTile, j1 - jt);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            sh[threadIdx.x] = hi[jt + threadIdx.x];
+            so[threadIdx.x] = lo[jt + threadIdx.x];
+        }
+        for (int k = threadIdx.x; k < 3 * cnt; k += kThreads) sl[k] = (float)lam[3 * (size_t)jt + k];
+        __syncthreads();
+        float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < cnt; ++k) {
+            const float4 h = sh[k];
+            const float4 l = so[k];
+            const float lx = sl[3 * k], ly = sl[3 * k + 1], lz = sl[3 * k + 2];
+            float dx = (hi_i.x - h.x) + (lo_i.x - l.x);
+            float dy = (hi_i.y - h.y) + (lo_i.y - l.y);
+            float dz = (hi_i.z - h.z) + (lo_i.z - l.z);
+            pair_free_f32(dx, dy, dz, lx, ly, lz, p, ux, uy, uz);
+            if (WALL) {
+                float Rz = (hi_i.z + h.z) + (lo_i.z + l.z);
+                pair_image_f32(dx, dy, Rz, hi_i.z, h.z, lx, ly, lz, p, ux, uy, uz);
+            }
+        }
+        Ux += (double)ux; Uy += (double)uy; Uz += (double)uz;
+    }
+    if (i < n) {
+        double* o = part + (size_t)blockIdx.y * 3 * n + 3 * (size_t)i;
+        o[0] = Ux; o[1] = Uy; o[2] = Uz;
+    }
+}
+
+__global__ void pack_positions(const double* __restrict__ r3, double4_32a* __restrict__ r4,
+                               float4* __restrict__ hi, float4* __restrict__ lo, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = r3[3 * (size_t)i], y = r3[3 * (size_t)i + 1], z = r3[3 * (size_t)i + 2];
+    if (r4) r4[i] = make_double4_32a(x, y, z, 0.0);
+    if (hi) {
+        float hx = (float)x, hy = (float)y, hz = (float)z;
+        hi[i] = make_float4(hx, hy, hz, 0.f);
+        lo[i] = make_float4((float)(x - hx), (float)(y - hy), (float)(z - hz), 0.f);
+    }
+}
+
+__global__ void sum_partials(const double* __restrict__ part, double* __restrict__ u,
+                             int n3, int splits) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n3) return;
+    double s = 0.0;
+    for (int t = 0; t < splits; ++t) s += part[(size_t)t * n3 + k];
+    u[k] = s;
+}
+
+static RpyParamsF f32_params(const RpyParams& q) {
+    return RpyParamsF{(float)q.a2, (float)q.four_a2, (float)q.inv8pieta, (float)q.k_far2,
+                      (float)q.k_far3, (float)q.mu0, (float)q.k_near1, (float)q.k_near2};
+}
+
+void launch_rpy_partial_f64(const double4_32a* r4, const double* lam, double* part, int n,
+                            const Split& sp, const RpyParams& prm, int wall, cudaStream_t st) {
+    if (n <= 0) return;
+    dim3 grid((n + kThreads - 1) / kThreads, sp.splits);
+    if (wall)
+        rpy_partial_f64<true><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, dev_params(prm));
+    else
+        rpy_partial_f64<false><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, dev_params(prm));
+    count_launch();
+}
+
+void launch_rpy_partial_mixed(const float4* hi, const float4* lo, const double* lam, double* part,
+                              int n, const Split& sp, const RpyParams& prm, int wall,
+                              cudaStream_t st) {
+    if (n <= 0) return;
+    dim3 grid((n + kThreads - 1) / kThreads, sp.splits);
+    if (wall)
+        rpy_partial_mixed<true><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, f32_params(prm));
+    else
+        rpy_partial_mixed<false><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, f32_params(prm));
+    count_launch();
+}
+
+void launch_pack_positions(const double* r3, double4_32a* r4, float4* hi, float4* lo, int n,
+                           cudaStream_t st) {
+    if (n <= 0) return;
+    pack_positions<<<(n + 255) / 256, 256, 0, st>>>(r3, r4, hi, lo, n);
+    count_launch();
+}
+
+void launch_sum_partials(const double* part, double* u, int n, int splits, cudaStream_t st) {
+    if (n <= 0) return;
+    int n3 = 3 * n;
+    sum_partials<<<(n3 + 255) / 256, 256, 0, st>>>(part, u, n3, splits);
+    count_launch();
+}
+
+}  // namespace am
+
+// ------------------------------------------------------------ C ABI -------
+namespace {
+thread_local std::string t_err = "";
+int fail(int code, const char* msg) {
+    t_err = msg;
+    return code;
+}
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+}  // namespace
+
+namespace am {
+const char* thread_error() { return t_err.c_str(); }
+}
+
+extern "C" AM_API size_t am_rpy_matvec_workspace(int n, int precision) {
+    if (n <= 0) return 0;
+    am::Split sp = am::choose_split(n, precision);
+    size_t pos = (precision == AM_MIXED) ? 2 * align256((size_t)n * sizeof(float4))
+                                         : align256((size_t)n * sizeof(double4_32a));
+    return pos + align256((size_t)sp.splits * 3 * n * sizeof(double));
+}
+
+extern "C" AM_API int am_rpy_matvec(const double* d_r, const double* d_lambda, double* d_u, int n,
+                                    double eta, double a, int wall, int precision, void* d_work,
+                                    size_t work_bytes, void* stream) {
+    if (n < 0) return fail(AM_ERR_ARG, "am_rpy_matvec: n < 0");
+    if (!(eta > 0.0) || !(a > 0.0)) return fail(AM_ERR_ARG, "am_rpy_matvec: eta and a must be > 0");
+    if (wall != 0 && wall != 1) return fail(AM_ERR_ARG, "am_rpy_matvec: wall must be 0 or 1");
+    if (precision != AM_FP64 && precision != AM_MIXED)
+        return fail(AM_ERR_ARG, "am_rpy_matvec: unknown precision");
+    if (n == 0) return AM_OK;
+    if (!d_r || !d_lambda || !d_u || !d_work) return fail(AM_ERR_ARG, "am_rpy_matvec: NULL pointer");
+    if (work_bytes < am_rpy_matvec_workspace(n, precision))
+        return fail(AM_ERR_ARG, "am_rpy_matvec: workspace too small");
+    if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0)
+        return fail(AM_ERR_ARG, "am_rpy_matvec: workspace not 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    am::Split sp = am::choose_split(n, precision);
+    am::RpyParams prm = am::make_params(eta, a);
+    char* w = static_cast<char*>(d_work);
+    if (precision == AM_MIXED) {
+        float4* hi = reinterpret_cast<float4*>(w);
+        float4* lo = reinterpret_cast<float4*>(w + align256((size_t)n * sizeof(float4)));
+        double* part = reinterpret_cast<double*>(w + 2 * align256((size_t)n * sizeof(float4)));
+        am::launch_pack_positions(d_r, nullptr, hi, lo, n, st);
+        am::launch_rpy_partial_mixed(hi, lo, d_lambda, part, n, sp, prm, wall, st);
+        am::launch_sum_partials(part, d_u, n, sp.splits, st);
+    } else {
+        double4_32a* r4 = reinterpret_cast<double4_32a*>(w);
+        double* part = reinterpret_cast<double*>(w + align256((size_t)n * sizeof(double4_32a)));
+        am::launch_pack_positions(d_r, r4, nullptr, nullptr, n, st);
+        am::launch_rpy_partial_f64(r4, d_lambda, part, n, sp, prm, wall, st);
+        am::launch_sum_partials(part, d_u, n, sp.splits, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AM_ERR_CUDA, cudaGetErrorString(e));
+    return AM_OK;
+}
+
+extern "C" AM_API int am_flops_per_pair(int wall) {
+    // Counted from pair_free_* and pair_image_* with FMA = 2 (rsqrt = 1):
+    // free: difference 3, r^2 5, rsqrt 1, ri^2 1, c1 3, c2 4, d.lambda 5,
+    //       scale 1, accumulate 12  -> 35
+    // image: Rz 1, R^2 5, rsqrt 1, s^2 1, hs 1, hx 2, ez 1, ez^2 1, A 1,
+    //        A^2 1, cI 10, cRR 10, cRz 12, czR 3, czz 9, rhat 2, dotR 5,
+    //        t 3, pre 1, accumulate 19  -> 89
+    return wall ? 35 + 89 : 35;
+}
+
+extern "C" AM_API long long am_kernel_launches(void) { return am::g_launches.load(); }

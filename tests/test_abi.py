@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/am.h declares; argument checks that need no GPU behave as stated."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2107_10800_gb300 import build, binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "am.h")).read()
+    return sorted(set(re.findall(r"AM_API\s+[\w\s\*]+?\b(am_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("am_create", "am_set_bodies", "am_set_constraints", "am_solve_step",
+                     "am_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in binding.SIGNATURES, name
+
+
+def test_only_am_symbols_exported():
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH],
+                         capture_output=True, text=True).stdout
+    funcs = [l.split()[-1] for l in out.splitlines() if " T " in l]
+    assert funcs and all(f.startswith("am_") for f in funcs), funcs
+
+
+def test_flop_counts(L):
+    assert binding.flops_per_pair(0) == 35
+    assert binding.flops_per_pair(1) > binding.flops_per_pair(0)
+
+
+def test_create_rejects_bad_config(L):
+    bad = [dict(eta=0.0), dict(a=-1.0), dict(wall=2), dict(tol=0.0), dict(restart=500)]
+    for kw in bad:
+        args = dict(eta=1.0, a=0.1, wall=0, precision=0, n_systems=1, tol=1e-8, restart=50,
+                    max_iter=100, corr_tol=1e-10, corr_max_iter=10, cuda_stream=None)
+        args.update({"blob_radius" if k == "a" else k: v for k, v in kw.items()})
+        args.pop("a", None)
+        cfg = binding.Config(args["eta"], args.get("blob_radius", 0.1), args["wall"],
+                             args["precision"], args["n_systems"], args["tol"], args["restart"],
+                             args["max_iter"], args["corr_tol"], args["corr_max_iter"], None)
+        h = ctypes.c_void_p()
+        assert L.am_create(ctypes.byref(cfg), ctypes.byref(h)) == binding.AM_ERR_ARG
+        assert not h.value
+
+
+def test_matvec_argument_checks(L):
+    assert L.am_rpy_matvec(None, None, None, -1, 1.0, 0.1, 0, 0, None, 0, None) == binding.AM_ERR_ARG
+    assert L.am_rpy_matvec(None, None, None, 0, 1.0, 0.1, 0, 0, None, 0, None) == binding.AM_OK
+    assert L.am_rpy_matvec(None, None, None, 10, 0.0, 0.1, 0, 0, None, 0, None) == binding.AM_ERR_ARG
+    assert L.am_rpy_matvec(None, None, None, 10, 1.0, 0.1, 0, 7, None, 0, None) == binding.AM_ERR_ARG
+    assert b"precision" in L.am_last_error(None)
+    assert L.am_rpy_matvec_workspace(0, 0) == 0
+    assert L.am_rpy_matvec_workspace(1000, 0) >= 1000 * 32 + 1000 * 24
+
+
+def test_null_handle_is_rejected(L):
+    assert L.am_solve(None, None, None, None, None) == binding.AM_ERR_ARG
+    L.am_destroy(None)
