@@ -212,6 +212,32 @@ AM_API int am_rpy_matvec(const double* d_r, const double* d_lambda,
                          void* stream);
 AM_API size_t am_rpy_matvec_workspace(int n, int precision);
 
+/* Allocation-free variant of am_rpy_matvec for callers that cannot call
+ * cudaMalloc: code that runs where allocating is not allowed or not safe,
+ * e.g. inside another library's allocation-free execution path, a host
+ * callback, or a process whose device memory is owned by a pool it must
+ * not grow.  The caller still passes inputs and outputs (d_r, d_lambda,
+ * d_u, n, eta, a, wall, precision and stream mean what they mean for
+ * am_rpy_matvec); the scratch lives in a fixed device array of
+ * AM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *  - Limit: n must satisfy am_rpy_matvec_workspace(n, precision) <=
+ *    AM_NOALLOC_SCRATCH_BYTES (about 100,000 blobs); larger n returns
+ *    AM_ERR_ARG with a message, and nothing is launched.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, once per device, with that device current);
+ *    make that first call before any stream capture.
+ *  - Every call on a device shares the one array: calls that overlap on the
+ *    GPU (other streams, other threads) race and corrupt each other.  The
+ *    array keeps the last call's contents; no part of it needs to start at
+ *    zero, since each call writes every scratch value it reads.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * The paper has no counterpart to this entry point. */
+#define AM_NOALLOC_SCRATCH_BYTES (8u << 20)
+AM_API int am_rpy_matvec_noalloc(const double* d_r, const double* d_lambda, double* d_u,
+                                 int n, double eta, double a, int wall, int precision,
+                                 void* stream);
+
 /* Pair arithmetic of the mobility kernels, counted with FMA = 2 flops, for
  * roofline figures: per pair of the free-space tensor and per pair of the
  * wall tensor (free part plus image part). */

@@ -64,6 +64,8 @@ SIGNATURES = {
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp,
                                      ctypes.c_size_t, _vp]),
     "am_rpy_matvec_workspace": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "am_rpy_matvec_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]),
     "am_flops_per_pair": (ctypes.c_int, [ctypes.c_int]),
     "am_kernel_launches": (ctypes.c_longlong, []),
     "am_mobility_timing": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -265,6 +267,19 @@ def rpy_matvec_ptr(d_r, d_lam, d_u, n, eta, a, wall, precision, d_work, work_byt
     rc = lib().am_rpy_matvec(d_r, d_lam, d_u, n, eta, a, wall, prec, d_work, work_bytes, stream)
     if rc != AM_OK:
         raise AmError(rc, lib().am_last_error(None).decode())
+
+
+def rpy_matvec_noalloc_ptr(d_r, d_lam, d_u, n, eta, a, wall, precision, stream=None):
+    """am_rpy_matvec_noalloc on raw device pointers (ints): the mobility
+    product with the library's fixed scratch array instead of a workspace,
+    for callers that cannot allocate device memory."""
+    prec = {"fp64": AM_FP64, "mixed": AM_MIXED}.get(precision, precision)
+    rc = lib().am_rpy_matvec_noalloc(d_r, d_lam, d_u, n, eta, a, wall, prec, stream)
+    if rc != AM_OK:
+        raise AmError(rc, lib().am_last_error(None).decode())
+
+
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 def rpy_matvec_workspace(n, precision):

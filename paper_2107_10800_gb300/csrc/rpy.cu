@@ -234,6 +234,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 namespace am {
 const char* thread_error() { return t_err.c_str(); }
+void set_thread_error(const std::string& msg) { t_err = msg; }
 }
 
 extern "C" AM_API size_t am_rpy_matvec_workspace(int n, int precision) {
