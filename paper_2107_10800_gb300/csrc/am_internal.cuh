@@ -33,7 +33,7 @@ struct RpyParams {
 RpyParams make_params(double eta, double a);
 
 // Source splitting of the all-pairs product: grid (target blocks, splits).
-struct Split { int splits; int chunk; };
+struct Split { int splits; int chunk; int tpt; };
 Split choose_split(int n, int precision);
 
 // ---- mobility product launchers (rpy.cu) ------------------------------
@@ -49,6 +49,16 @@ void launch_pack_positions(const double* r3, double4_32a* r4, float4* hi, float4
                            int n, cudaStream_t st);
 void launch_sum_partials(const double* part, double* u, int n, int splits,
                          cudaStream_t st);
+
+// Control block of a device-side Arnoldi cycle.
+struct ArnoldiCtrl {
+    int j;          // current column (number of completed steps when stopped)
+    int it;         // steps taken in this cycle
+    int budget;     // steps allowed in this cycle
+    int m;          // restart length
+    int stop;       // set when the cycle ends
+    double tol_abs; // stop when the residual estimate is <= tol_abs
+};
 
 // ---- device helpers -----------------------------------------------------
 // R(theta) v = 2 [ p (p.v) + s (p x v) + (s^2 - 1/2) v ]   (App. B, Eq. rot_mat)
@@ -106,6 +116,7 @@ struct am_handle {
     std::vector<int> G_dim;
     long long minv_total = 0, G_total = 0, pplus_total = 0, corr_total = 0;
     int max_body_blobs = 0;
+    int max_asm_links = 0;
     bool active_links = false;
     bool links_connected = true;
 
@@ -128,10 +139,16 @@ struct am_handle {
     double* d_pplus = nullptr; long long* d_pplus_off = nullptr;
     int* d_body_local = nullptr;
 
-    // device: preconditioner
-    double *d_minv = nullptr, *d_pcwork = nullptr, *d_Y = nullptr, *d_Nt = nullptr;
+    // device: preconditioner (matrices in FP64, or FP32 when pc32)
+    bool pc32 = false;
+    void *d_minv = nullptr, *d_pcwork = nullptr, *d_Y = nullptr;
+    double* d_Nt = nullptr;
     long long* d_minv_off = nullptr;
-    double* d_G = nullptr; double* d_Gwork = nullptr;
+    void *d_G = nullptr, *d_Gwork = nullptr;
+    int *d_pcw_body = nullptr, *d_pcw_chunk = nullptr, *d_pcw_off = nullptr;
+    int *d_pca_asm = nullptr, *d_pca_chunk = nullptr;
+    int n_pcw = 0, n_pca = 0;
+    double* d_ytp = nullptr;
     long long* d_G_off = nullptr; int* d_G_rank = nullptr;
     int* d_perm = nullptr; long long* d_perm_off = nullptr;
     double *d_pc_w = nullptr, *d_pc_Uhat = nullptr;
@@ -139,7 +156,7 @@ struct am_handle {
 
     // device: solver vectors
     double *d_b = nullptr, *d_x = nullptr, *d_xprev = nullptr, *d_t = nullptr,
-           *d_z = nullptr, *d_w = nullptr, *d_V = nullptr;
+           *d_z = nullptr, *d_w = nullptr, *d_V = nullptr, *d_Z = nullptr;
     double *d_Hm = nullptr, *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr,
            *d_coef = nullptr, *d_part = nullptr, *d_scal = nullptr, *d_xi = nullptr,
            *d_npart = nullptr, *d_rir = nullptr, *d_dx = nullptr;
@@ -150,7 +167,7 @@ struct am_handle {
 
     // device: mobility partial sums
     double* d_mv = nullptr;
-    am::Split split{1, 0};
+    am::Split split{1, 0, 1};
 
     // device: step
     double *d_qnew = nullptr, *d_thnew = nullptr, *d_corr = nullptr, *d_red = nullptr;
@@ -166,6 +183,19 @@ struct am_handle {
 
     cudaEvent_t ev[8] = {};
     bool geometry_valid = false;
+
+    // device-resident Arnoldi cycle: control block, fixed in/out vectors and
+    // one CUDA graph (WHILE node) per operator precision
+    am::ArnoldiCtrl* d_ctrl = nullptr;
+    am::ArnoldiCtrl* h_ctrl = nullptr;
+    double *d_vj = nullptr, *d_zj = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    long long graph_gen[2] = {-1, -1};
+    long long body_launches[2] = {0, 0};
+    long long body_pairs[2] = {0, 0};
+    long long layout_gen = 0;
+    bool graphs_ok = true;
 
     // per-launch timing of the all-pairs kernel (am_mobility_timing)
     bool timing = false;

@@ -35,6 +35,11 @@ cudaError_t dalloc(T** p, size_t count) {
     *p = nullptr;
     return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
 }
+cudaError_t balloc(void** p, size_t bytes) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    return cudaMalloc(p, std::max<size_t>(bytes, 16));
+}
 template <class T>
 void dfree(T** p) {
     if (*p) cudaFree(*p);
@@ -103,6 +108,8 @@ void free_links(am_handle* h) {
     dfree(&h->d_G); dfree(&h->d_Gwork); dfree(&h->d_G_off); dfree(&h->d_G_rank);
     dfree(&h->d_perm); dfree(&h->d_perm_off);
     dfree(&h->d_corr); dfree(&h->d_corr_off); dfree(&h->d_zbuf); dfree(&h->d_cbuf);
+    dfree(&h->d_pca_asm); dfree(&h->d_pca_chunk);
+    h->n_pca = 0;
 }
 
 void free_bodies(am_handle* h) {
@@ -112,12 +119,16 @@ void free_bodies(am_handle* h) {
     dfree(&h->d_r4); dfree(&h->d_d4); dfree(&h->d_rhi); dfree(&h->d_rlo); dfree(&h->d_r3);
     dfree(&h->d_minv); dfree(&h->d_pcwork); dfree(&h->d_Y); dfree(&h->d_Nt); dfree(&h->d_minv_off);
     dfree(&h->d_pc_w); dfree(&h->d_pc_Uhat); dfree(&h->d_mv);
+    dfree(&h->d_pcw_body); dfree(&h->d_pcw_chunk); dfree(&h->d_pcw_off); dfree(&h->d_ytp);
+    h->n_pcw = 0;
     dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters);
 }
 
 void free_solver(am_handle* h) {
     dfree(&h->d_b); dfree(&h->d_x); dfree(&h->d_xprev); dfree(&h->d_t); dfree(&h->d_z);
-    dfree(&h->d_w); dfree(&h->d_V); dfree(&h->d_rir); dfree(&h->d_dx);
+    dfree(&h->d_w); dfree(&h->d_V); dfree(&h->d_Z); dfree(&h->d_rir); dfree(&h->d_dx);
+    dfree(&h->d_vj); dfree(&h->d_zj);
+    h->layout_gen++;
     dfree(&h->d_Hm); dfree(&h->d_cs); dfree(&h->d_sn); dfree(&h->d_g); dfree(&h->d_coef);
     dfree(&h->d_xi); dfree(&h->d_part); dfree(&h->d_npart);
 }
@@ -130,6 +141,9 @@ int alloc_solver(am_handle* h) {
     CK(dalloc(&h->d_t, n)); CK(dalloc(&h->d_z, n)); CK(dalloc(&h->d_w, n));
     CK(dalloc(&h->d_rir, n)); CK(dalloc(&h->d_dx, n));
     CK(dalloc(&h->d_V, (size_t)h->ldv * (m + 1)));
+    CK(dalloc(&h->d_vj, n)); CK(dalloc(&h->d_zj, n));
+    h->layout_gen++;
+    CK(dalloc(&h->d_Z, (size_t)h->ldv * m));
     CK(dalloc(&h->d_Hm, (size_t)(m + 1) * m)); CK(dalloc(&h->d_cs, m)); CK(dalloc(&h->d_sn, m));
     CK(dalloc(&h->d_g, m + 1)); CK(dalloc(&h->d_coef, m + 1)); CK(dalloc(&h->d_xi, m + 1));
     CK(dalloc(&h->d_part, (size_t)(m + 1) * 64)); CK(dalloc(&h->d_npart, 4 * am::num_sms() + 64));
@@ -141,6 +155,7 @@ int alloc_solver(am_handle* h) {
 int build_links(am_handle* h, int P, const int* bp, const int* bq) {
     const int M = h->M, NA = h->NA;
     free_links(h);
+    h->layout_gen++;
     h->P = P;
     h->bp.assign(bp, bp + P);
     h->bq.assign(bq, bq + P);
@@ -169,6 +184,8 @@ int build_links(am_handle* h, int P, const int* bp, const int* bq) {
     }
     h->asm_link_off = al_off;
     h->asm_link_idx = al_idx;
+    h->max_asm_links = 0;
+    for (int a = 0; a < NA; ++a) h->max_asm_links = std::max(h->max_asm_links, al_off[a + 1] - al_off[a]);
     // connectivity: bodies of every articulated body joined by its links
     std::vector<int> parent(M);
     std::iota(parent.begin(), parent.end(), 0);
@@ -249,7 +266,15 @@ int build_links(am_handle* h, int P, const int* bp, const int* bq) {
     CK(dalloc(&h->d_asm_link_off, NA + 1)); CK(dalloc(&h->d_asm_link_idx, P));
     CK(dalloc(&h->d_link_local, P));
     CK(dalloc(&h->d_pplus, pplus.size())); CK(dalloc(&h->d_pplus_off, NA + 1));
-    CK(dalloc(&h->d_G, goff[NA])); CK(dalloc(&h->d_Gwork, 2 * goff[NA]));
+    const size_t esz = h->pc32 ? sizeof(float) : sizeof(double);
+    CK(balloc(&h->d_G, goff[NA] * esz)); CK(balloc(&h->d_Gwork, 2 * goff[NA] * esz));
+    std::vector<int> pca_asm, pca_chunk;
+    for (int a = 0; a < NA; ++a) {
+        const int m = 3 * (al_off[a + 1] - al_off[a]);
+        for (int c = 0; c * 32 < m; ++c) { pca_asm.push_back(a); pca_chunk.push_back(c); }
+    }
+    h->n_pca = (int)pca_asm.size();
+    CK(dalloc(&h->d_pca_asm, pca_asm.size())); CK(dalloc(&h->d_pca_chunk, pca_chunk.size()));
     CK(dalloc(&h->d_G_off, NA + 1)); CK(dalloc(&h->d_G_rank, NA));
     CK(dalloc(&h->d_perm, permoff[NA])); CK(dalloc(&h->d_perm_off, NA + 1));
     CK(dalloc(&h->d_corr, coff[NA])); CK(dalloc(&h->d_corr_off, NA + 1));
@@ -265,6 +290,8 @@ int build_links(am_handle* h, int P, const int* bp, const int* bq) {
     CK(h2d(h->d_G_off, goff.data(), NA + 1, s));
     CK(h2d(h->d_perm_off, permoff.data(), NA + 1, s));
     CK(h2d(h->d_corr_off, coff.data(), NA + 1, s));
+    CK(h2d(h->d_pca_asm, pca_asm.data(), pca_asm.size(), s));
+    CK(h2d(h->d_pca_chunk, pca_chunk.data(), pca_chunk.size(), s));
     CK(cudaStreamSynchronize(s));
     h->n = 3 * h->Nb + 6 * h->M + 3 * P;
     h->pc_valid = false;
@@ -355,6 +382,7 @@ extern "C" AM_API int am_create(const am_config* cfg, am_handle** out) {
     am_handle* h = new am_handle();
     h->cfg = c;
     h->restart = c.restart;
+    h->pc32 = (c.precision == AM_MIXED);
     h->prm = am::make_params(c.eta, c.blob_radius);
     if (c.cuda_stream) {
         h->stream = static_cast<cudaStream_t>(c.cuda_stream);
@@ -365,11 +393,13 @@ extern "C" AM_API int am_create(const am_config* cfg, am_handle** out) {
         }
         h->own_stream = true;
     }
-    bool ok = cudaMallocHost(reinterpret_cast<void**>(&h->h_scal), 16 * sizeof(double)) == cudaSuccess &&
+    bool ok = cudaMallocHost(reinterpret_cast<void**>(&h->h_scal), 32 * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(reinterpret_cast<void**>(&h->h_flags), sizeof(int)) == cudaSuccess &&
-              cudaMalloc(reinterpret_cast<void**>(&h->d_scal), 16 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&h->d_scal), 32 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(reinterpret_cast<void**>(&h->d_flags), sizeof(int)) == cudaSuccess &&
               cudaMalloc(reinterpret_cast<void**>(&h->d_red), 4 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&h->d_ctrl), sizeof(am::ArnoldiCtrl)) == cudaSuccess &&
+              cudaMallocHost(reinterpret_cast<void**>(&h->h_ctrl), sizeof(am::ArnoldiCtrl)) == cudaSuccess &&
               cudaMemset(h->d_flags, 0, sizeof(int)) == cudaSuccess;
     for (int k = 0; k < 8 && ok; ++k) ok = cudaEventCreate(&h->ev[k]) == cudaSuccess;
     if (!ok) {
@@ -395,6 +425,9 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
         if (c < 1) return set_err(h, AM_ERR_ARG, "am_set_bodies: body without blobs");
         maxb = std::max(maxb, c);
     }
+    if ((size_t)3 * maxb * (h->pc32 ? 4 : 8) > 200 * 1024)
+        return set_err(h, AM_ERR_ARG, "am_set_bodies: a body has more blobs than the preconditioner "
+                                      "build supports (8,533 in FP64, 17,066 in mixed precision)");
     const long long Nb = blob_offset[M];
     if (Nb > (1LL << 28)) return set_err(h, AM_ERR_ARG, "am_set_bodies: too many blobs");
     int NA = 0;
@@ -451,8 +484,18 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
     CK(dalloc(&h->d_asm_body_idx, M)); CK(dalloc(&h->d_body_local, M));
     CK(dalloc(&h->d_r4, Nb)); CK(dalloc(&h->d_d4, Nb)); CK(dalloc(&h->d_rhi, Nb));
     CK(dalloc(&h->d_rlo, Nb)); CK(dalloc(&h->d_r3, 3 * (size_t)Nb));
-    CK(dalloc(&h->d_minv, h->minv_total)); CK(dalloc(&h->d_pcwork, 2 * h->minv_total));
-    CK(dalloc(&h->d_Y, 18 * (size_t)Nb)); CK(dalloc(&h->d_Nt, 36 * (size_t)M));
+    const size_t esz = h->pc32 ? sizeof(float) : sizeof(double);
+    CK(balloc(&h->d_minv, h->minv_total * esz)); CK(balloc(&h->d_pcwork, 2 * h->minv_total * esz));
+    CK(balloc(&h->d_Y, 18 * (size_t)Nb * esz)); CK(dalloc(&h->d_Nt, 36 * (size_t)M));
+    std::vector<int> pcw_body, pcw_chunk, pcw_off(M + 1, 0);
+    for (int p = 0; p < M; ++p) {
+        const int m = 3 * (blob_offset[p + 1] - blob_offset[p]);
+        for (int c = 0; c * 32 < m; ++c) { pcw_body.push_back(p); pcw_chunk.push_back(c); }
+        pcw_off[p + 1] = (int)pcw_body.size();
+    }
+    h->n_pcw = (int)pcw_body.size();
+    CK(dalloc(&h->d_pcw_body, pcw_body.size())); CK(dalloc(&h->d_pcw_chunk, pcw_chunk.size()));
+    CK(dalloc(&h->d_pcw_off, M + 1)); CK(dalloc(&h->d_ytp, 6 * pcw_body.size()));
     CK(dalloc(&h->d_minv_off, M + 1)); CK(dalloc(&h->d_pc_w, 3 * (size_t)Nb));
     CK(dalloc(&h->d_pc_Uhat, 6 * (size_t)M));
     CK(dalloc(&h->d_mv, (size_t)h->split.splits * 3 * Nb));
@@ -471,6 +514,9 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
     CK(h2d(h->d_asm_body_idx, h->asm_body_idx.data(), M, s));
     CK(h2d(h->d_body_local, body_local.data(), M, s));
     CK(h2d(h->d_minv_off, moff.data(), M + 1, s));
+    CK(h2d(h->d_pcw_body, pcw_body.data(), pcw_body.size(), s));
+    CK(h2d(h->d_pcw_chunk, pcw_chunk.data(), pcw_chunk.size(), s));
+    CK(h2d(h->d_pcw_off, pcw_off.data(), M + 1, s));
     CK(cudaStreamSynchronize(s));
     rc = build_links(h, 0, nullptr, nullptr);
     if (rc) return rc;
@@ -734,7 +780,12 @@ extern "C" AM_API void am_destroy(am_handle* h) {
     free_links(h);
     free_bodies(h);
     free_solver(h);
-    dfree(&h->d_scal); dfree(&h->d_flags); dfree(&h->d_red);
+    dfree(&h->d_scal); dfree(&h->d_flags); dfree(&h->d_red); dfree(&h->d_ctrl);
+    if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+    for (int k = 0; k < 2; ++k) {
+        if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+        if (h->graph[k]) cudaGraphDestroy(h->graph[k]);
+    }
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->h_flags) cudaFreeHost(h->h_flags);
     if (h->h_iters) cudaFreeHost(h->h_iters);

@@ -2,129 +2,13 @@
 // apply, the block-diagonal preconditioner (build and apply), GMRES vector
 // kernels, and the Euler update with reconstruction and correction.
 #include "am_internal.cuh"
+#include "dev_util.cuh"
 #include "ops.cuh"
 #include "rpy_pair.cuh"
 
 #include <algorithm>
 
 namespace am {
-
-// ------------------------------------------------------------ helpers ---
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum over the block; every thread gets the result.  sh: >= 33 doubles.
-__device__ double block_sum(double v, double* sh) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        double r = (lane < (int)((blockDim.x + 31) >> 5)) ? sh[lane] : 0.0;
-        r = warp_sum(r);
-        if (lane == 0) sh[32] = r;
-    }
-    __syncthreads();
-    return sh[32];
-}
-
-__device__ __forceinline__ void cross3(const double* a, const double* b, double* o) {
-    o[0] = a[1] * b[2] - a[2] * b[1];
-    o[1] = a[2] * b[0] - a[0] * b[2];
-    o[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-// In-place lower Cholesky factor of the m x m matrix A (row-major, full
-// storage), cooperative over the block.  Returns false (to every thread) if
-// a pivot is not positive.
-__device__ bool block_cholesky(double* A, int m, double* sh) {
-    for (int k = 0; k < m; ++k) {
-        if (threadIdx.x == 0) {
-            double d = A[(size_t)k * m + k];
-            sh[0] = d;
-            if (d > 0.0) {
-                d = sqrt(d);
-                A[(size_t)k * m + k] = d;
-                sh[1] = 1.0 / d;
-            }
-        }
-        __syncthreads();
-        if (!(sh[0] > 0.0)) return false;
-        const double inv = sh[1];
-        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * m + k] *= inv;
-        __syncthreads();
-        const int len = m - k - 1;
-        for (int idx = threadIdx.x; idx < len * len; idx += blockDim.x) {
-            const int i = k + 1 + idx / len, j = k + 1 + idx % len;
-            if (j <= i) A[(size_t)i * m + j] -= A[(size_t)i * m + k] * A[(size_t)j * m + k];
-        }
-        __syncthreads();
-    }
-    return true;
-}
-
-// X = L^{-1} for the lower-triangular m x m L (both row-major), one column
-// per thread by forward substitution; X's upper triangle is left unset.
-__device__ void block_lower_inverse(const double* L, double* X, int m) {
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        X[(size_t)j * m + j] = 1.0 / L[(size_t)j * m + j];
-        for (int i = j + 1; i < m; ++i) {
-            double s = 0.0;
-            for (int k = j; k < i; ++k) s = fma(L[(size_t)i * m + k], X[(size_t)k * m + j], s);
-            X[(size_t)i * m + j] = -s / L[(size_t)i * m + i];
-        }
-    }
-    __syncthreads();
-}
-
-// O = X^T X restricted to the leading r x r block of the m x m lower X.
-__device__ void block_xtx(const double* X, int m, int r, double* O, int ldo) {
-    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
-        const int i = idx / r, j = idx % r;
-        const int k0 = i > j ? i : j;
-        double s = 0.0;
-        for (int k = k0; k < r; ++k) s = fma(X[(size_t)k * m + i], X[(size_t)k * m + j], s);
-        O[(size_t)i * ldo + j] = s;
-    }
-    __syncthreads();
-}
-
-// 6 x 6 symmetric positive definite inverse in one thread (Cholesky).
-__device__ bool spd6_inverse(const double* S, double* Out) {
-    double L[36];
-    for (int i = 0; i < 36; ++i) L[i] = 0.0;
-    for (int j = 0; j < 6; ++j) {
-        double d = 0.5 * (S[j * 6 + j] + S[j * 6 + j]);
-        for (int k = 0; k < j; ++k) d -= L[j * 6 + k] * L[j * 6 + k];
-        if (!(d > 0.0)) return false;
-        d = sqrt(d);
-        L[j * 6 + j] = d;
-        for (int i = j + 1; i < 6; ++i) {
-            double s = 0.5 * (S[i * 6 + j] + S[j * 6 + i]);
-            for (int k = 0; k < j; ++k) s -= L[i * 6 + k] * L[j * 6 + k];
-            L[i * 6 + j] = s / d;
-        }
-    }
-    // columns of the inverse: solve L L^T x = e_c
-    for (int c = 0; c < 6; ++c) {
-        double y[6];
-        for (int i = 0; i < 6; ++i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) s -= L[i * 6 + k] * y[k];
-            y[i] = s / L[i * 6 + i];
-        }
-        for (int i = 5; i >= 0; --i) {
-            double s = y[i];
-            for (int k = i + 1; k < 6; ++k) s -= L[k * 6 + i] * y[k];
-            y[i] = s / L[i * 6 + i];
-        }
-        for (int i = 0; i < 6; ++i) Out[i * 6 + c] = y[i];
-    }
-    return true;
-}
 
 // ------------------------------------------------------- pose, links ---
 // r_i = q_p + R(theta_p) rho_i  (Sec. 2.3)
@@ -268,393 +152,7 @@ __global__ void k_op_epilogue(int Nb, int M, int P, int nblob_blocks, int nbody_
     }
 }
 
-// ------------------------------------------------- preconditioner build ---
-// Per body p (one block): M_pp (same-body blobs only), its Cholesky factor,
-// the explicit inverse, Y_p = M_pp^-1 K_p, S_p = K_p^T Y_p and
-// N~_p = S_p^-1 (Sec. 3.1, the body mobility of the non-interacting body).
-__global__ void __launch_bounds__(256)
-k_pc_body_build(const int* __restrict__ blob_off, const double4_32a* __restrict__ r4,
-                const double4_32a* __restrict__ d4, const long long* __restrict__ moff,
-                double* __restrict__ minv, double* __restrict__ work, double* __restrict__ Y,
-                double* __restrict__ Nt, RpyParamsDev prm, int wall, int* flags) {
-    __shared__ double sh[64];
-    const int b = blockIdx.x;
-    const int i0 = blob_off[b];
-    const int nbl = blob_off[b + 1] - i0;
-    const int m = 3 * nbl;
-    double* A = minv + moff[b];
-    double* L = work + 2 * moff[b];
-    double* X = L + (size_t)m * m;
-    for (int idx = threadIdx.x; idx < nbl * nbl; idx += blockDim.x) {
-        const int ti = idx / nbl, sj = idx % nbl;
-        double T[9];
-        pair_tensor_f64(r4[i0 + ti], r4[i0 + sj], prm, wall, T);
-        for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 3; ++c) L[(size_t)(3 * ti + a) * m + 3 * sj + c] = T[3 * a + c];
-    }
-    __syncthreads();
-    if (!block_cholesky(L, m, sh)) {
-        if (threadIdx.x == 0) atomicOr(flags, kFlagSingular);
-        return;
-    }
-    block_lower_inverse(L, X, m);
-    block_xtx(X, m, m, A, m);
-    double* Yb = Y + 18 * (size_t)i0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        double y[6] = {0, 0, 0, 0, 0, 0};
-        for (int bb = 0; bb < nbl; ++bb) {
-            // row i of M^-1 = column i (symmetric)
-            const double v[3] = {A[(size_t)(3 * bb) * m + i], A[(size_t)(3 * bb + 1) * m + i],
-                                 A[(size_t)(3 * bb + 2) * m + i]};
-            const double4_32a dd = d4[i0 + bb];
-            const double d[3] = {dd.x, dd.y, dd.z};
-            double c[3];
-            cross3(d, v, c);
-            for (int a = 0; a < 3; ++a) { y[a] += v[a]; y[3 + a] += c[a]; }
-        }
-        for (int a = 0; a < 6; ++a) Yb[6 * (size_t)i + a] = y[a];
-    }
-    __syncthreads();
-    if (threadIdx.x < 36) {
-        const int c = threadIdx.x / 6, e = threadIdx.x % 6;
-        double s = 0.0;
-        for (int bb = 0; bb < nbl; ++bb) {
-            if (c < 3) {
-                s += Yb[6 * (size_t)(3 * bb + c) + e];
-            } else {
-                const double v[3] = {Yb[6 * (size_t)(3 * bb) + e], Yb[6 * (size_t)(3 * bb + 1) + e],
-                                     Yb[6 * (size_t)(3 * bb + 2) + e]};
-                const double4_32a dd = d4[i0 + bb];
-                const double d[3] = {dd.x, dd.y, dd.z};
-                double cr[3];
-                cross3(d, v, cr);
-                s += cr[c - 3];
-            }
-        }
-        sh[threadIdx.x] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double S[36];
-        for (int k = 0; k < 36; ++k) S[k] = sh[k];
-        if (!spd6_inverse(S, Nt + 36 * (size_t)b)) atomicOr(flags, kFlagSingular);
-    }
-}
-
-// 3x6 block of C for link n on one of its bodies: sigma [I, -l^x]
-// (sigma = +1, l = l_np on body p; sigma = -1, l = l_nq on body q), App. A.
-// W = E N~ (3x6).
-__device__ __forceinline__ void e_times_n(double sg, const double* l, const double* N, double* W) {
-    for (int c = 0; c < 6; ++c) {
-        // (l^x N[3:6, c]) = l x N[3:6, c]
-        const double v[3] = {N[3 * 6 + c], N[4 * 6 + c], N[5 * 6 + c]};
-        double cr[3];
-        cross3(l, v, cr);
-        for (int a = 0; a < 3; ++a) W[a * 6 + c] = sg * (N[a * 6 + c] - cr[a]);
-    }
-}
-
-// Per articulated body (one block): H_a = C_a N~_a C_a^T and the generalised
-// inverse G~_a (Eq. block_diag_const_res).  Symmetric pivoted Cholesky with
-// a relative threshold gives H(perm) ~ L L^T with L of rank r, and
-// G~ = perm [ (L11 L11^T)^-1 0 ; 0 0 ] perm^T, which solves H phi = c
-// exactly for every c in range(H) = range(C_a) (the pseudo-inverse of
-// Sec. 3.1 differs from it only in null(C_a^T), which C^T phi does not see).
-__global__ void __launch_bounds__(256)
-k_pc_asm_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
-               const int* __restrict__ bp, const int* __restrict__ bq,
-               const double* __restrict__ lp, const double* __restrict__ lq,
-               const double* __restrict__ Nt, const long long* __restrict__ goff,
-               double* __restrict__ G, double* __restrict__ gwork, int* __restrict__ perm_all,
-               const long long* __restrict__ poff, int* __restrict__ rank_out, double tol) {
-    __shared__ double shv[256];
-    __shared__ int shi[256];
-    __shared__ double sh[64];
-    __shared__ int s_rank;
-    const int a = blockIdx.x;
-    const int L0 = asm_link_off[a];
-    const int Pa = asm_link_off[a + 1] - L0;
-    const int m = 3 * Pa;
-    if (m == 0) return;
-    double* H = gwork + 2 * goff[a];
-    double* X = H + (size_t)m * m;
-    double* Ga = G + goff[a];
-    int* perm = perm_all + poff[a];
-    for (int idx = threadIdx.x; idx < Pa * Pa; idx += blockDim.x) {
-        const int r = idx / Pa, c = idx % Pa;
-        const int ln = asm_link_idx[L0 + r], lk = asm_link_idx[L0 + c];
-        double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int sn = 0; sn < 2; ++sn) {
-            const int bn = sn ? bq[ln] : bp[ln];
-            for (int sk = 0; sk < 2; ++sk) {
-                const int bk = sk ? bq[lk] : bp[lk];
-                if (bn != bk) continue;
-                double W[18];
-                e_times_n(sn ? -1.0 : 1.0, sn ? lq + 3 * ln : lp + 3 * ln, Nt + 36 * (size_t)bn, W);
-                const double* l = sk ? lq + 3 * lk : lp + 3 * lk;
-                const double sg = sk ? -1.0 : 1.0;
-                // (W E_k^T)[x][y] = sg (W[x][y] + sum_d W[x][3+d] (l^x)[d][y])
-                for (int x = 0; x < 3; ++x) {
-                    const double w3[3] = {W[x * 6 + 3], W[x * 6 + 4], W[x * 6 + 5]};
-                    // sum_d w3[d] (l^x)[d][y] = (w3^T l^x)_y = (l x w3)_y ... with sign:
-                    // (l^x)[d][y] = eps_{d k y} l_k, so sum_d w3_d eps_{dky} l_k = (w3 x l)_y
-                    double cr[3];
-                    cross3(w3, l, cr);
-                    for (int yy = 0; yy < 3; ++yy) blk[x * 3 + yy] += sg * (W[x * 6 + yy] + cr[yy]);
-                }
-            }
-        }
-        for (int x = 0; x < 3; ++x)
-            for (int yy = 0; yy < 3; ++yy) H[(size_t)(3 * r + x) * m + 3 * c + yy] = blk[x * 3 + yy];
-    }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
-    if (threadIdx.x == 0) s_rank = m;
-    __syncthreads();
-    double d0 = 0.0;
-    for (int k = 0; k < m; ++k) {
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
-            const double v = H[(size_t)i * m + i];
-            if (v > best) { best = v; bi = i; }
-        }
-        shv[threadIdx.x] = best;
-        shi[threadIdx.x] = bi;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                const double o = shv[threadIdx.x + s];
-                const int oi = shi[threadIdx.x + s];
-                if (o > shv[threadIdx.x] || (o == shv[threadIdx.x] && oi < shi[threadIdx.x])) {
-                    shv[threadIdx.x] = o;
-                    shi[threadIdx.x] = oi;
-                }
-            }
-            __syncthreads();
-        }
-        const double dmax = shv[0];
-        if (k == 0) d0 = dmax;
-        if (!(dmax > tol * d0) || !(dmax > 0.0)) {
-            if (threadIdx.x == 0) s_rank = k;
-            __syncthreads();
-            break;
-        }
-        const int j = shi[0];
-        __syncthreads();
-        if (j != k) {
-            for (int c = threadIdx.x; c < m; c += blockDim.x) {
-                const double t = H[(size_t)k * m + c];
-                H[(size_t)k * m + c] = H[(size_t)j * m + c];
-                H[(size_t)j * m + c] = t;
-            }
-            __syncthreads();
-            for (int r = threadIdx.x; r < m; r += blockDim.x) {
-                const double t = H[(size_t)r * m + k];
-                H[(size_t)r * m + k] = H[(size_t)r * m + j];
-                H[(size_t)r * m + j] = t;
-            }
-            if (threadIdx.x == 0) {
-                const int t = perm[k];
-                perm[k] = perm[j];
-                perm[j] = t;
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const double d = sqrt(H[(size_t)k * m + k]);
-            H[(size_t)k * m + k] = d;
-            sh[0] = 1.0 / d;
-        }
-        __syncthreads();
-        const double inv = sh[0];
-        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) H[(size_t)i * m + k] *= inv;
-        __syncthreads();
-        const int len = m - k - 1;
-        for (int idx = threadIdx.x; idx < len * len; idx += blockDim.x) {
-            const int i = k + 1 + idx / len, jj = k + 1 + idx % len;
-            H[(size_t)i * m + jj] -= H[(size_t)i * m + k] * H[(size_t)jj * m + k];
-        }
-        __syncthreads();
-    }
-    const int r = s_rank;
-    if (threadIdx.x == 0) rank_out[a] = r;
-    // X = L11^-1 (leading r x r of H, leading dimension m)
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-        X[(size_t)j * m + j] = 1.0 / H[(size_t)j * m + j];
-        for (int i = j + 1; i < r; ++i) {
-            double s = 0.0;
-            for (int k = j; k < i; ++k) s = fma(H[(size_t)i * m + k], X[(size_t)k * m + j], s);
-            X[(size_t)i * m + j] = -s / H[(size_t)i * m + i];
-        }
-    }
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Ga[idx] = 0.0;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
-        const int i = idx / r, j = idx % r;
-        const int k0 = i > j ? i : j;
-        double s = 0.0;
-        for (int k = k0; k < r; ++k) s = fma(X[(size_t)k * m + i], X[(size_t)k * m + j], s);
-        Ga[(size_t)perm[i] * m + perm[j]] = s;
-    }
-}
-
-// ------------------------------------------------- preconditioner apply ---
-// Solves the block-diagonal problem of Eq. precond for r = (r1, r2, r3):
-//   w = M~^-1 r1;  U^ = N~ (-r2 - K^T w)  (K^T w = Y^T r1)      [apply1]
-//   phi = G~ (r3 - C U^)                                       [apply2]
-//   U = U^ + N~ C^T phi;  lambda = w + Y U  (= M~^-1 (r1 + K U)) [apply3]
-__global__ void __launch_bounds__(128)
-k_pc_apply1(int Nb, const int* __restrict__ blob_off, const double* __restrict__ minv,
-            const long long* __restrict__ moff, const double* __restrict__ Y,
-            const double* __restrict__ Nt, const double* __restrict__ r,
-            double* __restrict__ w, double* __restrict__ Uhat) {
-    __shared__ double sh[64];
-    const int b = blockIdx.x;
-    const int i0 = blob_off[b];
-    const int m = 3 * (blob_off[b + 1] - i0);
-    const double* A = minv + moff[b];
-    const double* r1 = r + 3 * (size_t)i0;
-    const double* Yb = Y + 18 * (size_t)i0;
-    double yt[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < m; ++k) s = fma(A[(size_t)k * m + i], r1[k], s);
-        w[3 * (size_t)i0 + i] = s;
-        const double ri = r1[i];
-        for (int c = 0; c < 6; ++c) yt[c] = fma(Yb[6 * (size_t)i + c], ri, yt[c]);
-    }
-    double tot[6];
-    for (int c = 0; c < 6; ++c) tot[c] = block_sum(yt[c], sh);
-    if (threadIdx.x == 0) {
-        const double* r2 = r + 3 * (size_t)Nb + 6 * (size_t)b;
-        const double* N = Nt + 36 * (size_t)b;
-        double v[6];
-        for (int c = 0; c < 6; ++c) v[c] = -r2[c] - tot[c];
-        for (int a = 0; a < 6; ++a) {
-            double s = 0.0;
-            for (int c = 0; c < 6; ++c) s += N[a * 6 + c] * v[c];
-            Uhat[6 * (size_t)b + a] = s;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(128)
-k_pc_apply2(int Nb, int M, const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
-            const int* __restrict__ bp, const int* __restrict__ bq, const double* __restrict__ lp,
-            const double* __restrict__ lq, const double* __restrict__ Uhat,
-            const double* __restrict__ G, const long long* __restrict__ goff,
-            const double* __restrict__ r, double* __restrict__ z, double* __restrict__ cbuf) {
-    const int a = blockIdx.x;
-    const int L0 = asm_link_off[a];
-    const int Pa = asm_link_off[a + 1] - L0;
-    const int m = 3 * Pa;
-    if (m == 0) return;
-    const double* r3 = r + 3 * (size_t)Nb + 6 * (size_t)M;
-    double* c = cbuf + 3 * (size_t)L0;
-    for (int k = threadIdx.x; k < Pa; k += blockDim.x) {
-        const int n = asm_link_idx[L0 + k];
-        const double* up = Uhat + 6 * bp[n];
-        const double* uq = Uhat + 6 * bq[n];
-        double wp[3], wq[3];
-        cross3(up + 3, lp + 3 * n, wp);
-        cross3(uq + 3, lq + 3 * n, wq);
-        for (int x = 0; x < 3; ++x) c[3 * k + x] = r3[3 * n + x] - (up[x] + wp[x] - uq[x] - wq[x]);
-    }
-    __syncthreads();
-    const double* Ga = G + goff[a];
-    double* zf = z + 3 * (size_t)Nb + 6 * (size_t)M;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < m; ++k) s = fma(Ga[(size_t)k * m + i], c[k], s);
-        const int n = asm_link_idx[L0 + i / 3];
-        zf[3 * n + i % 3] = s;
-    }
-}
-
-__global__ void __launch_bounds__(128)
-k_pc_apply3(int Nb, int M, const int* __restrict__ blob_off, const double* __restrict__ Y,
-            const double* __restrict__ Nt, const double* __restrict__ w,
-            const double* __restrict__ Uhat, const int* __restrict__ bl_off,
-            const int* __restrict__ bl_idx, const double* __restrict__ lp,
-            const double* __restrict__ lq, double* __restrict__ z) {
-    __shared__ double sU[6];
-    const int b = blockIdx.x;
-    const double* phi = z + 3 * (size_t)Nb + 6 * (size_t)M;
-    if (threadIdx.x == 0) {
-        double f[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = bl_off[b]; k < bl_off[b + 1]; ++k) {
-            const int e = bl_idx[k];
-            const int n = e >> 1;
-            const double sg = (e & 1) ? -1.0 : 1.0;
-            const double* l = (e & 1) ? lq + 3 * n : lp + 3 * n;
-            const double* ph = phi + 3 * n;
-            double t[3];
-            cross3(l, ph, t);
-            for (int x = 0; x < 3; ++x) { f[x] += sg * ph[x]; f[3 + x] += sg * t[x]; }
-        }
-        const double* N = Nt + 36 * (size_t)b;
-        double* zU = z + 3 * (size_t)Nb + 6 * (size_t)b;
-        for (int x = 0; x < 6; ++x) {
-            double s = Uhat[6 * (size_t)b + x];
-            for (int c = 0; c < 6; ++c) s += N[x * 6 + c] * f[c];
-            sU[x] = s;
-            zU[x] = s;
-        }
-    }
-    __syncthreads();
-    const int i0 = blob_off[b];
-    const int m = 3 * (blob_off[b + 1] - i0);
-    const double* Yb = Y + 18 * (size_t)i0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        double s = w[3 * (size_t)i0 + i];
-        for (int c = 0; c < 6; ++c) s = fma(Yb[6 * (size_t)i + c], sU[c], s);
-        z[3 * (size_t)i0 + i] = s;
-    }
-}
-
 // --------------------------------------------------------- GMRES kernels ---
-// part[k * nch + c] = <V_k, w> over chunk c (k < jp1)
-__global__ void __launch_bounds__(256)
-k_dots(const double* __restrict__ V, size_t ldv, const double* __restrict__ w, int n,
-       int chunk, double* __restrict__ part, int nch) {
-    __shared__ double sh[64];
-    const int c = blockIdx.x, k = blockIdx.y;
-    const int i0 = c * chunk, i1 = min(n, i0 + chunk);
-    const double* v = V + (size_t)k * ldv;
-    double s = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(v[i], w[i], s);
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[(size_t)k * nch + c] = s;
-}
-
-// w -= sum_k h_k V_k with h_k = sum_c part[k][c]; hcol = h (or += h);
-// optional per-block partial sums of |w|^2 after the update.
-__global__ void __launch_bounds__(256)
-k_orth(const double* __restrict__ V, size_t ldv, double* __restrict__ w, int n,
-       const double* __restrict__ part, int nch, int jp1, double* __restrict__ hcol,
-       int accumulate, double* __restrict__ npart) {
-    extern __shared__ double coef[];
-    __shared__ double sh[64];
-    for (int k = threadIdx.x; k < jp1; k += blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < nch; ++c) s += part[(size_t)k * nch + c];
-        coef[k] = s;
-        if (blockIdx.x == 0) hcol[k] = accumulate ? hcol[k] + s : s;
-    }
-    __syncthreads();
-    double nn = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double v = w[i];
-        for (int k = 0; k < jp1; ++k) v = fma(-coef[k], V[(size_t)k * ldv + i], v);
-        w[i] = v;
-        nn = fma(v, v, nn);
-    }
-    if (npart) {
-        nn = block_sum(nn, sh);
-        if (threadIdx.x == 0) npart[blockIdx.x] = nn;
-    }
-}
-
 // |w|^2 partial sums (no orthogonalisation)
 __global__ void __launch_bounds__(256)
 k_norm_part(const double* __restrict__ w, int n, double* __restrict__ npart) {
@@ -693,40 +191,6 @@ __global__ void k_norm_finish(const double* __restrict__ npart, int nb, double* 
         scal[slot] = nrm;
         scal[slot + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
     }
-}
-
-// Arnoldi column j: H[0..j][j] = hcol, H[j+1][j] = |w|; apply the previous
-// Givens rotations, form the new one and update g.  scal[0] = |g[j+1]|
-// (residual estimate), scal[1] = |w|, scal[2] = 1/|w|.
-__global__ void k_arnoldi_finish(int j, const double* __restrict__ hcol,
-                                 const double* __restrict__ npart, int nb, double* __restrict__ H,
-                                 int ldh, double* __restrict__ cs, double* __restrict__ sn,
-                                 double* __restrict__ g, double* __restrict__ scal) {
-    __shared__ double sh[64];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += npart[i];
-    s = block_sum(s, sh);
-    if (threadIdx.x != 0) return;
-    const double nrm = sqrt(s);
-    double* h = H + (size_t)j * ldh;
-    for (int i = 0; i <= j; ++i) h[i] = hcol[i];
-    h[j + 1] = nrm;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-        h[i] = t;
-    }
-    const double d = hypot(h[j], h[j + 1]);
-    double c = 1.0, sg = 0.0;
-    if (d > 0.0) { c = h[j] / d; sg = h[j + 1] / d; }
-    cs[j] = c; sn[j] = sg;
-    h[j] = d;
-    h[j + 1] = 0.0;
-    g[j + 1] = -sg * g[j];
-    g[j] = c * g[j];
-    scal[0] = fabs(g[j + 1]);
-    scal[1] = nrm;
-    scal[2] = nrm > 0.0 ? 1.0 / nrm : 0.0;
 }
 
 // xi = H(0:k,0:k)^-1 g(0:k)  (upper triangular back substitution)
@@ -1104,6 +568,131 @@ __global__ void k_g2(int P, const int* __restrict__ bp, const int* __restrict__ 
 
 }  // namespace am
 
+namespace am {
+
+// ------------------------------------------- device-controlled Arnoldi ---
+// One Arnoldi step whose index j lives in device memory (ArnoldiCtrl), so the
+// same kernels can run inside a CUDA-graph WHILE node without the host.
+
+__global__ void k_ctrl_init(ArnoldiCtrl* c, int budget, int m, double tol_abs) {
+    c->j = 0; c->it = 0; c->budget = budget; c->m = m; c->stop = 0; c->tol_abs = tol_abs;
+}
+
+// out = V[j] (the vector to precondition)
+__global__ void k_copy_col(const double* __restrict__ V, size_t ldv, double* __restrict__ out, int n,
+                           const ArnoldiCtrl* __restrict__ c) {
+    const double* v = V + (size_t)c->j * ldv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = v[i];
+}
+
+// Z[j] = in (flexible GMRES keeps the preconditioned vectors)
+__global__ void k_store_col(const double* __restrict__ in, double* __restrict__ Z, size_t ldv, int n,
+                            const ArnoldiCtrl* __restrict__ c) {
+    double* z = Z + (size_t)c->j * ldv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) z[i] = in[i];
+}
+
+// part[k * nch + chunk] = <V_k, w> over chunk blockIdx.x, for the 8 basis
+// vectors k = 8 blockIdx.y + warp with k <= j (one warp per k)
+__global__ void __launch_bounds__(256)
+k_dots_dev(const double* __restrict__ V, size_t ldv, const double* __restrict__ w, int n, int chunk,
+           double* __restrict__ part, int nch, const ArnoldiCtrl* __restrict__ c) {
+    const int j = c->j;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k = blockIdx.y * 8 + wid;
+    if (k > j) return;
+    const int cb = blockIdx.x;
+    const int i0 = cb * chunk, i1 = min(n, i0 + chunk);
+    const double* v = V + (size_t)k * ldv;
+    double s = 0.0;
+    for (int i = i0 + lane; i < i1; i += 32) s = fma(v[i], w[i], s);
+    s = warp_sum(s);
+    if (lane == 0) part[(size_t)k * nch + cb] = s;
+}
+
+__global__ void __launch_bounds__(256)
+k_orth_dev(const double* __restrict__ V, size_t ldv, double* __restrict__ w, int n,
+           const double* __restrict__ part, int nch, double* __restrict__ hcol, int accumulate,
+           double* __restrict__ npart, const ArnoldiCtrl* __restrict__ c) {
+    extern __shared__ double coef[];
+    __shared__ double sh[64];
+    const int jp1 = c->j + 1;
+    for (int k = threadIdx.x; k < jp1; k += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < nch; ++q) s += part[(size_t)k * nch + q];
+        coef[k] = s;
+        if (blockIdx.x == 0) hcol[k] = accumulate ? hcol[k] + s : s;
+    }
+    __syncthreads();
+    double nn = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v = w[i];
+        for (int k = 0; k < jp1; ++k) v = fma(-coef[k], V[(size_t)k * ldv + i], v);
+        w[i] = v;
+        nn = fma(v, v, nn);
+    }
+    if (npart) {
+        nn = block_sum(nn, sh);
+        if (threadIdx.x == 0) npart[blockIdx.x] = nn;
+    }
+}
+
+__global__ void k_arnoldi_finish_dev(const ArnoldiCtrl* __restrict__ c, const double* __restrict__ hcol,
+                                     const double* __restrict__ npart, int nb, double* __restrict__ H,
+                                     int ldh, double* __restrict__ cs, double* __restrict__ sn,
+                                     double* __restrict__ g, double* __restrict__ scal) {
+    __shared__ double sh[64];
+    const int j = c->j;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += npart[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x != 0) return;
+    const double nrm = sqrt(s);
+    double* h = H + (size_t)j * ldh;
+    for (int i = 0; i <= j; ++i) h[i] = hcol[i];
+    h[j + 1] = nrm;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    const double d = hypot(h[j], h[j + 1]);
+    double cc = 1.0, sg = 0.0;
+    if (d > 0.0) { cc = h[j] / d; sg = h[j + 1] / d; }
+    cs[j] = cc; sn[j] = sg;
+    h[j] = d;
+    h[j + 1] = 0.0;
+    g[j + 1] = -sg * g[j];
+    g[j] = cc * g[j];
+    scal[0] = fabs(g[j + 1]);
+    scal[1] = nrm;
+    scal[2] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+}
+
+// V[j+1] = w / |w|
+__global__ void k_scale_dev(const double* __restrict__ w, double* __restrict__ V, size_t ldv, int n,
+                            const double* __restrict__ scal, const ArnoldiCtrl* __restrict__ c) {
+    const double a = scal[2];
+    double* v = V + (size_t)(c->j + 1) * ldv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = a * w[i];
+}
+
+// Advance j; stop on convergence of the residual estimate, breakdown, the
+// end of the cycle or the iteration budget.  Inside a graph WHILE node the
+// decision is the node's condition.
+__global__ void k_loop_ctrl(ArnoldiCtrl* c, const double* __restrict__ scal,
+                            cudaGraphConditionalHandle hc, int in_graph) {
+    const int j = c->j;
+    c->it += 1;
+    const double est = scal[0];
+    const bool stop = !(est > c->tol_abs) || scal[1] == 0.0 || j + 1 >= c->m || c->it >= c->budget;
+    c->j = j + 1;
+    c->stop = stop ? 1 : 0;
+    if (in_graph) cudaGraphSetConditional(hc, stop ? 0u : 1u);
+}
+
+}  // namespace am
+
 // =============================================================== host ===
 namespace am {
 
@@ -1173,39 +762,6 @@ void op_apply(am_handle* h, const double* y, double* out, bool fp64) {
     count_launch();
 }
 
-void pc_build(am_handle* h) {
-    cudaStream_t s = h->stream;
-    k_pc_body_build<<<h->M, 256, 0, s>>>(h->d_blob_off, h->d_r4, h->d_d4, h->d_minv_off, h->d_minv,
-                                          h->d_pcwork, h->d_Y, h->d_Nt, dev_params(h->prm),
-                                          h->cfg.wall, h->d_flags);
-    count_launch();
-    if (h->P) {
-        k_pc_asm_build<<<h->NA, 256, 0, s>>>(h->d_asm_link_off, h->d_asm_link_idx, h->d_bp, h->d_bq,
-                                              h->d_lp, h->d_lq, h->d_Nt, h->d_G_off, h->d_G,
-                                              h->d_Gwork, h->d_perm, h->d_perm_off, h->d_G_rank,
-                                              1e-11);
-        count_launch();
-    }
-    h->pc_valid = true;
-}
-
-void pc_apply(am_handle* h, const double* r, double* z) {
-    cudaStream_t s = h->stream;
-    k_pc_apply1<<<h->M, 128, 0, s>>>(h->Nb, h->d_blob_off, h->d_minv, h->d_minv_off, h->d_Y, h->d_Nt,
-                                      r, h->d_pc_w, h->d_pc_Uhat);
-    count_launch();
-    if (h->P) {
-        k_pc_apply2<<<h->NA, 128, 0, s>>>(h->Nb, h->M, h->d_asm_link_off, h->d_asm_link_idx, h->d_bp,
-                                           h->d_bq, h->d_lp, h->d_lq, h->d_pc_Uhat, h->d_G, h->d_G_off,
-                                           r, z, h->d_cbuf);
-        count_launch();
-    }
-    k_pc_apply3<<<h->M, 128, 0, s>>>(h->Nb, h->M, h->d_blob_off, h->d_Y, h->d_Nt, h->d_pc_w,
-                                      h->d_pc_Uhat, h->d_body_link_off, h->d_body_link_idx, h->d_lp,
-                                      h->d_lq, z);
-    count_launch();
-}
-
 void project_constraints(am_handle* h, double* x) {
     if (!h->P) return;
     cudaStream_t s = h->stream;
@@ -1234,10 +790,98 @@ static double norm2(am_handle* h, const double* v) {
     return read_scal(h, 2);
 }
 
-// GMRES(m), right preconditioned, CGS2, on A x = rhs with the operator in
-// FP64 (fp64) or in the handle's precision.  Stops when the true relative
-// residual (same operator) is <= tol or after `budget` iterations.
-// Returns the number of iterations; *rel = final true relative residual.
+// One Arnoldi step of flexible GMRES with the step index in device memory:
+// z = P^-1 V[j] (stored in Z[j]), w = A z, CGS2 against V[0..j], Givens
+// update, V[j+1] = w / |w|, then the loop control.
+static void issue_arnoldi_step(am_handle* h, bool fp64, cudaGraphConditionalHandle hc, bool in_graph) {
+    cudaStream_t s = h->stream;
+    const int n = h->n, m = h->restart;
+    const size_t ldv = (size_t)h->ldv;
+    const int nb = red_blocks(n);
+    const int nch = std::max(1, std::min(64, nblk(n, 1024)));
+    const int chunk = nblk(n, nch);
+    const dim3 dgrid(nch, (m + 1 + 7) / 8);
+    k_copy_col<<<nb, 256, 0, s>>>(h->d_V, ldv, h->d_vj, n, h->d_ctrl);
+    count_launch();
+    pc_apply(h, h->d_vj, h->d_zj);
+    k_store_col<<<nb, 256, 0, s>>>(h->d_zj, h->d_Z, ldv, n, h->d_ctrl);
+    count_launch();
+    op_apply(h, h->d_zj, h->d_w, fp64);
+    for (int pass = 0; pass < 2; ++pass) {
+        k_dots_dev<<<dgrid, 256, 0, s>>>(h->d_V, ldv, h->d_w, n, chunk, h->d_part, nch, h->d_ctrl);
+        k_orth_dev<<<nb, 256, (m + 1) * sizeof(double), s>>>(h->d_V, ldv, h->d_w, n, h->d_part, nch,
+                                                             h->d_coef, pass, pass ? h->d_npart : nullptr,
+                                                             h->d_ctrl);
+        count_launch(2);
+    }
+    k_arnoldi_finish_dev<<<1, 256, 0, s>>>(h->d_ctrl, h->d_coef, h->d_npart, nb, h->d_Hm, m + 1, h->d_cs,
+                                           h->d_sn, h->d_g, h->d_scal);
+    k_scale_dev<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_scal, h->d_ctrl);
+    k_loop_ctrl<<<1, 1, 0, s>>>(h->d_ctrl, h->d_scal, hc, in_graph ? 1 : 0);
+    count_launch(3);
+}
+
+// The graph of one Arnoldi cycle: a WHILE node whose body is one step,
+// captured once per handle layout and operator precision.
+static bool ensure_graph(am_handle* h, bool fp64) {
+    const int gi = fp64 ? 1 : 0;
+    if (h->gexec[gi] && h->graph_gen[gi] == h->layout_gen) return true;
+    if (h->gexec[gi]) { cudaGraphExecDestroy(h->gexec[gi]); h->gexec[gi] = nullptr; }
+    if (h->graph[gi]) { cudaGraphDestroy(h->graph[gi]); h->graph[gi] = nullptr; }
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    cudaGraphConditionalHandle hc;
+    if (cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    const long long l0 = g_launches.load();
+    const long long p0 = h->pairs;
+    const bool timing = h->timing;
+    h->timing = false;
+    bool ok = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        issue_arnoldi_step(h, fp64, hc, true);
+        cudaGraph_t out = nullptr;
+        ok = cudaStreamEndCapture(h->stream, &out) == cudaSuccess;
+    }
+    h->timing = timing;
+    h->body_launches[gi] = g_launches.load() - l0;
+    h->body_pairs[gi] = h->pairs - p0;
+    g_launches.store(l0);
+    h->pairs = p0;
+    cudaGetLastError();
+    if (!ok || cudaGraphInstantiate(&h->gexec[gi], g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        h->gexec[gi] = nullptr;
+        return false;
+    }
+    h->graph[gi] = g;
+    h->graph_gen[gi] = h->layout_gen;
+    return true;
+}
+
+// Flexible GMRES(m) (right preconditioning, x = x0 + Z xi with the stored
+// z_j = P^-1 v_j, so a preconditioner applied in FP32 is allowed), CGS2, on
+// A x = rhs with the operator in FP64 (fp64) or in the handle's precision.
+// Each restart cycle runs on the device as one graph launch (WHILE node over
+// Arnoldi steps); with per-kernel timing on, the same steps are launched
+// from the host instead (event records cannot live in a graph loop).
+// Stops when the true relative residual (same operator) is <= tol or after
+// `budget` steps.  Returns the number of steps; *rel = final true residual.
 static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp64, int budget,
                  double* rel, int* cycles) {
     cudaStream_t s = h->stream;
@@ -1245,14 +889,14 @@ static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp
     const int m = h->restart;
     const size_t ldv = (size_t)h->ldv;
     const int nb = red_blocks(n);
-    const int nch = std::max(1, std::min(64, nblk(n, 4096)));
-    const int chunk = nblk(n, nch);
     const double bnorm = norm2(h, rhs);
     *rel = 0.0;
     if (bnorm == 0.0) {
         cudaMemsetAsync(x, 0, n * sizeof(double), s);
         return 0;
     }
+    const bool use_graph = !h->timing && h->graphs_ok && ensure_graph(h, fp64);
+    const int gi = fp64 ? 1 : 0;
     int it = 0;
     while (true) {
         double* V0 = h->d_V;
@@ -1267,35 +911,27 @@ static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp
         ++*cycles;
         k_scale<<<nb, 256, 0, s>>>(V0, V0, n, h->d_scal + 5);
         k_init_g<<<1, 64, 0, s>>>(h->d_g, m + 1, h->d_scal, 4);
-        count_launch(2);
-        int kdone = 0;
-        for (int j = 0; j < m; ++j) {
-            const double* vj = h->d_V + j * ldv;
-            pc_apply(h, vj, h->d_z);
-            op_apply(h, h->d_z, h->d_w, fp64);
-            const int jp1 = j + 1;
-            for (int pass = 0; pass < 2; ++pass) {
-                k_dots<<<dim3(nch, jp1), 256, 0, s>>>(h->d_V, ldv, h->d_w, n, chunk, h->d_part, nch);
-                k_orth<<<nb, 256, jp1 * sizeof(double), s>>>(h->d_V, ldv, h->d_w, n, h->d_part, nch, jp1,
-                                                            h->d_coef, pass, pass ? h->d_npart : nullptr);
-                count_launch(2);
-            }
-            k_arnoldi_finish<<<1, 256, 0, s>>>(j, h->d_coef, h->d_npart, nb, h->d_Hm, m + 1, h->d_cs,
-                                                h->d_sn, h->d_g, h->d_scal);
-            k_scale<<<nb, 256, 0, s>>>(h->d_w, h->d_V + (j + 1) * ldv, n, h->d_scal + 2);
-            count_launch(2);
-            read_scal(h, 3);
-            ++it;
-            kdone = j + 1;
-            const double est = h->h_scal[0] / bnorm;
-            if (est <= tol || it >= budget || h->h_scal[1] == 0.0 || !(est == est)) break;
+        k_ctrl_init<<<1, 1, 0, s>>>(h->d_ctrl, budget - it, m, tol * bnorm);
+        count_launch(3);
+        if (use_graph) {
+            cudaGraphLaunch(h->gexec[gi], s);
+            cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(ArnoldiCtrl), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            g_launches.fetch_add(h->body_launches[gi] * h->h_ctrl->it);
+            h->pairs += h->body_pairs[gi] * h->h_ctrl->it;
+        } else {
+            do {
+                issue_arnoldi_step(h, fp64, 0, false);
+                cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(ArnoldiCtrl), cudaMemcpyDeviceToHost, s);
+                cudaStreamSynchronize(s);
+            } while (!h->h_ctrl->stop);
         }
+        const int kdone = h->h_ctrl->j;
+        it += h->h_ctrl->it;
         k_hessenberg_solve<<<1, 32, 0, s>>>(kdone, h->d_Hm, m + 1, h->d_g, h->d_xi);
-        k_combine<<<nb, 256, 0, s>>>(h->d_V, ldv, h->d_xi, kdone, n, h->d_t);
-        count_launch(2);
-        pc_apply(h, h->d_t, h->d_z);
-        k_axpy<<<nb, 256, 0, s>>>(x, h->d_z, n, 1.0);
-        count_launch();
+        k_combine<<<nb, 256, 0, s>>>(h->d_Z, ldv, h->d_xi, kdone, n, h->d_t);
+        k_axpy<<<nb, 256, 0, s>>>(x, h->d_t, n, 1.0);
+        count_launch(3);
     }
     return it;
 }

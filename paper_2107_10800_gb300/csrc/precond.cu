@@ -1,0 +1,479 @@
+// Block-diagonal preconditioner (Sec. 3.1): the exact solution of the
+// approximate problem Eq. precond, where M keeps only same-body blocks M^(pp).
+//
+// Build, per body p (one block): M^(pp) from the pair tensors, its Cholesky
+// factor, the explicit inverse, Y_p = (M^(pp))^-1 K_p, S_p = K_p^T Y_p and
+// N~_p = S_p^-1.  Per articulated body a (one block): H_a = C_a N~_a C_a^T and
+// its generalised inverse G~_a (Eq. block_diag_const_res) by symmetric pivoted
+// Cholesky: H(perm) = L L^T with L of rank r gives
+// G~ = perm [(L11 L11^T)^-1 0; 0 0] perm^T, which solves H phi = c exactly for
+// every c in range(H) = range(C_a).
+//
+// Apply, for r = (r1, r2, r3):
+//   w = M~^-1 r1;  U^ = N~ (-r2 - K^T w), with K^T w = Y^T r1
+//   phi = G~ (r3 - C U^)
+//   U = U^ + N~ C^T phi;  lambda = w + Y U  (= M~^-1 (r1 + K U)).
+// The dense products run over flattened (body, 32-row chunk) and
+// (articulated body, 32-row chunk) work items so that every SM gets work.
+//
+// Matrices are stored in T = double (FP64 path) or float (mixed path, where
+// the preconditioner only steers the inner iterations); vectors are FP64.
+#include "am_internal.cuh"
+#include "dev_util.cuh"
+#include "ops.cuh"
+#include "rpy_pair.cuh"
+
+#include <algorithm>
+
+namespace am {
+
+constexpr int kRows = 32;  // rows per apply work item
+
+template <class T>
+__global__ void __launch_bounds__(512)
+k_pcb_build(const int* __restrict__ blob_off, const double4_32a* __restrict__ r4,
+            const double4_32a* __restrict__ d4, const long long* __restrict__ moff,
+            T* __restrict__ minv, T* __restrict__ work, T* __restrict__ Y, double* __restrict__ Nt,
+            RpyK<double> prm, int wall, int* flags) {
+    __shared__ double sh[64];
+    const int b = blockIdx.x;
+    const int i0 = blob_off[b];
+    const int nbl = blob_off[b + 1] - i0;
+    const int m = 3 * nbl;
+    extern __shared__ unsigned char dyn_smem[];
+    T* colbuf = reinterpret_cast<T*>(dyn_smem);
+    T* A = minv + moff[b];
+    T* L = work + 2 * moff[b];
+    T* X = L + (size_t)m * m;
+    for (int idx = threadIdx.x; idx < nbl * nbl; idx += blockDim.x) {
+        const int ti = idx / nbl, sj = idx % nbl;
+        double Tt[9];
+        pair_tensor_f64(r4[i0 + ti], r4[i0 + sj], prm, wall, Tt);
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) L[(size_t)(3 * ti + a) * m + 3 * sj + c] = (T)Tt[3 * a + c];
+    }
+    __syncthreads();
+    if (!block_cholesky(L, m, sh)) {
+        if (threadIdx.x == 0) atomicOr(flags, kFlagSingular);
+        return;
+    }
+    block_lower_inverse(L, X, m, m, colbuf);
+    // A = X^T X: lower triangle computed, mirrored to the upper one
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        const int i = idx / m, j = idx % m;
+        if (j > i) continue;
+        T s = 0;
+        for (int k = i; k < m; ++k) s = fma(X[(size_t)k * m + i], X[(size_t)k * m + j], s);
+        A[idx] = s;
+        A[(size_t)j * m + i] = s;
+    }
+    __syncthreads();
+    T* Yb = Y + 18 * (size_t)i0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double y[6] = {0, 0, 0, 0, 0, 0};
+        for (int bb = 0; bb < nbl; ++bb) {
+            const double v[3] = {(double)A[(size_t)(3 * bb) * m + i], (double)A[(size_t)(3 * bb + 1) * m + i],
+                                 (double)A[(size_t)(3 * bb + 2) * m + i]};
+            const double4_32a dd = d4[i0 + bb];
+            const double d[3] = {dd.x, dd.y, dd.z};
+            double c[3];
+            cross3(d, v, c);
+            for (int a = 0; a < 3; ++a) { y[a] += v[a]; y[3 + a] += c[a]; }
+        }
+        for (int a = 0; a < 6; ++a) Yb[6 * (size_t)i + a] = (T)y[a];
+    }
+    __syncthreads();
+    if (threadIdx.x < 36) {
+        const int c = threadIdx.x / 6, e = threadIdx.x % 6;
+        double s = 0.0;
+        for (int bb = 0; bb < nbl; ++bb) {
+            if (c < 3) {
+                s += (double)Yb[6 * (size_t)(3 * bb + c) + e];
+            } else {
+                const double v[3] = {(double)Yb[6 * (size_t)(3 * bb) + e], (double)Yb[6 * (size_t)(3 * bb + 1) + e],
+                                     (double)Yb[6 * (size_t)(3 * bb + 2) + e]};
+                const double4_32a dd = d4[i0 + bb];
+                const double d[3] = {dd.x, dd.y, dd.z};
+                double cr[3];
+                cross3(d, v, cr);
+                s += cr[c - 3];
+            }
+        }
+        sh[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S[36];
+        for (int k = 0; k < 36; ++k) S[k] = sh[k];
+        if (!spd6_inverse(S, Nt + 36 * (size_t)b)) atomicOr(flags, kFlagSingular);
+    }
+}
+
+// W = E N~ for E = sigma [I, -l^x] (3 x 6 block of C on one body, App. A)
+__device__ __forceinline__ void e_times_n(double sg, const double* l, const double* N, double* W) {
+    for (int c = 0; c < 6; ++c) {
+        const double v[3] = {N[3 * 6 + c], N[4 * 6 + c], N[5 * 6 + c]};
+        double cr[3];
+        cross3(l, v, cr);
+        for (int a = 0; a < 3; ++a) W[a * 6 + c] = sg * (N[a * 6 + c] - cr[a]);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(512)
+k_pca_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
+            const int* __restrict__ bp, const int* __restrict__ bq, const double* __restrict__ lp,
+            const double* __restrict__ lq, const double* __restrict__ Nt,
+            const long long* __restrict__ goff, T* __restrict__ G, T* __restrict__ gwork,
+            int* __restrict__ perm_all, const long long* __restrict__ poff, int* __restrict__ rank_out,
+            double tol) {
+    __shared__ double shv[512];
+    __shared__ int shi[512];
+    extern __shared__ unsigned char dyn_smem[];
+    T* colbuf = reinterpret_cast<T*>(dyn_smem);
+    __shared__ double sh[64];
+    __shared__ int s_rank;
+    const int a = blockIdx.x;
+    const int L0 = asm_link_off[a];
+    const int Pa = asm_link_off[a + 1] - L0;
+    const int m = 3 * Pa;
+    if (m == 0) return;
+    T* H = gwork + 2 * goff[a];
+    T* X = H + (size_t)m * m;
+    T* Ga = G + goff[a];
+    int* perm = perm_all + poff[a];
+    for (int idx = threadIdx.x; idx < Pa * Pa; idx += blockDim.x) {
+        const int r = idx / Pa, c = idx % Pa;
+        const int ln = asm_link_idx[L0 + r], lk = asm_link_idx[L0 + c];
+        double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int sn = 0; sn < 2; ++sn) {
+            const int bn = sn ? bq[ln] : bp[ln];
+            for (int sk = 0; sk < 2; ++sk) {
+                const int bk = sk ? bq[lk] : bp[lk];
+                if (bn != bk) continue;
+                double W[18];
+                e_times_n(sn ? -1.0 : 1.0, sn ? lq + 3 * ln : lp + 3 * ln, Nt + 36 * (size_t)bn, W);
+                const double* l = sk ? lq + 3 * lk : lp + 3 * lk;
+                const double sg = sk ? -1.0 : 1.0;
+                // (W E_k^T)[x][y] = sg (W[x][y] + (W[x][3:6] x l)_y)
+                for (int x = 0; x < 3; ++x) {
+                    const double w3[3] = {W[x * 6 + 3], W[x * 6 + 4], W[x * 6 + 5]};
+                    double cr[3];
+                    cross3(w3, l, cr);
+                    for (int yy = 0; yy < 3; ++yy) blk[x * 3 + yy] += sg * (W[x * 6 + yy] + cr[yy]);
+                }
+            }
+        }
+        for (int x = 0; x < 3; ++x)
+            for (int yy = 0; yy < 3; ++yy) H[(size_t)(3 * r + x) * m + 3 * c + yy] = (T)blk[x * 3 + yy];
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
+    if (threadIdx.x == 0) s_rank = m;
+    __syncthreads();
+    double d0 = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+            const double v = (double)H[(size_t)i * m + i];
+            if (v > best) { best = v; bi = i; }
+        }
+        shv[threadIdx.x] = best;
+        shi[threadIdx.x] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double o = shv[threadIdx.x + s];
+                const int oi = shi[threadIdx.x + s];
+                if (o > shv[threadIdx.x] || (o == shv[threadIdx.x] && oi < shi[threadIdx.x])) {
+                    shv[threadIdx.x] = o;
+                    shi[threadIdx.x] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        const double dmax = shv[0];
+        if (k == 0) d0 = dmax;
+        if (!(dmax > tol * d0) || !(dmax > 0.0)) {
+            if (threadIdx.x == 0) s_rank = k;
+            __syncthreads();
+            break;
+        }
+        const int j = shi[0];
+        __syncthreads();
+        if (j != k) {
+            for (int c = threadIdx.x; c < m; c += blockDim.x) {
+                const T t = H[(size_t)k * m + c];
+                H[(size_t)k * m + c] = H[(size_t)j * m + c];
+                H[(size_t)j * m + c] = t;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < m; r += blockDim.x) {
+                const T t = H[(size_t)r * m + k];
+                H[(size_t)r * m + k] = H[(size_t)r * m + j];
+                H[(size_t)r * m + j] = t;
+            }
+            if (threadIdx.x == 0) {
+                const int t = perm[k];
+                perm[k] = perm[j];
+                perm[j] = t;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const T d = (T)sqrt((double)H[(size_t)k * m + k]);
+            H[(size_t)k * m + k] = d;
+            sh[0] = 1.0 / (double)d;
+        }
+        __syncthreads();
+        const T inv = (T)sh[0];
+        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) H[(size_t)i * m + k] *= inv;
+        __syncthreads();
+        const int len = m - k - 1;
+        for (int idx = threadIdx.x; idx < len * len; idx += blockDim.x) {
+            const int i = k + 1 + idx / len, jj = k + 1 + idx % len;
+            H[(size_t)i * m + jj] -= H[(size_t)i * m + k] * H[(size_t)jj * m + k];
+        }
+        __syncthreads();
+    }
+    const int r = s_rank;
+    if (threadIdx.x == 0) rank_out[a] = r;
+    block_lower_inverse(H, X, r, m, colbuf);
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Ga[idx] = (T)0;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+        const int i = idx / r, j = idx % r;
+        const int k0 = i > j ? i : j;
+        T s = 0;
+        for (int k = k0; k < r; ++k) s = fma(X[(size_t)k * m + i], X[(size_t)k * m + j], s);
+        Ga[(size_t)perm[i] * m + perm[j]] = s;
+    }
+}
+
+// ------------------------------------------------------------- apply ---
+// Work item it: body pcw_body[it], rows pcw_chunk[it]*32 .. +32.  128 threads:
+// lane = row within the chunk, warp = quarter of the columns.
+template <class T>
+__global__ void __launch_bounds__(128)
+k_pc_ap1(const int* __restrict__ pcw_body, const int* __restrict__ pcw_chunk,
+         const int* __restrict__ blob_off, const T* __restrict__ minv,
+         const long long* __restrict__ moff, const T* __restrict__ Y, const double* __restrict__ r,
+         double* __restrict__ w, double* __restrict__ ytp) {
+    __shared__ double red[4][kRows];
+    __shared__ double yred[4][6];
+    const int it = blockIdx.x;
+    const int b = pcw_body[it];
+    const int i0 = blob_off[b];
+    const int m = 3 * (blob_off[b + 1] - i0);
+    const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
+    const int row = pcw_chunk[it] * kRows + lane;
+    const T* A = minv + moff[b];
+    const double* r1 = r + 3 * (size_t)i0;
+    double s = 0.0;
+    if (row < m) {
+        T acc = 0;
+        for (int k = part; k < m; k += 4) acc = fma(A[(size_t)k * m + row], (T)r1[k], acc);
+        s = (double)acc;
+    }
+    red[part][lane] = s;
+    // partial Y^T r1 over this chunk's rows (warp `part` takes columns part, part+4)
+    double yv[6] = {0, 0, 0, 0, 0, 0};
+    if (part == 0 && row < m) {
+        const T* Yr = Y + 18 * (size_t)i0 + 6 * (size_t)row;
+        const double ri = r1[row];
+        for (int c = 0; c < 6; ++c) yv[c] = (double)Yr[c] * ri;
+    }
+    if (part == 0)
+        for (int c = 0; c < 6; ++c) {
+            const double t = warp_sum(yv[c]);
+            if (lane == 0) yred[0][c] = t;
+        }
+    __syncthreads();
+    if (part == 0) {
+        if (row < m) w[3 * (size_t)i0 + row] = red[0][lane] + red[1][lane] + red[2][lane] + red[3][lane];
+        if (lane < 6) ytp[6 * (size_t)it + lane] = yred[0][lane];
+    }
+}
+
+// U^_b = N~_b (-r2_b - sum of the body's Y^T r1 partials)
+__global__ void k_pc_uhat(int Nb, int M, const int* __restrict__ pcw_off,
+                          const double* __restrict__ Nt, const double* __restrict__ r,
+                          const double* __restrict__ ytp, double* __restrict__ Uhat) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= M) return;
+    double v[6];
+    const double* r2 = r + 3 * (size_t)Nb + 6 * (size_t)b;
+    for (int c = 0; c < 6; ++c) v[c] = -r2[c];
+    for (int it = pcw_off[b]; it < pcw_off[b + 1]; ++it)
+        for (int c = 0; c < 6; ++c) v[c] -= ytp[6 * (size_t)it + c];
+    const double* N = Nt + 36 * (size_t)b;
+    for (int a = 0; a < 6; ++a) {
+        double s = 0.0;
+        for (int c = 0; c < 6; ++c) s += N[a * 6 + c] * v[c];
+        Uhat[6 * (size_t)b + a] = s;
+    }
+}
+
+// c_n = r3_n - (C U^)_n
+__global__ void k_pc_cvec(int Nb, int M, int P, const int* __restrict__ bp, const int* __restrict__ bq,
+                          const double* __restrict__ lp, const double* __restrict__ lq,
+                          const double* __restrict__ Uhat, const double* __restrict__ r,
+                          double* __restrict__ cbuf) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= P) return;
+    const double* r3 = r + 3 * (size_t)Nb + 6 * (size_t)M;
+    const double* up = Uhat + 6 * bp[n];
+    const double* uq = Uhat + 6 * bq[n];
+    double wp[3], wq[3];
+    cross3(up + 3, lp + 3 * n, wp);
+    cross3(uq + 3, lq + 3 * n, wq);
+    for (int x = 0; x < 3; ++x) cbuf[3 * n + x] = r3[3 * n + x] - (up[x] + wp[x] - uq[x] - wq[x]);
+}
+
+// phi rows of one (articulated body, 32-row chunk) item: phi = G~ c
+template <class T>
+__global__ void __launch_bounds__(128)
+k_pc_ap2(int Nb, int M, const int* __restrict__ pca_asm, const int* __restrict__ pca_chunk,
+         const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
+         const T* __restrict__ G, const long long* __restrict__ goff, const double* __restrict__ cbuf,
+         double* __restrict__ z) {
+    __shared__ double red[4][kRows];
+    const int it = blockIdx.x;
+    const int a = pca_asm[it];
+    const int L0 = asm_link_off[a];
+    const int m = 3 * (asm_link_off[a + 1] - L0);
+    const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
+    const int row = pca_chunk[it] * kRows + lane;
+    const T* Ga = G + goff[a];
+    double s = 0.0;
+    if (row < m) {
+        T acc = 0;
+        for (int k = part; k < m; k += 4) {
+            const int n = asm_link_idx[L0 + k / 3];
+            acc = fma(Ga[(size_t)k * m + row], (T)cbuf[3 * n + k % 3], acc);
+        }
+        s = (double)acc;
+    }
+    red[part][lane] = s;
+    __syncthreads();
+    if (part == 0 && row < m) {
+        const int n = asm_link_idx[L0 + row / 3];
+        z[3 * (size_t)Nb + 6 * (size_t)M + 3 * n + row % 3] = red[0][lane] + red[1][lane] + red[2][lane] + red[3][lane];
+    }
+}
+
+// U_b = U^_b + N~_b (C^T phi)_b;  lambda rows = w + Y U
+template <class T>
+__global__ void __launch_bounds__(128)
+k_pc_ap3(int Nb, int M, const int* __restrict__ pcw_body, const int* __restrict__ pcw_chunk,
+         const int* __restrict__ blob_off, const T* __restrict__ Y, const double* __restrict__ Nt,
+         const double* __restrict__ w, const double* __restrict__ Uhat,
+         const int* __restrict__ bl_off, const int* __restrict__ bl_idx,
+         const double* __restrict__ lp, const double* __restrict__ lq, double* __restrict__ z) {
+    __shared__ double sU[6];
+    const int it = blockIdx.x;
+    const int b = pcw_body[it];
+    const double* phi = z + 3 * (size_t)Nb + 6 * (size_t)M;
+    if (threadIdx.x == 0) {
+        double f[6] = {0, 0, 0, 0, 0, 0};
+        for (int k = bl_off[b]; k < bl_off[b + 1]; ++k) {
+            const int e = bl_idx[k];
+            const int n = e >> 1;
+            const double sg = (e & 1) ? -1.0 : 1.0;
+            const double* l = (e & 1) ? lq + 3 * n : lp + 3 * n;
+            const double* ph = phi + 3 * n;
+            double t[3];
+            cross3(l, ph, t);
+            for (int x = 0; x < 3; ++x) { f[x] += sg * ph[x]; f[3 + x] += sg * t[x]; }
+        }
+        const double* N = Nt + 36 * (size_t)b;
+        for (int x = 0; x < 6; ++x) {
+            double s = Uhat[6 * (size_t)b + x];
+            for (int c = 0; c < 6; ++c) s += N[x * 6 + c] * f[c];
+            sU[x] = s;
+        }
+        if (pcw_chunk[it] == 0)
+            for (int x = 0; x < 6; ++x) z[3 * (size_t)Nb + 6 * (size_t)b + x] = sU[x];
+    }
+    __syncthreads();
+    const int i0 = blob_off[b];
+    const int m = 3 * (blob_off[b + 1] - i0);
+    const int row = pcw_chunk[it] * kRows + threadIdx.x;
+    if (threadIdx.x < kRows && row < m) {
+        const T* Yr = Y + 18 * (size_t)i0 + 6 * (size_t)row;
+        double s = w[3 * (size_t)i0 + row];
+        for (int c = 0; c < 6; ++c) s = fma((double)Yr[c], sU[c], s);
+        z[3 * (size_t)i0 + row] = s;
+    }
+}
+
+// ----------------------------------------------------------------- host ---
+template <class T>
+static void pc_build_t(am_handle* h, double tol) {
+    cudaStream_t s = h->stream;
+    // 16 warps per block unless the per-warp column buffers of the largest
+    // body or articulated body would exceed 200 KB of shared memory
+    auto pick = [](size_t col_bytes) {
+        int w = 16;
+        while (w > 1 && (size_t)w * col_bytes > 200 * 1024) w /= 2;
+        return w;
+    };
+    const size_t colb = (size_t)3 * h->max_body_blobs * sizeof(T);
+    const size_t cola = (size_t)3 * std::max(1, h->max_asm_links) * sizeof(T);
+    const int wb = pick(colb), wa = pick(cola);
+    const int threads_b = 32 * wb, threads_a = 32 * wa;
+    const size_t smem_b = wb * colb, smem_a = wa * cola;
+    if (smem_b > 48 * 1024)
+        cudaFuncSetAttribute(k_pcb_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+    if (smem_a > 48 * 1024)
+        cudaFuncSetAttribute(k_pca_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
+    k_pcb_build<T><<<h->M, threads_b, smem_b, s>>>(h->d_blob_off, h->d_r4, h->d_d4, h->d_minv_off,
+                                                 (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt,
+                                                 rpy_consts<double>(h->prm), h->cfg.wall, h->d_flags);
+    count_launch();
+    if (h->P) {
+        k_pca_build<T><<<h->NA, threads_a, smem_a, s>>>(h->d_asm_link_off, h->d_asm_link_idx, h->d_bp,
+                                                      h->d_bq, h->d_lp, h->d_lq, h->d_Nt, h->d_G_off,
+                                                      (T*)h->d_G, (T*)h->d_Gwork, h->d_perm,
+                                                      h->d_perm_off, h->d_G_rank, tol);
+        count_launch();
+    }
+}
+
+void pc_build(am_handle* h) {
+    if (h->pc32)
+        pc_build_t<float>(h, 1e-5);
+    else
+        pc_build_t<double>(h, 1e-11);
+    h->pc_valid = true;
+}
+
+template <class T>
+static void pc_apply_t(am_handle* h, const double* r, double* z) {
+    cudaStream_t s = h->stream;
+    k_pc_ap1<T><<<h->n_pcw, 128, 0, s>>>(h->d_pcw_body, h->d_pcw_chunk, h->d_blob_off, (const T*)h->d_minv,
+                                          h->d_minv_off, (const T*)h->d_Y, r, h->d_pc_w, h->d_ytp);
+    k_pc_uhat<<<(h->M + 127) / 128, 128, 0, s>>>(h->Nb, h->M, h->d_pcw_off, h->d_Nt, r, h->d_ytp,
+                                                  h->d_pc_Uhat);
+    count_launch(2);
+    if (h->P) {
+        k_pc_cvec<<<(h->P + 127) / 128, 128, 0, s>>>(h->Nb, h->M, h->P, h->d_bp, h->d_bq, h->d_lp, h->d_lq,
+                                                      h->d_pc_Uhat, r, h->d_cbuf);
+        k_pc_ap2<T><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk, h->d_asm_link_off,
+                                              h->d_asm_link_idx, (const T*)h->d_G, h->d_G_off, h->d_cbuf, z);
+        count_launch(2);
+    }
+    k_pc_ap3<T><<<h->n_pcw, 128, 0, s>>>(h->Nb, h->M, h->d_pcw_body, h->d_pcw_chunk, h->d_blob_off,
+                                          (const T*)h->d_Y, h->d_Nt, h->d_pc_w, h->d_pc_Uhat,
+                                          h->d_body_link_off, h->d_body_link_idx, h->d_lp, h->d_lq, z);
+    count_launch();
+}
+
+void pc_apply(am_handle* h, const double* r, double* z) {
+    if (h->pc32)
+        pc_apply_t<float>(h, r, z);
+    else
+        pc_apply_t<double>(h, r, z);
+}
+
+}  // namespace am

@@ -60,23 +60,24 @@ RpyParams make_params(double eta, double a) {
 }
 
 Split choose_split(int n, int precision) {
-    Split s{1, std::max(n, 1)};
+    Split s{1, std::max(n, 1), 1};
     if (n <= 0) return s;
-    int tiles = (n + kTile - 1) / kTile;
-    int tblocks = (n + kThreads - 1) / kThreads;
-    int want = 4 * num_sms();              // blocks to fill the GPU
-    int splits = std::max(1, std::min(tiles, (want + tblocks - 1) / tblocks));
-    int per = (tiles + splits - 1) / splits;  // tiles per chunk
+    const int want = 4 * num_sms();  // blocks to fill the GPU
+    // two targets per thread once one source chunk already fills the GPU
+    if (precision == AM_MIXED && (n + 2 * kThreads - 1) / (2 * kThreads) >= want) s.tpt = 2;
+    const int tiles = (n + kTile - 1) / kTile;
+    const int tblocks = (n + kThreads * s.tpt - 1) / (kThreads * s.tpt);
+    const int splits = std::max(1, std::min(tiles, (want + tblocks - 1) / tblocks));
+    const int per = (tiles + splits - 1) / splits;  // tiles per chunk
     s.chunk = per * kTile;
     s.splits = (n + s.chunk - 1) / s.chunk;
-    (void)precision;
     return s;
 }
 
 template <bool WALL>
 __global__ void __launch_bounds__(kThreads)
 rpy_partial_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam,
-                double* __restrict__ part, int n, int chunk, RpyParamsDev p) {
+                double* __restrict__ part, int n, int chunk, RpyK<double> k) {
     __shared__ double4_32a sr[kTile];
     __shared__ double sl[3 * kTile];
     const int i = blockIdx.x * kThreads + threadIdx.x;
@@ -88,71 +89,101 @@ rpy_partial_f64(const double4_32a* __restrict__ r4, const double* __restrict__ l
         const int cnt = min(kTile, j1 - jt);
         __syncthreads();
         if (threadIdx.x < cnt) sr[threadIdx.x] = r4[jt + threadIdx.x];
-        for (int k = threadIdx.x; k < 3 * cnt; k += kThreads) sl[k] = lam[3 * (size_t)jt + k];
+        for (int q = threadIdx.x; q < 3 * cnt; q += kThreads) sl[q] = lam[3 * (size_t)jt + q];
         __syncthreads();
 #pragma unroll 2
-        for (int k = 0; k < cnt; ++k) {
-            const double4_32a rj = sr[k];
-            const double lx = sl[3 * k], ly = sl[3 * k + 1], lz = sl[3 * k + 2];
-            pair_free_f64(ri.x - rj.x, ri.y - rj.y, ri.z - rj.z, lx, ly, lz, p, ux, uy, uz);
-            if (WALL)
-                pair_image_f64(ri.x - rj.x, ri.y - rj.y, ri.z + rj.z, ri.z, rj.z, lx, ly, lz, p,
-                               ux, uy, uz);
+        for (int q = 0; q < cnt; ++q) {
+            const double4_32a rj = sr[q];
+            const double lx = sl[3 * q], ly = sl[3 * q + 1], lz = sl[3 * q + 2];
+            const double dx = ri.x - rj.x, dy = ri.y - rj.y;
+            pair_free<double>(dx, dy, ri.z - rj.z, lx, ly, lz, k, ux, uy, uz);
+            if (WALL) pair_image<double>(dx, dy, ri.z + rj.z, ri.z, rj.z, lx, ly, lz, k, ux, uy, uz);
         }
     }
     if (i < n) {
         double* o = part + (size_t)blockIdx.y * 3 * n + 3 * (size_t)i;
-        o[0] = ux; o[1] = uy; o[2] = uz;
+        o[0] = k.A1 * ux; o[1] = k.A1 * uy; o[2] = k.A1 * uz;
     }
 }
 
-// Positions as hi + lo float pairs: differences of nearby blobs are formed
-// from the exact hi difference plus the lo difference, so they keep FP32
-// relative accuracy even far from the origin.  Pair terms and the sum over
-// one tile are FP32; tile sums are added in FP64.
-template <bool WALL>
-__global__ void __launch_bounds__(kThreads)
+// Positions as hi + lo float pairs (hi = float(x), lo = float(x - hi)).  A
+// pair's difference is first formed from hi alone; within a radius of a
+// quarter of the target's largest coordinate, where the rounding of hi
+// (1.2e-7 |x|) would exceed 5e-7 of the distance, the lo parts are added,
+// which keeps FP32 relative accuracy of nearby differences anywhere in the
+// domain.  Pair terms and the sum over one tile are FP32; tile sums are
+// folded into FP64.  TPT targets per thread share each shared-memory load.
+template <bool WALL, int TPT>
+__global__ void __launch_bounds__(kThreads, 4)
 rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
                   const double* __restrict__ lam, double* __restrict__ part, int n,
-                  int chunk, RpyParamsF p) {
+                  int chunk, RpyK<float> k) {
     __shared__ float4 sh[kTile];
     __shared__ float4 so[kTile];
-    __shared__ float sl[3 * kTile];
-    const int i = blockIdx.x * kThreads + threadIdx.x;
+    __shared__ float4 sl[kTile];
     const int j0 = blockIdx.y * chunk;
     const int j1 = min(n, j0 + chunk);
-    float4 hi_i = (i < n) ? hi[i] : make_float4(0.f, 0.f, 1.f, 0.f);
-    float4 lo_i = (i < n) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    double Ux = 0.0, Uy = 0.0, Uz = 0.0;
+    float4 hi_i[TPT], lo_i[TPT];
+    float near2[TPT];
+    double U[TPT][3];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int i = (blockIdx.x * TPT + t) * kThreads + threadIdx.x;
+        hi_i[t] = (i < n) ? hi[i] : make_float4(0.f, 0.f, 1.f, 0.f);
+        lo_i[t] = (i < n) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float nr = 0.25f * fmaxf(fabsf(hi_i[t].x), fmaxf(fabsf(hi_i[t].y), fabsf(hi_i[t].z)));
+        near2[t] = nr * nr;
+        U[t][0] = U[t][1] = U[t][2] = 0.0;
+    }
     for (int jt = j0; jt < j1; jt += kTile) {
         const int cnt = min(kTile, j1 - jt);
         __syncthreads();
         if (threadIdx.x < cnt) {
-            sh[threadIdx.x] = hi[jt + threadIdx.x];
-            so[threadIdx.x] = lo[jt + threadIdx.x];
+            const int j = jt + threadIdx.x;
+            sh[threadIdx.x] = hi[j];
+            so[threadIdx.x] = lo[j];
+            sl[threadIdx.x] = make_float4((float)lam[3 * (size_t)j], (float)lam[3 * (size_t)j + 1],
+                                          (float)lam[3 * (size_t)j + 2], 0.f);
         }
-        for (int k = threadIdx.x; k < 3 * cnt; k += kThreads) sl[k] = (float)lam[3 * (size_t)jt + k];
         __syncthreads();
-        float ux = 0.f, uy = 0.f, uz = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < cnt; ++k) {
-            const float4 h = sh[k];
-            const float4 l = so[k];
-            const float lx = sl[3 * k], ly = sl[3 * k + 1], lz = sl[3 * k + 2];
-            float dx = (hi_i.x - h.x) + (lo_i.x - l.x);
-            float dy = (hi_i.y - h.y) + (lo_i.y - l.y);
-            float dz = (hi_i.z - h.z) + (lo_i.z - l.z);
-            pair_free_f32(dx, dy, dz, lx, ly, lz, p, ux, uy, uz);
-            if (WALL) {
-                float Rz = (hi_i.z + h.z) + (lo_i.z + l.z);
-                pair_image_f32(dx, dy, Rz, hi_i.z, h.z, lx, ly, lz, p, ux, uy, uz);
+        float u[TPT][3];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) u[t][0] = u[t][1] = u[t][2] = 0.f;
+#pragma unroll 2
+        for (int q = 0; q < cnt; ++q) {
+            const float4 h = sh[q];
+            const float4 l = sl[q];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                float dx = hi_i[t].x - h.x, dy = hi_i[t].y - h.y, dz = hi_i[t].z - h.z;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < near2[t]) {
+                    const float4 o = so[q];
+                    dx += lo_i[t].x - o.x;
+                    dy += lo_i[t].y - o.y;
+                    dz += lo_i[t].z - o.z;
+                    r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                }
+                pair_free_r2<float>(dx, dy, dz, r2, l.x, l.y, l.z, k, u[t][0], u[t][1], u[t][2]);
+                if (WALL)
+                    pair_image<float>(dx, dy, hi_i[t].z + h.z, hi_i[t].z, h.z, l.x, l.y, l.z, k,
+                                      u[t][0], u[t][1], u[t][2]);
             }
         }
-        Ux += (double)ux; Uy += (double)uy; Uz += (double)uz;
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            U[t][0] += (double)u[t][0];
+            U[t][1] += (double)u[t][1];
+            U[t][2] += (double)u[t][2];
+        }
     }
-    if (i < n) {
-        double* o = part + (size_t)blockIdx.y * 3 * n + 3 * (size_t)i;
-        o[0] = Ux; o[1] = Uy; o[2] = Uz;
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int i = (blockIdx.x * TPT + t) * kThreads + threadIdx.x;
+        if (i < n) {
+            double* o = part + (size_t)blockIdx.y * 3 * n + 3 * (size_t)i;
+            o[0] = k.A1 * U[t][0]; o[1] = k.A1 * U[t][1]; o[2] = k.A1 * U[t][2];
+        }
     }
 }
 
@@ -178,19 +209,16 @@ __global__ void sum_partials(const double* __restrict__ part, double* __restrict
     u[k] = s;
 }
 
-static RpyParamsF f32_params(const RpyParams& q) {
-    return RpyParamsF{(float)q.a2, (float)q.four_a2, (float)q.inv8pieta, (float)q.k_far2,
-                      (float)q.k_far3, (float)q.mu0, (float)q.k_near1, (float)q.k_near2};
-}
 
 void launch_rpy_partial_f64(const double4_32a* r4, const double* lam, double* part, int n,
                             const Split& sp, const RpyParams& prm, int wall, cudaStream_t st) {
     if (n <= 0) return;
     dim3 grid((n + kThreads - 1) / kThreads, sp.splits);
+    const RpyK<double> k = rpy_consts<double>(prm);
     if (wall)
-        rpy_partial_f64<true><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, dev_params(prm));
+        rpy_partial_f64<true><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, k);
     else
-        rpy_partial_f64<false><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, dev_params(prm));
+        rpy_partial_f64<false><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, k);
     count_launch();
 }
 
@@ -198,11 +226,20 @@ void launch_rpy_partial_mixed(const float4* hi, const float4* lo, const double* 
                               int n, const Split& sp, const RpyParams& prm, int wall,
                               cudaStream_t st) {
     if (n <= 0) return;
-    dim3 grid((n + kThreads - 1) / kThreads, sp.splits);
-    if (wall)
-        rpy_partial_mixed<true><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, f32_params(prm));
-    else
-        rpy_partial_mixed<false><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, f32_params(prm));
+    const RpyK<float> k = rpy_consts<float>(prm);
+    const int per = kThreads * sp.tpt;
+    dim3 grid((n + per - 1) / per, sp.splits);
+    if (sp.tpt == 2) {
+        if (wall)
+            rpy_partial_mixed<true, 2><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k);
+        else
+            rpy_partial_mixed<false, 2><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k);
+    } else {
+        if (wall)
+            rpy_partial_mixed<true, 1><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k);
+        else
+            rpy_partial_mixed<false, 1><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k);
+    }
     count_launch();
 }
 
@@ -284,12 +321,13 @@ extern "C" AM_API int am_rpy_matvec(const double* d_r, const double* d_lambda, d
 
 extern "C" AM_API int am_flops_per_pair(int wall) {
     // Counted from pair_free_* and pair_image_* with FMA = 2 (rsqrt = 1):
-    // free: difference 3, r^2 5, rsqrt 1, ri^2 1, c1 3, c2 4, d.lambda 5,
-    //       scale 1, accumulate 12  -> 35
-    // image: Rz 1, R^2 5, rsqrt 1, s^2 1, hs 1, hx 2, ez 1, ez^2 1, A 1,
-    //        A^2 1, cI 10, cRR 10, cRz 12, czR 3, czz 9, rhat 2, dotR 5,
-    //        t 3, pre 1, accumulate 19  -> 89
-    return wall ? 35 + 89 : 35;
+    // free (pair_free): difference 3, r^2 5, rsqrt 1, ri^2 1, c1 3, c2 4,
+    //       d.lambda 5, scale 1, accumulate 12  -> 35
+    // image (pair_image): R3 1, R^2 5, rsqrt 1, s^2 1, hs 1, u 2, ez 1,
+    //       ez^2 1, A 1, A^2 1, t1 1, t2 1, cI 10, cRR 10, inner 4, cRz 3,
+    //       czR 3, czz 8, Rh 2, Rh.lambda 5, t 3, accumulate 19  -> 84
+    // (the factor 1/(8 pi eta) is applied once per target and tile)
+    return wall ? 35 + 84 : 35;
 }
 
 extern "C" AM_API long long am_kernel_launches(void) { return am::g_launches.load(); }

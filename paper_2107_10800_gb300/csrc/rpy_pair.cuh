@@ -1,134 +1,129 @@
 // Pair terms of the blob mobility (Sec. 2.3, Eq. RPY), shared by the
-// all-pairs product and the preconditioner's same-body blocks.  The formulas
-// are stated at the top of rpy.cu.
+// all-pairs product and the preconditioner's same-body blocks.
+//
+// The functions accumulate u / A1 with A1 = 1/(8 pi eta); callers multiply
+// the sums by A1 once.  With d = r_i - r_j, r = |d|, ri = 1/r:
+//   free, r >= 2a:  c1 = ri (1 + (2a^2/3) ri^2),  c2 = ri^3 (1 - 2a^2 ri^2)
+//   free, r <  2a:  c1 = (4/(3a)) (1 - 9r/(32a)), c2 = 1/(8 a^2 r)  (0 at r = 0)
+//   u/A1 += c1 lambda + c2 d (d . lambda)
+// which is (1/(8 pi eta r)) [(1 + 2a^2/(3r^2)) I + (1 - 2a^2/r^2) dhat dhat]
+// far and mu0 [(1 - 9r/(32a)) I + (3r/(32a)) dhat dhat] near, mu0 = 1/(6 pi eta a).
+//
+// Wall image part, R = x - y* (y* the mirror image of the source in z = 0),
+// s = 1/|R|, Rh = R s, h = source height, x3 = target height, ez = R3 s,
+// A = a^2 s^2, u = h x3 s^2, t1 = A ez^2, t2 = A^2 ez^2:
+//   cI  = -1 - 2u - 2/3 A + 2 t1 + 2/3 A^2 - 10/3 t2
+//   cRR = -1 + 6u + 2 A - 10 t1 - 10/3 A^2 + 70/3 t2
+//   cRz = 2 h s + ez (-2 cRR - 2 + 20/3 A^2)
+//   czR = 2 h s - 20/3 A^2 ez
+//   czz = -4 (h s)^2 - 4 t1 - 8/3 A^2 + 20 t2
+//   u/A1 += s [cI lambda + (cRR (Rh.lambda) + cRz lambda_3) Rh
+//              + (czR (Rh.lambda) + czz lambda_3) e3]
+// (the image terms of Blake's Green's function averaged over both blob
+// surfaces, (1 + a^2/6 lap_x)(1 + a^2/6 lap_y), exact for blobs above a).
 #pragma once
 #include "am_internal.cuh"
 
 namespace am {
 
-// ---------------------------------------------------------------- FP64 ---
-struct RpyParamsDev {
-    double a2, four_a2, inv8pieta, k_far2, k_far3, mu0, k_near1, k_near2;
+template <class T>
+struct RpyK {
+    T a2;        // a^2
+    T four_a2;   // 4 a^2 (contact distance squared)
+    T kf2;       // 2 a^2 / 3
+    T kf3;       // 2 a^2
+    T kn0;       // 4 / (3 a)
+    T kn1;       // 9 / (32 a)
+    T kn2;       // 1 / (8 a^2)
+    double A1;   // 1 / (8 pi eta)
 };
 
-__device__ __forceinline__ void pair_free_f64(double dx, double dy, double dz,
-                                              double lx, double ly, double lz,
-                                              const RpyParamsDev& p,
-                                              double& ux, double& uy, double& uz) {
-    double r2 = dx * dx + dy * dy + dz * dz;
-    double c1, c2;
-    if (r2 >= p.four_a2) {
-        double ri = rsqrt(r2);
-        double ri2 = ri * ri;
-        c1 = ri * fma(p.k_far2, ri2, p.inv8pieta);
-        c2 = ri * ri2 * fma(-p.k_far3, ri2, p.inv8pieta);
+template <class T>
+inline RpyK<T> rpy_consts(const RpyParams& q) {
+    RpyK<T> k;
+    k.a2 = (T)q.a2;
+    k.four_a2 = (T)q.four_a2;
+    k.kf2 = (T)(2.0 * q.a2 / 3.0);
+    k.kf3 = (T)(2.0 * q.a2);
+    k.kn0 = (T)(4.0 / (3.0 * q.a));
+    k.kn1 = (T)(9.0 / (32.0 * q.a));
+    k.kn2 = (T)(1.0 / (8.0 * q.a2));
+    k.A1 = q.inv8pieta;
+    return k;
+}
+
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float sqt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqt(double x) { return sqrt(x); }
+
+template <class T>
+__device__ __forceinline__ void pair_free_r2(T dx, T dy, T dz, T r2, T lx, T ly, T lz,
+                                             const RpyK<T>& k, T& ux, T& uy, T& uz) {
+    T c1, c2;
+    if (r2 >= k.four_a2) {
+        const T ri = rsq(r2);
+        const T ri2 = ri * ri;
+        c1 = ri * fma(k.kf2, ri2, (T)1);
+        c2 = (ri * ri2) * fma(-k.kf3, ri2, (T)1);
     } else {
-        double r = sqrt(r2);
-        c1 = p.mu0 * fma(-p.k_near1, r, 1.0);
-        c2 = (r2 > 0.0) ? p.k_near2 / r : 0.0;
+        const T r = sqt(r2);
+        c1 = k.kn0 * fma(-k.kn1, r, (T)1);
+        c2 = (r2 > (T)0) ? k.kn2 / r : (T)0;
     }
-    double s = c2 * (dx * lx + dy * ly + dz * lz);
-    ux = fma(c1, lx, fma(s, dx, ux));
-    uy = fma(c1, ly, fma(s, dy, uy));
-    uz = fma(c1, lz, fma(s, dz, uz));
+    const T sdl = c2 * fma(dx, lx, fma(dy, ly, dz * lz));
+    ux = fma(c1, lx, fma(sdl, dx, ux));
+    uy = fma(c1, ly, fma(sdl, dy, uy));
+    uz = fma(c1, lz, fma(sdl, dz, uz));
 }
 
-__device__ __forceinline__ void pair_image_f64(double Rx, double Ry, double Rz,
-                                               double x3, double h,
-                                               double lx, double ly, double lz,
-                                               const RpyParamsDev& p,
-                                               double& ux, double& uy, double& uz) {
-    double s = rsqrt(Rx * Rx + Ry * Ry + Rz * Rz);
-    double s2 = s * s;
-    double hs = h * s;
-    double hx = hs * (x3 * s);
-    double ez = Rz * s;
-    double ez2 = ez * ez;
-    double A = p.a2 * s2;
-    double A2 = A * A;
-    double cI = -1.0 - 2.0 * hx + A * fma(2.0, ez2, -2.0 / 3.0) + A2 * fma(-10.0 / 3.0, ez2, 2.0 / 3.0);
-    double cRR = -1.0 + 6.0 * hx + A * fma(-10.0, ez2, 2.0) + A2 * fma(70.0 / 3.0, ez2, -10.0 / 3.0);
-    double cRz = fma(ez, -12.0 * hx + A * fma(20.0, ez2, -4.0) + A2 * fma(-140.0 / 3.0, ez2, 40.0 / 3.0), 2.0 * hs);
-    double czR = fma(-20.0 / 3.0 * A2, ez, 2.0 * hs);
-    double czz = -4.0 * hs * hs - 4.0 * A * ez2 + A2 * fma(20.0, ez2, -8.0 / 3.0);
-    double rx = Rx * s, ry = Ry * s;
-    double dotR = rx * lx + ry * ly + ez * lz;
-    double t = fma(cRR, dotR, cRz * lz);
-    double pre = p.inv8pieta * s;
-    ux = fma(pre, fma(cI, lx, t * rx), ux);
-    uy = fma(pre, fma(cI, ly, t * ry), uy);
-    uz = fma(pre, fma(cI, lz, fma(t, ez, fma(czR, dotR, czz * lz))), uz);
+template <class T>
+__device__ __forceinline__ void pair_free(T dx, T dy, T dz, T lx, T ly, T lz, const RpyK<T>& k,
+                                          T& ux, T& uy, T& uz) {
+    pair_free_r2<T>(dx, dy, dz, fma(dx, dx, fma(dy, dy, dz * dz)), lx, ly, lz, k, ux, uy, uz);
 }
 
-// --------------------------------------------------------------- mixed ---
-struct RpyParamsF {
-    float a2, four_a2, inv8pieta, k_far2, k_far3, mu0, k_near1, k_near2;
-};
-
-__device__ __forceinline__ void pair_free_f32(float dx, float dy, float dz,
-                                              float lx, float ly, float lz,
-                                              const RpyParamsF& p,
-                                              float& ux, float& uy, float& uz) {
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float c1, c2;
-    if (r2 >= p.four_a2) {
-        float ri = rsqrtf(r2);
-        float ri2 = ri * ri;
-        c1 = ri * fmaf(p.k_far2, ri2, p.inv8pieta);
-        c2 = ri * ri2 * fmaf(-p.k_far3, ri2, p.inv8pieta);
-    } else {
-        float r = sqrtf(r2);
-        c1 = p.mu0 * fmaf(-p.k_near1, r, 1.0f);
-        c2 = (r2 > 0.0f) ? p.k_near2 / r : 0.0f;
-    }
-    float s = c2 * fmaf(dx, lx, fmaf(dy, ly, dz * lz));
-    ux = fmaf(c1, lx, fmaf(s, dx, ux));
-    uy = fmaf(c1, ly, fmaf(s, dy, uy));
-    uz = fmaf(c1, lz, fmaf(s, dz, uz));
+template <class T>
+__device__ __forceinline__ void pair_image(T Rx, T Ry, T Rz, T x3, T h, T lx, T ly, T lz,
+                                           const RpyK<T>& k, T& ux, T& uy, T& uz) {
+    const T s = rsq(fma(Rx, Rx, fma(Ry, Ry, Rz * Rz)));
+    const T s2 = s * s;
+    const T hs = h * s;
+    const T u = hs * (x3 * s);
+    const T ez = Rz * s;
+    const T ez2 = ez * ez;
+    const T A = k.a2 * s2;
+    const T A2 = A * A;
+    const T t1 = A * ez2;
+    const T t2 = A2 * ez2;
+    const T cI = fma((T)(-10.0 / 3.0), t2, fma((T)(2.0 / 3.0), A2, fma((T)2, t1, fma((T)(-2.0 / 3.0), A, fma((T)-2, u, (T)-1)))));
+    const T cRR = fma((T)(70.0 / 3.0), t2, fma((T)(-10.0 / 3.0), A2, fma((T)-10, t1, fma((T)2, A, fma((T)6, u, (T)-1)))));
+    const T inner = fma((T)(20.0 / 3.0), A2, fma((T)-2, cRR, (T)-2));
+    const T hs2 = (T)2 * hs;
+    const T cRz = fma(ez, inner, hs2);
+    const T czR = fma((T)(-20.0 / 3.0) * A2, ez, hs2);
+    const T czz = fma((T)-4, hs * hs, fma((T)20, t2, fma((T)(-8.0 / 3.0), A2, (T)-4 * t1)));
+    const T rx = Rx * s, ry = Ry * s;
+    const T dotR = fma(rx, lx, fma(ry, ly, ez * lz));
+    const T t = fma(cRR, dotR, cRz * lz);
+    ux = fma(s, fma(cI, lx, t * rx), ux);
+    uy = fma(s, fma(cI, ly, t * ry), uy);
+    uz = fma(s, fma(cI, lz, fma(t, ez, fma(czR, dotR, czz * lz))), uz);
 }
 
-__device__ __forceinline__ void pair_image_f32(float Rx, float Ry, float Rz, float x3, float h,
-                                               float lx, float ly, float lz,
-                                               const RpyParamsF& p,
-                                               float& ux, float& uy, float& uz) {
-    float s = rsqrtf(fmaf(Rx, Rx, fmaf(Ry, Ry, Rz * Rz)));
-    float s2 = s * s;
-    float hs = h * s;
-    float hx = hs * (x3 * s);
-    float ez = Rz * s;
-    float ez2 = ez * ez;
-    float A = p.a2 * s2;
-    float A2 = A * A;
-    float cI = -1.0f - 2.0f * hx + A * fmaf(2.0f, ez2, -2.0f / 3.0f) + A2 * fmaf(-10.0f / 3.0f, ez2, 2.0f / 3.0f);
-    float cRR = -1.0f + 6.0f * hx + A * fmaf(-10.0f, ez2, 2.0f) + A2 * fmaf(70.0f / 3.0f, ez2, -10.0f / 3.0f);
-    float cRz = fmaf(ez, -12.0f * hx + A * fmaf(20.0f, ez2, -4.0f) + A2 * fmaf(-140.0f / 3.0f, ez2, 40.0f / 3.0f), 2.0f * hs);
-    float czR = fmaf(-20.0f / 3.0f * A2, ez, 2.0f * hs);
-    float czz = -4.0f * hs * hs - 4.0f * A * ez2 + A2 * fmaf(20.0f, ez2, -8.0f / 3.0f);
-    float rx = Rx * s, ry = Ry * s;
-    float dotR = fmaf(rx, lx, fmaf(ry, ly, ez * lz));
-    float t = fmaf(cRR, dotR, cRz * lz);
-    float pre = p.inv8pieta * s;
-    ux = fmaf(pre, fmaf(cI, lx, t * rx), ux);
-    uy = fmaf(pre, fmaf(cI, ly, t * ry), uy);
-    uz = fmaf(pre, fmaf(cI, lz, fmaf(t, ez, fmaf(czR, dotR, czz * lz))), uz);
-}
-
-
-// Full 3x3 tensor T (row-major, T[3a+b]: velocity a at x from force b at y).
-__device__ __forceinline__ void pair_tensor_f64(double4_32a x, double4_32a y, const RpyParamsDev& p,
-                                                int wall, double* T) {
+// Full 3x3 tensor T (row-major, T[3a+b]: velocity a at x from force b at y),
+// FP64, including the 1/(8 pi eta) factor.
+__device__ __forceinline__ void pair_tensor_f64(double4_32a x, double4_32a y, const RpyK<double>& k,
+                                                int wall, double* Tt) {
     for (int b = 0; b < 3; ++b) {
         double l[3] = {0.0, 0.0, 0.0};
         l[b] = 1.0;
         double ux = 0.0, uy = 0.0, uz = 0.0;
-        pair_free_f64(x.x - y.x, x.y - y.y, x.z - y.z, l[0], l[1], l[2], p, ux, uy, uz);
-        if (wall) pair_image_f64(x.x - y.x, x.y - y.y, x.z + y.z, x.z, y.z, l[0], l[1], l[2], p, ux, uy, uz);
-        T[b] = ux; T[3 + b] = uy; T[6 + b] = uz;
+        pair_free<double>(x.x - y.x, x.y - y.y, x.z - y.z, l[0], l[1], l[2], k, ux, uy, uz);
+        if (wall)
+            pair_image<double>(x.x - y.x, x.y - y.y, x.z + y.z, x.z, y.z, l[0], l[1], l[2], k, ux, uy, uz);
+        Tt[b] = k.A1 * ux; Tt[3 + b] = k.A1 * uy; Tt[6 + b] = k.A1 * uz;
     }
-}
-
-inline RpyParamsDev dev_params(const RpyParams& q) {
-    return RpyParamsDev{q.a2, q.four_a2, q.inv8pieta, q.k_far2, q.k_far3, q.mu0, q.k_near1, q.k_near2};
 }
 
 }  // namespace am

@@ -116,6 +116,14 @@ def test_preconditioner_matches_oracle(chains):
     assert rel(s.apply_precond(r), S.apply_preconditioner(r)) <= FP64_SOLVE
 
 
+def test_preconditioner_fp32_storage_matches_oracle(chains):
+    # mixed handles keep the preconditioner's matrices in FP32
+    w, S = chains
+    s = binding.Solver.from_workload(w, precision="mixed")
+    r = np.random.default_rng(3).standard_normal(S.n)
+    assert rel(s.apply_precond(r), S.apply_preconditioner(r)) <= 1e-4
+
+
 def test_solve_chains_matches_dense_solution(chains):
     w, S = chains
     s = binding.Solver.from_workload(w, tol=1e-13)
