@@ -122,17 +122,30 @@ class Solver:
     """One handle of the library (am_create ... am_destroy)."""
 
     def __init__(self, eta=1.0, a=0.1, wall=0, precision="fp64", tol=1e-10, restart=50,
-                 max_iter=500, corr_tol=1e-10, corr_max_iter=20, stream=None):
+                 max_iter=500, corr_tol=1e-10, corr_max_iter=20, stream=None, n_systems=1):
         L = lib()
         prec = {"fp64": AM_FP64, "mixed": AM_MIXED}[precision]
-        cfg = Config(eta, a, wall, prec, 1, tol, restart, max_iter, corr_tol, corr_max_iter,
+        cfg = Config(eta, a, wall, prec, n_systems, tol, restart, max_iter, corr_tol, corr_max_iter,
                      stream)
         h = _vp()
         rc = L.am_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != AM_OK:
             raise AmError(rc, "am_create failed (" + L.am_last_error(None).decode() + ")")
         self.h = h
-        self.M = self.Nb = self.P = 0
+        self.S = n_systems
+        self.sizes = [(0, 0, 0)] * n_systems  # (bodies, blobs, links) per system
+
+    @property
+    def M(self):
+        return sum(z[0] for z in self.sizes)
+
+    @property
+    def Nb(self):
+        return sum(z[1] for z in self.sizes)
+
+    @property
+    def P(self):
+        return sum(z[2] for z in self.sizes)
 
     def _check(self, rc, allow_nc=False):
         if rc == AM_OK or (allow_nc and rc == AM_ERR_NOT_CONVERGED):
@@ -150,7 +163,7 @@ class Solver:
         except Exception:
             pass
 
-    def set_bodies(self, q, theta, blob_offset, rho, F, assembly, slip=None):
+    def set_bodies(self, q, theta, blob_offset, rho, F, assembly, slip=None, system=0):
         M = len(np.asarray(theta).reshape(-1, 4))
         off, off_p = _i(blob_offset)
         Nb = int(off[-1])
@@ -160,10 +173,11 @@ class Solver:
         fa, fp = _d(F, 6 * M)
         sa, sp = _d(slip, 3 * Nb)
         aa, ap = _i(assembly)
-        self._check(lib().am_set_bodies(self.h, 0, M, qp, tp, off_p, rp, fp, sp, ap))
-        self.M, self.Nb, self.P = M, Nb, 0
+        self._check(lib().am_set_bodies(self.h, system, M, qp, tp, off_p, rp, fp, sp, ap))
+        self.sizes = list(self.sizes)
+        self.sizes[system] = (M, Nb, 0)
 
-    def set_constraints(self, body_p, body_q, dl_p, dl_q, dl_p_dot=None, dl_q_dot=None):
+    def set_constraints(self, body_p, body_q, dl_p, dl_q, dl_p_dot=None, dl_q_dot=None, system=0):
         bp, bpp = _i(body_p)
         bq, bqp = _i(body_q)
         P = len(bp)
@@ -171,16 +185,18 @@ class Solver:
         a2, p2 = _d(dl_q, 3 * P)
         a3, p3 = _d(dl_p_dot, 3 * P)
         a4, p4 = _d(dl_q_dot, 3 * P)
-        self._check(lib().am_set_constraints(self.h, 0, P, bpp, bqp, p1, p2, p3, p4))
-        self.P = P
+        self._check(lib().am_set_constraints(self.h, system, P, bpp, bqp, p1, p2, p3, p4))
+        self.sizes = list(self.sizes)
+        self.sizes[system] = (self.sizes[system][0], self.sizes[system][1], P)
 
-    def set_joints(self, body_p, body_q, joints):
+    def set_joints(self, body_p, body_q, joints, system=0):
         bp, bpp = _i(body_p)
         bq, bqp = _i(body_q)
         P = len(bp)
         ja, jp = _d(joints, 3 * P)
-        self._check(lib().am_set_joints(self.h, 0, P, bpp, bqp, jp))
-        self.P = P
+        self._check(lib().am_set_joints(self.h, system, P, bpp, bqp, jp))
+        self.sizes = list(self.sizes)
+        self.sizes[system] = (self.sizes[system][0], self.sizes[system][1], P)
 
     @property
     def n(self):
@@ -209,16 +225,26 @@ class Solver:
                     allow_nc=True)
         return U.reshape(-1, 6), phi.reshape(-1, 3), lam.reshape(-1, 3), st.as_dict()
 
-    def bodies(self):
-        q, qp = _out(3 * self.M)
-        th, tp = _out(4 * self.M)
-        self._check(lib().am_get_bodies(self.h, 0, qp, tp))
+    def bodies(self, system=0):
+        M = self.sizes[system][0]
+        q, qp = _out(3 * M)
+        th, tp = _out(4 * M)
+        self._check(lib().am_get_bodies(self.h, system, qp, tp))
         return q.reshape(-1, 3), th.reshape(-1, 4)
 
-    def blobs(self):
-        r, rp = _out(3 * self.Nb)
-        self._check(lib().am_get_blobs(self.h, 0, rp))
+    def blobs(self, system=0):
+        Nb = self.sizes[system][1]
+        r, rp = _out(3 * Nb)
+        self._check(lib().am_get_blobs(self.h, system, rp))
         return r.reshape(-1, 3)
+
+    def split(self, U, phi, lam):
+        """Per-system views of solve outputs (which concatenate the systems)."""
+        out, b0, l0, p0 = [], 0, 0, 0
+        for M, Nb, P in self.sizes:
+            out.append((U[b0:b0 + M], phi[p0:p0 + P], lam[l0:l0 + Nb]))
+            b0 += M; l0 += Nb; p0 += P
+        return out
 
     def apply_mobility(self, lam):
         la, lp = _d(lam, 3 * self.Nb)
@@ -247,17 +273,33 @@ class Solver:
                                              ctypes.byref(k)))
         return ms.value, k.value
 
-    @classmethod
-    def from_workload(cls, w, t=0.0, **kw):
-        """A solver holding a workload dict of paper_2107_10800_gb300.workloads."""
-        s = cls(eta=w["eta"], a=w["a"], wall=w["wall"], **kw)
-        s.set_bodies(w["q"], w["theta"], w["blob_offset"], w["rho"], w["F"], w["assembly"])
+    def load(self, w, system=0, t=0.0):
+        """Set system `system` from a workload dict of
+        paper_2107_10800_gb300.workloads."""
+        self.set_bodies(w["q"], w["theta"], w["blob_offset"], w["rho"], w["F"], w["assembly"],
+                        system=system)
         if len(w["body_p"]):
             if w.get("dl") is not None:
                 dlp, dlq, dlpd, dlqd = w["dl"](t)
-                s.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd)
+                self.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd, system=system)
             else:
-                s.set_joints(w["body_p"], w["body_q"], w["joints"])
+                self.set_joints(w["body_p"], w["body_q"], w["joints"], system=system)
+
+    @classmethod
+    def from_workload(cls, w, t=0.0, **kw):
+        """A solver holding one workload dict."""
+        s = cls(eta=w["eta"], a=w["a"], wall=w["wall"], **kw)
+        s.load(w, 0, t)
+        return s
+
+    @classmethod
+    def from_workloads(cls, ws, t=0.0, **kw):
+        """A solver holding several independent workloads (one system each;
+        they must share eta, a and wall)."""
+        w0 = ws[0]
+        s = cls(eta=w0["eta"], a=w0["a"], wall=w0["wall"], n_systems=len(ws), **kw)
+        for k, w in enumerate(ws):
+            s.load(w, k, t)
         return s
 
 

@@ -98,6 +98,17 @@ __device__ __forceinline__ void quat_from_rotvec(double gx, double gy, double gz
 }  // namespace am
 
 // ---- the handle -----------------------------------------------------------
+// Host copy of one system (suspension) as last set by the caller; local body
+// indices.  The device layout concatenates all systems.
+struct am_sys_rec {
+    bool has_bodies = false;
+    int M = 0, Nb = 0, NA = 0, P = 0;
+    std::vector<double> q, theta, rho, F, slip;
+    std::vector<int> blob_off, asm_of_body;
+    std::vector<int> bp, bq;
+    std::vector<double> dlp, dlq, dlpd, dlqd;  // dlpd empty: passive links
+};
+
 struct am_handle {
     am_config cfg{};
     cudaStream_t stream = nullptr;
@@ -105,9 +116,35 @@ struct am_handle {
     std::string err;
     am::RpyParams prm{};
 
-    // sizes
+    // sizes (all systems together)
     int M = 0, Nb = 0, P = 0, NA = 0, n = 0;
     bool have_bodies = false;
+
+    // systems: host records, layout state and per-system offsets
+    int S = 1;
+    std::vector<am_sys_rec> sys;
+    bool dirty = true;        // records changed since the device layout was built
+    bool committed = false;   // a device layout exists
+    std::vector<int> sys_body0, sys_blob0, sys_link0, sys_asm0;
+    // per-system device data of the batched solve
+    int* d_sys_of_elem = nullptr;                 // n: system of each unknown
+    int *d_chunk_start = nullptr, *d_chunk_end = nullptr, *d_sys_chunk_off = nullptr;
+    int nchunks = 0;
+    int* d_sys_of_blob = nullptr;                 // Nb
+    int *d_sys_blob0 = nullptr, *d_sys_nb = nullptr, *d_sys_nch = nullptr;
+    long long* d_sys_poff = nullptr;
+    // batched GMRES scalars (per system)
+    double *d_Hs = nullptr, *d_css = nullptr, *d_sns = nullptr, *d_gs = nullptr, *d_coefs = nullptr,
+           *d_xis = nullptr, *d_bnorm_s = nullptr, *d_beta_s = nullptr, *d_inv_s = nullptr,
+           *d_tol_s = nullptr, *d_sysred = nullptr, *d_hcols = nullptr;
+    int *d_active = nullptr, *d_kdone = nullptr;
+    // all-pairs work items (block-diagonal over systems) and their queue
+    void* d_items = nullptr;
+    int n_items = 0;
+    int* d_item_counter = nullptr;
+    int mv_tpt = 1, mv_chunk = 0, mv_grid = 0, mv_grid64 = 0;
+    long long mv_part_total = 0;
+    bool mv_tuned = false;
 
     // host structure
     std::vector<int> blob_off, asm_of_body, bp, bq;

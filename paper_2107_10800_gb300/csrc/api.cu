@@ -131,6 +131,15 @@ void free_solver(am_handle* h) {
     h->layout_gen++;
     dfree(&h->d_Hm); dfree(&h->d_cs); dfree(&h->d_sn); dfree(&h->d_g); dfree(&h->d_coef);
     dfree(&h->d_xi); dfree(&h->d_part); dfree(&h->d_npart);
+    dfree(&h->d_sys_of_elem); dfree(&h->d_sys_of_blob); dfree(&h->d_chunk_start); dfree(&h->d_chunk_end);
+    dfree(&h->d_sys_chunk_off); dfree(&h->d_Hs); dfree(&h->d_css); dfree(&h->d_sns); dfree(&h->d_gs);
+    dfree(&h->d_coefs); dfree(&h->d_xis); dfree(&h->d_hcols); dfree(&h->d_bnorm_s); dfree(&h->d_beta_s);
+    dfree(&h->d_inv_s); dfree(&h->d_tol_s); dfree(&h->d_sysred); dfree(&h->d_active); dfree(&h->d_kdone);
+    dfree(&h->d_sys_blob0); dfree(&h->d_sys_nb); dfree(&h->d_sys_nch); dfree(&h->d_sys_poff);
+    dfree(&h->d_item_counter);
+    if (h->d_items) cudaFree(h->d_items);
+    h->d_items = nullptr;
+    h->n_items = 0;
 }
 
 int alloc_solver(am_handle* h) {
@@ -194,13 +203,15 @@ int build_links(am_handle* h, int P, const int* bp, const int* bq) {
         return x;
     };
     for (int n = 0; n < P; ++n) parent[find(bp[n])] = find(bq[n]);
+    // An articulated body with links must be connected by them; one without
+    // links (not set yet) only blocks time steps.
     h->links_connected = true;
     for (int a = 0; a < NA; ++a) {
         const int b0 = h->asm_body_idx[h->asm_body_off[a]];
         for (int k = h->asm_body_off[a]; k < h->asm_body_off[a + 1]; ++k)
             if (find(h->asm_body_idx[k]) != find(b0)) {
                 h->links_connected = false;
-                if (P > 0)
+                if (al_off[a + 1] > al_off[a])
                     return set_err(h, AM_ERR_ARG, "am_set_constraints: articulated body " + std::to_string(a) +
                                                       " is not connected by its links");
             }
@@ -332,6 +343,8 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 int prepare(am_handle* h, const char* who, bool warm, am_step_stats* st) {
     cudaStream_t s = h->stream;
     am::launch_geometry(h);
+    if (!h->mv_tuned && am::mobility_autotune(h))
+        return set_err(h, AM_ERR_CUDA, std::string(who) + ": mobility autotuning failed");
     CK(cudaEventRecord(h->ev[0], s));
     am::pc_build(h);
     CK(cudaEventRecord(h->ev[1], s));
@@ -358,8 +371,15 @@ int copy_outputs(am_handle* h, double* U, double* phi, double* lam) {
     return AM_OK;
 }
 
+int commit(am_handle* h, const char* who);
+bool all_have_bodies(const am_handle* h);
+
 int check_handle(am_handle* h, const char* who, bool need_bodies) {
     if (!h) { return AM_ERR_ARG; }
+    if (need_bodies && h->dirty && all_have_bodies(h)) {
+        const int rc = commit(h, who);
+        if (rc) return rc;
+    }
     if (need_bodies && !h->have_bodies) return set_err(h, AM_ERR_ARG, std::string(who) + ": no bodies set");
     return AM_OK;
 }
@@ -376,13 +396,16 @@ extern "C" AM_API int am_create(const am_config* cfg, am_handle** out) {
     if (c.corr_max_iter == 0) c.corr_max_iter = 20;
     if (c.n_systems == 0) c.n_systems = 1;
     if (!(c.eta > 0.0) || !(c.blob_radius > 0.0) || (c.wall != 0 && c.wall != 1) ||
-        (c.precision != AM_FP64 && c.precision != AM_MIXED) || c.n_systems != 1 || !(c.tol > 0.0) ||
+        (c.precision != AM_FP64 && c.precision != AM_MIXED) || c.n_systems < 1 || c.n_systems > 65536 ||
+        !(c.tol > 0.0) ||
         c.restart < 1 || c.restart > 200 || c.max_iter < 1 || !(c.corr_tol > 0.0) || c.corr_max_iter < 1)
         return AM_ERR_ARG;
     am_handle* h = new am_handle();
     h->cfg = c;
     h->restart = c.restart;
     h->pc32 = (c.precision == AM_MIXED);
+    h->S = c.n_systems;
+    h->sys.resize(h->S);
     h->prm = am::make_params(c.eta, c.blob_radius);
     if (c.cuda_stream) {
         h->stream = static_cast<cudaStream_t>(c.cuda_stream);
@@ -410,12 +433,13 @@ extern "C" AM_API int am_create(const am_config* cfg, am_handle** out) {
     return AM_OK;
 }
 
-extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const double* q, const double* theta,
-                                    const int* blob_offset, const double* rho, const double* F,
-                                    const double* slip, const int* asm_of_body) {
-    if (!h) return AM_ERR_ARG;
+namespace {
+
+// Checks one system's bodies; returns its articulated-body count and largest
+// body (blobs).
+int validate_bodies(am_handle* h, int M, const double* q, const double* theta, const int* blob_offset,
+                    const double* rho, const double* F, const int* asm_of_body, int* NA_out, int* maxb_out) {
     const char* who = "am_set_bodies";
-    if (system != 0) return set_err(h, AM_ERR_ARG, "am_set_bodies: system out of range");
     if (M <= 0 || !q || !theta || !blob_offset || !rho || !F || !asm_of_body)
         return set_err(h, AM_ERR_ARG, "am_set_bodies: n_bodies <= 0 or NULL array");
     if (blob_offset[0] != 0) return set_err(h, AM_ERR_ARG, "am_set_bodies: blob_offset[0] != 0");
@@ -428,8 +452,7 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
     if ((size_t)3 * maxb * (h->pc32 ? 4 : 8) > 200 * 1024)
         return set_err(h, AM_ERR_ARG, "am_set_bodies: a body has more blobs than the preconditioner "
                                       "build supports (8,533 in FP64, 17,066 in mixed precision)");
-    const long long Nb = blob_offset[M];
-    if (Nb > (1LL << 28)) return set_err(h, AM_ERR_ARG, "am_set_bodies: too many blobs");
+    if (blob_offset[M] > (1 << 28)) return set_err(h, AM_ERR_ARG, "am_set_bodies: too many blobs");
     int NA = 0;
     for (int p = 0; p < M; ++p) {
         if (asm_of_body[p] < 0 || asm_of_body[p] >= M)
@@ -442,13 +465,23 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
         if (!cnt[a]) return set_err(h, AM_ERR_ARG, "am_set_bodies: unused assembly index");
     int rc = check_quats(h, M, theta, who);
     if (rc) return rc;
+    *NA_out = NA;
+    *maxb_out = maxb;
+    return AM_OK;
+}
 
+// Device layout of the bodies of all systems (concatenated arrays).
+int build_layout(am_handle* h, int M, int Nb, int NA, int maxb, const double* q, const double* theta,
+                 const int* blob_offset, const double* rho, const double* F, const double* slip,
+                 const int* asm_of_body) {
+    std::vector<int> cnt(NA, 0);
+    for (int p = 0; p < M; ++p) cnt[asm_of_body[p]]++;
     free_links(h);
     free_bodies(h);
     free_solver(h);
     h->have_bodies = false;
     h->M = M;
-    h->Nb = (int)Nb;
+    h->Nb = Nb;
     h->NA = NA;
     h->P = 0;
     h->max_body_blobs = maxb;
@@ -474,7 +507,6 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
         moff[p + 1] = moff[p] + m * m;
     }
     h->minv_total = moff[M];
-    h->split = am::choose_split((int)Nb, h->cfg.precision);
     cudaStream_t s = h->stream;
     CK(dalloc(&h->d_q, 3 * (size_t)M)); CK(dalloc(&h->d_theta, 4 * (size_t)M));
     CK(dalloc(&h->d_rho, 3 * (size_t)Nb)); CK(dalloc(&h->d_F, 6 * (size_t)M));
@@ -498,7 +530,6 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
     CK(dalloc(&h->d_pcw_off, M + 1)); CK(dalloc(&h->d_ytp, 6 * pcw_body.size()));
     CK(dalloc(&h->d_minv_off, M + 1)); CK(dalloc(&h->d_pc_w, 3 * (size_t)Nb));
     CK(dalloc(&h->d_pc_Uhat, 6 * (size_t)M));
-    CK(dalloc(&h->d_mv, (size_t)h->split.splits * 3 * Nb));
     CK(dalloc(&h->d_qnew, 3 * (size_t)M)); CK(dalloc(&h->d_thnew, 4 * (size_t)M));
     CK(dalloc(&h->d_iters, NA));
     if (h->h_iters) cudaFreeHost(h->h_iters);
@@ -518,16 +549,206 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
     CK(h2d(h->d_pcw_chunk, pcw_chunk.data(), pcw_chunk.size(), s));
     CK(h2d(h->d_pcw_off, pcw_off.data(), M + 1, s));
     CK(cudaStreamSynchronize(s));
-    rc = build_links(h, 0, nullptr, nullptr);
+    return AM_OK;
+}
+
+// Per-system maps of the batched solve: system of every unknown, dot-product
+// chunks that never straddle two systems (listed system by system), the
+// per-system GMRES scalars and the mobility bookkeeping.
+int build_system_maps(am_handle* h) {
+    const int S = h->S, n = h->n, m = h->restart;
+    std::vector<int> sys_of_elem(n), sys_of_blob(h->Nb);
+    std::vector<int> cs, ce, coff(S + 1, 0);
+    const int nl = 3 * h->Nb, nu = 6 * h->M;
+    for (int sI = 0; sI < S; ++sI) {
+        const am_sys_rec& r = h->sys[sI];
+        const int segs[3][2] = {{3 * h->sys_blob0[sI], 3 * (h->sys_blob0[sI] + r.Nb)},
+                                {nl + 6 * h->sys_body0[sI], nl + 6 * (h->sys_body0[sI] + r.M)},
+                                {nl + nu + 3 * h->sys_link0[sI], nl + nu + 3 * (h->sys_link0[sI] + r.P)}};
+        for (auto& sg : segs) {
+            for (int i = sg[0]; i < sg[1]; ++i) sys_of_elem[i] = sI;
+            for (int c0 = sg[0]; c0 < sg[1]; c0 += 1024) {
+                cs.push_back(c0);
+                ce.push_back(std::min(sg[1], c0 + 1024));
+            }
+        }
+        for (int i = 0; i < r.Nb; ++i) sys_of_blob[h->sys_blob0[sI] + i] = sI;
+        coff[sI + 1] = (int)cs.size();
+    }
+    h->nchunks = (int)cs.size();
+    cudaStream_t st = h->stream;
+    CK(dalloc(&h->d_sys_of_elem, n)); CK(dalloc(&h->d_sys_of_blob, h->Nb));
+    CK(dalloc(&h->d_chunk_start, cs.size())); CK(dalloc(&h->d_chunk_end, ce.size()));
+    CK(dalloc(&h->d_sys_chunk_off, S + 1));
+    CK(dalloc(&h->d_Hs, (size_t)S * (m + 1) * m)); CK(dalloc(&h->d_css, (size_t)S * m));
+    CK(dalloc(&h->d_sns, (size_t)S * m)); CK(dalloc(&h->d_gs, (size_t)S * (m + 1)));
+    CK(dalloc(&h->d_coefs, (size_t)S * (m + 1))); CK(dalloc(&h->d_xis, (size_t)S * (m + 1)));
+    CK(dalloc(&h->d_hcols, (size_t)S * (m + 1)));
+    CK(dalloc(&h->d_bnorm_s, S)); CK(dalloc(&h->d_beta_s, S)); CK(dalloc(&h->d_inv_s, S));
+    CK(dalloc(&h->d_tol_s, S)); CK(dalloc(&h->d_sysred, 4 * (size_t)S + 16));
+    CK(dalloc(&h->d_active, S)); CK(dalloc(&h->d_kdone, S));
+    CK(dalloc(&h->d_part, (size_t)(m + 1) * std::max(1, h->nchunks)));
+    CK(dalloc(&h->d_npart, std::max(h->nchunks, 4 * am::num_sms() + 64)));
+    std::vector<int> b0(S), nb(S);
+    for (int sI = 0; sI < S; ++sI) { b0[sI] = h->sys_blob0[sI]; nb[sI] = h->sys[sI].Nb; }
+    CK(dalloc(&h->d_sys_blob0, S)); CK(dalloc(&h->d_sys_nb, S));
+    CK(dalloc(&h->d_sys_nch, S)); CK(dalloc(&h->d_sys_poff, S));
+    CK(dalloc(&h->d_item_counter, 1));
+    CK(h2d(h->d_sys_of_elem, sys_of_elem.data(), n, st));
+    CK(h2d(h->d_sys_of_blob, sys_of_blob.data(), h->Nb, st));
+    CK(h2d(h->d_chunk_start, cs.data(), cs.size(), st));
+    CK(h2d(h->d_chunk_end, ce.data(), ce.size(), st));
+    CK(h2d(h->d_sys_chunk_off, coff.data(), S + 1, st));
+    CK(h2d(h->d_sys_blob0, b0.data(), S, st));
+    CK(h2d(h->d_sys_nb, nb.data(), S, st));
+    CK(cudaStreamSynchronize(st));
+    h->mv_tuned = false;
+    return am::mobility_layout(h, h->cfg.precision == AM_MIXED ? 2 : 1, 0) ? AM_ERR_CUDA : AM_OK;
+}
+
+bool all_have_bodies(const am_handle* h) {
+    for (const auto& r : h->sys)
+        if (!r.has_bodies) return false;
+    return true;
+}
+
+// Copies the device state (positions, orientations, link vectors, which
+// steps advance) back into the records before they are rebuilt.
+int sync_records(am_handle* h) {
+    if (!h->committed || h->dirty) return AM_OK;
+    std::vector<double> q(3 * (size_t)h->M), th(4 * (size_t)h->M), dlp(3 * (size_t)h->P), dlq(3 * (size_t)h->P);
+    cudaStream_t s = h->stream;
+    CK(d2h(q.data(), h->d_q, q.size(), s));
+    CK(d2h(th.data(), h->d_theta, th.size(), s));
+    if (h->P) {
+        CK(d2h(dlp.data(), h->d_dlp, dlp.size(), s));
+        CK(d2h(dlq.data(), h->d_dlq, dlq.size(), s));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int sI = 0; sI < h->S; ++sI) {
+        am_sys_rec& r = h->sys[sI];
+        const int b0 = h->sys_body0[sI], l0 = h->sys_link0[sI];
+        std::copy(q.begin() + 3 * b0, q.begin() + 3 * (b0 + r.M), r.q.begin());
+        std::copy(th.begin() + 4 * b0, th.begin() + 4 * (b0 + r.M), r.theta.begin());
+        if (r.P) {
+            std::copy(dlp.begin() + 3 * l0, dlp.begin() + 3 * (l0 + r.P), r.dlp.begin());
+            std::copy(dlq.begin() + 3 * l0, dlq.begin() + 3 * (l0 + r.P), r.dlq.begin());
+        }
+    }
+    return AM_OK;
+}
+
+// Builds the device layout of all systems from the records.
+int commit(am_handle* h, const char* who) {
+    if (!h->dirty && h->committed) return AM_OK;
+    if (!all_have_bodies(h)) return set_err(h, AM_ERR_ARG, std::string(who) + ": some system has no bodies");
+    const int S = h->S;
+    h->sys_body0.assign(S, 0); h->sys_blob0.assign(S, 0); h->sys_link0.assign(S, 0); h->sys_asm0.assign(S, 0);
+    int M = 0, Nb = 0, NA = 0, P = 0, maxb = 0;
+    bool any_slip = false, any_active = false;
+    for (int sI = 0; sI < S; ++sI) {
+        const am_sys_rec& r = h->sys[sI];
+        h->sys_body0[sI] = M; h->sys_blob0[sI] = Nb; h->sys_link0[sI] = P; h->sys_asm0[sI] = NA;
+        M += r.M; Nb += r.Nb; NA += r.NA; P += r.P;
+        for (int p = 0; p < r.M; ++p) maxb = std::max(maxb, r.blob_off[p + 1] - r.blob_off[p]);
+        any_slip |= !r.slip.empty();
+        any_active |= !r.dlpd.empty();
+    }
+    std::vector<double> q, th, rho, F, slip, dlp, dlq, dlpd, dlqd;
+    std::vector<int> off(1, 0), asmb, bp, bq;
+    for (int sI = 0; sI < S; ++sI) {
+        const am_sys_rec& r = h->sys[sI];
+        q.insert(q.end(), r.q.begin(), r.q.end());
+        th.insert(th.end(), r.theta.begin(), r.theta.end());
+        rho.insert(rho.end(), r.rho.begin(), r.rho.end());
+        F.insert(F.end(), r.F.begin(), r.F.end());
+        if (any_slip) {
+            if (r.slip.empty()) slip.insert(slip.end(), 3 * (size_t)r.Nb, 0.0);
+            else slip.insert(slip.end(), r.slip.begin(), r.slip.end());
+        }
+        for (int p = 0; p < r.M; ++p) {
+            off.push_back(h->sys_blob0[sI] + r.blob_off[p + 1]);
+            asmb.push_back(h->sys_asm0[sI] + r.asm_of_body[p]);
+        }
+        for (int k = 0; k < r.P; ++k) {
+            bp.push_back(h->sys_body0[sI] + r.bp[k]);
+            bq.push_back(h->sys_body0[sI] + r.bq[k]);
+        }
+        dlp.insert(dlp.end(), r.dlp.begin(), r.dlp.end());
+        dlq.insert(dlq.end(), r.dlq.begin(), r.dlq.end());
+        if (r.dlpd.empty()) {
+            dlpd.insert(dlpd.end(), 3 * (size_t)r.P, 0.0);
+            dlqd.insert(dlqd.end(), 3 * (size_t)r.P, 0.0);
+        } else {
+            dlpd.insert(dlpd.end(), r.dlpd.begin(), r.dlpd.end());
+            dlqd.insert(dlqd.end(), r.dlqd.begin(), r.dlqd.end());
+        }
+    }
+    h->committed = false;
+    int rc = build_layout(h, M, Nb, NA, maxb, q.data(), th.data(), off.data(), rho.data(), F.data(),
+                          any_slip ? slip.data() : nullptr, asmb.data());
     if (rc) return rc;
+    rc = build_links(h, P, bp.data(), bq.data());
+    if (rc) return rc;
+    cudaStream_t s = h->stream;
+    CK(h2d(h->d_dlp, dlp.data(), dlp.size(), s));
+    CK(h2d(h->d_dlq, dlq.data(), dlq.size(), s));
+    CK(h2d(h->d_dlpd, dlpd.data(), dlpd.size(), s));
+    CK(h2d(h->d_dlqd, dlqd.data(), dlqd.size(), s));
+    CK(cudaStreamSynchronize(s));
+    h->active_links = any_active;
+    rc = build_system_maps(h);
+    if (rc) return set_err(h, rc, std::string(who) + ": device allocation failed");
     h->have_bodies = true;
+    h->committed = true;
+    h->dirty = false;
     am::launch_geometry(h);
     CK(cudaGetLastError());
     rc = device_flags_to_status(h, who);
     if (rc) {
         h->have_bodies = false;
+        h->committed = false;
+        h->dirty = true;
         return rc;
     }
+    return AM_OK;
+}
+
+int check_system(am_handle* h, int system, const char* who) {
+    if (system < 0 || system >= h->S) return set_err(h, AM_ERR_ARG, std::string(who) + ": system out of range");
+    return AM_OK;
+}
+
+}  // namespace
+
+extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const double* q, const double* theta,
+                                    const int* blob_offset, const double* rho, const double* F,
+                                    const double* slip, const int* asm_of_body) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_system(h, system, "am_set_bodies");
+    if (rc) return rc;
+    int NA = 0, maxb = 0;
+    rc = validate_bodies(h, M, q, theta, blob_offset, rho, F, asm_of_body, &NA, &maxb);
+    if (rc) return rc;
+    rc = sync_records(h);
+    if (rc) return rc;
+    am_sys_rec& r = h->sys[system];
+    const int Nb = blob_offset[M];
+    r.has_bodies = true;
+    r.M = M; r.Nb = Nb; r.NA = NA; r.P = 0;
+    r.q.assign(q, q + 3 * (size_t)M);
+    r.theta.assign(theta, theta + 4 * (size_t)M);
+    r.rho.assign(rho, rho + 3 * (size_t)Nb);
+    r.F.assign(F, F + 6 * (size_t)M);
+    if (slip) r.slip.assign(slip, slip + 3 * (size_t)Nb); else r.slip.clear();
+    r.blob_off.assign(blob_offset, blob_offset + M + 1);
+    r.asm_of_body.assign(asm_of_body, asm_of_body + M);
+    r.bp.clear(); r.bq.clear(); r.dlp.clear(); r.dlq.clear(); r.dlpd.clear(); r.dlqd.clear();
+    h->dirty = true;
+    h->have_bodies = false;
+    // one system: build the device layout now (errors surface here); several:
+    // on first use, so that loading S systems does not rebuild S times
+    if (h->S == 1) return commit(h, "am_set_bodies");
     return AM_OK;
 }
 
@@ -535,35 +756,58 @@ extern "C" AM_API int am_set_constraints(am_handle* h, int system, int P, const 
                                          const double* dlp, const double* dlq, const double* dlpd,
                                          const double* dlqd) {
     if (!h) return AM_ERR_ARG;
-    int rc = check_handle(h, "am_set_constraints", true);
+    int rc = check_system(h, system, "am_set_constraints");
     if (rc) return rc;
-    if (system != 0) return set_err(h, AM_ERR_ARG, "am_set_constraints: system out of range");
+    am_sys_rec& r = h->sys[system];
+    if (!r.has_bodies) return set_err(h, AM_ERR_ARG, "am_set_constraints: no bodies set for this system");
     if (P < 0 || (P > 0 && (!bp || !bq || !dlp || !dlq)))
         return set_err(h, AM_ERR_ARG, "am_set_constraints: n_links < 0 or NULL array");
     if ((dlpd == nullptr) != (dlqd == nullptr))
         return set_err(h, AM_ERR_ARG, "am_set_constraints: give both link derivatives or neither");
     for (int n = 0; n < P; ++n) {
-        if (bp[n] < 0 || bp[n] >= h->M || bq[n] < 0 || bq[n] >= h->M)
+        if (bp[n] < 0 || bp[n] >= r.M || bq[n] < 0 || bq[n] >= r.M)
             return set_err(h, AM_ERR_ARG, "am_set_constraints: body index out of range");
         if (bp[n] == bq[n]) return set_err(h, AM_ERR_ARG, "am_set_constraints: link joins a body to itself");
-        if (h->asm_of_body[bp[n]] != h->asm_of_body[bq[n]])
+        if (r.asm_of_body[bp[n]] != r.asm_of_body[bq[n]])
             return set_err(h, AM_ERR_ARG, "am_set_constraints: link joins two articulated bodies");
     }
-    const bool same = (P == h->P) && std::equal(bp, bp + P, h->bp.begin()) &&
-                      std::equal(bq, bq + P, h->bq.begin());
+    const bool same = h->committed && !h->dirty && P == r.P && std::equal(bp, bp + P, r.bp.begin()) &&
+                      std::equal(bq, bq + P, r.bq.begin());
     if (!same) {
-        rc = build_links(h, P, bp, bq);
+        rc = sync_records(h);
         if (rc) return rc;
     }
-    cudaStream_t s = h->stream;
-    CK(h2d(h->d_dlp, dlp, 3 * (size_t)P, s));
-    CK(h2d(h->d_dlq, dlq, 3 * (size_t)P, s));
-    h->active_links = dlpd != nullptr;
+    r.P = P;
+    r.bp.assign(bp, bp + P); r.bq.assign(bq, bq + P);
+    r.dlp.assign(dlp, dlp + 3 * (size_t)P); r.dlq.assign(dlq, dlq + 3 * (size_t)P);
     if (dlpd) {
-        CK(h2d(h->d_dlpd, dlpd, 3 * (size_t)P, s));
-        CK(h2d(h->d_dlqd, dlqd, 3 * (size_t)P, s));
+        r.dlpd.assign(dlpd, dlpd + 3 * (size_t)P);
+        r.dlqd.assign(dlqd, dlqd + 3 * (size_t)P);
+    } else {
+        r.dlpd.clear(); r.dlqd.clear();
+    }
+    if (!same) {
+        h->dirty = true;
+        h->have_bodies = false;
+        if (h->S == 1) return commit(h, "am_set_constraints");
+        return AM_OK;
+    }
+    // same connectivity: update this system's link vectors in place
+    cudaStream_t s = h->stream;
+    const size_t o = 3 * (size_t)h->sys_link0[system];
+    CK(h2d(h->d_dlp + o, dlp, 3 * (size_t)P, s));
+    CK(h2d(h->d_dlq + o, dlq, 3 * (size_t)P, s));
+    if (dlpd) {
+        CK(h2d(h->d_dlpd + o, dlpd, 3 * (size_t)P, s));
+        CK(h2d(h->d_dlqd + o, dlqd, 3 * (size_t)P, s));
+    } else if (P) {
+        CK(cudaMemsetAsync(h->d_dlpd + o, 0, 3 * (size_t)P * sizeof(double), s));
+        CK(cudaMemsetAsync(h->d_dlqd + o, 0, 3 * (size_t)P * sizeof(double), s));
     }
     CK(cudaStreamSynchronize(s));
+    bool any_active = false;
+    for (const auto& rr : h->sys) any_active |= !rr.dlpd.empty();
+    h->active_links = any_active;
     h->pc_valid = false;
     return AM_OK;
 }
@@ -571,18 +815,19 @@ extern "C" AM_API int am_set_constraints(am_handle* h, int system, int P, const 
 extern "C" AM_API int am_set_joints(am_handle* h, int system, int P, const int* bp, const int* bq,
                                     const double* joint) {
     if (!h) return AM_ERR_ARG;
-    int rc = check_handle(h, "am_set_joints", true);
+    int rc = check_system(h, system, "am_set_joints");
     if (rc) return rc;
+    am_sys_rec& r = h->sys[system];
+    if (!r.has_bodies) return set_err(h, AM_ERR_ARG, "am_set_joints: no bodies set for this system");
     if (P < 0 || (P > 0 && (!bp || !bq || !joint)))
         return set_err(h, AM_ERR_ARG, "am_set_joints: n_links < 0 or NULL array");
-    std::vector<double> q(3 * (size_t)h->M), th(4 * (size_t)h->M);
-    cudaStream_t s = h->stream;
-    CK(d2h(q.data(), h->d_q, q.size(), s));
-    CK(d2h(th.data(), h->d_theta, th.size(), s));
-    CK(cudaStreamSynchronize(s));
+    rc = sync_records(h);
+    if (rc) return rc;
+    const std::vector<double>& q = r.q;
+    const std::vector<double>& th = r.theta;
     std::vector<double> dlp(3 * (size_t)P), dlq(3 * (size_t)P);
     for (int n = 0; n < P; ++n) {
-        if (bp[n] < 0 || bp[n] >= h->M || bq[n] < 0 || bq[n] >= h->M)
+        if (bp[n] < 0 || bp[n] >= r.M || bq[n] < 0 || bq[n] >= r.M)
             return set_err(h, AM_ERR_ARG, "am_set_joints: body index out of range");
         double v[3];
         for (int a = 0; a < 3; ++a) v[a] = joint[3 * n + a] - q[3 * bp[n] + a];
@@ -676,10 +921,12 @@ extern "C" AM_API int am_get_bodies(am_handle* h, int system, double* q, double*
     if (!h) return AM_ERR_ARG;
     int rc = check_handle(h, "am_get_bodies", true);
     if (rc) return rc;
-    if (system != 0) return set_err(h, AM_ERR_ARG, "am_get_bodies: system out of range");
+    rc = check_system(h, system, "am_get_bodies");
+    if (rc) return rc;
     cudaStream_t s = h->stream;
-    if (q) CK(d2h(q, h->d_q, 3 * (size_t)h->M, s));
-    if (theta) CK(d2h(theta, h->d_theta, 4 * (size_t)h->M, s));
+    const size_t b0 = h->sys_body0[system], M = h->sys[system].M;
+    if (q) CK(d2h(q, h->d_q + 3 * b0, 3 * M, s));
+    if (theta) CK(d2h(theta, h->d_theta + 4 * b0, 4 * M, s));
     CK(cudaStreamSynchronize(s));
     return AM_OK;
 }
@@ -688,11 +935,14 @@ extern "C" AM_API int am_get_blobs(am_handle* h, int system, double* r) {
     if (!h) return AM_ERR_ARG;
     int rc = check_handle(h, "am_get_blobs", true);
     if (rc) return rc;
-    if (system != 0 || !r) return set_err(h, AM_ERR_ARG, "am_get_blobs: bad argument");
+    rc = check_system(h, system, "am_get_blobs");
+    if (rc) return rc;
+    if (!r) return set_err(h, AM_ERR_ARG, "am_get_blobs: NULL array");
     am::launch_geometry(h);
     CK(cudaGetLastError());
     am::take_flags(h);
-    CK(d2h(r, h->d_r3, 3 * (size_t)h->Nb, h->stream));
+    const size_t i0 = h->sys_blob0[system], Nb = h->sys[system].Nb;
+    CK(d2h(r, h->d_r3 + 3 * i0, 3 * Nb, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return AM_OK;
 }
@@ -706,6 +956,8 @@ extern "C" AM_API int am_apply_mobility(am_handle* h, const double* lam, double*
     am::launch_geometry(h);
     rc = device_flags_to_status(h, "am_apply_mobility");
     if (rc) return rc;
+    if (!h->mv_tuned && am::mobility_autotune(h))
+        return set_err(h, AM_ERR_CUDA, "am_apply_mobility: mobility autotuning failed");
     CK(h2d(h->d_t, lam, 3 * (size_t)h->Nb, s));
     am::mobility_apply(h, h->d_t, h->d_w, false);
     CK(cudaGetLastError());
@@ -723,6 +975,8 @@ extern "C" AM_API int am_apply_operator(am_handle* h, const double* y, double* A
     am::launch_geometry(h);
     rc = device_flags_to_status(h, "am_apply_operator");
     if (rc) return rc;
+    if (!h->mv_tuned && am::mobility_autotune(h))
+        return set_err(h, AM_ERR_CUDA, "am_apply_operator: mobility autotuning failed");
     CK(h2d(h->d_t, y, h->n, s));
     am::op_apply(h, h->d_t, h->d_w, false);
     CK(cudaGetLastError());

@@ -76,7 +76,9 @@ __global__ void k_rhs(int Nb, int M, int P, const double* __restrict__ slip,
 // out_U      = -K^T lambda + C^T phi
 // out_phi    = C U   (per link: u_p + omega_p x l_np - u_q - omega_q x l_nq)
 __global__ void k_op_epilogue(int Nb, int M, int P, int nblob_blocks, int nbody_blocks,
-                              const double* __restrict__ part, int splits,
+                              const double* __restrict__ part, const int* __restrict__ sys_of_blob,
+                              const int* __restrict__ sys_blob0, const int* __restrict__ sys_nb,
+                              const int* __restrict__ sys_nch, const long long* __restrict__ sys_poff,
                               const double* __restrict__ y, double* __restrict__ out,
                               const int* __restrict__ body_of_blob, const int* __restrict__ blob_off,
                               const double4_32a* __restrict__ d4, const int* __restrict__ bl_off,
@@ -92,10 +94,12 @@ __global__ void k_op_epilogue(int Nb, int M, int P, int nblob_blocks, int nbody_
     if (b < nblob_blocks) {
         const int i = b * blockDim.x + threadIdx.x;
         if (i >= Nb) return;
-        const size_t n3 = 3 * (size_t)Nb;
+        const int sy = sys_of_blob[i];
+        const size_t n3 = 3 * (size_t)sys_nb[sy];
+        const double* pb = part + sys_poff[sy] + 3 * (size_t)(i - sys_blob0[sy]);
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (int t = 0; t < splits; ++t) {
-            const double* pp = part + t * n3 + 3 * (size_t)i;
+        for (int t = 0; t < sys_nch[sy]; ++t) {
+            const double* pp = pb + t * n3;
             s0 += pp[0]; s1 += pp[1]; s2 += pp[2];
         }
         const int p = body_of_blob[i];
@@ -153,83 +157,9 @@ __global__ void k_op_epilogue(int Nb, int M, int P, int nblob_blocks, int nbody_
 }
 
 // --------------------------------------------------------- GMRES kernels ---
-// |w|^2 partial sums (no orthogonalisation)
-__global__ void __launch_bounds__(256)
-k_norm_part(const double* __restrict__ w, int n, double* __restrict__ npart) {
-    __shared__ double sh[64];
-    double nn = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        nn = fma(w[i], w[i], nn);
-    nn = block_sum(nn, sh);
-    if (threadIdx.x == 0) npart[blockIdx.x] = nn;
-}
-
-// r = b - Ax and per-block |r|^2
-__global__ void __launch_bounds__(256)
-k_residual(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
-           int n, double* __restrict__ npart) {
-    __shared__ double sh[64];
-    double nn = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double v = b[i] - Ax[i];
-        r[i] = v;
-        nn = fma(v, v, nn);
-    }
-    nn = block_sum(nn, sh);
-    if (threadIdx.x == 0) npart[blockIdx.x] = nn;
-}
-
-// scal[slot] = sqrt(sum npart); scal[slot+1] = 1/that (0 if zero)
-__global__ void k_norm_finish(const double* __restrict__ npart, int nb, double* __restrict__ scal,
-                              int slot) {
-    __shared__ double sh[64];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += npart[i];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) {
-        const double nrm = sqrt(s);
-        scal[slot] = nrm;
-        scal[slot + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
-    }
-}
-
-// xi = H(0:k,0:k)^-1 g(0:k)  (upper triangular back substitution)
-__global__ void k_hessenberg_solve(int k, const double* __restrict__ H, int ldh,
-                                   const double* __restrict__ g, double* __restrict__ xi) {
-    if (threadIdx.x != 0) return;
-    for (int i = k - 1; i >= 0; --i) {
-        double s = g[i];
-        for (int c = i + 1; c < k; ++c) s -= H[(size_t)c * ldh + i] * xi[c];
-        const double d = H[(size_t)i * ldh + i];
-        xi[i] = d != 0.0 ? s / d : 0.0;
-    }
-}
-
-// t = sum_{k<kk} xi_k V_k
-__global__ void k_combine(const double* __restrict__ V, size_t ldv, const double* __restrict__ xi,
-                          int kk, int n, double* __restrict__ t) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < kk; ++k) s = fma(xi[k], V[(size_t)k * ldv + i], s);
-        t[i] = s;
-    }
-}
-
-// y = a * x (a read from device memory), and optional g[0] = |.|
-__global__ void k_scale(const double* __restrict__ x, double* __restrict__ y, int n,
-                        const double* __restrict__ a) {
-    const double s = *a;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        y[i] = s * x[i];
-}
-
 __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int n, double a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         y[i] = fma(a, x[i], y[i]);
-}
-
-__global__ void k_init_g(double* __restrict__ g, int len, const double* __restrict__ scal, int slot) {
-    for (int i = threadIdx.x; i < len; i += blockDim.x) g[i] = (i == 0) ? scal[slot] : 0.0;
 }
 
 // zero the lambda and U blocks and put B - C U0 in the phi block: the
@@ -592,103 +522,264 @@ __global__ void k_store_col(const double* __restrict__ in, double* __restrict__ 
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) z[i] = in[i];
 }
 
-// part[k * nch + chunk] = <V_k, w> over chunk blockIdx.x, for the 8 basis
-// vectors k = 8 blockIdx.y + warp with k <= j (one warp per k)
+// ---- per-system (batched) GMRES kernels ----------------------------------
+// Unknowns of system s occupy three segments of the global vector (its
+// blobs' lambda, its bodies' U, its links' phi); the dot-product chunks never
+// straddle two systems and are listed system by system
+// (sys_chunk_off[s] .. sys_chunk_off[s+1]).
+
+// npart[c] = sum of v^2 over chunk c
 __global__ void __launch_bounds__(256)
-k_dots_dev(const double* __restrict__ V, size_t ldv, const double* __restrict__ w, int n, int chunk,
-           double* __restrict__ part, int nch, const ArnoldiCtrl* __restrict__ c) {
+k_chunk_sq(const double* __restrict__ v, const int* __restrict__ cs, const int* __restrict__ ce,
+           double* __restrict__ npart) {
+    __shared__ double sh[64];
+    const int c = blockIdx.x;
+    double a = 0.0;
+    for (int i = cs[c] + threadIdx.x; i < ce[c]; i += blockDim.x) a = fma(v[i], v[i], a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) npart[c] = a;
+}
+
+// r = b - Ax and npart[c] = sum of r^2 over chunk c
+__global__ void __launch_bounds__(256)
+k_chunk_resid(const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
+              const int* __restrict__ cs, const int* __restrict__ ce, double* __restrict__ npart) {
+    __shared__ double sh[64];
+    const int c = blockIdx.x;
+    double a = 0.0;
+    for (int i = cs[c] + threadIdx.x; i < ce[c]; i += blockDim.x) {
+        const double v = b[i] - Ax[i];
+        r[i] = v;
+        a = fma(v, v, a);
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) npart[c] = a;
+}
+
+// out[s] = sqrt(sum of the system's chunk partials)
+__global__ void k_sys_norm(const double* __restrict__ npart, const int* __restrict__ coff, int S,
+                           double* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double a = 0.0;
+    for (int c = coff[s]; c < coff[s + 1]; ++c) a += npart[c];
+    out[s] = sqrt(a);
+}
+
+// Start of a restart cycle, one block: per system the relative residual
+// beta_s / ||b_s||; systems above tol are active, with v_0 scale 1/beta_s,
+// g = (beta_s, 0, ...), absolute stop threshold tol ||b_s||.  red[0] = max
+// relative residual (NaN if any is not finite), red[1] = active count.
+__global__ void k_cycle_init(int S, int m, double tol, const double* __restrict__ beta,
+                             const double* __restrict__ bnorm, int* __restrict__ active,
+                             double* __restrict__ inv, double* __restrict__ g, int* __restrict__ kdone,
+                             double* __restrict__ tol_s, double* __restrict__ red) {
+    __shared__ double smax[256];
+    __shared__ int scnt[256];
+    __shared__ int sbad[256];
+    double mx = 0.0;
+    int cnt = 0, bad = 0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const double bn = bnorm[s], be = beta[s];
+        const double rel = bn > 0.0 ? be / bn : 0.0;
+        const bool finite = (rel == rel) && rel < 1e300;
+        const bool act = finite && bn > 0.0 && rel > tol;
+        active[s] = act ? 1 : 0;
+        inv[s] = act ? 1.0 / be : 0.0;
+        double* gs = g + (size_t)s * (m + 1);
+        gs[0] = act ? be : 0.0;
+        for (int k = 1; k <= m; ++k) gs[k] = 0.0;
+        kdone[s] = 0;
+        tol_s[s] = tol * bn;
+        if (finite) mx = fmax(mx, rel); else bad = 1;
+        cnt += act ? 1 : 0;
+    }
+    smax[threadIdx.x] = mx;
+    scnt[threadIdx.x] = cnt;
+    sbad[threadIdx.x] = bad;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+            scnt[threadIdx.x] += scnt[threadIdx.x + o];
+            sbad[threadIdx.x] |= sbad[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        red[0] = sbad[0] ? nan("") : smax[0];
+        red[1] = (double)scnt[0];
+    }
+}
+
+// v *= a[system of the element]
+__global__ void k_scale_sys(double* __restrict__ v, int n, const int* __restrict__ sys_of,
+                            const double* __restrict__ a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v[i] *= a[sys_of[i]];
+}
+
+// v = 0 on the elements of inactive systems
+__global__ void k_mask_sys(double* __restrict__ v, int n, const int* __restrict__ sys_of,
+                           const int* __restrict__ active) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (!active[sys_of[i]]) v[i] = 0.0;
+}
+
+// part[k * nchunks + c] = <V_k, w> over chunk c for k = 8 blockIdx.y + warp <= j
+__global__ void __launch_bounds__(256)
+k_chunk_dots(const double* __restrict__ V, size_t ldv, const double* __restrict__ w,
+             const int* __restrict__ cs, const int* __restrict__ ce, double* __restrict__ part,
+             int nchunks, const ArnoldiCtrl* __restrict__ c) {
     const int j = c->j;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k = blockIdx.y * 8 + wid;
     if (k > j) return;
     const int cb = blockIdx.x;
-    const int i0 = cb * chunk, i1 = min(n, i0 + chunk);
     const double* v = V + (size_t)k * ldv;
     double s = 0.0;
-    for (int i = i0 + lane; i < i1; i += 32) s = fma(v[i], w[i], s);
+    for (int i = cs[cb] + lane; i < ce[cb]; i += 32) s = fma(v[i], w[i], s);
     s = warp_sum(s);
-    if (lane == 0) part[(size_t)k * nch + cb] = s;
+    if (lane == 0) part[(size_t)k * nchunks + cb] = s;
 }
 
-__global__ void __launch_bounds__(256)
-k_orth_dev(const double* __restrict__ V, size_t ldv, double* __restrict__ w, int n,
-           const double* __restrict__ part, int nch, double* __restrict__ hcol, int accumulate,
-           double* __restrict__ npart, const ArnoldiCtrl* __restrict__ c) {
-    extern __shared__ double coef[];
-    __shared__ double sh[64];
+// coef[s][k] = sum over the system's chunks; hcol[s][k] = (hcol +) coef
+__global__ void k_sys_coef(const double* __restrict__ part, int nchunks, const int* __restrict__ coff,
+                           int m1, double* __restrict__ coef, double* __restrict__ hcol, int accumulate,
+                           const ArnoldiCtrl* __restrict__ c) {
+    const int s = blockIdx.x;
     const int jp1 = c->j + 1;
     for (int k = threadIdx.x; k < jp1; k += blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < nch; ++q) s += part[(size_t)k * nch + q];
-        coef[k] = s;
-        if (blockIdx.x == 0) hcol[k] = accumulate ? hcol[k] + s : s;
-    }
-    __syncthreads();
-    double nn = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double v = w[i];
-        for (int k = 0; k < jp1; ++k) v = fma(-coef[k], V[(size_t)k * ldv + i], v);
-        w[i] = v;
-        nn = fma(v, v, nn);
-    }
-    if (npart) {
-        nn = block_sum(nn, sh);
-        if (threadIdx.x == 0) npart[blockIdx.x] = nn;
+        double a = 0.0;
+        for (int q = coff[s]; q < coff[s + 1]; ++q) a += part[(size_t)k * nchunks + q];
+        coef[(size_t)s * m1 + k] = a;
+        double* hc = hcol + (size_t)s * m1 + k;
+        *hc = accumulate ? *hc + a : a;
     }
 }
 
-__global__ void k_arnoldi_finish_dev(const ArnoldiCtrl* __restrict__ c, const double* __restrict__ hcol,
-                                     const double* __restrict__ npart, int nb, double* __restrict__ H,
-                                     int ldh, double* __restrict__ cs, double* __restrict__ sn,
-                                     double* __restrict__ g, double* __restrict__ scal) {
-    __shared__ double sh[64];
+// w_i -= sum_{k <= j} coef[system of i][k] V_k,i
+__global__ void __launch_bounds__(256)
+k_orth_sys(const double* __restrict__ V, size_t ldv, double* __restrict__ w, int n,
+           const int* __restrict__ sys_of, const double* __restrict__ coef, int m1,
+           const ArnoldiCtrl* __restrict__ c) {
+    const int jp1 = c->j + 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double* cf = coef + (size_t)sys_of[i] * m1;
+        double v = w[i];
+        for (int k = 0; k < jp1; ++k) v = fma(-cf[k], V[(size_t)k * ldv + i], v);
+        w[i] = v;
+    }
+}
+
+// Per active system (one thread each): H column j, Givens rotations, the
+// residual estimate; a system stops (kdone = j + 1) when the estimate reaches
+// its threshold or the step breaks down.  inv[s] = 1/|w_s| (0 if stopped).
+__global__ void k_arnoldi_finish_sys(const ArnoldiCtrl* __restrict__ c, const double* __restrict__ hcol,
+                                     const double* __restrict__ npart, const int* __restrict__ coff, int S,
+                                     int m, double* __restrict__ H, double* __restrict__ cs,
+                                     double* __restrict__ sn, double* __restrict__ g, int* __restrict__ active,
+                                     int* __restrict__ kdone, const double* __restrict__ tol_s,
+                                     double* __restrict__ inv) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    if (!active[s]) { inv[s] = 0.0; return; }
     const int j = c->j;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += npart[i];
-    s = block_sum(s, sh);
-    if (threadIdx.x != 0) return;
-    const double nrm = sqrt(s);
-    double* h = H + (size_t)j * ldh;
-    for (int i = 0; i <= j; ++i) h[i] = hcol[i];
+    const int m1 = m + 1;
+    double a = 0.0;
+    for (int q = coff[s]; q < coff[s + 1]; ++q) a += npart[q];
+    const double nrm = sqrt(a);
+    double* h = H + ((size_t)s * m + j) * m1;
+    const double* hc = hcol + (size_t)s * m1;
+    double* css = cs + (size_t)s * m;
+    double* sns = sn + (size_t)s * m;
+    double* gs = g + (size_t)s * m1;
+    for (int i = 0; i <= j; ++i) h[i] = hc[i];
     h[j + 1] = nrm;
     for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        const double t = css[i] * h[i] + sns[i] * h[i + 1];
+        h[i + 1] = -sns[i] * h[i] + css[i] * h[i + 1];
         h[i] = t;
     }
     const double d = hypot(h[j], h[j + 1]);
     double cc = 1.0, sg = 0.0;
     if (d > 0.0) { cc = h[j] / d; sg = h[j + 1] / d; }
-    cs[j] = cc; sn[j] = sg;
+    css[j] = cc; sns[j] = sg;
     h[j] = d;
     h[j + 1] = 0.0;
-    g[j + 1] = -sg * g[j];
-    g[j] = cc * g[j];
-    scal[0] = fabs(g[j + 1]);
-    scal[1] = nrm;
-    scal[2] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    gs[j + 1] = -sg * gs[j];
+    gs[j] = cc * gs[j];
+    const double est = fabs(gs[j + 1]);
+    const bool stop = !(est > tol_s[s]) || nrm == 0.0;
+    inv[s] = (!stop && nrm > 0.0) ? 1.0 / nrm : 0.0;
+    if (stop) { active[s] = 0; kdone[s] = j + 1; }
 }
 
-// V[j+1] = w / |w|
-__global__ void k_scale_dev(const double* __restrict__ w, double* __restrict__ V, size_t ldv, int n,
-                            const double* __restrict__ scal, const ArnoldiCtrl* __restrict__ c) {
-    const double a = scal[2];
+// V[j+1] = w * inv[system]
+__global__ void k_next_basis(const double* __restrict__ w, double* __restrict__ V, size_t ldv, int n,
+                             const int* __restrict__ sys_of, const double* __restrict__ inv,
+                             const ArnoldiCtrl* __restrict__ c) {
     double* v = V + (size_t)(c->j + 1) * ldv;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = a * w[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v[i] = inv[sys_of[i]] * w[i];
 }
 
-// Advance j; stop on convergence of the residual estimate, breakdown, the
-// end of the cycle or the iteration budget.  Inside a graph WHILE node the
-// decision is the node's condition.
-__global__ void k_loop_ctrl(ArnoldiCtrl* c, const double* __restrict__ scal,
-                            cudaGraphConditionalHandle hc, int in_graph) {
-    const int j = c->j;
-    c->it += 1;
-    const double est = scal[0];
-    const bool stop = !(est > c->tol_abs) || scal[1] == 0.0 || j + 1 >= c->m || c->it >= c->budget;
-    c->j = j + 1;
-    c->stop = stop ? 1 : 0;
-    if (in_graph) cudaGraphSetConditional(hc, stop ? 0u : 1u);
+// Advance j; the cycle ends when no system is active, at the restart length
+// or at the step budget (still-active systems then close at j + 1).
+__global__ void k_loop_ctrl_sys(ArnoldiCtrl* c, int* __restrict__ active, int* __restrict__ kdone, int S,
+                                cudaGraphConditionalHandle hc, int in_graph) {
+    __shared__ int scnt[256];
+    __shared__ int s_stop;
+    const int j1 = c->j + 1;
+    int cnt = 0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) cnt += active[s];
+    scnt[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) scnt[threadIdx.x] += scnt[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_stop = (scnt[0] == 0 || j1 >= c->m || c->it + 1 >= c->budget) ? 1 : 0;
+    __syncthreads();
+    if (s_stop)
+        for (int s = threadIdx.x; s < S; s += blockDim.x)
+            if (active[s]) { kdone[s] = j1; active[s] = 0; }
+    if (threadIdx.x == 0) {
+        c->it += 1;
+        c->j = j1;
+        c->stop = s_stop;
+        if (in_graph) cudaGraphSetConditional(hc, s_stop ? 0u : 1u);
+    }
+}
+
+// xi_s = H_s(0:k, 0:k)^-1 g_s(0:k), k = kdone[s]  (one thread per system)
+__global__ void k_hess_solve_sys(const double* __restrict__ H, const double* __restrict__ g,
+                                 const int* __restrict__ kdone, double* __restrict__ xi, int S, int m) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int k = kdone[s], m1 = m + 1;
+    const double* Hs = H + (size_t)s * m * m1;
+    const double* gs = g + (size_t)s * m1;
+    double* xs = xi + (size_t)s * m1;
+    for (int i = k - 1; i >= 0; --i) {
+        double a = gs[i];
+        for (int q = i + 1; q < k; ++q) a -= Hs[(size_t)q * m1 + i] * xs[q];
+        const double d = Hs[(size_t)i * m1 + i];
+        xs[i] = d != 0.0 ? a / d : 0.0;
+    }
+}
+
+// t_i = sum_{k < kdone[s]} xi_s[k] Z_k,i with s the system of i
+__global__ void k_combine_sys(const double* __restrict__ Z, size_t ldv, const double* __restrict__ xi,
+                              const int* __restrict__ kdone, const int* __restrict__ sys_of, int n, int m1,
+                              double* __restrict__ t) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = sys_of[i];
+        const double* xs = xi + (size_t)s * m1;
+        double a = 0.0;
+        for (int k = 0; k < kdone[s]; ++k) a = fma(xs[k], Z[(size_t)k * ldv + i], a);
+        t[i] = a;
+    }
 }
 
 }  // namespace am
@@ -738,27 +829,25 @@ static void timing_mark(am_handle* h) {
 
 static void mobility_partial(am_handle* h, const double* lam, bool fp64) {
     timing_mark(h);
-    if (fp64 || h->cfg.precision == AM_FP64)
-        launch_rpy_partial_f64(h->d_r4, lam, h->d_mv, h->Nb, h->split, h->prm, h->cfg.wall, h->stream);
-    else
-        launch_rpy_partial_mixed(h->d_rhi, h->d_rlo, lam, h->d_mv, h->Nb, h->split, h->prm,
-                                 h->cfg.wall, h->stream);
+    launch_items(h, lam, fp64);
     timing_mark(h);
-    h->pairs += (long long)h->Nb * h->Nb;
+    long long pairs = 0;
+    for (const auto& r : h->sys) pairs += (long long)r.Nb * r.Nb;
+    h->pairs += pairs;
 }
 
 void mobility_apply(am_handle* h, const double* lam, double* u, bool fp64) {
     mobility_partial(h, lam, fp64);
-    launch_sum_partials(h->d_mv, u, h->Nb, h->split.splits, h->stream);
+    launch_sum_items(h, u);
 }
 
 void op_apply(am_handle* h, const double* y, double* out, bool fp64) {
     mobility_partial(h, y, fp64);
     const int nbb = nblk(h->Nb, 128), nbody = nblk(h->M, 4), nlink = nblk(h->P, 128);
     k_op_epilogue<<<nbb + nbody + nlink, 128, 0, h->stream>>>(
-        h->Nb, h->M, h->P, nbb, nbody, h->d_mv, h->split.splits, y, out, h->d_body_of_blob,
-        h->d_blob_off, h->d_d4, h->d_body_link_off, h->d_body_link_idx, h->d_lp, h->d_lq, h->d_bp,
-        h->d_bq);
+        h->Nb, h->M, h->P, nbb, nbody, h->d_mv, h->d_sys_of_blob, h->d_sys_blob0, h->d_sys_nb,
+        h->d_sys_nch, h->d_sys_poff, y, out, h->d_body_of_blob, h->d_blob_off, h->d_d4,
+        h->d_body_link_off, h->d_body_link_idx, h->d_lp, h->d_lq, h->d_bp, h->d_bq);
     count_launch();
 }
 
@@ -775,32 +864,37 @@ void project_constraints(am_handle* h, double* x) {
 
 static int red_blocks(int n) { return std::min(nblk(n, 256), 2 * num_sms()); }
 
-static double read_scal(am_handle* h, int count) {
+static void read_scal(am_handle* h, int count) {
     cudaMemcpyAsync(h->h_scal, h->d_scal, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     cudaStreamSynchronize(h->stream);
-    return h->h_scal[0];
 }
 
-// ||v||_2 into h_scal[0] (synchronous)
-static double norm2(am_handle* h, const double* v) {
-    const int nb = red_blocks(h->n);
-    k_norm_part<<<nb, 256, 0, h->stream>>>(v, h->n, h->d_npart);
-    k_norm_finish<<<1, 256, 0, h->stream>>>(h->d_npart, nb, h->d_scal, 0);
+// per-system 2-norms of v into out (S doubles, device)
+static void sys_norms(am_handle* h, const double* v, double* out) {
+    k_chunk_sq<<<h->nchunks, 256, 0, h->stream>>>(v, h->d_chunk_start, h->d_chunk_end, h->d_npart);
+    k_sys_norm<<<nblk(h->S, 128), 128, 0, h->stream>>>(h->d_npart, h->d_sys_chunk_off, h->S, out);
     count_launch(2);
-    return read_scal(h, 2);
 }
 
-// One Arnoldi step of flexible GMRES with the step index in device memory:
-// z = P^-1 V[j] (stored in Z[j]), w = A z, CGS2 against V[0..j], Givens
-// update, V[j+1] = w / |w|, then the loop control.
+// per-system residual r = b - A x (operator in FP64 or the handle's
+// precision) and its norms into out
+static void sys_residual(am_handle* h, const double* b, const double* x, double* r, double* out, bool fp64) {
+    op_apply(h, x, h->d_w, fp64);
+    k_chunk_resid<<<h->nchunks, 256, 0, h->stream>>>(b, h->d_w, r, h->d_chunk_start, h->d_chunk_end, h->d_npart);
+    k_sys_norm<<<nblk(h->S, 128), 128, 0, h->stream>>>(h->d_npart, h->d_sys_chunk_off, h->S, out);
+    count_launch(2);
+}
+
+// One Arnoldi step of flexible GMRES for every system at once, with the step
+// index in device memory: z = P^-1 V[j] (stored in Z[j]), w = A z, CGS2 with
+// per-system coefficients, per-system Givens updates and stopping,
+// V[j+1] = w / |w_s|, then the loop control.
 static void issue_arnoldi_step(am_handle* h, bool fp64, cudaGraphConditionalHandle hc, bool in_graph) {
     cudaStream_t s = h->stream;
-    const int n = h->n, m = h->restart;
+    const int n = h->n, m = h->restart, m1 = m + 1, S = h->S;
     const size_t ldv = (size_t)h->ldv;
     const int nb = red_blocks(n);
-    const int nch = std::max(1, std::min(64, nblk(n, 1024)));
-    const int chunk = nblk(n, nch);
-    const dim3 dgrid(nch, (m + 1 + 7) / 8);
+    const dim3 dgrid(h->nchunks, (m1 + 7) / 8);
     k_copy_col<<<nb, 256, 0, s>>>(h->d_V, ldv, h->d_vj, n, h->d_ctrl);
     count_launch();
     pc_apply(h, h->d_vj, h->d_zj);
@@ -808,17 +902,20 @@ static void issue_arnoldi_step(am_handle* h, bool fp64, cudaGraphConditionalHand
     count_launch();
     op_apply(h, h->d_zj, h->d_w, fp64);
     for (int pass = 0; pass < 2; ++pass) {
-        k_dots_dev<<<dgrid, 256, 0, s>>>(h->d_V, ldv, h->d_w, n, chunk, h->d_part, nch, h->d_ctrl);
-        k_orth_dev<<<nb, 256, (m + 1) * sizeof(double), s>>>(h->d_V, ldv, h->d_w, n, h->d_part, nch,
-                                                             h->d_coef, pass, pass ? h->d_npart : nullptr,
-                                                             h->d_ctrl);
-        count_launch(2);
+        k_chunk_dots<<<dgrid, 256, 0, s>>>(h->d_V, ldv, h->d_w, h->d_chunk_start, h->d_chunk_end, h->d_part,
+                                           h->nchunks, h->d_ctrl);
+        k_sys_coef<<<S, 64, 0, s>>>(h->d_part, h->nchunks, h->d_sys_chunk_off, m1, h->d_coefs, h->d_hcols,
+                                     pass, h->d_ctrl);
+        k_orth_sys<<<nb, 256, 0, s>>>(h->d_V, ldv, h->d_w, n, h->d_sys_of_elem, h->d_coefs, m1, h->d_ctrl);
+        count_launch(3);
     }
-    k_arnoldi_finish_dev<<<1, 256, 0, s>>>(h->d_ctrl, h->d_coef, h->d_npart, nb, h->d_Hm, m + 1, h->d_cs,
-                                           h->d_sn, h->d_g, h->d_scal);
-    k_scale_dev<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_scal, h->d_ctrl);
-    k_loop_ctrl<<<1, 1, 0, s>>>(h->d_ctrl, h->d_scal, hc, in_graph ? 1 : 0);
-    count_launch(3);
+    k_chunk_sq<<<h->nchunks, 256, 0, s>>>(h->d_w, h->d_chunk_start, h->d_chunk_end, h->d_npart);
+    k_arnoldi_finish_sys<<<nblk(S, 128), 128, 0, s>>>(h->d_ctrl, h->d_hcols, h->d_npart, h->d_sys_chunk_off, S,
+                                                       m, h->d_Hs, h->d_css, h->d_sns, h->d_gs, h->d_active,
+                                                       h->d_kdone, h->d_tol_s, h->d_inv_s);
+    k_next_basis<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s, h->d_ctrl);
+    k_loop_ctrl_sys<<<1, 256, 0, s>>>(h->d_ctrl, h->d_active, h->d_kdone, S, hc, in_graph ? 1 : 0);
+    count_launch(4);
 }
 
 // The graph of one Arnoldi cycle: a WHILE node whose body is one step,
@@ -875,44 +972,39 @@ static bool ensure_graph(am_handle* h, bool fp64) {
 }
 
 // Flexible GMRES(m) (right preconditioning, x = x0 + Z xi with the stored
-// z_j = P^-1 v_j, so a preconditioner applied in FP32 is allowed), CGS2, on
-// A x = rhs with the operator in FP64 (fp64) or in the handle's precision.
-// Each restart cycle runs on the device as one graph launch (WHILE node over
-// Arnoldi steps); with per-kernel timing on, the same steps are launched
-// from the host instead (event records cannot live in a graph loop).
-// Stops when the true relative residual (same operator) is <= tol or after
-// `budget` steps.  Returns the number of steps; *rel = final true residual.
+// z_j = P^-1 v_j, so a preconditioner applied in FP32 is allowed), CGS2, for
+// all systems of the handle at once: each system has its own Krylov basis
+// segment, Hessenberg matrix, Givens rotations and stopping test
+// ||b_s - A x_s|| <= tol ||b_s||; converged systems drop out.  The operator is
+// FP64 (fp64) or the handle's precision.  Each restart cycle runs on the
+// device as one graph launch (WHILE node over Arnoldi steps); with
+// per-kernel timing on, the same steps are launched from the host instead
+// (event records cannot live in a graph loop).  Returns the number of steps;
+// *rel = the largest final relative residual.
 static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp64, int budget,
                  double* rel, int* cycles) {
     cudaStream_t s = h->stream;
-    const int n = h->n;
-    const int m = h->restart;
+    const int n = h->n, m = h->restart, m1 = m + 1, S = h->S;
     const size_t ldv = (size_t)h->ldv;
     const int nb = red_blocks(n);
-    const double bnorm = norm2(h, rhs);
-    *rel = 0.0;
-    if (bnorm == 0.0) {
-        cudaMemsetAsync(x, 0, n * sizeof(double), s);
-        return 0;
-    }
+    sys_norms(h, rhs, h->d_bnorm_s);
     const bool use_graph = !h->timing && h->graphs_ok && ensure_graph(h, fp64);
     const int gi = fp64 ? 1 : 0;
     int it = 0;
+    *rel = 0.0;
     while (true) {
-        double* V0 = h->d_V;
-        op_apply(h, x, h->d_w, fp64);
-        k_residual<<<nb, 256, 0, s>>>(rhs, h->d_w, V0, n, h->d_npart);
-        k_norm_finish<<<1, 256, 0, s>>>(h->d_npart, nb, h->d_scal, 4);
-        count_launch(2);
-        read_scal(h, 6);
-        const double beta = h->h_scal[4];
-        *rel = beta / bnorm;
-        if (*rel <= tol || it >= budget || !(beta == beta)) break;
+        sys_residual(h, rhs, x, h->d_V, h->d_beta_s, fp64);
+        k_cycle_init<<<1, 256, 0, s>>>(S, m, tol, h->d_beta_s, h->d_bnorm_s, h->d_active, h->d_inv_s, h->d_gs,
+                                       h->d_kdone, h->d_tol_s, h->d_scal);
+        count_launch();
+        read_scal(h, 2);
+        *rel = h->h_scal[0];
+        const int n_active = (int)h->h_scal[1];
+        if (n_active == 0 || it >= budget || !(*rel == *rel)) break;
         ++*cycles;
-        k_scale<<<nb, 256, 0, s>>>(V0, V0, n, h->d_scal + 5);
-        k_init_g<<<1, 64, 0, s>>>(h->d_g, m + 1, h->d_scal, 4);
-        k_ctrl_init<<<1, 1, 0, s>>>(h->d_ctrl, budget - it, m, tol * bnorm);
-        count_launch(3);
+        k_scale_sys<<<nb, 256, 0, s>>>(h->d_V, n, h->d_sys_of_elem, h->d_inv_s);
+        k_ctrl_init<<<1, 1, 0, s>>>(h->d_ctrl, budget - it, m, 0.0);
+        count_launch(2);
         if (use_graph) {
             cudaGraphLaunch(h->gexec[gi], s);
             cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(ArnoldiCtrl), cudaMemcpyDeviceToHost, s);
@@ -926,10 +1018,9 @@ static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp
                 cudaStreamSynchronize(s);
             } while (!h->h_ctrl->stop);
         }
-        const int kdone = h->h_ctrl->j;
         it += h->h_ctrl->it;
-        k_hessenberg_solve<<<1, 32, 0, s>>>(kdone, h->d_Hm, m + 1, h->d_g, h->d_xi);
-        k_combine<<<nb, 256, 0, s>>>(h->d_Z, ldv, h->d_xi, kdone, n, h->d_t);
+        k_hess_solve_sys<<<nblk(S, 128), 128, 0, s>>>(h->d_Hs, h->d_gs, h->d_kdone, h->d_xis, S, m);
+        k_combine_sys<<<nb, 256, 0, s>>>(h->d_Z, ldv, h->d_xis, h->d_kdone, h->d_sys_of_elem, n, m1, h->d_t);
         k_axpy<<<nb, 256, 0, s>>>(x, h->d_t, n, 1.0);
         count_launch(3);
     }
@@ -944,19 +1035,25 @@ int solve(am_handle* h, am_step_stats* st) {
     if (h->cfg.precision == AM_FP64) {
         it = gmres(h, h->d_b, h->d_x, tol, true, budget, &rel, &cycles);
     } else {
-        // Iterative refinement: FP64 residual outside, mixed-precision
-        // GMRES for the correction inside.
+        // Iterative refinement per system: FP64 residual outside,
+        // mixed-precision GMRES for the correction inside (systems already
+        // at tol get a zero right-hand side and drop out).
         cudaStream_t s = h->stream;
         const int nb = red_blocks(h->n);
-        const double bnorm = norm2(h, h->d_b);
+        double* bn_out = h->d_sysred;           // ||b_s|| of the outer problem
+        double* be_out = h->d_sysred + h->S;    // ||b_s - A x_s|| (FP64 operator)
+        sys_norms(h, h->d_b, bn_out);
         for (int outer = 0; outer < 20; ++outer) {
-            op_apply(h, h->d_x, h->d_w, true);
-            k_residual<<<nb, 256, 0, s>>>(h->d_b, h->d_w, h->d_rir, h->n, h->d_npart);
-            k_norm_finish<<<1, 256, 0, s>>>(h->d_npart, nb, h->d_scal, 4);
-            count_launch(2);
-            read_scal(h, 6);
-            rel = bnorm > 0.0 ? h->h_scal[4] / bnorm : 0.0;
-            if (rel <= tol || it >= budget || !(rel == rel)) break;
+            sys_residual(h, h->d_b, h->d_x, h->d_rir, be_out, true);
+            k_cycle_init<<<1, 256, 0, s>>>(h->S, h->restart, tol, be_out, bn_out, h->d_active,
+                                           h->d_inv_s, h->d_gs, h->d_kdone, h->d_tol_s, h->d_scal);
+            count_launch();
+            read_scal(h, 2);
+            rel = h->h_scal[0];
+            const int n_active = (int)h->h_scal[1];
+            if (n_active == 0 || it >= budget || !(rel == rel)) break;
+            k_mask_sys<<<nb, 256, 0, s>>>(h->d_rir, h->n, h->d_sys_of_elem, h->d_active);
+            count_launch();
             const double tin = std::max(1e-6, 0.3 * tol / rel);
             cudaMemsetAsync(h->d_dx, 0, h->n * sizeof(double), s);
             double rin = 0.0;

@@ -27,6 +27,13 @@ int solve(am_handle* h, am_step_stats* st);
 // Euler update + reconstruction + correction (Sec. 4.3) from the solution
 // in d_x; writes the new q, theta into the handle.
 int advance(am_handle* h, double dt, am_step_stats* st);
+// Block-diagonal mobility product of all systems (rpy.cu): work items for
+// tpt targets per thread and source chunks (0 = automatic), their launch,
+// the sum of the partials, and the autotuner that picks (tpt, chunk).
+int mobility_layout(am_handle* h, int tpt, int chunk);
+void launch_items(am_handle* h, const double* lam, bool fp64);
+void launch_sum_items(am_handle* h, double* u);
+int mobility_autotune(am_handle* h);
 // Read and clear the device error flags.
 int take_flags(am_handle* h);
 

@@ -25,10 +25,12 @@
 // kernel adds the chunks.
 #include "am_internal.cuh"
 #include "rpy_pair.cuh"
+#include "ops.cuh"
 
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 namespace am {
 
@@ -331,3 +333,324 @@ extern "C" AM_API int am_flops_per_pair(int wall) {
 }
 
 extern "C" AM_API long long am_kernel_launches(void) { return am::g_launches.load(); }
+
+// ======================================================================
+// Block-diagonal product over the systems of a handle (batched form).
+// Work items (system, block of targets, chunk of sources) are pulled from an
+// atomic queue by a persistent grid sized to the resident blocks of all SMs;
+// items are ordered largest first.  The partial sums of system s, chunk c,
+// blob i go to part[poff_s + c * 3 N_s + 3 (i - blob0_s)].
+namespace am {
+
+struct MvItem {
+    int t0, t1;       // targets [t0, t1)
+    int j0, j1;       // sources [j0, j1)
+    int tbase, n3;    // first blob of the system, 3 N_s
+    long long pbase;  // poff_s + c * 3 N_s
+};
+
+template <bool WALL>
+__global__ void __launch_bounds__(kThreads)
+rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam,
+              double* __restrict__ part, const MvItem* __restrict__ items, int n_items,
+              int* __restrict__ counter, RpyK<double> k) {
+    __shared__ double4_32a sr[kTile];
+    __shared__ double sl[3 * kTile];
+    __shared__ int s_item;
+    for (int round = 0;; ++round) {
+        // first item = the block's own index (spread over the SMs as the
+        // blocks are), later ones from the queue
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(counter, 1);
+        __syncthreads();
+        const int itn = s_item;
+        if (itn >= n_items) break;
+        const MvItem m = items[itn];
+        // items built for two targets per thread span 2 x 128 targets
+        for (int tb = m.t0; tb < m.t1; tb += kThreads) {
+        const int i = tb + threadIdx.x;
+        double4_32a ri = (i < m.t1) ? r4[i] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
+        double ux = 0.0, uy = 0.0, uz = 0.0;
+        for (int jt = m.j0; jt < m.j1; jt += kTile) {
+            const int cnt = min(kTile, m.j1 - jt);
+            __syncthreads();
+            if (threadIdx.x < cnt) sr[threadIdx.x] = r4[jt + threadIdx.x];
+            for (int q = threadIdx.x; q < 3 * cnt; q += kThreads) sl[q] = lam[3 * (size_t)jt + q];
+            __syncthreads();
+#pragma unroll 2
+            for (int q = 0; q < cnt; ++q) {
+                const double4_32a rj = sr[q];
+                const double lx = sl[3 * q], ly = sl[3 * q + 1], lz = sl[3 * q + 2];
+                const double dx = ri.x - rj.x, dy = ri.y - rj.y;
+                pair_free<double>(dx, dy, ri.z - rj.z, lx, ly, lz, k, ux, uy, uz);
+                if (WALL) pair_image<double>(dx, dy, ri.z + rj.z, ri.z, rj.z, lx, ly, lz, k, ux, uy, uz);
+            }
+        }
+        if (i < m.t1) {
+            double* o = part + m.pbase + 3 * (size_t)(i - m.tbase);
+            o[0] = k.A1 * ux; o[1] = k.A1 * uy; o[2] = k.A1 * uz;
+        }
+        }
+    }
+}
+
+template <bool WALL, int TPT>
+__global__ void __launch_bounds__(kThreads, 4)
+rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
+                const double* __restrict__ lam, double* __restrict__ part,
+                const MvItem* __restrict__ items, int n_items, int* __restrict__ counter,
+                RpyK<float> k) {
+    __shared__ float4 sh[kTile];
+    __shared__ float4 so[kTile];
+    __shared__ float4 sl[kTile];
+    __shared__ int s_item;
+    for (int round = 0;; ++round) {
+        // first item = the block's own index (spread over the SMs as the
+        // blocks are), later ones from the queue
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(counter, 1);
+        __syncthreads();
+        const int itn = s_item;
+        if (itn >= n_items) break;
+        const MvItem m = items[itn];
+        float4 hi_i[TPT], lo_i[TPT];
+        float near2[TPT];
+        double U[TPT][3];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            const int i = m.t0 + t * kThreads + threadIdx.x;
+            hi_i[t] = (i < m.t1) ? hi[i] : make_float4(0.f, 0.f, 1.f, 0.f);
+            lo_i[t] = (i < m.t1) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float nr = 0.25f * fmaxf(fabsf(hi_i[t].x), fmaxf(fabsf(hi_i[t].y), fabsf(hi_i[t].z)));
+            near2[t] = nr * nr;
+            U[t][0] = U[t][1] = U[t][2] = 0.0;
+        }
+        for (int jt = m.j0; jt < m.j1; jt += kTile) {
+            const int cnt = min(kTile, m.j1 - jt);
+            __syncthreads();
+            if (threadIdx.x < cnt) {
+                const int j = jt + threadIdx.x;
+                sh[threadIdx.x] = hi[j];
+                so[threadIdx.x] = lo[j];
+                sl[threadIdx.x] = make_float4((float)lam[3 * (size_t)j], (float)lam[3 * (size_t)j + 1],
+                                              (float)lam[3 * (size_t)j + 2], 0.f);
+            }
+            __syncthreads();
+            float u[TPT][3];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) u[t][0] = u[t][1] = u[t][2] = 0.f;
+#pragma unroll 2
+            for (int q = 0; q < cnt; ++q) {
+                const float4 h = sh[q];
+                const float4 l = sl[q];
+#pragma unroll
+                for (int t = 0; t < TPT; ++t) {
+                    float dx = hi_i[t].x - h.x, dy = hi_i[t].y - h.y, dz = hi_i[t].z - h.z;
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (r2 < near2[t]) {
+                        const float4 o = so[q];
+                        dx += lo_i[t].x - o.x;
+                        dy += lo_i[t].y - o.y;
+                        dz += lo_i[t].z - o.z;
+                        r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    }
+                    pair_free_r2<float>(dx, dy, dz, r2, l.x, l.y, l.z, k, u[t][0], u[t][1], u[t][2]);
+                    if (WALL)
+                        pair_image<float>(dx, dy, hi_i[t].z + h.z, hi_i[t].z, h.z, l.x, l.y, l.z, k,
+                                          u[t][0], u[t][1], u[t][2]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                U[t][0] += (double)u[t][0];
+                U[t][1] += (double)u[t][1];
+                U[t][2] += (double)u[t][2];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            const int i = m.t0 + t * kThreads + threadIdx.x;
+            if (i < m.t1) {
+                double* o = part + m.pbase + 3 * (size_t)(i - m.tbase);
+                o[0] = k.A1 * U[t][0]; o[1] = k.A1 * U[t][1]; o[2] = k.A1 * U[t][2];
+            }
+        }
+    }
+}
+
+// u_i = sum over the chunks of i's system of the partial sums
+__global__ void k_sum_items(int Nb, const double* __restrict__ part, const int* __restrict__ sys_of_blob,
+                            const int* __restrict__ sys_blob0, const int* __restrict__ sys_nb,
+                            const int* __restrict__ sys_nch, const long long* __restrict__ sys_poff,
+                            double* __restrict__ u) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nb) return;
+    const int s = sys_of_blob[i];
+    const size_t n3 = 3 * (size_t)sys_nb[s];
+    const double* p = part + sys_poff[s] + 3 * (size_t)(i - sys_blob0[s]);
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int q = 0; q < sys_nch[s]; ++q) {
+        a += p[q * n3]; b += p[q * n3 + 1]; c += p[q * n3 + 2];
+    }
+    u[3 * (size_t)i] = a; u[3 * (size_t)i + 1] = b; u[3 * (size_t)i + 2] = c;
+}
+
+template <class F>
+static int resident_grid(F kernel) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0) != cudaSuccess || per <= 0)
+        per = 4;
+    return per * num_sms();
+}
+
+// Work items for tpt targets per thread and source chunks of `chunk` blobs
+// (0: choose so that the items fill the GPU).  Returns 0 on success.
+int mobility_layout(am_handle* h, int tpt, int chunk) {
+    const int S = h->S;
+    if (h->cfg.precision != AM_MIXED) tpt = 1;
+    if (chunk <= 0) {
+        // about 8 resident waves of items over all systems
+        long long pairs = 0;
+        for (int s = 0; s < S; ++s) pairs += (long long)h->sys[s].Nb * h->sys[s].Nb;
+        const long long want = 8LL * 4 * num_sms();
+        const long long per_item = std::max<long long>(pairs / want, (long long)kThreads * tpt * kTile);
+        chunk = (int)std::max<long long>(kTile, per_item / (kThreads * tpt) / kTile * kTile);
+    }
+    std::vector<MvItem> items;
+    std::vector<int> nch(S);
+    std::vector<long long> poff(S);
+    long long off = 0;
+    for (int s = 0; s < S; ++s) {
+        const int nb = h->sys[s].Nb, b0 = h->sys_blob0[s];
+        nch[s] = std::max(1, (nb + chunk - 1) / chunk);
+        poff[s] = off;
+        for (int c = 0; c < nch[s]; ++c) {
+            const int j0 = b0 + c * chunk, j1 = std::min(b0 + nb, j0 + chunk);
+            for (int t0 = b0; t0 < b0 + nb; t0 += kThreads * tpt) {
+                MvItem it;
+                it.t0 = t0; it.t1 = std::min(b0 + nb, t0 + kThreads * tpt);
+                it.j0 = j0; it.j1 = j1; it.tbase = b0; it.n3 = 3 * nb;
+                it.pbase = off + (long long)c * 3 * nb;
+                items.push_back(it);
+            }
+        }
+        off += (long long)nch[s] * 3 * nb;
+    }
+    std::stable_sort(items.begin(), items.end(), [](const MvItem& a, const MvItem& b) {
+        return (long long)(a.t1 - a.t0) * (a.j1 - a.j0) > (long long)(b.t1 - b.t0) * (b.j1 - b.j0);
+    });
+    cudaStream_t st = h->stream;
+    if (h->d_items) cudaFree(h->d_items);
+    h->d_items = nullptr;
+    if (h->d_mv) cudaFree(h->d_mv);
+    h->d_mv = nullptr;
+    if (cudaMalloc(&h->d_items, std::max<size_t>(items.size(), 1) * sizeof(MvItem)) != cudaSuccess) return 1;
+    if (cudaMalloc(reinterpret_cast<void**>(&h->d_mv), std::max<long long>(off, 1) * sizeof(double)) != cudaSuccess)
+        return 1;
+    if (cudaMemcpyAsync(h->d_items, items.data(), items.size() * sizeof(MvItem), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(h->d_sys_nch, nch.data(), S * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(h->d_sys_poff, poff.data(), S * sizeof(long long), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+        return 1;
+    cudaStreamSynchronize(st);
+    h->n_items = (int)items.size();
+    const int n_it = std::max(1, h->n_items);
+    h->mv_tpt = tpt;
+    h->mv_chunk = chunk;
+    h->mv_part_total = off;
+    if (h->cfg.precision == AM_MIXED) {
+        if (h->cfg.wall)
+            h->mv_grid = tpt == 2 ? resident_grid(rpy_items_mixed<true, 2>) : resident_grid(rpy_items_mixed<true, 1>);
+        else
+            h->mv_grid = tpt == 2 ? resident_grid(rpy_items_mixed<false, 2>) : resident_grid(rpy_items_mixed<false, 1>);
+    } else {
+        h->mv_grid = h->cfg.wall ? resident_grid(rpy_items_f64<true>) : resident_grid(rpy_items_f64<false>);
+    }
+    h->mv_grid64 = h->cfg.wall ? resident_grid(rpy_items_f64<true>) : resident_grid(rpy_items_f64<false>);
+    // never more blocks than items
+    h->mv_grid = std::min(h->mv_grid, n_it);
+    h->mv_grid64 = std::min(h->mv_grid64, n_it);
+    h->layout_gen++;
+    return 0;
+}
+
+// The partial sums of u = M lambda for all systems (FP64 or the handle's
+// precision); the queue counter is reset first.
+void launch_items(am_handle* h, const double* lam, bool fp64) {
+    cudaStream_t st = h->stream;
+    cudaMemsetAsync(h->d_item_counter, 0, sizeof(int), st);
+    const MvItem* items = static_cast<const MvItem*>(h->d_items);
+    if (fp64 || h->cfg.precision == AM_FP64) {
+        const RpyK<double> k = rpy_consts<double>(h->prm);
+        if (h->cfg.wall)
+            rpy_items_f64<true><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,
+                                                                  h->d_item_counter, k);
+        else
+            rpy_items_f64<false><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,
+                                                                   h->d_item_counter, k);
+    } else {
+        const RpyK<float> k = rpy_consts<float>(h->prm);
+#define AM_MIXED_ITEMS(W, T)                                                                             \
+    rpy_items_mixed<W, T><<<h->mv_grid, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items, \
+                                                           h->n_items, h->d_item_counter, k)
+        if (h->cfg.wall) {
+            if (h->mv_tpt == 2) AM_MIXED_ITEMS(true, 2); else AM_MIXED_ITEMS(true, 1);
+        } else {
+            if (h->mv_tpt == 2) AM_MIXED_ITEMS(false, 2); else AM_MIXED_ITEMS(false, 1);
+        }
+#undef AM_MIXED_ITEMS
+    }
+    count_launch();
+}
+
+void launch_sum_items(am_handle* h, double* u) {
+    if (h->Nb <= 0) return;
+    k_sum_items<<<(h->Nb + 255) / 256, 256, 0, h->stream>>>(h->Nb, h->d_mv, h->d_sys_of_blob, h->d_sys_blob0,
+                                                            h->d_sys_nb, h->d_sys_nch, h->d_sys_poff, u);
+    count_launch();
+}
+
+// Autotuner: times the handle's product for candidate (targets per thread,
+// source chunk) pairs on the current positions and keeps the fastest.
+int mobility_autotune(am_handle* h) {
+    std::vector<std::pair<int, int>> cand;
+    const bool mixed = h->cfg.precision == AM_MIXED;
+    long long maxnb = 0;
+    for (const auto& r : h->sys) maxnb = std::max<long long>(maxnb, r.Nb);
+    for (int tpt : (mixed ? std::vector<int>{1, 2} : std::vector<int>{1}))
+        for (int chunk : {0, 512, 1024, 2048, 4096, 8192})
+            if (chunk == 0 || chunk <= 2 * maxnb) cand.push_back({tpt, chunk});
+    cudaStream_t st = h->stream;
+    double* lam = nullptr;
+    if (cudaMalloc(&lam, 3 * (size_t)std::max(h->Nb, 1) * sizeof(double)) != cudaSuccess) return 1;
+    cudaMemsetAsync(lam, 0, 3 * (size_t)h->Nb * sizeof(double), st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::pair<int, int> pick = cand[0];
+    const bool timing = h->timing;
+    h->timing = false;
+    for (auto c : cand) {
+        if (mobility_layout(h, c.first, c.second)) continue;
+        launch_items(h, lam, false);  // warm-up
+        cudaEventRecord(e0, st);
+        launch_items(h, lam, false);
+        launch_items(h, lam, false);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; pick = c; }
+    }
+    h->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(lam);
+    cudaGetLastError();
+    h->mv_tuned = true;
+    return mobility_layout(h, pick.first, pick.second);
+}
+
+}  // namespace am

@@ -164,6 +164,36 @@ def diatom_colony(seed, n_rods=32, nx=40, ny=2, spacing=0.2, a=0.1,
                 joints=None, dl=dl, phases=phases)
 
 
+def batched_chains(seed, n_systems=256, lo=500, hi=20_000, a=0.1, eta=1.0):
+    """Independent free-space suspensions of chains (the batched form): blob
+    counts drawn log-uniform in [lo, hi] from the seed, rounded to whole
+    12-blob icosahedral bodies, bodies in chains of 8 (the last chain of a
+    suspension shorter) joined by ball joints, each suspension in a cube whose
+    side keeps the body density of chains_free_space (32 bodies in a cube of
+    side 10).  Returns a list of workload dicts."""
+    rng = np.random.default_rng(np.random.Philox(seed))
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n_systems))
+    out = []
+    for k, nb in enumerate(sizes):
+        M = max(2, int(round(nb / 12.0)))
+        n_chains = (M + 7) // 8
+        w = chains_free_space(seed * 100003 + k, n_chains=n_chains, bodies_per_chain=8, a=a,
+                              box=10.0 * (M / 32.0) ** (1.0 / 3.0), eta=eta)
+        # trim to exactly M bodies (drop the tail of the last chain)
+        keep = M
+        w["q"] = w["q"][:keep]
+        w["theta"] = w["theta"][:keep]
+        w["F"] = w["F"][:keep]
+        w["rho"] = w["rho"][:12 * keep]
+        w["blob_offset"] = w["blob_offset"][:keep + 1]
+        w["assembly"] = w["assembly"][:keep]
+        lk = (w["body_p"] < keep) & (w["body_q"] < keep)
+        w["body_p"], w["body_q"], w["joints"] = w["body_p"][lk], w["body_q"][lk], w["joints"][lk]
+        w["name"] = "batched_chains[%d]" % k
+        out.append(w)
+    return out
+
+
 def _fibonacci_ellipsoid(n, axes):
     """n quasi-uniform points on an ellipsoid (Fibonacci lattice on the unit
     sphere, stretched along the axes)."""

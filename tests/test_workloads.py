@@ -56,3 +56,16 @@ def test_seeds_are_reproducible():
     assert np.array_equal(a["q"], b["q"]) and np.array_equal(a["F"], b["F"])
     c = W.chains_free_space(6)
     assert not np.array_equal(a["q"], c["q"])
+
+
+def test_batched_chains_sizes():
+    ws = W.batched_chains(1)
+    nb = np.array([W.counts(w)[0] for w in ws])
+    assert len(ws) == 256
+    assert nb.min() >= 500 - 12 and nb.max() <= 20_000 + 12
+    assert np.all(nb % 12 == 0)
+    # log-uniform: the median is near the geometric mean of the bounds
+    assert 2000 < np.median(nb) < 5000
+    for w in ws[:5]:
+        S = System(w)
+        assert np.abs(constraint_g(S.q, S.theta, S.dl_p, S.dl_q, S.bp, S.bq)).max() < 1e-13
