@@ -15,8 +15,17 @@ Features of body p, in the body frame of p (FEAT = 128 values):
                                         block-diagonal solution P~^-1 b
         log(blobs of p) / 5             1 value
   and zeros up to 128; L = 4.
-Target: the body-frame correction from the block-diagonal velocity to the
-solved one, R_p^T (U_p - U_pc,p) (6 values, padded to OUT = 8).
+Target: the background flow of the body.  The solution satisfies
+M lambda - K U = u_s; its block-diagonal part M~ lambda (blobs of the same
+body only) is what the body's own forces do, so u_ext = (M - M~) lambda is
+the flow the other bodies induce at its blobs.  Its target is the body-frame
+fit of u_ext by NFLOW = 29 flows on the body-frame blob offsets rho
+(translation 3, rotation 3, traceless symmetric strain 5, quadratic 18, see
+flow_basis): the coefficients c_p minimising |B_p c - R_p^T u_ext,p|^2 +
+eps |c|^2 with eps = RIDGE tr(B_p^T B_p) / NFLOW, zero padded to OUT = 32.
+The initial guess solves the block-diagonal problem with the predicted flow
+moved to the right-hand side: x0 = P~^-1 (u_s - u_fit, -F, B), u_fit at
+blob i of body p = R_p B_p(rho_i) c_p.
 
 MLP (DEPTH = 3 hidden layers of WIDTH = 256, ReLU):
   a0 = (x - mu) / sd;  a_l = relu(a_{l-1} W_l^T + b_l), l = 1..3;
@@ -31,7 +40,9 @@ import numpy as np
 from .kinematics import rotation_matrix, quat_mul
 
 FEAT = 128
-OUT = 8
+OUT = 32
+NFLOW = 29
+RIDGE = 1e-6
 WIDTH = 256
 DEPTH = 3
 KNN = 16
@@ -72,14 +83,76 @@ def features(q, theta, F, blob_offset, U_pc, system_of_body, wall):
     return X
 
 
-def targets(theta, U, U_pc):
-    """(M, OUT) body-frame corrections R_p^T (U_p - U_pc,p), zero padded."""
+# monomials of the quadratic flows, in column order
+_QUAD = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+
+def flow_basis(rho):
+    """(3n, NFLOW) body-frame flows at the offsets rho (n, 3); row 3i + c is
+    velocity component c at blob i.  Columns: e_k (k = 0..2); e_k x rho
+    (k = 0..2); E rho for the strains E01, E02, E12 (symmetric unit
+    off-diagonal pairs), diag(1, -1, 0), diag(1, 0, -1); then for each
+    component c and monomial (i, j) in _QUAD the flow rho_i rho_j e_c."""
+    rho = np.asarray(rho, float)
+    n = len(rho)
+    B = np.zeros((n, 3, NFLOW))
+    for k in range(3):
+        B[:, k, k] = 1.0
+        e = np.zeros(3)
+        e[k] = 1.0
+        B[:, :, 3 + k] = np.cross(e, rho)
+    strains = []
+    for (i, j) in ((0, 1), (0, 2), (1, 2)):
+        E = np.zeros((3, 3))
+        E[i, j] = E[j, i] = 1.0
+        strains.append(E)
+    strains.append(np.diag([1.0, -1.0, 0.0]))
+    strains.append(np.diag([1.0, 0.0, -1.0]))
+    for k, E in enumerate(strains):
+        B[:, :, 6 + k] = rho @ E.T
+    for c in range(3):
+        for m, (i, j) in enumerate(_QUAD):
+            B[:, c, 11 + 6 * c + m] = rho[:, i] * rho[:, j]
+    return B.reshape(3 * n, NFLOW)
+
+
+def background_flow(M_dense, lam, blob_offset):
+    """u_ext = (M - M~) lambda: the full mobility product minus the blocks of
+    blobs of the same body."""
+    lam = np.asarray(lam, float).ravel()
+    u = M_dense @ lam
+    off = np.asarray(blob_offset)
+    for p in range(len(off) - 1):
+        s = slice(3 * off[p], 3 * off[p + 1])
+        u[s] -= M_dense[s, s] @ lam[s]
+    return u
+
+
+def flow_targets(theta, rho, blob_offset, u_ext, ridge=RIDGE):
+    """(M, OUT) ridge fits of the body-frame background flow (module
+    docstring), zero padded."""
     R = rotation_matrix(np.asarray(theta, float))
-    dU = (np.asarray(U, float) - np.asarray(U_pc, float)).reshape(-1, 6)
-    T = np.zeros((len(dU), OUT))
-    T[:, :3] = np.einsum("nba,nb->na", R, dU[:, :3])
-    T[:, 3:6] = np.einsum("nba,nb->na", R, dU[:, 3:])
+    off = np.asarray(blob_offset)
+    u = np.asarray(u_ext, float).reshape(-1, 3)
+    T = np.zeros((len(off) - 1, OUT))
+    for p in range(len(off) - 1):
+        B = flow_basis(np.asarray(rho)[off[p]:off[p + 1]])
+        ub = (u[off[p]:off[p + 1]] @ R[p]).ravel()  # rows R_p^T u_i
+        G = B.T @ B
+        eps = ridge * np.trace(G) / NFLOW
+        T[p, :NFLOW] = np.linalg.solve(G + eps * np.eye(NFLOW), B.T @ ub)
     return T
+
+
+def flow_field(theta, rho, blob_offset, C):
+    """(Nb, 3) lab-frame flow u_fit of the coefficients C (M, >= NFLOW)."""
+    R = rotation_matrix(np.asarray(theta, float))
+    off = np.asarray(blob_offset)
+    out = np.zeros((off[-1], 3))
+    for p in range(len(off) - 1):
+        B = flow_basis(np.asarray(rho)[off[p]:off[p + 1]])
+        out[off[p]:off[p + 1]] = (B @ np.asarray(C, float)[p, :NFLOW]).reshape(-1, 3) @ R[p].T
+    return out
 
 
 def shapes():
