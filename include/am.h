@@ -70,7 +70,9 @@ typedef struct {
     double blob_radius;  /* a (> 0), the same for every blob                */
     int    wall;         /* 0: free space; 1: no-slip wall at z = 0         */
     int    precision;    /* AM_FP64 or AM_MIXED                             */
-    int    n_systems;    /* independent suspensions in the handle (1)       */
+    int    n_systems;    /* independent suspensions S in the handle
+                            (1..65536; 0 -> 1), each with its own
+                            bodies, links and GMRES state               */
     double tol;          /* GMRES stop: ||b - A y||_2 <= tol ||b||_2        */
     int    restart;      /* GMRES restart length m (1..200); 0 -> 50        */
     int    max_iter;     /* total GMRES iterations cap; 0 -> 500            */
@@ -95,11 +97,23 @@ typedef struct {
     double ms_gmres;        /* device time: GMRES                            */
     double ms_update;       /* device time: Euler update, reconstruction,
                                correction                                    */
+    int    learned_systems; /* systems whose initial guess came from the
+                               learned model (am_set_learned)                */
+    double rel_residual0;   /* true ||b - A y0||_2 / ||b||_2 of the initial
+                               guess (max over systems)                      */
 } am_step_stats;
 
 /* Create a solver handle.  cfg is copied.  Errors: AM_ERR_ARG for eta <= 0,
- * blob_radius <= 0, wall not 0/1, unknown precision, n_systems != 1,
- * tol <= 0 or restart/max_iter out of range; AM_ERR_CUDA. */
+ * blob_radius <= 0, wall not 0/1, unknown precision, n_systems outside
+ * 1..65536, tol <= 0 or restart/max_iter out of range; AM_ERR_CUDA.
+ *
+ * Several systems (n_systems = S > 1): every system is set separately
+ * (am_set_bodies/am_set_constraints with its index) and the device layout is
+ * built once all have bodies.  Every solve handles all systems at once, each
+ * with its own GMRES (own Krylov basis, Givens rotations and stopping test on
+ * its own ||b_s||); rel_residual and iteration counts in am_step_stats are
+ * the maxima over systems.  Outputs and the link vectors of am_solve_step
+ * are the systems' arrays concatenated in system order. */
 AM_API int am_create(const am_config* cfg, am_handle** out);
 
 /* Set the bodies of system `system` (0 <= system < n_systems) at the
@@ -259,6 +273,79 @@ AM_API int am_alu_peak(int fp64, double* flops);
 
 /* Kernels launched by this library in this process so far. */
 AM_API long long am_kernel_launches(void);
+
+/* ---- learned initial guess ----------------------------------------------
+ * The paper has no learned component.  These calls add an initial guess for
+ * cold starts (am_solve, and the first am_solve_step) predicted per body by
+ * a small network from its neighbourhood:
+ *   features of body p (AM_MLP_FEAT floats), in its body frame: for the 16
+ *     nearest other bodies k of its system (by |q_k - q_p| rounded to 1e-8,
+ *     ties by lower body index; zeros when fewer), R_p^T (q_k - q_p) / 4 and
+ *     the relative quaternion theta_p^* theta_k with s >= 0 (7 floats each);
+ *     then q_p,z / 4 (0 in free space), R_p^T f_p, R_p^T tau_p, the
+ *     body-frame (u, omega) of the block-diagonal solution P~^-1 b (Sec.
+ *     3.1), log(blobs of p) / 5; the far flow R_p^T u_far(q_p) and its
+ *     body-frame gradient (central differences of step 0.5 along the body
+ *     axes, row-major), u_far being the flow of point forces at the
+ *     tracking points of the bodies of the other articulated bodies of the
+ *     system, each the sum of its blob forces in P~^-1 b, through the blob
+ *     pair tensor (free or wall; FP32 pair terms); zeros;
+ *   target (AM_MLP_OUT floats): the background flow of the body, i.e.
+ *     u_ext = (M - M~) lambda at its blobs (what the other bodies' forces
+ *     induce there; M~ keeps only blob pairs of the same body), fitted in
+ *     the body frame by 29 flows on the body-frame offsets rho: e_k,
+ *     e_k x rho, E rho for the strains E01, E02, E12, diag(1,-1,0),
+ *     diag(1,0,-1), and rho_i rho_j e_c for c = 0..2, (i,j) = 00, 01, 02,
+ *     11, 12, 22; ridge 1e-6 tr(B^T B) / 29; 3 zeros;
+ *   network: (x - mu) / sd, three ReLU layers of 256, a linear layer to 32,
+ *     times sd_out.  Parameters flat in the order W1, b1, ..., W4, b4 (W
+ *     row-major, outputs x inputs), AM_MLP_PARAMS floats.
+ * Training runs in FP32 on the GPU (mini-batch Adam on the mean squared
+ * error of the normalised output); the solver evaluates the network with
+ * BF16 operands and FP32 accumulation on the tensor cores.  The guess is the
+ * block-diagonal solve with the predicted flow moved to the right-hand side,
+ * x0 = P~^-1 (u_s - u_fit, -F, B), which satisfies C U = B. */
+#define AM_MLP_FEAT 144
+#define AM_MLP_OUT 32
+#define AM_MLP_PARAMS 176928
+typedef struct am_mlp am_mlp;
+
+/* New network with He-initialised weights from `seed`, zero biases,
+ * mu = 0, sd = sd_out = 1; all its work runs on `stream` (cudaStream_t or
+ * NULL).  Errors: AM_ERR_ARG, AM_ERR_CUDA. */
+AM_API int am_mlp_create(unsigned long long seed, void* stream, am_mlp** out);
+AM_API void am_mlp_destroy(am_mlp* m);
+AM_API int am_mlp_num_params(void);
+/* Parameters to / from host (AM_MLP_PARAMS floats). */
+AM_API int am_mlp_get_params(am_mlp* m, float* params);
+AM_API int am_mlp_set_params(am_mlp* m, const float* params);
+/* Input normalisation mu, sd (AM_MLP_FEAT each, sd > 0) and output scale
+ * sd_out (AM_MLP_OUT, > 0). */
+AM_API int am_mlp_set_norm(am_mlp* m, const float* mu, const float* sd, const float* sd_out);
+/* FP32 loss and its gradient over n samples X (n x FEAT), T (n x OUT):
+ * loss = mean over samples and outputs of (y_n - T / sd_out)^2, y_n the
+ * network output before the sd_out scale; grad: AM_MLP_PARAMS floats (NULL
+ * to skip).  For checking the training kernels. */
+AM_API int am_mlp_loss_grad(am_mlp* m, const float* X, const float* T, int n, double* loss,
+                            float* grad);
+/* `epochs` passes of mini-batch Adam (beta 0.9, 0.999, eps 1e-8, learning
+ * rate lr) over n samples, shuffled each epoch from `seed`; *final_loss (or
+ * NULL) receives the mean batch loss of the last epoch. */
+AM_API int am_mlp_train(am_mlp* m, const float* X, const float* T, int n, int epochs, int batch,
+                        double lr, unsigned long long seed, double* final_loss);
+/* Predictions Y (n x OUT, scaled by sd_out) of X (n x FEAT): bf16 = 1 the
+ * tensor-core path the solver uses, 0 the FP32 training path. */
+AM_API int am_mlp_predict(am_mlp* m, const float* X, int n, int bf16, float* Y);
+/* Features X (M x FEAT) of all bodies of all systems at the current pose
+ * and, when T is not NULL, the targets T (M x OUT) of the solution of the
+ * last am_solve (same pose; one FP64 mobility product).  Errors:
+ * AM_ERR_ARG (no bodies), AM_ERR_CUDA. */
+AM_API int am_learned_features(am_handle* h, float* X, float* T);
+/* Use `model` (NULL: none) for the initial guess of cold starts.  check != 0:
+ * per system, keep P~^-1 b where its residual is smaller than the learned
+ * guess's (two extra operator products).  The handle does not own the
+ * model; keep it alive while it is set. */
+AM_API int am_set_learned(am_handle* h, am_mlp* model, int check);
 
 /* Destroy a handle and free its device memory (NULL is a no-op). */
 AM_API void am_destroy(am_handle* h);

@@ -14,7 +14,18 @@ Features of body p, in the body frame of p (FEAT = 128 values):
         R_p^T u_pc, R_p^T omega_pc      6 values: body velocity of the
                                         block-diagonal solution P~^-1 b
         log(blobs of p) / 5             1 value
-  and zeros up to 128; L = 4.
+        R_p^T u_far(q_p)                3 values: far flow (below)
+        J, row-major                    9 values: its body-frame gradient
+                                        by central differences along the
+                                        body axes, J_cj = (R_p^T (u_far(q_p
+                                        + h R_p e_j) - u_far(q_p - h R_p
+                                        e_j)))_c / 2h, h = 0.5
+  and zeros up to 144; L = 4.  The far flow is the flow of point forces at
+  the tracking points of the bodies of the other articulated bodies of the
+  system: u_far(x) = sum_k M(x, q_k) f_k over bodies k of the same system
+  and another articulated body, M the blob pair tensor (free or wall) with
+  the blob radius, f_k the sum over k's blobs of the blob forces of the
+  block-diagonal solution P~^-1 b.
 Target: the background flow of the body.  The solution satisfies
 M lambda - K U = u_s; its block-diagonal part M~ lambda (blobs of the same
 body only) is what the body's own forces do, so u_ext = (M - M~) lambda is
@@ -38,8 +49,9 @@ Parameters are flattened in the order W1, b1, W2, b2, W3, b3, W4, b4
 import numpy as np
 
 from .kinematics import rotation_matrix, quat_mul
+from .mobility import pair_tensor
 
-FEAT = 128
+FEAT = 144
 OUT = 32
 NFLOW = 29
 RIDGE = 1e-6
@@ -47,10 +59,38 @@ WIDTH = 256
 DEPTH = 3
 KNN = 16
 LSCALE = 4.0
+FAR_H = 0.5
 
 
-def features(q, theta, F, blob_offset, U_pc, system_of_body, wall):
-    """(M, FEAT) features of every body (see module docstring)."""
+def far_flow(q, theta, f, system_of_body, assembly, a, eta, wall):
+    """Body-frame far flow R_p^T u_far(q_p) (M, 3) and its body-frame
+    central-difference gradient J (M, 3, 3), J[p, c, j] = d u_c / d x_j
+    along body axis j (module docstring)."""
+    q = np.asarray(q, float)
+    R = rotation_matrix(np.asarray(theta, float))
+    f = np.asarray(f, float).reshape(-1, 3)
+    sysb = np.asarray(system_of_body)
+    asm = np.asarray(assembly)
+    M = len(q)
+    u = np.zeros((M, 7, 3))
+    for p in range(M):
+        src = np.nonzero((sysb == sysb[p]) & (asm != asm[p]))[0]
+        if len(src) == 0:
+            continue
+        steps = np.zeros((7, 3))
+        for j in range(3):
+            steps[1 + 2 * j] = FAR_H * R[p][:, j]
+            steps[2 + 2 * j] = -FAR_H * R[p][:, j]
+        x = q[p] + steps  # (7, 3) evaluation points
+        T = pair_tensor(x[:, None, :], q[src][None, :, :], a, eta, wall)  # (7, S, 3, 3)
+        u[p] = np.einsum("esab,sb->ea", T, f[src]) @ R[p]  # rows R_p^T u
+    J = np.stack([(u[:, 1 + 2 * j] - u[:, 2 + 2 * j]) / (2 * FAR_H) for j in range(3)], axis=2)
+    return u[:, 0], J
+
+
+def features(q, theta, F, blob_offset, U_pc, system_of_body, wall, lam_pc, assembly, a, eta):
+    """(M, FEAT) features of every body (see module docstring); lam_pc
+    (3Nb) are the blob forces of the block-diagonal solution."""
     q = np.asarray(q, float)
     theta = np.asarray(theta, float)
     F = np.asarray(F, float).reshape(-1, 6)
@@ -80,6 +120,13 @@ def features(q, theta, F, blob_offset, U_pc, system_of_body, wall):
         X[p, base + 7:base + 10] = R[p].T @ U_pc[p, :3]
         X[p, base + 10:base + 13] = R[p].T @ U_pc[p, 3:]
         X[p, base + 13] = np.log(nblob[p]) / 5.0
+    off = np.asarray(blob_offset)
+    lam = np.asarray(lam_pc, float).reshape(-1, 3)
+    f = np.stack([lam[off[k]:off[k + 1]].sum(axis=0) for k in range(M)]) if M else np.zeros((0, 3))
+    u, J = far_flow(q, theta, f, system_of_body, assembly, a, eta, wall)
+    fb = 7 * KNN + 14
+    X[:, fb:fb + 3] = u
+    X[:, fb + 3:fb + 12] = J.reshape(M, 9)
     return X
 
 

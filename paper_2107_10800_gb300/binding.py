@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libam.so")
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 _vp = ctypes.c_void_p
+_fp = ctypes.POINTER(ctypes.c_float)
 
 
 class Config(ctypes.Structure):
@@ -41,7 +42,8 @@ class StepStats(ctypes.Structure):
                 ("g2_before", ctypes.c_double), ("g2_after", ctypes.c_double),
                 ("corr_iterations", ctypes.c_int), ("pairs", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_int), ("ms_precond", ctypes.c_double),
-                ("ms_gmres", ctypes.c_double), ("ms_update", ctypes.c_double)]
+                ("ms_gmres", ctypes.c_double), ("ms_update", ctypes.c_double),
+                ("learned_systems", ctypes.c_int), ("rel_residual0", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,6 +72,18 @@ SIGNATURES = {
     "am_kernel_launches": (ctypes.c_longlong, []),
     "am_mobility_timing": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "am_alu_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
+    "am_mlp_create": (ctypes.c_int, [ctypes.c_ulonglong, _vp, ctypes.POINTER(_vp)]),
+    "am_mlp_destroy": (None, [_vp]),
+    "am_mlp_num_params": (ctypes.c_int, []),
+    "am_mlp_get_params": (ctypes.c_int, [_vp, _fp]),
+    "am_mlp_set_params": (ctypes.c_int, [_vp, _fp]),
+    "am_mlp_set_norm": (ctypes.c_int, [_vp, _fp, _fp, _fp]),
+    "am_mlp_loss_grad": (ctypes.c_int, [_vp, _fp, _fp, ctypes.c_int, _dp, _fp]),
+    "am_mlp_train": (ctypes.c_int, [_vp, _fp, _fp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_ulonglong, _dp]),
+    "am_mlp_predict": (ctypes.c_int, [_vp, _fp, ctypes.c_int, ctypes.c_int, _fp]),
+    "am_learned_features": (ctypes.c_int, [_vp, _fp, _fp]),
+    "am_set_learned": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "am_destroy": (None, [_vp]),
     "am_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -264,6 +278,23 @@ class Solver:
         self._check(lib().am_apply_precond(self.h, rp, op))
         return o
 
+    def learned_features(self, targets=False):
+        """Features (M x 144) of all bodies at the current pose and, with
+        targets=True, the background-flow targets (M x 32) of the last
+        solve's solution."""
+        X = np.empty((self.M, MLP_FEAT), dtype=np.float32)
+        T = np.empty((self.M, MLP_OUT), dtype=np.float32) if targets else None
+        rc = lib().am_learned_features(self.h, X.ctypes.data_as(_fp),
+                                       T.ctypes.data_as(_fp) if targets else None)
+        self._check(rc)
+        return (X, T) if targets else X
+
+    def set_learned(self, model, check=True):
+        """Use `model` (an Mlp, or None) for the initial guess of cold starts."""
+        self._mlp = model  # keep it alive while the handle uses it
+        rc = lib().am_set_learned(self.h, model.m if model is not None else None, 1 if check else 0)
+        self._check(rc)
+
     def mobility_timing(self, enable):
         """(total ms, launches) of the all-pairs kernel recorded so far;
         enable=True clears and starts recording, False stops."""
@@ -301,6 +332,93 @@ class Solver:
         for k, w in enumerate(ws):
             s.load(w, k, t)
         return s
+
+
+MLP_FEAT = 144
+MLP_OUT = 32
+
+
+def _f32(a, shape=None):
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and arr.shape != shape:
+        arr = arr.reshape(shape)
+    return arr, arr.ctypes.data_as(_fp)
+
+
+class Mlp:
+    """The learned initial-guess network of the library (am_mlp_*)."""
+
+    def __init__(self, seed=0, stream=None):
+        m = _vp()
+        rc = lib().am_mlp_create(seed, stream, ctypes.byref(m))
+        if rc != AM_OK:
+            raise AmError(rc, lib().am_last_error(None).decode())
+        self.m = m
+        self.n_params = int(lib().am_mlp_num_params())
+
+    def _check(self, rc):
+        if rc != AM_OK:
+            raise AmError(rc, lib().am_last_error(None).decode())
+
+    def close(self):
+        if self.m:
+            lib().am_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        p = np.empty(self.n_params, dtype=np.float32)
+        self._check(lib().am_mlp_get_params(self.m, p.ctypes.data_as(_fp)))
+        return p
+
+    def set_params(self, p):
+        arr, ptr = _f32(np.ravel(p))
+        if arr.size != self.n_params:
+            raise ValueError("expected %d parameters" % self.n_params)
+        self._check(lib().am_mlp_set_params(self.m, ptr))
+
+    def set_norm(self, mu, sd, sd_out):
+        a, pa = _f32(np.ravel(mu))
+        b, pb = _f32(np.ravel(sd))
+        c, pc = _f32(np.ravel(sd_out))
+        if a.size != MLP_FEAT or b.size != MLP_FEAT or c.size != MLP_OUT:
+            raise ValueError("mu, sd: 144 values; sd_out: 32")
+        self._check(lib().am_mlp_set_norm(self.m, pa, pb, pc))
+
+    def loss_grad(self, X, T):
+        x, px = _f32(X)
+        t, pt = _f32(T)
+        n = x.shape[0]
+        if x.shape != (n, MLP_FEAT) or t.shape != (n, MLP_OUT):
+            raise ValueError("X: n x 144, T: n x 32")
+        loss = ctypes.c_double()
+        g = np.empty(self.n_params, dtype=np.float32)
+        self._check(lib().am_mlp_loss_grad(self.m, px, pt, n, ctypes.byref(loss), g.ctypes.data_as(_fp)))
+        return loss.value, g
+
+    def train(self, X, T, epochs, batch=256, lr=1e-3, seed=0):
+        x, px = _f32(X)
+        t, pt = _f32(T)
+        n = x.shape[0]
+        if x.shape != (n, MLP_FEAT) or t.shape != (n, MLP_OUT):
+            raise ValueError("X: n x 144, T: n x 32")
+        loss = ctypes.c_double()
+        self._check(lib().am_mlp_train(self.m, px, pt, n, epochs, batch, lr, seed, ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, X, bf16=True):
+        x, px = _f32(X)
+        n = x.shape[0]
+        if x.shape != (n, MLP_FEAT):
+            raise ValueError("X: n x 144")
+        Y = np.empty((n, MLP_OUT), dtype=np.float32)
+        self._check(lib().am_mlp_predict(self.m, px, n, 1 if bf16 else 0, Y.ctypes.data_as(_fp)))
+        return Y
 
 
 def rpy_matvec_ptr(d_r, d_lam, d_u, n, eta, a, wall, precision, d_work, work_bytes, stream=None):

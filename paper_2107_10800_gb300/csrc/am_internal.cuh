@@ -131,6 +131,7 @@ struct am_handle {
     int *d_chunk_start = nullptr, *d_chunk_end = nullptr, *d_sys_chunk_off = nullptr;
     int nchunks = 0;
     int* d_sys_of_blob = nullptr;                 // Nb
+    int* d_sys_body_off = nullptr;                // S + 1: first body of each system
     int *d_sys_blob0 = nullptr, *d_sys_nb = nullptr, *d_sys_nch = nullptr;
     long long* d_sys_poff = nullptr;
     // batched GMRES scalars (per system)
@@ -233,6 +234,10 @@ struct am_handle {
     long long body_pairs[2] = {0, 0};
     long long layout_gen = 0;
     bool graphs_ok = true;
+
+    // learned initial guess of cold starts (am_set_learned; not owned)
+    am_mlp* mlp = nullptr;
+    bool mlp_check = true;
 
     // per-launch timing of the all-pairs kernel (am_mobility_timing)
     bool timing = false;

@@ -131,7 +131,7 @@ void free_solver(am_handle* h) {
     h->layout_gen++;
     dfree(&h->d_Hm); dfree(&h->d_cs); dfree(&h->d_sn); dfree(&h->d_g); dfree(&h->d_coef);
     dfree(&h->d_xi); dfree(&h->d_part); dfree(&h->d_npart);
-    dfree(&h->d_sys_of_elem); dfree(&h->d_sys_of_blob); dfree(&h->d_chunk_start); dfree(&h->d_chunk_end);
+    dfree(&h->d_sys_of_elem); dfree(&h->d_sys_of_blob); dfree(&h->d_sys_body_off); dfree(&h->d_chunk_start); dfree(&h->d_chunk_end);
     dfree(&h->d_sys_chunk_off); dfree(&h->d_Hs); dfree(&h->d_css); dfree(&h->d_sns); dfree(&h->d_gs);
     dfree(&h->d_coefs); dfree(&h->d_xis); dfree(&h->d_hcols); dfree(&h->d_bnorm_s); dfree(&h->d_beta_s);
     dfree(&h->d_inv_s); dfree(&h->d_tol_s); dfree(&h->d_sysred); dfree(&h->d_active); dfree(&h->d_kdone);
@@ -354,6 +354,13 @@ int prepare(am_handle* h, const char* who, bool warm, am_step_stats* st) {
     if (warm && h->have_warm) {
         CK(cudaMemcpyAsync(h->d_x, h->d_xprev, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         am::project_constraints(h, h->d_x);
+    } else if (h->mlp) {
+        // learned guess; with the check, systems where P~^-1 b (left in
+        // d_dx) has the smaller residual keep P~^-1 b
+        if (am::learned_x0(h, h->d_x))
+            return set_err(h, AM_ERR_CUDA, std::string(who) + ": learned initial guess failed");
+        int kept = h->mlp_check ? am::pick_initial(h, h->d_x, h->d_dx) : 0;
+        if (st) st->learned_systems = h->S - kept;
     } else {
         am::pc_apply(h, h->d_b, h->d_x);
     }
@@ -589,8 +596,10 @@ int build_system_maps(am_handle* h) {
     CK(dalloc(&h->d_active, S)); CK(dalloc(&h->d_kdone, S));
     CK(dalloc(&h->d_part, (size_t)(m + 1) * std::max(1, h->nchunks)));
     CK(dalloc(&h->d_npart, std::max(h->nchunks, 4 * am::num_sms() + 64)));
-    std::vector<int> b0(S), nb(S);
-    for (int sI = 0; sI < S; ++sI) { b0[sI] = h->sys_blob0[sI]; nb[sI] = h->sys[sI].Nb; }
+    std::vector<int> b0(S), nb(S), bo(S + 1, h->M);
+    for (int sI = 0; sI < S; ++sI) { b0[sI] = h->sys_blob0[sI]; nb[sI] = h->sys[sI].Nb; bo[sI] = h->sys_body0[sI]; }
+    CK(dalloc(&h->d_sys_body_off, S + 1));
+    CK(h2d(h->d_sys_body_off, bo.data(), S + 1, st));
     CK(dalloc(&h->d_sys_blob0, S)); CK(dalloc(&h->d_sys_nb, S));
     CK(dalloc(&h->d_sys_nch, S)); CK(dalloc(&h->d_sys_poff, S));
     CK(dalloc(&h->d_item_counter, 1));
@@ -860,6 +869,27 @@ extern "C" AM_API int am_solve(am_handle* h, am_step_stats* stats, double* U, do
     if (stats) *stats = st;
     if (rc == AM_ERR_NOT_CONVERGED) set_err(h, rc, "am_solve: GMRES did not reach the tolerance");
     return rc;
+}
+
+extern "C" AM_API int am_learned_features(am_handle* h, float* X, float* T) {
+    if (!h) return AM_ERR_ARG;
+    if (!X) return set_err(h, AM_ERR_ARG, "am_learned_features: NULL feature array");
+    int rc = check_handle(h, "am_learned_features", true);
+    if (rc) return rc;
+    am::launch_geometry(h);
+    am::pc_build(h);
+    CK(cudaGetLastError());
+    rc = device_flags_to_status(h, "am_learned_features");
+    if (rc) return rc;
+    if (am::learned_features(h, X, T)) return set_err(h, AM_ERR_CUDA, "am_learned_features: kernel failed");
+    return AM_OK;
+}
+
+extern "C" AM_API int am_set_learned(am_handle* h, am_mlp* model, int check) {
+    if (!h) return AM_ERR_ARG;
+    h->mlp = model;
+    h->mlp_check = check != 0;
+    return AM_OK;
 }
 
 extern "C" AM_API int am_solve_step(am_handle* h, double t, double dt, const double* dlp_next,

@@ -885,6 +885,39 @@ static void sys_residual(am_handle* h, const double* b, const double* x, double*
     count_launch(2);
 }
 
+// x <- xalt in every system whose residual is smaller with xalt; counts
+// the systems that switched into *nsw
+__global__ void k_pick_sys(double* __restrict__ x, const double* __restrict__ xalt, int n,
+                           const int* __restrict__ sys_of, const double* __restrict__ rx,
+                           const double* __restrict__ ralt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = sys_of[i];
+        if (ralt[s] < rx[s]) x[i] = xalt[i];
+    }
+}
+
+__global__ void k_count_pick(int S, const double* __restrict__ rx, const double* __restrict__ ralt,
+                             double* __restrict__ out) {
+    __shared__ double sh[64];
+    double c = 0.0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) c += (ralt[s] < rx[s]) ? 1.0 : 0.0;
+    c = block_sum(c, sh);
+    if (threadIdx.x == 0) out[0] = c;
+}
+
+int pick_initial(am_handle* h, double* x, const double* xalt) {
+    const int S = h->S;
+    double* rx = h->d_sysred + 2 * (size_t)S;
+    double* ra = h->d_sysred + 3 * (size_t)S;
+    sys_residual(h, h->d_b, x, h->d_rir, rx, false);
+    sys_residual(h, h->d_b, xalt, h->d_rir, ra, false);
+    k_pick_sys<<<red_blocks(h->n), 256, 0, h->stream>>>(x, xalt, h->n, h->d_sys_of_elem, rx, ra);
+    k_count_pick<<<1, 256, 0, h->stream>>>(S, rx, ra, h->d_scal);
+    count_launch(2);
+    read_scal(h, 1);
+    return (int)h->h_scal[0];
+}
+
 // One Arnoldi step of flexible GMRES for every system at once, with the step
 // index in device memory: z = P^-1 V[j] (stored in Z[j]), w = A z, CGS2 with
 // per-system coefficients, per-system Givens updates and stopping,
@@ -982,7 +1015,7 @@ static bool ensure_graph(am_handle* h, bool fp64) {
 // (event records cannot live in a graph loop).  Returns the number of steps;
 // *rel = the largest final relative residual.
 static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp64, int budget,
-                 double* rel, int* cycles) {
+                 double* rel, int* cycles, double* rel0 = nullptr) {
     cudaStream_t s = h->stream;
     const int n = h->n, m = h->restart, m1 = m + 1, S = h->S;
     const size_t ldv = (size_t)h->ldv;
@@ -992,6 +1025,7 @@ static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp
     const int gi = fp64 ? 1 : 0;
     int it = 0;
     *rel = 0.0;
+    bool first = true;
     while (true) {
         sys_residual(h, rhs, x, h->d_V, h->d_beta_s, fp64);
         k_cycle_init<<<1, 256, 0, s>>>(S, m, tol, h->d_beta_s, h->d_bnorm_s, h->d_active, h->d_inv_s, h->d_gs,
@@ -999,6 +1033,8 @@ static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp
         count_launch();
         read_scal(h, 2);
         *rel = h->h_scal[0];
+        if (first && rel0) *rel0 = *rel;
+        first = false;
         const int n_active = (int)h->h_scal[1];
         if (n_active == 0 || it >= budget || !(*rel == *rel)) break;
         ++*cycles;
@@ -1033,7 +1069,7 @@ int solve(am_handle* h, am_step_stats* st) {
     int cycles = 0, it = 0;
     double rel = 0.0;
     if (h->cfg.precision == AM_FP64) {
-        it = gmres(h, h->d_b, h->d_x, tol, true, budget, &rel, &cycles);
+        it = gmres(h, h->d_b, h->d_x, tol, true, budget, &rel, &cycles, &st->rel_residual0);
     } else {
         // Iterative refinement per system: FP64 residual outside,
         // mixed-precision GMRES for the correction inside (systems already
@@ -1050,6 +1086,7 @@ int solve(am_handle* h, am_step_stats* st) {
             count_launch();
             read_scal(h, 2);
             rel = h->h_scal[0];
+            if (outer == 0) st->rel_residual0 = rel;
             const int n_active = (int)h->h_scal[1];
             if (n_active == 0 || it >= budget || !(rel == rel)) break;
             k_mask_sys<<<nb, 256, 0, s>>>(h->d_rir, h->n, h->d_sys_of_elem, h->d_active);

@@ -34,6 +34,16 @@ int mobility_layout(am_handle* h, int tpt, int chunk);
 void launch_items(am_handle* h, const double* lam, bool fp64);
 void launch_sum_items(am_handle* h, double* u);
 int mobility_autotune(am_handle* h);
+// Per system, replace x by xalt where xalt has the smaller residual
+// |b - A x| (operator in the handle's precision); returns how many systems
+// took xalt.  Uses d_w, d_rir and the upper half of d_sysred.
+int pick_initial(am_handle* h, double* x, const double* xalt);
+// Learned initial guess (mlp.cu): x = P~^-1 (b - predicted background
+// flow), with x_pc = P~^-1 b left in d_dx; uses d_rir.
+int learned_x0(am_handle* h, double* x);
+// Features (and background-flow targets of the solution in d_x) of all
+// bodies to host X, T; uses d_dx and d_w.
+int learned_features(am_handle* h, float* X, float* T);
 // Read and clear the device error flags.
 int take_flags(am_handle* h);
 

@@ -78,3 +78,21 @@ def test_matvec_argument_checks(L):
 def test_null_handle_is_rejected(L):
     assert L.am_solve(None, None, None, None, None) == binding.AM_ERR_ARG
     L.am_destroy(None)
+
+
+def test_learned_constants_match_oracle(L):
+    from oracle import mlp as om
+    text = open(os.path.join(ROOT, "include", "am.h")).read()
+    consts = dict(re.findall(r"#define (AM_MLP_\w+) (\d+)", text))
+    assert int(consts["AM_MLP_FEAT"]) == om.FEAT == binding.MLP_FEAT
+    assert int(consts["AM_MLP_OUT"]) == om.OUT == binding.MLP_OUT
+    assert int(consts["AM_MLP_PARAMS"]) == om.n_params() == L.am_mlp_num_params()
+
+
+def test_learned_argument_checks(L):
+    assert L.am_set_learned(None, None, 1) == binding.AM_ERR_ARG
+    assert L.am_learned_features(None, None, None) == binding.AM_ERR_ARG
+    assert L.am_mlp_create(0, None, None) == binding.AM_ERR_ARG
+    assert L.am_mlp_get_params(None, None) == binding.AM_ERR_ARG
+    assert L.am_mlp_train(None, None, None, 0, 1, 1, 1e-3, 0, None) == binding.AM_ERR_ARG
+    L.am_mlp_destroy(None)

@@ -32,9 +32,14 @@ def test_gradient_matches_finite_differences():
 def test_features_rigid_motion_invariant():
     w = W.chains_free_space(2)
     M = len(w["q"])
-    U = np.random.default_rng(2).standard_normal((M, 6))
+    Nb = w["blob_offset"][-1]
+    rng = np.random.default_rng(2)
+    U = rng.standard_normal((M, 6))
+    lam = rng.standard_normal((Nb, 3))
     sysb = np.zeros(M, int)
-    X0 = mlp.features(w["q"], w["theta"], w["F"], w["blob_offset"], U, sysb, 0)
+    X0 = mlp.features(w["q"], w["theta"], w["F"], w["blob_offset"], U, sysb, 0, lam, w["assembly"],
+                      0.1, 1.0)
+    assert np.abs(X0[:, 126:138]).max() > 0  # four chains: far flow present
     # rotate and translate everything rigidly (forces, velocities with it)
     rot = quat_from_rotvec(np.array([0.3, -0.7, 0.2]))
     Rr = rotation_matrix(rot)
@@ -42,21 +47,46 @@ def test_features_rigid_motion_invariant():
     th2 = quat_mul(np.broadcast_to(rot, w["theta"].shape), w["theta"])
     F2 = np.concatenate([w["F"][:, :3] @ Rr.T, w["F"][:, 3:] @ Rr.T], axis=1)
     U2 = np.concatenate([U[:, :3] @ Rr.T, U[:, 3:] @ Rr.T], axis=1)
-    X2 = mlp.features(q2, th2, F2, w["blob_offset"], U2, sysb, 0)
+    X2 = mlp.features(q2, th2, F2, w["blob_offset"], U2, sysb, 0, lam @ Rr.T, w["assembly"], 0.1, 1.0)
     assert np.abs(X0 - X2).max() < 1e-12
+
+
+def test_far_flow_is_the_oseen_flow_of_other_assemblies():
+    # one body far from a forced body of another articulated body: u_far is
+    # the Oseen flow of the force and J its gradient (to O(a^2/r^2) and the
+    # O(h^2/r^2) of the central difference); bodies of the same articulated
+    # body do not count
+    q = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [60.0, -20.0, 30.0]])
+    f = np.array([[0.0, 0.0, 0.0], [3.0, 1.0, -2.0], [1.0, -2.0, 0.5]])
+    th = np.tile([1.0, 0.0, 0.0, 0.0], (3, 1))  # body frames = lab frame
+    u, J = mlp.far_flow(q, th, f, np.zeros(3, int), np.array([0, 0, 1]), 0.1, 1.0, 0)
+
+    def oseen(d, g):
+        r = np.linalg.norm(d)
+        return (g + d * (d @ g) / r ** 2) / (8 * np.pi * r)
+
+    d = q[0] - q[2]
+    assert np.allclose(u[0], oseen(d, f[2]), rtol=1e-5)
+    # analytic gradient of the Oseen flow by a fine difference of the formula
+    Jo = np.stack([(oseen(d + 1e-6 * e, f[2]) - oseen(d - 1e-6 * e, f[2])) / 2e-6 for e in np.eye(3)], axis=1)
+    assert np.abs(J[0] - Jo).max() < 1e-3 * np.abs(Jo).max()
+    # body 2 feels bodies 0 and 1, body 1 only body 2
+    assert np.allclose(u[1], oseen(q[1] - q[2], f[2]), rtol=1e-5)
+    assert np.allclose(u[2], oseen(q[2] - q[0], f[0]) + oseen(q[2] - q[1], f[1]), rtol=1e-5)
 
 
 def test_features_layout():
     w = W.chains_free_space(3, n_chains=1, bodies_per_chain=3)
     M = len(w["q"])
     X = mlp.features(w["q"], np.tile([1.0, 0, 0, 0], (M, 1)), w["F"], w["blob_offset"],
-                     np.zeros((M, 6)), np.zeros(M, int), 0)
+                     np.zeros((M, 6)), np.zeros(M, int), 0, np.ones((36, 3)), w["assembly"], 0.1, 1.0)
     # identity orientations: relative quaternions are the identity
     assert np.allclose(X[:, 3:7][:, 0], 1.0) and np.allclose(X[:, 3:7][:, 1:], 0.0)
-    # two other bodies, 14 empty slots, then the scalar block
+    # two other bodies, 14 empty slots, then the scalar block; one chain:
+    # no far flow; zeros to the end
     assert np.all(X[:, 14:7 * 16] == 0.0)
     assert np.allclose(X[:, 7 * 16 + 13], np.log(12) / 5)
-    assert np.all(X[:, 7 * 16 + 14:] == 0.0)
+    assert np.all(X[:, 7 * 16 + 14:] == 0.0) and X.shape[1] == 144
     # nearest first
     d1 = np.linalg.norm(X[:, 0:3], axis=1)
     d2 = np.linalg.norm(X[:, 7:10], axis=1)
