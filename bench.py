@@ -213,6 +213,42 @@ def matvec_at_scale(torch, binding, W, stream, fp32_peak, fp64_peak):
     return out
 
 
+def products_compared(binding, W, fp32_peak, fp64_peak, n=60_000):
+    """The three pair arithmetics of the solver on the same blobs (the first
+    n blobs of the bacteria suspension, as single-blob bodies of one
+    handle): FP64, double-float (the mixed solver's outer residual) and
+    mixed FP32.  Kernel time from CUDA events around each launch of the
+    all-pairs kernel (am_mobility_timing), second call of each."""
+    w = W.bacteria_wall(1)
+    s = binding.Solver.from_workload(w, precision="mixed")
+    r = s.blobs()[:n]
+    s.close()
+    s = binding.Solver(eta=w["eta"], a=w["a"], wall=1, precision="mixed")
+    th = np.tile([1.0, 0.0, 0.0, 0.0], (n, 1))
+    s.set_bodies(r, th, np.arange(n + 1), np.zeros((n, 3)), np.zeros((n, 6)), np.arange(n))
+    lam = np.random.default_rng(0).standard_normal(r.shape)
+    fpp = binding.flops_per_pair(1)
+    out = {"workload": "first %d blobs of the 1,000-bacteria suspension above a wall" % n}
+    ref = None
+    for arith in ("fp64", "df64", "mixed"):
+        s.apply_mobility_ex(lam, arith)  # warm-up (and autotuning on the first call)
+        s.mobility_timing(True)
+        u = s.apply_mobility_ex(lam, arith)
+        ms, launches = s.mobility_timing(False)
+        if ref is None:
+            ref = u
+        err = float(np.abs(u - ref).max() / np.abs(ref).max())
+        t = ms * 1e-3 / max(launches, 1)
+        pairs = float(n) * n
+        peak = fp64_peak if arith == "fp64" else fp32_peak
+        out[arith] = {"ms": ms / max(launches, 1), "pairs_per_s": pairs / t,
+                      "tflops_algorithmic": pairs * fpp / t / 1e12,
+                      "frac_of_fma_peak": pairs * fpp / t / peak,
+                      "max_rel_diff_vs_fp64": err}
+    s.close()
+    return out
+
+
 def batched_form(torch, binding, W, stream, steps=2):
     """One handle holding the 256 free-space chain suspensions (blob counts
     log-uniform in [500, 20,000], 1.41 M blobs), mixed precision, solved
@@ -360,6 +396,7 @@ def run_ours(args):
         return
 
     at_scale = matvec_at_scale(torch, binding, W, stream, fp32_peak, fp64_peak)
+    compared = products_compared(binding, W, fp32_peak, fp64_peak) if world == 1 else None
     batched = batched_form(torch, binding, W, stream) if world == 1 else None
     fpp = binding.flops_per_pair(1)
     avg_launch_s = (mob_ms * 1e-3) / max(mob_launches, 1)
@@ -369,7 +406,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None,
-                "kernel": "rpy_partial_%s<wall>" % ("f64" if args.precision == "fp64" else "mixed"),
+                "kernel": "rpy_items_%s<wall>" % ("f64" if args.precision == "fp64" else "mixed"),
                 "flop_per_pair": fpp, "pairs_per_launch": nb * nb,
                 "launch_ms": avg_launch_s * 1e3, "launches": mob_launches,
                 "launch_timing": "CUDA events around each launch in %d further steps "
@@ -404,7 +441,7 @@ def run_ours(args):
             "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks,
-            "matvec_at_scale": at_scale, "batched_form": batched}
+            "matvec_at_scale": at_scale, "products_compared": compared, "batched_form": batched}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -60,8 +60,13 @@ extern "C" {
 
 /* ---- precision of the blob mobility product --------------------------- */
 #define AM_FP64  0   /* every operation in FP64                              */
-#define AM_MIXED 1   /* pair terms in FP32, per-target sums in FP64; outer
-                        residual, Arnoldi and constraint algebra in FP64     */
+#define AM_MIXED 1   /* pair terms in FP32, per-target sums in FP64; the
+                        outer residual of the refinement with double-float
+                        pair terms (AM_DF64); Arnoldi and constraint algebra
+                        in FP64                                              */
+#define AM_DF64  2   /* pair terms in double-float arithmetic (pairs of
+                        floats, ~2^-44 relative), sums in FP64: only as the
+                        arithmetic of am_apply_mobility_ex                   */
 
 typedef struct am_handle am_handle;
 
@@ -197,6 +202,13 @@ AM_API int am_get_blobs(am_handle* h, int system, double* r);
 /* One blob mobility product u = M lambda at the current pose (Eq. RPY),
  * host arrays of 3Nb.  For checking and benchmarking the hot kernel. */
 AM_API int am_apply_mobility(am_handle* h, const double* lambda, double* u);
+
+/* As am_apply_mobility with the pair arithmetic chosen: AM_FP64, AM_MIXED
+ * (FP32 pair terms) or AM_DF64 (double-float pair terms, the arithmetic of
+ * the mixed solver's outer residual), whatever the handle's precision.  For
+ * checking and benchmarking the products.  Errors: AM_ERR_ARG (unknown
+ * arithmetic, no bodies), AM_ERR_CUDA. */
+AM_API int am_apply_mobility_ex(am_handle* h, const double* lambda, double* u, int arithmetic);
 
 /* y -> A y for the full operator of Eq. linear_system at the current pose
  * (y and Ay: 3Nb + 6M + 3P, ordered (lambda, U, phi)). */

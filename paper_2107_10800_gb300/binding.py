@@ -16,6 +16,7 @@ AM_ERR_NONUNIT_QUAT = -5
 AM_ERR_SINGULAR = -6
 AM_FP64 = 0
 AM_MIXED = 1
+AM_DF64 = 2
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libam.so")
 
@@ -60,6 +61,7 @@ SIGNATURES = {
     "am_get_bodies": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "am_get_blobs": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "am_apply_mobility": (ctypes.c_int, [_vp, _dp, _dp]),
+    "am_apply_mobility_ex": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int]),
     "am_apply_operator": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_apply_precond": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_rpy_matvec": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
@@ -264,6 +266,14 @@ class Solver:
         la, lp = _d(lam, 3 * self.Nb)
         u, up = _out(3 * self.Nb)
         self._check(lib().am_apply_mobility(self.h, lp, up))
+        return u.reshape(-1, 3)
+
+    def apply_mobility_ex(self, lam, arithmetic):
+        """u = M lambda with the pair arithmetic "fp64", "mixed" or "df64"."""
+        mode = {"fp64": AM_FP64, "mixed": AM_MIXED, "df64": AM_DF64}[arithmetic]
+        la, lp = _d(lam, 3 * self.Nb)
+        u, up = _out(3 * self.Nb)
+        self._check(lib().am_apply_mobility_ex(self.h, lp, up, mode))
         return u.reshape(-1, 3)
 
     def apply_operator(self, y):

@@ -60,6 +60,15 @@ struct ArnoldiCtrl {
     double tol_abs; // stop when the residual estimate is <= tol_abs
 };
 
+// One work item of the block-diagonal all-pairs product: targets [t0, t1)
+// against sources [j0, j1) of one system, partial sums at pbase.
+struct MvItem {
+    int t0, t1;       // targets [t0, t1)
+    int j0, j1;       // sources [j0, j1)
+    int tbase, n3;    // first blob of the system, 3 N_s
+    long long pbase;  // poff_s + c * 3 N_s
+};
+
 // ---- device helpers -----------------------------------------------------
 // R(theta) v = 2 [ p (p.v) + s (p x v) + (s^2 - 1/2) v ]   (App. B, Eq. rot_mat)
 __device__ __forceinline__ void quat_rotate(double s, double px, double py, double pz,
@@ -143,7 +152,7 @@ struct am_handle {
     void* d_items = nullptr;
     int n_items = 0;
     int* d_item_counter = nullptr;
-    int mv_tpt = 1, mv_chunk = 0, mv_grid = 0, mv_grid64 = 0;
+    int mv_tpt = 1, mv_chunk = 0, mv_grid = 0, mv_grid64 = 0, mv_griddf = 0;
     long long mv_part_total = 0;
     bool mv_tuned = false;
 

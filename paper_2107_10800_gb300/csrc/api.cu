@@ -996,6 +996,32 @@ extern "C" AM_API int am_apply_mobility(am_handle* h, const double* lam, double*
     return AM_OK;
 }
 
+extern "C" AM_API int am_apply_mobility_ex(am_handle* h, const double* lam, double* u, int arithmetic) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_apply_mobility_ex", true);
+    if (rc) return rc;
+    if (!lam || !u) return set_err(h, AM_ERR_ARG, "am_apply_mobility_ex: NULL array");
+    int mode;
+    switch (arithmetic) {
+        case AM_FP64: mode = am::kOpFP64; break;
+        case AM_MIXED: mode = am::kOpMixed; break;
+        case AM_DF64: mode = am::kOpDF; break;
+        default: return set_err(h, AM_ERR_ARG, "am_apply_mobility_ex: unknown arithmetic");
+    }
+    cudaStream_t s = h->stream;
+    am::launch_geometry(h);
+    rc = device_flags_to_status(h, "am_apply_mobility_ex");
+    if (rc) return rc;
+    if (!h->mv_tuned && am::mobility_autotune(h))
+        return set_err(h, AM_ERR_CUDA, "am_apply_mobility_ex: mobility autotuning failed");
+    CK(h2d(h->d_t, lam, 3 * (size_t)h->Nb, s));
+    am::mobility_apply(h, h->d_t, h->d_w, mode);
+    CK(cudaGetLastError());
+    CK(d2h(u, h->d_w, 3 * (size_t)h->Nb, s));
+    CK(cudaStreamSynchronize(s));
+    return AM_OK;
+}
+
 extern "C" AM_API int am_apply_operator(am_handle* h, const double* y, double* Ay) {
     if (!h) return AM_ERR_ARG;
     int rc = check_handle(h, "am_apply_operator", true);

@@ -9,12 +9,16 @@ constexpr int kFlagWall = 1;        // a blob centre at or below height a
 constexpr int kFlagSingular = 2;    // a body block of M or N~ not SPD
 constexpr int kFlagCorrection = 4;  // correction normal equations not SPD
 
+// Arithmetic of a mobility product: the handle's precision, FP64,
+// double-float pair terms (rpy_df.cu), or the mixed FP32 pair terms.
+constexpr int kOpHandle = 0, kOpFP64 = 1, kOpDF = 2, kOpMixed = 3;
+
 // Geometry of the current pose: blob positions, lab link vectors, B, b.
 void launch_geometry(am_handle* h);
-// out = A y (Eq. linear_system) with the handle's mobility precision or FP64.
-void op_apply(am_handle* h, const double* y, double* out, bool fp64);
+// out = A y (Eq. linear_system) with the mobility product of `mode`.
+void op_apply(am_handle* h, const double* y, double* out, int mode);
 // Blob mobility product only: u = M lambda (3Nb).
-void mobility_apply(am_handle* h, const double* lam, double* u, bool fp64);
+void mobility_apply(am_handle* h, const double* lam, double* u, int mode);
 // Block-diagonal preconditioner (Sec. 3.1): build at the current pose, apply.
 void pc_build(am_handle* h);
 void pc_apply(am_handle* h, const double* r, double* z);
@@ -31,7 +35,9 @@ int advance(am_handle* h, double dt, am_step_stats* st);
 // tpt targets per thread and source chunks (0 = automatic), their launch,
 // the sum of the partials, and the autotuner that picks (tpt, chunk).
 int mobility_layout(am_handle* h, int tpt, int chunk);
-void launch_items(am_handle* h, const double* lam, bool fp64);
+void launch_items(am_handle* h, const double* lam, int mode);
+int df_resident_grid(bool wall);
+void launch_items_df(am_handle* h, const double* lam);
 void launch_sum_items(am_handle* h, double* u);
 int mobility_autotune(am_handle* h);
 // Per system, replace x by xalt where xalt has the smaller residual

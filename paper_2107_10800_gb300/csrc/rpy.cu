@@ -342,13 +342,6 @@ extern "C" AM_API long long am_kernel_launches(void) { return am::g_launches.loa
 // blob i go to part[poff_s + c * 3 N_s + 3 (i - blob0_s)].
 namespace am {
 
-struct MvItem {
-    int t0, t1;       // targets [t0, t1)
-    int j0, j1;       // sources [j0, j1)
-    int tbase, n3;    // first blob of the system, 3 N_s
-    long long pbase;  // poff_s + c * 3 N_s
-};
-
 template <bool WALL>
 __global__ void __launch_bounds__(kThreads)
 rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam,
@@ -571,17 +564,23 @@ int mobility_layout(am_handle* h, int tpt, int chunk) {
     // never more blocks than items
     h->mv_grid = std::min(h->mv_grid, n_it);
     h->mv_grid64 = std::min(h->mv_grid64, n_it);
+    h->mv_griddf = std::min(df_resident_grid(h->cfg.wall != 0), n_it);
     h->layout_gen++;
     return 0;
 }
 
-// The partial sums of u = M lambda for all systems (FP64 or the handle's
-// precision); the queue counter is reset first.
-void launch_items(am_handle* h, const double* lam, bool fp64) {
+// The partial sums of u = M lambda for all systems (mode: the handle's
+// precision, FP64 or double-float); the queue counter is reset first.
+void launch_items(am_handle* h, const double* lam, int mode) {
+    if (mode == kOpDF) {
+        launch_items_df(h, lam);
+        return;
+    }
+    const bool fp64 = mode == kOpFP64 || (mode == kOpHandle && h->cfg.precision == AM_FP64);
     cudaStream_t st = h->stream;
     cudaMemsetAsync(h->d_item_counter, 0, sizeof(int), st);
     const MvItem* items = static_cast<const MvItem*>(h->d_items);
-    if (fp64 || h->cfg.precision == AM_FP64) {
+    if (fp64) {
         const RpyK<double> k = rpy_consts<double>(h->prm);
         if (h->cfg.wall)
             rpy_items_f64<true><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,

@@ -1,0 +1,200 @@
+// The blob mobility product u = M lambda (Sec. 2.3, Eq. RPY; wall: the
+// Rotne-Prager-Blake tensor) with the pair terms in double-float arithmetic
+// (df64.cuh) on the FP32 pipes.  Same closed forms as rpy_pair.cuh (free
+// space: far r >= 2a, overlapping r < 2a, self; wall: the five-coefficient
+// image part), same work items as the FP64 and mixed products; each tile of
+// 128 sources is summed in df and folded into FP64.  Relative error per pair
+// a few units of 2^-44, against 2^-53 for FP64 and 2^-24 for the mixed
+// product, at about an eighth of the FP64 cost: the mixed solver uses it for
+// its outer residuals.
+#include "am_internal.cuh"
+#include "df64.cuh"
+#include "ops.cuh"
+
+namespace am {
+
+namespace {
+
+// constants of the pair terms as df (see RpyK)
+struct RpyDf {
+    df a2, four_a2, kf2, kf3, kn0, kn1, kn2;
+    double A1;
+};
+
+RpyDf rpy_df_consts(const RpyParams& q) {
+    auto split = [](double x) {
+        const float h = (float)x;
+        return df{h, (float)(x - (double)h)};
+    };
+    RpyDf k;
+    k.a2 = split(q.a2);
+    k.four_a2 = split(q.four_a2);
+    k.kf2 = split(2.0 * q.a2 / 3.0);
+    k.kf3 = split(2.0 * q.a2);
+    k.kn0 = split(4.0 / (3.0 * q.a));
+    k.kn1 = split(9.0 / (32.0 * q.a));
+    k.kn2 = split(1.0 / (8.0 * q.a2));
+    k.A1 = q.inv8pieta;
+    return k;
+}
+
+__device__ __forceinline__ df dfc(double c) { return df_from(c); }
+__device__ __forceinline__ df one_plus(df x) { return df_add(df{1.0f, 0.0f}, x); }
+
+// u/A1 += c1 lambda + c2 d (d . lambda), the free-space pair of rpy_pair.cuh
+__device__ __forceinline__ void pair_free_df(df dx, df dy, df dz, df r2, df lx, df ly, df lz,
+                                             const RpyDf& k, df& ux, df& uy, df& uz) {
+    df c1, c2;
+    if (df_ge(r2, k.four_a2)) {
+        const df ri = df_rsqrt(r2);
+        const df ri2 = df_mul(ri, ri);
+        c1 = df_mul(ri, one_plus(df_mul(k.kf2, ri2)));
+        c2 = df_mul(df_mul(ri, ri2), one_plus(df_neg(df_mul(k.kf3, ri2))));
+    } else if (r2.h > 0.0f) {
+        const df ri = df_rsqrt(r2);
+        const df r = df_mul(r2, ri);
+        c1 = df_mul(k.kn0, one_plus(df_neg(df_mul(k.kn1, r))));
+        c2 = df_mul(k.kn2, ri);
+    } else {
+        c1 = k.kn0;
+        c2 = df{0.0f, 0.0f};
+    }
+    const df sdl = df_mul(c2, df_fma(dx, lx, df_fma(dy, ly, df_mul(dz, lz))));
+    ux = df_fma(c1, lx, df_fma(sdl, dx, ux));
+    uy = df_fma(c1, ly, df_fma(sdl, dy, uy));
+    uz = df_fma(c1, lz, df_fma(sdl, dz, uz));
+}
+
+// the wall image part of rpy_pair.cuh: R = x - y*, x3 target height, h
+// source height
+__device__ __forceinline__ void pair_image_df(df Rx, df Ry, df Rz, df x3, df h, df lx, df ly, df lz,
+                                              const RpyDf& k, df& ux, df& uy, df& uz) {
+    const df s = df_rsqrt(df_fma(Rx, Rx, df_fma(Ry, Ry, df_mul(Rz, Rz))));
+    const df s2 = df_mul(s, s);
+    const df hs = df_mul(h, s);
+    const df u = df_mul(hs, df_mul(x3, s));
+    const df ez = df_mul(Rz, s);
+    const df ez2 = df_mul(ez, ez);
+    const df A = df_mul(k.a2, s2);
+    const df A2 = df_mul(A, A);
+    const df t1 = df_mul(A, ez2);
+    const df t2 = df_mul(A2, ez2);
+    // cI = -1 - 2u - 2/3 A + 2 t1 + 2/3 A^2 - 10/3 t2
+    df cI = df_add(df{-1.0f, 0.0f}, df_scale2(u, -2.0f));
+    cI = df_fma(dfc(-2.0 / 3.0), A, cI);
+    cI = df_add(cI, df_scale2(t1, 2.0f));
+    cI = df_fma(dfc(2.0 / 3.0), A2, cI);
+    cI = df_fma(dfc(-10.0 / 3.0), t2, cI);
+    // cRR = -1 + 6u + 2A - 10 t1 - 10/3 A^2 + 70/3 t2
+    df cRR = df_add(df{-1.0f, 0.0f}, df_mul_f(u, 6.0f));
+    cRR = df_add(cRR, df_scale2(A, 2.0f));
+    cRR = df_add(cRR, df_mul_f(t1, -10.0f));
+    cRR = df_fma(dfc(-10.0 / 3.0), A2, cRR);
+    cRR = df_fma(dfc(70.0 / 3.0), t2, cRR);
+    // cRz = 2 h s + ez (-2 cRR - 2 + 20/3 A^2), czR = 2 h s - 20/3 A^2 ez
+    const df hs2 = df_scale2(hs, 2.0f);
+    const df inner = df_fma(dfc(20.0 / 3.0), A2, df_add(df_scale2(cRR, -2.0f), df{-2.0f, 0.0f}));
+    const df cRz = df_fma(ez, inner, hs2);
+    const df czR = df_fma(df_mul(dfc(-20.0 / 3.0), A2), ez, hs2);
+    // czz = -4 (h s)^2 - 4 t1 - 8/3 A^2 + 20 t2
+    df czz = df_scale2(df_mul(hs, hs), -4.0f);
+    czz = df_add(czz, df_scale2(t1, -4.0f));
+    czz = df_fma(dfc(-8.0 / 3.0), A2, czz);
+    czz = df_add(czz, df_mul_f(t2, 20.0f));
+    const df rx = df_mul(Rx, s), ry = df_mul(Ry, s);
+    const df dotR = df_fma(rx, lx, df_fma(ry, ly, df_mul(ez, lz)));
+    const df t = df_fma(cRR, dotR, df_mul(cRz, lz));
+    ux = df_fma(s, df_fma(cI, lx, df_mul(t, rx)), ux);
+    uy = df_fma(s, df_fma(cI, ly, df_mul(t, ry)), uy);
+    uz = df_fma(s, df_fma(cI, lz, df_fma(t, ez, df_fma(czR, dotR, df_mul(czz, lz)))), uz);
+}
+
+template <bool WALL>
+__global__ void __launch_bounds__(kThreads)
+rpy_items_df(const float4* __restrict__ hi, const float4* __restrict__ lo, const double* __restrict__ lam,
+             double* __restrict__ part, const MvItem* __restrict__ items, int n_items,
+             int* __restrict__ counter, RpyDf k) {
+    __shared__ float4 sh[kTile];
+    __shared__ float4 so[kTile];
+    __shared__ float4 slh[kTile];
+    __shared__ float4 sll[kTile];
+    __shared__ int s_item;
+    for (int round = 0;; ++round) {
+        // first item = the block's own index, later ones from the queue
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(counter, 1);
+        __syncthreads();
+        const int itn = s_item;
+        if (itn >= n_items) break;
+        const MvItem m = items[itn];
+        // items built for two targets per thread span 2 x 128 targets
+        for (int tb = m.t0; tb < m.t1; tb += kThreads) {
+            const int i = tb + threadIdx.x;
+            const float4 xh = (i < m.t1) ? hi[i] : make_float4(0.f, 0.f, 1.f, 0.f);
+            const float4 xl = (i < m.t1) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const df xx{xh.x, xl.x}, xy{xh.y, xl.y}, xz{xh.z, xl.z};
+            double U0 = 0.0, U1 = 0.0, U2 = 0.0;
+            for (int jt = m.j0; jt < m.j1; jt += kTile) {
+                const int cnt = min(kTile, m.j1 - jt);
+                __syncthreads();
+                if (threadIdx.x < cnt) {
+                    const int j = jt + threadIdx.x;
+                    sh[threadIdx.x] = hi[j];
+                    so[threadIdx.x] = lo[j];
+                    const df a = df_from(lam[3 * (size_t)j]), b = df_from(lam[3 * (size_t)j + 1]),
+                             c = df_from(lam[3 * (size_t)j + 2]);
+                    slh[threadIdx.x] = make_float4(a.h, b.h, c.h, 0.f);
+                    sll[threadIdx.x] = make_float4(a.l, b.l, c.l, 0.f);
+                }
+                __syncthreads();
+                df ux{0.f, 0.f}, uy{0.f, 0.f}, uz{0.f, 0.f};
+                for (int q = 0; q < cnt; ++q) {
+                    const float4 yh = sh[q], yl = so[q], lh = slh[q], ll = sll[q];
+                    const df lx{lh.x, ll.x}, ly{lh.y, ll.y}, lz{lh.z, ll.z};
+                    const df yz{yh.z, yl.z};
+                    const df dx = df_sub(xx, df{yh.x, yl.x});
+                    const df dy = df_sub(xy, df{yh.y, yl.y});
+                    const df dz = df_sub(xz, yz);
+                    const df r2 = df_fma(dx, dx, df_fma(dy, dy, df_mul(dz, dz)));
+                    pair_free_df(dx, dy, dz, r2, lx, ly, lz, k, ux, uy, uz);
+                    if (WALL) pair_image_df(dx, dy, df_add(xz, yz), xz, yz, lx, ly, lz, k, ux, uy, uz);
+                }
+                U0 += df_to(ux);
+                U1 += df_to(uy);
+                U2 += df_to(uz);
+            }
+            if (i < m.t1) {
+                double* o = part + m.pbase + 3 * (size_t)(i - m.tbase);
+                o[0] = k.A1 * U0; o[1] = k.A1 * U1; o[2] = k.A1 * U2;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int df_resident_grid(bool wall) {
+    int per = 0;
+    cudaError_t e = wall ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rpy_items_df<true>, kThreads, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rpy_items_df<false>, kThreads, 0);
+    if (e != cudaSuccess || per <= 0) per = 4;
+    return per * num_sms();
+}
+
+// Partial sums of u = M lambda for all systems with double-float pair terms
+// (the queue counter is reset first); positions from the hi/lo arrays.
+void launch_items_df(am_handle* h, const double* lam) {
+    cudaStream_t st = h->stream;
+    cudaMemsetAsync(h->d_item_counter, 0, sizeof(int), st);
+    const MvItem* items = static_cast<const MvItem*>(h->d_items);
+    const RpyDf k = rpy_df_consts(h->prm);
+    if (h->cfg.wall)
+        rpy_items_df<true><<<h->mv_griddf, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items, h->n_items,
+                                                             h->d_item_counter, k);
+    else
+        rpy_items_df<false><<<h->mv_griddf, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items,
+                                                              h->n_items, h->d_item_counter, k);
+    count_launch();
+}
+
+}  // namespace am

@@ -60,6 +60,34 @@ def test_mobility_mixed_matches_oracle(n, wall):
     assert rel(u, ref) <= MIXED
 
 
+DF64_MATVEC = 1e-11
+
+
+@pytest.mark.parametrize("n", [13, 300, 1000])
+@pytest.mark.parametrize("wall", [0, 1])
+def test_mobility_df64_matches_oracle(n, wall):
+    # double-float pair terms (the mixed solver's outer residual), positions
+    # far from the origin so that the hi/lo split of the positions matters
+    r, lam = W.random_blobs(300 + n, n, a=0.1, wall=wall)
+    r = r + np.array([250.0, -125.0, 0.0])
+    for prec in ("mixed", "fp64"):
+        s = loose_blobs_solver(r, 0.1, wall, prec)
+        ref = om.mobility_matvec(r, lam, 0.1, 1.0, wall)
+        assert rel(s.apply_mobility_ex(lam, "df64"), ref) <= DF64_MATVEC
+        assert rel(s.apply_mobility_ex(lam, "fp64"), ref) <= FP64_MATVEC
+        assert rel(s.apply_mobility_ex(lam, "mixed"), ref) <= MIXED
+
+
+def test_mobility_df64_overlap_and_contact():
+    r = np.array([[0, 0, 1.0], [0.05, 0, 1.0], [0.25, 0, 1.0], [0.25, 0.2, 1.0], [0.25, 0.2, 1.0],
+                  [0.45, 0.2, 1.0]])
+    lam = np.random.default_rng(1).standard_normal(r.shape)
+    for wall in (0, 1):
+        s = loose_blobs_solver(r, 0.1, wall, "mixed")
+        ref = om.mobility_matvec(r, lam, 0.1, 1.0, wall)
+        assert rel(s.apply_mobility_ex(lam, "df64"), ref) <= DF64_MATVEC
+
+
 def test_mobility_overlap_and_contact():
     # overlapping blobs (r < 2a), exact contact (r = 2a) and coincident
     # free-space blobs (r = 0 between distinct blobs gives mu0 I)
@@ -169,6 +197,21 @@ def test_solve_mixed_reaches_fp64_residual():
     lam_o, U_o, _ = S.split(y)
     assert rel(U.ravel(), U_o) <= MIXED
     assert rel(lam.ravel(), lam_o) <= MIXED
+
+
+def test_solve_mixed_tight_tolerance_true_residual():
+    # the refinement stops on double-float residuals: the oracle's FP64 true
+    # residual of the returned solution confirms the reported one
+    w = small_colony(5)
+    S = System(w, t=0.03)
+    s = binding.Solver.from_workload(w, t=0.03, tol=1e-11, precision="mixed")
+    U, phi, lam, st = s.solve()
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-11
+    y = np.concatenate([lam.ravel(), U.ravel(), phi.ravel()])
+    b = S.rhs()
+    true_rel = np.linalg.norm(b - S.apply_A(y)) / np.linalg.norm(b)
+    assert true_rel <= 2e-11
+    assert abs(true_rel - st["rel_residual"]) <= 1e-12
 
 
 def test_euler_step_open_chains_matches_oracle(chains):
