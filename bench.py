@@ -249,6 +249,50 @@ def products_compared(binding, W, fp32_peak, fp64_peak, n=60_000):
     return out
 
 
+def learned_form(binding, W):
+    """The learned initial guess: a network trained on the GPU (suspensions
+    of 32 bacteria, seeds 1000-1047, two poses each: 52,224 samples, 20
+    epochs), then cold-start solves at relative residual 1e-8 on held-out
+    suspensions: 556 bacteria (200,160 blobs; mixed precision) from P~^-1 b
+    and from the learned guess, and 100 bacteria (36,000 blobs) in plain FP64,
+    mixed, and mixed with the learned guess.  Host wall time of the second
+    am_solve of each handle (every am_solve starts cold; the first one also
+    tunes the product layout)."""
+    from paper_2107_10800_gb300 import learned
+    t0 = time.perf_counter()
+    X, T = learned.collect(list(range(1000, 1048)), n_bact=32, poses=2, systems_per_handle=16)
+    t1 = time.perf_counter()
+    net, loss = learned.train(X, T, epochs=20, batch=256, lr=1e-3, seed=0)
+    t2 = time.perf_counter()
+    out = {"training": {"samples": int(len(X)), "final_loss": loss, "collect_s": t1 - t0,
+                        "train_s": t2 - t1}}
+
+    def run(w, precision, model):
+        s = binding.Solver.from_workload(w, precision=precision, tol=1e-8, max_iter=2000)
+        if model is not None:
+            s.set_learned(model, check=True)
+        s.solve()  # warm-up: autotuning of the product layout (every am_solve starts cold)
+        tt = time.perf_counter()
+        _, _, _, st = s.solve()
+        wall = time.perf_counter() - tt
+        s.close()
+        return {"solve_ms": 1e3 * wall, "iterations": st["iterations"],
+                "rel_residual0": st["rel_residual0"], "rel_residual": st["rel_residual"],
+                "learned_systems": st["learned_systems"]}
+
+    big = learned.bacteria_at_density(20100, 556)
+    out["bacteria_556"] = {"blobs": int(big["blob_offset"][-1]),
+                           "mixed_block_diagonal_start": run(big, "mixed", None),
+                           "mixed_learned_start": run(big, "mixed", net)}
+    small = learned.bacteria_at_density(20200, 100)
+    out["bacteria_100"] = {"blobs": int(small["blob_offset"][-1]),
+                           "fp64": run(small, "fp64", None),
+                           "mixed": run(small, "mixed", None),
+                           "mixed_learned_start": run(small, "mixed", net)}
+    net.close()
+    return out
+
+
 def batched_form(torch, binding, W, stream, steps=2):
     """One handle holding the 256 free-space chain suspensions (blob counts
     log-uniform in [500, 20,000], 1.41 M blobs), mixed precision, solved
@@ -279,6 +323,24 @@ def batched_form(torch, binding, W, stream, steps=2):
             "ms_precond": st["ms_precond"], "ms_gmres": st["ms_gmres"], "setup_s": setup_s}
 
 
+def combine_ranks(torch, total_s, pairs, e2e_ms_mean, steps, device):
+    """Whole-job figures over the ranks of the process group: the timed
+    region is the slowest rank's, the pairs are all ranks' (independent
+    suspensions, weak scaling).  Returns (seconds, pairs, end-to-end pairs/s
+    per step at the slowest rank's end-to-end step time)."""
+    tt = torch.tensor([total_s, float(pairs), e2e_ms_mean], dtype=torch.float64, device=device)
+    tmax = tt.clone()
+    torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    tsum = tt.clone()
+    torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1]), float(tsum[1]) / steps / (float(tmax[2]) * 1e-3)
+
+
+def rank_workload(W, rank):
+    """The colony of one rank: seed 1 + rank (independent suspensions)."""
+    return W.diatom_colony(1 + rank)
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -295,7 +357,7 @@ def run_ours(args):
         torch.distributed.barrier()
     _b.build()
     L = binding.lib()
-    w = W.diatom_colony(1 + rank)
+    w = rank_workload(W, rank)
     nb, M, P, n = W.counts(w)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -375,17 +437,9 @@ def run_ours(args):
         k += 1
     e2e_rate = st["pairs"] / (statistics.mean(e2e_ms) * 1e-3)
 
-    # aggregate over ranks: max time, summed pairs
     if world > 1:
-        tt = torch.tensor([total_s, float(pairs), statistics.mean(e2e_ms)], dtype=torch.float64,
-                          device="cuda")
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = tt.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        total_s_all = float(tmax[0])
-        pairs_all = float(tsum[1])
-        e2e_rate = float(tsum[1]) / args.steps / (float(tmax[2]) * 1e-3)
+        total_s_all, pairs_all, e2e_rate = combine_ranks(torch, total_s, pairs, statistics.mean(e2e_ms),
+                                                         args.steps, "cuda")
     else:
         total_s_all = total_s
         pairs_all = float(pairs)
@@ -398,6 +452,7 @@ def run_ours(args):
     at_scale = matvec_at_scale(torch, binding, W, stream, fp32_peak, fp64_peak)
     compared = products_compared(binding, W, fp32_peak, fp64_peak) if world == 1 else None
     batched = batched_form(torch, binding, W, stream) if world == 1 else None
+    learned_res = learned_form(binding, W) if world == 1 else None
     fpp = binding.flops_per_pair(1)
     avg_launch_s = (mob_ms * 1e-3) / max(mob_launches, 1)
     achieved = nb * nb * fpp / avg_launch_s
@@ -441,7 +496,8 @@ def run_ours(args):
             "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks,
-            "matvec_at_scale": at_scale, "products_compared": compared, "batched_form": batched}
+            "matvec_at_scale": at_scale, "products_compared": compared, "batched_form": batched,
+            "learned_form": learned_res}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

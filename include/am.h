@@ -300,7 +300,8 @@ AM_API long long am_kernel_launches(void);
  *     body-frame gradient (central differences of step 0.5 along the body
  *     axes, row-major), u_far being the flow of point forces at the
  *     tracking points of the bodies of the other articulated bodies of the
- *     system, each the sum of its blob forces in P~^-1 b, through the blob
+ *     system within a distance 16 of q_p, each the sum of its blob forces
+ *     in P~^-1 b, through the blob
  *     pair tensor (free or wall; FP32 pair terms); zeros;
  *   target (AM_MLP_OUT floats): the background flow of the body, i.e.
  *     u_ext = (M - M~) lambda at its blobs (what the other bodies' forces

@@ -22,10 +22,12 @@ Features of body p, in the body frame of p (FEAT = 128 values):
                                         e_j)))_c / 2h, h = 0.5
   and zeros up to 144; L = 4.  The far flow is the flow of point forces at
   the tracking points of the bodies of the other articulated bodies of the
-  system: u_far(x) = sum_k M(x, q_k) f_k over bodies k of the same system
-  and another articulated body, M the blob pair tensor (free or wall) with
-  the blob radius, f_k the sum over k's blobs of the blob forces of the
-  block-diagonal solution P~^-1 b.
+  system within FAR_R of q_p: u_far(x) = sum_k M(x, q_k) f_k over bodies k
+  of the same system and another articulated body with |q_k - q_p|^2 <=
+  FAR_R^2, M the blob pair tensor (free or wall) with the blob radius, f_k
+  the sum over k's blobs of the blob forces of the block-diagonal solution
+  P~^-1 b.  (The cutoff keeps the feature's scale independent of the size
+  of the suspension.)
 Target: the background flow of the body.  The solution satisfies
 M lambda - K U = u_s; its block-diagonal part M~ lambda (blobs of the same
 body only) is what the body's own forces do, so u_ext = (M - M~) lambda is
@@ -60,6 +62,7 @@ DEPTH = 3
 KNN = 16
 LSCALE = 4.0
 FAR_H = 0.5
+FAR_R = 16.0
 
 
 def far_flow(q, theta, f, system_of_body, assembly, a, eta, wall):
@@ -74,7 +77,8 @@ def far_flow(q, theta, f, system_of_body, assembly, a, eta, wall):
     M = len(q)
     u = np.zeros((M, 7, 3))
     for p in range(M):
-        src = np.nonzero((sysb == sysb[p]) & (asm != asm[p]))[0]
+        d2 = np.sum((q - q[p]) ** 2, axis=1)
+        src = np.nonzero((sysb == sysb[p]) & (asm != asm[p]) & (d2 <= FAR_R ** 2))[0]
         if len(src) == 0:
             continue
         steps = np.zeros((7, 3))

@@ -10,7 +10,8 @@
 // the far flow R_p^T u_far(q_p) and its body-frame gradient by central
 // differences along the body axes (step 0.5), where u_far is the flow of
 // point forces f_k (the summed blob forces of P~^-1 b) at the tracking points
-// of the bodies of the other articulated bodies of the system; zeros to 144.
+// of the bodies of the other articulated bodies of the system within 16 of
+// q_p; zeros to 144.
 // Target (OUT = 32): the background flow u_ext = (M - M~) lambda that the
 // other bodies induce at the body's blobs, fitted in the body frame by
 // NFLOW = 29 flows on the body-frame offsets rho (translation, rotation,
@@ -42,7 +43,7 @@ using am::quat_rotate;
 using am::quat_rotate_inv;
 
 constexpr int FEAT = 144, OUT = 32, NFLOW = 29, WIDTH = 256, NLAYER = 4, KNN = 16;
-constexpr double LSCALE = 4.0, RIDGE = 1e-6, FAR_H = 0.5;
+constexpr double LSCALE = 4.0, RIDGE = 1e-6, FAR_H = 0.5, FAR_R = 16.0;
 const int kDims[NLAYER + 1] = {FEAT, WIDTH, WIDTH, WIDTH, OUT};
 
 size_t layer_w_off(int l) {
@@ -132,7 +133,8 @@ __global__ void k_body_force(int M, const int* __restrict__ blob_off, const doub
 }
 
 // Far-flow features of body p (one thread): the flow of the point forces f_k
-// of the other articulated bodies' bodies of its system at q_p and at
+// of the other articulated bodies' bodies of its system within FAR_R of q_p
+// at q_p and at
 // q_p +- h R_p e_j, pair terms in FP32 (blob pair tensor with the blob
 // radius), sums in FP32; written to X[126 .. 137].
 __global__ void k_far_flow(int M, const double* __restrict__ q, const double* __restrict__ th,
@@ -158,9 +160,12 @@ __global__ void k_far_flow(int M, const double* __restrict__ q, const double* __
     }
     float acc[7][3];
     for (int e = 0; e < 7; ++e) acc[e][0] = acc[e][1] = acc[e][2] = 0.f;
+    const double px = q[3 * (size_t)p], py = q[3 * (size_t)p + 1], pz = q[3 * (size_t)p + 2];
     for (int kb = b0; kb < b1; ++kb) {
         if (asm_of_body[kb] == ap) continue;
         const double qx = q[3 * (size_t)kb], qy = q[3 * (size_t)kb + 1], qz = q[3 * (size_t)kb + 2];
+        const double ex = qx - px, ey = qy - py, ez = qz - pz;
+        if (ex * ex + ey * ey + ez * ez > FAR_R * FAR_R) continue;
         const float fx = (float)f[3 * (size_t)kb], fy = (float)f[3 * (size_t)kb + 1], fz = (float)f[3 * (size_t)kb + 2];
 #pragma unroll
         for (int e = 0; e < 7; ++e) {

@@ -620,6 +620,19 @@ int mobility_autotune(am_handle* h) {
     for (int tpt : (mixed ? std::vector<int>{1, 2} : std::vector<int>{1}))
         for (int chunk : {0, 512, 1024, 2048, 4096, 8192})
             if (chunk == 0 || chunk <= 2 * maxnb) cand.push_back({tpt, chunk});
+    // One system of modest size: the items all start at once, so the
+    // slowest SM sets the time; chunks that make the item count a multiple
+    // of the SM count (k = 1..6 items per SM) balance the last wave.
+    if (h->S == 1 && maxnb * maxnb <= 4000000000LL) {
+        for (int tpt : (mixed ? std::vector<int>{1, 2} : std::vector<int>{1})) {
+            const long long ntb = (maxnb + (long long)kThreads * tpt - 1) / ((long long)kThreads * tpt);
+            for (int k = 1; k <= 6; ++k) {
+                const long long c = ((long long)k * num_sms() + ntb - 1) / ntb;  // chunks per system
+                const long long chunk = (maxnb + c - 1) / c;
+                if (chunk >= 32) cand.push_back({tpt, (int)chunk});
+            }
+        }
+    }
     cudaStream_t st = h->stream;
     double* lam = nullptr;
     if (cudaMalloc(&lam, 3 * (size_t)std::max(h->Nb, 1) * sizeof(double)) != cudaSuccess) return 1;

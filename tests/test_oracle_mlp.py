@@ -56,7 +56,7 @@ def test_far_flow_is_the_oseen_flow_of_other_assemblies():
     # the Oseen flow of the force and J its gradient (to O(a^2/r^2) and the
     # O(h^2/r^2) of the central difference); bodies of the same articulated
     # body do not count
-    q = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [60.0, -20.0, 30.0]])
+    q = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [12.0, -4.0, 6.0]])
     f = np.array([[0.0, 0.0, 0.0], [3.0, 1.0, -2.0], [1.0, -2.0, 0.5]])
     th = np.tile([1.0, 0.0, 0.0, 0.0], (3, 1))  # body frames = lab frame
     u, J = mlp.far_flow(q, th, f, np.zeros(3, int), np.array([0, 0, 1]), 0.1, 1.0, 0)
@@ -66,13 +66,26 @@ def test_far_flow_is_the_oseen_flow_of_other_assemblies():
         return (g + d * (d @ g) / r ** 2) / (8 * np.pi * r)
 
     d = q[0] - q[2]
-    assert np.allclose(u[0], oseen(d, f[2]), rtol=1e-5)
+    # RPY differs from Oseen by O(a^2 / r^2) ~ 5e-5 at r = 14
+    assert np.allclose(u[0], oseen(d, f[2]), rtol=2e-4)
     # analytic gradient of the Oseen flow by a fine difference of the formula
     Jo = np.stack([(oseen(d + 1e-6 * e, f[2]) - oseen(d - 1e-6 * e, f[2])) / 2e-6 for e in np.eye(3)], axis=1)
-    assert np.abs(J[0] - Jo).max() < 1e-3 * np.abs(Jo).max()
+    assert np.abs(J[0] - Jo).max() < 1e-2 * np.abs(Jo).max()
     # body 2 feels bodies 0 and 1, body 1 only body 2
-    assert np.allclose(u[1], oseen(q[1] - q[2], f[2]), rtol=1e-5)
-    assert np.allclose(u[2], oseen(q[2] - q[0], f[0]) + oseen(q[2] - q[1], f[1]), rtol=1e-5)
+    assert np.allclose(u[1], oseen(q[1] - q[2], f[2]), rtol=2e-4)
+    assert np.allclose(u[2], oseen(q[2] - q[0], f[0]) + oseen(q[2] - q[1], f[1]), rtol=2e-4)
+
+
+def test_far_flow_cutoff():
+    # sources beyond FAR_R of the body do not count, those inside do
+    th = np.tile([1.0, 0.0, 0.0, 0.0], (3, 1))
+    f = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 3.0], [1.0, 2.0, 3.0]])
+    q = np.array([[0.0, 0.0, 0.0], [mlp.FAR_R - 0.5, 0.0, 0.0], [0.0, mlp.FAR_R + 0.5, 0.0]])
+    u, J = mlp.far_flow(q, th, f, np.zeros(3, int), np.arange(3), 0.1, 1.0, 0)
+    d = q[0] - q[1]
+    r = np.linalg.norm(d)
+    expect = (f[1] + d * (d @ f[1]) / r ** 2) / (8 * np.pi * r)
+    assert np.allclose(u[0], expect, rtol=1e-4)
 
 
 def test_features_layout():
