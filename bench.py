@@ -392,7 +392,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    step_ms, pairs, iters, resid = [], 0, [], []
+    step_ms, pairs, iters, resid, precond_ms = [], 0, [], [], []
     launches0 = binding.kernel_launches()
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
@@ -407,6 +407,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             pairs += st["pairs"]
+            precond_ms.append(st["ms_precond"])
             iters.append(st["iterations"])
             resid.append(st["rel_residual"])
             k += 1
@@ -490,6 +491,7 @@ def run_ours(args):
                        "parallelism": "independent suspension per GPU" if world > 1 else "1 GPU"},
             "solve_ms_per_step": 1e3 * total_s_all / args.steps,
             "gmres_iterations_per_step": statistics.mean(iters),
+            "precond_build_ms_per_step": statistics.mean(precond_ms),
             "max_rel_residual": max(resid),
             "wall_s_timed_region": t_wall,
             "roofline": roofline, "cpu_baseline": cpu,

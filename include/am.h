@@ -102,8 +102,9 @@ typedef struct {
     double ms_gmres;        /* device time: GMRES                            */
     double ms_update;       /* device time: Euler update, reconstruction,
                                correction                                    */
-    int    learned_systems; /* systems whose initial guess came from the
-                               learned model (am_set_learned)                */
+    int    learned_systems; /* systems whose initial guess used the learned
+                               model (am_set_learned; with the check: a
+                               positive step along it)                       */
     double rel_residual0;   /* true ||b - A y0||_2 / ||b||_2 of the initial
                                guess (max over systems)                      */
 } am_step_stats;
@@ -355,9 +356,11 @@ AM_API int am_mlp_predict(am_mlp* m, const float* X, int n, int bf16, float* Y);
  * AM_ERR_ARG (no bodies), AM_ERR_CUDA. */
 AM_API int am_learned_features(am_handle* h, float* X, float* T);
 /* Use `model` (NULL: none) for the initial guess of cold starts.  check != 0:
- * per system, keep P~^-1 b where its residual is smaller than the learned
- * guess's (two extra operator products).  The handle does not own the
- * model; keep it alive while it is set. */
+ * per system, the point x_pc + beta (x_learned - x_pc) with the smallest
+ * residual on that line, beta = -<r_pc, w> / <w, w>, w = r_learned - r_pc
+ * (two extra operator products; never a larger residual than P~^-1 b);
+ * check == 0: the learned guess itself.  The handle does not own the model;
+ * keep it alive while it is set. */
 AM_API int am_set_learned(am_handle* h, am_mlp* model, int check);
 
 /* Destroy a handle and free its device memory (NULL is a no-op). */

@@ -355,12 +355,13 @@ int prepare(am_handle* h, const char* who, bool warm, am_step_stats* st) {
         CK(cudaMemcpyAsync(h->d_x, h->d_xprev, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         am::project_constraints(h, h->d_x);
     } else if (h->mlp) {
-        // learned guess; with the check, systems where P~^-1 b (left in
-        // d_dx) has the smaller residual keep P~^-1 b
+        // learned guess; with the check, per system the point on the line
+        // from P~^-1 b (left in d_dx) through the learned guess with the
+        // smallest residual
         if (am::learned_x0(h, h->d_x))
             return set_err(h, AM_ERR_CUDA, std::string(who) + ": learned initial guess failed");
-        int kept = h->mlp_check ? am::pick_initial(h, h->d_x, h->d_dx) : 0;
-        if (st) st->learned_systems = h->S - kept;
+        const int used = h->mlp_check ? am::line_initial(h, h->d_x, h->d_dx) : h->S;
+        if (st) st->learned_systems = used;
     } else {
         am::pc_apply(h, h->d_b, h->d_x);
     }

@@ -566,10 +566,6 @@ __global__ void k_sys_norm(const double* __restrict__ npart, const int* __restri
     out[s] = sqrt(a);
 }
 
-// Start of a restart cycle, one block: per system the relative residual
-// beta_s / ||b_s||; systems above tol are active, with v_0 scale 1/beta_s,
-// g = (beta_s, 0, ...), absolute stop threshold tol ||b_s||.  red[0] = max
-// relative residual (NaN if any is not finite), red[1] = active count.
 // out = min over systems (with b_s != 0) of |r_s| / |b_s|
 __global__ void k_sys_minrel(int S, const double* __restrict__ beta, const double* __restrict__ bnorm,
                              double* __restrict__ out) {
@@ -586,6 +582,10 @@ __global__ void k_sys_minrel(int S, const double* __restrict__ beta, const doubl
     if (threadIdx.x == 0) out[0] = smin[0];
 }
 
+// Start of a restart cycle, one block: per system the relative residual
+// beta_s / ||b_s||; systems above tol are active, with v_0 scale 1/beta_s,
+// g = (beta_s, 0, ...), absolute stop threshold tol ||b_s||.  red[0] = max
+// relative residual (NaN if any is not finite), red[1] = active count.
 __global__ void k_cycle_init(int S, int m, double tol, const double* __restrict__ beta,
                              const double* __restrict__ bnorm, int* __restrict__ active,
                              double* __restrict__ inv, double* __restrict__ g, int* __restrict__ kdone,
@@ -901,35 +901,58 @@ static void sys_residual(am_handle* h, const double* b, const double* x, double*
     count_launch(2);
 }
 
-// x <- xalt in every system whose residual is smaller with xalt; counts
-// the systems that switched into *nsw
-__global__ void k_pick_sys(double* __restrict__ x, const double* __restrict__ xalt, int n,
-                           const int* __restrict__ sys_of, const double* __restrict__ rx,
-                           const double* __restrict__ ralt) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int s = sys_of[i];
-        if (ralt[s] < rx[s]) x[i] = xalt[i];
-    }
-}
-
-__global__ void k_count_pick(int S, const double* __restrict__ rx, const double* __restrict__ ralt,
-                             double* __restrict__ out) {
+// Per chunk c, with w = rl - rp: part[c] = <rp, w>, part[nch + c] = <w, w>
+__global__ void __launch_bounds__(256)
+k_chunk_line(const double* __restrict__ rp, const double* __restrict__ rl, const int* __restrict__ cs,
+             const int* __restrict__ ce, int nch, double* __restrict__ part) {
     __shared__ double sh[64];
-    double c = 0.0;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) c += (ralt[s] < rx[s]) ? 1.0 : 0.0;
-    c = block_sum(c, sh);
-    if (threadIdx.x == 0) out[0] = c;
+    const int c = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = cs[c] + threadIdx.x; i < ce[c]; i += blockDim.x) {
+        const double w = rl[i] - rp[i];
+        a = fma(rp[i], w, a);
+        b = fma(w, w, b);
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) { part[c] = a; part[nch + c] = b; }
 }
 
-int pick_initial(am_handle* h, double* x, const double* xalt) {
+// Per system the step along xl - xp that minimises |r(xp + beta (xl - xp))|:
+// beta_s = -<rp, w> / <w, w> (0 when w = 0); out[0] = systems with beta > 0.
+__global__ void k_sys_line(const double* __restrict__ part, const int* __restrict__ coff, int S, int nch,
+                           double* __restrict__ beta, double* __restrict__ out) {
+    __shared__ double sh[64];
+    double cnt = 0.0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int c = coff[s]; c < coff[s + 1]; ++c) { a += part[c]; b += part[nch + c]; }
+        const double bs = b > 0.0 ? -a / b : 0.0;
+        beta[s] = bs;
+        cnt += bs > 0.0 ? 1.0 : 0.0;
+    }
+    cnt = block_sum(cnt, sh);
+    if (threadIdx.x == 0) out[0] = cnt;
+}
+
+// x = xp + beta_s (x - xp)
+__global__ void k_line_combine(double* __restrict__ x, const double* __restrict__ xp, int n,
+                               const int* __restrict__ sys_of, const double* __restrict__ beta) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] = fma(beta[sys_of[i]], x[i] - xp[i], xp[i]);
+}
+
+int line_initial(am_handle* h, double* x, const double* xp) {
     const int S = h->S;
-    double* rx = h->d_sysred + 2 * (size_t)S;
-    double* ra = h->d_sysred + 3 * (size_t)S;
-    sys_residual(h, h->d_b, x, h->d_rir, rx, false);
-    sys_residual(h, h->d_b, xalt, h->d_rir, ra, false);
-    k_pick_sys<<<red_blocks(h->n), 256, 0, h->stream>>>(x, xalt, h->n, h->d_sys_of_elem, rx, ra);
-    k_count_pick<<<1, 256, 0, h->stream>>>(S, rx, ra, h->d_scal);
-    count_launch(2);
+    double* beta = h->d_sysred + 2 * (size_t)S;
+    double* rn = h->d_sysred + 3 * (size_t)S;
+    sys_residual(h, h->d_b, x, h->d_rir, rn, kOpHandle);   // r of the learned guess
+    sys_residual(h, h->d_b, xp, h->d_z, rn, kOpHandle);    // r of P~^-1 b
+    k_chunk_line<<<h->nchunks, 256, 0, h->stream>>>(h->d_z, h->d_rir, h->d_chunk_start, h->d_chunk_end,
+                                                    h->nchunks, h->d_part);
+    k_sys_line<<<1, 256, 0, h->stream>>>(h->d_part, h->d_sys_chunk_off, S, h->nchunks, beta, h->d_scal);
+    k_line_combine<<<red_blocks(h->n), 256, 0, h->stream>>>(x, xp, h->n, h->d_sys_of_elem, beta);
+    count_launch(3);
     read_scal(h, 1);
     return (int)h->h_scal[0];
 }

@@ -40,10 +40,11 @@ int df_resident_grid(bool wall);
 void launch_items_df(am_handle* h, const double* lam);
 void launch_sum_items(am_handle* h, double* u);
 int mobility_autotune(am_handle* h);
-// Per system, replace x by xalt where xalt has the smaller residual
-// |b - A x| (operator in the handle's precision); returns how many systems
-// took xalt.  Uses d_w, d_rir and the upper half of d_sysred.
-int pick_initial(am_handle* h, double* x, const double* xalt);
+// Per system, x <- xp + beta_s (x - xp) with beta_s minimising the
+// residual |b - A x| on that line (operator in the handle's precision);
+// returns how many systems have beta_s > 0.  Uses d_w, d_rir, d_z, d_part
+// and the upper half of d_sysred.
+int line_initial(am_handle* h, double* x, const double* xp);
 // Learned initial guess (mlp.cu): x = P~^-1 (b - predicted background
 // flow), with x_pc = P~^-1 b left in d_dx; uses d_rir.
 int learned_x0(am_handle* h, double* x);

@@ -1,11 +1,13 @@
 // Block-diagonal preconditioner (Sec. 3.1): the exact solution of the
 // approximate problem Eq. precond, where M keeps only same-body blocks M^(pp).
 //
-// Build, per body p (one block): M^(pp) from the pair tensors, its Cholesky
-// factor, the explicit inverse, Y_p = (M^(pp))^-1 K_p, S_p = K_p^T Y_p and
+// Build, per body p (one block): M^(pp) from the pair tensors, its explicit
+// inverse by blocked Cholesky, blocked triangular inverse and X^T X on 32 x 32
+// shared-memory tiles, Y_p = (M^(pp))^-1 K_p, S_p = K_p^T Y_p and
 // N~_p = S_p^-1.  Per articulated body a (one block): H_a = C_a N~_a C_a^T and
 // its generalised inverse G~_a (Eq. block_diag_const_res) by symmetric pivoted
-// Cholesky: H(perm) = L L^T with L of rank r gives
+// Cholesky (column by column, then the blocked inverse of the rank-r factor):
+// H(perm) = L L^T with L of rank r gives
 // G~ = perm [(L11 L11^T)^-1 0; 0 0] perm^T, which solves H phi = c exactly for
 // every c in range(H) = range(C_a).
 //
@@ -30,18 +32,19 @@ namespace am {
 constexpr int kRows = 32;  // rows per apply work item
 
 template <class T>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(kPcThreads)
 k_pcb_build(const int* __restrict__ blob_off, const double4_32a* __restrict__ r4,
             const double4_32a* __restrict__ d4, const long long* __restrict__ moff,
             T* __restrict__ minv, T* __restrict__ work, T* __restrict__ Y, double* __restrict__ Nt,
             RpyK<double> prm, int wall, int* flags) {
     __shared__ double sh[64];
+    __shared__ PcTiles<T> tiles;
+    __shared__ int s_bad;
     const int b = blockIdx.x;
     const int i0 = blob_off[b];
     const int nbl = blob_off[b + 1] - i0;
     const int m = 3 * nbl;
-    extern __shared__ unsigned char dyn_smem[];
-    T* colbuf = reinterpret_cast<T*>(dyn_smem);
+    if (threadIdx.x == 0) s_bad = 0;
     T* A = minv + moff[b];
     T* L = work + 2 * moff[b];
     T* X = L + (size_t)m * m;
@@ -53,21 +56,12 @@ k_pcb_build(const int* __restrict__ blob_off, const double4_32a* __restrict__ r4
             for (int c = 0; c < 3; ++c) L[(size_t)(3 * ti + a) * m + 3 * sj + c] = (T)Tt[3 * a + c];
     }
     __syncthreads();
-    if (!block_cholesky(L, m, sh)) {
+    // (M^(pp))^-1 by blocked Cholesky, triangular inverse and X^T X
+    blocked_spd_inverse(L, X, A, m, tiles, &s_bad);
+    if (s_bad) {
         if (threadIdx.x == 0) atomicOr(flags, kFlagSingular);
         return;
     }
-    block_lower_inverse(L, X, m, m, colbuf);
-    // A = X^T X: lower triangle computed, mirrored to the upper one
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-        const int i = idx / m, j = idx % m;
-        if (j > i) continue;
-        T s = 0;
-        for (int k = i; k < m; ++k) s = fma(X[(size_t)k * m + i], X[(size_t)k * m + j], s);
-        A[idx] = s;
-        A[(size_t)j * m + i] = s;
-    }
-    __syncthreads();
     T* Yb = Y + 18 * (size_t)i0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double y[6] = {0, 0, 0, 0, 0, 0};
@@ -120,24 +114,26 @@ __device__ __forceinline__ void e_times_n(double sg, const double* l, const doub
 }
 
 template <class T>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(kPcThreads)
 k_pca_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
             const int* __restrict__ bp, const int* __restrict__ bq, const double* __restrict__ lp,
             const double* __restrict__ lq, const double* __restrict__ Nt,
             const long long* __restrict__ goff, T* __restrict__ G, T* __restrict__ gwork,
             int* __restrict__ perm_all, const long long* __restrict__ poff, int* __restrict__ rank_out,
             double tol) {
-    __shared__ double shv[512];
-    __shared__ int shi[512];
     extern __shared__ unsigned char dyn_smem[];
-    T* colbuf = reinterpret_cast<T*>(dyn_smem);
-    __shared__ double sh[64];
-    __shared__ int s_rank;
+    T* colk = reinterpret_cast<T*>(dyn_smem);  // m values: the pivot column
+    __shared__ PcTiles<T> tiles;
+    __shared__ double s_wv[32];
+    __shared__ int s_wi[32];
+    __shared__ double s_pv;
+    __shared__ int s_pi;
     const int a = blockIdx.x;
     const int L0 = asm_link_off[a];
     const int Pa = asm_link_off[a + 1] - L0;
     const int m = 3 * Pa;
     if (m == 0) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T* H = gwork + 2 * goff[a];
     T* X = H + (size_t)m * m;
     T* Ga = G + goff[a];
@@ -168,39 +164,40 @@ k_pca_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_li
             for (int yy = 0; yy < 3; ++yy) H[(size_t)(3 * r + x) * m + 3 * c + yy] = (T)blk[x * 3 + yy];
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
-    if (threadIdx.x == 0) s_rank = m;
     __syncthreads();
+    // symmetric pivoted Cholesky (largest remaining diagonal first, ties to
+    // the lower index), stopped at the first pivot <= tol * the first one
     double d0 = 0.0;
+    int r = m;
     for (int k = 0; k < m; ++k) {
         double best = -1.0;
-        int bi = k;
+        int bi = 0x7fffffff;
         for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
             const double v = (double)H[(size_t)i * m + i];
-            if (v > best) { best = v; bi = i; }
+            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
         }
-        shv[threadIdx.x] = best;
-        shi[threadIdx.x] = bi;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_wv[wid] = best; s_wi[wid] = bi; }
         __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                const double o = shv[threadIdx.x + s];
-                const int oi = shi[threadIdx.x + s];
-                if (o > shv[threadIdx.x] || (o == shv[threadIdx.x] && oi < shi[threadIdx.x])) {
-                    shv[threadIdx.x] = o;
-                    shi[threadIdx.x] = oi;
-                }
+        if (wid == 0) {
+            best = lane < nw ? s_wv[lane] : -1.0;
+            bi = lane < nw ? s_wi[lane] : 0x7fffffff;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
-            __syncthreads();
+            if (lane == 0) { s_pv = best; s_pi = bi; }
         }
-        const double dmax = shv[0];
-        if (k == 0) d0 = dmax;
-        if (!(dmax > tol * d0) || !(dmax > 0.0)) {
-            if (threadIdx.x == 0) s_rank = k;
-            __syncthreads();
-            break;
-        }
-        const int j = shi[0];
         __syncthreads();
+        const double dmax = s_pv;
+        const int j = s_pi;
+        if (k == 0) d0 = dmax;
+        if (!(dmax > tol * d0) || !(dmax > 0.0)) { r = k; break; }
         if (j != k) {
             for (int c = threadIdx.x; c < m; c += blockDim.x) {
                 const T t = H[(size_t)k * m + c];
@@ -208,10 +205,10 @@ k_pca_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_li
                 H[(size_t)j * m + c] = t;
             }
             __syncthreads();
-            for (int r = threadIdx.x; r < m; r += blockDim.x) {
-                const T t = H[(size_t)r * m + k];
-                H[(size_t)r * m + k] = H[(size_t)r * m + j];
-                H[(size_t)r * m + j] = t;
+            for (int rr = threadIdx.x; rr < m; rr += blockDim.x) {
+                const T t = H[(size_t)rr * m + k];
+                H[(size_t)rr * m + k] = H[(size_t)rr * m + j];
+                H[(size_t)rr * m + j] = t;
             }
             if (threadIdx.x == 0) {
                 const int t = perm[k];
@@ -220,33 +217,29 @@ k_pca_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_li
             }
             __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            const T d = (T)sqrt((double)H[(size_t)k * m + k]);
-            H[(size_t)k * m + k] = d;
-            sh[0] = 1.0 / (double)d;
-        }
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) colk[i] = H[(size_t)i * m + k];
         __syncthreads();
-        const T inv = (T)sh[0];
-        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) H[(size_t)i * m + k] *= inv;
-        __syncthreads();
+        // trailing update H_ij -= h_ik h_jk / h_kk and the scaled column
+        const T dk = colk[k];
+        const T sdk = (T)sqrt((double)dk);
+        const T invd = (T)1 / dk;
         const int len = m - k - 1;
         for (int idx = threadIdx.x; idx < len * len; idx += blockDim.x) {
             const int i = k + 1 + idx / len, jj = k + 1 + idx % len;
-            H[(size_t)i * m + jj] -= H[(size_t)i * m + k] * H[(size_t)jj * m + k];
+            H[(size_t)i * m + jj] -= colk[i] * colk[jj] * invd;
         }
+        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) H[(size_t)i * m + k] = colk[i] / sdk;
+        if (threadIdx.x == 0) H[(size_t)k * m + k] = sdk;
         __syncthreads();
     }
-    const int r = s_rank;
     if (threadIdx.x == 0) rank_out[a] = r;
-    block_lower_inverse(H, X, r, m, colbuf);
+    // (L11 L11^T)^-1 of the rank-r leading block, blocked (written over H)
+    blocked_chol_inverse(H, X, H, r, m, tiles);
     for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Ga[idx] = (T)0;
     __syncthreads();
     for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
-        const int i = idx / r, j = idx % r;
-        const int k0 = i > j ? i : j;
-        T s = 0;
-        for (int k = k0; k < r; ++k) s = fma(X[(size_t)k * m + i], X[(size_t)k * m + j], s);
-        Ga[(size_t)perm[i] * m + perm[j]] = s;
+        const int i = idx / r, jj = idx % r;
+        Ga[(size_t)perm[i] * m + perm[jj]] = H[(size_t)i * m + jj];
     }
 }
 
@@ -411,28 +404,17 @@ k_pc_ap3(int Nb, int M, const int* __restrict__ pcw_body, const int* __restrict_
 template <class T>
 static void pc_build_t(am_handle* h, double tol) {
     cudaStream_t s = h->stream;
-    // 16 warps per block unless the per-warp column buffers of the largest
-    // body or articulated body would exceed 200 KB of shared memory
-    auto pick = [](size_t col_bytes) {
-        int w = 16;
-        while (w > 1 && (size_t)w * col_bytes > 200 * 1024) w /= 2;
-        return w;
-    };
-    const size_t colb = (size_t)3 * h->max_body_blobs * sizeof(T);
-    const size_t cola = (size_t)3 * std::max(1, h->max_asm_links) * sizeof(T);
-    const int wb = pick(colb), wa = pick(cola);
-    const int threads_b = 32 * wb, threads_a = 32 * wa;
-    const size_t smem_b = wb * colb, smem_a = wa * cola;
-    if (smem_b > 48 * 1024)
-        cudaFuncSetAttribute(k_pcb_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+    // one block of kPcThreads per body and per articulated body (the tile
+    // routines assume that block size)
+    const size_t smem_a = (size_t)3 * std::max(1, h->max_asm_links) * sizeof(T);  // pivot column
     if (smem_a > 48 * 1024)
         cudaFuncSetAttribute(k_pca_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
-    k_pcb_build<T><<<h->M, threads_b, smem_b, s>>>(h->d_blob_off, h->d_r4, h->d_d4, h->d_minv_off,
+    k_pcb_build<T><<<h->M, kPcThreads, 0, s>>>(h->d_blob_off, h->d_r4, h->d_d4, h->d_minv_off,
                                                  (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt,
                                                  rpy_consts<double>(h->prm), h->cfg.wall, h->d_flags);
     count_launch();
     if (h->P) {
-        k_pca_build<T><<<h->NA, threads_a, smem_a, s>>>(h->d_asm_link_off, h->d_asm_link_idx, h->d_bp,
+        k_pca_build<T><<<h->NA, kPcThreads, smem_a, s>>>(h->d_asm_link_off, h->d_asm_link_idx, h->d_bp,
                                                       h->d_bq, h->d_lp, h->d_lq, h->d_Nt, h->d_G_off,
                                                       (T*)h->d_G, (T*)h->d_Gwork, h->d_perm,
                                                       h->d_perm_off, h->d_G_rank, tol);

@@ -171,9 +171,10 @@ def test_initial_guess_assembly_matches_oracle():
     assert np.abs(C @ U.ravel() - S.B_vec()).max() <= 1e-12 * np.abs(U).max()
 
 
-def test_residual_check_keeps_block_diagonal_guess():
-    # a network with a large wrong output: with the check every system keeps
-    # P~^-1 b and the solve is the plain one
+def test_line_search_is_never_worse_than_block_diagonal_guess():
+    # a network with a large wrong output: with the check every system takes
+    # the point of least residual on the line from P~^-1 b through the
+    # learned guess, so its initial residual is at most that of P~^-1 b
     ws = [learned.bacteria_at_density(15, 2), learned.bacteria_at_density(16, 2)]
     net = constant_net(np.full(om.OUT, 50.0, np.float32))
     base = binding.Solver.from_workloads(ws, tol=1e-10)
@@ -181,9 +182,14 @@ def test_residual_check_keeps_block_diagonal_guess():
     s = binding.Solver.from_workloads(ws, tol=1e-10)
     s.set_learned(net, check=True)
     U1, _, _, st1 = s.solve()
-    assert st1["learned_systems"] == 0
-    assert st1["iterations"] == st0["iterations"]
-    assert rel(U1, U0) <= 1e-12
+    assert st1["rel_residual0"] <= st0["rel_residual0"] * (1 + 1e-12)
+    assert st1["rel_residual"] <= 1e-10
+    assert rel(U1, U0) <= 1e-8
+    # without the check the wrong guess is used as it is
+    s2 = binding.Solver.from_workloads(ws, tol=1e-10)
+    s2.set_learned(net, check=False)
+    _, _, _, st2 = s2.solve()
+    assert st2["rel_residual0"] > 10 * st0["rel_residual0"]
 
 
 def test_zero_network_gives_block_diagonal_solution():
