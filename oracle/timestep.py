@@ -203,3 +203,57 @@ def euler_step(w, q, theta, t, dt, delta=1e-10, solve_tol=1e-12, x0=None,
                 g2_before=g2, g2_after=float(np.sum(g_after * g_after)),
                 corr_iters=corr_its, y=y, q_star=q_s, theta_star=theta_s)
     return q_n, th_n, info
+
+
+def _stage_update(w, q0, theta0, U, assembly, bp, bq, h, dlp_end, dlq_end, delta):
+    """Move the pose (q0, theta0) by h with body velocities U: each
+    articulated body's centre by h times its mean body velocity (Eq. ucom),
+    each orientation by theta_{omega h} . theta; reconstruct with the link
+    vectors at the end (Eq. pseudo-inv-sol, reconst-up-COM) and correct when
+    ||g*||^2 >= delta (Sec. 4.2).  Returns (q, theta, g2_before, g2_after)."""
+    asm = assemblies_of(assembly, bp)
+    q_com = {a_: q0[bodies].mean(axis=0) + h * U[bodies, :3].mean(axis=0)
+             for a_, (bodies, _) in asm.items()}
+    theta_s = quat_mul(quat_from_rotvec(U[:, 3:] * h), theta0)
+    q_s = reconstruct(q_com, theta_s, dlp_end, dlq_end, assembly, bp, bq)
+    g = constraint_g(q_s, theta_s, dlp_end, dlq_end, bp, bq) if len(bp) else np.zeros((0, 3))
+    g2 = float(np.sum(g * g))
+    if g2 >= delta:
+        q_n, th_n, _ = correct(q_s, theta_s, dlp_end, dlq_end, assembly, bp, bq, delta)
+    else:
+        q_n, th_n = q_s, theta_s
+    g_after = constraint_g(q_n, th_n, dlp_end, dlq_end, bp, bq) if len(bp) else np.zeros((0, 3))
+    return q_n, th_n, g2, float(np.sum(g_after * g_after))
+
+
+def midpoint_step(w, q, theta, t, dt, delta=1e-10, solve_tol=1e-12, dl_now=None, dl_half=None,
+                  dl_next=None):
+    """One explicit midpoint (RK2) step (App. "Midpoint scheme"): velocities
+    at t; half step to the midpoint pose (reconstruction and correction with
+    the link vectors at t + dt/2); velocities at the midpoint (links and
+    their derivatives at t + dt/2); full step from the pose at t with the
+    midpoint velocities, reconstruction and correction at t + dt.
+    dl_half = (dlp, dlq, dlp_dot, dlq_dot) at t + dt/2 and dl_next = (dlp,
+    dlq) at t + dt default to w["dl"] when the workload has time-dependent
+    links and to the links at t otherwise.  Returns (q, theta, info)."""
+    S = System(w, q=q, theta=theta, dl=dl_now, t=t)
+    b = S.rhs()
+    y0, its0, hist0 = S.gmres(b=b, x0=S.apply_preconditioner(b), tol=solve_tol)
+    U0 = S.split(y0)[1].reshape(-1, 6)
+    bp, bq, assembly = S.bp, S.bq, S.assembly
+    if dl_half is None:
+        dl_half = w["dl"](t + 0.5 * dt) if w.get("dl") is not None else (S.dl_p, S.dl_q, None, None)
+    if dl_next is None:
+        dl_next = w["dl"](t + dt)[:2] if w.get("dl") is not None else (S.dl_p, S.dl_q)
+    q_h, th_h, g2h, _ = _stage_update(w, S.q, S.theta, U0, assembly, bp, bq, 0.5 * dt,
+                                      dl_half[0], dl_half[1], delta)
+    S2 = System(w, q=q_h, theta=th_h, dl=tuple(dl_half), t=t + 0.5 * dt)
+    b2 = S2.rhs()
+    y1, its1, hist1 = S2.gmres(b=b2, x0=S2.apply_preconditioner(b2), tol=solve_tol)
+    lam1, U1, phi1 = S2.split(y1)
+    U1 = U1.reshape(-1, 6)
+    q_n, th_n, g2, g2a = _stage_update(w, S.q, S.theta, U1, assembly, bp, bq, dt, dl_next[0], dl_next[1],
+                                       delta)
+    info = dict(U=U1, lam=lam1, phi=phi1, U0=U0, q_half=q_h, theta_half=th_h, gmres_iters=its0 + its1,
+                residual=max(hist0[-1], hist1[-1]), g2_before=g2, g2_after=g2a, g2_half=g2h, y=y1)
+    return q_n, th_n, info

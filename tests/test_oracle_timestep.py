@@ -133,3 +133,59 @@ def test_open_chain_needs_no_correction():
     q, th, info = ts.euler_step(w, w["q"], w["theta"], 0.0, 1e-2, delta=1e-10)
     assert info["g2_before"] < 1e-24
     assert info["corr_iters"] == {}
+
+
+def _two_free_bodies():
+    # two icosahedral shells 2.6 apart in free space under constant forces
+    # and torques: the motion is nonlinear only through their hydrodynamic
+    # coupling, which is smooth at this separation
+    from oracle.kinematics import quat_from_rotvec
+    ico = workloads.icosahedron(0.5)
+    q = np.array([[0.0, 0.0, 0.0], [2.5, 0.5, -0.3]])
+    th = np.stack([quat_from_rotvec(np.array([0.3, 0.2, -0.1])), quat_from_rotvec(np.array([-0.5, 0.1, 0.7]))])
+    F = np.array([[1.0, 0.5, -0.2, 0.3, -0.4, 0.8], [-0.7, 0.2, 0.4, -0.6, 0.5, 0.2]])
+    return dict(name="two", eta=1.0, a=0.1, wall=0, q=q, theta=th, blob_offset=np.array([0, 12, 24]),
+                rho=np.concatenate([ico, ico]), F=F, assembly=np.array([0, 1]),
+                body_p=np.zeros(0, int), body_q=np.zeros(0, int), joints=np.zeros((0, 3)), dl=None)
+
+
+def _integrate(stepper, w, T, N):
+    # passive links: body-frame link vectors from the joints at the initial
+    # pose, kept for every step
+    S0 = System(w)
+    dl0 = (S0.dl_p, S0.dl_q, None, None)
+    q, th = w["q"].copy(), w["theta"].copy()
+    dt = T / N
+    for k in range(N):
+        q, th, _ = stepper(w, q, th, k * dt, dt, solve_tol=1e-13, dl_now=dl0)
+    return q, th
+
+
+def test_midpoint_step_is_second_order_and_euler_first():
+    # error at T against a 128-step midpoint reference, halving dt: the
+    # explicit midpoint scheme (App. "Midpoint scheme") divides the error by
+    # 4, Euler (Sec. 4.3) by 2
+    w = _two_free_bodies()
+    T = 2.0
+    qr, thr = _integrate(ts.midpoint_step, w, T, 128)
+    for stepper, lo, hi in ((ts.midpoint_step, 3.6, 4.5), (ts.euler_step, 1.85, 2.15)):
+        errs = []
+        for N in (4, 8, 16):
+            q, th = _integrate(stepper, w, T, N)
+            errs.append(max(np.abs(q - qr).max(), np.abs(th - thr).max()))
+        for e1, e2 in zip(errs, errs[1:]):
+            assert lo < e1 / e2 < hi, (stepper.__name__, errs)
+
+
+def test_midpoint_step_beats_euler_on_a_chain():
+    # three linked shells: the same number of steps is more accurate with
+    # the midpoint scheme, and the links stay closed (ball joints)
+    w = workloads.chains_free_space(3, n_chains=1, bodies_per_chain=3)
+    T = 2.0
+    qr, _ = _integrate(ts.midpoint_step, w, T, 64)
+    qm, thm = _integrate(ts.midpoint_step, w, T, 8)
+    qe, _ = _integrate(ts.euler_step, w, T, 8)
+    assert np.abs(qm - qr).max() < 0.5 * np.abs(qe - qr).max()
+    S = System(w)
+    g = ts.constraint_g(qm, thm, S.dl_p, S.dl_q, S.bp, S.bq)
+    assert np.abs(g).max() < 1e-9
