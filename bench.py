@@ -293,6 +293,33 @@ def learned_form(binding, W):
     return out
 
 
+def rk2_form(binding, W, steps=5, warmup=2):
+    """The explicit midpoint (RK2) step on the bench colony: two solves, two
+    reconstructions and corrections per step, FP64 and mixed, relative
+    residual 1e-8.  Host wall time per step (each call ends with the outputs
+    on the host), after warm-up steps."""
+    out = {"workload": WORKLOAD.replace("FP64, ", "") + ", explicit midpoint step"}
+    for prec in ("fp64", "mixed"):
+        w = W.diatom_colony(1)
+        s = binding.Solver.from_workload(w, t=0.0, tol=TOL, precision=prec)
+        times, iters, resid = [], [], []
+        for k in range(warmup + steps):
+            t = k * DT
+            if k:
+                dlp, dlq, dlpd, dlqd = w["dl"](t)
+                s.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd)
+            t0 = time.perf_counter()
+            _, _, _, st = s.step_rk2(t, DT, dl_half=w["dl"](t + 0.5 * DT), dl_next=w["dl"](t + DT)[:2])
+            if k >= warmup:
+                times.append(time.perf_counter() - t0)
+                iters.append(st["iterations"])
+                resid.append(st["rel_residual"])
+        s.close()
+        out[prec] = {"ms_per_step": 1e3 * statistics.mean(times), "gmres_iterations_per_step": statistics.mean(iters),
+                     "max_rel_residual": max(resid)}
+    return out
+
+
 def batched_form(torch, binding, W, stream, steps=2):
     """One handle holding the 256 free-space chain suspensions (blob counts
     log-uniform in [500, 20,000], 1.41 M blobs), mixed precision, solved
@@ -454,6 +481,7 @@ def run_ours(args):
     compared = products_compared(binding, W, fp32_peak, fp64_peak) if world == 1 else None
     batched = batched_form(torch, binding, W, stream) if world == 1 else None
     learned_res = learned_form(binding, W) if world == 1 else None
+    rk2_res = rk2_form(binding, W) if world == 1 else None
     fpp = binding.flops_per_pair(1)
     avg_launch_s = (mob_ms * 1e-3) / max(mob_launches, 1)
     achieved = nb * nb * fpp / avg_launch_s
@@ -499,7 +527,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks,
             "matvec_at_scale": at_scale, "products_compared": compared, "batched_form": batched,
-            "learned_form": learned_res}
+            "learned_form": learned_res, "rk2_form": rk2_res}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

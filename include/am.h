@@ -194,6 +194,30 @@ AM_API int am_solve_step(am_handle* h, double t, double dt,
                          am_step_stats* stats,
                          double* U_out, double* phi_out, double* lambda_out);
 
+/* One explicit midpoint (RK2) step of App. "Midpoint scheme" from t to
+ * t + dt: solve at t (warm-started), move each articulated body's centre and
+ * orientations by dt/2 with those velocities and reconstruct (with the
+ * nonlinear correction when ||g*||^2 >= corr_tol) using the link vectors at
+ * t + dt/2, solve at that midpoint, then move the pose at t by dt with the
+ * midpoint velocities and reconstruct and correct with the link vectors at
+ * t + dt.
+ *   dl_p_half, dl_q_half          3P each: body-frame link vectors at
+ *                                 t + dt/2, or NULL to keep the current ones
+ *   dl_p_half_dot, dl_q_half_dot  3P each: their time derivatives (active
+ *                                 links: required; passive links: NULL)
+ *   dl_p_next, dl_q_next          3P each: link vectors at t + dt, or NULL
+ * Outputs (any may be NULL) are the midpoint solution (the velocities used
+ * for the update).  stats: iterations and times of both solves summed,
+ * rel_residual the larger, g2 of the final reconstruction.  As for
+ * am_solve_step, the link derivatives for t + dt must be set by
+ * am_set_constraints before the next step.  Errors: as am_solve_step. */
+AM_API int am_solve_step_rk2(am_handle* h, double t, double dt,
+                             const double* dl_p_half, const double* dl_q_half,
+                             const double* dl_p_half_dot, const double* dl_q_half_dot,
+                             const double* dl_p_next, const double* dl_q_next,
+                             am_step_stats* stats,
+                             double* U_out, double* phi_out, double* lambda_out);
+
 /* Current bodies (after the last step): q 3M, theta 4M; either may be NULL. */
 AM_API int am_get_bodies(am_handle* h, int system, double* q, double* theta);
 

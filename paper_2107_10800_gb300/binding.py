@@ -58,6 +58,8 @@ SIGNATURES = {
     "am_solve": (ctypes.c_int, [_vp, ctypes.POINTER(StepStats), _dp, _dp, _dp]),
     "am_solve_step": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _dp, _dp,
                                      ctypes.POINTER(StepStats), _dp, _dp, _dp]),
+    "am_solve_step_rk2": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
+                                         ctypes.POINTER(StepStats), _dp, _dp, _dp]),
     "am_get_bodies": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
     "am_get_blobs": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "am_apply_mobility": (ctypes.c_int, [_vp, _dp, _dp]),
@@ -238,6 +240,29 @@ class Solver:
             a1, p1 = _d(dl_next[0], 3 * self.P)
             a2, p2 = _d(dl_next[1], 3 * self.P)
         self._check(lib().am_solve_step(self.h, t, dt, p1, p2, ctypes.byref(st), Up, pp, lp),
+                    allow_nc=True)
+        return U.reshape(-1, 6), phi.reshape(-1, 3), lam.reshape(-1, 3), st.as_dict()
+
+    def step_rk2(self, t, dt, dl_half=None, dl_next=None):
+        """Explicit midpoint step; dl_half = (dlp, dlq) or (dlp, dlq, dlpd,
+        dlqd) at t + dt/2, dl_next = (dlp, dlq) at t + dt (None: keep)."""
+        st = StepStats()
+        U, Up = _out(6 * self.M)
+        phi, pp = _out(3 * self.P)
+        lam, lp = _out(3 * self.Nb)
+        keep = []
+
+        def arr(v):
+            if v is None:
+                return None
+            a, p = _d(v, 3 * self.P)
+            keep.append(a)
+            return p
+        h = list(dl_half) if dl_half is not None else [None, None]
+        h += [None] * (4 - len(h))
+        nx = list(dl_next) if dl_next is not None else [None, None]
+        self._check(lib().am_solve_step_rk2(self.h, t, dt, arr(h[0]), arr(h[1]), arr(h[2]), arr(h[3]),
+                                            arr(nx[0]), arr(nx[1]), ctypes.byref(st), Up, pp, lp),
                     allow_nc=True)
         return U.reshape(-1, 6), phi.reshape(-1, 3), lam.reshape(-1, 3), st.as_dict()
 

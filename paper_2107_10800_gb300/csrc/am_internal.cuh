@@ -218,6 +218,7 @@ struct am_handle {
 
     // device: step
     double *d_qnew = nullptr, *d_thnew = nullptr, *d_corr = nullptr, *d_red = nullptr;
+    double *d_q0 = nullptr, *d_th0 = nullptr;   // pose at t_k during a midpoint step
     double *d_zbuf = nullptr, *d_cbuf = nullptr;
     long long* d_corr_off = nullptr;
     int* d_iters = nullptr;

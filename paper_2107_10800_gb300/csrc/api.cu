@@ -121,7 +121,7 @@ void free_bodies(am_handle* h) {
     dfree(&h->d_pc_w); dfree(&h->d_pc_Uhat); dfree(&h->d_mv);
     dfree(&h->d_pcw_body); dfree(&h->d_pcw_chunk); dfree(&h->d_pcw_off); dfree(&h->d_ytp);
     h->n_pcw = 0;
-    dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters);
+    dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters); dfree(&h->d_q0); dfree(&h->d_th0);
 }
 
 void free_solver(am_handle* h) {
@@ -539,6 +539,7 @@ int build_layout(am_handle* h, int M, int Nb, int NA, int maxb, const double* q,
     CK(dalloc(&h->d_minv_off, M + 1)); CK(dalloc(&h->d_pc_w, 3 * (size_t)Nb));
     CK(dalloc(&h->d_pc_Uhat, 6 * (size_t)M));
     CK(dalloc(&h->d_qnew, 3 * (size_t)M)); CK(dalloc(&h->d_thnew, 4 * (size_t)M));
+    CK(dalloc(&h->d_q0, 3 * (size_t)M)); CK(dalloc(&h->d_th0, 4 * (size_t)M));
     CK(dalloc(&h->d_iters, NA));
     if (h->h_iters) cudaFreeHost(h->h_iters);
     h->h_iters = nullptr;
@@ -945,6 +946,125 @@ extern "C" AM_API int am_solve_step(am_handle* h, double t, double dt, const dou
     h->pc_valid = false;
     if (stats) *stats = st;
     if (rs == AM_ERR_NOT_CONVERGED) set_err(h, rs, "am_solve_step: GMRES did not reach the tolerance");
+    return rs;
+}
+
+// Link vectors at the end of a (half) step into d_dlp1/d_dlq1: the given
+// host arrays, or the current ones.
+static int set_end_links(am_handle* h, const double* dlp, const double* dlq) {
+    if (!h->P) return AM_OK;
+    cudaStream_t s = h->stream;
+    if (dlp) {
+        CK(h2d(h->d_dlp1, dlp, 3 * (size_t)h->P, s));
+        CK(h2d(h->d_dlq1, dlq, 3 * (size_t)h->P, s));
+    } else {
+        CK(cudaMemcpyAsync(h->d_dlp1, h->d_dlp, 3 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(h->d_dlq1, h->d_dlq, 3 * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    return AM_OK;
+}
+
+// One solve at the current pose (warm-started) with its timings into st.
+static int stage_solve(am_handle* h, const char* who, am_step_stats* st, int* rs) {
+    cudaStream_t s = h->stream;
+    int rc = prepare(h, who, true, st);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev[2], s));
+    *rs = am::solve(h, st);
+    CK(cudaEventRecord(h->ev[3], s));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->d_xprev, h->d_x, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    h->have_warm = true;
+    CK(cudaEventSynchronize(h->ev[3]));
+    st->ms_gmres = elapsed(h->ev[2], h->ev[3]);
+    return AM_OK;
+}
+
+extern "C" AM_API int am_solve_step_rk2(am_handle* h, double t, double dt, const double* dlp_half,
+                                        const double* dlq_half, const double* dlpd_half,
+                                        const double* dlqd_half, const double* dlp_next,
+                                        const double* dlq_next, am_step_stats* stats, double* U, double* phi,
+                                        double* lam) {
+    const char* who = "am_solve_step_rk2";
+    if (!h) return AM_ERR_ARG;
+    (void)t;
+    int rc = check_handle(h, who, true);
+    if (rc) return rc;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(h, AM_ERR_ARG, std::string(who) + ": dt must be > 0");
+    if ((dlp_half == nullptr) != (dlq_half == nullptr) || (dlp_next == nullptr) != (dlq_next == nullptr) ||
+        (dlpd_half == nullptr) != (dlqd_half == nullptr))
+        return set_err(h, AM_ERR_ARG, std::string(who) + ": give both link arrays of a pair or neither");
+    if (h->P && h->active_links && !dlpd_half)
+        return set_err(h, AM_ERR_ARG, std::string(who) + ": active links need their derivatives at the midpoint");
+    if (!h->active_links && dlpd_half)
+        return set_err(h, AM_ERR_ARG, std::string(who) + ": passive links take no derivatives");
+    if (!h->links_connected)
+        return set_err(h, AM_ERR_ARG, std::string(who) + ": an articulated body of several bodies has no links "
+                                                          "joining them (set them with am_set_constraints)");
+    const long long l0 = am::g_launches.load();
+    h->pairs = 0;
+    cudaStream_t s = h->stream;
+    am_step_stats s1{}, s2{}, uh{}, uf{};
+    int rs1 = AM_OK, rs2 = AM_OK;
+    // stage 1: velocities at t_k
+    rc = stage_solve(h, who, &s1, &rs1);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->d_q0, h->d_q, 3 * h->M * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->d_th0, h->d_theta, 4 * h->M * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // half step to the midpoint pose (reconstruction and correction at t_k+1/2)
+    rc = set_end_links(h, dlp_half, dlq_half);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev[4], s));
+    rc = am::advance(h, 0.5 * dt, &uh);
+    CK(cudaEventRecord(h->ev[5], s));
+    if (rc) return rc;
+    rc = device_flags_to_status(h, who);
+    if (rc) return rc;
+    if (dlpd_half) {
+        CK(h2d(h->d_dlpd, dlpd_half, 3 * (size_t)h->P, s));
+        CK(h2d(h->d_dlqd, dlqd_half, 3 * (size_t)h->P, s));
+    }
+    float ms_half = 0.f;
+    CK(cudaEventSynchronize(h->ev[5]));
+    cudaEventElapsedTime(&ms_half, h->ev[4], h->ev[5]);
+    // stage 2: velocities at the midpoint (warm start from stage 1)
+    rc = stage_solve(h, who, &s2, &rs2);
+    if (rc) return rc;
+    rc = copy_outputs(h, U, phi, lam);
+    if (rc) return rc;
+    // full step from the pose at t_k with the midpoint velocities
+    CK(cudaMemcpyAsync(h->d_q, h->d_q0, 3 * h->M * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->d_theta, h->d_th0, 4 * h->M * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rc = set_end_links(h, dlp_next, dlq_next);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev[4], s));
+    rc = am::advance(h, dt, &uf);
+    CK(cudaEventRecord(h->ev[5], s));
+    CK(cudaGetLastError());
+    if (rc) return rc;
+    rc = device_flags_to_status(h, who);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    am_step_stats st{};
+    st.iterations = s1.iterations + s2.iterations;
+    st.restarts = s1.restarts + s2.restarts;
+    st.rel_residual = std::max(s1.rel_residual, s2.rel_residual);
+    st.rel_residual0 = s2.rel_residual0;
+    st.constraint_residual = std::max(s1.constraint_residual, s2.constraint_residual);
+    st.g2_before = uf.g2_before;
+    st.g2_after = uf.g2_after;
+    st.corr_iterations = std::max(uh.corr_iterations, uf.corr_iterations);
+    st.ms_precond = s1.ms_precond + s2.ms_precond;
+    st.ms_gmres = s1.ms_gmres + s2.ms_gmres;
+    st.ms_update = ms_half + elapsed(h->ev[4], h->ev[5]);
+    st.learned_systems = s1.learned_systems;
+    st.pairs = h->pairs;
+    st.kernel_launches = (int)(am::g_launches.load() - l0);
+    const int rs = rs1 != AM_OK ? rs1 : rs2;
+    st.status = rs;
+    h->pc_valid = false;
+    if (stats) *stats = st;
+    if (rs == AM_ERR_NOT_CONVERGED) set_err(h, rs, std::string(who) + ": GMRES did not reach the tolerance");
     return rs;
 }
 
