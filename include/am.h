@@ -235,6 +235,16 @@ AM_API int am_apply_mobility(am_handle* h, const double* lambda, double* u);
  * arithmetic, no bodies), AM_ERR_CUDA. */
 AM_API int am_apply_mobility_ex(am_handle* h, const double* lambda, double* u, int arithmetic);
 
+/* Layout of the all-pairs product of h instead of the autotuned one: work
+ * items of 128 x targets_per_thread targets (2: two targets per thread in
+ * paired FP32 lanes; mixed precision only, FP64 handles use 1) against
+ * source chunks of source_chunk blobs (0: a default that fills the GPU).
+ * targets_per_thread = 0 restores autotuning before the next product.  The
+ * layout is rebuilt (and autotuned) whenever the bodies change.  A
+ * measurement and testing aid, not in the paper.  Errors: AM_ERR_ARG (no
+ * bodies, values out of range), AM_ERR_CUDA. */
+AM_API int am_set_mobility_layout(am_handle* h, int targets_per_thread, int source_chunk);
+
 /* y -> A y for the full operator of Eq. linear_system at the current pose
  * (y and Ay: 3Nb + 6M + 3P, ordered (lambda, U, phi)). */
 AM_API int am_apply_operator(am_handle* h, const double* y, double* Ay);

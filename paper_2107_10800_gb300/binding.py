@@ -64,6 +64,7 @@ SIGNATURES = {
     "am_get_blobs": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "am_apply_mobility": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_apply_mobility_ex": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int]),
+    "am_set_mobility_layout": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "am_apply_operator": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_apply_precond": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_rpy_matvec": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
@@ -300,6 +301,10 @@ class Solver:
         u, up = _out(3 * self.Nb)
         self._check(lib().am_apply_mobility_ex(self.h, lp, up, mode))
         return u.reshape(-1, 3)
+
+    def set_mobility_layout(self, targets_per_thread, source_chunk=0):
+        """Fix the all-pairs product layout (0 targets per thread: autotune)."""
+        self._check(lib().am_set_mobility_layout(self.h, targets_per_thread, source_chunk))
 
     def apply_operator(self, y):
         ya, yp = _d(y, self.n)

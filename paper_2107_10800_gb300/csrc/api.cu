@@ -1143,6 +1143,23 @@ extern "C" AM_API int am_apply_mobility_ex(am_handle* h, const double* lam, doub
     return AM_OK;
 }
 
+extern "C" AM_API int am_set_mobility_layout(am_handle* h, int targets_per_thread, int source_chunk) {
+    if (!h) return AM_ERR_ARG;
+    int rc = check_handle(h, "am_set_mobility_layout", true);
+    if (rc) return rc;
+    if (targets_per_thread < 0 || targets_per_thread > 2 || source_chunk < 0)
+        return set_err(h, AM_ERR_ARG, "am_set_mobility_layout: targets_per_thread must be 0, 1 or 2 and "
+                                      "source_chunk >= 0");
+    if (targets_per_thread == 0) {
+        h->mv_tuned = false;  // tuned again before the next product
+        return AM_OK;
+    }
+    if (am::mobility_layout(h, targets_per_thread, source_chunk))
+        return set_err(h, AM_ERR_CUDA, "am_set_mobility_layout: device allocation failed");
+    h->mv_tuned = true;
+    return AM_OK;
+}
+
 extern "C" AM_API int am_apply_operator(am_handle* h, const double* y, double* Ay) {
     if (!h) return AM_ERR_ARG;
     int rc = check_handle(h, "am_apply_operator", true);

@@ -471,6 +471,141 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
     }
 }
 
+// ---- paired FP32 arithmetic: two targets per thread in the lanes of float2
+// registers (__ffma2_rn and friends: one instruction for both targets), the
+// source values in shared memory already duplicated and negated so that one
+// 128-bit load gives ready register pairs.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+
+// free-space pair for r >= 2a in both lanes (rpy_pair.cuh, far branch)
+__device__ __forceinline__ void pair_free_far2(float2 dx, float2 dy, float2 dz, float2 r2, float2 lx, float2 ly,
+                                               float2 lz, float2 kf2, float2 nkf3, float2& ux, float2& uy,
+                                               float2& uz) {
+    const float2 one = bc2(1.f);
+    const float2 ri = rsq2(r2);
+    const float2 ri2 = mul2(ri, ri);
+    const float2 c1 = mul2(ri, fma2(kf2, ri2, one));
+    const float2 c2 = mul2(mul2(ri, ri2), fma2(nkf3, ri2, one));
+    const float2 sdl = mul2(c2, fma2(dx, lx, fma2(dy, ly, mul2(dz, lz))));
+    ux = fma2(c1, lx, fma2(sdl, dx, ux));
+    uy = fma2(c1, ly, fma2(sdl, dy, uy));
+    uz = fma2(c1, lz, fma2(sdl, dz, uz));
+}
+
+// wall image part of rpy_pair.cuh in both lanes
+__device__ __forceinline__ void pair_image2(float2 Rx, float2 Ry, float2 Rz, float2 x3, float2 h, float2 lx,
+                                            float2 ly, float2 lz, float2 a2, float2& ux, float2& uy, float2& uz) {
+    const float2 s = rsq2(fma2(Rx, Rx, fma2(Ry, Ry, mul2(Rz, Rz))));
+    const float2 s2 = mul2(s, s);
+    const float2 hs = mul2(h, s);
+    const float2 u = mul2(hs, mul2(x3, s));
+    const float2 ez = mul2(Rz, s);
+    const float2 ez2 = mul2(ez, ez);
+    const float2 A = mul2(a2, s2);
+    const float2 A2 = mul2(A, A);
+    const float2 t1 = mul2(A, ez2);
+    const float2 t2 = mul2(A2, ez2);
+    const float2 cI = fma2(bc2(-10.f / 3.f), t2, fma2(bc2(2.f / 3.f), A2, fma2(bc2(2.f), t1,
+                      fma2(bc2(-2.f / 3.f), A, fma2(bc2(-2.f), u, bc2(-1.f))))));
+    const float2 cRR = fma2(bc2(70.f / 3.f), t2, fma2(bc2(-10.f / 3.f), A2, fma2(bc2(-10.f), t1,
+                       fma2(bc2(2.f), A, fma2(bc2(6.f), u, bc2(-1.f))))));
+    const float2 inner = fma2(bc2(20.f / 3.f), A2, fma2(bc2(-2.f), cRR, bc2(-2.f)));
+    const float2 hs2 = add2(hs, hs);
+    const float2 cRz = fma2(ez, inner, hs2);
+    const float2 czR = fma2(mul2(bc2(-20.f / 3.f), A2), ez, hs2);
+    const float2 czz = fma2(bc2(-4.f), mul2(hs, hs), fma2(bc2(20.f), t2, fma2(bc2(-8.f / 3.f), A2,
+                       mul2(bc2(-4.f), t1))));
+    const float2 rx = mul2(Rx, s), ry = mul2(Ry, s);
+    const float2 dotR = fma2(rx, lx, fma2(ry, ly, mul2(ez, lz)));
+    const float2 t = fma2(cRR, dotR, mul2(cRz, lz));
+    ux = fma2(s, fma2(cI, lx, mul2(t, rx)), ux);
+    uy = fma2(s, fma2(cI, ly, mul2(t, ry)), uy);
+    uz = fma2(s, fma2(cI, lz, fma2(t, ez, fma2(czR, dotR, mul2(czz, lz)))), uz);
+}
+
+// The mixed product with two targets per thread (items of 256 targets):
+// target t0 + threadIdx.x in lane x, t0 + 128 + threadIdx.x in lane y.
+// Differences always include the lo parts of the positions; pairs closer
+// than 2a in either lane (same-body neighbours) take the scalar formula.
+template <bool WALL>
+__global__ void __launch_bounds__(kThreads, 4)
+rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
+                   const double* __restrict__ lam, double* __restrict__ part,
+                   const MvItem* __restrict__ items, int n_items, int* __restrict__ counter,
+                   RpyK<float> k) {
+    // per source: (-hx,-hx,-hy,-hy) (-hz,-hz,-ox,-ox) (-oy,-oy,-oz,-oz)
+    // (lx,lx,ly,ly) (lz,lz,hz,hz)
+    __shared__ float4 sq[5][kTile];
+    __shared__ int s_item;
+    const float2 kf2 = bc2(k.kf2), nkf3 = bc2(-k.kf3), a2 = bc2(k.a2);
+    for (int round = 0;; ++round) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(counter, 1);
+        __syncthreads();
+        const int itn = s_item;
+        if (itn >= n_items) break;
+        const MvItem m = items[itn];
+        const int i0 = m.t0 + threadIdx.x, i1 = m.t0 + kThreads + threadIdx.x;
+        const float4 h0 = (i0 < m.t1) ? hi[i0] : make_float4(0.f, 0.f, 1.f, 0.f);
+        const float4 h1 = (i1 < m.t1) ? hi[i1] : make_float4(0.f, 0.f, 1.f, 0.f);
+        const float4 l0 = (i0 < m.t1) ? lo[i0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 l1 = (i1 < m.t1) ? lo[i1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 HX = make_float2(h0.x, h1.x), HY = make_float2(h0.y, h1.y), HZ = make_float2(h0.z, h1.z);
+        const float2 LX = make_float2(l0.x, l1.x), LY = make_float2(l0.y, l1.y), LZ = make_float2(l0.z, l1.z);
+        double U[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        for (int jt = m.j0; jt < m.j1; jt += kTile) {
+            const int cnt = min(kTile, m.j1 - jt);
+            __syncthreads();
+            if (threadIdx.x < cnt) {
+                const int j = jt + threadIdx.x;
+                const float4 h = hi[j], o = lo[j];
+                const float lx = (float)lam[3 * (size_t)j], ly = (float)lam[3 * (size_t)j + 1],
+                            lz = (float)lam[3 * (size_t)j + 2];
+                sq[0][threadIdx.x] = make_float4(-h.x, -h.x, -h.y, -h.y);
+                sq[1][threadIdx.x] = make_float4(-h.z, -h.z, -o.x, -o.x);
+                sq[2][threadIdx.x] = make_float4(-o.y, -o.y, -o.z, -o.z);
+                sq[3][threadIdx.x] = make_float4(lx, lx, ly, ly);
+                sq[4][threadIdx.x] = make_float4(lz, lz, h.z, h.z);
+            }
+            __syncthreads();
+            float2 ux = bc2(0.f), uy = bc2(0.f), uz = bc2(0.f);
+#pragma unroll 2
+            for (int q = 0; q < cnt; ++q) {
+                const float4 v0 = sq[0][q], v1 = sq[1][q], v2 = sq[2][q], v3 = sq[3][q], v4 = sq[4][q];
+                const float2 dx = add2(add2(HX, make_float2(v0.x, v0.y)), add2(LX, make_float2(v1.z, v1.w)));
+                const float2 dy = add2(add2(HY, make_float2(v0.z, v0.w)), add2(LY, make_float2(v2.x, v2.y)));
+                const float2 dz = add2(add2(HZ, make_float2(v1.x, v1.y)), add2(LZ, make_float2(v2.z, v2.w)));
+                const float2 lx = make_float2(v3.x, v3.y), ly = make_float2(v3.z, v3.w), lz = make_float2(v4.x, v4.y);
+                const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                if (r2.x < k.four_a2 || r2.y < k.four_a2) {
+                    pair_free_r2<float>(dx.x, dy.x, dz.x, r2.x, lx.x, ly.x, lz.x, k, ux.x, uy.x, uz.x);
+                    pair_free_r2<float>(dx.y, dy.y, dz.y, r2.y, lx.y, ly.y, lz.y, k, ux.y, uy.y, uz.y);
+                } else {
+                    pair_free_far2(dx, dy, dz, r2, lx, ly, lz, kf2, nkf3, ux, uy, uz);
+                }
+                if (WALL) {
+                    const float2 hz = make_float2(v4.z, v4.w);
+                    pair_image2(dx, dy, add2(HZ, hz), HZ, hz, lx, ly, lz, a2, ux, uy, uz);
+                }
+            }
+            U[0][0] += (double)ux.x; U[0][1] += (double)uy.x; U[0][2] += (double)uz.x;
+            U[1][0] += (double)ux.y; U[1][1] += (double)uy.y; U[1][2] += (double)uz.y;
+        }
+        if (i0 < m.t1) {
+            double* o = part + m.pbase + 3 * (size_t)(i0 - m.tbase);
+            o[0] = k.A1 * U[0][0]; o[1] = k.A1 * U[0][1]; o[2] = k.A1 * U[0][2];
+        }
+        if (i1 < m.t1) {
+            double* o = part + m.pbase + 3 * (size_t)(i1 - m.tbase);
+            o[0] = k.A1 * U[1][0]; o[1] = k.A1 * U[1][1]; o[2] = k.A1 * U[1][2];
+        }
+    }
+}
+
 // u_i = sum over the chunks of i's system of the partial sums
 __global__ void k_sum_items(int Nb, const double* __restrict__ part, const int* __restrict__ sys_of_blob,
                             const int* __restrict__ sys_blob0, const int* __restrict__ sys_nb,
@@ -554,9 +689,9 @@ int mobility_layout(am_handle* h, int tpt, int chunk) {
     h->mv_part_total = off;
     if (h->cfg.precision == AM_MIXED) {
         if (h->cfg.wall)
-            h->mv_grid = tpt == 2 ? resident_grid(rpy_items_mixed<true, 2>) : resident_grid(rpy_items_mixed<true, 1>);
+            h->mv_grid = tpt == 2 ? resident_grid(rpy_items_mixed_x2<true>) : resident_grid(rpy_items_mixed<true, 1>);
         else
-            h->mv_grid = tpt == 2 ? resident_grid(rpy_items_mixed<false, 2>) : resident_grid(rpy_items_mixed<false, 1>);
+            h->mv_grid = tpt == 2 ? resident_grid(rpy_items_mixed_x2<false>) : resident_grid(rpy_items_mixed<false, 1>);
     } else {
         h->mv_grid = h->cfg.wall ? resident_grid(rpy_items_f64<true>) : resident_grid(rpy_items_f64<false>);
     }
@@ -593,11 +728,15 @@ void launch_items(am_handle* h, const double* lam, int mode) {
 #define AM_MIXED_ITEMS(W, T)                                                                             \
     rpy_items_mixed<W, T><<<h->mv_grid, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items, \
                                                            h->n_items, h->d_item_counter, k)
+#define AM_MIXED_X2(W)                                                                               \
+    rpy_items_mixed_x2<W><<<h->mv_grid, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items,  \
+                                                           h->n_items, h->d_item_counter, k)
         if (h->cfg.wall) {
-            if (h->mv_tpt == 2) AM_MIXED_ITEMS(true, 2); else AM_MIXED_ITEMS(true, 1);
+            if (h->mv_tpt == 2) AM_MIXED_X2(true); else AM_MIXED_ITEMS(true, 1);
         } else {
-            if (h->mv_tpt == 2) AM_MIXED_ITEMS(false, 2); else AM_MIXED_ITEMS(false, 1);
+            if (h->mv_tpt == 2) AM_MIXED_X2(false); else AM_MIXED_ITEMS(false, 1);
         }
+#undef AM_MIXED_X2
 #undef AM_MIXED_ITEMS
     }
     count_launch();

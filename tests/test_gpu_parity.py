@@ -88,6 +88,34 @@ def test_mobility_df64_overlap_and_contact():
         assert rel(s.apply_mobility_ex(lam, "df64"), ref) <= DF64_MATVEC
 
 
+@pytest.mark.parametrize("wall", [0, 1])
+@pytest.mark.parametrize("layout", [(1, 0), (2, 0), (2, 96), (1, 300), (2, 300)])
+def test_mobility_mixed_layouts_match_oracle(wall, layout):
+    # every work-item layout of the mixed product, including two targets per
+    # thread in paired FP32 lanes, ragged items and overlapping blobs
+    r, lam = W.random_blobs(400 + wall, 1000, a=0.1, wall=wall)
+    r = r + np.array([250.0, -125.0, 0.0])
+    r[1] = r[0] + np.array([0.05, 0.0, 0.0])      # overlapping pair
+    r[200] = r[1] + np.array([0.0, 0.2, 0.0])     # contact at 2a
+    s = loose_blobs_solver(r, 0.1, wall, "mixed")
+    s.set_mobility_layout(*layout)
+    ref = om.mobility_matvec(r, lam, 0.1, 1.0, wall)
+    for _ in range(2):
+        assert rel(s.apply_mobility_ex(lam, "mixed"), ref) <= MIXED
+    assert rel(s.apply_mobility_ex(lam, "df64"), ref) <= DF64_MATVEC
+
+
+def test_solve_mixed_with_paired_layout_matches_oracle():
+    w = small_colony(4)
+    S = System(w, t=0.02)
+    s = binding.Solver.from_workload(w, t=0.02, tol=1e-9, precision="mixed")
+    s.set_mobility_layout(2, 64)
+    U, phi, lam, st = s.solve()
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-9
+    lam_o, U_o, _ = S.split(S.solve_formal())
+    assert rel(U.ravel(), U_o) <= MIXED
+
+
 def test_mobility_overlap_and_contact():
     # overlapping blobs (r < 2a), exact contact (r = 2a) and coincident
     # free-space blobs (r = 0 between distinct blobs gives mu0 I)
