@@ -35,6 +35,11 @@ TOL = 1e-8
 WORKLOAD = ("diatom colony above a no-slip wall: 32 rods of 2x40 blobs (2,560 blobs, a=0.1), "
             "62 sliding links, dt=1e-3, FP64, GMRES relative residual 1e-8")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+# DRAM bytes (read + write) of one launch of the FP64 wall product on this
+# colony, from an ncu capture of the bench's own timed steps
+# (dram__bytes_read.sum + dram__bytes_write.sum); None where no capture of
+# the kernel as it now stands exists
+TRAFFIC_BYTES = {"fp64": 206080, "mixed": None}
 
 
 def parse():
@@ -173,44 +178,59 @@ def run_reference(args):
 
 
 def matvec_at_scale(torch, binding, W, stream, fp32_peak, fp64_peak):
-    """The all-pairs wall product at the bacteria-suspension scale (1,000
-    bacteria, 360,000 blobs, a = 0.05): mixed precision on all blobs, FP64 on
-    the first 40,000 (an FP64 launch on all blobs takes seconds).  Timed with
-    CUDA events around each am_rpy_matvec call, after warm-up."""
+    """The solver's all-pairs wall product at the bacteria-suspension scale
+    (1,000 bacteria, 360,000 blobs, a = 0.05): the mixed work-queue kernel
+    with two targets per thread in paired FP32 lanes and 4,096-source chunks
+    on all blobs, the FP64 kernel on the first 40,000 (an FP64 product on
+    all blobs takes about 20 s).  The blobs are single-blob bodies of one
+    handle; kernel time from CUDA events around each launch
+    (am_mobility_timing), after a warm-up product."""
     w = W.bacteria_wall(1)
     s = binding.Solver.from_workload(w, precision="mixed")
-    r = s.blobs()
+    R = s.blobs()
     s.close()
     out = {"workload": "bacteria above a wall: 1,000 x (200-blob head + 16 x 10-blob flagellum), "
                        "360,000 blobs, a=0.05"}
-    lam = np.random.default_rng(0).standard_normal(r.shape)
     fpp = binding.flops_per_pair(1)
-    for prec, n, reps, peak in (("mixed", len(r), 5, fp32_peak), ("fp64", 40_000, 3, fp64_peak)):
-        dr = torch.tensor(r[:n], device="cuda")
-        dl = torch.tensor(lam[:n], device="cuda")
-        du = torch.empty_like(dr)
-        nbytes = binding.rpy_matvec_workspace(n, prec)
-        work = torch.empty(nbytes // 8 + 64, dtype=torch.float64, device="cuda")
-        wp = (work.data_ptr() + 255) // 256 * 256
-        call = lambda: binding.rpy_matvec_ptr(dr.data_ptr(), dl.data_ptr(), du.data_ptr(), n,
-                                              w["eta"], w["a"], 1, prec, wp, nbytes, stream.cuda_stream)
-        call()
-        torch.cuda.synchronize()
-        times = []
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            call()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1) * 1e-3)
-        t = statistics.median(times)
+    for prec, n, layout, peak in (("mixed", len(R), (2, 4096), fp32_peak), ("fp64", 40_000, (1, 0), fp64_peak)):
+        r = R[:n]
+        s = binding.Solver(eta=w["eta"], a=w["a"], wall=1, precision=prec)
+        s.set_bodies(r, np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)), np.arange(n + 1), np.zeros((n, 3)),
+                     np.zeros((n, 6)), np.arange(n))
+        s.set_mobility_layout(*layout)
+        lam = np.random.default_rng(0).standard_normal(r.shape)
+        s.apply_mobility_ex(lam, prec)  # warm-up
+        s.mobility_timing(True)
+        for _ in range(2 if prec == "mixed" else 1):
+            s.apply_mobility_ex(lam, prec)
+        ms, launches = s.mobility_timing(False)
+        s.close()
+        t = ms * 1e-3 / max(launches, 1)
         pairs = float(n) * n
         out[prec] = {"blobs": n, "ms": t * 1e3, "pairs_per_s": pairs / t,
-                     "tflops": pairs * fpp / t / 1e12, "frac_of_fma_peak": pairs * fpp / t / peak}
-        del dr, dl, du, work
+                     "tflops": pairs * fpp / t / 1e12, "frac_of_fma_peak": pairs * fpp / t / peak,
+                     "kernel": "rpy_items_mixed_x2<wall>" if prec == "mixed" else "rpy_items_f64<wall>"}
     return out
+
+
+def steric_at_scale(binding, W, reps=3):
+    """The steric repulsion (soft potential between bacteria, cutoff 2a +
+    8 b with b = a, and the wall term) on the 1,000-bacteria suspension:
+    host time of am_steric_forces (pose, pair search, body sums, 8.6 MB of
+    forces back to the host), median of `reps` calls after a warm-up."""
+    w = W.bacteria_wall(1)
+    s = binding.Solver.from_workload(w, precision="mixed")
+    a = w["a"]
+    s.set_repulsion(0.1, a, 2 * a + 8 * a, 0.1, a)
+    s.steric_forces()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        f = s.steric_forces()
+        ts.append(time.perf_counter() - t0)
+    s.close()
+    return {"workload": "1,000 bacteria, 360,000 blobs above a wall; cutoff 10a",
+            "ms": 1e3 * statistics.median(ts), "blobs_with_force": int(np.count_nonzero(np.abs(f).sum(axis=1)))}
 
 
 def products_compared(binding, W, fp32_peak, fp64_peak, n=60_000):
@@ -479,6 +499,7 @@ def run_ours(args):
 
     at_scale = matvec_at_scale(torch, binding, W, stream, fp32_peak, fp64_peak)
     compared = products_compared(binding, W, fp32_peak, fp64_peak) if world == 1 else None
+    steric = steric_at_scale(binding, W) if world == 1 else None
     batched = batched_form(torch, binding, W, stream) if world == 1 else None
     learned_res = learned_form(binding, W) if world == 1 else None
     rk2_res = rk2_form(binding, W) if world == 1 else None
@@ -489,7 +510,7 @@ def run_ours(args):
     clocks = clk.summary()
     roofline = {"bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": TRAFFIC_BYTES[args.precision],
                 "kernel": "rpy_items_%s<wall>" % ("f64" if args.precision == "fp64" else "mixed"),
                 "flop_per_pair": fpp, "pairs_per_launch": nb * nb,
                 "launch_ms": avg_launch_s * 1e3, "launches": mob_launches,
@@ -527,7 +548,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks,
             "matvec_at_scale": at_scale, "products_compared": compared, "batched_form": batched,
-            "learned_form": learned_res, "rk2_form": rk2_res}
+            "learned_form": learned_res, "rk2_form": rk2_res, "steric": steric}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
