@@ -235,6 +235,25 @@ AM_API int am_apply_mobility(am_handle* h, const double* lambda, double* u);
  * arithmetic, no bodies), AM_ERR_CUDA. */
 AM_API int am_apply_mobility_ex(am_handle* h, const double* lambda, double* u, int arithmetic);
 
+/* Steric repulsion (Sec. 5.3 uses one between bacteria and with the wall
+ * without giving its form; this is the library's).  Between blobs of
+ * different articulated bodies closer than `cutoff`:
+ *     U(r) = eps (1 + (2a - r) / range)   r <  2a
+ *     U(r) = eps exp((2a - r) / range)    r >= 2a
+ * and, with a wall, on every blob at height h:
+ *     U_w(h) = eps_wall (1 + (a - h) / range_wall)   h <  a
+ *     U_w(h) = eps_wall exp((a - h) / range_wall)    h >= a
+ * The blob forces -grad U reach each body as force and torque about its
+ * tracking point (K^T f) and are added to its external force and torque at
+ * every solve and step.  eps = eps_wall = 0 turns it off (the default).
+ * Positions must stay below about 1e4 in magnitude (the pair search screens
+ * candidates in FP32).  Errors: AM_ERR_ARG (negative values, non-positive
+ * range with eps > 0, wall term without a wall). */
+AM_API int am_set_repulsion(am_handle* h, double eps, double range, double cutoff,
+                            double eps_wall, double range_wall);
+/* The steric blob forces (3Nb) at the current pose (zeros when off). */
+AM_API int am_steric_forces(am_handle* h, double* f);
+
 /* Layout of the all-pairs product of h instead of the autotuned one: work
  * items of 128 x targets_per_thread targets (2: two targets per thread in
  * paired FP32 lanes; mixed precision only, FP64 handles use 1) against

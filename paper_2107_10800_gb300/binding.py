@@ -65,6 +65,9 @@ SIGNATURES = {
     "am_apply_mobility": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_apply_mobility_ex": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int]),
     "am_set_mobility_layout": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "am_set_repulsion": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double]),
+    "am_steric_forces": (ctypes.c_int, [_vp, _dp]),
     "am_apply_operator": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_apply_precond": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_rpy_matvec": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
@@ -301,6 +304,15 @@ class Solver:
         u, up = _out(3 * self.Nb)
         self._check(lib().am_apply_mobility_ex(self.h, lp, up, mode))
         return u.reshape(-1, 3)
+
+    def set_repulsion(self, eps, range_, cutoff, eps_wall=0.0, range_wall=1.0):
+        """Steric repulsion between articulated bodies and with the wall."""
+        self._check(lib().am_set_repulsion(self.h, eps, range_, cutoff, eps_wall, range_wall))
+
+    def steric_forces(self):
+        f, fp = _out(3 * self.Nb)
+        self._check(lib().am_steric_forces(self.h, fp))
+        return f.reshape(-1, 3)
 
     def set_mobility_layout(self, targets_per_thread, source_chunk=0):
         """Fix the all-pairs product layout (0 targets per thread: autotune)."""

@@ -219,6 +219,11 @@ struct am_handle {
     // device: step
     double *d_qnew = nullptr, *d_thnew = nullptr, *d_corr = nullptr, *d_red = nullptr;
     double *d_q0 = nullptr, *d_th0 = nullptr;   // pose at t_k during a midpoint step
+
+    // steric repulsion (am_set_repulsion): parameters and blob forces (3Nb)
+    bool steric_on = false;
+    double st_eps = 0.0, st_b = 1.0, st_rc = 0.0, st_eps_w = 0.0, st_b_w = 1.0;
+    double* d_fst = nullptr;
     double *d_zbuf = nullptr, *d_cbuf = nullptr;
     long long* d_corr_off = nullptr;
     int* d_iters = nullptr;

@@ -121,7 +121,7 @@ void free_bodies(am_handle* h) {
     dfree(&h->d_pc_w); dfree(&h->d_pc_Uhat); dfree(&h->d_mv);
     dfree(&h->d_pcw_body); dfree(&h->d_pcw_chunk); dfree(&h->d_pcw_off); dfree(&h->d_ytp);
     h->n_pcw = 0;
-    dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters); dfree(&h->d_q0); dfree(&h->d_th0);
+    dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters); dfree(&h->d_q0); dfree(&h->d_th0); dfree(&h->d_fst);
 }
 
 void free_solver(am_handle* h) {
@@ -540,6 +540,7 @@ int build_layout(am_handle* h, int M, int Nb, int NA, int maxb, const double* q,
     CK(dalloc(&h->d_pc_Uhat, 6 * (size_t)M));
     CK(dalloc(&h->d_qnew, 3 * (size_t)M)); CK(dalloc(&h->d_thnew, 4 * (size_t)M));
     CK(dalloc(&h->d_q0, 3 * (size_t)M)); CK(dalloc(&h->d_th0, 4 * (size_t)M));
+    CK(dalloc(&h->d_fst, 3 * (size_t)Nb));
     CK(dalloc(&h->d_iters, NA));
     if (h->h_iters) cudaFreeHost(h->h_iters);
     h->h_iters = nullptr;
@@ -1139,6 +1140,42 @@ extern "C" AM_API int am_apply_mobility_ex(am_handle* h, const double* lam, doub
     am::mobility_apply(h, h->d_t, h->d_w, mode);
     CK(cudaGetLastError());
     CK(d2h(u, h->d_w, 3 * (size_t)h->Nb, s));
+    CK(cudaStreamSynchronize(s));
+    return AM_OK;
+}
+
+extern "C" AM_API int am_set_repulsion(am_handle* h, double eps, double range, double cutoff, double eps_wall,
+                                       double range_wall) {
+    if (!h) return AM_ERR_ARG;
+    if (!(eps >= 0.0) || !(cutoff >= 0.0) || !(eps_wall >= 0.0) || (eps > 0.0 && !(range > 0.0)) ||
+        (eps_wall > 0.0 && !(range_wall > 0.0)) || !std::isfinite(eps) || !std::isfinite(cutoff) ||
+        !std::isfinite(eps_wall))
+        return set_err(h, AM_ERR_ARG, "am_set_repulsion: need eps, cutoff, eps_wall >= 0 and positive ranges");
+    if (eps_wall > 0.0 && !h->cfg.wall)
+        return set_err(h, AM_ERR_ARG, "am_set_repulsion: wall repulsion needs a handle with a wall");
+    h->st_eps = eps;
+    h->st_b = range > 0.0 ? range : 1.0;
+    h->st_rc = eps > 0.0 ? cutoff : 0.0;
+    h->st_eps_w = eps_wall;
+    h->st_b_w = range_wall > 0.0 ? range_wall : 1.0;
+    h->steric_on = (eps > 0.0 && cutoff > 0.0) || eps_wall > 0.0;
+    return AM_OK;
+}
+
+extern "C" AM_API int am_steric_forces(am_handle* h, double* f) {
+    if (!h) return AM_ERR_ARG;
+    if (!f) return set_err(h, AM_ERR_ARG, "am_steric_forces: NULL array");
+    int rc = check_handle(h, "am_steric_forces", true);
+    if (rc) return rc;
+    cudaStream_t s = h->stream;
+    am::launch_geometry(h);
+    rc = device_flags_to_status(h, "am_steric_forces");
+    if (rc) return rc;
+    if (h->steric_on) {
+        CK(d2h(f, h->d_fst, 3 * (size_t)h->Nb, s));
+    } else {
+        std::fill(f, f + 3 * (size_t)h->Nb, 0.0);
+    }
     CK(cudaStreamSynchronize(s));
     return AM_OK;
 }

@@ -831,6 +831,7 @@ void launch_geometry(am_handle* h) {
     }
     k_rhs<<<nblk(h->n, 256), 256, 0, s>>>(h->Nb, h->M, h->P, h->d_slip, h->d_F, h->d_B, h->d_b);
     count_launch();
+    steric_apply(h);
 }
 
 static void timing_mark(am_handle* h) {

@@ -51,6 +51,9 @@ int learned_x0(am_handle* h, double* x);
 // Features (and background-flow targets of the solution in d_x) of all
 // bodies to host X, T; uses d_dx and d_w.
 int learned_features(am_handle* h, float* X, float* T);
+// Steric repulsion (steric.cu): blob forces at the current pose and their
+// body sums subtracted from the force rows of d_b; no-op when off.
+void steric_apply(am_handle* h);
 // Read and clear the device error flags.
 int take_flags(am_handle* h);
 
