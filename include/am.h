@@ -85,6 +85,11 @@ typedef struct {
                             ||g*||_2^2 >= delta; 0 -> 1e-10                 */
     int    corr_max_iter;/* Gauss-Newton iteration cap; 0 -> 20             */
     void*  cuda_stream;  /* cudaStream_t to run on; NULL -> library stream  */
+    int    single_blob;  /* 1: every body is one blob of radius blob_radius
+                            at its tracking point, with rotational coupling
+                            (Sec. 2.4; free space, AM_FP64); the problem is
+                            Eq. linear_system_general on (U, phi) and the
+                            blob arguments of am_set_bodies are ignored   */
 } am_config;
 
 typedef struct {
@@ -111,7 +116,8 @@ typedef struct {
 
 /* Create a solver handle.  cfg is copied.  Errors: AM_ERR_ARG for eta <= 0,
  * blob_radius <= 0, wall not 0/1, unknown precision, n_systems outside
- * 1..65536, tol <= 0 or restart/max_iter out of range; AM_ERR_CUDA.
+ * 1..65536, tol <= 0 or restart/max_iter out of range, single_blob not 0/1
+ * or with a wall or mixed precision; AM_ERR_CUDA.
  *
  * Several systems (n_systems = S > 1): every system is set separately
  * (am_set_bodies/am_set_constraints with its index) and the device layout is
@@ -225,7 +231,9 @@ AM_API int am_get_bodies(am_handle* h, int system, double* q, double* theta);
 AM_API int am_get_blobs(am_handle* h, int system, double* r);
 
 /* One blob mobility product u = M lambda at the current pose (Eq. RPY),
- * host arrays of 3Nb.  For checking and benchmarking the hot kernel. */
+ * host arrays of 3Nb.  For checking and benchmarking the hot kernel.  With
+ * single_blob: the body mobility N, (f, tau) per body in and (u, omega) per
+ * body out, 6M each. */
 AM_API int am_apply_mobility(am_handle* h, const double* lambda, double* u);
 
 /* As am_apply_mobility with the pair arithmetic chosen: AM_FP64, AM_MIXED

@@ -33,7 +33,7 @@ class Config(ctypes.Structure):
                 ("n_systems", ctypes.c_int), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("corr_tol", ctypes.c_double), ("corr_max_iter", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("single_blob", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -144,11 +144,13 @@ class Solver:
     """One handle of the library (am_create ... am_destroy)."""
 
     def __init__(self, eta=1.0, a=0.1, wall=0, precision="fp64", tol=1e-10, restart=50,
-                 max_iter=500, corr_tol=1e-10, corr_max_iter=20, stream=None, n_systems=1):
+                 max_iter=500, corr_tol=1e-10, corr_max_iter=20, stream=None, n_systems=1,
+                 single_blob=False):
         L = lib()
         prec = {"fp64": AM_FP64, "mixed": AM_MIXED}[precision]
         cfg = Config(eta, a, wall, prec, n_systems, tol, restart, max_iter, corr_tol, corr_max_iter,
-                     stream)
+                     stream, 1 if single_blob else 0)
+        self.single_blob = bool(single_blob)
         h = _vp()
         rc = L.am_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != AM_OK:
@@ -187,11 +189,13 @@ class Solver:
 
     def set_bodies(self, q, theta, blob_offset, rho, F, assembly, slip=None, system=0):
         M = len(np.asarray(theta).reshape(-1, 4))
+        if self.single_blob:  # the body is the blob: no blob arrays
+            blob_offset, rho, slip = np.zeros(M + 1, np.int32), np.zeros((1, 3)), None
         off, off_p = _i(blob_offset)
         Nb = int(off[-1])
         qa, qp = _d(q, 3 * M)
         ta, tp = _d(theta, 4 * M)
-        ra, rp = _d(rho, 3 * Nb)
+        ra, rp = _d(rho, 3 * Nb if not self.single_blob else 3)
         fa, fp = _d(F, 6 * M)
         sa, sp = _d(slip, 3 * Nb)
         aa, ap = _i(assembly)
@@ -292,10 +296,13 @@ class Solver:
         return out
 
     def apply_mobility(self, lam):
-        la, lp = _d(lam, 3 * self.Nb)
-        u, up = _out(3 * self.Nb)
+        """u = M lambda (3Nb); with single_blob the body mobility, (f, tau)
+        per body in and (u, omega) out (6M)."""
+        k = 6 * self.M if self.single_blob else 3 * self.Nb
+        la, lp = _d(lam, k)
+        u, up = _out(k)
         self._check(lib().am_apply_mobility(self.h, lp, up))
-        return u.reshape(-1, 3)
+        return u.reshape(-1, 6 if self.single_blob else 3)
 
     def apply_mobility_ex(self, lam, arithmetic):
         """u = M lambda with the pair arithmetic "fp64", "mixed" or "df64"."""

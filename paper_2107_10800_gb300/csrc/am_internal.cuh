@@ -222,6 +222,7 @@ struct am_handle {
 
     // steric repulsion (am_set_repulsion): parameters and blob forces (3Nb)
     bool steric_on = false;
+    bool sb = false;   // single-blob bodies (am_config.single_blob)
     double st_eps = 0.0, st_b = 1.0, st_rc = 0.0, st_eps_w = 0.0, st_b_w = 1.0;
     double* d_fst = nullptr;
     double *d_zbuf = nullptr, *d_cbuf = nullptr;

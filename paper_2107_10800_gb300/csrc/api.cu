@@ -343,7 +343,7 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 int prepare(am_handle* h, const char* who, bool warm, am_step_stats* st) {
     cudaStream_t s = h->stream;
     am::launch_geometry(h);
-    if (!h->mv_tuned && am::mobility_autotune(h))
+    if (!h->sb && !h->mv_tuned && am::mobility_autotune(h))
         return set_err(h, AM_ERR_CUDA, std::string(who) + ": mobility autotuning failed");
     CK(cudaEventRecord(h->ev[0], s));
     am::pc_build(h);
@@ -406,12 +406,15 @@ extern "C" AM_API int am_create(const am_config* cfg, am_handle** out) {
     if (!(c.eta > 0.0) || !(c.blob_radius > 0.0) || (c.wall != 0 && c.wall != 1) ||
         (c.precision != AM_FP64 && c.precision != AM_MIXED) || c.n_systems < 1 || c.n_systems > 65536 ||
         !(c.tol > 0.0) ||
-        c.restart < 1 || c.restart > 200 || c.max_iter < 1 || !(c.corr_tol > 0.0) || c.corr_max_iter < 1)
+        c.restart < 1 || c.restart > 200 || c.max_iter < 1 || !(c.corr_tol > 0.0) || c.corr_max_iter < 1 ||
+        (c.single_blob != 0 && c.single_blob != 1) ||
+        (c.single_blob && (c.wall || c.precision != AM_FP64)))
         return AM_ERR_ARG;
     am_handle* h = new am_handle();
     h->cfg = c;
     h->restart = c.restart;
     h->pc32 = (c.precision == AM_MIXED);
+    h->sb = c.single_blob != 0;
     h->S = c.n_systems;
     h->sys.resize(h->S);
     h->prm = am::make_params(c.eta, c.blob_radius);
@@ -452,7 +455,7 @@ int validate_bodies(am_handle* h, int M, const double* q, const double* theta, c
         return set_err(h, AM_ERR_ARG, "am_set_bodies: n_bodies <= 0 or NULL array");
     if (blob_offset[0] != 0) return set_err(h, AM_ERR_ARG, "am_set_bodies: blob_offset[0] != 0");
     int maxb = 0;
-    for (int p = 0; p < M; ++p) {
+    for (int p = 0; p < M && !h->sb; ++p) {
         const int c = blob_offset[p + 1] - blob_offset[p];
         if (c < 1) return set_err(h, AM_ERR_ARG, "am_set_bodies: body without blobs");
         maxb = std::max(maxb, c);
@@ -740,6 +743,15 @@ extern "C" AM_API int am_set_bodies(am_handle* h, int system, int M, const doubl
     int rc = check_system(h, system, "am_set_bodies");
     if (rc) return rc;
     int NA = 0, maxb = 0;
+    // single-blob bodies carry no blobs of their own: the body is the blob
+    std::vector<int> no_blobs;
+    static const double no_rho = 0.0;
+    if (h->sb && M > 0) {
+        no_blobs.assign(M + 1, 0);
+        blob_offset = no_blobs.data();
+        rho = &no_rho;
+        slip = nullptr;
+    }
     rc = validate_bodies(h, M, q, theta, blob_offset, rho, F, asm_of_body, &NA, &maxb);
     if (rc) return rc;
     rc = sync_records(h);
@@ -890,6 +902,7 @@ extern "C" AM_API int am_learned_features(am_handle* h, float* X, float* T) {
 
 extern "C" AM_API int am_set_learned(am_handle* h, am_mlp* model, int check) {
     if (!h) return AM_ERR_ARG;
+    if (h->sb && model) return set_err(h, AM_ERR_ARG, "am_set_learned: not for single-blob bodies");
     h->mlp = model;
     h->mlp_check = check != 0;
     return AM_OK;
@@ -1108,6 +1121,14 @@ extern "C" AM_API int am_apply_mobility(am_handle* h, const double* lam, double*
     am::launch_geometry(h);
     rc = device_flags_to_status(h, "am_apply_mobility");
     if (rc) return rc;
+    if (h->sb) {  // (f, tau) per body in, (u, omega) per body out
+        CK(h2d(h->d_t, lam, 6 * (size_t)h->M, s));
+        am::sb_mobility(h, h->d_t, h->d_w);
+        CK(cudaGetLastError());
+        CK(d2h(u, h->d_w, 6 * (size_t)h->M, s));
+        CK(cudaStreamSynchronize(s));
+        return AM_OK;
+    }
     if (!h->mv_tuned && am::mobility_autotune(h))
         return set_err(h, AM_ERR_CUDA, "am_apply_mobility: mobility autotuning failed");
     CK(h2d(h->d_t, lam, 3 * (size_t)h->Nb, s));

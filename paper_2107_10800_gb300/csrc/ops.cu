@@ -831,6 +831,10 @@ void launch_geometry(am_handle* h) {
     }
     k_rhs<<<nblk(h->n, 256), 256, 0, s>>>(h->Nb, h->M, h->P, h->d_slip, h->d_F, h->d_B, h->d_b);
     count_launch();
+    if (h->sb) {
+        sb_rhs(h);
+        return;
+    }
     steric_apply(h);
 }
 
@@ -859,6 +863,10 @@ void mobility_apply(am_handle* h, const double* lam, double* u, int mode) {
 }
 
 void op_apply(am_handle* h, const double* y, double* out, int mode) {
+    if (h->sb) {
+        sb_op_apply(h, y, out);
+        return;
+    }
     mobility_partial(h, y, mode);
     const int nbb = nblk(h->Nb, 128), nbody = nblk(h->M, 4), nlink = nblk(h->P, 128);
     k_op_epilogue<<<nbb + nbody + nlink, 128, 0, h->stream>>>(

@@ -54,6 +54,16 @@ int learned_features(am_handle* h, float* X, float* T);
 // Steric repulsion (steric.cu): blob forces at the current pose and their
 // body sums subtracted from the force rows of d_b; no-op when off.
 void steric_apply(am_handle* h);
+// Single-blob mode (single_blob.cu): grand mobility product v = N g (6M),
+// the right-hand side (N F, B), the operator, the preconditioner.
+void sb_mobility(am_handle* h, const double* g, double* v);
+void sb_rhs(am_handle* h);
+void sb_op_apply(am_handle* h, const double* y, double* out);
+void sb_pc_build(am_handle* h);
+void sb_pc_apply(am_handle* h, const double* r, double* z);
+// phi rows of the preconditioner (precond.cu): z_phi = G~ (r_phi - C U^)
+// with U^ in d_pc_Uhat.
+void pc_apply_links(am_handle* h, const double* r, double* z);
 // Read and clear the device error flags.
 int take_flags(am_handle* h);
 

@@ -422,7 +422,34 @@ static void pc_build_t(am_handle* h, double tol) {
     }
 }
 
+void pc_apply_links(am_handle* h, const double* r, double* z) {
+    cudaStream_t s = h->stream;
+    k_pc_cvec<<<(h->P + 127) / 128, 128, 0, s>>>(h->Nb, h->M, h->P, h->d_bp, h->d_bq, h->d_lp, h->d_lq,
+                                                  h->d_pc_Uhat, r, h->d_cbuf);
+    if (h->pc32)
+        k_pc_ap2<float><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk, h->d_asm_link_off,
+                                                  h->d_asm_link_idx, (const float*)h->d_G, h->d_G_off, h->d_cbuf, z);
+    else
+        k_pc_ap2<double><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk, h->d_asm_link_off,
+                                                   h->d_asm_link_idx, (const double*)h->d_G, h->d_G_off, h->d_cbuf, z);
+    count_launch(2);
+}
+
 void pc_build(am_handle* h) {
+    if (h->sb) {
+        sb_pc_build(h);
+        if (h->P) {
+            const size_t smem_a = (size_t)3 * std::max(1, h->max_asm_links) * sizeof(double);
+            if (smem_a > 48 * 1024)
+                cudaFuncSetAttribute(k_pca_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
+            k_pca_build<double><<<h->NA, kPcThreads, smem_a, h->stream>>>(
+                h->d_asm_link_off, h->d_asm_link_idx, h->d_bp, h->d_bq, h->d_lp, h->d_lq, h->d_Nt, h->d_G_off,
+                (double*)h->d_G, (double*)h->d_Gwork, h->d_perm, h->d_perm_off, h->d_G_rank, 1e-11);
+            count_launch();
+        }
+        h->pc_valid = true;
+        return;
+    }
     if (h->pc32)
         pc_build_t<float>(h, 1e-5);
     else
@@ -452,6 +479,10 @@ static void pc_apply_t(am_handle* h, const double* r, double* z) {
 }
 
 void pc_apply(am_handle* h, const double* r, double* z) {
+    if (h->sb) {
+        sb_pc_apply(h, r, z);
+        return;
+    }
     if (h->pc32)
         pc_apply_t<float>(h, r, z);
     else
