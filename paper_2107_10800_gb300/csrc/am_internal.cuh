@@ -13,6 +13,7 @@ namespace am {
 
 constexpr int kTile = 128;        // sources per shared-memory tile
 constexpr int kThreads = 128;     // threads per block of the pair kernels
+constexpr int kSbChunks = 16;     // most source chunks of the single-blob body mobility
 constexpr double kPi = 3.14159265358979323846;
 
 extern std::atomic<long long> g_launches;
@@ -223,6 +224,7 @@ struct am_handle {
     // steric repulsion (am_set_repulsion): parameters and blob forces (3Nb)
     bool steric_on = false;
     bool sb = false;   // single-blob bodies (am_config.single_blob)
+    double* d_sbpart = nullptr;   // kSbChunks x 6M partial sums of the body mobility
     double st_eps = 0.0, st_b = 1.0, st_rc = 0.0, st_eps_w = 0.0, st_b_w = 1.0;
     double* d_fst = nullptr;
     double *d_zbuf = nullptr, *d_cbuf = nullptr;

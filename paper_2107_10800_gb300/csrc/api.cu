@@ -121,7 +121,7 @@ void free_bodies(am_handle* h) {
     dfree(&h->d_pc_w); dfree(&h->d_pc_Uhat); dfree(&h->d_mv);
     dfree(&h->d_pcw_body); dfree(&h->d_pcw_chunk); dfree(&h->d_pcw_off); dfree(&h->d_ytp);
     h->n_pcw = 0;
-    dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters); dfree(&h->d_q0); dfree(&h->d_th0); dfree(&h->d_fst);
+    dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters); dfree(&h->d_q0); dfree(&h->d_th0); dfree(&h->d_fst); dfree(&h->d_sbpart);
 }
 
 void free_solver(am_handle* h) {
@@ -544,6 +544,7 @@ int build_layout(am_handle* h, int M, int Nb, int NA, int maxb, const double* q,
     CK(dalloc(&h->d_qnew, 3 * (size_t)M)); CK(dalloc(&h->d_thnew, 4 * (size_t)M));
     CK(dalloc(&h->d_q0, 3 * (size_t)M)); CK(dalloc(&h->d_th0, 4 * (size_t)M));
     CK(dalloc(&h->d_fst, 3 * (size_t)Nb));
+    if (h->sb) CK(dalloc(&h->d_sbpart, (size_t)am::kSbChunks * 6 * M));
     CK(dalloc(&h->d_iters, NA));
     if (h->h_iters) cudaFreeHost(h->h_iters);
     h->h_iters = nullptr;

@@ -22,6 +22,7 @@
 #include "ops.cuh"
 #include "rpy_pair.cuh"
 
+#include <algorithm>
 #include <climits>
 
 namespace am {
@@ -88,7 +89,10 @@ k_sb_mobility(int M, const double* __restrict__ q, const int* __restrict__ sys_o
     __syncthreads();
     if (live) { atomicMin(&s_lo, j0); atomicMax(&s_hi, j1); }
     __syncthreads();
-    const int lo_all = s_lo, hi_all = s_hi;
+    // this block's share of the sources: chunk blockIdx.y of gridDim.y
+    const int span = s_hi - s_lo;
+    const int lo_all = s_lo + (int)((long long)span * blockIdx.y / gridDim.y);
+    const int hi_all = s_lo + (int)((long long)span * (blockIdx.y + 1) / gridDim.y);
     const double pi = 3.14159265358979323846;
     const double ctr_far = 1.0 / (8.0 * pi * eta);          // c r^2
     const double cnear = 1.0 / (16.0 * pi * eta * a * a);   // c / (s - 3 s^2 / 8)
@@ -146,9 +150,18 @@ k_sb_mobility(int M, const double* __restrict__ q, const int* __restrict__ sys_o
         }
     }
     if (!live) return;
-    double* o = v + 6 * (size_t)i;
+    double* o = v + 6 * ((size_t)blockIdx.y * M + i);  // partial sums of chunk blockIdx.y
     o[0] = k.A1 * ux; o[1] = k.A1 * uy; o[2] = k.A1 * uz;
     o[3] = wx; o[4] = wy; o[5] = wz;
+}
+
+// v = sum over the nc chunks of the partial sums (fixed order)
+__global__ void k_sb_sum(int n6, int nc, const double* __restrict__ part, double* __restrict__ v) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n6) return;
+    double a = 0.0;
+    for (int c = 0; c < nc; ++c) a += part[(size_t)c * n6 + t];
+    v[t] = a;
 }
 
 // out_U = U - v (v = N C^T phi); out_phi = C U
@@ -199,10 +212,16 @@ static double sb_mur(const am_handle* h) {
 }
 
 void sb_mobility(am_handle* h, const double* g, double* v) {
-    k_sb_mobility<<<nb(h->M, kThreads), kThreads, 0, h->stream>>>(
+    // source chunks so that the grid has about 4 blocks per SM (at most
+    // kSbChunks; the partial sums live in d_sbpart)
+    const int tb = nb(h->M, kThreads);
+    const int nc = std::max(1, std::min(kSbChunks, (4 * num_sms() + tb - 1) / tb));
+    dim3 grid(tb, nc);
+    k_sb_mobility<<<grid, kThreads, 0, h->stream>>>(
         h->M, h->d_q, h->d_sys_of_elem, h->d_sys_body_off, g, rpy_consts<double>(h->prm), h->cfg.eta,
-        h->cfg.blob_radius, v);
-    count_launch();
+        h->cfg.blob_radius, h->d_sbpart);
+    k_sb_sum<<<nb(6LL * h->M, 256), 256, 0, h->stream>>>(6 * h->M, nc, h->d_sbpart, v);
+    count_launch(2);
     long long pairs = 0;
     for (const auto& r : h->sys) pairs += (long long)r.M * r.M;
     h->pairs += pairs;
