@@ -300,6 +300,20 @@ AM_API int am_rpy_matvec(const double* d_r, const double* d_lambda,
                          void* stream);
 AM_API size_t am_rpy_matvec_workspace(int n, int precision);
 
+/* Rows row0 .. row0 + nrows - 1 of the product u = M(r) lambda against all
+ * n sources: the local step of a suspension sharded by blobs over several
+ * GPUs, after the positions and forces of all shards have been gathered.
+ *   d_r, d_lambda  3n doubles (all blobs, device); d_u  3 nrows doubles
+ *   d_work         at least am_rpy_matvec_rows_workspace(n, nrows,
+ *                  precision) bytes, 256-byte aligned
+ * Otherwise as am_rpy_matvec (with row0 = 0 and nrows = n the two agree).
+ * Errors: AM_ERR_ARG (rows outside 0 .. n - 1 and as am_rpy_matvec),
+ * AM_ERR_CUDA. */
+AM_API int am_rpy_matvec_rows(const double* d_r, const double* d_lambda, double* d_u, int n,
+                              int row0, int nrows, double eta, double a, int wall, int precision,
+                              void* d_work, size_t work_bytes, void* stream);
+AM_API size_t am_rpy_matvec_rows_workspace(int n, int nrows, int precision);
+
 /* Allocation-free variant of am_rpy_matvec for callers that cannot call
  * cudaMalloc: code that runs where allocating is not allowed or not safe,
  * e.g. inside another library's allocation-free execution path, a host

@@ -74,6 +74,10 @@ SIGNATURES = {
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp,
                                      ctypes.c_size_t, _vp]),
     "am_rpy_matvec_workspace": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "am_rpy_matvec_rows": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp,
+                                          ctypes.c_size_t, _vp]),
+    "am_rpy_matvec_rows_workspace": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "am_rpy_matvec_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]),
     "am_flops_per_pair": (ctypes.c_int, [ctypes.c_int]),
@@ -499,6 +503,21 @@ def rpy_matvec_noalloc_ptr(d_r, d_lam, d_u, n, eta, a, wall, precision, stream=N
 
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def rpy_matvec_rows_ptr(d_r, d_lam, d_u, n, row0, nrows, eta, a, wall, precision, d_work, work_bytes,
+                        stream=None):
+    """am_rpy_matvec_rows on raw device pointers (ints)."""
+    prec = {"fp64": AM_FP64, "mixed": AM_MIXED}.get(precision, precision)
+    rc = lib().am_rpy_matvec_rows(d_r, d_lam, d_u, n, row0, nrows, eta, a, wall, prec, d_work, work_bytes,
+                                  stream)
+    if rc != AM_OK:
+        raise AmError(rc, lib().am_last_error(None).decode())
+
+
+def rpy_matvec_rows_workspace(n, nrows, precision):
+    prec = {"fp64": AM_FP64, "mixed": AM_MIXED}.get(precision, precision)
+    return int(lib().am_rpy_matvec_rows_workspace(n, nrows, prec))
 
 
 def rpy_matvec_workspace(n, precision):

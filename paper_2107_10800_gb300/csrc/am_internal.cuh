@@ -36,10 +36,16 @@ RpyParams make_params(double eta, double a);
 // Source splitting of the all-pairs product: grid (target blocks, splits).
 struct Split { int splits; int chunk; int tpt; };
 Split choose_split(int n, int precision);
+Split choose_split_rows(int n, int nt, int precision);
 
 // ---- mobility product launchers (rpy.cu) ------------------------------
 // FP64: r4 = (x, y, z, 0) per blob.  Mixed: hi/lo float4 positions.
 // Writes partial sums part[s][3n] for s < splits.
+void launch_rpy_partial_f64_rows(const double4_32a* r4, const double* lam, double* part, int n, int t0, int nt,
+                                 const Split& sp, const RpyParams& prm, int wall, cudaStream_t st);
+void launch_rpy_partial_mixed_rows(const float4* hi, const float4* lo, const double* lam, double* part, int n,
+                                   int t0, int nt, const Split& sp, const RpyParams& prm, int wall,
+                                   cudaStream_t st);
 void launch_rpy_partial_f64(const double4_32a* r4, const double* lam, double* part,
                             int n, const Split& sp, const RpyParams& prm, int wall,
                             cudaStream_t st);

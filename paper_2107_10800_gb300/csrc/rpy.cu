@@ -61,14 +61,17 @@ RpyParams make_params(double eta, double a) {
     return p;
 }
 
-Split choose_split(int n, int precision) {
+Split choose_split(int n, int precision) { return choose_split_rows(n, n, precision); }
+
+// n sources, nt targets
+Split choose_split_rows(int n, int nt, int precision) {
     Split s{1, std::max(n, 1), 1};
-    if (n <= 0) return s;
+    if (n <= 0 || nt <= 0) return s;
     const int want = 4 * num_sms();  // blocks to fill the GPU
     // two targets per thread once one source chunk already fills the GPU
-    if (precision == AM_MIXED && (n + 2 * kThreads - 1) / (2 * kThreads) >= want) s.tpt = 2;
+    if (precision == AM_MIXED && (nt + 2 * kThreads - 1) / (2 * kThreads) >= want) s.tpt = 2;
     const int tiles = (n + kTile - 1) / kTile;
-    const int tblocks = (n + kThreads * s.tpt - 1) / (kThreads * s.tpt);
+    const int tblocks = (nt + kThreads * s.tpt - 1) / (kThreads * s.tpt);
     const int splits = std::max(1, std::min(tiles, (want + tblocks - 1) / tblocks));
     const int per = (tiles + splits - 1) / splits;  // tiles per chunk
     s.chunk = per * kTile;
@@ -79,13 +82,15 @@ Split choose_split(int n, int precision) {
 template <bool WALL>
 __global__ void __launch_bounds__(kThreads)
 rpy_partial_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam,
-                double* __restrict__ part, int n, int chunk, RpyK<double> k) {
+                double* __restrict__ part, int n, int chunk, RpyK<double> k, int t0, int nt) {
     __shared__ double4_32a sr[kTile];
     __shared__ double sl[3 * kTile];
-    const int i = blockIdx.x * kThreads + threadIdx.x;
+    // targets t0 .. t0 + nt - 1 against sources 0 .. n - 1
+    const int it = blockIdx.x * kThreads + threadIdx.x;
+    const int i = t0 + it;
     const int j0 = blockIdx.y * chunk;
     const int j1 = min(n, j0 + chunk);
-    double4_32a ri = (i < n) ? r4[i] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
+    double4_32a ri = (it < nt) ? r4[i] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
     double ux = 0.0, uy = 0.0, uz = 0.0;
     for (int jt = j0; jt < j1; jt += kTile) {
         const int cnt = min(kTile, j1 - jt);
@@ -102,8 +107,8 @@ rpy_partial_f64(const double4_32a* __restrict__ r4, const double* __restrict__ l
             if (WALL) pair_image<double>(dx, dy, ri.z + rj.z, ri.z, rj.z, lx, ly, lz, k, ux, uy, uz);
         }
     }
-    if (i < n) {
-        double* o = part + (size_t)blockIdx.y * 3 * n + 3 * (size_t)i;
+    if (it < nt) {
+        double* o = part + (size_t)blockIdx.y * 3 * nt + 3 * (size_t)it;
         o[0] = k.A1 * ux; o[1] = k.A1 * uy; o[2] = k.A1 * uz;
     }
 }
@@ -119,7 +124,7 @@ template <bool WALL, int TPT>
 __global__ void __launch_bounds__(kThreads, 4)
 rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
                   const double* __restrict__ lam, double* __restrict__ part, int n,
-                  int chunk, RpyK<float> k) {
+                  int chunk, RpyK<float> k, int t0, int nt) {
     __shared__ float4 sh[kTile];
     __shared__ float4 so[kTile];
     __shared__ float4 sl[kTile];
@@ -130,9 +135,10 @@ rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
     double U[TPT][3];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
-        const int i = (blockIdx.x * TPT + t) * kThreads + threadIdx.x;
-        hi_i[t] = (i < n) ? hi[i] : make_float4(0.f, 0.f, 1.f, 0.f);
-        lo_i[t] = (i < n) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int it = (blockIdx.x * TPT + t) * kThreads + threadIdx.x;
+        const int i = t0 + it;
+        hi_i[t] = (it < nt) ? hi[i] : make_float4(0.f, 0.f, 1.f, 0.f);
+        lo_i[t] = (it < nt) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float nr = 0.25f * fmaxf(fabsf(hi_i[t].x), fmaxf(fabsf(hi_i[t].y), fabsf(hi_i[t].z)));
         near2[t] = nr * nr;
         U[t][0] = U[t][1] = U[t][2] = 0.0;
@@ -181,9 +187,9 @@ rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
     }
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
-        const int i = (blockIdx.x * TPT + t) * kThreads + threadIdx.x;
-        if (i < n) {
-            double* o = part + (size_t)blockIdx.y * 3 * n + 3 * (size_t)i;
+        const int it = (blockIdx.x * TPT + t) * kThreads + threadIdx.x;
+        if (it < nt) {
+            double* o = part + (size_t)blockIdx.y * 3 * nt + 3 * (size_t)it;
             o[0] = k.A1 * U[t][0]; o[1] = k.A1 * U[t][1]; o[2] = k.A1 * U[t][2];
         }
     }
@@ -212,37 +218,50 @@ __global__ void sum_partials(const double* __restrict__ part, double* __restrict
 }
 
 
-void launch_rpy_partial_f64(const double4_32a* r4, const double* lam, double* part, int n,
-                            const Split& sp, const RpyParams& prm, int wall, cudaStream_t st) {
-    if (n <= 0) return;
-    dim3 grid((n + kThreads - 1) / kThreads, sp.splits);
+// Targets t0 .. t0 + nt - 1 against all n sources; partial sums of split c
+// at part[c * 3 nt + 3 (i - t0)].
+void launch_rpy_partial_f64_rows(const double4_32a* r4, const double* lam, double* part, int n, int t0, int nt,
+                                 const Split& sp, const RpyParams& prm, int wall, cudaStream_t st) {
+    if (n <= 0 || nt <= 0) return;
+    dim3 grid((nt + kThreads - 1) / kThreads, sp.splits);
     const RpyK<double> k = rpy_consts<double>(prm);
     if (wall)
-        rpy_partial_f64<true><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, k);
+        rpy_partial_f64<true><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, k, t0, nt);
     else
-        rpy_partial_f64<false><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, k);
+        rpy_partial_f64<false><<<grid, kThreads, 0, st>>>(r4, lam, part, n, sp.chunk, k, t0, nt);
     count_launch();
+}
+
+void launch_rpy_partial_mixed_rows(const float4* hi, const float4* lo, const double* lam, double* part, int n,
+                                   int t0, int nt, const Split& sp, const RpyParams& prm, int wall,
+                                   cudaStream_t st) {
+    if (n <= 0 || nt <= 0) return;
+    const RpyK<float> k = rpy_consts<float>(prm);
+    const int per = kThreads * sp.tpt;
+    dim3 grid((nt + per - 1) / per, sp.splits);
+    if (sp.tpt == 2) {
+        if (wall)
+            rpy_partial_mixed<true, 2><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k, t0, nt);
+        else
+            rpy_partial_mixed<false, 2><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k, t0, nt);
+    } else {
+        if (wall)
+            rpy_partial_mixed<true, 1><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k, t0, nt);
+        else
+            rpy_partial_mixed<false, 1><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k, t0, nt);
+    }
+    count_launch();
+}
+
+void launch_rpy_partial_f64(const double4_32a* r4, const double* lam, double* part, int n,
+                            const Split& sp, const RpyParams& prm, int wall, cudaStream_t st) {
+    launch_rpy_partial_f64_rows(r4, lam, part, n, 0, n, sp, prm, wall, st);
 }
 
 void launch_rpy_partial_mixed(const float4* hi, const float4* lo, const double* lam, double* part,
                               int n, const Split& sp, const RpyParams& prm, int wall,
                               cudaStream_t st) {
-    if (n <= 0) return;
-    const RpyK<float> k = rpy_consts<float>(prm);
-    const int per = kThreads * sp.tpt;
-    dim3 grid((n + per - 1) / per, sp.splits);
-    if (sp.tpt == 2) {
-        if (wall)
-            rpy_partial_mixed<true, 2><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k);
-        else
-            rpy_partial_mixed<false, 2><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k);
-    } else {
-        if (wall)
-            rpy_partial_mixed<true, 1><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k);
-        else
-            rpy_partial_mixed<false, 1><<<grid, kThreads, 0, st>>>(hi, lo, lam, part, n, sp.chunk, k);
-    }
-    count_launch();
+    launch_rpy_partial_mixed_rows(hi, lo, lam, part, n, 0, n, sp, prm, wall, st);
 }
 
 void launch_pack_positions(const double* r3, double4_32a* r4, float4* hi, float4* lo, int n,
@@ -315,6 +334,52 @@ extern "C" AM_API int am_rpy_matvec(const double* d_r, const double* d_lambda, d
         am::launch_pack_positions(d_r, r4, nullptr, nullptr, n, st);
         am::launch_rpy_partial_f64(r4, d_lambda, part, n, sp, prm, wall, st);
         am::launch_sum_partials(part, d_u, n, sp.splits, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AM_ERR_CUDA, cudaGetErrorString(e));
+    return AM_OK;
+}
+
+extern "C" AM_API size_t am_rpy_matvec_rows_workspace(int n, int nrows, int precision) {
+    if (n <= 0 || nrows <= 0) return 0;
+    am::Split sp = am::choose_split_rows(n, nrows, precision);
+    size_t pos = (precision == AM_MIXED) ? 2 * align256((size_t)n * sizeof(float4))
+                                         : align256((size_t)n * sizeof(double4_32a));
+    return pos + align256((size_t)sp.splits * 3 * nrows * sizeof(double));
+}
+
+extern "C" AM_API int am_rpy_matvec_rows(const double* d_r, const double* d_lambda, double* d_u, int n, int row0,
+                                         int nrows, double eta, double a, int wall, int precision, void* d_work,
+                                         size_t work_bytes, void* stream) {
+    if (n < 0 || nrows < 0 || row0 < 0 || (long long)row0 + nrows > n)
+        return fail(AM_ERR_ARG, "am_rpy_matvec_rows: need 0 <= row0, 0 <= nrows, row0 + nrows <= n");
+    if (!(eta > 0.0) || !(a > 0.0)) return fail(AM_ERR_ARG, "am_rpy_matvec_rows: eta and a must be > 0");
+    if (wall != 0 && wall != 1) return fail(AM_ERR_ARG, "am_rpy_matvec_rows: wall must be 0 or 1");
+    if (precision != AM_FP64 && precision != AM_MIXED)
+        return fail(AM_ERR_ARG, "am_rpy_matvec_rows: unknown precision");
+    if (n == 0 || nrows == 0) return AM_OK;
+    if (!d_r || !d_lambda || !d_u || !d_work) return fail(AM_ERR_ARG, "am_rpy_matvec_rows: NULL pointer");
+    if (work_bytes < am_rpy_matvec_rows_workspace(n, nrows, precision))
+        return fail(AM_ERR_ARG, "am_rpy_matvec_rows: workspace too small");
+    if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0)
+        return fail(AM_ERR_ARG, "am_rpy_matvec_rows: workspace not 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    am::Split sp = am::choose_split_rows(n, nrows, precision);
+    am::RpyParams prm = am::make_params(eta, a);
+    char* w = static_cast<char*>(d_work);
+    if (precision == AM_MIXED) {
+        float4* hi = reinterpret_cast<float4*>(w);
+        float4* lo = reinterpret_cast<float4*>(w + align256((size_t)n * sizeof(float4)));
+        double* part = reinterpret_cast<double*>(w + 2 * align256((size_t)n * sizeof(float4)));
+        am::launch_pack_positions(d_r, nullptr, hi, lo, n, st);
+        am::launch_rpy_partial_mixed_rows(hi, lo, d_lambda, part, n, row0, nrows, sp, prm, wall, st);
+        am::launch_sum_partials(part, d_u, nrows, sp.splits, st);
+    } else {
+        double4_32a* r4 = reinterpret_cast<double4_32a*>(w);
+        double* part = reinterpret_cast<double*>(w + align256((size_t)n * sizeof(double4_32a)));
+        am::launch_pack_positions(d_r, r4, nullptr, nullptr, n, st);
+        am::launch_rpy_partial_f64_rows(r4, d_lambda, part, n, row0, nrows, sp, prm, wall, st);
+        am::launch_sum_partials(part, d_u, nrows, sp.splits, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(AM_ERR_CUDA, cudaGetErrorString(e));
