@@ -200,6 +200,13 @@ struct am_handle {
     long long* d_minv_off = nullptr;
     void *d_G = nullptr, *d_Gwork = nullptr;
     int *d_pcw_body = nullptr, *d_pcw_chunk = nullptr, *d_pcw_off = nullptr;
+    // body preconditioner build: bodies of <= 64 rows first (n_pcb_small),
+    // then the larger ones, built by clusters of pcb_cs CTAs when pcb_cs > 1
+    int* d_pcb_list = nullptr;
+    int n_pcb_small = 0, pcb_cs = 1;
+    // the same for the articulated-body build (by 3 x links rows)
+    int* d_pca_list = nullptr;
+    int n_pca_small = 0, pca_cs = 1;
     int *d_pca_asm = nullptr, *d_pca_chunk = nullptr;
     int n_pcw = 0, n_pca = 0;
     double* d_ytp = nullptr;

@@ -98,6 +98,23 @@ bool host_inverse(std::vector<double>& A, int n) {
     return true;
 }
 
+// Order of the per-body or per-articulated-body preconditioner builds:
+// matrices of at most two 32-row tiles (rows[i] <= 64) first, one CTA each,
+// then the larger ones, built by clusters of cs CTAs: cs doubles (up to 8)
+// while the larger ones' clusters still fit twice the SM count.
+void split_for_build(const std::vector<int>& rows, std::vector<int>& list, int& n_small, int& cs) {
+    const int n = (int)rows.size();
+    list.clear();
+    for (int i = 0; i < n; ++i)
+        if (rows[i] <= 2 * 32) list.push_back(i);
+    n_small = (int)list.size();
+    for (int i = 0; i < n; ++i)
+        if (rows[i] > 2 * 32) list.push_back(i);
+    const long long large = n - n_small;
+    cs = 1;
+    while (cs < 8 && large > 0 && large * cs * 2 <= 2LL * am::num_sms()) cs *= 2;
+}
+
 void free_links(am_handle* h) {
     dfree(&h->d_bp); dfree(&h->d_bq); dfree(&h->d_dlp); dfree(&h->d_dlq);
     dfree(&h->d_dlpd); dfree(&h->d_dlqd); dfree(&h->d_dlp1); dfree(&h->d_dlq1);
@@ -108,8 +125,10 @@ void free_links(am_handle* h) {
     dfree(&h->d_G); dfree(&h->d_Gwork); dfree(&h->d_G_off); dfree(&h->d_G_rank);
     dfree(&h->d_perm); dfree(&h->d_perm_off);
     dfree(&h->d_corr); dfree(&h->d_corr_off); dfree(&h->d_zbuf); dfree(&h->d_cbuf);
-    dfree(&h->d_pca_asm); dfree(&h->d_pca_chunk);
+    dfree(&h->d_pca_asm); dfree(&h->d_pca_chunk); dfree(&h->d_pca_list);
     h->n_pca = 0;
+    h->n_pca_small = 0;
+    h->pca_cs = 1;
 }
 
 void free_bodies(am_handle* h) {
@@ -120,6 +139,9 @@ void free_bodies(am_handle* h) {
     dfree(&h->d_minv); dfree(&h->d_pcwork); dfree(&h->d_Y); dfree(&h->d_Nt); dfree(&h->d_minv_off);
     dfree(&h->d_pc_w); dfree(&h->d_pc_Uhat); dfree(&h->d_mv);
     dfree(&h->d_pcw_body); dfree(&h->d_pcw_chunk); dfree(&h->d_pcw_off); dfree(&h->d_ytp);
+    dfree(&h->d_pcb_list);
+    h->n_pcb_small = 0;
+    h->pcb_cs = 1;
     h->n_pcw = 0;
     dfree(&h->d_qnew); dfree(&h->d_thnew); dfree(&h->d_iters); dfree(&h->d_q0); dfree(&h->d_th0); dfree(&h->d_fst); dfree(&h->d_sbpart);
 }
@@ -279,11 +301,15 @@ int build_links(am_handle* h, int P, const int* bp, const int* bq) {
     CK(dalloc(&h->d_pplus, pplus.size())); CK(dalloc(&h->d_pplus_off, NA + 1));
     const size_t esz = h->pc32 ? sizeof(float) : sizeof(double);
     CK(balloc(&h->d_G, goff[NA] * esz)); CK(balloc(&h->d_Gwork, 2 * goff[NA] * esz));
-    std::vector<int> pca_asm, pca_chunk;
+    std::vector<int> pca_asm, pca_chunk, pca_rows(NA), pca_list;
     for (int a = 0; a < NA; ++a) {
         const int m = 3 * (al_off[a + 1] - al_off[a]);
+        pca_rows[a] = m;
         for (int c = 0; c * 32 < m; ++c) { pca_asm.push_back(a); pca_chunk.push_back(c); }
     }
+    split_for_build(pca_rows, pca_list, h->n_pca_small, h->pca_cs);
+    CK(dalloc(&h->d_pca_list, std::max(NA, 1)));
+    if (NA) CK(h2d(h->d_pca_list, pca_list.data(), NA, s));
     h->n_pca = (int)pca_asm.size();
     CK(dalloc(&h->d_pca_asm, pca_asm.size())); CK(dalloc(&h->d_pca_chunk, pca_chunk.size()));
     CK(dalloc(&h->d_G_off, NA + 1)); CK(dalloc(&h->d_G_rank, NA));
@@ -537,6 +563,10 @@ int build_layout(am_handle* h, int M, int Nb, int NA, int maxb, const double* q,
         pcw_off[p + 1] = (int)pcw_body.size();
     }
     h->n_pcw = (int)pcw_body.size();
+    std::vector<int> pcb_rows(M), pcb_list;
+    for (int p = 0; p < M; ++p) pcb_rows[p] = 3 * (blob_offset[p + 1] - blob_offset[p]);
+    split_for_build(pcb_rows, pcb_list, h->n_pcb_small, h->pcb_cs);
+    CK(dalloc(&h->d_pcb_list, std::max(M, 1)));
     CK(dalloc(&h->d_pcw_body, pcw_body.size())); CK(dalloc(&h->d_pcw_chunk, pcw_chunk.size()));
     CK(dalloc(&h->d_pcw_off, M + 1)); CK(dalloc(&h->d_ytp, 6 * pcw_body.size()));
     CK(dalloc(&h->d_minv_off, M + 1)); CK(dalloc(&h->d_pc_w, 3 * (size_t)Nb));
@@ -559,6 +589,7 @@ int build_layout(am_handle* h, int M, int Nb, int NA, int maxb, const double* q,
     CK(h2d(h->d_asm_body_idx, h->asm_body_idx.data(), M, s));
     CK(h2d(h->d_body_local, body_local.data(), M, s));
     CK(h2d(h->d_minv_off, moff.data(), M + 1, s));
+    if (M) CK(h2d(h->d_pcb_list, pcb_list.data(), M, s));
     CK(h2d(h->d_pcw_body, pcw_body.data(), pcw_body.size(), s));
     CK(h2d(h->d_pcw_chunk, pcw_chunk.data(), pcw_chunk.size(), s));
     CK(h2d(h->d_pcw_off, pcw_off.data(), M + 1, s));

@@ -65,10 +65,16 @@ __device__ bool block_cholesky(T* A, int m, double* sh) {
 // A = M^-1 for an m x m symmetric positive definite M (row-major, full
 // storage in global memory) by blocked right-looking Cholesky M = L L^T,
 // the blocked lower-triangular inverse X = L^-1 and A = X^T X, every step a
-// product of 32 x 32 tiles staged in shared memory.  One block of kPcThreads
-// threads per matrix; L and X are m x m scratch (L may alias nothing else).
-// A non-positive pivot sets *bad (shared) and is replaced by 1 so that the
-// block still reaches every barrier; the result is then meaningless.
+// product of 32 x 32 tiles staged in shared memory.  A team of CTAs of
+// kPcThreads threads works on one matrix: one CTA, or the CTAs of a thread
+// block cluster, which share the tiles of every step round robin and meet at
+// the cluster barrier (release/acquire: the tiles one CTA wrote to global
+// memory are seen by the others after it).  L and X are m x m scratch (L may
+// alias nothing else).  A non-positive pivot sets *bad (shared) and is
+// replaced by 1 so that every CTA still reaches every barrier; the result is
+// then meaningless.  Every CTA of a team takes the same branches (the
+// diagonal tiles are factored redundantly in each), so the barrier counts
+// agree.
 constexpr int kNB = 32;
 constexpr int kPcThreads = 256;
 
@@ -122,13 +128,34 @@ __device__ __forceinline__ void tile_lower_inverse(const T (*S)[kNB + 1], T (*D)
     }
 }
 
+struct CtaTeam {
+    __device__ __forceinline__ int rank() const { return 0; }
+    __device__ __forceinline__ int size() const { return 1; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+struct ClusterTeam {
+    int r, n;
+    __device__ __forceinline__ ClusterTeam() {
+        unsigned v;
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(v));
+        r = (int)v;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(v));
+        n = (int)v;
+    }
+    __device__ __forceinline__ int rank() const { return r; }
+    __device__ __forceinline__ int size() const { return n; }
+    __device__ __forceinline__ void sync() const {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+};
+
 // Blocked right-looking Cholesky in place (lower triangle of the leading
 // n x n block of L, leading dimension ld).
-template <class T>
-__device__ void blocked_cholesky(T* L, int n, int ld, PcTiles<T>& s, int* bad) {
+template <class T, class Team>
+__device__ void blocked_cholesky(T* L, int n, int ld, PcTiles<T>& s, int* bad, const Team& team) {
     constexpr int E = kNB * kNB / kPcThreads;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // --- Cholesky, in place in L (lower triangle) ---
     for (int k0 = 0; k0 < n; k0 += kNB) {
         const int kw = min(kNB, n - k0);
         __syncthreads();
@@ -151,13 +178,11 @@ __device__ void blocked_cholesky(T* L, int n, int ld, PcTiles<T>& s, int* bad) {
         }
         __syncthreads();
         tile_lower_inverse(s.a, s.b, kw);
-        for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
-            const int i = idx / kNB, j = idx % kNB;
-            if (i < kw && j <= i) L[(size_t)(k0 + i) * ld + k0 + j] = s.a[i][j];
-        }
         __syncthreads();
         // panel below the diagonal block: L_rk = M_rk L_kk^-T
-        for (int r0 = k0 + kNB; r0 < n; r0 += kNB) {
+        int q = 0;
+        for (int r0 = k0 + kNB; r0 < n; r0 += kNB, ++q) {
+            if (q % team.size() != team.rank()) continue;
             tile_load(s.c, L, ld, n, r0, k0, false);
             __syncthreads();
             T acc[E];
@@ -172,10 +197,20 @@ __device__ void blocked_cholesky(T* L, int n, int ld, PcTiles<T>& s, int* bad) {
             }
             __syncthreads();
         }
+        // every CTA has read M_kk: the factor may replace it now
+        team.sync();
+        if (team.rank() == 0)
+            for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+                const int i = idx / kNB, j = idx % kNB;
+                if (i < kw && j <= i) L[(size_t)(k0 + i) * ld + k0 + j] = s.a[i][j];
+            }
+        __syncthreads();
         // trailing update of the lower triangle: M_IJ -= L_Ik L_Jk^T
+        q = 0;
         for (int i0 = k0 + kNB; i0 < n; i0 += kNB) {
-            tile_load(s.a, L, ld, n, i0, k0, false);
-            for (int j0 = k0 + kNB; j0 <= i0; j0 += kNB) {
+            for (int j0 = k0 + kNB; j0 <= i0; j0 += kNB, ++q) {
+                if (q % team.size() != team.rank()) continue;
+                tile_load(s.a, L, ld, n, i0, k0, false);
                 tile_load(s.b, L, ld, n, j0, k0, false);
                 __syncthreads();
                 T acc[E];
@@ -190,18 +225,23 @@ __device__ void blocked_cholesky(T* L, int n, int ld, PcTiles<T>& s, int* bad) {
                 __syncthreads();
             }
         }
+        team.sync();
     }
-    __syncthreads();
 }
 
 // From the lower Cholesky factor L (n x n, leading dimension ld): X = L^-1
-// (lower) and A = X^T X = (L L^T)^-1 (full), blocked.
-template <class T>
-__device__ void blocked_chol_inverse(const T* L, T* X, T* A, int n, int ld, PcTiles<T>& s) {
+// (lower) and A = X^T X = (L L^T)^-1 (full), blocked.  X by block columns
+// right-looking: the diagonal blocks X_KK = L_KK^-1 first, then for each K
+// the updates B_IJ -= L_IK X_KJ (I > K, J <= K) of the strictly lower blocks
+// B (kept in X, zero at the start), each block of row K + 1 finished as
+// X_IJ = X_II B_IJ by the CTA that adds its last term.  A may alias L.
+template <class T, class Team>
+__device__ void blocked_chol_inverse(const T* L, T* X, T* A, int n, int ld, PcTiles<T>& s, const Team& team) {
     constexpr int E = kNB * kNB / kPcThreads;
-    // --- X = L^-1: diagonal blocks, then block rows below ---
-    for (int k0 = 0; k0 < n; k0 += kNB) {
-        const int kw = min(kNB, n - k0);
+    const int nt = (n + kNB - 1) / kNB;
+    // --- diagonal blocks of X; the strictly lower blocks start at zero ---
+    for (int k = team.rank(); k < nt; k += team.size()) {
+        const int k0 = k * kNB, kw = min(kNB, n - k0);
         __syncthreads();
         tile_load(s.a, L, ld, n, k0, k0, false);
         __syncthreads();
@@ -211,41 +251,60 @@ __device__ void blocked_chol_inverse(const T* L, T* X, T* A, int n, int ld, PcTi
             const int i = idx / kNB, j = idx % kNB;
             if (i < kw && j < kw) X[(size_t)(k0 + i) * ld + k0 + j] = s.b[i][j];
         }
+        for (int j0 = 0; j0 < k0; j0 += kNB)
+            for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+                const int i = idx / kNB, j = idx % kNB;
+                if (i < kw) X[(size_t)(k0 + i) * ld + j0 + j] = (T)0;
+            }
     }
-    for (int j0 = 0; j0 < n; j0 += kNB) {
-        for (int i0 = j0 + kNB; i0 < n; i0 += kNB) {
-            // T = sum_{K = J .. I-1} L_IK X_KJ, then X_IJ = -X_II T
-            T acc[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] = 0;
-            for (int q0 = j0; q0 < i0; q0 += kNB) {
+    team.sync();
+    // --- strictly lower blocks, one block column step K at a time ---
+    for (int K = 0; K + 1 < nt; ++K) {
+        const int K0 = K * kNB;
+        int q = 0;
+        for (int I = K + 1; I < nt; ++I) {
+            const int I0 = I * kNB;
+            for (int J = 0; J <= K; ++J, ++q) {
+                if (q % team.size() != team.rank()) continue;
+                const int J0 = J * kNB;
                 __syncthreads();
-                tile_load(s.a, L, ld, n, i0, q0, false);
-                tile_load(s.b, X, ld, n, q0, j0, false);
+                tile_load(s.a, L, ld, n, I0, K0, false);  // L_IK
+                tile_load(s.b, X, ld, n, K0, J0, false);  // X_KJ
                 __syncthreads();
-                tile_mac<T, false>(s.a, s.b, acc);
-            }
-            __syncthreads();
+                T acc[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int idx = threadIdx.x + e * kPcThreads;
-                s.c[idx / kNB][idx % kNB] = acc[e];
-            }
-            tile_load(s.a, X, ld, n, i0, i0, false);
-            __syncthreads();
+                for (int e = 0; e < E; ++e) {
+                    const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
+                    acc[e] = (I0 + r < n && J0 + c < n) ? -X[(size_t)(I0 + r) * ld + J0 + c] : (T)0;
+                }
+                tile_mac<T, false>(s.a, s.b, acc);  // acc = -(B_IJ - L_IK X_KJ)
+                if (I == K + 1) {
+                    __syncthreads();
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] = 0;
-            tile_mac<T, false>(s.a, s.c, acc);
+                    for (int e = 0; e < E; ++e) {
+                        const int idx = threadIdx.x + e * kPcThreads;
+                        s.c[idx / kNB][idx % kNB] = acc[e];
+                    }
+                    tile_load(s.a, X, ld, n, I0, I0, false);  // X_II
+                    __syncthreads();
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
-                if (i0 + r < n && j0 + c < n) X[(size_t)(i0 + r) * ld + j0 + c] = -acc[e];
+                    for (int e = 0; e < E; ++e) acc[e] = 0;
+                    tile_mac<T, false>(s.a, s.c, acc);  // acc = -X_II B_IJ
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
+                    if (I0 + r < n && J0 + c < n) X[(size_t)(I0 + r) * ld + J0 + c] = -acc[e];
+                }
             }
         }
+        team.sync();
     }
     // --- A = X^T X (lower triangle, mirrored) ---
+    int q = 0;
     for (int i0 = 0; i0 < n; i0 += kNB) {
-        for (int j0 = 0; j0 <= i0; j0 += kNB) {
+        for (int j0 = 0; j0 <= i0; j0 += kNB, ++q) {
+            if (q % team.size() != team.rank()) continue;
             T acc[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) acc[e] = 0;
@@ -267,13 +326,13 @@ __device__ void blocked_chol_inverse(const T* L, T* X, T* A, int n, int ld, PcTi
             }
         }
     }
-    __syncthreads();
+    team.sync();
 }
 
-template <class T>
-__device__ void blocked_spd_inverse(T* L, T* X, T* A, int m, PcTiles<T>& s, int* bad) {
-    blocked_cholesky(L, m, m, s, bad);
-    blocked_chol_inverse(L, X, A, m, m, s);
+template <class T, class Team>
+__device__ void blocked_spd_inverse(T* L, T* X, T* A, int m, PcTiles<T>& s, int* bad, const Team& team) {
+    blocked_cholesky(L, m, m, s, bad, team);
+    blocked_chol_inverse(L, X, A, m, m, s, team);
 }
 
 // 6 x 6 symmetric positive definite inverse in one thread (Cholesky).

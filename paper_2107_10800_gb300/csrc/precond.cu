@@ -4,9 +4,11 @@
 // Build, per body p (one block): M^(pp) from the pair tensors, its explicit
 // inverse by blocked Cholesky, blocked triangular inverse and X^T X on 32 x 32
 // shared-memory tiles, Y_p = (M^(pp))^-1 K_p, S_p = K_p^T Y_p and
-// N~_p = S_p^-1.  Per articulated body a (one block): H_a = C_a N~_a C_a^T and
-// its generalised inverse G~_a (Eq. block_diag_const_res) by symmetric pivoted
-// Cholesky (column by column, then the blocked inverse of the rank-r factor):
+// N~_p = S_p^-1 (a body of more than two tiles takes a cluster of CTAs when
+// such bodies are too few to fill the GPU).  Per articulated body a (one
+// block): H_a = C_a N~_a C_a^T and its generalised inverse G~_a
+// (Eq. block_diag_const_res) by symmetric pivoted Cholesky (32-column panels,
+// then the blocked inverse of the rank-r factor):
 // H(perm) = L L^T with L of rank r gives
 // G~ = perm [(L11 L11^T)^-1 0; 0 0] perm^T, which solves H phi = c exactly for
 // every c in range(H) = range(C_a).
@@ -31,16 +33,21 @@ namespace am {
 
 constexpr int kRows = 32;  // rows per apply work item
 
-template <class T>
+// One body per team: body_list[blockIdx.x / team size]; a cluster team
+// splits the pair tensors, the tiles of the blocked inverse and the rows of
+// Y among its CTAs, and its first CTA forms N~_p.
+template <class T, class Team>
 __global__ void __launch_bounds__(kPcThreads)
-k_pcb_build(const int* __restrict__ blob_off, const double4_32a* __restrict__ r4,
-            const double4_32a* __restrict__ d4, const long long* __restrict__ moff,
-            T* __restrict__ minv, T* __restrict__ work, T* __restrict__ Y, double* __restrict__ Nt,
-            RpyK<double> prm, int wall, int* flags) {
+k_pcb_build(const int* __restrict__ body_list, const int* __restrict__ blob_off,
+            const double4_32a* __restrict__ r4, const double4_32a* __restrict__ d4,
+            const long long* __restrict__ moff, T* __restrict__ minv, T* __restrict__ work,
+            T* __restrict__ Y, double* __restrict__ Nt, RpyK<double> prm, int wall, int* flags) {
     __shared__ double sh[64];
     __shared__ PcTiles<T> tiles;
     __shared__ int s_bad;
-    const int b = blockIdx.x;
+    const Team team;
+    const int tr = team.rank(), ts = team.size();
+    const int b = body_list[blockIdx.x / ts];
     const int i0 = blob_off[b];
     const int nbl = blob_off[b + 1] - i0;
     const int m = 3 * nbl;
@@ -48,22 +55,22 @@ k_pcb_build(const int* __restrict__ blob_off, const double4_32a* __restrict__ r4
     T* A = minv + moff[b];
     T* L = work + 2 * moff[b];
     T* X = L + (size_t)m * m;
-    for (int idx = threadIdx.x; idx < nbl * nbl; idx += blockDim.x) {
+    for (int idx = threadIdx.x + tr * blockDim.x; idx < nbl * nbl; idx += blockDim.x * ts) {
         const int ti = idx / nbl, sj = idx % nbl;
         double Tt[9];
         pair_tensor_f64(r4[i0 + ti], r4[i0 + sj], prm, wall, Tt);
         for (int a = 0; a < 3; ++a)
             for (int c = 0; c < 3; ++c) L[(size_t)(3 * ti + a) * m + 3 * sj + c] = (T)Tt[3 * a + c];
     }
-    __syncthreads();
+    team.sync();
     // (M^(pp))^-1 by blocked Cholesky, triangular inverse and X^T X
-    blocked_spd_inverse(L, X, A, m, tiles, &s_bad);
+    blocked_spd_inverse(L, X, A, m, tiles, &s_bad, team);
     if (s_bad) {
-        if (threadIdx.x == 0) atomicOr(flags, kFlagSingular);
+        if (threadIdx.x == 0 && tr == 0) atomicOr(flags, kFlagSingular);
         return;
     }
     T* Yb = Y + 18 * (size_t)i0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    for (int i = threadIdx.x + tr * blockDim.x; i < m; i += blockDim.x * ts) {
         double y[6] = {0, 0, 0, 0, 0, 0};
         for (int bb = 0; bb < nbl; ++bb) {
             const double v[3] = {(double)A[(size_t)(3 * bb) * m + i], (double)A[(size_t)(3 * bb + 1) * m + i],
@@ -76,7 +83,8 @@ k_pcb_build(const int* __restrict__ blob_off, const double4_32a* __restrict__ r4
         }
         for (int a = 0; a < 6; ++a) Yb[6 * (size_t)i + a] = (T)y[a];
     }
-    __syncthreads();
+    team.sync();
+    if (tr != 0) return;
     if (threadIdx.x < 36) {
         const int c = threadIdx.x / 6, e = threadIdx.x % 6;
         double s = 0.0;
@@ -113,22 +121,30 @@ __device__ __forceinline__ void e_times_n(double sg, const double* l, const doub
     }
 }
 
-template <class T>
+// One articulated body per team: asm_list[blockIdx.x / team size].  In a
+// cluster team the first CTA takes the column steps of each panel (pivot
+// search and swaps included) and the team shares the trailing tiles, the
+// blocked inverse and the scatter into G~; the first CTA publishes the rank
+// (or -1 while the factorisation goes on) in rank_out[a] before each team
+// barrier, so every CTA leaves the panel loop at the same panel.
+template <class T, class Team>
 __global__ void __launch_bounds__(kPcThreads)
-k_pca_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
-            const int* __restrict__ bp, const int* __restrict__ bq, const double* __restrict__ lp,
-            const double* __restrict__ lq, const double* __restrict__ Nt,
+k_pca_build(const int* __restrict__ asm_list, const int* __restrict__ asm_link_off,
+            const int* __restrict__ asm_link_idx, const int* __restrict__ bp, const int* __restrict__ bq,
+            const double* __restrict__ lp, const double* __restrict__ lq, const double* __restrict__ Nt,
             const long long* __restrict__ goff, T* __restrict__ G, T* __restrict__ gwork,
             int* __restrict__ perm_all, const long long* __restrict__ poff, int* __restrict__ rank_out,
             double tol) {
     extern __shared__ unsigned char dyn_smem[];
-    T* colk = reinterpret_cast<T*>(dyn_smem);  // m values: the pivot column
+    double* dg = reinterpret_cast<double*>(dyn_smem);  // m values: the Schur-complement diagonal
     __shared__ PcTiles<T> tiles;
     __shared__ double s_wv[32];
     __shared__ int s_wi[32];
     __shared__ double s_pv;
     __shared__ int s_pi;
-    const int a = blockIdx.x;
+    const Team team;
+    const int tr = team.rank(), ts = team.size();
+    const int a = asm_list[blockIdx.x / ts];
     const int L0 = asm_link_off[a];
     const int Pa = asm_link_off[a + 1] - L0;
     const int m = 3 * Pa;
@@ -138,7 +154,7 @@ k_pca_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_li
     T* X = H + (size_t)m * m;
     T* Ga = G + goff[a];
     int* perm = perm_all + poff[a];
-    for (int idx = threadIdx.x; idx < Pa * Pa; idx += blockDim.x) {
+    for (int idx = threadIdx.x + tr * blockDim.x; idx < Pa * Pa; idx += blockDim.x * ts) {
         const int r = idx / Pa, c = idx % Pa;
         const int ln = asm_link_idx[L0 + r], lk = asm_link_idx[L0 + c];
         double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -163,81 +179,127 @@ k_pca_build(const int* __restrict__ asm_link_off, const int* __restrict__ asm_li
         for (int x = 0; x < 3; ++x)
             for (int yy = 0; yy < 3; ++yy) H[(size_t)(3 * r + x) * m + 3 * c + yy] = (T)blk[x * 3 + yy];
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
-    __syncthreads();
+    if (tr == 0)
+        for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
+    team.sync();
     // symmetric pivoted Cholesky (largest remaining diagonal first, ties to
-    // the lower index), stopped at the first pivot <= tol * the first one
+    // the lower index), stopped at the first pivot <= tol * the first one;
+    // blocked: within a panel of 32 columns each column is formed from the
+    // panel's earlier columns (left-looking) with the Schur-complement
+    // diagonal dg kept up to date for the pivot search, and after the panel
+    // the trailing block (both triangles, which the row and column swaps
+    // read) takes one tile-product update.
+    if (tr == 0)
+        for (int i = threadIdx.x; i < m; i += blockDim.x) dg[i] = (double)H[(size_t)i * m + i];
+    __syncthreads();
     double d0 = 0.0;
     int r = m;
-    for (int k = 0; k < m; ++k) {
-        double best = -1.0;
-        int bi = 0x7fffffff;
-        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
-            const double v = (double)H[(size_t)i * m + i];
-            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, best, o);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) { s_wv[wid] = best; s_wi[wid] = bi; }
-        __syncthreads();
-        if (wid == 0) {
-            best = lane < nw ? s_wv[lane] : -1.0;
-            bi = lane < nw ? s_wi[lane] : 0x7fffffff;
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, best, o);
-                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    for (int k0 = 0; k0 < m; k0 += kNB) {
+        const int kend = min(m, k0 + kNB);
+        if (tr == 0) {
+            bool stop = false;
+            for (int k = k0; k < kend; ++k) {
+                double best = -1.0;
+                int bi = 0x7fffffff;
+                for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+                    const double v = dg[i];
+                    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_down_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+                }
+                if (lane == 0) { s_wv[wid] = best; s_wi[wid] = bi; }
+                __syncthreads();
+                if (wid == 0) {
+                    best = lane < nw ? s_wv[lane] : -1.0;
+                    bi = lane < nw ? s_wi[lane] : 0x7fffffff;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const double ov = __shfl_down_sync(0xffffffffu, best, o);
+                        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+                    }
+                    if (lane == 0) { s_pv = best; s_pi = bi; }
+                }
+                __syncthreads();
+                const double dmax = s_pv;
+                const int j = s_pi;
+                if (k == 0) d0 = dmax;
+                if (!(dmax > tol * d0) || !(dmax > 0.0)) { r = k; stop = true; break; }
+                if (j != k) {
+                    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+                        const T t = H[(size_t)k * m + c];
+                        H[(size_t)k * m + c] = H[(size_t)j * m + c];
+                        H[(size_t)j * m + c] = t;
+                    }
+                    __syncthreads();
+                    for (int rr = threadIdx.x; rr < m; rr += blockDim.x) {
+                        const T t = H[(size_t)rr * m + k];
+                        H[(size_t)rr * m + k] = H[(size_t)rr * m + j];
+                        H[(size_t)rr * m + j] = t;
+                    }
+                    if (threadIdx.x == 0) {
+                        const int t = perm[k];
+                        perm[k] = perm[j];
+                        perm[j] = t;
+                        const double td = dg[k];
+                        dg[k] = dg[j];
+                        dg[j] = td;
+                    }
+                    __syncthreads();
+                }
+                // column k: Schur value from the panel's earlier columns, scaled
+                const double sk = sqrt(dmax);
+                const T* rowk = H + (size_t)k * m;
+                for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+                    T* rowi = H + (size_t)i * m;
+                    double v = (double)rowi[k];
+                    for (int t = k0; t < k; ++t) v -= (double)rowi[t] * (double)rowk[t];
+                    if (i == k) {
+                        rowi[k] = (T)sk;
+                    } else {
+                        const double l = v / sk;
+                        rowi[k] = (T)l;
+                        dg[i] -= l * l;
+                    }
+                }
+                __syncthreads();
             }
-            if (lane == 0) { s_pv = best; s_pi = bi; }
+            if (threadIdx.x == 0) rank_out[a] = stop ? r : -1;
         }
-        __syncthreads();
-        const double dmax = s_pv;
-        const int j = s_pi;
-        if (k == 0) d0 = dmax;
-        if (!(dmax > tol * d0) || !(dmax > 0.0)) { r = k; break; }
-        if (j != k) {
-            for (int c = threadIdx.x; c < m; c += blockDim.x) {
-                const T t = H[(size_t)k * m + c];
-                H[(size_t)k * m + c] = H[(size_t)j * m + c];
-                H[(size_t)j * m + c] = t;
+        team.sync();
+        const int st = *reinterpret_cast<volatile const int*>(rank_out + a);
+        if (st >= 0) { r = st; break; }
+        // trailing update of rows and columns >= kend by the panel's columns
+        constexpr int E = kNB * kNB / kPcThreads;
+        int q = 0;
+        for (int i0 = kend; i0 < m; i0 += kNB) {
+            for (int j0 = kend; j0 < m; j0 += kNB, ++q) {
+                if (q % ts != tr) continue;
+                tile_load(tiles.a, H, m, m, i0, k0, false);
+                tile_load(tiles.b, H, m, m, j0, k0, false);
+                __syncthreads();
+                T acc[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[e] = 0;
+                tile_mac<T, true>(tiles.a, tiles.b, acc);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int idx = threadIdx.x + e * kPcThreads, rr = idx / kNB, c = idx % kNB;
+                    if (i0 + rr < m && j0 + c < m) H[(size_t)(i0 + rr) * m + j0 + c] -= acc[e];
+                }
+                __syncthreads();
             }
-            __syncthreads();
-            for (int rr = threadIdx.x; rr < m; rr += blockDim.x) {
-                const T t = H[(size_t)rr * m + k];
-                H[(size_t)rr * m + k] = H[(size_t)rr * m + j];
-                H[(size_t)rr * m + j] = t;
-            }
-            if (threadIdx.x == 0) {
-                const int t = perm[k];
-                perm[k] = perm[j];
-                perm[j] = t;
-            }
-            __syncthreads();
         }
-        for (int i = k + threadIdx.x; i < m; i += blockDim.x) colk[i] = H[(size_t)i * m + k];
-        __syncthreads();
-        // trailing update H_ij -= h_ik h_jk / h_kk and the scaled column
-        const T dk = colk[k];
-        const T sdk = (T)sqrt((double)dk);
-        const T invd = (T)1 / dk;
-        const int len = m - k - 1;
-        for (int idx = threadIdx.x; idx < len * len; idx += blockDim.x) {
-            const int i = k + 1 + idx / len, jj = k + 1 + idx % len;
-            H[(size_t)i * m + jj] -= colk[i] * colk[jj] * invd;
-        }
-        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) H[(size_t)i * m + k] = colk[i] / sdk;
-        if (threadIdx.x == 0) H[(size_t)k * m + k] = sdk;
-        __syncthreads();
+        team.sync();
     }
-    if (threadIdx.x == 0) rank_out[a] = r;
+    if (threadIdx.x == 0 && tr == 0) rank_out[a] = r;
     // (L11 L11^T)^-1 of the rank-r leading block, blocked (written over H)
-    blocked_chol_inverse(H, X, H, r, m, tiles);
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Ga[idx] = (T)0;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+    blocked_chol_inverse(H, X, H, r, m, tiles, team);
+    for (int idx = threadIdx.x + tr * blockDim.x; idx < m * m; idx += blockDim.x * ts) Ga[idx] = (T)0;
+    team.sync();
+    for (int idx = threadIdx.x + tr * blockDim.x; idx < r * r; idx += blockDim.x * ts) {
         const int i = idx / r, jj = idx % r;
         Ga[(size_t)perm[i] * m + perm[jj]] = H[(size_t)i * m + jj];
     }
@@ -401,25 +463,68 @@ k_pc_ap3(int Nb, int M, const int* __restrict__ pcw_body, const int* __restrict_
 }
 
 // ----------------------------------------------------------------- host ---
+// Launch of a build kernel over the items list[0 .. n): one CTA each, or
+// one cluster of cs CTAs each.
+template <class K, class... Args>
+static void launch_team(K kernel, int n, int cs, size_t smem, cudaStream_t s, Args... args) {
+    if (n <= 0) return;
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3((unsigned)(n * cs));
+    lc.blockDim = dim3(kPcThreads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    lc.attrs = at;
+    lc.numAttrs = cs > 1 ? 1 : 0;
+    cudaLaunchKernelEx(&lc, kernel, args...);
+    count_launch();
+}
+
+template <class T>
+static void pca_build_t(am_handle* h, double tol) {
+    const size_t smem = (size_t)3 * std::max(1, h->max_asm_links) * sizeof(double);  // Schur diagonal
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_pca_build<T, CtaTeam>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_pca_build<T, ClusterTeam>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    const int n_one = h->pca_cs > 1 ? h->n_pca_small : h->NA;
+    launch_team(k_pca_build<T, CtaTeam>, n_one, 1, smem, h->stream, (const int*)h->d_pca_list,
+                (const int*)h->d_asm_link_off, (const int*)h->d_asm_link_idx, (const int*)h->d_bp,
+                (const int*)h->d_bq, (const double*)h->d_lp, (const double*)h->d_lq, (const double*)h->d_Nt,
+                (const long long*)h->d_G_off, (T*)h->d_G, (T*)h->d_Gwork, h->d_perm,
+                (const long long*)h->d_perm_off, h->d_G_rank, tol);
+    if (h->pca_cs > 1)
+        launch_team(k_pca_build<T, ClusterTeam>, h->NA - h->n_pca_small, h->pca_cs, smem, h->stream,
+                    (const int*)(h->d_pca_list + h->n_pca_small), (const int*)h->d_asm_link_off,
+                    (const int*)h->d_asm_link_idx, (const int*)h->d_bp, (const int*)h->d_bq,
+                    (const double*)h->d_lp, (const double*)h->d_lq, (const double*)h->d_Nt,
+                    (const long long*)h->d_G_off, (T*)h->d_G, (T*)h->d_Gwork, h->d_perm,
+                    (const long long*)h->d_perm_off, h->d_G_rank, tol);
+}
+
 template <class T>
 static void pc_build_t(am_handle* h, double tol) {
     cudaStream_t s = h->stream;
     // one block of kPcThreads per body and per articulated body (the tile
     // routines assume that block size)
-    const size_t smem_a = (size_t)3 * std::max(1, h->max_asm_links) * sizeof(T);  // pivot column
-    if (smem_a > 48 * 1024)
-        cudaFuncSetAttribute(k_pca_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
-    k_pcb_build<T><<<h->M, kPcThreads, 0, s>>>(h->d_blob_off, h->d_r4, h->d_d4, h->d_minv_off,
-                                                 (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt,
-                                                 rpy_consts<double>(h->prm), h->cfg.wall, h->d_flags);
-    count_launch();
-    if (h->P) {
-        k_pca_build<T><<<h->NA, kPcThreads, smem_a, s>>>(h->d_asm_link_off, h->d_asm_link_idx, h->d_bp,
-                                                      h->d_bq, h->d_lp, h->d_lq, h->d_Nt, h->d_G_off,
-                                                      (T*)h->d_G, (T*)h->d_Gwork, h->d_perm,
-                                                      h->d_perm_off, h->d_G_rank, tol);
-        count_launch();
-    }
+    // bodies of one or two 32-row tiles one CTA each; larger bodies one
+    // cluster of pcb_cs CTAs each when they are too few to fill the GPU
+    const int n_one = h->pcb_cs > 1 ? h->n_pcb_small : h->M;
+    launch_team(k_pcb_build<T, CtaTeam>, n_one, 1, 0, s, (const int*)h->d_pcb_list, (const int*)h->d_blob_off,
+                (const double4_32a*)h->d_r4, (const double4_32a*)h->d_d4, (const long long*)h->d_minv_off,
+                (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt, rpy_consts<double>(h->prm), h->cfg.wall,
+                h->d_flags);
+    if (h->pcb_cs > 1)
+        launch_team(k_pcb_build<T, ClusterTeam>, h->M - h->n_pcb_small, h->pcb_cs, 0, s,
+                    (const int*)(h->d_pcb_list + h->n_pcb_small), (const int*)h->d_blob_off,
+                    (const double4_32a*)h->d_r4, (const double4_32a*)h->d_d4, (const long long*)h->d_minv_off,
+                    (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt, rpy_consts<double>(h->prm),
+                    h->cfg.wall, h->d_flags);
+    if (h->P) pca_build_t<T>(h, tol);
 }
 
 void pc_apply_links(am_handle* h, const double* r, double* z) {
@@ -438,15 +543,7 @@ void pc_apply_links(am_handle* h, const double* r, double* z) {
 void pc_build(am_handle* h) {
     if (h->sb) {
         sb_pc_build(h);
-        if (h->P) {
-            const size_t smem_a = (size_t)3 * std::max(1, h->max_asm_links) * sizeof(double);
-            if (smem_a > 48 * 1024)
-                cudaFuncSetAttribute(k_pca_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
-            k_pca_build<double><<<h->NA, kPcThreads, smem_a, h->stream>>>(
-                h->d_asm_link_off, h->d_asm_link_idx, h->d_bp, h->d_bq, h->d_lp, h->d_lq, h->d_Nt, h->d_G_off,
-                (double*)h->d_G, (double*)h->d_Gwork, h->d_perm, h->d_perm_off, h->d_G_rank, 1e-11);
-            count_launch();
-        }
+        if (h->P) pca_build_t<double>(h, 1e-11);
         h->pc_valid = true;
         return;
     }
