@@ -110,21 +110,52 @@ __device__ __forceinline__ void tile_mac(const T (*A)[kNB + 1], const T (*B)[kNB
     }
 }
 
-// inverse of the lower triangle of S (kw x kw) into D (zeros above the
-// diagonal); thread j computes column j by forward substitution
+// In place: the lower Cholesky factor of the leading kw x kw part of the
+// tile S (right-looking, one column per step, every thread of the block).
+// A non-positive pivot sets *bad and is replaced by 1.
+template <class T>
+__device__ __forceinline__ void tile_cholesky(T (*S)[kNB + 1], int kw, int* bad) {
+    for (int j = 0; j < kw; ++j) {
+        T d = S[j][j];
+        if (!(d > (T)0)) d = (T)1;
+        const T sd = sqrt(d);
+        const int i = threadIdx.x;
+        if (i > j && i < kw) S[i][j] /= sd;
+        __syncthreads();
+        // the pivot itself (read by no one in this half-step) and the
+        // trailing lower triangle
+        if (threadIdx.x == 0) {
+            if (!(S[j][j] > (T)0)) *bad = 1;
+            S[j][j] = sd;
+        }
+        const int w = kw - 1 - j;
+        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+            const int r = j + 1 + idx / w, c = j + 1 + idx % w;
+            if (c <= r) S[r][c] -= S[r][j] * S[c][j];
+        }
+        __syncthreads();
+    }
+}
+
+// D = S^-1 for the lower triangle of S (kw x kw), zeros elsewhere in D:
+// forward substitution on the identity, one row of D per step, that row's
+// updates of the rows below spread over the block (every thread calls).
 template <class T>
 __device__ __forceinline__ void tile_lower_inverse(const T (*S)[kNB + 1], T (*D)[kNB + 1], int kw) {
-    const int j = threadIdx.x;
-    if (j < kNB) {
-        for (int i = 0; i < kNB; ++i) D[i][j] = (T)0;
-        if (j < kw) {
-            D[j][j] = (T)1 / S[j][j];
-            for (int i = j + 1; i < kw; ++i) {
-                T s = 0;
-                for (int t = j; t < i; ++t) s = fma(S[i][t], D[t][j], s);
-                D[i][j] = -s / S[i][i];
-            }
+    for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+        const int i = idx / kNB, j = idx % kNB;
+        D[i][j] = (i == j && i < kw) ? (T)1 : (T)0;
+    }
+    __syncthreads();
+    for (int i = 0; i < kw; ++i) {
+        if (threadIdx.x <= i) D[i][threadIdx.x] /= S[i][i];
+        __syncthreads();
+        const int w = i + 1;
+        for (int idx = threadIdx.x; idx < (kw - 1 - i) * w; idx += blockDim.x) {
+            const int q = i + 1 + idx / w, jj = idx % w;
+            D[q][jj] -= S[q][i] * D[i][jj];
         }
+        __syncthreads();
     }
 }
 
@@ -155,28 +186,12 @@ struct ClusterTeam {
 template <class T, class Team>
 __device__ void blocked_cholesky(T* L, int n, int ld, PcTiles<T>& s, int* bad, const Team& team) {
     constexpr int E = kNB * kNB / kPcThreads;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k0 = 0; k0 < n; k0 += kNB) {
         const int kw = min(kNB, n - k0);
         __syncthreads();
         tile_load(s.a, L, ld, n, k0, k0, false);
         __syncthreads();
-        if (wid == 0) {
-            for (int j = 0; j < kw; ++j) {
-                if (lane == j) {
-                    T d = s.a[j][j];
-                    if (!(d > (T)0)) { *bad = 1; d = (T)1; }
-                    s.a[j][j] = sqrt(d);
-                }
-                __syncwarp();
-                if (lane > j && lane < kw) s.a[lane][j] /= s.a[j][j];
-                __syncwarp();
-                if (lane > j && lane < kw)
-                    for (int c = j + 1; c <= lane; ++c) s.a[lane][c] -= s.a[lane][j] * s.a[c][j];
-                __syncwarp();
-            }
-        }
-        __syncthreads();
+        tile_cholesky(s.a, kw, bad);
         tile_lower_inverse(s.a, s.b, kw);
         __syncthreads();
         // panel below the diagonal block: L_rk = M_rk L_kk^-T

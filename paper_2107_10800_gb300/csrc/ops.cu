@@ -710,16 +710,18 @@ __global__ void k_arnoldi_finish_sys(const ArnoldiCtrl* __restrict__ c, const do
     double* css = cs + (size_t)s * m;
     double* sns = sn + (size_t)s * m;
     double* gs = g + (size_t)s * m1;
-    for (int i = 0; i <= j; ++i) h[i] = hc[i];
-    h[j + 1] = nrm;
+    // the earlier rotations applied in order; only the running entry carries
+    // from one rotation to the next, the rest are loads and stores
+    double carry = hc[0];
     for (int i = 0; i < j; ++i) {
-        const double t = css[i] * h[i] + sns[i] * h[i + 1];
-        h[i + 1] = -sns[i] * h[i] + css[i] * h[i + 1];
+        const double b = hc[i + 1];
+        const double t = css[i] * carry + sns[i] * b;
+        carry = -sns[i] * carry + css[i] * b;
         h[i] = t;
     }
-    const double d = hypot(h[j], h[j + 1]);
+    const double d = hypot(carry, nrm);
     double cc = 1.0, sg = 0.0;
-    if (d > 0.0) { cc = h[j] / d; sg = h[j + 1] / d; }
+    if (d > 0.0) { cc = carry / d; sg = nrm / d; }
     css[j] = cc; sns[j] = sg;
     h[j] = d;
     h[j + 1] = 0.0;

@@ -138,9 +138,7 @@ k_pca_build(const int* __restrict__ asm_list, const int* __restrict__ asm_link_o
     extern __shared__ unsigned char dyn_smem[];
     double* dg = reinterpret_cast<double*>(dyn_smem);  // m values: the Schur-complement diagonal
     __shared__ PcTiles<T> tiles;
-    __shared__ double s_wv[32];
-    __shared__ int s_wi[32];
-    __shared__ double s_pv;
+    __shared__ double s_pv, s_sk, s_isk;
     __shared__ int s_pi;
     const Team team;
     const int tr = team.rank(), ts = team.size();
@@ -149,7 +147,7 @@ k_pca_build(const int* __restrict__ asm_list, const int* __restrict__ asm_link_o
     const int Pa = asm_link_off[a + 1] - L0;
     const int m = 3 * Pa;
     if (m == 0) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T* H = gwork + 2 * goff[a];
     T* X = H + (size_t)m * m;
     T* Ga = G + goff[a];
@@ -199,28 +197,25 @@ k_pca_build(const int* __restrict__ asm_list, const int* __restrict__ asm_link_o
         if (tr == 0) {
             bool stop = false;
             for (int k = k0; k < kend; ++k) {
-                double best = -1.0;
-                int bi = 0x7fffffff;
-                for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
-                    const double v = dg[i];
-                    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_down_sync(0xffffffffu, best, o);
-                    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-                }
-                if (lane == 0) { s_wv[wid] = best; s_wi[wid] = bi; }
-                __syncthreads();
+                // pivot: warp 0 scans the remaining diagonal
                 if (wid == 0) {
-                    best = lane < nw ? s_wv[lane] : -1.0;
-                    bi = lane < nw ? s_wi[lane] : 0x7fffffff;
+                    double best = -1.0;
+                    int bi = 0x7fffffff;
+                    for (int i = k + lane; i < m; i += 32) {
+                        const double v = dg[i];
+                        if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+                    }
                     for (int o = 16; o > 0; o >>= 1) {
                         const double ov = __shfl_down_sync(0xffffffffu, best, o);
                         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
                         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
                     }
-                    if (lane == 0) { s_pv = best; s_pi = bi; }
+                    if (lane == 0) {
+                        s_pv = best;
+                        s_pi = bi;
+                        s_sk = best > 0.0 ? sqrt(best) : 1.0;
+                        s_isk = 1.0 / s_sk;
+                    }
                 }
                 __syncthreads();
                 const double dmax = s_pv;
@@ -228,16 +223,32 @@ k_pca_build(const int* __restrict__ asm_list, const int* __restrict__ asm_link_o
                 if (k == 0) d0 = dmax;
                 if (!(dmax > tol * d0) || !(dmax > 0.0)) { r = k; stop = true; break; }
                 if (j != k) {
-                    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-                        const T t = H[(size_t)k * m + c];
-                        H[(size_t)k * m + c] = H[(size_t)j * m + c];
-                        H[(size_t)j * m + c] = t;
-                    }
-                    __syncthreads();
-                    for (int rr = threadIdx.x; rr < m; rr += blockDim.x) {
-                        const T t = H[(size_t)rr * m + k];
-                        H[(size_t)rr * m + k] = H[(size_t)rr * m + j];
-                        H[(size_t)rr * m + j] = t;
+                    // rows k, j and columns k, j exchanged in one pass: the
+                    // row entries off columns k, j, the column entries off
+                    // rows k, j, and the 2 x 2 block of both
+                    for (int x = threadIdx.x; x < 2 * m; x += blockDim.x) {
+                        if (x < m) {
+                            const int c = x;
+                            if (c == j) continue;
+                            if (c == k) {
+                                const T hkk = H[(size_t)k * m + k], hjj = H[(size_t)j * m + j];
+                                const T hkj = H[(size_t)k * m + j], hjk = H[(size_t)j * m + k];
+                                H[(size_t)k * m + k] = hjj;
+                                H[(size_t)j * m + j] = hkk;
+                                H[(size_t)k * m + j] = hjk;
+                                H[(size_t)j * m + k] = hkj;
+                            } else {
+                                const T t = H[(size_t)k * m + c];
+                                H[(size_t)k * m + c] = H[(size_t)j * m + c];
+                                H[(size_t)j * m + c] = t;
+                            }
+                        } else {
+                            const int rr = x - m;
+                            if (rr == k || rr == j) continue;
+                            const T t = H[(size_t)rr * m + k];
+                            H[(size_t)rr * m + k] = H[(size_t)rr * m + j];
+                            H[(size_t)rr * m + j] = t;
+                        }
                     }
                     if (threadIdx.x == 0) {
                         const int t = perm[k];
@@ -249,17 +260,33 @@ k_pca_build(const int* __restrict__ asm_list, const int* __restrict__ asm_link_o
                     }
                     __syncthreads();
                 }
-                // column k: Schur value from the panel's earlier columns, scaled
-                const double sk = sqrt(dmax);
-                const T* rowk = H + (size_t)k * m;
+                // column k: Schur value from the panel's earlier columns (at
+                // most 31, loaded together and summed in T, groups of 8 past
+                // the panel's count skipped), scaled by the pivot's inverse
+                // square root (formed once, by the thread that found it)
+                const double sk = s_sk, isk = s_isk;
+                const T* rowk = H + (size_t)k * m + k0;
+                const int nk = k - k0;
                 for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
                     T* rowi = H + (size_t)i * m;
-                    double v = (double)rowi[k];
-                    for (int t = k0; t < k; ++t) v -= (double)rowi[t] * (double)rowk[t];
+                    T pa[kNB], pb[kNB];
+#pragma unroll
+                    for (int t = 0; t < kNB; ++t) {
+                        pa[t] = t < nk ? rowi[k0 + t] : (T)0;
+                        pb[t] = t < nk ? rowk[t] : (T)0;
+                    }
+                    T acc = 0;
+#pragma unroll
+                    for (int g = 0; g < kNB; g += 8)
+                        if (g < nk) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) acc = fma(pa[g + u], pb[g + u], acc);
+                        }
+                    const double v = (double)rowi[k] - (double)acc;
                     if (i == k) {
                         rowi[k] = (T)sk;
                     } else {
-                        const double l = v / sk;
+                        const double l = v * isk;
                         rowi[k] = (T)l;
                         dg[i] -= l * l;
                     }
@@ -326,9 +353,21 @@ k_pc_ap1(const int* __restrict__ pcw_body, const int* __restrict__ pcw_chunk,
     const double* r1 = r + 3 * (size_t)i0;
     double s = 0.0;
     if (row < m) {
-        T acc = 0;
-        for (int k = part; k < m; k += 4) acc = fma(A[(size_t)k * m + row], (T)r1[k], acc);
-        s = (double)acc;
+        // eight independent loads in flight per thread, four partial sums
+        T acc[4] = {0, 0, 0, 0};
+        int k = part;
+        for (; k + 28 < m; k += 32) {
+            T av[8], rv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                av[u] = A[(size_t)(k + 4 * u) * m + row];
+                rv[u] = (T)r1[k + 4 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u & 3] = fma(av[u], rv[u], acc[u & 3]);
+        }
+        for (; k < m; k += 4) acc[0] = fma(A[(size_t)k * m + row], (T)r1[k], acc[0]);
+        s = (double)((acc[0] + acc[1]) + (acc[2] + acc[3]));
     }
     red[part][lane] = s;
     // partial Y^T r1 over this chunk's rows (warp `part` takes columns part, part+4)
@@ -350,22 +389,28 @@ k_pc_ap1(const int* __restrict__ pcw_body, const int* __restrict__ pcw_chunk,
     }
 }
 
-// U^_b = N~_b (-r2_b - sum of the body's Y^T r1 partials)
+// U^_b = N~_b (-r2_b - sum of the body's Y^T r1 partials); one warp per body
 __global__ void k_pc_uhat(int Nb, int M, const int* __restrict__ pcw_off,
                           const double* __restrict__ Nt, const double* __restrict__ r,
                           const double* __restrict__ ytp, double* __restrict__ Uhat) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (b >= M) return;
-    double v[6];
-    const double* r2 = r + 3 * (size_t)Nb + 6 * (size_t)b;
-    for (int c = 0; c < 6; ++c) v[c] = -r2[c];
-    for (int it = pcw_off[b]; it < pcw_off[b + 1]; ++it)
-        for (int c = 0; c < 6; ++c) v[c] -= ytp[6 * (size_t)it + c];
-    const double* N = Nt + 36 * (size_t)b;
-    for (int a = 0; a < 6; ++a) {
+    double v = 0.0;
+    if (lane < 6) {
+        v = -r[3 * (size_t)Nb + 6 * (size_t)b + lane];
+#pragma unroll 4
+        for (int it = pcw_off[b]; it < pcw_off[b + 1]; ++it) v -= ytp[6 * (size_t)it + lane];
+    }
+    double vv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) vv[c] = __shfl_sync(0xffffffffu, v, c);
+    if (lane < 6) {
+        const double* N = Nt + 36 * (size_t)b + 6 * lane;
         double s = 0.0;
-        for (int c = 0; c < 6; ++c) s += N[a * 6 + c] * v[c];
-        Uhat[6 * (size_t)b + a] = s;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s += N[c] * vv[c];
+        Uhat[6 * (size_t)b + lane] = s;
     }
 }
 
@@ -392,7 +437,9 @@ k_pc_ap2(int Nb, int M, const int* __restrict__ pca_asm, const int* __restrict__
          const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
          const T* __restrict__ G, const long long* __restrict__ goff, const double* __restrict__ cbuf,
          double* __restrict__ z) {
+    constexpr int kStage = 1024;  // entries of c staged in shared memory at a time
     __shared__ double red[4][kRows];
+    __shared__ double cs[kStage];
     const int it = blockIdx.x;
     const int a = pca_asm[it];
     const int L0 = asm_link_off[a];
@@ -400,15 +447,29 @@ k_pc_ap2(int Nb, int M, const int* __restrict__ pca_asm, const int* __restrict__
     const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
     const int row = pca_chunk[it] * kRows + lane;
     const T* Ga = G + goff[a];
-    double s = 0.0;
-    if (row < m) {
-        T acc = 0;
-        for (int k = part; k < m; k += 4) {
-            const int n = asm_link_idx[L0 + k / 3];
-            acc = fma(Ga[(size_t)k * m + row], (T)cbuf[3 * n + k % 3], acc);
+    T acc[4] = {0, 0, 0, 0};
+    for (int c0 = 0; c0 < m; c0 += kStage) {
+        const int cn = min(kStage, m - c0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cn; k += blockDim.x) {
+            const int kk = c0 + k;
+            cs[k] = cbuf[3 * asm_link_idx[L0 + kk / 3] + kk % 3];
         }
-        s = (double)acc;
+        __syncthreads();
+        if (row < m) {
+            const T* Gc = Ga + (size_t)c0 * m + row;
+            int k = part;
+            for (; k + 28 < cn; k += 32) {
+                T gv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) gv[u] = Gc[(size_t)(k + 4 * u) * m];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u & 3] = fma(gv[u], (T)cs[k + 4 * u], acc[u & 3]);
+            }
+            for (; k < cn; k += 4) acc[0] = fma(Gc[(size_t)k * m], (T)cs[k], acc[0]);
+        }
     }
+    const double s = row < m ? (double)((acc[0] + acc[1]) + (acc[2] + acc[3])) : 0.0;
     red[part][lane] = s;
     __syncthreads();
     if (part == 0 && row < m) {
@@ -429,9 +490,11 @@ k_pc_ap3(int Nb, int M, const int* __restrict__ pcw_body, const int* __restrict_
     const int it = blockIdx.x;
     const int b = pcw_body[it];
     const double* phi = z + 3 * (size_t)Nb + 6 * (size_t)M;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // (C^T phi)_b: the body's link ends spread over the lanes of warp 0
+        const int lane = threadIdx.x;
         double f[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = bl_off[b]; k < bl_off[b + 1]; ++k) {
+        for (int k = bl_off[b] + lane; k < bl_off[b + 1]; k += 32) {
             const int e = bl_idx[k];
             const int n = e >> 1;
             const double sg = (e & 1) ? -1.0 : 1.0;
@@ -441,14 +504,16 @@ k_pc_ap3(int Nb, int M, const int* __restrict__ pcw_body, const int* __restrict_
             cross3(l, ph, t);
             for (int x = 0; x < 3; ++x) { f[x] += sg * ph[x]; f[3 + x] += sg * t[x]; }
         }
-        const double* N = Nt + 36 * (size_t)b;
-        for (int x = 0; x < 6; ++x) {
-            double s = Uhat[6 * (size_t)b + x];
-            for (int c = 0; c < 6; ++c) s += N[x * 6 + c] * f[c];
-            sU[x] = s;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f[c] = warp_sum(f[c]);
+        if (lane < 6) {
+            const double* N = Nt + 36 * (size_t)b + 6 * lane;
+            double s = Uhat[6 * (size_t)b + lane];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s += N[c] * f[c];
+            sU[lane] = s;
+            if (pcw_chunk[it] == 0) z[3 * (size_t)Nb + 6 * (size_t)b + lane] = s;
         }
-        if (pcw_chunk[it] == 0)
-            for (int x = 0; x < 6; ++x) z[3 * (size_t)Nb + 6 * (size_t)b + x] = sU[x];
     }
     __syncthreads();
     const int i0 = blob_off[b];
@@ -559,7 +624,7 @@ static void pc_apply_t(am_handle* h, const double* r, double* z) {
     cudaStream_t s = h->stream;
     k_pc_ap1<T><<<h->n_pcw, 128, 0, s>>>(h->d_pcw_body, h->d_pcw_chunk, h->d_blob_off, (const T*)h->d_minv,
                                           h->d_minv_off, (const T*)h->d_Y, r, h->d_pc_w, h->d_ytp);
-    k_pc_uhat<<<(h->M + 127) / 128, 128, 0, s>>>(h->Nb, h->M, h->d_pcw_off, h->d_Nt, r, h->d_ytp,
+    k_pc_uhat<<<(h->M + 3) / 4, 128, 0, s>>>(h->Nb, h->M, h->d_pcw_off, h->d_Nt, r, h->d_ytp,
                                                   h->d_pc_Uhat);
     count_launch(2);
     if (h->P) {
