@@ -180,6 +180,29 @@ def test_preconditioner_fp32_storage_matches_oracle(chains):
     assert rel(s.apply_precond(r), S.apply_preconditioner(r)) <= 1e-4
 
 
+def test_preconditioner_cluster_build_matches_oracle():
+    # 12 rods of 2 x 40 blobs (240 rows each) and one articulated body of 22
+    # links (66 rows, rank 55): both builds take clusters of CTAs.  The link
+    # block of r lies in range(C), where every generalised inverse of
+    # C N~ C^T gives the same lambda, U and C^T phi.  FP32 storage: the
+    # error is bounded by about kappa * 2^-24 with kappa = 1.1e4 for
+    # C N~ C^T on range(C) here (M^(pp): 43), i.e. 6.6e-4; bar 2e-3.
+    w = W.diatom_colony(5, n_rods=12, nx=40)
+    S = System(w)
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(S.n)
+    C = S.C_dense()
+    nl, nu = 3 * S.Nb, 6 * S.M_bodies
+    r[nl + nu:] = C @ rng.standard_normal(nu)
+    lam_o, U_o, phi_o = S.split(S.apply_preconditioner(r))
+    for precision, bar in (("fp64", FP64_SOLVE), ("mixed", 2e-3)):
+        s = binding.Solver.from_workload(w, precision=precision)
+        lam, U, phi = S.split(s.apply_precond(r))
+        assert rel(lam, lam_o) <= bar
+        assert rel(U, U_o) <= bar
+        assert rel(C.T @ phi, C.T @ phi_o) <= bar
+
+
 def test_solve_chains_matches_dense_solution(chains):
     w, S = chains
     s = binding.Solver.from_workload(w, tol=1e-13)
