@@ -508,13 +508,6 @@ __global__ void k_ctrl_init(ArnoldiCtrl* c, int budget, int m, double tol_abs) {
     c->j = 0; c->it = 0; c->budget = budget; c->m = m; c->stop = 0; c->tol_abs = tol_abs;
 }
 
-// out = V[j] (the vector to precondition)
-__global__ void k_copy_col(const double* __restrict__ V, size_t ldv, double* __restrict__ out, int n,
-                           const ArnoldiCtrl* __restrict__ c) {
-    const double* v = V + (size_t)c->j * ldv;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = v[i];
-}
-
 // Z[j] = in (flexible GMRES keeps the preconditioned vectors)
 __global__ void k_store_col(const double* __restrict__ in, double* __restrict__ Z, size_t ldv, int n,
                             const ArnoldiCtrl* __restrict__ c) {
@@ -628,11 +621,14 @@ __global__ void k_cycle_init(int S, int m, double tol, const double* __restrict_
     }
 }
 
-// v *= a[system of the element]
+// v *= a[system of the element]; the result also into copy (if not null)
 __global__ void k_scale_sys(double* __restrict__ v, int n, const int* __restrict__ sys_of,
-                            const double* __restrict__ a) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        v[i] *= a[sys_of[i]];
+                            const double* __restrict__ a, double* __restrict__ copy = nullptr) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double t = v[i] * a[sys_of[i]];
+        v[i] = t;
+        if (copy) copy[i] = t;
+    }
 }
 
 // v = 0 on the elements of inactive systems
@@ -688,19 +684,16 @@ k_orth_sys(const double* __restrict__ V, size_t ldv, double* __restrict__ w, int
     }
 }
 
-// Per active system (one thread each): H column j, Givens rotations, the
-// residual estimate; a system stops (kdone = j + 1) when the estimate reaches
-// its threshold or the step breaks down.  inv[s] = 1/|w_s| (0 if stopped).
-__global__ void k_arnoldi_finish_sys(const ArnoldiCtrl* __restrict__ c, const double* __restrict__ hcol,
-                                     const double* __restrict__ npart, const int* __restrict__ coff, int S,
-                                     int m, double* __restrict__ H, double* __restrict__ cs,
-                                     double* __restrict__ sn, double* __restrict__ g, int* __restrict__ active,
-                                     int* __restrict__ kdone, const double* __restrict__ tol_s,
-                                     double* __restrict__ inv) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+// Per active system: H column j, Givens rotations, the residual estimate; a
+// system stops (kdone = j + 1) when the estimate reaches its threshold or
+// the step breaks down.  inv[s] = 1/|w_s| (0 if stopped).
+__device__ __forceinline__ void finish_one(int s, int j, int m, const double* __restrict__ hcol,
+                                           const double* __restrict__ npart, const int* __restrict__ coff,
+                                           double* __restrict__ H, double* __restrict__ cs,
+                                           double* __restrict__ sn, double* __restrict__ g,
+                                           int* __restrict__ active, int* __restrict__ kdone,
+                                           const double* __restrict__ tol_s, double* __restrict__ inv) {
     if (!active[s]) { inv[s] = 0.0; return; }
-    const int j = c->j;
     const int m1 = m + 1;
     double a = 0.0;
     for (int q = coff[s]; q < coff[s + 1]; ++q) a += npart[q];
@@ -733,19 +726,23 @@ __global__ void k_arnoldi_finish_sys(const ArnoldiCtrl* __restrict__ c, const do
     if (stop) { active[s] = 0; kdone[s] = j + 1; }
 }
 
-// V[j+1] = w * inv[system]
-__global__ void k_next_basis(const double* __restrict__ w, double* __restrict__ V, size_t ldv, int n,
-                             const int* __restrict__ sys_of, const double* __restrict__ inv,
-                             const ArnoldiCtrl* __restrict__ c) {
-    double* v = V + (size_t)(c->j + 1) * ldv;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        v[i] = inv[sys_of[i]] * w[i];
+// One thread per system.
+__global__ void k_arnoldi_finish_sys(const ArnoldiCtrl* __restrict__ c, const double* __restrict__ hcol,
+                                     const double* __restrict__ npart, const int* __restrict__ coff, int S,
+                                     int m, double* __restrict__ H, double* __restrict__ cs,
+                                     double* __restrict__ sn, double* __restrict__ g, int* __restrict__ active,
+                                     int* __restrict__ kdone, const double* __restrict__ tol_s,
+                                     double* __restrict__ inv) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    finish_one(s, c->j, m, hcol, npart, coff, H, cs, sn, g, active, kdone, tol_s, inv);
 }
 
 // Advance j; the cycle ends when no system is active, at the restart length
-// or at the step budget (still-active systems then close at j + 1).
-__global__ void k_loop_ctrl_sys(ArnoldiCtrl* c, int* __restrict__ active, int* __restrict__ kdone, int S,
-                                cudaGraphConditionalHandle hc, int in_graph) {
+// or at the step budget (still-active systems then close at j + 1).  Every
+// thread of the one block calls it.
+__device__ void loop_ctrl(ArnoldiCtrl* c, int* __restrict__ active, int* __restrict__ kdone, int S,
+                          cudaGraphConditionalHandle hc, int in_graph) {
     __shared__ int scnt[256];
     __shared__ int s_stop;
     const int j1 = c->j + 1;
@@ -762,12 +759,48 @@ __global__ void k_loop_ctrl_sys(ArnoldiCtrl* c, int* __restrict__ active, int* _
     if (s_stop)
         for (int s = threadIdx.x; s < S; s += blockDim.x)
             if (active[s]) { kdone[s] = j1; active[s] = 0; }
+    __syncthreads();
     if (threadIdx.x == 0) {
         c->it += 1;
         c->j = j1;
         c->stop = s_stop;
         if (in_graph) cudaGraphSetConditional(hc, s_stop ? 0u : 1u);
     }
+}
+
+// The systems' step ends and the loop control in one block of 256 threads
+// (S <= 256): every system's finish_one, then loop_ctrl.
+__global__ void __launch_bounds__(256)
+k_arnoldi_finish_ctrl(ArnoldiCtrl* c, const double* __restrict__ hcol, const double* __restrict__ npart,
+                      const int* __restrict__ coff, int S, int m, double* __restrict__ H,
+                      double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                      int* __restrict__ active, int* __restrict__ kdone, const double* __restrict__ tol_s,
+                      double* __restrict__ inv, cudaGraphConditionalHandle hc, int in_graph) {
+    const int j = c->j;
+    for (int s = threadIdx.x; s < S; s += blockDim.x)
+        finish_one(s, j, m, hcol, npart, coff, H, cs, sn, g, active, kdone, tol_s, inv);
+    __syncthreads();
+    loop_ctrl(c, active, kdone, S, hc, in_graph);
+}
+
+// V[j+1] = w * inv[system], also into vj (the next step's vector to
+// precondition); with the loop control already advanced (j_ahead), the
+// column is V[j].
+__global__ void k_next_basis(const double* __restrict__ w, double* __restrict__ V, size_t ldv, int n,
+                             const int* __restrict__ sys_of, const double* __restrict__ inv,
+                             const ArnoldiCtrl* __restrict__ c, double* __restrict__ vj, int j_ahead) {
+    double* v = V + (size_t)(c->j + (j_ahead ? 0 : 1)) * ldv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double t = inv[sys_of[i]] * w[i];
+        v[i] = t;
+        vj[i] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_loop_ctrl_sys(ArnoldiCtrl* c, int* __restrict__ active, int* __restrict__ kdone, int S,
+                cudaGraphConditionalHandle hc, int in_graph) {
+    loop_ctrl(c, active, kdone, S, hc, in_graph);
 }
 
 // xi_s = H_s(0:k, 0:k)^-1 g_s(0:k), k = kdone[s]  (one thread per system)
@@ -978,9 +1011,7 @@ static void issue_arnoldi_step(am_handle* h, bool fp64, cudaGraphConditionalHand
     const size_t ldv = (size_t)h->ldv;
     const int nb = red_blocks(n);
     const dim3 dgrid(h->nchunks, (m1 + 7) / 8);
-    k_copy_col<<<nb, 256, 0, s>>>(h->d_V, ldv, h->d_vj, n, h->d_ctrl);
-    count_launch();
-    pc_apply(h, h->d_vj, h->d_zj);
+    pc_apply(h, h->d_vj, h->d_zj);  // vj = V[j], written with V[j]
     k_store_col<<<nb, 256, 0, s>>>(h->d_zj, h->d_Z, ldv, n, h->d_ctrl);
     count_launch();
     op_apply(h, h->d_zj, h->d_w, fp64);
@@ -993,12 +1024,24 @@ static void issue_arnoldi_step(am_handle* h, bool fp64, cudaGraphConditionalHand
         count_launch(3);
     }
     k_chunk_sq<<<h->nchunks, 256, 0, s>>>(h->d_w, h->d_chunk_start, h->d_chunk_end, h->d_npart);
-    k_arnoldi_finish_sys<<<nblk(S, 128), 128, 0, s>>>(h->d_ctrl, h->d_hcols, h->d_npart, h->d_sys_chunk_off, S,
-                                                       m, h->d_Hs, h->d_css, h->d_sns, h->d_gs, h->d_active,
-                                                       h->d_kdone, h->d_tol_s, h->d_inv_s);
-    k_next_basis<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s, h->d_ctrl);
-    k_loop_ctrl_sys<<<1, 256, 0, s>>>(h->d_ctrl, h->d_active, h->d_kdone, S, hc, in_graph ? 1 : 0);
-    count_launch(4);
+    count_launch();
+    if (S <= 256) {
+        // finish and loop control in one block; j has advanced for next_basis
+        k_arnoldi_finish_ctrl<<<1, 256, 0, s>>>(h->d_ctrl, h->d_hcols, h->d_npart, h->d_sys_chunk_off, S, m,
+                                                 h->d_Hs, h->d_css, h->d_sns, h->d_gs, h->d_active, h->d_kdone,
+                                                 h->d_tol_s, h->d_inv_s, hc, in_graph ? 1 : 0);
+        k_next_basis<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s, h->d_ctrl,
+                                         h->d_vj, 1);
+        count_launch(2);
+    } else {
+        k_arnoldi_finish_sys<<<nblk(S, 128), 128, 0, s>>>(h->d_ctrl, h->d_hcols, h->d_npart, h->d_sys_chunk_off,
+                                                           S, m, h->d_Hs, h->d_css, h->d_sns, h->d_gs,
+                                                           h->d_active, h->d_kdone, h->d_tol_s, h->d_inv_s);
+        k_next_basis<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s, h->d_ctrl,
+                                         h->d_vj, 0);
+        k_loop_ctrl_sys<<<1, 256, 0, s>>>(h->d_ctrl, h->d_active, h->d_kdone, S, hc, in_graph ? 1 : 0);
+        count_launch(3);
+    }
 }
 
 // The graph of one Arnoldi cycle: a WHILE node whose body is one step,
@@ -1088,7 +1131,7 @@ static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp
         const int n_active = (int)h->h_scal[1];
         if (n_active == 0 || it >= budget || !(*rel == *rel)) break;
         ++*cycles;
-        k_scale_sys<<<nb, 256, 0, s>>>(h->d_V, n, h->d_sys_of_elem, h->d_inv_s);
+        k_scale_sys<<<nb, 256, 0, s>>>(h->d_V, n, h->d_sys_of_elem, h->d_inv_s, h->d_vj);
         k_ctrl_init<<<1, 1, 0, s>>>(h->d_ctrl, budget - it, m, 0.0);
         count_launch(2);
         if (use_graph) {
