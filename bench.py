@@ -344,6 +344,41 @@ def rk2_form(binding, W, steps=5, warmup=2):
     return out
 
 
+def guess_form(binding, W, steps=8, warmup=3):
+    """The bench colony's Euler step with the initial guess of each solve
+    taken from the solution history (am_set_initial_guess): order 1 = the
+    previous solution (the headline's), 2 and 3 = the extrapolation in time
+    through the last 2 or 3 solutions; FP64 and mixed, relative residual
+    1e-8.  Host wall time per step after warm-up steps."""
+    out = {"workload": WORKLOAD.replace("FP64, ", "") + ", Euler step, initial guess from the history"}
+    for prec in ("fp64", "mixed"):
+        res = {}
+        for order in (1, 2, 3):
+            w = W.diatom_colony(1)
+            s = binding.Solver.from_workload(w, t=0.0, tol=TOL, precision=prec)
+            s.set_initial_guess(order)
+            times, iters, resid, r0 = [], [], [], []
+            for k in range(warmup + steps):
+                t = k * DT
+                if k:
+                    dlp, dlq, dlpd, dlqd = w["dl"](t)
+                    s.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd)
+                t0 = time.perf_counter()
+                _, _, _, st = s.step(t, DT, dl_next=w["dl"](t + DT)[:2])
+                if k >= warmup:
+                    times.append(time.perf_counter() - t0)
+                    iters.append(st["iterations"])
+                    resid.append(st["rel_residual"])
+                    r0.append(st["rel_residual0"])
+            s.close()
+            res["order_%d" % order] = {"ms_per_step": 1e3 * statistics.mean(times),
+                                       "gmres_iterations_per_step": statistics.mean(iters),
+                                       "initial_rel_residual": statistics.mean(r0),
+                                       "max_rel_residual": max(resid)}
+        out[prec] = res
+    return out
+
+
 def single_blob_form(binding, W, steps=3, warmup=2):
     """Single-blob bodies with rotational coupling (free space): 400
     filaments of 15 spheres (a = 0.5, neighbours 1.05 apart, ball joints),
@@ -529,6 +564,7 @@ def run_ours(args):
     batched = batched_form(torch, binding, W, stream) if world == 1 else None
     learned_res = learned_form(binding, W) if world == 1 else None
     rk2_res = rk2_form(binding, W) if world == 1 else None
+    guess_res = guess_form(binding, W) if world == 1 else None
     sb_res = single_blob_form(binding, W) if world == 1 else None
     fpp = binding.flops_per_pair(1)
     avg_launch_s = (mob_ms * 1e-3) / max(mob_launches, 1)
@@ -575,7 +611,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks,
             "matvec_at_scale": at_scale, "products_compared": compared, "batched_form": batched,
-            "learned_form": learned_res, "rk2_form": rk2_res, "steric": steric,
+            "learned_form": learned_res, "rk2_form": rk2_res, "guess_form": guess_res, "steric": steric,
             "single_blob_form": sb_res}
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -438,6 +438,27 @@ AM_API int am_learned_features(am_handle* h, float* X, float* T);
  * keep it alive while it is set. */
 AM_API int am_set_learned(am_handle* h, am_mlp* model, int check);
 
+/* Initial guess of the time-step solves (am_solve_step, both stages of
+ * am_solve_step_rk2), which keep the solutions of the last three solves
+ * with their times (t, and t + dt/2 for the midpoint stage):
+ *   order 0  P~^-1 b (or the learned guess, am_set_learned) every solve;
+ *   order 1  the previous solve's solution (the default; Sec. 3.1);
+ *   order 2, 3  lambda and U from the polynomial in time through the last
+ *            2 or 3 solutions (Lagrange form in their times) evaluated at
+ *            the new solve's time, phi from the previous solution (with a
+ *            rank-deficient C, phi is determined only modulo null(C^T)):
+ *            an extrapolation that is not in the paper.
+ * Every guess from the history is projected so that C U = B.  Fewer
+ * solutions than the order, two history times closer than 1e-12 (1 + |t|)
+ * apart, or a Lagrange weight above 16 in magnitude lower the order for
+ * that solve; a solve at the time of the newest entry replaces it; a new
+ * layout (am_set_bodies, am_set_constraints with another connectivity)
+ * empties the history.  The converged solution does not depend
+ * on the order beyond the tolerance; the iteration count does.  am_solve
+ * neither reads nor extends the history.  Errors: AM_ERR_ARG (order outside
+ * 0..3). */
+AM_API int am_set_initial_guess(am_handle* h, int order);
+
 /* Destroy a handle and free its device memory (NULL is a no-op). */
 AM_API void am_destroy(am_handle* h);
 

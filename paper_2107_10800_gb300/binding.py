@@ -96,6 +96,7 @@ SIGNATURES = {
     "am_mlp_predict": (ctypes.c_int, [_vp, _fp, ctypes.c_int, ctypes.c_int, _fp]),
     "am_learned_features": (ctypes.c_int, [_vp, _fp, _fp]),
     "am_set_learned": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "am_set_initial_guess": (ctypes.c_int, [_vp, ctypes.c_int]),
     "am_destroy": (None, [_vp]),
     "am_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -324,6 +325,11 @@ class Solver:
         f, fp = _out(3 * self.Nb)
         self._check(lib().am_steric_forces(self.h, fp))
         return f.reshape(-1, 3)
+
+    def set_initial_guess(self, order):
+        """Initial guess of the time-step solves: 0 P~^-1 b, 1 the previous
+        solution, 2 or 3 the extrapolation in time through the last 2 or 3."""
+        self._check(lib().am_set_initial_guess(self.h, int(order)))
 
     def set_mobility_layout(self, targets_per_thread, source_chunk=0):
         """Fix the all-pairs product layout (0 targets per thread: autotune)."""

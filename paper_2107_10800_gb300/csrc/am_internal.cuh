@@ -216,7 +216,7 @@ struct am_handle {
     bool pc_valid = false;
 
     // device: solver vectors
-    double *d_b = nullptr, *d_x = nullptr, *d_xprev = nullptr, *d_t = nullptr,
+    double *d_b = nullptr, *d_x = nullptr, *d_t = nullptr,
            *d_z = nullptr, *d_w = nullptr, *d_V = nullptr, *d_Z = nullptr;
     double *d_Hm = nullptr, *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr,
            *d_coef = nullptr, *d_part = nullptr, *d_scal = nullptr, *d_xi = nullptr,
@@ -224,7 +224,12 @@ struct am_handle {
     int restart = 50;
     int ldv = 0;
     long long pairs = 0;
-    bool have_warm = false;
+    // solution history of the time-step solves (most recent: slot hist_head)
+    double* d_xhist = nullptr;  // 3 x n
+    double t_hist[3] = {0, 0, 0};
+    int n_hist = 0, hist_head = 0;
+    int guess_order = 1;        // am_set_initial_guess
+    double t_solve = 0.0;       // time of the time-step solve being prepared
 
     // device: mobility partial sums
     double* d_mv = nullptr;

@@ -147,7 +147,7 @@ void free_bodies(am_handle* h) {
 }
 
 void free_solver(am_handle* h) {
-    dfree(&h->d_b); dfree(&h->d_x); dfree(&h->d_xprev); dfree(&h->d_t); dfree(&h->d_z);
+    dfree(&h->d_b); dfree(&h->d_x); dfree(&h->d_xhist); dfree(&h->d_t); dfree(&h->d_z);
     dfree(&h->d_w); dfree(&h->d_V); dfree(&h->d_Z); dfree(&h->d_rir); dfree(&h->d_dx);
     dfree(&h->d_vj); dfree(&h->d_zj);
     h->layout_gen++;
@@ -168,7 +168,7 @@ int alloc_solver(am_handle* h) {
     const int n = h->n;
     const int m = h->restart;
     h->ldv = (n + 31) & ~31;
-    CK(dalloc(&h->d_b, n)); CK(dalloc(&h->d_x, n)); CK(dalloc(&h->d_xprev, n));
+    CK(dalloc(&h->d_b, n)); CK(dalloc(&h->d_x, n)); CK(dalloc(&h->d_xhist, 3 * (size_t)n));
     CK(dalloc(&h->d_t, n)); CK(dalloc(&h->d_z, n)); CK(dalloc(&h->d_w, n));
     CK(dalloc(&h->d_rir, n)); CK(dalloc(&h->d_dx, n));
     CK(dalloc(&h->d_V, (size_t)h->ldv * (m + 1)));
@@ -178,8 +178,70 @@ int alloc_solver(am_handle* h) {
     CK(dalloc(&h->d_Hm, (size_t)(m + 1) * m)); CK(dalloc(&h->d_cs, m)); CK(dalloc(&h->d_sn, m));
     CK(dalloc(&h->d_g, m + 1)); CK(dalloc(&h->d_coef, m + 1)); CK(dalloc(&h->d_xi, m + 1));
     CK(dalloc(&h->d_part, (size_t)(m + 1) * 64)); CK(dalloc(&h->d_npart, 4 * am::num_sms() + 64));
-    h->have_warm = false;
+    h->n_hist = 0;
+    h->hist_head = 0;
     return AM_OK;
+}
+
+// Weights w[0..k) of the Lagrange polynomial through the nodes tn[0..k),
+// evaluated at t.
+void lagrange_weights(const double* tn, int k, double t, double* w) {
+    for (int i = 0; i < k; ++i) {
+        double v = 1.0;
+        for (int j = 0; j < k; ++j)
+            if (j != i) v *= (t - tn[j]) / (tn[i] - tn[j]);
+        w[i] = v;
+    }
+}
+
+// The initial guess of a time-step solve at time t from the history into x
+// (am_set_initial_guess); false if the history is not used.
+bool guess_from_history(am_handle* h, double t, double* x) {
+    if (h->guess_order < 1 || h->n_hist < 1) return false;
+    const double* slot[3];
+    double tn[3];
+    for (int i = 0; i < h->n_hist; ++i) {
+        const int k = (h->hist_head - i + 3) % 3;
+        slot[i] = h->d_xhist + (size_t)k * h->n;
+        tn[i] = h->t_hist[k];
+    }
+    int k = std::min(h->guess_order, h->n_hist);
+    double w[3] = {1.0, 0.0, 0.0};
+    for (; k > 1; --k) {
+        bool ok = true;
+        const double sep = 1e-12 * (1.0 + std::fabs(t));
+        for (int i = 0; i < k && ok; ++i)
+            for (int j = i + 1; j < k && ok; ++j) ok = std::fabs(tn[i] - tn[j]) > sep;
+        if (!ok) continue;
+        lagrange_weights(tn, k, t, w);
+        for (int i = 0; i < k; ++i) ok = ok && std::isfinite(w[i]) && std::fabs(w[i]) <= 16.0;
+        if (ok) break;
+    }
+    if (k <= 1) {
+        cudaMemcpyAsync(x, slot[0], h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    } else {
+        // lambda and U extrapolated; phi from the newest solution (with a
+        // rank-deficient C each solve's phi is one representative modulo
+        // null(C^T), and those of different solves need not lie on one
+        // smooth curve)
+        const int n_phi = 3 * h->P;
+        am::combine_vectors(h, x, slot, w, k, h->n - n_phi);
+        cudaMemcpyAsync(x + (h->n - n_phi), slot[0] + (h->n - n_phi), n_phi * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream);
+    }
+    return true;
+}
+
+// Append the solution of a time-step solve at time t to the history (a
+// solve at the time of the most recent entry replaces it).
+void push_history(am_handle* h, double t, const double* x) {
+    if (!(h->n_hist > 0 && h->t_hist[h->hist_head] == t)) {
+        h->hist_head = (h->hist_head + 1) % 3;
+        h->n_hist = std::min(h->n_hist + 1, 3);
+    }
+    h->t_hist[h->hist_head] = t;
+    cudaMemcpyAsync(h->d_xhist + (size_t)h->hist_head * h->n, x, h->n * sizeof(double),
+                    cudaMemcpyDeviceToDevice, h->stream);
 }
 
 // Links and everything that depends on them.  Empty (P = 0) is valid.
@@ -377,8 +439,7 @@ int prepare(am_handle* h, const char* who, bool warm, am_step_stats* st) {
     CK(cudaGetLastError());
     int rc = device_flags_to_status(h, who);
     if (rc) return rc;
-    if (warm && h->have_warm) {
-        CK(cudaMemcpyAsync(h->d_x, h->d_xprev, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (warm && guess_from_history(h, h->t_solve, h->d_x)) {
         am::project_constraints(h, h->d_x);
     } else if (h->mlp) {
         // learned guess; with the check, per system the point on the line
@@ -932,6 +993,13 @@ extern "C" AM_API int am_learned_features(am_handle* h, float* X, float* T) {
     return AM_OK;
 }
 
+extern "C" AM_API int am_set_initial_guess(am_handle* h, int order) {
+    if (!h) return AM_ERR_ARG;
+    if (order < 0 || order > 3) return set_err(h, AM_ERR_ARG, "am_set_initial_guess: order must be 0..3");
+    h->guess_order = order;
+    return AM_OK;
+}
+
 extern "C" AM_API int am_set_learned(am_handle* h, am_mlp* model, int check) {
     if (!h) return AM_ERR_ARG;
     if (h->sb && model) return set_err(h, AM_ERR_ARG, "am_set_learned: not for single-blob bodies");
@@ -944,7 +1012,6 @@ extern "C" AM_API int am_solve_step(am_handle* h, double t, double dt, const dou
                                     const double* dlq_next, am_step_stats* stats, double* U, double* phi,
                                     double* lam) {
     if (!h) return AM_ERR_ARG;
-    (void)t;
     am_step_stats st{};
     int rc = check_handle(h, "am_solve_step", true);
     if (rc) return rc;
@@ -957,6 +1024,7 @@ extern "C" AM_API int am_solve_step(am_handle* h, double t, double dt, const dou
     const long long l0 = am::g_launches.load();
     h->pairs = 0;
     cudaStream_t s = h->stream;
+    h->t_solve = t;
     rc = prepare(h, "am_solve_step", true, &st);
     if (rc) return rc;
     CK(cudaEventRecord(h->ev[2], s));
@@ -965,8 +1033,8 @@ extern "C" AM_API int am_solve_step(am_handle* h, double t, double dt, const dou
     CK(cudaGetLastError());
     rc = copy_outputs(h, U, phi, lam);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(h->d_xprev, h->d_x, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    h->have_warm = true;
+    push_history(h, t, h->d_x);
+    CK(cudaGetLastError());
     if (h->P) {
         if (dlp_next) {
             CK(h2d(h->d_dlp1, dlp_next, 3 * (size_t)h->P, s));
@@ -1010,17 +1078,19 @@ static int set_end_links(am_handle* h, const double* dlp, const double* dlq) {
     return AM_OK;
 }
 
-// One solve at the current pose (warm-started) with its timings into st.
-static int stage_solve(am_handle* h, const char* who, am_step_stats* st, int* rs) {
+// One solve at the current pose at time t (guess from the history) with its
+// timings into st.
+static int stage_solve(am_handle* h, const char* who, double t, am_step_stats* st, int* rs) {
     cudaStream_t s = h->stream;
+    h->t_solve = t;
     int rc = prepare(h, who, true, st);
     if (rc) return rc;
     CK(cudaEventRecord(h->ev[2], s));
     *rs = am::solve(h, st);
     CK(cudaEventRecord(h->ev[3], s));
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(h->d_xprev, h->d_x, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    h->have_warm = true;
+    push_history(h, t, h->d_x);
+    CK(cudaGetLastError());
     CK(cudaEventSynchronize(h->ev[3]));
     st->ms_gmres = elapsed(h->ev[2], h->ev[3]);
     return AM_OK;
@@ -1033,7 +1103,6 @@ extern "C" AM_API int am_solve_step_rk2(am_handle* h, double t, double dt, const
                                         double* lam) {
     const char* who = "am_solve_step_rk2";
     if (!h) return AM_ERR_ARG;
-    (void)t;
     int rc = check_handle(h, who, true);
     if (rc) return rc;
     if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(h, AM_ERR_ARG, std::string(who) + ": dt must be > 0");
@@ -1053,7 +1122,7 @@ extern "C" AM_API int am_solve_step_rk2(am_handle* h, double t, double dt, const
     am_step_stats s1{}, s2{}, uh{}, uf{};
     int rs1 = AM_OK, rs2 = AM_OK;
     // stage 1: velocities at t_k
-    rc = stage_solve(h, who, &s1, &rs1);
+    rc = stage_solve(h, who, t, &s1, &rs1);
     if (rc) return rc;
     CK(cudaMemcpyAsync(h->d_q0, h->d_q, 3 * h->M * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->d_th0, h->d_theta, 4 * h->M * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1074,7 +1143,7 @@ extern "C" AM_API int am_solve_step_rk2(am_handle* h, double t, double dt, const
     CK(cudaEventSynchronize(h->ev[5]));
     cudaEventElapsedTime(&ms_half, h->ev[4], h->ev[5]);
     // stage 2: velocities at the midpoint (warm start from stage 1)
-    rc = stage_solve(h, who, &s2, &rs2);
+    rc = stage_solve(h, who, t + 0.5 * dt, &s2, &rs2);
     if (rc) return rc;
     rc = copy_outputs(h, U, phi, lam);
     if (rc) return rc;

@@ -924,6 +924,25 @@ void project_constraints(am_handle* h, double* x) {
 
 static int red_blocks(int n) { return std::min(nblk(n, 256), 2 * num_sms()); }
 
+__global__ void k_combine3(double* __restrict__ x, const double* __restrict__ v0,
+                           const double* __restrict__ v1, const double* __restrict__ v2, double w0,
+                           double w1, double w2, int k, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double a = w0 * v0[i];
+        if (k > 1) a = fma(w1, v1[i], a);
+        if (k > 2) a = fma(w2, v2[i], a);
+        x[i] = a;
+    }
+}
+
+void combine_vectors(am_handle* h, double* x, const double* const* v, const double* w, int k, int len) {
+    if (len <= 0) return;
+    k_combine3<<<red_blocks(len), 256, 0, h->stream>>>(x, v[0], k > 1 ? v[1] : v[0], k > 2 ? v[2] : v[0],
+                                                         w[0], k > 1 ? w[1] : 0.0, k > 2 ? w[2] : 0.0, k, len);
+    count_launch();
+}
+
+
 static void read_scal(am_handle* h, int count) {
     cudaMemcpyAsync(h->h_scal, h->d_scal, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     cudaStreamSynchronize(h->stream);

@@ -25,6 +25,8 @@ void pc_apply(am_handle* h, const double* r, double* z);
 // Project the U block of x onto C U = B with the preconditioner
 // (x += P~^-1 (0, 0, B - C U)).
 void project_constraints(am_handle* h, double* x);
+// x = sum_{i < k} w[i] v[i] over the first len entries (k <= 3 vectors)
+void combine_vectors(am_handle* h, double* x, const double* const* v, const double* w, int k, int len);
 // Solve A x = b (d_b, d_x in the handle; d_x holds the initial guess).
 // Returns AM_OK or AM_ERR_NOT_CONVERGED; fills iteration fields of st.
 int solve(am_handle* h, am_step_stats* st);

@@ -77,6 +77,7 @@ def test_matvec_argument_checks(L):
 
 def test_null_handle_is_rejected(L):
     assert L.am_solve(None, None, None, None, None) == binding.AM_ERR_ARG
+    assert L.am_set_initial_guess(None, 1) == binding.AM_ERR_ARG
     L.am_destroy(None)
 
 
