@@ -142,7 +142,7 @@ AM_API int am_create(const am_config* cfg, am_handle** out);
  *   slip             3Nb  slip velocities u_s of Eq. linear_system, or NULL
  *   assembly_of_body M    int, articulated-body index of each body, in
  *                         0 .. n_assemblies-1, every index used
- * Replaces any earlier bodies (and drops links and the warm start).
+ * Replaces any earlier bodies (and drops links and the solution history).
  * Errors: AM_ERR_ARG, AM_ERR_NONUNIT_QUAT, AM_ERR_WALL_PENETRATION (wall and
  * some r_i,z <= a), AM_ERR_CUDA. */
 AM_API int am_set_bodies(am_handle* h, int system, int n_bodies,
@@ -183,7 +183,8 @@ AM_API int am_solve(am_handle* h, am_step_stats* stats,
                     double* U_out, double* phi_out, double* lambda_out);
 
 /* One explicit Euler step of Sec. 4.3 from t to t + dt: solve Eq.
- * linear_system at t (warm-started from the previous step's solution),
+ * linear_system at t (initial guess from the earlier solves, see
+ * am_set_initial_guess; the previous solution by default),
  * move each articulated body's centre by dt times its mean body velocity
  * (Eq. ucom) and each orientation by theta_{omega dt} . theta, rebuild the
  * positions with the pseudo-inverse of the connectivity (Eq. pseudo-inv-sol,
@@ -201,7 +202,7 @@ AM_API int am_solve_step(am_handle* h, double t, double dt,
                          double* U_out, double* phi_out, double* lambda_out);
 
 /* One explicit midpoint (RK2) step of App. "Midpoint scheme" from t to
- * t + dt: solve at t (warm-started), move each articulated body's centre and
+ * t + dt: solve at t (guess as am_solve_step), move each articulated body's centre and
  * orientations by dt/2 with those velocities and reconstruct (with the
  * nonlinear correction when ||g*||^2 >= corr_tol) using the link vectors at
  * t + dt/2, solve at that midpoint, then move the pose at t by dt with the

@@ -1142,7 +1142,8 @@ extern "C" AM_API int am_solve_step_rk2(am_handle* h, double t, double dt, const
     float ms_half = 0.f;
     CK(cudaEventSynchronize(h->ev[5]));
     cudaEventElapsedTime(&ms_half, h->ev[4], h->ev[5]);
-    // stage 2: velocities at the midpoint (warm start from stage 1)
+    // stage 2: velocities at the midpoint (guess from the history, which
+    // now ends with stage 1)
     rc = stage_solve(h, who, t + 0.5 * dt, &s2, &rs2);
     if (rc) return rc;
     rc = copy_outputs(h, U, phi, lam);
