@@ -325,11 +325,15 @@ AM_API size_t am_rpy_matvec_rows_workspace(int n, int nrows, int precision);
  * AM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
  * the library holds until the process exits.
  *  - Limit: n must satisfy am_rpy_matvec_workspace(n, precision) <=
- *    AM_NOALLOC_SCRATCH_BYTES (about 100,000 blobs); larger n returns
- *    AM_ERR_ARG with a message, and nothing is launched.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, once per device, with that device current);
- *    make that first call before any stream capture.
+ *    AM_NOALLOC_SCRATCH_BYTES, evaluated with the device of the call
+ *    current (the source split, and with it the scratch, depends on the
+ *    SM count); on a 152-SM GB300 that is n <= about 150,000 blobs for
+ *    either precision.  Larger n returns AM_ERR_ARG with a message, and
+ *    nothing is launched.
+ *  - Every call looks up the array's device address on the current device
+ *    (cudaGetSymbolAddress; not a stream operation).  The first call on a
+ *    device may load the library's device code there: make that first call
+ *    before any stream capture.
  *  - Every call on a device shares the one array: calls that overlap on the
  *    GPU (other streams, other threads) race and corrupt each other.  The
  *    array keeps the last call's contents; no part of it needs to start at

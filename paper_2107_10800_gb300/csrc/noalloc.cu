@@ -4,7 +4,6 @@
 // device array of this file instead of a caller workspace.
 #include "am_internal.cuh"
 
-#include <mutex>
 #include <string>
 
 namespace am {
@@ -15,10 +14,6 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[AM_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 // errors are reported through am_last_error(NULL), like am_rpy_matvec's
 int fail(int code, const std::string& msg) {
     am::set_thread_error(msg);
@@ -27,23 +22,17 @@ int fail(int code, const std::string& msg) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of a __device__ array is not a device
-// address).
+// Device address of the scratch array on the current device.  The host-side
+// name of a __device__ array is not a device address, so it is looked up with
+// the device current, on every call: the lookup is not a stream operation,
+// and a cached address would go stale if the module were loaded again (after
+// a device reset, in a new primary context).
 int scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(AM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(AM_ERR_ARG, "device index out of range");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(AM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(AM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = p;
     return AM_OK;
 }
 

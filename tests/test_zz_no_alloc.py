@@ -61,6 +61,9 @@ def test_noalloc_matches_workspace_version_twice(torch, prec, wall):
         assert np.all(np.isfinite(got))
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err <= TOL[prec], (seed, n, err)
+        # the same kernels with the same source split in the same order:
+        # the two results agree bit for bit
+        assert np.array_equal(got, ref), (seed, n, err)
 
 
 def test_noalloc_rejects_sizes_beyond_scratch(torch):
