@@ -91,20 +91,30 @@ rpy_partial_f64(const double4_32a* __restrict__ r4, const double* __restrict__ l
     const int j0 = blockIdx.y * chunk;
     const int j1 = min(n, j0 + chunk);
     double4_32a ri = (it < nt) ? r4[i] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
+    const double nx3 = -ri.z;
     double ux = 0.0, uy = 0.0, uz = 0.0;
     for (int jt = j0; jt < j1; jt += kTile) {
         const int cnt = min(kTile, j1 - jt);
         __syncthreads();
-        if (threadIdx.x < cnt) sr[threadIdx.x] = r4[jt + threadIdx.x];
+        if (threadIdx.x < cnt) {
+            double4_32a v = r4[jt + threadIdx.x];
+            v.w = 2.0 * v.z;  // twice the source height, for the wall term
+            sr[threadIdx.x] = v;
+        }
         for (int q = threadIdx.x; q < 3 * cnt; q += kThreads) sl[q] = lam[3 * (size_t)jt + q];
         __syncthreads();
 #pragma unroll 2
         for (int q = 0; q < cnt; ++q) {
             const double4_32a rj = sr[q];
             const double lx = sl[3 * q], ly = sl[3 * q + 1], lz = sl[3 * q + 2];
-            const double dx = ri.x - rj.x, dy = ri.y - rj.y;
-            pair_free<double>(dx, dy, ri.z - rj.z, lx, ly, lz, k, ux, uy, uz);
-            if (WALL) pair_image<double>(dx, dy, ri.z + rj.z, ri.z, rj.z, lx, ly, lz, k, ux, uy, uz);
+            const double dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
+            if (WALL) {
+                const double rxy2 = fma(dx, dx, dy * dy);
+                pair_wall_r2<double>(dx, dy, dz, rxy2, fma(dz, dz, rxy2), ri.z + rj.z, rj.w, nx3, lx, ly, lz, k,
+                                     ux, uy, uz);
+            } else {
+                pair_free<double>(dx, dy, dz, lx, ly, lz, k, ux, uy, uz);
+            }
         }
     }
     if (it < nt) {
@@ -148,7 +158,8 @@ rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
         __syncthreads();
         if (threadIdx.x < cnt) {
             const int j = jt + threadIdx.x;
-            sh[threadIdx.x] = hi[j];
+            const float4 hj = hi[j];
+            sh[threadIdx.x] = make_float4(hj.x, hj.y, hj.z, 2.f * hj.z);  // .w: twice the height
             so[threadIdx.x] = lo[j];
             sl[threadIdx.x] = make_float4((float)lam[3 * (size_t)j], (float)lam[3 * (size_t)j + 1],
                                           (float)lam[3 * (size_t)j + 2], 0.f);
@@ -164,18 +175,21 @@ rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
 #pragma unroll
             for (int t = 0; t < TPT; ++t) {
                 float dx = hi_i[t].x - h.x, dy = hi_i[t].y - h.y, dz = hi_i[t].z - h.z;
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float rxy2 = fmaf(dx, dx, dy * dy);
+                float r2 = fmaf(dz, dz, rxy2);
                 if (r2 < near2[t]) {
                     const float4 o = so[q];
                     dx += lo_i[t].x - o.x;
                     dy += lo_i[t].y - o.y;
                     dz += lo_i[t].z - o.z;
-                    r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    rxy2 = fmaf(dx, dx, dy * dy);
+                    r2 = fmaf(dz, dz, rxy2);
                 }
-                pair_free_r2<float>(dx, dy, dz, r2, l.x, l.y, l.z, k, u[t][0], u[t][1], u[t][2]);
                 if (WALL)
-                    pair_image<float>(dx, dy, hi_i[t].z + h.z, hi_i[t].z, h.z, l.x, l.y, l.z, k,
-                                      u[t][0], u[t][1], u[t][2]);
+                    pair_wall_r2<float>(dx, dy, dz, rxy2, r2, hi_i[t].z + h.z, h.w, -hi_i[t].z, l.x, l.y, l.z, k,
+                                        u[t][0], u[t][1], u[t][2]);
+                else
+                    pair_free_r2<float>(dx, dy, dz, r2, l.x, l.y, l.z, k, u[t][0], u[t][1], u[t][2]);
             }
         }
 #pragma unroll
@@ -428,20 +442,30 @@ rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam
         for (int tb = m.t0; tb < m.t1; tb += kThreads) {
         const int i = tb + threadIdx.x;
         double4_32a ri = (i < m.t1) ? r4[i] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
+        const double nx3 = -ri.z;
         double ux = 0.0, uy = 0.0, uz = 0.0;
         for (int jt = m.j0; jt < m.j1; jt += kTile) {
             const int cnt = min(kTile, m.j1 - jt);
             __syncthreads();
-            if (threadIdx.x < cnt) sr[threadIdx.x] = r4[jt + threadIdx.x];
+            if (threadIdx.x < cnt) {
+                double4_32a v = r4[jt + threadIdx.x];
+                v.w = 2.0 * v.z;  // twice the source height, for the wall term
+                sr[threadIdx.x] = v;
+            }
             for (int q = threadIdx.x; q < 3 * cnt; q += kThreads) sl[q] = lam[3 * (size_t)jt + q];
             __syncthreads();
 #pragma unroll 2
             for (int q = 0; q < cnt; ++q) {
                 const double4_32a rj = sr[q];
                 const double lx = sl[3 * q], ly = sl[3 * q + 1], lz = sl[3 * q + 2];
-                const double dx = ri.x - rj.x, dy = ri.y - rj.y;
-                pair_free<double>(dx, dy, ri.z - rj.z, lx, ly, lz, k, ux, uy, uz);
-                if (WALL) pair_image<double>(dx, dy, ri.z + rj.z, ri.z, rj.z, lx, ly, lz, k, ux, uy, uz);
+                const double dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
+                if (WALL) {
+                    const double rxy2 = fma(dx, dx, dy * dy);
+                    pair_wall_r2<double>(dx, dy, dz, rxy2, fma(dz, dz, rxy2), ri.z + rj.z, rj.w, nx3, lx, ly,
+                                         lz, k, ux, uy, uz);
+                } else {
+                    pair_free<double>(dx, dy, dz, lx, ly, lz, k, ux, uy, uz);
+                }
             }
         }
         if (i < m.t1) {
@@ -488,7 +512,8 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
             __syncthreads();
             if (threadIdx.x < cnt) {
                 const int j = jt + threadIdx.x;
-                sh[threadIdx.x] = hi[j];
+                const float4 hj = hi[j];
+                sh[threadIdx.x] = make_float4(hj.x, hj.y, hj.z, 2.f * hj.z);  // .w: twice the height
                 so[threadIdx.x] = lo[j];
                 sl[threadIdx.x] = make_float4((float)lam[3 * (size_t)j], (float)lam[3 * (size_t)j + 1],
                                               (float)lam[3 * (size_t)j + 2], 0.f);
@@ -504,18 +529,21 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
 #pragma unroll
                 for (int t = 0; t < TPT; ++t) {
                     float dx = hi_i[t].x - h.x, dy = hi_i[t].y - h.y, dz = hi_i[t].z - h.z;
-                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float rxy2 = fmaf(dx, dx, dy * dy);
+                    float r2 = fmaf(dz, dz, rxy2);
                     if (r2 < near2[t]) {
                         const float4 o = so[q];
                         dx += lo_i[t].x - o.x;
                         dy += lo_i[t].y - o.y;
                         dz += lo_i[t].z - o.z;
-                        r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        rxy2 = fmaf(dx, dx, dy * dy);
+                        r2 = fmaf(dz, dz, rxy2);
                     }
-                    pair_free_r2<float>(dx, dy, dz, r2, l.x, l.y, l.z, k, u[t][0], u[t][1], u[t][2]);
                     if (WALL)
-                        pair_image<float>(dx, dy, hi_i[t].z + h.z, hi_i[t].z, h.z, l.x, l.y, l.z, k,
-                                          u[t][0], u[t][1], u[t][2]);
+                        pair_wall_r2<float>(dx, dy, dz, rxy2, r2, hi_i[t].z + h.z, h.w, -hi_i[t].z, l.x, l.y, l.z,
+                                            k, u[t][0], u[t][1], u[t][2]);
+                    else
+                        pair_free_r2<float>(dx, dy, dz, r2, l.x, l.y, l.z, k, u[t][0], u[t][1], u[t][2]);
                 }
             }
 #pragma unroll
@@ -546,67 +574,76 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
 
-// free-space pair for r >= 2a in both lanes (rpy_pair.cuh, far branch)
-__device__ __forceinline__ void pair_free_far2(float2 dx, float2 dy, float2 dz, float2 r2, float2 lx, float2 ly,
-                                               float2 lz, float2 kf2, float2 nkf3, float2& ux, float2& uy,
-                                               float2& uz) {
+// Free-space pair plus wall image in both lanes: pair_wall_r2 of
+// rpy_pair.cuh (same operations in the same order), with the free-space
+// coefficients of the far branch; pairs closer than 2a in either lane take
+// free_coefs per lane.  nx3 = -x3 per lane.
+template <bool WALL>
+__device__ __forceinline__ void pair2(float2 dx, float2 dy, float2 dz, float2 rxy2, float2 r2, float2 Rz, float2 h2,
+                                      float2 nx3, float2 lx, float2 ly, float2 lz, const RpyK<float>& k,
+                                      float2& ux, float2& uy, float2& uz) {
     const float2 one = bc2(1.f);
-    const float2 ri = rsq2(r2);
-    const float2 ri2 = mul2(ri, ri);
-    const float2 c1 = mul2(ri, fma2(kf2, ri2, one));
-    const float2 c2 = mul2(mul2(ri, ri2), fma2(nkf3, ri2, one));
-    const float2 sdl = mul2(c2, fma2(dx, lx, fma2(dy, ly, mul2(dz, lz))));
-    ux = fma2(c1, lx, fma2(sdl, dx, ux));
-    uy = fma2(c1, ly, fma2(sdl, dy, uy));
-    uz = fma2(c1, lz, fma2(sdl, dz, uz));
-}
-
-// wall image part of rpy_pair.cuh in both lanes
-__device__ __forceinline__ void pair_image2(float2 Rx, float2 Ry, float2 Rz, float2 x3, float2 h, float2 lx,
-                                            float2 ly, float2 lz, float2 a2, float2& ux, float2& uy, float2& uz) {
-    const float2 s = rsq2(fma2(Rx, Rx, fma2(Ry, Ry, mul2(Rz, Rz))));
-    const float2 s2 = mul2(s, s);
-    const float2 hs = mul2(h, s);
-    const float2 u = mul2(hs, mul2(x3, s));
-    const float2 ez = mul2(Rz, s);
-    const float2 ez2 = mul2(ez, ez);
-    const float2 A = mul2(a2, s2);
-    const float2 A2 = mul2(A, A);
-    const float2 t1 = mul2(A, ez2);
-    const float2 t2 = mul2(A2, ez2);
-    const float2 cI = fma2(bc2(-10.f / 3.f), t2, fma2(bc2(2.f / 3.f), A2, fma2(bc2(2.f), t1,
-                      fma2(bc2(-2.f / 3.f), A, fma2(bc2(-2.f), u, bc2(-1.f))))));
-    const float2 cRR = fma2(bc2(70.f / 3.f), t2, fma2(bc2(-10.f / 3.f), A2, fma2(bc2(-10.f), t1,
-                       fma2(bc2(2.f), A, fma2(bc2(6.f), u, bc2(-1.f))))));
-    const float2 inner = fma2(bc2(20.f / 3.f), A2, fma2(bc2(-2.f), cRR, bc2(-2.f)));
-    const float2 hs2 = add2(hs, hs);
-    const float2 cRz = fma2(ez, inner, hs2);
-    const float2 czR = fma2(mul2(bc2(-20.f / 3.f), A2), ez, hs2);
-    const float2 czz = fma2(bc2(-4.f), mul2(hs, hs), fma2(bc2(20.f), t2, fma2(bc2(-8.f / 3.f), A2,
-                       mul2(bc2(-4.f), t1))));
-    const float2 rx = mul2(Rx, s), ry = mul2(Ry, s);
-    const float2 dotR = fma2(rx, lx, fma2(ry, ly, mul2(ez, lz)));
-    const float2 t = fma2(cRR, dotR, mul2(cRz, lz));
-    ux = fma2(s, fma2(cI, lx, mul2(t, rx)), ux);
-    uy = fma2(s, fma2(cI, ly, mul2(t, ry)), uy);
-    uz = fma2(s, fma2(cI, lz, fma2(t, ez, fma2(czR, dotR, mul2(czz, lz)))), uz);
+    float2 c1f, c2f;
+    if (r2.x < k.four_a2 || r2.y < k.four_a2) {
+        free_coefs<float>(r2.x, k, c1f.x, c2f.x);
+        free_coefs<float>(r2.y, k, c1f.y, c2f.y);
+    } else {
+        const float2 ri = rsq2(r2);
+        const float2 ri2 = mul2(ri, ri);
+        c1f = mul2(ri, fma2(bc2(k.kf2), ri2, one));
+        c2f = mul2(mul2(ri, ri2), fma2(bc2(-k.kf3), ri2, one));
+    }
+    const float2 dlxy = fma2(dx, lx, mul2(dy, ly));
+    const float2 Df = fma2(dz, lz, dlxy);
+    const float2 sdl = mul2(c2f, Df);
+    if (!WALL) {
+        ux = fma2(c1f, lx, fma2(sdl, dx, ux));
+        uy = fma2(c1f, ly, fma2(sdl, dy, uy));
+        uz = fma2(c1f, lz, fma2(sdl, dz, uz));
+        return;
+    }
+    const float2 Rz2 = mul2(Rz, Rz);
+    const float2 Di = fma2(Rz, lz, dlxy);
+    const float2 s = rsq2(add2(rxy2, Rz2));
+    const float2 w = mul2(s, s), s3 = mul2(s, w), w2 = mul2(w, w);
+    const float2 c1 = fma2(h2, nx3, bc2(k.wc1));
+    const float2 c2 = fma2(Rz2, bc2(k.w2a2), bc2(k.wc2));
+    const float2 c3 = mul2(Rz2, bc2(k.wc3));
+    const float2 x1 = fma2(w, c3, c2);
+    const float2 cI = fma2(w, fma2(w, x1, c1), bc2(-1.f));
+    const float2 y = fma2(w, c3, x1);
+    const float2 yz = fma2(w, c3, y);
+    const float2 cRR = fma2(mul2(w2, y), bc2(-2.f), fma2(cI, bc2(-3.f), bc2(-4.f)));
+    const float2 A4w2n = mul2(w2, bc2(-k.wa4));
+    const float2 inner = fma2(cRR, bc2(-2.f), fma2(A4w2n, bc2(-1.f), bc2(-2.f)));
+    const float2 P = mul2(s3, fma2(cRR, Di, mul2(fma2(Rz, inner, h2), lz)));
+    const float2 Q = mul2(s3, fma2(h2, Df, fma2(mul2(A4w2n, Rz), Di, mul2(mul2(w, fma2(yz, bc2(-2.f), bc2(k.wi2))), lz))));
+    const float2 cc = fma2(s, cI, c1f);
+    const float2 pp = add2(sdl, P);
+    ux = fma2(cc, lx, fma2(pp, dx, ux));
+    uy = fma2(cc, ly, fma2(pp, dy, uy));
+    uz = fma2(cc, lz, fma2(sdl, dz, fma2(P, Rz, add2(uz, Q))));
 }
 
 // The mixed product with two targets per thread (items of 256 targets):
 // target t0 + threadIdx.x in lane x, t0 + 128 + threadIdx.x in lane y.
-// Differences always include the lo parts of the positions; pairs closer
-// than 2a in either lane (same-body neighbours) take the scalar formula.
+// Differences are formed from the hi parts; within a quarter of the
+// target's largest coordinate (either lane), where the rounding of hi
+// would exceed 5e-7 of the distance, the lo parts are added (as in
+// rpy_items_mixed).  The sources are staged duplicated in shared memory so
+// that one 128-bit load gives ready register pairs: (-hx, -hx, -hy, -hy),
+// (2hz, 2hz, lz, lz), (lx, lx, ly, ly), and the lo parts (-ox, -ox, -oy, -oy),
+// (-oz, -oz) apart, read only for near pairs.
 template <bool WALL>
 __global__ void __launch_bounds__(kThreads, 4)
 rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
                    const double* __restrict__ lam, double* __restrict__ part,
                    const MvItem* __restrict__ items, int n_items, int* __restrict__ counter,
                    RpyK<float> k) {
-    // per source: (-hx,-hx,-hy,-hy) (-hz,-hz,-ox,-ox) (-oy,-oy,-oz,-oz)
-    // (lx,lx,ly,ly) (lz,lz,hz,hz)
-    __shared__ float4 sq[5][kTile];
+    __shared__ float4 sq[3][kTile];
+    __shared__ float4 so[kTile];
+    __shared__ float2 soz[kTile];
     __shared__ int s_item;
-    const float2 kf2 = bc2(k.kf2), nkf3 = bc2(-k.kf3), a2 = bc2(k.a2);
     for (int round = 0;; ++round) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(counter, 1);
@@ -621,6 +658,10 @@ rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
         const float4 l1 = (i1 < m.t1) ? lo[i1] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float2 HX = make_float2(h0.x, h1.x), HY = make_float2(h0.y, h1.y), HZ = make_float2(h0.z, h1.z);
         const float2 LX = make_float2(l0.x, l1.x), LY = make_float2(l0.y, l1.y), LZ = make_float2(l0.z, l1.z);
+        const float2 NX3 = make_float2(-h0.z, -h1.z);
+        const float n0 = 0.25f * fmaxf(fabsf(h0.x), fmaxf(fabsf(h0.y), fabsf(h0.z)));
+        const float n1 = 0.25f * fmaxf(fabsf(h1.x), fmaxf(fabsf(h1.y), fabsf(h1.z)));
+        const float near2x = n0 * n0, near2y = n1 * n1;
         double U[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
         for (int jt = m.j0; jt < m.j1; jt += kTile) {
             const int cnt = min(kTile, m.j1 - jt);
@@ -631,31 +672,33 @@ rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
                 const float lx = (float)lam[3 * (size_t)j], ly = (float)lam[3 * (size_t)j + 1],
                             lz = (float)lam[3 * (size_t)j + 2];
                 sq[0][threadIdx.x] = make_float4(-h.x, -h.x, -h.y, -h.y);
-                sq[1][threadIdx.x] = make_float4(-h.z, -h.z, -o.x, -o.x);
-                sq[2][threadIdx.x] = make_float4(-o.y, -o.y, -o.z, -o.z);
-                sq[3][threadIdx.x] = make_float4(lx, lx, ly, ly);
-                sq[4][threadIdx.x] = make_float4(lz, lz, h.z, h.z);
+                sq[1][threadIdx.x] = make_float4(2.f * h.z, 2.f * h.z, lz, lz);
+                sq[2][threadIdx.x] = make_float4(lx, lx, ly, ly);
+                so[threadIdx.x] = make_float4(-o.x, -o.x, -o.y, -o.y);
+                soz[threadIdx.x] = make_float2(-o.z, -o.z);
             }
             __syncthreads();
             float2 ux = bc2(0.f), uy = bc2(0.f), uz = bc2(0.f);
 #pragma unroll 2
             for (int q = 0; q < cnt; ++q) {
-                const float4 v0 = sq[0][q], v1 = sq[1][q], v2 = sq[2][q], v3 = sq[3][q], v4 = sq[4][q];
-                const float2 dx = add2(add2(HX, make_float2(v0.x, v0.y)), add2(LX, make_float2(v1.z, v1.w)));
-                const float2 dy = add2(add2(HY, make_float2(v0.z, v0.w)), add2(LY, make_float2(v2.x, v2.y)));
-                const float2 dz = add2(add2(HZ, make_float2(v1.x, v1.y)), add2(LZ, make_float2(v2.z, v2.w)));
-                const float2 lx = make_float2(v3.x, v3.y), ly = make_float2(v3.z, v3.w), lz = make_float2(v4.x, v4.y);
-                const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                if (r2.x < k.four_a2 || r2.y < k.four_a2) {
-                    pair_free_r2<float>(dx.x, dy.x, dz.x, r2.x, lx.x, ly.x, lz.x, k, ux.x, uy.x, uz.x);
-                    pair_free_r2<float>(dx.y, dy.y, dz.y, r2.y, lx.y, ly.y, lz.y, k, ux.y, uy.y, uz.y);
-                } else {
-                    pair_free_far2(dx, dy, dz, r2, lx, ly, lz, kf2, nkf3, ux, uy, uz);
+                const float4 v0 = sq[0][q], v1 = sq[1][q], v2 = sq[2][q];
+                const float2 h2 = make_float2(v1.x, v1.y);
+                float2 dx = add2(HX, make_float2(v0.x, v0.y));
+                float2 dy = add2(HY, make_float2(v0.z, v0.w));
+                float2 dz = fma2(h2, bc2(-0.5f), HZ);
+                const float2 Rz = fma2(h2, bc2(0.5f), HZ);
+                float2 rxy2 = fma2(dx, dx, mul2(dy, dy));
+                float2 r2 = fma2(dz, dz, rxy2);
+                if (r2.x < near2x || r2.y < near2y) {
+                    const float4 o = so[q];
+                    dx = add2(dx, add2(LX, make_float2(o.x, o.y)));
+                    dy = add2(dy, add2(LY, make_float2(o.z, o.w)));
+                    dz = add2(dz, add2(LZ, soz[q]));
+                    rxy2 = fma2(dx, dx, mul2(dy, dy));
+                    r2 = fma2(dz, dz, rxy2);
                 }
-                if (WALL) {
-                    const float2 hz = make_float2(v4.z, v4.w);
-                    pair_image2(dx, dy, add2(HZ, hz), HZ, hz, lx, ly, lz, a2, ux, uy, uz);
-                }
+                pair2<WALL>(dx, dy, dz, rxy2, r2, Rz, h2, NX3, make_float2(v2.x, v2.y), make_float2(v2.z, v2.w),
+                            make_float2(v1.z, v1.w), k, ux, uy, uz);
             }
             U[0][0] += (double)ux.x; U[0][1] += (double)uy.x; U[0][2] += (double)uz.x;
             U[1][0] += (double)ux.y; U[1][1] += (double)uy.y; U[1][2] += (double)uz.y;

@@ -35,6 +35,13 @@ struct RpyK {
     T kn0;       // 4 / (3 a)
     T kn1;       // 9 / (32 a)
     T kn2;       // 1 / (8 a^2)
+    // wall coefficients of pair_wall (polynomial form in w = s^2)
+    T wc1;       // -2 a^2 / 3
+    T w2a2;      // 2 a^2
+    T wc2;       // 2 a^4 / 3
+    T wc3;       // -10 a^4 / 3
+    T wa4;       // 20 a^4 / 3
+    T wi2;       // -4 a^4 / 3
     double A1;   // 1 / (8 pi eta)
 };
 
@@ -48,6 +55,13 @@ inline RpyK<T> rpy_consts(const RpyParams& q) {
     k.kn0 = (T)(4.0 / (3.0 * q.a));
     k.kn1 = (T)(9.0 / (32.0 * q.a));
     k.kn2 = (T)(1.0 / (8.0 * q.a2));
+    const double a4 = q.a2 * q.a2;
+    k.wc1 = (T)(-2.0 * q.a2 / 3.0);
+    k.w2a2 = (T)(2.0 * q.a2);
+    k.wc2 = (T)(2.0 * a4 / 3.0);
+    k.wc3 = (T)(-10.0 * a4 / 3.0);
+    k.wa4 = (T)(20.0 * a4 / 3.0);
+    k.wi2 = (T)(-4.0 * a4 / 3.0);
     k.A1 = q.inv8pieta;
     return k;
 }
@@ -57,10 +71,9 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float sqt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqt(double x) { return sqrt(x); }
 
+// the free-space coefficients c1, c2 of a pair at squared distance r2
 template <class T>
-__device__ __forceinline__ void pair_free_r2(T dx, T dy, T dz, T r2, T lx, T ly, T lz,
-                                             const RpyK<T>& k, T& ux, T& uy, T& uz) {
-    T c1, c2;
+__device__ __forceinline__ void free_coefs(T r2, const RpyK<T>& k, T& c1, T& c2) {
     if (r2 >= k.four_a2) {
         const T ri = rsq(r2);
         const T ri2 = ri * ri;
@@ -71,6 +84,13 @@ __device__ __forceinline__ void pair_free_r2(T dx, T dy, T dz, T r2, T lx, T ly,
         c1 = k.kn0 * fma(-k.kn1, r, (T)1);
         c2 = (r2 > (T)0) ? k.kn2 / r : (T)0;
     }
+}
+
+template <class T>
+__device__ __forceinline__ void pair_free_r2(T dx, T dy, T dz, T r2, T lx, T ly, T lz,
+                                             const RpyK<T>& k, T& ux, T& uy, T& uz) {
+    T c1, c2;
+    free_coefs<T>(r2, k, c1, c2);
     const T sdl = c2 * fma(dx, lx, fma(dy, ly, dz * lz));
     ux = fma(c1, lx, fma(sdl, dx, ux));
     uy = fma(c1, ly, fma(sdl, dy, uy));
@@ -109,6 +129,57 @@ __device__ __forceinline__ void pair_image(T Rx, T Ry, T Rz, T x3, T h, T lx, T 
     ux = fma(s, fma(cI, lx, t * rx), ux);
     uy = fma(s, fma(cI, ly, t * ry), uy);
     uz = fma(s, fma(cI, lz, fma(t, ez, fma(czR, dotR, czz * lz))), uz);
+}
+
+// Free-space pair plus wall image of one source, fused (the sum of
+// pair_free_r2 and pair_image, reorganised; the products are the same up to
+// rounding).  With w = s^2, R = (dx, dy, Rz), h2 = 2h, D = R . lambda and
+//   c1 = -2 h x3 - 2a^2/3,  c2 = 2a^2 Rz^2 + 2a^4/3,  c3 = -10a^4 Rz^2 / 3,
+// the image coefficients above are polynomials in w:
+//   cI  = -1 + w c1 + w^2 c2 + w^3 c3
+//   cRR = -1 - 3 w c1 - 5 w^2 c2 - 7 w^3 c3 = -4 - 3 cI - 2 w^2 (c2 + 2 w c3)
+//   s^2 cRz = s^3 (2h + Rz (20/3 a^4 w^2 - 2 cRR - 2))
+//   s^2 czR = s^3 (2h - 20/3 a^4 w^2 Rz)
+//   s czz   = s^3 (-4h^2 - 2 w (c2 + 3 w c3) - 4/3 a^4 w)
+// and, applied to the unnormalised R (Rh = R s, Rh . lambda = s D),
+//   u/A1 += s cI lambda + P R + Q e3,
+//   P = s^3 cRR D + s^2 cRz lambda_3,  Q = s^2 czR D + s czz lambda_3.
+// In Q, 2h D - 4h^2 lambda_3 = 2h (d . lambda) because D - 2h lambda_3 =
+// d . lambda (R_z - 2h = d_z), so
+//   Q = s^3 (2h (d . lambda) - 20/3 a^4 w^2 Rz D
+//            + w (-2 (c2 + 3 w c3) - 4/3 a^4) lambda_3)
+// with no negated operand (the paired-lane form has no free negation).
+// The free and image parts share one multiply-add per component of lambda
+// and of d (R_x = d_x, R_y = d_y).  rxy2 = dx^2 + dy^2 and r2 = rxy2 + dz^2
+// come from the caller; nx3 = -x3 (target height).
+template <class T>
+__device__ __forceinline__ void pair_wall_r2(T dx, T dy, T dz, T rxy2, T r2, T Rz, T h2, T nx3, T lx,
+                                             T ly, T lz, const RpyK<T>& k, T& ux, T& uy, T& uz) {
+    const T Rz2 = Rz * Rz;
+    const T dlxy = fma(dx, lx, dy * ly);
+    const T Df = fma(dz, lz, dlxy);   // d . lambda
+    const T Di = fma(Rz, lz, dlxy);   // R . lambda
+    T c1f, c2f;
+    free_coefs<T>(r2, k, c1f, c2f);
+    const T sdl = c2f * Df;
+    const T s = rsq(rxy2 + Rz2);
+    const T w = s * s, s3 = s * w, w2 = w * w;
+    const T c1 = fma(h2, nx3, k.wc1);
+    const T c2 = fma(Rz2, k.w2a2, k.wc2);
+    const T c3 = Rz2 * k.wc3;
+    const T x1 = fma(w, c3, c2);
+    const T cI = fma(w, fma(w, x1, c1), (T)-1);
+    const T y = fma(w, c3, x1);                 // c2 + 2 w c3
+    const T yz = fma(w, c3, y);                 // c2 + 3 w c3
+    const T cRR = fma(w2 * y, (T)-2, fma(cI, (T)-3, (T)-4));
+    const T A4w2n = w2 * -k.wa4;                // -20/3 a^4 w^2
+    const T P = s3 * fma(cRR, Di, fma(Rz, fma(cRR, (T)-2, fma(A4w2n, (T)-1, (T)-2)), h2) * lz);
+    const T Q = s3 * fma(h2, Df, fma(A4w2n * Rz, Di, (w * fma(yz, (T)-2, k.wi2)) * lz));
+    const T cc = fma(s, cI, c1f);
+    const T pp = sdl + P;
+    ux = fma(cc, lx, fma(pp, dx, ux));
+    uy = fma(cc, ly, fma(pp, dy, uy));
+    uz = fma(cc, lz, fma(sdl, dz, fma(P, Rz, uz + Q)));
 }
 
 // Full 3x3 tensor T (row-major, T[3a+b]: velocity a at x from force b at y),
