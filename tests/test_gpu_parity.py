@@ -337,22 +337,27 @@ def test_not_converged_reports_status(chains):
 # --------------------------------------------------------- full sizes ---
 @pytest.mark.slow
 def test_colony_full_size_solve():
-    # 2,560 blobs, wall, 62 links: a tight solve agrees with the oracle's
-    # formal solution; sampled mobility rows agree with the oracle's rows.
+    # 2,560 blobs, wall, 62 links (8,058 unknowns, C of rank 155): a solve
+    # to relative residual 1e-12 agrees with the oracle's dense solve of the
+    # whole saddle-point system at the FP64 bar, in lambda, U and C^T phi
+    # (phi itself is unique only modulo null(C^T)); sampled mobility rows
+    # agree with the oracle's rows.  The errors follow the residual (the
+    # oracle's dense and formal solutions agree to about 5e-13).
     w = W.diatom_colony(1)
     t = 0.05
     S = System(w, t=t)
-    s = binding.Solver.from_workload(w, t=t, tol=1e-12)
+    s = binding.Solver.from_workload(w, t=t, tol=1e-12, max_iter=2000)
     rows = np.random.default_rng(0).choice(S.Nb, 64, replace=False)
     lam = np.random.default_rng(1).standard_normal((S.Nb, 3))
     u = s.apply_mobility(lam)
     assert rel(u[rows], om.mobility_rows(S.r, lam, rows, S.a, S.eta, 1)) <= FP64_MATVEC
     U, phi, lamg, st = s.solve()
-    assert st["status"] == 0
-    y = S.solve_formal()
-    lam_o, U_o, phi_o = S.split(y)
-    assert rel(U.ravel(), U_o) <= 1e-8
-    assert rel(S.C_dense().T @ phi.ravel(), S.C_dense().T @ phi_o) <= 1e-8
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-12
+    lam_o, U_o, phi_o = S.split(S.solve_dense())
+    C = S.C_dense()
+    assert rel(lamg.ravel(), lam_o) <= FP64_SOLVE
+    assert rel(U.ravel(), U_o) <= FP64_SOLVE
+    assert rel(C.T @ phi.ravel(), C.T @ phi_o) <= FP64_SOLVE
 
 
 @pytest.mark.slow
