@@ -23,6 +23,10 @@ The far forms are the vorticity (half the curl) of the regularised
 Stokeslet and of the rotlet, which the surface averages of Eq. RPY leave
 unchanged (both are harmonic); the overlapping forms are the published
 closed forms for equal spheres (Wajnryb, Mizerski, Zuk and Szymczak 2013).
+Both are pinned by quadrature of the surface averages that define the
+tensor (a force spread over the surface of one blob, a torque as the
+surface density (3/(8 pi a^3)) T x n, the rotation of the other blob as
+(3/(2a)) <n x u> over its surface), overlapping and separated.
 """
 import numpy as np
 

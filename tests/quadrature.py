@@ -61,3 +61,37 @@ def double_average(G, xi, xj, a, eta, nt, nphi):
     for k in range(len(A)):
         out += w[k] * np.einsum("j,jab->ab", w, G(A[k][None, :], B, eta))
     return out
+
+
+def _cross_matrices(n):
+    """[n_k]x for each row n_k (so that [n]x v = n x v)."""
+    Z = np.zeros((len(n), 3, 3))
+    Z[:, 0, 1], Z[:, 0, 2] = -n[:, 2], n[:, 1]
+    Z[:, 1, 0], Z[:, 1, 2] = n[:, 2], -n[:, 0]
+    Z[:, 2, 0], Z[:, 2, 1] = -n[:, 1], n[:, 0]
+    return Z
+
+
+def rotational_averages(xi, xj, a, eta, nt, nphi):
+    """Rotation-from-force and rotation-from-torque couplings of two blobs of
+    radius a about xi (rotating) and xj (forced), by the surface averages
+    that define the generalised RPY tensor (Sec. 2.4: a force F_j spread
+    evenly over the surface of blob j, a torque T_j as the surface force
+    density (3/(8 pi a^3)) T_j x n; the rotation of blob i as the rigid
+    rotation fitted to the flow on its surface, (3/(2a)) <n x u>_{S_i}, which
+    returns omega for u = omega x (x - xi)):
+        M_rt = (3/(2a)) < [n_x]x <G(x, y)>_y >_x
+        M_rr = -(3/(2a))^2 < [n_x]x <G(x, y) [n_y]x>_y >_x
+    with G the Oseen tensor.  Returns (M_rt, M_rr)."""
+    pts, w = sphere_rule(nt, nphi)
+    X = _cross_matrices(pts)
+    A = xi + a * pts
+    B = xj + a * pts
+    rt = np.zeros((3, 3))
+    rr = np.zeros((3, 3))
+    for k in range(len(A)):
+        G = oseen(A[k][None, :], B, eta)
+        rt += w[k] * X[k] @ np.einsum("j,jab->ab", w, G)
+        rr += w[k] * X[k] @ np.einsum("j,jab,jbc->ac", w, G, X)
+    c = 3.0 / (2.0 * a)
+    return c * rt, -c * c * rr

@@ -1,15 +1,20 @@
 """Pins of the single-blob oracle (generalised RPY tensor, free space): the
 rotational far forms against finite-difference vorticity of the pinned
-translational tensor and of the rotlet, continuity at contact and at
-coincidence, symmetry and positive definiteness (overlaps included), and the
-dense against the formal solution of the constrained problem."""
+translational tensor and of the rotlet; the overlapping and the separated
+forms against quadrature of the surface averages that define the tensor;
+continuity at contact and at coincidence, symmetry and positive
+definiteness (overlaps included), and the dense against the formal solution
+of the constrained problem."""
 import numpy as np
+import pytest
 
 from oracle import single_blob as sb
 from oracle.mobility import rpy_free_pair
 from paper_2107_10800_gb300 import workloads as W
+from quadrature import rotational_averages
 
 A, ETA = 0.1, 1.3
+DIR = np.array([0.36, -0.48, 0.8]) / np.linalg.norm([0.36, -0.48, 0.8])
 
 
 def curl_half(field, x, h=1e-5):
@@ -77,3 +82,51 @@ def test_constrained_single_blob_solve_dense_equals_formal():
     assert np.abs(U - Uf).max() < 1e-10 * np.abs(Uf).max()
     assert np.abs(C.T @ phi - C.T @ phif).max() < 1e-9 * np.abs(C.T @ phif).max()
     assert np.abs(C @ U - s.S.B_vec()).max() < 1e-12 * np.abs(U).max()
+
+
+# Overlapping blobs: the integrand is singular on the circle where the two
+# surfaces cross, so the quadrature converges slowly (about 5e-4 to 1.2e-3
+# with 32 x 64 points per sphere at these separations, 1e-4 to 3e-4 with
+# 48 x 96); 3e-3 still separates the closed forms from coefficients that
+# keep continuity at contact and coincidence but are wrong
+# (test_overlap_pin_rejects_contact_continuous_perturbations).
+OVERLAP_QUAD = 3e-3
+
+
+@pytest.mark.parametrize("r_over_a", [0.6, 1.2, 1.7])
+def test_overlapping_rotational_pairs_equal_double_surface_averages(r_over_a):
+    d = r_over_a * A * DIR
+    Qrt, Qrr = rotational_averages(np.zeros(3), -d, A, ETA, 32, 64)
+    Ert, Err = sb.pair_rt(d, A, ETA), sb.pair_rr(d, A, ETA)
+    assert np.abs(Qrt - Ert).max() <= OVERLAP_QUAD * np.abs(Ert).max()
+    assert np.abs(Qrr - Err).max() <= OVERLAP_QUAD * np.abs(Err).max()
+
+
+def test_separated_rotational_pairs_equal_double_surface_averages():
+    # beyond contact the integrand is smooth: the far forms to rounding
+    for r_over_a in (2.5, 4.0):
+        d = r_over_a * A * DIR
+        Qrt, Qrr = rotational_averages(np.zeros(3), -d, A, ETA, 32, 64)
+        assert np.abs(Qrt - sb.pair_rt(d, A, ETA)).max() <= 1e-10 * np.abs(Qrt).max()
+        assert np.abs(Qrr - sb.pair_rr(d, A, ETA)).max() <= 1e-10 * np.abs(Qrr).max()
+
+
+def test_overlap_pin_rejects_contact_continuous_perturbations():
+    # Perturbed overlap coefficients that keep the values at r = 0 and at
+    # r = 2a: rotation-from-torque I-coefficient 1 + (alpha + e) s + (beta -
+    # e/4) s^3 (1 + 2 alpha + 8 beta fixed), rotation-from-force
+    # (1 + e) s + (-3/8 - e/2) s^2 (2 alpha + 4 beta fixed), s = r/a, with a
+    # coefficient change e = 1/32 (2.3 % and 8.4 % of the tensors at
+    # r = 1.2a).  The quadrature must tell them apart by a wide margin.
+    e = 1.0 / 32.0
+    r_over_a = 1.2
+    d = r_over_a * A * DIR
+    s = r_over_a
+    Qrt, Qrr = rotational_averages(np.zeros(3), -d, A, ETA, 32, 64)
+    ee = np.outer(DIR, DIR)
+    cI = 1 + (-27.0 / 32.0 + e) * s + (5.0 / 64.0 - e / 4) * s ** 3
+    rr_bad = (cI * np.eye(3) + (9 * s / 32 - 3 * s ** 3 / 64) * ee) / (8 * np.pi * ETA * A ** 3)
+    c = ((1 + e) * s - (3.0 / 8.0 + e / 2) * s * s) / (16 * np.pi * ETA * A * A)
+    rt_bad = -c * sb.cross_matrix(DIR)
+    assert np.abs(Qrr - rr_bad).max() > 5 * OVERLAP_QUAD * np.abs(Qrr).max()
+    assert np.abs(Qrt - rt_bad).max() > 5 * OVERLAP_QUAD * np.abs(Qrt).max()
