@@ -1,0 +1,90 @@
+"""Single workloads for profilers (ncu): each case runs one small, fixed
+piece of the solver's hot path a few times and exits, so that a capture of
+one kernel (-k, -c) ends quickly.  Nothing here is timed.
+
+    python -m paper_2107_10800_gb300.profile_cases product --blobs 60000 [--arith mixed|fp64|df64]
+    python -m paper_2107_10800_gb300.profile_cases colony --precision fp64|mixed [--steps 3] [--host-steps]
+    python -m paper_2107_10800_gb300.profile_cases batched [--steps 1]
+
+product: the all-pairs wall product u = M lambda on the first N blobs of the
+1,000-bacteria suspension above a wall (each blob its own body, so the
+product is the solver's work-queue kernel on one system), two targets per
+thread and 4,096-source chunks for the mixed arithmetic; `--calls` products.
+colony: Euler steps of the diatom colony (2,560 blobs, 62 sliding links,
+dt = 1e-3, relative residual 1e-8); with --host-steps the Arnoldi steps are
+launched from the host (per-launch timing of the product on) instead of
+from the CUDA-graph loop, whose kernels profilers do not capture.
+batched: steps of the 256 free-space chain suspensions in one handle
+(mixed precision).
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2107_10800_gb300 import build, binding, workloads as W  # noqa: E402
+
+
+def product(blobs, arith, calls):
+    w = W.bacteria_wall(1)
+    s = binding.Solver.from_workload(w, precision="mixed")
+    r = s.blobs()[:blobs]
+    s.close()
+    n = len(r)
+    s = binding.Solver(eta=w["eta"], a=w["a"], wall=1, precision="mixed")
+    s.set_bodies(r, np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)), np.arange(n + 1), np.zeros((n, 3)),
+                 np.zeros((n, 6)), np.arange(n))
+    s.set_mobility_layout(2 if arith == "mixed" else 1, 4096 if arith == "mixed" else 0)
+    lam = np.random.default_rng(0).standard_normal(r.shape)
+    for _ in range(calls):
+        s.apply_mobility_ex(lam, arith)
+    s.close()
+
+
+def colony(precision, steps, host_steps=False):
+    w = W.diatom_colony(1)
+    s = binding.Solver.from_workload(w, t=0.0, tol=1e-8, precision=precision)
+    if host_steps:
+        s.mobility_timing(True)
+    for k in range(steps):
+        t = k * 1e-3
+        if k:
+            dlp, dlq, dlpd, dlqd = w["dl"](t)
+            s.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd)
+        s.step(t, 1e-3, dl_next=w["dl"](t + 1e-3)[:2])
+    s.close()
+
+
+def batched(steps):
+    s = binding.Solver.from_workloads(W.batched_chains(1), tol=1e-8, precision="mixed")
+    for k in range(steps):
+        s.step(k * 1e-3, 1e-3)
+    s.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["product", "colony", "batched"])
+    ap.add_argument("--blobs", type=int, default=60000)
+    ap.add_argument("--arith", default="mixed", choices=["mixed", "fp64", "df64"])
+    ap.add_argument("--calls", type=int, default=3)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--host-steps", action="store_true")
+    a = ap.parse_args()
+    build.build()
+    if a.case == "product":
+        product(a.blobs, a.arith, a.calls)
+    elif a.case == "colony":
+        colony(a.precision, a.steps, a.host_steps)
+    else:
+        batched(a.steps)
+
+
+if __name__ == "__main__":
+    main()
