@@ -82,32 +82,42 @@ def test_extrapolation_starts_closer_and_iterates_less(precision):
 
 
 def test_extrapolated_midpoint_steps_match_oracle():
-    # stages at t and t + dt/2 enter the history with their own times
+    # stages at t and t + dt/2 enter the history with their own times.  The
+    # stage systems of this colony are consistent only to about 1e-10 after
+    # the first stage (prescribed sliding against the reconstructed pose;
+    # the oracle's dense solve leaves 5e-11), and restarted GMRES stalls
+    # above that (measured on GB300 after 400 iterations: 4.4e-10 in the
+    # first step, 2.3e-9 in the second), so a stage may stop at the step
+    # budget; the poses still agree.  The stage residuals reached with the
+    # extrapolated guess are checked against those of the same steps from
+    # the previous solution (order 1): a guess that left the stage solves
+    # far above the plain guess's level is caught.
     w = W.diatom_colony(7, n_rods=4, nx=8)
     t0, dt = 0.05, 1e-2
-    s = binding.Solver.from_workload(w, t=t0, tol=1e-12, max_iter=400)
-    s.set_initial_guess(3)
+    resid, poses = {}, {}
+    for order in (1, 3):
+        s = binding.Solver.from_workload(w, t=t0, tol=1e-12, max_iter=400)
+        s.set_initial_guess(order)
+        resid[order] = []
+        for k in range(2):
+            t = t0 + k * dt
+            if k:
+                dlp, dlq, dlpd, dlqd = w["dl"](t)
+                s.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd)
+            U, phi, lam, st = s.step_rk2(t, dt, dl_half=w["dl"](t + 0.5 * dt), dl_next=w["dl"](t + dt)[:2])
+            assert st["status"] in (0, binding.AM_ERR_NOT_CONVERGED)
+            resid[order].append(st["rel_residual"])  # the larger of the two stages
+        poses[order] = s.bodies()
+        s.close()
+    for r3, r1 in zip(resid[3], resid[1]):
+        assert r3 <= max(10 * r1, 1e-12), (resid[3], resid[1])
     qo, tho = w["q"], w["theta"]
     for k in range(2):
-        t = t0 + k * dt
-        if k:
-            dlp, dlq, dlpd, dlqd = w["dl"](t)
-            s.set_constraints(w["body_p"], w["body_q"], dlp, dlq, dlpd, dlqd)
-        U, phi, lam, st = s.step_rk2(t, dt, dl_half=w["dl"](t + 0.5 * dt), dl_next=w["dl"](t + dt)[:2])
-        # the stage systems of this colony are consistent only to about
-        # 1e-10 after the first stage (prescribed sliding against the
-        # reconstructed pose; the oracle's dense solve leaves 5e-11), so a
-        # stage may stop at the step budget (measured on GB300: 4.4e-10
-        # after 432 iterations, restarted GMRES nearing the least-squares
-        # floor); the poses still agree.  Both stage solves must still reach
-        # 1e-9 (rel_residual is the larger of the two), so a guess that left
-        # them at the budget far above the floor is caught.
-        assert st["status"] in (0, binding.AM_ERR_NOT_CONVERGED)
-        assert st["rel_residual"] <= 1e-9, st
-        qo, tho, _ = ots.midpoint_step(w, qo, tho, t, dt, delta=1e-10, solve_tol=1e-13)
-    q, th = s.bodies()
-    assert rel(q, qo) <= FP64_SOLVE
-    assert rel(th, tho) <= FP64_SOLVE
+        qo, tho, _ = ots.midpoint_step(w, qo, tho, t0 + k * dt, dt, delta=1e-10, solve_tol=1e-13)
+    for order in (1, 3):
+        q, th = poses[order]
+        assert rel(q, qo) <= FP64_SOLVE
+        assert rel(th, tho) <= FP64_SOLVE
 
 
 def test_repeated_time_falls_back_to_the_previous_solution():
