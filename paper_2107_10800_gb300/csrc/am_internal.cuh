@@ -74,9 +74,25 @@ struct MvItem {
     int j0, j1;       // sources [j0, j1)
     int tbase, n3;    // first blob of the system, 3 N_s
     long long pbase;  // poff_s + c * 3 N_s
+    int sys, pad;     // system index
 };
 
 // ---- device helpers -----------------------------------------------------
+// End of a work-queue kernel (counter[0]: next item, counter[1]: blocks
+// finished): the last block to finish zeroes both for the next launch.
+// Every block has taken its last item before it counts itself finished, so
+// no block reads the queue after the reset.
+__device__ __forceinline__ void item_queue_done(int* counter) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&counter[1], 1) == (int)gridDim.x - 1) {
+            counter[0] = 0;
+            counter[1] = 0;
+        }
+    }
+}
+
 // R(theta) v = 2 [ p (p.v) + s (p x v) + (s^2 - 1/2) v ]   (App. B, Eq. rot_mat)
 __device__ __forceinline__ void quat_rotate(double s, double px, double py, double pz,
                                             double vx, double vy, double vz,
@@ -155,11 +171,13 @@ struct am_handle {
            *d_xis = nullptr, *d_bnorm_s = nullptr, *d_beta_s = nullptr, *d_inv_s = nullptr,
            *d_tol_s = nullptr, *d_sysred = nullptr, *d_hcols = nullptr;
     int *d_active = nullptr, *d_kdone = nullptr;
+    int* d_arn_cnt = nullptr;  // S + 1 arrival counts of the fused Arnoldi step kernels
+    int chunk_len = 1024, chunk_threads = 256;  // dot-product chunk length, threads per chunk block
     // all-pairs work items (block-diagonal over systems) and their queue
     void* d_items = nullptr;
     int n_items = 0;
     int* d_item_counter = nullptr;
-    int mv_tpt = 1, mv_chunk = 0, mv_grid = 0, mv_grid64 = 0, mv_griddf = 0;
+    int mv_tpt = 1, mv_chunk = 0, mv_tgroup = 0, mv_grid = 0, mv_grid64 = 0, mv_griddf = 0;
     long long mv_part_total = 0;
     bool mv_tuned = false;
 

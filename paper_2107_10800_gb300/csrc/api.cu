@@ -158,7 +158,7 @@ void free_solver(am_handle* h) {
     dfree(&h->d_coefs); dfree(&h->d_xis); dfree(&h->d_hcols); dfree(&h->d_bnorm_s); dfree(&h->d_beta_s);
     dfree(&h->d_inv_s); dfree(&h->d_tol_s); dfree(&h->d_sysred); dfree(&h->d_active); dfree(&h->d_kdone);
     dfree(&h->d_sys_blob0); dfree(&h->d_sys_nb); dfree(&h->d_sys_nch); dfree(&h->d_sys_poff);
-    dfree(&h->d_item_counter);
+    dfree(&h->d_item_counter); dfree(&h->d_arn_cnt);
     if (h->d_items) cudaFree(h->d_items);
     h->d_items = nullptr;
     h->n_items = 0;
@@ -666,6 +666,15 @@ int build_system_maps(am_handle* h) {
     std::vector<int> sys_of_elem(n), sys_of_blob(h->Nb);
     std::vector<int> cs, ce, coff(S + 1, 0);
     const int nl = 3 * h->Nb, nu = 6 * h->M;
+    // Chunk length: about n / (4 x SMs), rounded up to a power of two in
+    // 64 .. 1024, so that the FP64 dot products and orthogonalisation of a
+    // small system still spread over all SMs (GB300 has 2 FP64 FMAs per SM
+    // per cycle); the chunk kernels run 256 threads a block.
+    const long long per = ((long long)n + 4LL * am::num_sms() - 1) / (4LL * am::num_sms());
+    int clen = 64;
+    while (clen < per && clen < 1024) clen *= 2;
+    h->chunk_len = clen;
+    h->chunk_threads = 256;
     for (int sI = 0; sI < S; ++sI) {
         const am_sys_rec& r = h->sys[sI];
         const int segs[3][2] = {{3 * h->sys_blob0[sI], 3 * (h->sys_blob0[sI] + r.Nb)},
@@ -673,9 +682,9 @@ int build_system_maps(am_handle* h) {
                                 {nl + nu + 3 * h->sys_link0[sI], nl + nu + 3 * (h->sys_link0[sI] + r.P)}};
         for (auto& sg : segs) {
             for (int i = sg[0]; i < sg[1]; ++i) sys_of_elem[i] = sI;
-            for (int c0 = sg[0]; c0 < sg[1]; c0 += 1024) {
+            for (int c0 = sg[0]; c0 < sg[1]; c0 += clen) {
                 cs.push_back(c0);
-                ce.push_back(std::min(sg[1], c0 + 1024));
+                ce.push_back(std::min(sg[1], c0 + clen));
             }
         }
         for (int i = 0; i < r.Nb; ++i) sys_of_blob[h->sys_blob0[sI] + i] = sI;
@@ -693,6 +702,8 @@ int build_system_maps(am_handle* h) {
     CK(dalloc(&h->d_bnorm_s, S)); CK(dalloc(&h->d_beta_s, S)); CK(dalloc(&h->d_inv_s, S));
     CK(dalloc(&h->d_tol_s, S)); CK(dalloc(&h->d_sysred, 4 * (size_t)S + 16));
     CK(dalloc(&h->d_active, S)); CK(dalloc(&h->d_kdone, S));
+    CK(dalloc(&h->d_arn_cnt, S + 1));
+    CK(cudaMemsetAsync(h->d_arn_cnt, 0, (S + 1) * sizeof(int), st));
     CK(dalloc(&h->d_part, (size_t)(m + 1) * std::max(1, h->nchunks)));
     CK(dalloc(&h->d_npart, std::max(h->nchunks, 4 * am::num_sms() + 64)));
     std::vector<int> b0(S), nb(S), bo(S + 1, h->M);
@@ -701,7 +712,8 @@ int build_system_maps(am_handle* h) {
     CK(h2d(h->d_sys_body_off, bo.data(), S + 1, st));
     CK(dalloc(&h->d_sys_blob0, S)); CK(dalloc(&h->d_sys_nb, S));
     CK(dalloc(&h->d_sys_nch, S)); CK(dalloc(&h->d_sys_poff, S));
-    CK(dalloc(&h->d_item_counter, 1));
+    CK(dalloc(&h->d_item_counter, 2));  // work queue: next item, blocks finished (both start at 0)
+    CK(cudaMemsetAsync(h->d_item_counter, 0, 2 * sizeof(int), st));
     CK(h2d(h->d_sys_of_elem, sys_of_elem.data(), n, st));
     CK(h2d(h->d_sys_of_blob, sys_of_blob.data(), h->Nb, st));
     CK(h2d(h->d_chunk_start, cs.data(), cs.size(), st));

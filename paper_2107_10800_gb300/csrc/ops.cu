@@ -508,13 +508,6 @@ __global__ void k_ctrl_init(ArnoldiCtrl* c, int budget, int m, double tol_abs) {
     c->j = 0; c->it = 0; c->budget = budget; c->m = m; c->stop = 0; c->tol_abs = tol_abs;
 }
 
-// Z[j] = in (flexible GMRES keeps the preconditioned vectors)
-__global__ void k_store_col(const double* __restrict__ in, double* __restrict__ Z, size_t ldv, int n,
-                            const ArnoldiCtrl* __restrict__ c) {
-    double* z = Z + (size_t)c->j * ldv;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) z[i] = in[i];
-}
-
 // ---- per-system (batched) GMRES kernels ----------------------------------
 // Unknowns of system s occupy three segments of the global vector (its
 // blobs' lambda, its bodies' U, its links' phi); the dot-product chunks never
@@ -638,65 +631,17 @@ __global__ void k_mask_sys(double* __restrict__ v, int n, const int* __restrict_
         if (!active[sys_of[i]]) v[i] = 0.0;
 }
 
-// part[k * nchunks + c] = <V_k, w> over chunk c for k = 8 blockIdx.y + warp <= j
-__global__ void __launch_bounds__(256)
-k_chunk_dots(const double* __restrict__ V, size_t ldv, const double* __restrict__ w,
-             const int* __restrict__ cs, const int* __restrict__ ce, double* __restrict__ part,
-             int nchunks, const ArnoldiCtrl* __restrict__ c) {
-    const int j = c->j;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int k = blockIdx.y * 8 + wid;
-    if (k > j) return;
-    const int cb = blockIdx.x;
-    const double* v = V + (size_t)k * ldv;
-    double s = 0.0;
-    for (int i = cs[cb] + lane; i < ce[cb]; i += 32) s = fma(v[i], w[i], s);
-    s = warp_sum(s);
-    if (lane == 0) part[(size_t)k * nchunks + cb] = s;
-}
-
-// coef[s][k] = sum over the system's chunks; hcol[s][k] = (hcol +) coef
-__global__ void k_sys_coef(const double* __restrict__ part, int nchunks, const int* __restrict__ coff,
-                           int m1, double* __restrict__ coef, double* __restrict__ hcol, int accumulate,
-                           const ArnoldiCtrl* __restrict__ c) {
-    const int s = blockIdx.x;
-    const int jp1 = c->j + 1;
-    for (int k = threadIdx.x; k < jp1; k += blockDim.x) {
-        double a = 0.0;
-        for (int q = coff[s]; q < coff[s + 1]; ++q) a += part[(size_t)k * nchunks + q];
-        coef[(size_t)s * m1 + k] = a;
-        double* hc = hcol + (size_t)s * m1 + k;
-        *hc = accumulate ? *hc + a : a;
-    }
-}
-
-// w_i -= sum_{k <= j} coef[system of i][k] V_k,i
-__global__ void __launch_bounds__(256)
-k_orth_sys(const double* __restrict__ V, size_t ldv, double* __restrict__ w, int n,
-           const int* __restrict__ sys_of, const double* __restrict__ coef, int m1,
-           const ArnoldiCtrl* __restrict__ c) {
-    const int jp1 = c->j + 1;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double* cf = coef + (size_t)sys_of[i] * m1;
-        double v = w[i];
-        for (int k = 0; k < jp1; ++k) v = fma(-cf[k], V[(size_t)k * ldv + i], v);
-        w[i] = v;
-    }
-}
-
-// Per active system: H column j, Givens rotations, the residual estimate; a
-// system stops (kdone = j + 1) when the estimate reaches its threshold or
-// the step breaks down.  inv[s] = 1/|w_s| (0 if stopped).
-__device__ __forceinline__ void finish_one(int s, int j, int m, const double* __restrict__ hcol,
-                                           const double* __restrict__ npart, const int* __restrict__ coff,
+// Per active system, with a = |w_s|^2: H column j, Givens rotations, the
+// residual estimate; a system stops (kdone = j + 1) when the estimate
+// reaches its threshold or the step breaks down.  inv[s] = 1/|w_s| (0 if
+// stopped).
+__device__ __forceinline__ void finish_one(int s, int j, int m, const double* __restrict__ hcol, double a,
                                            double* __restrict__ H, double* __restrict__ cs,
                                            double* __restrict__ sn, double* __restrict__ g,
                                            int* __restrict__ active, int* __restrict__ kdone,
                                            const double* __restrict__ tol_s, double* __restrict__ inv) {
     if (!active[s]) { inv[s] = 0.0; return; }
     const int m1 = m + 1;
-    double a = 0.0;
-    for (int q = coff[s]; q < coff[s + 1]; ++q) a += npart[q];
     const double nrm = sqrt(a);
     double* h = H + ((size_t)s * m + j) * m1;
     const double* hc = hcol + (size_t)s * m1;
@@ -726,18 +671,6 @@ __device__ __forceinline__ void finish_one(int s, int j, int m, const double* __
     if (stop) { active[s] = 0; kdone[s] = j + 1; }
 }
 
-// One thread per system.
-__global__ void k_arnoldi_finish_sys(const ArnoldiCtrl* __restrict__ c, const double* __restrict__ hcol,
-                                     const double* __restrict__ npart, const int* __restrict__ coff, int S,
-                                     int m, double* __restrict__ H, double* __restrict__ cs,
-                                     double* __restrict__ sn, double* __restrict__ g, int* __restrict__ active,
-                                     int* __restrict__ kdone, const double* __restrict__ tol_s,
-                                     double* __restrict__ inv) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    finish_one(s, c->j, m, hcol, npart, coff, H, cs, sn, g, active, kdone, tol_s, inv);
-}
-
 // Advance j; the cycle ends when no system is active, at the restart length
 // or at the step budget (still-active systems then close at j + 1).  Every
 // thread of the one block calls it.
@@ -747,7 +680,7 @@ __device__ void loop_ctrl(ArnoldiCtrl* c, int* __restrict__ active, int* __restr
     __shared__ int s_stop;
     const int j1 = c->j + 1;
     int cnt = 0;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) cnt += active[s];
+    for (int s = threadIdx.x; s < S; s += blockDim.x) cnt += __ldcg(active + s);  // set by other blocks
     scnt[threadIdx.x] = cnt;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -758,7 +691,7 @@ __device__ void loop_ctrl(ArnoldiCtrl* c, int* __restrict__ active, int* __restr
     __syncthreads();
     if (s_stop)
         for (int s = threadIdx.x; s < S; s += blockDim.x)
-            if (active[s]) { kdone[s] = j1; active[s] = 0; }
+            if (__ldcg(active + s)) { kdone[s] = j1; active[s] = 0; }
     __syncthreads();
     if (threadIdx.x == 0) {
         c->it += 1;
@@ -768,19 +701,148 @@ __device__ void loop_ctrl(ArnoldiCtrl* c, int* __restrict__ active, int* __restr
     }
 }
 
-// The systems' step ends and the loop control in one block of 256 threads
-// (S <= 256): every system's finish_one, then loop_ctrl.
-__global__ void __launch_bounds__(256)
-k_arnoldi_finish_ctrl(ArnoldiCtrl* c, const double* __restrict__ hcol, const double* __restrict__ npart,
-                      const int* __restrict__ coff, int S, int m, double* __restrict__ H,
-                      double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
-                      int* __restrict__ active, int* __restrict__ kdone, const double* __restrict__ tol_s,
-                      double* __restrict__ inv, cudaGraphConditionalHandle hc, int in_graph) {
-    const int j = c->j;
-    for (int s = threadIdx.x; s < S; s += blockDim.x)
-        finish_one(s, j, m, hcol, npart, coff, H, cs, sn, g, active, kdone, tol_s, inv);
+// ---- one Arnoldi step after w = A z: CGS2, norm, Givens, loop control --
+// Three kernels of one block per dot-product chunk (chunks never straddle
+// systems).  After a block has written its chunk's partial sums it counts
+// itself in cnt[s] (s its system); the block that completes the count (the
+// system's last) sums the system's partials in chunk order, and in the last
+// kernel the last system's last block (count cnt[S]) also runs the loop
+// control.  The completing block zeroes its count for the next use.  The
+// arithmetic and its order are those of separate dot, coefficient,
+// orthogonalisation, norm and step-end kernels.
+
+// true in every thread of the block that completes cnt[idx] = total
+__device__ bool arrive_last(int* cnt, int idx, int total) {
+    __shared__ int s_last;
     __syncthreads();
-    loop_ctrl(c, active, kdone, S, hc, in_graph);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int t = atomicAdd(&cnt[idx], 1);
+        s_last = (t == total - 1) ? 1 : 0;
+        if (s_last) cnt[idx] = 0;
+    }
+    __syncthreads();
+    const bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// part[k * nchunks + b] = <V_k, w> over chunk [c0, c1), k <= j (a warp per k)
+__device__ __forceinline__ void chunk_dots(const double* __restrict__ V, size_t ldv, const double* w, int c0,
+                                           int c1, int j, double* __restrict__ part, int nchunks, int b) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = wid; k <= j; k += nw) {
+        const double* v = V + (size_t)k * ldv;
+        double a = 0.0;
+        for (int i = c0 + lane; i < c1; i += 32) a = fma(v[i], w[i], a);
+        a = warp_sum(a);
+        if (lane == 0) part[(size_t)k * nchunks + b] = a;
+    }
+}
+
+// coef[s][k] = sum over the system's chunks (a warp per k, its lanes over
+// the chunks); hcol[s][k] = (hcol +) coef
+__device__ __forceinline__ void sys_coef(int s, const double* part, int nchunks, const int* __restrict__ coff,
+                                         int m1, int j, double* __restrict__ coef, double* __restrict__ hcol,
+                                         int accumulate) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int q0 = coff[s], q1 = coff[s + 1];
+    for (int k = wid; k <= j; k += nw) {
+        const double* pk = part + (size_t)k * nchunks;
+        double a = 0.0;
+        for (int q = q0 + lane; q < q1; q += 32) a += __ldcg(pk + q);  // other blocks' sums
+        a = warp_sum(a);
+        if (lane == 0) {
+            coef[(size_t)s * m1 + k] = a;
+            double* hc = hcol + (size_t)s * m1 + k;
+            *hc = accumulate ? *hc + a : a;
+        }
+    }
+}
+
+// w_i -= sum_{k <= j} coef[s][k] V_k,i over the chunk; returns the thread's
+// share of |w|^2 over the chunk (after the update).  When the chunk is
+// shorter than the block, the block's G = blockDim / len groups of len
+// threads each sum every G-th term of an element's sum (shorter dependent
+// FP64 chains), combined in shared memory (sh: blockDim doubles).
+__device__ __forceinline__ double chunk_orth(const double* __restrict__ V, size_t ldv, double* w, int c0,
+                                             int c1, int j, const double* cf, int len, double* sh) {
+    const int per = min((int)blockDim.x, len);  // threads per group
+    const int G = blockDim.x / per;
+    const int e = threadIdx.x % per, g = threadIdx.x / per;
+    double a = 0.0;
+    for (int i0 = c0; i0 < c1; i0 += per) {
+        const int i = i0 + e;
+        double p = 0.0;
+        if (i < c1)
+            for (int k = g; k <= j; k += G) p = fma(cf[k], V[(size_t)k * ldv + i], p);
+        if (G > 1) {
+            __syncthreads();
+            sh[threadIdx.x] = p;
+            __syncthreads();
+            if (g == 0)
+                for (int q = 1; q < G; ++q) p += sh[q * per + e];
+        }
+        if (g == 0 && i < c1) {
+            const double v = w[i] - p;
+            w[i] = v;
+            a = fma(v, v, a);
+        }
+    }
+    return a;
+}
+
+// Z[j] = z (flexible GMRES keeps the preconditioned vectors); first CGS
+// pass: dots and coefficients
+__global__ void __launch_bounds__(256)
+k_arn_dots(const double* __restrict__ V, size_t ldv, const double* __restrict__ w,
+           const double* __restrict__ z, double* __restrict__ Z, const int* __restrict__ cs,
+           const int* __restrict__ ce, const int* __restrict__ sys_of, const int* __restrict__ coff,
+           double* __restrict__ part, int nchunks, int m1, double* __restrict__ coef, double* __restrict__ hcol,
+           int* __restrict__ cnt, const ArnoldiCtrl* __restrict__ c) {
+    const int j = c->j, b = blockIdx.x, c0 = cs[b], c1 = ce[b], s = sys_of[c0];
+    double* zc = Z + (size_t)j * ldv;
+    for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) zc[i] = z[i];
+    chunk_dots(V, ldv, w, c0, c1, j, part, nchunks, b);
+    if (arrive_last(cnt, s, coff[s + 1] - coff[s])) sys_coef(s, part, nchunks, coff, m1, j, coef, hcol, 0);
+}
+
+// first CGS pass: orthogonalisation; second pass: dots and coefficients
+__global__ void __launch_bounds__(256)
+k_arn_orth_dots(const double* __restrict__ V, size_t ldv, double* __restrict__ w, const int* __restrict__ cs,
+                const int* __restrict__ ce, const int* __restrict__ sys_of, const int* __restrict__ coff, int clen,
+                double* __restrict__ part, int nchunks, int m1, double* __restrict__ coef,
+                double* __restrict__ hcol, int* __restrict__ cnt, const ArnoldiCtrl* __restrict__ c) {
+    __shared__ double sh[256];
+    const int j = c->j, b = blockIdx.x, c0 = cs[b], c1 = ce[b], s = sys_of[c0];
+    chunk_orth(V, ldv, w, c0, c1, j, coef + (size_t)s * m1, clen, sh);
+    __syncthreads();  // the chunk of w is updated before its dots
+    chunk_dots(V, ldv, w, c0, c1, j, part, nchunks, b);
+    if (arrive_last(cnt, s, coff[s + 1] - coff[s])) sys_coef(s, part, nchunks, coff, m1, j, coef, hcol, 1);
+}
+
+// second pass: orthogonalisation and |w|^2; per system the step end
+// (finish_one), then the loop control
+__global__ void __launch_bounds__(256)
+k_arn_orth_finish(const double* __restrict__ V, size_t ldv, double* __restrict__ w, const int* __restrict__ cs,
+                  const int* __restrict__ ce, const int* __restrict__ sys_of, const int* __restrict__ coff, int clen,
+                  double* __restrict__ npart, int m1, const double* __restrict__ coef,
+                  const double* __restrict__ hcol, int* __restrict__ cnt, int S, int m, double* __restrict__ H,
+                  double* __restrict__ csv, double* __restrict__ snv, double* __restrict__ g,
+                  int* __restrict__ active, int* __restrict__ kdone, const double* __restrict__ tol_s,
+                  double* __restrict__ inv, ArnoldiCtrl* c, cudaGraphConditionalHandle hc, int in_graph) {
+    __shared__ double sh[256];
+    const int j = c->j, b = blockIdx.x, c0 = cs[b], c1 = ce[b], s = sys_of[c0];
+    double a = chunk_orth(V, ldv, w, c0, c1, j, coef + (size_t)s * m1, clen, sh);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) npart[b] = a;
+    if (arrive_last(cnt, s, coff[s + 1] - coff[s])) {
+        double w2 = 0.0;
+        for (int q = coff[s] + threadIdx.x; q < coff[s + 1]; q += blockDim.x) w2 += __ldcg(npart + q);
+        w2 = block_sum(w2, sh);
+        if (threadIdx.x == 0) finish_one(s, j, m, hcol, w2, H, csv, snv, g, active, kdone, tol_s, inv);
+        if (arrive_last(cnt, S, S)) loop_ctrl(c, active, kdone, S, hc, in_graph);
+    }
 }
 
 // V[j+1] = w * inv[system], also into vj (the next step's vector to
@@ -795,12 +857,6 @@ __global__ void k_next_basis(const double* __restrict__ w, double* __restrict__ 
         v[i] = t;
         vj[i] = t;
     }
-}
-
-__global__ void __launch_bounds__(256)
-k_loop_ctrl_sys(ArnoldiCtrl* c, int* __restrict__ active, int* __restrict__ kdone, int S,
-                cudaGraphConditionalHandle hc, int in_graph) {
-    loop_ctrl(c, active, kdone, S, hc, in_graph);
 }
 
 // xi_s = H_s(0:k, 0:k)^-1 g_s(0:k), k = kdone[s]  (one thread per system)
@@ -883,9 +939,9 @@ static void timing_mark(am_handle* h) {
     cudaEventRecord(h->tev[h->tev_used++], h->stream);
 }
 
-static void mobility_partial(am_handle* h, const double* lam, int mode) {
+static void mobility_partial(am_handle* h, const double* lam, int mode, const int* active = nullptr) {
     timing_mark(h);
-    launch_items(h, lam, mode);
+    launch_items(h, lam, mode, active);
     timing_mark(h);
     long long pairs = 0;
     for (const auto& r : h->sys) pairs += (long long)r.Nb * r.Nb;
@@ -897,12 +953,12 @@ void mobility_apply(am_handle* h, const double* lam, double* u, int mode) {
     launch_sum_items(h, u);
 }
 
-void op_apply(am_handle* h, const double* y, double* out, int mode) {
+void op_apply(am_handle* h, const double* y, double* out, int mode, const int* active) {
     if (h->sb) {
         sb_op_apply(h, y, out);
         return;
     }
-    mobility_partial(h, y, mode);
+    mobility_partial(h, y, mode, active);
     const int nbb = nblk(h->Nb, 128), nbody = nblk(h->M, 4), nlink = nblk(h->P, 128);
     k_op_epilogue<<<nbb + nbody + nlink, 128, 0, h->stream>>>(
         h->Nb, h->M, h->P, nbb, nbody, h->d_mv, h->d_sys_of_blob, h->d_sys_blob0, h->d_sys_nb,
@@ -1028,39 +1084,24 @@ static void issue_arnoldi_step(am_handle* h, bool fp64, cudaGraphConditionalHand
     cudaStream_t s = h->stream;
     const int n = h->n, m = h->restart, m1 = m + 1, S = h->S;
     const size_t ldv = (size_t)h->ldv;
-    const int nb = red_blocks(n);
-    const dim3 dgrid(h->nchunks, (m1 + 7) / 8);
+    const int nb = red_blocks(n), nch = h->nchunks, ct = h->chunk_threads;
     pc_apply(h, h->d_vj, h->d_zj);  // vj = V[j], written with V[j]
-    k_store_col<<<nb, 256, 0, s>>>(h->d_zj, h->d_Z, ldv, n, h->d_ctrl);
-    count_launch();
-    op_apply(h, h->d_zj, h->d_w, fp64);
-    for (int pass = 0; pass < 2; ++pass) {
-        k_chunk_dots<<<dgrid, 256, 0, s>>>(h->d_V, ldv, h->d_w, h->d_chunk_start, h->d_chunk_end, h->d_part,
-                                           h->nchunks, h->d_ctrl);
-        k_sys_coef<<<S, 64, 0, s>>>(h->d_part, h->nchunks, h->d_sys_chunk_off, m1, h->d_coefs, h->d_hcols,
-                                     pass, h->d_ctrl);
-        k_orth_sys<<<nb, 256, 0, s>>>(h->d_V, ldv, h->d_w, n, h->d_sys_of_elem, h->d_coefs, m1, h->d_ctrl);
-        count_launch(3);
-    }
-    k_chunk_sq<<<h->nchunks, 256, 0, s>>>(h->d_w, h->d_chunk_start, h->d_chunk_end, h->d_npart);
-    count_launch();
-    if (S <= 256) {
-        // finish and loop control in one block; j has advanced for next_basis
-        k_arnoldi_finish_ctrl<<<1, 256, 0, s>>>(h->d_ctrl, h->d_hcols, h->d_npart, h->d_sys_chunk_off, S, m,
-                                                 h->d_Hs, h->d_css, h->d_sns, h->d_gs, h->d_active, h->d_kdone,
-                                                 h->d_tol_s, h->d_inv_s, hc, in_graph ? 1 : 0);
-        k_next_basis<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s, h->d_ctrl,
-                                         h->d_vj, 1);
-        count_launch(2);
-    } else {
-        k_arnoldi_finish_sys<<<nblk(S, 128), 128, 0, s>>>(h->d_ctrl, h->d_hcols, h->d_npart, h->d_sys_chunk_off,
-                                                           S, m, h->d_Hs, h->d_css, h->d_sns, h->d_gs,
-                                                           h->d_active, h->d_kdone, h->d_tol_s, h->d_inv_s);
-        k_next_basis<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s, h->d_ctrl,
-                                         h->d_vj, 0);
-        k_loop_ctrl_sys<<<1, 256, 0, s>>>(h->d_ctrl, h->d_active, h->d_kdone, S, hc, in_graph ? 1 : 0);
-        count_launch(3);
-    }
+    // the input of a stopped system is zero: its product skips the pairs
+    op_apply(h, h->d_zj, h->d_w, fp64, S > 1 ? h->d_active : nullptr);
+    k_arn_dots<<<nch, ct, 0, s>>>(h->d_V, ldv, h->d_w, h->d_zj, h->d_Z, h->d_chunk_start, h->d_chunk_end,
+                                   h->d_sys_of_elem, h->d_sys_chunk_off, h->d_part, nch, m1, h->d_coefs,
+                                   h->d_hcols, h->d_arn_cnt, h->d_ctrl);
+    k_arn_orth_dots<<<nch, ct, 0, s>>>(h->d_V, ldv, h->d_w, h->d_chunk_start, h->d_chunk_end, h->d_sys_of_elem,
+                                        h->d_sys_chunk_off, h->chunk_len, h->d_part, nch, m1, h->d_coefs, h->d_hcols,
+                                        h->d_arn_cnt, h->d_ctrl);
+    k_arn_orth_finish<<<nch, ct, 0, s>>>(h->d_V, ldv, h->d_w, h->d_chunk_start, h->d_chunk_end,
+                                          h->d_sys_of_elem, h->d_sys_chunk_off, h->chunk_len, h->d_npart, m1, h->d_coefs,
+                                          h->d_hcols, h->d_arn_cnt, S, m, h->d_Hs, h->d_css, h->d_sns, h->d_gs,
+                                          h->d_active, h->d_kdone, h->d_tol_s, h->d_inv_s, h->d_ctrl, hc,
+                                          in_graph ? 1 : 0);
+    // j has advanced: V[j] = w / |w_s| and the next step's input
+    k_next_basis<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s, h->d_ctrl, h->d_vj, 1);
+    count_launch(4);
 }
 
 // The graph of one Arnoldi cycle: a WHILE node whose body is one step,
@@ -1133,6 +1174,7 @@ static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp
     const size_t ldv = (size_t)h->ldv;
     const int nb = red_blocks(n);
     sys_norms(h, rhs, h->d_bnorm_s);
+    cudaMemsetAsync(h->d_arn_cnt, 0, (S + 1) * sizeof(int), s);  // arrival counts of the step kernels
     const bool use_graph = !h->timing && h->graphs_ok && ensure_graph(h, fp64);
     const int gi = fp64 ? 1 : 0;
     int it = 0;

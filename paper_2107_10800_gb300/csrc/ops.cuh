@@ -16,7 +16,9 @@ constexpr int kOpHandle = 0, kOpFP64 = 1, kOpDF = 2, kOpMixed = 3;
 // Geometry of the current pose: blob positions, lab link vectors, B, b.
 void launch_geometry(am_handle* h);
 // out = A y (Eq. linear_system) with the mobility product of `mode`.
-void op_apply(am_handle* h, const double* y, double* out, int mode);
+// active: per-system flags (device); systems with flag 0 get a zero
+// mobility product without its pair arithmetic (nullptr: all systems)
+void op_apply(am_handle* h, const double* y, double* out, int mode, const int* active = nullptr);
 // Blob mobility product only: u = M lambda (3Nb).
 void mobility_apply(am_handle* h, const double* lam, double* u, int mode);
 // Block-diagonal preconditioner (Sec. 3.1): build at the current pose, apply.
@@ -36,8 +38,8 @@ int advance(am_handle* h, double dt, am_step_stats* st);
 // Block-diagonal mobility product of all systems (rpy.cu): work items for
 // tpt targets per thread and source chunks (0 = automatic), their launch,
 // the sum of the partials, and the autotuner that picks (tpt, chunk).
-int mobility_layout(am_handle* h, int tpt, int chunk);
-void launch_items(am_handle* h, const double* lam, int mode);
+int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup = 0);
+void launch_items(am_handle* h, const double* lam, int mode, const int* active = nullptr);
 int df_resident_grid(bool wall);
 void launch_items_df(am_handle* h, const double* lam);
 void launch_sum_items(am_handle* h, double* u);

@@ -421,11 +421,23 @@ extern "C" AM_API long long am_kernel_launches(void) { return am::g_launches.loa
 // blob i go to part[poff_s + c * 3 N_s + 3 (i - blob0_s)].
 namespace am {
 
+// An item of a stopped system (active[sys] == 0; the system's input is
+// zero) writes zero partial sums instead of evaluating its pairs.
+__device__ __forceinline__ bool item_skipped(const MvItem& m, const int* __restrict__ active,
+                                             double* __restrict__ part) {
+    if (!active || active[m.sys]) return false;
+    for (int i = m.t0 + threadIdx.x; i < m.t1; i += blockDim.x) {
+        double* o = part + m.pbase + 3 * (size_t)(i - m.tbase);
+        o[0] = 0.0; o[1] = 0.0; o[2] = 0.0;
+    }
+    return true;
+}
+
 template <bool WALL>
 __global__ void __launch_bounds__(kThreads)
 rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam,
               double* __restrict__ part, const MvItem* __restrict__ items, int n_items,
-              int* __restrict__ counter, RpyK<double> k) {
+              int* __restrict__ counter, RpyK<double> k, const int* __restrict__ active) {
     __shared__ double4_32a sr[kTile];
     __shared__ double sl[3 * kTile];
     __shared__ int s_item;
@@ -438,11 +450,15 @@ rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam
         const int itn = s_item;
         if (itn >= n_items) break;
         const MvItem m = items[itn];
+        if (item_skipped(m, active, part)) continue;
         // items built for two targets per thread span 2 x 128 targets
         for (int tb = m.t0; tb < m.t1; tb += kThreads) {
         const int i = tb + threadIdx.x;
         double4_32a ri = (i < m.t1) ? r4[i] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
         const double nx3 = -ri.z;
+        // warps with no target of the item (items of fewer targets than
+        // the block) only help stage the sources
+        const bool warp_live = tb + (int)(threadIdx.x & ~31u) < m.t1;
         double ux = 0.0, uy = 0.0, uz = 0.0;
         for (int jt = m.j0; jt < m.j1; jt += kTile) {
             const int cnt = min(kTile, m.j1 - jt);
@@ -454,6 +470,7 @@ rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam
             }
             for (int q = threadIdx.x; q < 3 * cnt; q += kThreads) sl[q] = lam[3 * (size_t)jt + q];
             __syncthreads();
+            if (!warp_live) continue;
 #pragma unroll 2
             for (int q = 0; q < cnt; ++q) {
                 const double4_32a rj = sr[q];
@@ -474,6 +491,7 @@ rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam
         }
         }
     }
+    item_queue_done(counter);
 }
 
 template <bool WALL, int TPT>
@@ -481,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
                 const double* __restrict__ lam, double* __restrict__ part,
                 const MvItem* __restrict__ items, int n_items, int* __restrict__ counter,
-                RpyK<float> k) {
+                RpyK<float> k, const int* __restrict__ active) {
     __shared__ float4 sh[kTile];
     __shared__ float4 so[kTile];
     __shared__ float4 sl[kTile];
@@ -495,6 +513,7 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
         const int itn = s_item;
         if (itn >= n_items) break;
         const MvItem m = items[itn];
+        if (item_skipped(m, active, part)) continue;
         float4 hi_i[TPT], lo_i[TPT];
         float near2[TPT];
         double U[TPT][3];
@@ -507,6 +526,8 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
             near2[t] = nr * nr;
             U[t][0] = U[t][1] = U[t][2] = 0.0;
         }
+        // warps with no target of the item only help stage the sources
+        const bool warp_live = m.t0 + (int)(threadIdx.x & ~31u) < m.t1;
         for (int jt = m.j0; jt < m.j1; jt += kTile) {
             const int cnt = min(kTile, m.j1 - jt);
             __syncthreads();
@@ -519,6 +540,7 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
                                               (float)lam[3 * (size_t)j + 2], 0.f);
             }
             __syncthreads();
+            if (!warp_live) continue;
             float u[TPT][3];
 #pragma unroll
             for (int t = 0; t < TPT; ++t) u[t][0] = u[t][1] = u[t][2] = 0.f;
@@ -562,6 +584,7 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
             }
         }
     }
+    item_queue_done(counter);
 }
 
 // ---- paired FP32 arithmetic: two targets per thread in the lanes of float2
@@ -639,7 +662,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
                    const double* __restrict__ lam, double* __restrict__ part,
                    const MvItem* __restrict__ items, int n_items, int* __restrict__ counter,
-                   RpyK<float> k) {
+                   RpyK<float> k, const int* __restrict__ active) {
     __shared__ float4 sq[3][kTile];
     __shared__ float4 so[kTile];
     __shared__ float2 soz[kTile];
@@ -651,6 +674,7 @@ rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
         const int itn = s_item;
         if (itn >= n_items) break;
         const MvItem m = items[itn];
+        if (item_skipped(m, active, part)) continue;
         const int i0 = m.t0 + threadIdx.x, i1 = m.t0 + kThreads + threadIdx.x;
         const float4 h0 = (i0 < m.t1) ? hi[i0] : make_float4(0.f, 0.f, 1.f, 0.f);
         const float4 h1 = (i1 < m.t1) ? hi[i1] : make_float4(0.f, 0.f, 1.f, 0.f);
@@ -712,6 +736,7 @@ rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
             o[0] = k.A1 * U[1][0]; o[1] = k.A1 * U[1][1]; o[2] = k.A1 * U[1][2];
         }
     }
+    item_queue_done(counter);
 }
 
 // u_i = sum over the chunks of i's system of the partial sums
@@ -741,9 +766,12 @@ static int resident_grid(F kernel) {
 
 // Work items for tpt targets per thread and source chunks of `chunk` blobs
 // (0: choose so that the items fill the GPU).  Returns 0 on success.
-int mobility_layout(am_handle* h, int tpt, int chunk) {
+int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup) {
     const int S = h->S;
     if (h->cfg.precision != AM_MIXED) tpt = 1;
+    // targets per item: a block's targets, or (one target per thread) 32 or
+    // 64 of them so that small systems spread over more SMs
+    if (tpt == 2 || tgroup <= 0 || tgroup > kThreads || tgroup % 32) tgroup = kThreads * tpt;
     if (chunk <= 0) {
         // about 8 resident waves of items over all systems
         long long pairs = 0;
@@ -762,11 +790,12 @@ int mobility_layout(am_handle* h, int tpt, int chunk) {
         poff[s] = off;
         for (int c = 0; c < nch[s]; ++c) {
             const int j0 = b0 + c * chunk, j1 = std::min(b0 + nb, j0 + chunk);
-            for (int t0 = b0; t0 < b0 + nb; t0 += kThreads * tpt) {
+            for (int t0 = b0; t0 < b0 + nb; t0 += tgroup) {
                 MvItem it;
-                it.t0 = t0; it.t1 = std::min(b0 + nb, t0 + kThreads * tpt);
+                it.t0 = t0; it.t1 = std::min(b0 + nb, t0 + tgroup);
                 it.j0 = j0; it.j1 = j1; it.tbase = b0; it.n3 = 3 * nb;
                 it.pbase = off + (long long)c * 3 * nb;
+                it.sys = s; it.pad = 0;
                 items.push_back(it);
             }
         }
@@ -794,6 +823,7 @@ int mobility_layout(am_handle* h, int tpt, int chunk) {
     const int n_it = std::max(1, h->n_items);
     h->mv_tpt = tpt;
     h->mv_chunk = chunk;
+    h->mv_tgroup = tgroup;
     h->mv_part_total = off;
     if (h->cfg.precision == AM_MIXED) {
         if (h->cfg.wall)
@@ -813,32 +843,31 @@ int mobility_layout(am_handle* h, int tpt, int chunk) {
 }
 
 // The partial sums of u = M lambda for all systems (mode: the handle's
-// precision, FP64 or double-float); the queue counter is reset first.
-void launch_items(am_handle* h, const double* lam, int mode) {
+// precision, FP64 or double-float).
+void launch_items(am_handle* h, const double* lam, int mode, const int* active) {
     if (mode == kOpDF) {
         launch_items_df(h, lam);
         return;
     }
     const bool fp64 = mode == kOpFP64 || (mode == kOpHandle && h->cfg.precision == AM_FP64);
-    cudaStream_t st = h->stream;
-    cudaMemsetAsync(h->d_item_counter, 0, sizeof(int), st);
+    cudaStream_t st = h->stream;  // the queue counter is zero (reset by the last launch's last block)
     const MvItem* items = static_cast<const MvItem*>(h->d_items);
     if (fp64) {
         const RpyK<double> k = rpy_consts<double>(h->prm);
         if (h->cfg.wall)
             rpy_items_f64<true><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,
-                                                                  h->d_item_counter, k);
+                                                                  h->d_item_counter, k, active);
         else
             rpy_items_f64<false><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,
-                                                                   h->d_item_counter, k);
+                                                                   h->d_item_counter, k, active);
     } else {
         const RpyK<float> k = rpy_consts<float>(h->prm);
 #define AM_MIXED_ITEMS(W, T)                                                                             \
     rpy_items_mixed<W, T><<<h->mv_grid, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items, \
-                                                           h->n_items, h->d_item_counter, k)
+                                                           h->n_items, h->d_item_counter, k, active)
 #define AM_MIXED_X2(W)                                                                               \
     rpy_items_mixed_x2<W><<<h->mv_grid, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items,  \
-                                                           h->n_items, h->d_item_counter, k)
+                                                           h->n_items, h->d_item_counter, k, active)
         if (h->cfg.wall) {
             if (h->mv_tpt == 2) AM_MIXED_X2(true); else AM_MIXED_ITEMS(true, 1);
         } else {
@@ -860,23 +889,32 @@ void launch_sum_items(am_handle* h, double* u) {
 // Autotuner: times the handle's product for candidate (targets per thread,
 // source chunk) pairs on the current positions and keeps the fastest.
 int mobility_autotune(am_handle* h) {
-    std::vector<std::pair<int, int>> cand;
+    struct Cand { int tpt, chunk, tgroup; };
+    std::vector<Cand> cand;
     const bool mixed = h->cfg.precision == AM_MIXED;
     long long maxnb = 0;
     for (const auto& r : h->sys) maxnb = std::max<long long>(maxnb, r.Nb);
     for (int tpt : (mixed ? std::vector<int>{1, 2} : std::vector<int>{1}))
         for (int chunk : {0, 512, 1024, 2048, 4096, 8192})
-            if (chunk == 0 || chunk <= 2 * maxnb) cand.push_back({tpt, chunk});
+            if (chunk == 0 || chunk <= 2 * maxnb) cand.push_back({tpt, chunk, 0});
     // One system of modest size: the items all start at once, so the
     // slowest SM sets the time; chunks that make the item count a multiple
-    // of the SM count (k = 1..6 items per SM) balance the last wave.
+    // of the SM count (k = 1..6 items per SM) balance the last wave.  Small
+    // systems also try items of 32 or 64 targets (one target per thread),
+    // which spread a few thousand blobs over all SMs: with 2 FP64 FMAs per
+    // SM per cycle one 128 x 128 item of FP64 pairs takes tens of us.
     if (h->S == 1 && maxnb * maxnb <= 4000000000LL) {
         for (int tpt : (mixed ? std::vector<int>{1, 2} : std::vector<int>{1})) {
-            const long long ntb = (maxnb + (long long)kThreads * tpt - 1) / ((long long)kThreads * tpt);
-            for (int k = 1; k <= 6; ++k) {
-                const long long c = ((long long)k * num_sms() + ntb - 1) / ntb;  // chunks per system
-                const long long chunk = (maxnb + c - 1) / c;
-                if (chunk >= 32) cand.push_back({tpt, (int)chunk});
+            for (int tg : {kThreads * tpt, 64, 32}) {
+                if (tpt == 2 && tg != kThreads * tpt) continue;
+                if (tg != kThreads * tpt && maxnb > 16384) continue;
+                const long long ntb = (maxnb + tg - 1) / tg;
+                for (int k = 1; k <= 6; ++k) {
+                    const long long c = ((long long)k * num_sms() + ntb - 1) / ntb;  // chunks per system
+                    const long long chunk = (maxnb + c - 1) / c;
+                    if (chunk >= 32) cand.push_back({tpt, (int)chunk, tg == kThreads * tpt ? 0 : tg});
+                }
+                if (tg != kThreads * tpt) cand.push_back({tpt, 32, tg});
             }
         }
     }
@@ -888,11 +926,11 @@ int mobility_autotune(am_handle* h) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    std::pair<int, int> pick = cand[0];
+    Cand pick = cand[0];
     const bool timing = h->timing;
     h->timing = false;
     for (auto c : cand) {
-        if (mobility_layout(h, c.first, c.second)) continue;
+        if (mobility_layout(h, c.tpt, c.chunk, c.tgroup)) continue;
         launch_items(h, lam, false);  // warm-up
         cudaEventRecord(e0, st);
         launch_items(h, lam, false);
@@ -909,7 +947,7 @@ int mobility_autotune(am_handle* h) {
     cudaFree(lam);
     cudaGetLastError();
     h->mv_tuned = true;
-    return mobility_layout(h, pick.first, pick.second);
+    return mobility_layout(h, pick.tpt, pick.chunk, pick.tgroup);
 }
 
 }  // namespace am

@@ -134,6 +134,8 @@ rpy_items_df(const float4* __restrict__ hi, const float4* __restrict__ lo, const
             const float4 xl = (i < m.t1) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
             const df xx{xh.x, xl.x}, xy{xh.y, xl.y}, xz{xh.z, xl.z};
             double U0 = 0.0, U1 = 0.0, U2 = 0.0;
+            // warps with no target of the item only help stage the sources
+            const bool warp_live = tb + (int)(threadIdx.x & ~31u) < m.t1;
             for (int jt = m.j0; jt < m.j1; jt += kTile) {
                 const int cnt = min(kTile, m.j1 - jt);
                 __syncthreads();
@@ -147,6 +149,7 @@ rpy_items_df(const float4* __restrict__ hi, const float4* __restrict__ lo, const
                     sll[threadIdx.x] = make_float4(a.l, b.l, c.l, 0.f);
                 }
                 __syncthreads();
+                if (!warp_live) continue;
                 df ux{0.f, 0.f}, uy{0.f, 0.f}, uz{0.f, 0.f};
                 for (int q = 0; q < cnt; ++q) {
                     const float4 yh = sh[q], yl = so[q], lh = slh[q], ll = sll[q];
@@ -169,6 +172,7 @@ rpy_items_df(const float4* __restrict__ hi, const float4* __restrict__ lo, const
             }
         }
     }
+    item_queue_done(counter);
 }
 
 }  // namespace
@@ -181,11 +185,10 @@ int df_resident_grid(bool wall) {
     return per * num_sms();
 }
 
-// Partial sums of u = M lambda for all systems with double-float pair terms
-// (the queue counter is reset first); positions from the hi/lo arrays.
+// Partial sums of u = M lambda for all systems with double-float pair terms;
+// positions from the hi/lo arrays.
 void launch_items_df(am_handle* h, const double* lam) {
-    cudaStream_t st = h->stream;
-    cudaMemsetAsync(h->d_item_counter, 0, sizeof(int), st);
+    cudaStream_t st = h->stream;  // the queue counter is zero (reset by the last launch's last block)
     const MvItem* items = static_cast<const MvItem*>(h->d_items);
     const RpyDf k = rpy_df_consts(h->prm);
     if (h->cfg.wall)

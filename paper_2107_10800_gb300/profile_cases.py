@@ -4,7 +4,7 @@ one kernel (-k, -c) ends quickly.  Nothing here is timed.
 
     python -m paper_2107_10800_gb300.profile_cases product --blobs 60000 [--arith mixed|fp64|df64]
     python -m paper_2107_10800_gb300.profile_cases colony --precision fp64|mixed [--steps 3] [--host-steps]
-    python -m paper_2107_10800_gb300.profile_cases batched [--steps 1]
+    python -m paper_2107_10800_gb300.profile_cases batched [--steps 1] [--host-steps]
 
 product: the all-pairs wall product u = M lambda on the first N blobs of the
 1,000-bacteria suspension above a wall (each blob its own body, so the
@@ -15,7 +15,7 @@ dt = 1e-3, relative residual 1e-8); with --host-steps the Arnoldi steps are
 launched from the host (per-launch timing of the product on) instead of
 from the CUDA-graph loop, whose kernels profilers do not capture.
 batched: steps of the 256 free-space chain suspensions in one handle
-(mixed precision).
+(mixed precision); --host-steps as for colony.
 """
 import argparse
 import os
@@ -60,8 +60,10 @@ def colony(precision, steps, host_steps=False):
     s.close()
 
 
-def batched(steps):
+def batched(steps, host_steps=False):
     s = binding.Solver.from_workloads(W.batched_chains(1), tol=1e-8, precision="mixed")
+    if host_steps:
+        s.mobility_timing(True)
     for k in range(steps):
         s.step(k * 1e-3, 1e-3)
     s.close()
@@ -83,7 +85,7 @@ def main():
     elif a.case == "colony":
         colony(a.precision, a.steps, a.host_steps)
     else:
-        batched(a.steps)
+        batched(a.steps, a.host_steps)
 
 
 if __name__ == "__main__":
