@@ -338,6 +338,7 @@ def learned_form(binding, W):
                 "rel_residual0": st["rel_residual0"], "rel_residual": st["rel_residual"],
                 "learned_systems": st["learned_systems"]}
 
+    out["held_out_100"] = learned_held_out(binding, learned, net)
     big = learned.bacteria_at_density(20100, 556)
     out["bacteria_556"] = {"blobs": int(big["blob_offset"][-1]),
                            "mixed_block_diagonal_start": run(big, "mixed", None),
@@ -348,6 +349,43 @@ def learned_form(binding, W):
                            "mixed": run(small, "mixed", None),
                            "mixed_learned_start": run(small, "mixed", net)}
     net.close()
+    return out
+
+
+def learned_held_out(binding, learned, net, seeds=range(20300, 20320), n_bact=100):
+    """Cold-start solves of held-out suspensions of 100 bacteria (36,000
+    blobs, mixed precision, relative residual 1e-8), one handle per seed and
+    start, with the product layout fixed (one target per thread, source
+    chunks chosen for the size) so both starts run the same kernels: GMRES
+    iterations, initial relative residual and host wall time of the solve,
+    per seed and as mean and standard deviation."""
+    res = {"plain": [], "learned": []}
+    for seed in seeds:
+        w = learned.bacteria_at_density(seed, n_bact)
+        for name, model in (("plain", None), ("learned", net)):
+            s = binding.Solver.from_workload(w, precision="mixed", tol=1e-8, max_iter=2000)
+            s.set_mobility_layout(1, 0)
+            if model is not None:
+                s.set_learned(model, check=True)
+            t0 = time.perf_counter()
+            _, _, _, st = s.solve()
+            ms = 1e3 * (time.perf_counter() - t0)
+            s.close()
+            res[name].append((st["iterations"], st["rel_residual0"], ms, st["rel_residual"]))
+
+    def stats(v):
+        a = np.array(v, dtype=float)
+        return {"mean": float(a.mean()), "std": float(a.std())}
+
+    out = {"workload": "%d held-out suspensions of %d bacteria above a wall (seeds %d-%d), mixed, "
+                       "cold start, relative residual 1e-8" % (len(seeds), n_bact, seeds[0], seeds[-1])}
+    for name in ("plain", "learned"):
+        r = res[name]
+        out[name] = {"iterations": stats([x[0] for x in r]), "rel_residual0": stats([x[1] for x in r]),
+                     "solve_ms": stats([x[2] for x in r]), "max_rel_residual": max(x[3] for x in r)}
+    d = [l[0] - p[0] for p, l in zip(res["plain"], res["learned"])]
+    out["iteration_change_per_seed"] = d
+    out["iteration_change"] = stats(d)
     return out
 
 

@@ -123,6 +123,15 @@ rpy_partial_f64(const double4_32a* __restrict__ r4, const double* __restrict__ l
     }
 }
 
+// hi + lo += t with Knuth's TwoSum (rounding error of hi + t kept in lo):
+// the compensated accumulation of the tile sums of the mixed kernels
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float t) {
+    const float s = __fadd_rn(hi, t);
+    const float v = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(t, v)));
+    hi = s;
+}
+
 // Positions as hi + lo float pairs (hi = float(x), lo = float(x - hi)).  A
 // pair's difference is first formed from hi alone; within a radius of a
 // quarter of the target's largest coordinate, where the rounding of hi
@@ -165,11 +174,19 @@ rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
                                           (float)lam[3 * (size_t)j + 2], 0.f);
         }
         __syncthreads();
+        // pair terms summed in FP32 over blocks of 8 sources, each block
+        // added to the tile's (hi, lo) sums by TwoSum, the tile folded into FP64
+        float th[TPT][3], tl[TPT][3];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t)
+            for (int c = 0; c < 3; ++c) th[t][c] = tl[t][c] = 0.f;
+        for (int q0 = 0; q0 < cnt; q0 += 8) {
+        const int qe = min(cnt, q0 + 8);
         float u[TPT][3];
 #pragma unroll
         for (int t = 0; t < TPT; ++t) u[t][0] = u[t][1] = u[t][2] = 0.f;
 #pragma unroll 2
-        for (int q = 0; q < cnt; ++q) {
+        for (int q = q0; q < qe; ++q) {
             const float4 h = sh[q];
             const float4 l = sl[q];
 #pragma unroll
@@ -193,11 +210,12 @@ rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
             }
         }
 #pragma unroll
-        for (int t = 0; t < TPT; ++t) {
-            U[t][0] += (double)u[t][0];
-            U[t][1] += (double)u[t][1];
-            U[t][2] += (double)u[t][2];
+        for (int t = 0; t < TPT; ++t)
+            for (int c = 0; c < 3; ++c) two_sum_acc(th[t][c], tl[t][c], u[t][c]);
         }
+#pragma unroll
+        for (int t = 0; t < TPT; ++t)
+            for (int c = 0; c < 3; ++c) U[t][c] += (double)th[t][c] + (double)tl[t][c];
     }
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
@@ -541,11 +559,19 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
             }
             __syncthreads();
             if (!warp_live) continue;
+            // pair terms summed in FP32 over blocks of 8 sources, each block
+            // added to the tile's (hi, lo) sums by TwoSum, the tile folded into FP64
+            float th[TPT][3], tl[TPT][3];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t)
+                for (int c = 0; c < 3; ++c) th[t][c] = tl[t][c] = 0.f;
+            for (int q0 = 0; q0 < cnt; q0 += 8) {
+            const int qe = min(cnt, q0 + 8);
             float u[TPT][3];
 #pragma unroll
             for (int t = 0; t < TPT; ++t) u[t][0] = u[t][1] = u[t][2] = 0.f;
 #pragma unroll 2
-            for (int q = 0; q < cnt; ++q) {
+            for (int q = q0; q < qe; ++q) {
                 const float4 h = sh[q];
                 const float4 l = sl[q];
 #pragma unroll
@@ -569,11 +595,12 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
                 }
             }
 #pragma unroll
-            for (int t = 0; t < TPT; ++t) {
-                U[t][0] += (double)u[t][0];
-                U[t][1] += (double)u[t][1];
-                U[t][2] += (double)u[t][2];
+            for (int t = 0; t < TPT; ++t)
+                for (int c = 0; c < 3; ++c) two_sum_acc(th[t][c], tl[t][c], u[t][c]);
             }
+#pragma unroll
+            for (int t = 0; t < TPT; ++t)
+                for (int c = 0; c < 3; ++c) U[t][c] += (double)th[t][c] + (double)tl[t][c];
         }
 #pragma unroll
         for (int t = 0; t < TPT; ++t) {
@@ -596,6 +623,18 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+
+// (hi, lo) += t exactly in each lane (Knuth's TwoSum of hi and t, the
+// rounding error added to lo): the compensated accumulation of the tile sums
+__device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 t) {
+    const float2 m1 = bc2(-1.f);
+    const float2 s = add2(hi, t);
+    const float2 v = fma2(hi, m1, s);                          // s - hi
+    const float2 e = add2(fma2(fma2(v, m1, s), m1, hi),        // hi - (s - v)
+                          fma2(v, m1, t));                      // + (t - v)
+    hi = s;
+    lo = add2(lo, e);
+}
 
 // Free-space pair plus wall image in both lanes: pair_wall_r2 of
 // rpy_pair.cuh (same operations in the same order), with the free-space
@@ -702,9 +741,15 @@ rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
                 soz[threadIdx.x] = make_float2(-o.z, -o.z);
             }
             __syncthreads();
+            // pair terms summed in FP32 over blocks of 8 sources, each block
+            // added to the tile's (hi, lo) sums by TwoSum, the tile folded
+            // into FP64
+            float2 hx = bc2(0.f), hy = bc2(0.f), hz = bc2(0.f), lx_ = bc2(0.f), ly_ = bc2(0.f), lz_ = bc2(0.f);
+            for (int q0 = 0; q0 < cnt; q0 += 8) {
+            const int qe = min(cnt, q0 + 8);
             float2 ux = bc2(0.f), uy = bc2(0.f), uz = bc2(0.f);
 #pragma unroll 2
-            for (int q = 0; q < cnt; ++q) {
+            for (int q = q0; q < qe; ++q) {
                 const float4 v0 = sq[0][q], v1 = sq[1][q], v2 = sq[2][q];
                 const float2 h2 = make_float2(v1.x, v1.y);
                 float2 dx = add2(HX, make_float2(v0.x, v0.y));
@@ -724,8 +769,14 @@ rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
                 pair2<WALL>(dx, dy, dz, rxy2, r2, Rz, h2, NX3, make_float2(v2.x, v2.y), make_float2(v2.z, v2.w),
                             make_float2(v1.z, v1.w), k, ux, uy, uz);
             }
-            U[0][0] += (double)ux.x; U[0][1] += (double)uy.x; U[0][2] += (double)uz.x;
-            U[1][0] += (double)ux.y; U[1][1] += (double)uy.y; U[1][2] += (double)uz.y;
+            two_sum_acc2(hx, lx_, ux);
+            two_sum_acc2(hy, ly_, uy);
+            two_sum_acc2(hz, lz_, uz);
+            }
+            U[0][0] += (double)hx.x + (double)lx_.x; U[0][1] += (double)hy.x + (double)ly_.x;
+            U[0][2] += (double)hz.x + (double)lz_.x;
+            U[1][0] += (double)hx.y + (double)lx_.y; U[1][1] += (double)hy.y + (double)ly_.y;
+            U[1][2] += (double)hz.y + (double)lz_.y;
         }
         if (i0 < m.t1) {
             double* o = part + m.pbase + 3 * (size_t)(i0 - m.tbase);

@@ -206,18 +206,20 @@ def test_zero_network_gives_block_diagonal_solution():
 
 
 def test_trained_network_on_held_out_suspensions():
-    # train on suspensions of 8 bacteria (seeds 1000..), evaluate one handle
-    # per held-out seed (20000..).  What the network gains is reported: the
-    # initial true residual is lower than that of P~^-1 b, the solve reaches
-    # the same tolerance, and the GMRES iterations are printed beside the
-    # plain ones.  (A perfect prediction of this target shortens the oracle's
-    # GMRES from 15 to 12 iterations on two bacteria; the trained network
-    # explains part of it.)
+    # Train on suspensions of 8 bacteria (seeds 1000..), evaluate one handle
+    # per held-out seed (20000..20011), FP64, relative residual 1e-8.  What
+    # the network gains: the initial true residual falls on every held-out
+    # seed (measured on GB300: ratios 0.40-0.97, geometric mean 0.61), and
+    # the GMRES iterations do not grow (measured: 257 plain, 255 learned over
+    # the twelve seeds, -2..+1 per seed).  It gains no iterations worth the
+    # name: GMRES iterations follow the logarithm of the residual reduction
+    # still to go, and even an exact prediction of this target only takes
+    # the oracle's GMRES from 15 to 12 iterations on two bacteria.
     X, T = learned.collect(list(range(1000, 1064)), n_bact=8, poses=2, systems_per_handle=32)
     net, loss = learned.train(X, T, epochs=20, batch=256, lr=1e-3, seed=0)
     assert loss < 0.5  # normalised MSE on the training set
     ratios, it_b, it_l = [], [], []
-    for seed in range(20000, 20004):
+    for seed in range(20000, 20012):
         out = learned.cold_start_iterations([learned.bacteria_at_density(seed, 8)], net,
                                             precision="fp64", tol=1e-8)
         b, l = out["block_diagonal"], out["learned"]
@@ -226,5 +228,9 @@ def test_trained_network_on_held_out_suspensions():
         ratios.append(l["rel_residual0"] / b["rel_residual0"])
         it_b.append(b["iterations"])
         it_l.append(l["iterations"])
-    print("initial residual ratio", ratios, "iterations plain", it_b, "learned", it_l)
-    assert np.exp(np.mean(np.log(ratios))) < 1.0
+    print("initial residual ratio", np.round(ratios, 3), "iterations plain", it_b, "learned", it_l)
+    assert np.exp(np.mean(np.log(ratios))) < 0.8
+    assert max(ratios) < 1.0
+    # no iteration cost on the whole: the per-seed changes are -2..+1, so
+    # the bar leaves a quarter of an iteration per seed of slack
+    assert sum(it_l) <= sum(it_b) + len(it_b) // 4, (it_b, it_l)
