@@ -1,8 +1,8 @@
 // The blob mobility product u = M lambda (Sec. 2.3, Eq. RPY; wall: the
 // Rotne-Prager-Blake tensor) with the pair terms in double-float arithmetic
 // (df64.cuh) on the FP32 pipes.  Same closed forms as rpy_pair.cuh (free
-// space: far r >= 2a, overlapping r < 2a, self; wall: the five-coefficient
-// image part), same work items as the FP64 and mixed products; each tile of
+// space: far r >= 2a, overlapping r < 2a, self; wall: the fused free-space
+// and image pair), same work items as the FP64 and mixed products; each tile of
 // 128 sources is summed in df and folded into FP64.  Relative error per pair
 // a few units of 2^-44, against 2^-53 for FP64 and 2^-24 for the mixed
 // product, at about an eighth of the FP64 cost: the mixed solver uses it for
@@ -18,6 +18,7 @@ namespace {
 // constants of the pair terms as df (see RpyK)
 struct RpyDf {
     df a2, four_a2, kf2, kf3, kn0, kn1, kn2;
+    df wc1, w2a2, wc2, wc3, nwa4, wi2;  // wall polynomial coefficients (pair_wall_r2)
     double A1;
 };
 
@@ -34,6 +35,13 @@ RpyDf rpy_df_consts(const RpyParams& q) {
     k.kn0 = split(4.0 / (3.0 * q.a));
     k.kn1 = split(9.0 / (32.0 * q.a));
     k.kn2 = split(1.0 / (8.0 * q.a2));
+    const double a4 = q.a2 * q.a2;
+    k.wc1 = split(-2.0 * q.a2 / 3.0);
+    k.w2a2 = split(2.0 * q.a2);
+    k.wc2 = split(2.0 * a4 / 3.0);
+    k.wc3 = split(-10.0 * a4 / 3.0);
+    k.nwa4 = split(-20.0 * a4 / 3.0);
+    k.wi2 = split(-4.0 * a4 / 3.0);
     k.A1 = q.inv8pieta;
     return k;
 }
@@ -41,72 +49,72 @@ RpyDf rpy_df_consts(const RpyParams& q) {
 __device__ __forceinline__ df dfc(double c) { return df_from(c); }
 __device__ __forceinline__ df one_plus(df x) { return df_add(df{1.0f, 0.0f}, x); }
 
-// u/A1 += c1 lambda + c2 d (d . lambda), the free-space pair of rpy_pair.cuh
-__device__ __forceinline__ void pair_free_df(df dx, df dy, df dz, df r2, df lx, df ly, df lz,
-                                             const RpyDf& k, df& ux, df& uy, df& uz) {
-    df c1, c2;
+// the free-space coefficients c1, c2 at squared distance r2 (rpy_pair.cuh)
+__device__ __forceinline__ void free_coefs_df(df r2, const RpyDf& k, df& c1, df& c2) {
+    const df one{1.0f, 0.0f};
     if (df_ge(r2, k.four_a2)) {
         const df ri = df_rsqrt(r2);
         const df ri2 = df_mul(ri, ri);
-        c1 = df_mul(ri, one_plus(df_mul(k.kf2, ri2)));
-        c2 = df_mul(df_mul(ri, ri2), one_plus(df_neg(df_mul(k.kf3, ri2))));
+        c1 = df_mul(ri, df_fma(k.kf2, ri2, one));
+        c2 = df_mul(df_mul(ri, ri2), df_fma(df_neg(k.kf3), ri2, one));
     } else if (r2.h > 0.0f) {
         const df ri = df_rsqrt(r2);
         const df r = df_mul(r2, ri);
-        c1 = df_mul(k.kn0, one_plus(df_neg(df_mul(k.kn1, r))));
+        c1 = df_mul(k.kn0, df_fma(df_neg(k.kn1), r, one));
         c2 = df_mul(k.kn2, ri);
     } else {
         c1 = k.kn0;
         c2 = df{0.0f, 0.0f};
     }
+}
+
+// u/A1 += c1 lambda + c2 d (d . lambda), the free-space pair of rpy_pair.cuh
+__device__ __forceinline__ void pair_free_df(df dx, df dy, df dz, df r2, df lx, df ly, df lz,
+                                             const RpyDf& k, df& ux, df& uy, df& uz) {
+    df c1, c2;
+    free_coefs_df(r2, k, c1, c2);
     const df sdl = df_mul(c2, df_fma(dx, lx, df_fma(dy, ly, df_mul(dz, lz))));
     ux = df_fma(c1, lx, df_fma(sdl, dx, ux));
     uy = df_fma(c1, ly, df_fma(sdl, dy, uy));
     uz = df_fma(c1, lz, df_fma(sdl, dz, uz));
 }
 
-// the wall image part of rpy_pair.cuh: R = x - y*, x3 target height, h
-// source height
-__device__ __forceinline__ void pair_image_df(df Rx, df Ry, df Rz, df x3, df h, df lx, df ly, df lz,
-                                              const RpyDf& k, df& ux, df& uy, df& uz) {
-    const df s = df_rsqrt(df_fma(Rx, Rx, df_fma(Ry, Ry, df_mul(Rz, Rz))));
-    const df s2 = df_mul(s, s);
-    const df hs = df_mul(h, s);
-    const df u = df_mul(hs, df_mul(x3, s));
-    const df ez = df_mul(Rz, s);
-    const df ez2 = df_mul(ez, ez);
-    const df A = df_mul(k.a2, s2);
-    const df A2 = df_mul(A, A);
-    const df t1 = df_mul(A, ez2);
-    const df t2 = df_mul(A2, ez2);
-    // cI = -1 - 2u - 2/3 A + 2 t1 + 2/3 A^2 - 10/3 t2
-    df cI = df_add(df{-1.0f, 0.0f}, df_scale2(u, -2.0f));
-    cI = df_fma(dfc(-2.0 / 3.0), A, cI);
-    cI = df_add(cI, df_scale2(t1, 2.0f));
-    cI = df_fma(dfc(2.0 / 3.0), A2, cI);
-    cI = df_fma(dfc(-10.0 / 3.0), t2, cI);
-    // cRR = -1 + 6u + 2A - 10 t1 - 10/3 A^2 + 70/3 t2
-    df cRR = df_add(df{-1.0f, 0.0f}, df_mul_f(u, 6.0f));
-    cRR = df_add(cRR, df_scale2(A, 2.0f));
-    cRR = df_add(cRR, df_mul_f(t1, -10.0f));
-    cRR = df_fma(dfc(-10.0 / 3.0), A2, cRR);
-    cRR = df_fma(dfc(70.0 / 3.0), t2, cRR);
-    // cRz = 2 h s + ez (-2 cRR - 2 + 20/3 A^2), czR = 2 h s - 20/3 A^2 ez
-    const df hs2 = df_scale2(hs, 2.0f);
-    const df inner = df_fma(dfc(20.0 / 3.0), A2, df_add(df_scale2(cRR, -2.0f), df{-2.0f, 0.0f}));
-    const df cRz = df_fma(ez, inner, hs2);
-    const df czR = df_fma(df_mul(dfc(-20.0 / 3.0), A2), ez, hs2);
-    // czz = -4 (h s)^2 - 4 t1 - 8/3 A^2 + 20 t2
-    df czz = df_scale2(df_mul(hs, hs), -4.0f);
-    czz = df_add(czz, df_scale2(t1, -4.0f));
-    czz = df_fma(dfc(-8.0 / 3.0), A2, czz);
-    czz = df_add(czz, df_mul_f(t2, 20.0f));
-    const df rx = df_mul(Rx, s), ry = df_mul(Ry, s);
-    const df dotR = df_fma(rx, lx, df_fma(ry, ly, df_mul(ez, lz)));
-    const df t = df_fma(cRR, dotR, df_mul(cRz, lz));
-    ux = df_fma(s, df_fma(cI, lx, df_mul(t, rx)), ux);
-    uy = df_fma(s, df_fma(cI, ly, df_mul(t, ry)), uy);
-    uz = df_fma(s, df_fma(cI, lz, df_fma(t, ez, df_fma(czR, dotR, df_mul(czz, lz)))), uz);
+// Free-space pair plus wall image of one source in double-float: the same
+// operations as pair_wall_r2 of rpy_pair.cuh (polynomials in w = s^2 on the
+// unnormalised image vector R = (dx, dy, Rz)), scalings by small integers as
+// exact (powers of two) or single-float multiplies.  h2 = twice the source
+// height, nx3 = minus the target height.
+__device__ __forceinline__ void pair_wall_df(df dx, df dy, df dz, df rxy2, df r2, df Rz, df h2, df nx3, df lx,
+                                             df ly, df lz, const RpyDf& k, df& ux, df& uy, df& uz) {
+    const df Rz2 = df_mul(Rz, Rz);
+    const df dlxy = df_fma(dx, lx, df_mul(dy, ly));
+    const df Df = df_fma(dz, lz, dlxy);  // d . lambda
+    const df Di = df_fma(Rz, lz, dlxy);  // R . lambda
+    df c1f, c2f;
+    free_coefs_df(r2, k, c1f, c2f);
+    const df sdl = df_mul(c2f, Df);
+    const df s = df_rsqrt(df_add(rxy2, Rz2));
+    const df w = df_mul(s, s), s3 = df_mul(s, w), w2 = df_mul(w, w);
+    const df c1 = df_fma(h2, nx3, k.wc1);
+    const df c2 = df_fma(Rz2, k.w2a2, k.wc2);
+    const df c3 = df_mul(Rz2, k.wc3);
+    const df x1 = df_fma(w, c3, c2);
+    const df cI = df_fma(w, df_fma(w, x1, c1), df{-1.0f, 0.0f});
+    const df y = df_fma(w, c3, x1);   // c2 + 2 w c3
+    const df yz = df_fma(w, c3, y);   // c2 + 3 w c3
+    // cRR = -4 - 3 cI - 2 w^2 y
+    const df cRR = df_add(df_scale2(df_mul(w2, y), -2.0f), df_add(df_mul_f(cI, -3.0f), df{-4.0f, 0.0f}));
+    const df A4w2n = df_mul(w2, k.nwa4);  // -20/3 a^4 w^2
+    // inner = -2 cRR - 2 - A4w2n
+    const df inner = df_add(df_add(df_scale2(cRR, -2.0f), df{-2.0f, 0.0f}), df_neg(A4w2n));
+    const df P = df_mul(s3, df_fma(cRR, Di, df_mul(df_fma(Rz, inner, h2), lz)));
+    const df Q = df_mul(s3, df_fma(h2, Df, df_fma(df_mul(A4w2n, Rz), Di,
+                                                   df_mul(df_mul(w, df_add(df_scale2(yz, -2.0f), k.wi2)), lz))));
+    const df cc = df_fma(s, cI, c1f);
+    const df pp = df_add(sdl, P);
+    ux = df_fma(cc, lx, df_fma(pp, dx, ux));
+    uy = df_fma(cc, ly, df_fma(pp, dy, uy));
+    uz = df_fma(cc, lz, df_fma(sdl, dz, df_fma(P, Rz, df_add(uz, Q))));
 }
 
 template <bool WALL>
@@ -133,6 +141,7 @@ rpy_items_df(const float4* __restrict__ hi, const float4* __restrict__ lo, const
             const float4 xh = (i < m.t1) ? hi[i] : make_float4(0.f, 0.f, 1.f, 0.f);
             const float4 xl = (i < m.t1) ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
             const df xx{xh.x, xl.x}, xy{xh.y, xl.y}, xz{xh.z, xl.z};
+            const df nx3 = df_neg(xz);
             double U0 = 0.0, U1 = 0.0, U2 = 0.0;
             // warps with no target of the item only help stage the sources
             const bool warp_live = tb + (int)(threadIdx.x & ~31u) < m.t1;
@@ -158,9 +167,14 @@ rpy_items_df(const float4* __restrict__ hi, const float4* __restrict__ lo, const
                     const df dx = df_sub(xx, df{yh.x, yl.x});
                     const df dy = df_sub(xy, df{yh.y, yl.y});
                     const df dz = df_sub(xz, yz);
-                    const df r2 = df_fma(dx, dx, df_fma(dy, dy, df_mul(dz, dz)));
-                    pair_free_df(dx, dy, dz, r2, lx, ly, lz, k, ux, uy, uz);
-                    if (WALL) pair_image_df(dx, dy, df_add(xz, yz), xz, yz, lx, ly, lz, k, ux, uy, uz);
+                    if (WALL) {
+                        const df rxy2 = df_fma(dx, dx, df_mul(dy, dy));
+                        pair_wall_df(dx, dy, dz, rxy2, df_fma(dz, dz, rxy2), df_add(xz, yz), df_scale2(yz, 2.0f),
+                                     nx3, lx, ly, lz, k, ux, uy, uz);
+                    } else {
+                        const df r2 = df_fma(dx, dx, df_fma(dy, dy, df_mul(dz, dz)));
+                        pair_free_df(dx, dy, dz, r2, lx, ly, lz, k, ux, uy, uz);
+                    }
                 }
                 U0 += df_to(ux);
                 U1 += df_to(uy);
