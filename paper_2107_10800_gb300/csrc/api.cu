@@ -418,6 +418,8 @@ int device_flags_to_status(am_handle* h, const char* who) {
                                                "(bodies need at least three non-collinear blobs)");
     if (f & am::kFlagCorrection)
         return set_err(h, AM_ERR_SINGULAR, std::string(who) + ": correction normal equations not positive definite");
+    if (f & am::kFlagTensor)
+        return set_err(h, AM_ERR_CUDA, std::string(who) + ": a tensor-core wait of the network timed out");
     return AM_OK;
 }
 
@@ -447,6 +449,8 @@ int prepare(am_handle* h, const char* who, bool warm, am_step_stats* st) {
         // smallest residual
         if (am::learned_x0(h, h->d_x))
             return set_err(h, AM_ERR_CUDA, std::string(who) + ": learned initial guess failed");
+        rc = device_flags_to_status(h, who);  // the network's tensor-core waits
+        if (rc) return rc;
         const int used = h->mlp_check ? am::line_initial(h, h->d_x, h->d_dx) : h->S;
         if (st) st->learned_systems = used;
     } else {

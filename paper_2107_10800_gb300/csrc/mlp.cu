@@ -22,6 +22,7 @@
 #include "dev_util.cuh"
 #include "ops.cuh"
 #include "rpy_pair.cuh"
+#include "tc_gemm.cuh"
 
 #include <cuda_bf16.h>
 
@@ -486,63 +487,6 @@ __global__ void k_normalize_bf16(const float* __restrict__ X, const float* __res
     A[e] = __float2bfloat16((X[e] - mu[c]) / sd[c]);
 }
 
-__device__ __forceinline__ uint32_t ld_bf16x2(const __nv_bfloat16* p) {
-    return *reinterpret_cast<const uint32_t*>(p);
-}
-
-// Out[r][o] = act(sum_i A[r][i] W[o][i] + b[o]) with warp-level BF16 tensor
-// cores (mma.sync m16n8k16, FP32 accumulate).  Block: 4 warps, 64 rows x 64
-// outputs; warp w: rows 16w..16w+15, eight 8-wide output tiles.  `in` is a
-// multiple of 16; A rows beyond n read as zero.
-__global__ void __launch_bounds__(128)
-k_linear_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ W,
-              const float* __restrict__ b, __nv_bfloat16* __restrict__ Obf, float* __restrict__ Of,
-              const float* __restrict__ sdo, int n, int in, int out, int relu) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int r0 = blockIdx.y * 64 + warp * 16;
-    const int o0 = blockIdx.x * 64;
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const int ra = r0 + g, rb = r0 + g + 8;
-    for (int k0 = 0; k0 < in; k0 += 16) {
-        const uint32_t z = 0u;
-        const uint32_t a0 = ra < n ? ld_bf16x2(A + (size_t)ra * in + k0 + 2 * t) : z;
-        const uint32_t a1 = rb < n ? ld_bf16x2(A + (size_t)rb * in + k0 + 2 * t) : z;
-        const uint32_t a2 = ra < n ? ld_bf16x2(A + (size_t)ra * in + k0 + 2 * t + 8) : z;
-        const uint32_t a3 = rb < n ? ld_bf16x2(A + (size_t)rb * in + k0 + 2 * t + 8) : z;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int o = o0 + 8 * j + g;
-            const uint32_t b0 = o < out ? ld_bf16x2(W + (size_t)o * in + k0 + 2 * t) : z;
-            const uint32_t b1 = o < out ? ld_bf16x2(W + (size_t)o * in + k0 + 2 * t + 8) : z;
-            asm volatile(
-                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                : "+f"(acc[j][0]), "+f"(acc[j][1]), "+f"(acc[j][2]), "+f"(acc[j][3])
-                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = h ? rb : ra;
-            if (r >= n) continue;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int o = o0 + 8 * j + 2 * t + c;
-                if (o >= out) continue;
-                float v = acc[j][2 * h + c] + b[o];
-                if (relu) v = fmaxf(v, 0.f);
-                if (Of) Of[(size_t)r * out + o] = sdo ? v * sdo[o] : v;
-                else Obf[(size_t)r * out + o] = __float2bfloat16(v);
-            }
-        }
-    }
-}
-
 }  // namespace
 
 // ===================================================================== model
@@ -557,6 +501,7 @@ struct am_mlp {
     float* d_a[NLAYER + 1] = {};
     __nv_bfloat16 *d_h0 = nullptr, *d_h1 = nullptr;
     int* d_rows = nullptr;
+    int* d_flag = nullptr;  // tensor-core wait timeouts of the standalone prediction
     double* d_loss = nullptr;
     int data_n = 0;
     cudaStream_t st = nullptr;
@@ -646,21 +591,25 @@ void refresh_bf16(am_mlp* m) {
     m->bf_valid = true;
 }
 
-// BF16 tensor-core prediction of n rows (X device) into Y (device, n x OUT,
-// scaled by sd_out)
-void predict_bf16(am_mlp* m, const float* X, int n, float* Y) {
+// BF16 prediction of n rows (X device) into Y (device, n x OUT, scaled by
+// sd_out): each layer on the tcgen05 tensor cores (tc_gemm.cuh), one block
+// per 128 rows, FP32 accumulators in tensor memory, bias and ReLU in the
+// epilogue; a timed-out tensor-core wait sets am::kFlagTensor in *flags.
+void predict_bf16(am_mlp* m, const float* X, int n, float* Y, int* flags) {
     cudaStream_t s = m->st;
     refresh_bf16(m);
     k_normalize_bf16<<<(n * FEAT + 255) / 256, 256, 0, s>>>(X, m->d_mu, m->d_sd, m->d_h0, n);
     am::count_launch();
     __nv_bfloat16* hin = m->d_h0;
     __nv_bfloat16* hout = m->d_h1;
+    static_assert(am::tc::kFlagTensorTimeout == am::kFlagTensor, "one flag bit for tensor-core timeouts");
     for (int l = 0; l < NLAYER; ++l) {
         const bool last = l == NLAYER - 1;
-        dim3 grid((kDims[l + 1] + 63) / 64, (n + 63) / 64);
-        k_linear_bf16<<<grid, 128, 0, s>>>(hin, m->d_wbf + layer_w_off(l), b_of(m, l), last ? nullptr : hout,
-                                           last ? Y : nullptr, last ? m->d_sdo : nullptr, n, kDims[l],
-                                           kDims[l + 1], last ? 0 : 1);
+        const int smem = am::tc::smem_bytes(kDims[l], kDims[l + 1]);
+        cudaFuncSetAttribute(am::tc::k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        am::tc::k_linear_tc<<<(n + am::tc::kRows - 1) / am::tc::kRows, 128, smem, s>>>(
+            hin, m->d_wbf + layer_w_off(l), b_of(m, l), last ? nullptr : hout, last ? Y : nullptr,
+            last ? m->d_sdo : nullptr, n, kDims[l], kDims[l + 1], last ? 0 : 1, flags);
         am::count_launch();
         std::swap(hin, hout);
     }
@@ -694,7 +643,7 @@ extern "C" AM_API int am_mlp_create(unsigned long long seed, void* stream, am_ml
         (e = cudaMalloc(&m->d_v, np * sizeof(float))) || (e = cudaMalloc(&m->d_g, np * sizeof(float))) ||
         (e = cudaMalloc(&m->d_wbf, np * sizeof(__nv_bfloat16))) || (e = cudaMalloc(&m->d_mu, FEAT * sizeof(float))) ||
         (e = cudaMalloc(&m->d_sd, FEAT * sizeof(float))) || (e = cudaMalloc(&m->d_sdo, OUT * sizeof(float))) ||
-        (e = cudaMalloc(&m->d_loss, sizeof(double))))
+        (e = cudaMalloc(&m->d_loss, sizeof(double))) || (e = cudaMalloc(&m->d_flag, sizeof(int))))
         return fail(e);
     cudaMemcpy(m->d_p, p.data(), np * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemset(m->d_m, 0, np * sizeof(float));
@@ -713,7 +662,7 @@ extern "C" AM_API void am_mlp_destroy(am_mlp* m) {
     for (void* p : {(void*)m->d_p, (void*)m->d_m, (void*)m->d_v, (void*)m->d_g, (void*)m->d_wbf, (void*)m->d_mu,
                     (void*)m->d_sd, (void*)m->d_sdo, (void*)m->d_X, (void*)m->d_T, (void*)m->d_bx, (void*)m->d_bt,
                     (void*)m->d_dz0, (void*)m->d_dz1, (void*)m->d_h0, (void*)m->d_h1, (void*)m->d_rows,
-                    (void*)m->d_loss})
+                    (void*)m->d_loss, (void*)m->d_flag})
         if (p) cudaFree(p);
     for (int l = 0; l <= NLAYER; ++l) {
         if (m->d_z[l]) cudaFree(m->d_z[l]);
@@ -834,7 +783,8 @@ extern "C" AM_API int am_mlp_predict(am_mlp* m, const float* X, int n, int bf16,
     if (rc) return rc;
     float* dY = m->d_bt;
     if (bf16) {
-        predict_bf16(m, m->d_X, n, dY);
+        MCK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->st));
+        predict_bf16(m, m->d_X, n, dY, m->d_flag);
     } else {
         forward32(m, m->d_X, n);
         MCK(cudaMemcpyAsync(dY, m->d_z[NLAYER], (size_t)n * OUT * sizeof(float), cudaMemcpyDeviceToDevice, m->st));
@@ -843,7 +793,10 @@ extern "C" AM_API int am_mlp_predict(am_mlp* m, const float* X, int n, int bf16,
     }
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(Y, dY, (size_t)n * OUT * sizeof(float), cudaMemcpyDeviceToHost, m->st));
+    int flag = 0;
+    if (bf16) MCK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, m->st));
     MCK(cudaStreamSynchronize(m->st));
+    if (flag) return mlp_fail(AM_ERR_CUDA, "am_mlp_predict: a tensor-core wait timed out");
     return AM_OK;
 }
 
@@ -883,7 +836,7 @@ int learned_x0(am_handle* h, double* x) {
     if (features_dev(h, xpc, m->d_bx, nullptr)) return 1;
     cudaStream_t keep = m->st;
     m->st = s;
-    predict_bf16(m, m->d_bx, h->M, m->d_bt);
+    predict_bf16(m, m->d_bx, h->M, m->d_bt, h->d_flags);
     m->st = keep;
     // right-hand side with the predicted background flow moved over, then
     // the block-diagonal solve (which keeps C U = B)

@@ -8,6 +8,7 @@ namespace am {
 constexpr int kFlagWall = 1;        // a blob centre at or below height a
 constexpr int kFlagSingular = 2;    // a body block of M or N~ not SPD
 constexpr int kFlagCorrection = 4;  // correction normal equations not SPD
+constexpr int kFlagTensor = 1 << 8; // a tensor-core (tcgen05) wait timed out (tc_gemm.cuh)
 
 // Arithmetic of a mobility product: the handle's precision, FP64,
 // double-float pair terms (rpy_df.cu), or the mixed FP32 pair terms.

@@ -5,6 +5,7 @@ one kernel (-k, -c) ends quickly.  Nothing here is timed.
     python -m paper_2107_10800_gb300.profile_cases product --blobs 60000 [--arith mixed|fp64|df64]
     python -m paper_2107_10800_gb300.profile_cases colony --precision fp64|mixed [--steps 3] [--host-steps]
     python -m paper_2107_10800_gb300.profile_cases batched [--steps 1] [--host-steps]
+    python -m paper_2107_10800_gb300.profile_cases mlp [--rows 65536] [--calls 3]
 
 product: the all-pairs wall product u = M lambda on the first N blobs of the
 1,000-bacteria suspension above a wall (each blob its own body, so the
@@ -16,6 +17,8 @@ launched from the host (per-launch timing of the product on) instead of
 from the CUDA-graph loop, whose kernels profilers do not capture.
 batched: steps of the 256 free-space chain suspensions in one handle
 (mixed precision); --host-steps as for colony.
+mlp: BF16 predictions of the learned-guess network (random weights) for
+`--rows` feature rows: four tcgen05 layer launches per call.
 """
 import argparse
 import os
@@ -69,9 +72,18 @@ def batched(steps, host_steps=False):
     s.close()
 
 
+def mlp(rows, calls):
+    net = binding.Mlp(seed=1)
+    X = np.random.default_rng(0).standard_normal((rows, binding.MLP_FEAT)).astype(np.float32)
+    for _ in range(calls):
+        net.predict(X, bf16=True)
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["product", "colony", "batched"])
+    ap.add_argument("case", choices=["product", "colony", "batched", "mlp"])
+    ap.add_argument("--rows", type=int, default=65536)
     ap.add_argument("--blobs", type=int, default=60000)
     ap.add_argument("--arith", default="mixed", choices=["mixed", "fp64", "df64"])
     ap.add_argument("--calls", type=int, default=3)
@@ -84,8 +96,10 @@ def main():
         product(a.blobs, a.arith, a.calls)
     elif a.case == "colony":
         colony(a.precision, a.steps, a.host_steps)
-    else:
+    elif a.case == "batched":
         batched(a.steps, a.host_steps)
+    else:
+        mlp(a.rows, a.calls)
 
 
 if __name__ == "__main__":
