@@ -172,6 +172,7 @@ struct am_handle {
            *d_tol_s = nullptr, *d_sysred = nullptr, *d_hcols = nullptr;
     int *d_active = nullptr, *d_kdone = nullptr;
     int* d_arn_cnt = nullptr;  // S + 1 arrival counts of the fused Arnoldi step kernels
+    int* d_pcb_cnt = nullptr;  // M arrival counts of the preconditioner apply (per body)
     int chunk_len = 1024, chunk_threads = 256;  // dot-product chunk length, threads per chunk block
     // all-pairs work items (block-diagonal over systems) and their queue
     void* d_items = nullptr;

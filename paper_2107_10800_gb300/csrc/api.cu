@@ -138,7 +138,7 @@ void free_bodies(am_handle* h) {
     dfree(&h->d_r4); dfree(&h->d_d4); dfree(&h->d_rhi); dfree(&h->d_rlo); dfree(&h->d_r3);
     dfree(&h->d_minv); dfree(&h->d_pcwork); dfree(&h->d_Y); dfree(&h->d_Nt); dfree(&h->d_minv_off);
     dfree(&h->d_pc_w); dfree(&h->d_pc_Uhat); dfree(&h->d_mv);
-    dfree(&h->d_pcw_body); dfree(&h->d_pcw_chunk); dfree(&h->d_pcw_off); dfree(&h->d_ytp);
+    dfree(&h->d_pcw_body); dfree(&h->d_pcw_chunk); dfree(&h->d_pcw_off); dfree(&h->d_ytp); dfree(&h->d_pcb_cnt);
     dfree(&h->d_pcb_list);
     h->n_pcb_small = 0;
     h->pcb_cs = 1;
@@ -634,6 +634,8 @@ int build_layout(am_handle* h, int M, int Nb, int NA, int maxb, const double* q,
     CK(dalloc(&h->d_pcb_list, std::max(M, 1)));
     CK(dalloc(&h->d_pcw_body, pcw_body.size())); CK(dalloc(&h->d_pcw_chunk, pcw_chunk.size()));
     CK(dalloc(&h->d_pcw_off, M + 1)); CK(dalloc(&h->d_ytp, 6 * pcw_body.size()));
+    CK(dalloc(&h->d_pcb_cnt, M));
+    CK(cudaMemsetAsync(h->d_pcb_cnt, 0, std::max(M, 1) * sizeof(int), s));
     CK(dalloc(&h->d_minv_off, M + 1)); CK(dalloc(&h->d_pc_w, 3 * (size_t)Nb));
     CK(dalloc(&h->d_pc_Uhat, 6 * (size_t)M));
     CK(dalloc(&h->d_qnew, 3 * (size_t)M)); CK(dalloc(&h->d_thnew, 4 * (size_t)M));

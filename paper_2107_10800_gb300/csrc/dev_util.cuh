@@ -25,6 +25,26 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return sh[32];
 }
 
+// Arrival count of the blocks that share a reduction: every block that has
+// written its partial results calls it (all threads); true in every thread
+// of the block that completes cnt[idx] = total, which then reads the
+// others' partials (with __ldcg: they bypass this SM's L1) and has zeroed
+// the count for the next use.  No block waits for another.
+__device__ __forceinline__ bool arrive_last(int* cnt, int idx, int total) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int t = atomicAdd(&cnt[idx], 1);
+        s_last = (t == total - 1) ? 1 : 0;
+        if (s_last) cnt[idx] = 0;
+    }
+    __syncthreads();
+    const bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
+
 __device__ __forceinline__ void cross3(const double* a, const double* b, double* o) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];

@@ -711,22 +711,6 @@ __device__ void loop_ctrl(ArnoldiCtrl* c, int* __restrict__ active, int* __restr
 // arithmetic and its order are those of separate dot, coefficient,
 // orthogonalisation, norm and step-end kernels.
 
-// true in every thread of the block that completes cnt[idx] = total
-__device__ bool arrive_last(int* cnt, int idx, int total) {
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const int t = atomicAdd(&cnt[idx], 1);
-        s_last = (t == total - 1) ? 1 : 0;
-        if (s_last) cnt[idx] = 0;
-    }
-    __syncthreads();
-    const bool last = s_last != 0;
-    if (last) __threadfence();
-    return last;
-}
-
 // part[k * nchunks + b] = <V_k, w> over chunk [c0, c1), k <= j (a warp per k)
 __device__ __forceinline__ void chunk_dots(const double* __restrict__ V, size_t ldv, const double* w, int c0,
                                            int c1, int j, double* __restrict__ part, int nchunks, int b) {

@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(128)
 k_pc_ap1(const int* __restrict__ pcw_body, const int* __restrict__ pcw_chunk,
          const int* __restrict__ blob_off, const T* __restrict__ minv,
          const long long* __restrict__ moff, const T* __restrict__ Y, const double* __restrict__ r,
-         double* __restrict__ w, double* __restrict__ ytp) {
+         double* __restrict__ w, double* __restrict__ ytp, int Nb, const int* __restrict__ pcw_off,
+         const double* __restrict__ Nt, double* __restrict__ Uhat, int* __restrict__ body_cnt) {
     __shared__ double red[4][kRows];
     __shared__ double yred[4][6];
     const int it = blockIdx.x;
@@ -387,30 +388,23 @@ k_pc_ap1(const int* __restrict__ pcw_body, const int* __restrict__ pcw_chunk,
         if (row < m) w[3 * (size_t)i0 + row] = red[0][lane] + red[1][lane] + red[2][lane] + red[3][lane];
         if (lane < 6) ytp[6 * (size_t)it + lane] = yred[0][lane];
     }
-}
-
-// U^_b = N~_b (-r2_b - sum of the body's Y^T r1 partials); one warp per body
-__global__ void k_pc_uhat(int Nb, int M, const int* __restrict__ pcw_off,
-                          const double* __restrict__ Nt, const double* __restrict__ r,
-                          const double* __restrict__ ytp, double* __restrict__ Uhat) {
-    const int b = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= M) return;
-    double v = 0.0;
-    if (lane < 6) {
-        v = -r[3 * (size_t)Nb + 6 * (size_t)b + lane];
-#pragma unroll 4
-        for (int it = pcw_off[b]; it < pcw_off[b + 1]; ++it) v -= ytp[6 * (size_t)it + lane];
-    }
-    double vv[6];
+    // the body's last item: U^_b = N~_b (-r2_b - sum of the body's Y^T r1 partials)
+    if (arrive_last(body_cnt, b, pcw_off[b + 1] - pcw_off[b]) && part == 0) {
+        double v = 0.0;
+        if (lane < 6) {
+            v = -r[3 * (size_t)Nb + 6 * (size_t)b + lane];
+            for (int q = pcw_off[b]; q < pcw_off[b + 1]; ++q) v -= __ldcg(ytp + 6 * (size_t)q + lane);
+        }
+        double vv[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) vv[c] = __shfl_sync(0xffffffffu, v, c);
-    if (lane < 6) {
-        const double* N = Nt + 36 * (size_t)b + 6 * lane;
-        double s = 0.0;
+        for (int c = 0; c < 6; ++c) vv[c] = __shfl_sync(0xffffffffu, v, c);
+        if (lane < 6) {
+            const double* N = Nt + 36 * (size_t)b + 6 * lane;
+            double t = 0.0;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s += N[c] * vv[c];
-        Uhat[6 * (size_t)b + lane] = s;
+            for (int c = 0; c < 6; ++c) t += N[c] * vv[c];
+            Uhat[6 * (size_t)b + lane] = t;
+        }
     }
 }
 
@@ -430,13 +424,17 @@ __global__ void k_pc_cvec(int Nb, int M, int P, const int* __restrict__ bp, cons
     for (int x = 0; x < 3; ++x) cbuf[3 * n + x] = r3[3 * n + x] - (up[x] + wp[x] - uq[x] - wq[x]);
 }
 
-// phi rows of one (articulated body, 32-row chunk) item: phi = G~ c
-template <class T>
+// phi rows of one (articulated body, 32-row chunk) item: phi = G~ c, with c
+// read from cbuf (k_pc_cvec) or, FUSED, formed here from U^ and r3 for the
+// entries this block stages (c_n = r3_n - (C U^)_n)
+template <class T, bool FUSED>
 __global__ void __launch_bounds__(128)
 k_pc_ap2(int Nb, int M, const int* __restrict__ pca_asm, const int* __restrict__ pca_chunk,
          const int* __restrict__ asm_link_off, const int* __restrict__ asm_link_idx,
          const T* __restrict__ G, const long long* __restrict__ goff, const double* __restrict__ cbuf,
-         double* __restrict__ z) {
+         double* __restrict__ z, const int* __restrict__ bp, const int* __restrict__ bq,
+         const double* __restrict__ lp, const double* __restrict__ lq, const double* __restrict__ Uhat,
+         const double* __restrict__ r) {
     constexpr int kStage = 1024;  // entries of c staged in shared memory at a time
     __shared__ double red[4][kRows];
     __shared__ double cs[kStage];
@@ -453,7 +451,17 @@ k_pc_ap2(int Nb, int M, const int* __restrict__ pca_asm, const int* __restrict__
         __syncthreads();
         for (int k = threadIdx.x; k < cn; k += blockDim.x) {
             const int kk = c0 + k;
-            cs[k] = cbuf[3 * asm_link_idx[L0 + kk / 3] + kk % 3];
+            const int n = asm_link_idx[L0 + kk / 3], x = kk % 3;
+            if (FUSED) {
+                const double* up = Uhat + 6 * bp[n];
+                const double* uq = Uhat + 6 * bq[n];
+                double wp[3], wq[3];
+                cross3(up + 3, lp + 3 * n, wp);
+                cross3(uq + 3, lq + 3 * n, wq);
+                cs[k] = r[3 * (size_t)Nb + 6 * (size_t)M + 3 * n + x] - (up[x] + wp[x] - uq[x] - wq[x]);
+            } else {
+                cs[k] = cbuf[3 * n + x];
+            }
         }
         __syncthreads();
         if (row < m) {
@@ -597,15 +605,22 @@ void pc_apply_links(am_handle* h, const double* r, double* z) {
     k_pc_cvec<<<(h->P + 127) / 128, 128, 0, s>>>(h->Nb, h->M, h->P, h->d_bp, h->d_bq, h->d_lp, h->d_lq,
                                                   h->d_pc_Uhat, r, h->d_cbuf);
     if (h->pc32)
-        k_pc_ap2<float><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk, h->d_asm_link_off,
-                                                  h->d_asm_link_idx, (const float*)h->d_G, h->d_G_off, h->d_cbuf, z);
+        k_pc_ap2<float, false><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk,
+                                                         h->d_asm_link_off, h->d_asm_link_idx, (const float*)h->d_G,
+                                                         h->d_G_off, h->d_cbuf, z, nullptr, nullptr, nullptr,
+                                                         nullptr, nullptr, nullptr);
     else
-        k_pc_ap2<double><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk, h->d_asm_link_off,
-                                                   h->d_asm_link_idx, (const double*)h->d_G, h->d_G_off, h->d_cbuf, z);
+        k_pc_ap2<double, false><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk,
+                                                          h->d_asm_link_off, h->d_asm_link_idx, (const double*)h->d_G,
+                                                          h->d_G_off, h->d_cbuf, z, nullptr, nullptr, nullptr,
+                                                          nullptr, nullptr, nullptr);
     count_launch(2);
 }
 
 void pc_build(am_handle* h) {
+    // arrival counts of the apply's per-body reductions (each completing
+    // block zeroes its own; zeroed here as well, outside any graph)
+    if (h->d_pcb_cnt) cudaMemsetAsync(h->d_pcb_cnt, 0, std::max(h->M, 1) * sizeof(int), h->stream);
     if (h->sb) {
         sb_pc_build(h);
         if (h->P) pca_build_t<double>(h, 1e-11);
@@ -622,17 +637,17 @@ void pc_build(am_handle* h) {
 template <class T>
 static void pc_apply_t(am_handle* h, const double* r, double* z) {
     cudaStream_t s = h->stream;
+    // w and Y^T r1 per (body, chunk) item; the body's last item forms U^
     k_pc_ap1<T><<<h->n_pcw, 128, 0, s>>>(h->d_pcw_body, h->d_pcw_chunk, h->d_blob_off, (const T*)h->d_minv,
-                                          h->d_minv_off, (const T*)h->d_Y, r, h->d_pc_w, h->d_ytp);
-    k_pc_uhat<<<(h->M + 3) / 4, 128, 0, s>>>(h->Nb, h->M, h->d_pcw_off, h->d_Nt, r, h->d_ytp,
-                                                  h->d_pc_Uhat);
-    count_launch(2);
+                                          h->d_minv_off, (const T*)h->d_Y, r, h->d_pc_w, h->d_ytp, h->Nb,
+                                          h->d_pcw_off, h->d_Nt, h->d_pc_Uhat, h->d_pcb_cnt);
+    count_launch();
     if (h->P) {
-        k_pc_cvec<<<(h->P + 127) / 128, 128, 0, s>>>(h->Nb, h->M, h->P, h->d_bp, h->d_bq, h->d_lp, h->d_lq,
-                                                      h->d_pc_Uhat, r, h->d_cbuf);
-        k_pc_ap2<T><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk, h->d_asm_link_off,
-                                              h->d_asm_link_idx, (const T*)h->d_G, h->d_G_off, h->d_cbuf, z);
-        count_launch(2);
+        // phi = G~ (r3 - C U^), c formed per staged entry
+        k_pc_ap2<T, true><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk, h->d_asm_link_off,
+                                                    h->d_asm_link_idx, (const T*)h->d_G, h->d_G_off, nullptr, z,
+                                                    h->d_bp, h->d_bq, h->d_lp, h->d_lq, h->d_pc_Uhat, r);
+        count_launch();
     }
     k_pc_ap3<T><<<h->n_pcw, 128, 0, s>>>(h->Nb, h->M, h->d_pcw_body, h->d_pcw_chunk, h->d_blob_off,
                                           (const T*)h->d_Y, h->d_Nt, h->d_pc_w, h->d_pc_Uhat,

@@ -123,6 +123,10 @@ rpy_partial_f64(const double4_32a* __restrict__ r4, const double* __restrict__ l
     }
 }
 
+// sources per FP32 partial sum of the mixed kernels before it is added to
+// the tile's compensated (hi, lo) sums
+constexpr int kSumBlock = 16;
+
 // hi + lo += t with Knuth's TwoSum (rounding error of hi + t kept in lo):
 // the compensated accumulation of the tile sums of the mixed kernels
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float t) {
@@ -174,14 +178,14 @@ rpy_partial_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
                                           (float)lam[3 * (size_t)j + 2], 0.f);
         }
         __syncthreads();
-        // pair terms summed in FP32 over blocks of 8 sources, each block
+        // pair terms summed in FP32 over blocks of kSumBlock sources, each block
         // added to the tile's (hi, lo) sums by TwoSum, the tile folded into FP64
         float th[TPT][3], tl[TPT][3];
 #pragma unroll
         for (int t = 0; t < TPT; ++t)
             for (int c = 0; c < 3; ++c) th[t][c] = tl[t][c] = 0.f;
-        for (int q0 = 0; q0 < cnt; q0 += 8) {
-        const int qe = min(cnt, q0 + 8);
+        for (int q0 = 0; q0 < cnt; q0 += kSumBlock) {
+        const int qe = min(cnt, q0 + kSumBlock);
         float u[TPT][3];
 #pragma unroll
         for (int t = 0; t < TPT; ++t) u[t][0] = u[t][1] = u[t][2] = 0.f;
@@ -559,14 +563,14 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
             }
             __syncthreads();
             if (!warp_live) continue;
-            // pair terms summed in FP32 over blocks of 8 sources, each block
+            // pair terms summed in FP32 over blocks of kSumBlock sources, each block
             // added to the tile's (hi, lo) sums by TwoSum, the tile folded into FP64
             float th[TPT][3], tl[TPT][3];
 #pragma unroll
             for (int t = 0; t < TPT; ++t)
                 for (int c = 0; c < 3; ++c) th[t][c] = tl[t][c] = 0.f;
-            for (int q0 = 0; q0 < cnt; q0 += 8) {
-            const int qe = min(cnt, q0 + 8);
+            for (int q0 = 0; q0 < cnt; q0 += kSumBlock) {
+            const int qe = min(cnt, q0 + kSumBlock);
             float u[TPT][3];
 #pragma unroll
             for (int t = 0; t < TPT; ++t) u[t][0] = u[t][1] = u[t][2] = 0.f;
@@ -741,12 +745,12 @@ rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
                 soz[threadIdx.x] = make_float2(-o.z, -o.z);
             }
             __syncthreads();
-            // pair terms summed in FP32 over blocks of 8 sources, each block
+            // pair terms summed in FP32 over blocks of kSumBlock sources, each block
             // added to the tile's (hi, lo) sums by TwoSum, the tile folded
             // into FP64
             float2 hx = bc2(0.f), hy = bc2(0.f), hz = bc2(0.f), lx_ = bc2(0.f), ly_ = bc2(0.f), lz_ = bc2(0.f);
-            for (int q0 = 0; q0 < cnt; q0 += 8) {
-            const int qe = min(cnt, q0 + 8);
+            for (int q0 = 0; q0 < cnt; q0 += kSumBlock) {
+            const int qe = min(cnt, q0 + kSumBlock);
             float2 ux = bc2(0.f), uy = bc2(0.f), uz = bc2(0.f);
 #pragma unroll 2
             for (int q = q0; q < qe; ++q) {
