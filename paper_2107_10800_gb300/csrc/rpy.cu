@@ -701,7 +701,7 @@ __device__ __forceinline__ void pair2(float2 dx, float2 dy, float2 dz, float2 rx
 // (2hz, 2hz, lz, lz), (lx, lx, ly, ly), and the lo parts (-ox, -ox, -oy, -oy),
 // (-oz, -oz) apart, read only for near pairs.
 template <bool WALL>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 5)
 rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
                    const double* __restrict__ lam, double* __restrict__ part,
                    const MvItem* __restrict__ items, int n_items, int* __restrict__ counter,
