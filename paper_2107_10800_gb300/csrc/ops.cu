@@ -1201,6 +1201,51 @@ static int gmres(am_handle* h, const double* rhs, double* x, double tol, bool fp
     return it;
 }
 
+// m2[s] += |u_i|^2 over the blobs of system s, u = M lambda summed from the
+// partials of the last mobility product (a warp whose blobs share one system
+// adds once)
+__global__ void k_sys_mob_norm2(int Nb, const double* __restrict__ part, const int* __restrict__ sys_of_blob,
+                                const int* __restrict__ sys_blob0, const int* __restrict__ sys_nb,
+                                const int* __restrict__ sys_nch, const long long* __restrict__ sys_poff,
+                                double* __restrict__ m2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int s = -1;
+    double v = 0.0;
+    if (i < Nb) {
+        s = sys_of_blob[i];
+        const size_t n3 = 3 * (size_t)sys_nb[s];
+        const double* p = part + sys_poff[s] + 3 * (size_t)(i - sys_blob0[s]);
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int q = 0; q < sys_nch[s]; ++q) { a += p[q * n3]; b += p[q * n3 + 1]; c += p[q * n3 + 2]; }
+        v = a * a + b * b + c * c;
+    }
+    const int s0 = __shfl_sync(0xffffffffu, s, 0);
+    if (__all_sync(0xffffffffu, s == s0)) {
+        v = warp_sum(v);
+        if (lane == 0 && s0 >= 0) atomicAdd(&m2[s0], v);
+    } else if (s >= 0) {
+        atomicAdd(&m2[s], v);
+    }
+}
+
+// The outer residual after a correction dx computed from an accurate
+// residual r (rir): r - A dx = the inner solve's final residual r32 = r -
+// A32 dx (the mixed operator) plus (A32 - A) dx, whose norm is below
+// eps |M32 lambda_dx| (only the pair terms differ).  Per system the decision
+// norm is |r32_s| + eps |M32 lambda_dx|_s; systems that were already within
+// tol (not corrected) keep their norm.
+__global__ void k_sys_resid_bound(int S, double tol, double eps, const double* __restrict__ bn,
+                                  const double* __restrict__ beta32, const double* __restrict__ m2,
+                                  double* __restrict__ be) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double b = bn[s], e = be[s];
+    const double rel = b > 0.0 ? e / b : 0.0;
+    const bool corrected = (rel == rel) && rel < 1e300 && b > 0.0 && rel > tol;
+    if (corrected) be[s] = beta32[s] + eps * sqrt(m2[s]);
+}
+
 int solve(am_handle* h, am_step_stats* st) {
     const double tol = h->cfg.tol;
     const int budget = h->cfg.max_iter;
@@ -1219,13 +1264,24 @@ int solve(am_handle* h, am_step_stats* st) {
         double* bn_out = h->d_sysred;           // ||b_s|| of the outer problem
         double* be_out = h->d_sysred + h->S;    // ||b_s - A x_s|| (double-float operator)
         sys_norms(h, h->d_b, bn_out);
+        // accurate: rir holds b - A x with double-float pair terms.  After a
+        // correction from an accurate residual the next residual is the
+        // inner solve's final mixed residual with an error bound (no
+        // double-float product); after that one, the next is double-float
+        // again, so bound terms never accumulate.
+        bool accurate = false, updated = false;
         for (int outer = 0; outer < 20; ++outer) {
             // The first residual only seeds the first correction, so the
             // mixed operator (error ~1e-7 |b|) computes it unless some system
             // is within 1e-5 of converged; every stopping decision is taken
-            // on a double-float residual.
+            // on a double-float residual or on the bound above.
             bool res64 = outer > 0;
-            sys_residual(h, h->d_b, h->d_x, h->d_rir, be_out, res64 ? kOpDF : kOpHandle);
+            if (updated) {
+                res64 = true;  // rir and be_out were set from the inner solve
+            } else {
+                sys_residual(h, h->d_b, h->d_x, h->d_rir, be_out, res64 ? kOpDF : kOpHandle);
+            }
+            accurate = res64 && !updated;
             k_cycle_init<<<1, 256, 0, s>>>(h->S, h->restart, tol, be_out, bn_out, h->d_active,
                                            h->d_inv_s, h->d_gs, h->d_kdone, h->d_tol_s, h->d_scal);
             count_launch();
@@ -1235,6 +1291,7 @@ int solve(am_handle* h, am_step_stats* st) {
                 read_scal(h, 3);
                 if (h->h_scal[2] < 1e-5 || h->h_scal[1] == 0.0) {
                     res64 = true;
+                    accurate = true;
                     sys_residual(h, h->d_b, h->d_x, h->d_rir, be_out, kOpDF);
                     k_cycle_init<<<1, 256, 0, s>>>(h->S, h->restart, tol, be_out, bn_out, h->d_active,
                                                    h->d_inv_s, h->d_gs, h->d_kdone, h->d_tol_s, h->d_scal);
@@ -1254,6 +1311,20 @@ int solve(am_handle* h, am_step_stats* st) {
             it += gmres(h, h->d_rir, h->d_dx, tin, false, budget - it, &rin, &cycles);
             k_axpy<<<nb, 256, 0, s>>>(h->d_x, h->d_dx, h->n, 1.0);
             count_launch();
+            updated = false;
+            if (accurate && !h->sb) {
+                // gmres ended on sys_residual: V[0] = rir - A32 dx, beta_s its
+                // norms, and the mobility partials hold M32 lambda_dx
+                double* m2 = h->d_sysred + 2 * (size_t)h->S;
+                cudaMemsetAsync(m2, 0, h->S * sizeof(double), s);
+                k_sys_mob_norm2<<<nblk(h->Nb, 256), 256, 0, s>>>(h->Nb, h->d_mv, h->d_sys_of_blob, h->d_sys_blob0,
+                                                                 h->d_sys_nb, h->d_sys_nch, h->d_sys_poff, m2);
+                k_sys_resid_bound<<<nblk(h->S, 128), 128, 0, s>>>(h->S, tol, kMixedProductError, bn_out,
+                                                                  h->d_beta_s, m2, be_out);
+                cudaMemcpyAsync(h->d_rir, h->d_V, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+                count_launch(2);
+                updated = true;
+            }
         }
     }
     if (h->P) {

@@ -9,6 +9,10 @@ constexpr int kFlagWall = 1;        // a blob centre at or below height a
 constexpr int kFlagSingular = 2;    // a body block of M or N~ not SPD
 constexpr int kFlagCorrection = 4;  // correction normal equations not SPD
 constexpr int kFlagTensor = 1 << 8; // a tensor-core (tcgen05) wait timed out (tc_gemm.cuh)
+// Bound on the relative error of the mixed mobility product, |(M32 - M) l|
+// <= kMixedProductError |M32 l| (20 times the largest measured, 4.7e-7 at
+// 60,000 wall blobs against FP64): the bound term of the residual update
+constexpr double kMixedProductError = 1e-5;
 
 // Arithmetic of a mobility product: the handle's precision, FP64,
 // double-float pair terms (rpy_df.cu), or the mixed FP32 pair terms.
