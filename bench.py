@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # colony, from an ncu capture of the bench's own timed steps
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where no capture of
 # the kernel as it now stands exists
-TRAFFIC_BYTES = {"fp64": 201472, "mixed": None}
+TRAFFIC_BYTES = {"fp64": 196864, "mixed": None}
 
 
 def parse():
