@@ -99,3 +99,23 @@ def test_partial_batch_is_an_error():
     s.set_bodies(w["q"], w["theta"], w["blob_offset"], w["rho"], w["F"], w["assembly"], system=0)
     with pytest.raises(binding.AmError):
         s.solve()
+
+
+@pytest.mark.parametrize("precision,tol,bar", [("fp64", 1e-13, 1e-10), ("mixed", 1e-8, 1e-5)])
+def test_many_small_systems(precision, tol, bar):
+    # 300 systems (more than the 256 threads of the loop-control block, so
+    # its per-system loops stride), one short chain each, 2-4 bodies: they
+    # stop at different iterations, so the products skip stopped systems and
+    # the per-system arrival counts of the Arnoldi kernels and (mixed) the
+    # per-system residual bound all see many systems
+    ws = [W.chains_free_space(100 + k, n_chains=1, bodies_per_chain=2 + k % 3) for k in range(300)]
+    s = binding.Solver.from_workloads(ws, tol=tol, precision=precision, max_iter=2000)
+    U, phi, lam, st = s.solve()
+    assert st["status"] == 0 and st["rel_residual"] <= tol
+    for k, (w, (Us, ps, ls)) in enumerate(zip(ws, s.split(U, phi, lam))):
+        if k % 10:  # every tenth system against the oracle's dense solve
+            continue
+        S = System(w)
+        lo, uo, po = S.split(S.solve_dense())
+        assert rel(Us, uo) <= bar, k
+        assert rel(ls, lo) <= bar, k
