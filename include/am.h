@@ -96,7 +96,13 @@ typedef struct {
     int    status;          /* return code of the call                       */
     int    iterations;      /* GMRES iterations (Arnoldi steps)              */
     int    restarts;        /* GMRES cycles started                          */
-    double rel_residual;    /* true ||b - A y||_2 / ||b||_2 at exit          */
+    double rel_residual;    /* ||b - A y||_2 / ||b||_2 at exit: AM_FP64 the
+                               true residual with FP64 products; AM_MIXED
+                               the residual with double-float products, or
+                               after a correction computed from one, an
+                               upper bound of it (the inner mixed residual
+                               plus 1e-5 |M32 lambda_dx|, the mixed
+                               product's error bound)                        */
     double constraint_residual; /* max_n |(C U - B)_n| at exit               */
     double g2_before;       /* ||g*||_2^2 after reconstruction (Sec. 4.3)    */
     double g2_after;        /* ||g||_2^2 at the end of the step              */
