@@ -90,6 +90,21 @@ typedef struct {
                             (Sec. 2.4; free space, AM_FP64); the problem is
                             Eq. linear_system_general on (U, phi) and the
                             blob arguments of am_set_bodies are ignored   */
+    double box[3];       /* all 0: unbounded fluid (free space or wall).
+                            All > 0: triply periodic box [0, Lx) x [0, Ly)
+                            x [0, Lz) with zero mean flow (the periodic
+                            suspensions of Sec. 5.3; here without the
+                            wall): the blob mobility is the RPY tensor
+                            periodised by spectral Ewald summation
+                            (O(N log N)); needs wall = 0, AM_FP64, one
+                            system, multi-blob bodies and every side
+                            longer than 6 a.  Bodies are not wrapped: q
+                            stays continuous, the product wraps blob
+                            centres into the box                         */
+    double ewald_tol;    /* relative accuracy of the periodic product
+                            (1e-14 .. 1e-3); 0 -> 1e-10                 */
+    double ewald_xi;     /* Ewald splitting parameter (1/length); 0 ->
+                            chosen for the least work per product        */
 } am_config;
 
 typedef struct {
@@ -475,6 +490,17 @@ AM_API void am_destroy(am_handle* h);
 
 /* Message of the last error of h, or of the calling thread's last stateless
  * call when h is NULL; never NULL. */
+/* Parameters of a periodic handle's product (after am_set_bodies):
+ * params (6): xi (Ewald splitting), r_c (real-space cutoff), sigma (width
+ *             of the Gaussian of the grid transfer), hx, hy, hz (grid
+ *             spacings);
+ * sizes (6):  Mx, My, Mz (grid points per side), P (Gaussian support in
+ *             points per side), real-space pairs within r_c at the current
+ *             pose (the target itself included), cells of the cell list.
+ * Either pointer may be NULL.  Errors: AM_ERR_ARG for a handle without a
+ * box or without bodies. */
+AM_API int am_periodic_info(am_handle* h, double* params, long long* sizes);
+
 AM_API const char* am_last_error(const am_handle* h);
 
 #ifdef __cplusplus

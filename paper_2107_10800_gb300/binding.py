@@ -33,7 +33,9 @@ class Config(ctypes.Structure):
                 ("n_systems", ctypes.c_int), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("corr_tol", ctypes.c_double), ("corr_max_iter", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p), ("single_blob", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("single_blob", ctypes.c_int),
+                ("box", ctypes.c_double * 3), ("ewald_tol", ctypes.c_double),
+                ("ewald_xi", ctypes.c_double)]
 
 
 class StepStats(ctypes.Structure):
@@ -97,6 +99,7 @@ SIGNATURES = {
     "am_learned_features": (ctypes.c_int, [_vp, _fp, _fp]),
     "am_set_learned": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "am_set_initial_guess": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "am_periodic_info": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "am_destroy": (None, [_vp]),
     "am_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -150,11 +153,13 @@ class Solver:
 
     def __init__(self, eta=1.0, a=0.1, wall=0, precision="fp64", tol=1e-10, restart=50,
                  max_iter=500, corr_tol=1e-10, corr_max_iter=20, stream=None, n_systems=1,
-                 single_blob=False):
+                 single_blob=False, box=None, ewald_tol=0.0, ewald_xi=0.0):
+        """box: (Lx, Ly, Lz) of a triply periodic box, or None (unbounded)."""
         L = lib()
         prec = {"fp64": AM_FP64, "mixed": AM_MIXED}[precision]
+        bx = (ctypes.c_double * 3)(*([0.0, 0.0, 0.0] if box is None else [float(v) for v in box]))
         cfg = Config(eta, a, wall, prec, n_systems, tol, restart, max_iter, corr_tol, corr_max_iter,
-                     stream, 1 if single_blob else 0)
+                     stream, 1 if single_blob else 0, bx, ewald_tol, ewald_xi)
         self.single_blob = bool(single_blob)
         h = _vp()
         rc = L.am_create(ctypes.byref(cfg), ctypes.byref(h))
@@ -317,6 +322,16 @@ class Solver:
         self._check(lib().am_apply_mobility_ex(self.h, lp, up, mode))
         return u.reshape(-1, 3)
 
+    def periodic_info(self):
+        """Parameters of a periodic handle's product (am_periodic_info)."""
+        d = np.empty(6, np.float64)
+        i = np.empty(6, np.int64)
+        self._check(lib().am_periodic_info(self.h, d.ctypes.data_as(_dp),
+                                           i.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))))
+        return {"xi": d[0], "r_c": d[1], "sigma": d[2], "h": tuple(d[3:6]),
+                "grid": tuple(int(v) for v in i[0:3]), "support": int(i[3]),
+                "real_pairs": int(i[4]), "cells": int(i[5])}
+
     def set_repulsion(self, eps, range_, cutoff, eps_wall=0.0, range_wall=1.0):
         """Steric repulsion between articulated bodies and with the wall."""
         self._check(lib().am_set_repulsion(self.h, eps, range_, cutoff, eps_wall, range_wall))
@@ -387,7 +402,10 @@ class Solver:
 
     @classmethod
     def from_workload(cls, w, t=0.0, **kw):
-        """A solver holding one workload dict."""
+        """A solver holding one workload dict (a periodic one when the dict
+        has a "box")."""
+        if w.get("box") is not None and "box" not in kw:
+            kw["box"] = w["box"]
         s = cls(eta=w["eta"], a=w["a"], wall=w["wall"], **kw)
         s.load(w, 0, t)
         return s

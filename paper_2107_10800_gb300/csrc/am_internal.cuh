@@ -129,6 +129,10 @@ __device__ __forceinline__ void quat_from_rotvec(double gx, double gy, double gz
 
 }  // namespace am
 
+namespace am {
+struct PeriodicPlan;  // periodic.cu
+}
+
 // ---- the handle -----------------------------------------------------------
 // Host copy of one system (suspension) as last set by the caller; local body
 // indices.  The device layout concatenates all systems.
@@ -252,6 +256,11 @@ struct am_handle {
 
     // device: mobility partial sums
     double* d_mv = nullptr;
+    // periodic box (cfg.box): spectral Ewald plan, real-space pairs of the
+    // current pose, status of the last binning
+    am::PeriodicPlan* per = nullptr;
+    long long per_nnz = 0;
+    int per_status = 0;
     am::Split split{1, 0, 1};
 
     // device: step

@@ -408,7 +408,14 @@ int check_quats(am_handle* h, int M, const double* theta, const char* who) {
     return AM_OK;
 }
 
+bool box_set(const am_config& c) { return c.box[0] != 0.0 || c.box[1] != 0.0 || c.box[2] != 0.0; }
+
 int device_flags_to_status(am_handle* h, const char* who) {
+    if (h->per_status) {
+        const int rc = h->per_status;
+        h->per_status = 0;
+        return set_err(h, rc, std::string(who) + ": " + h->err);
+    }
     const int f = am::take_flags(h);
     if (f & am::kFlagWall)
         return set_err(h, AM_ERR_WALL_PENETRATION, std::string(who) + ": a blob centre is at or below height a");
@@ -501,6 +508,16 @@ extern "C" AM_API int am_create(const am_config* cfg, am_handle** out) {
         (c.single_blob != 0 && c.single_blob != 1) ||
         (c.single_blob && (c.wall || c.precision != AM_FP64)))
         return AM_ERR_ARG;
+    if (box_set(c)) {
+        // periodic box: every side positive and finite; free space, FP64,
+        // one system of multi-blob bodies
+        for (int d = 0; d < 3; ++d)
+            if (!(c.box[d] > 0.0) || !std::isfinite(c.box[d])) return AM_ERR_ARG;
+        if (c.wall || c.single_blob || c.precision != AM_FP64 || c.n_systems != 1) return AM_ERR_ARG;
+        if (c.ewald_tol == 0.0) c.ewald_tol = 1e-10;
+        if (!(c.ewald_tol >= 1e-14 && c.ewald_tol <= 1e-3) || !(c.ewald_xi >= 0.0) || !std::isfinite(c.ewald_xi))
+            return AM_ERR_ARG;
+    }
     am_handle* h = new am_handle();
     h->cfg = c;
     h->restart = c.restart;
@@ -729,6 +746,10 @@ int build_system_maps(am_handle* h) {
     CK(h2d(h->d_sys_nb, nb.data(), S, st));
     CK(cudaStreamSynchronize(st));
     h->mv_tuned = false;
+    if (box_set(h->cfg)) {
+        const int rc = am::periodic_setup(h);
+        if (rc) return set_err(h, rc, "am_set_bodies: " + h->err);
+    }
     return am::mobility_layout(h, h->cfg.precision == AM_MIXED ? 2 : 1, 0) ? AM_ERR_CUDA : AM_OK;
 }
 
@@ -1000,6 +1021,7 @@ extern "C" AM_API int am_solve(am_handle* h, am_step_stats* stats, double* U, do
 extern "C" AM_API int am_learned_features(am_handle* h, float* X, float* T) {
     if (!h) return AM_ERR_ARG;
     if (!X) return set_err(h, AM_ERR_ARG, "am_learned_features: NULL feature array");
+    if (box_set(h->cfg)) return set_err(h, AM_ERR_ARG, "am_learned_features: not for a periodic box");
     int rc = check_handle(h, "am_learned_features", true);
     if (rc) return rc;
     am::launch_geometry(h);
@@ -1021,6 +1043,7 @@ extern "C" AM_API int am_set_initial_guess(am_handle* h, int order) {
 extern "C" AM_API int am_set_learned(am_handle* h, am_mlp* model, int check) {
     if (!h) return AM_ERR_ARG;
     if (h->sb && model) return set_err(h, AM_ERR_ARG, "am_set_learned: not for single-blob bodies");
+    if (box_set(h->cfg) && model) return set_err(h, AM_ERR_ARG, "am_set_learned: not for a periodic box");
     h->mlp = model;
     h->mlp_check = check != 0;
     return AM_OK;
@@ -1271,6 +1294,8 @@ extern "C" AM_API int am_apply_mobility_ex(am_handle* h, const double* lam, doub
         case AM_DF64: mode = am::kOpDF; break;
         default: return set_err(h, AM_ERR_ARG, "am_apply_mobility_ex: unknown arithmetic");
     }
+    if (box_set(h->cfg) && arithmetic != AM_FP64)
+        return set_err(h, AM_ERR_ARG, "am_apply_mobility_ex: a periodic box has the FP64 product only");
     cudaStream_t s = h->stream;
     am::launch_geometry(h);
     rc = device_flags_to_status(h, "am_apply_mobility_ex");
@@ -1294,6 +1319,8 @@ extern "C" AM_API int am_set_repulsion(am_handle* h, double eps, double range, d
         return set_err(h, AM_ERR_ARG, "am_set_repulsion: need eps, cutoff, eps_wall >= 0 and positive ranges");
     if (eps_wall > 0.0 && !h->cfg.wall)
         return set_err(h, AM_ERR_ARG, "am_set_repulsion: wall repulsion needs a handle with a wall");
+    if (eps > 0.0 && box_set(h->cfg))
+        return set_err(h, AM_ERR_ARG, "am_set_repulsion: not for a periodic box");
     h->st_eps = eps;
     h->st_b = range > 0.0 ? range : 1.0;
     h->st_rc = eps > 0.0 ? cutoff : 0.0;
@@ -1406,6 +1433,7 @@ extern "C" AM_API void am_destroy(am_handle* h) {
     free_links(h);
     free_bodies(h);
     free_solver(h);
+    am::periodic_free(h);
     dfree(&h->d_scal); dfree(&h->d_flags); dfree(&h->d_red); dfree(&h->d_ctrl);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (int k = 0; k < 2; ++k) {
@@ -1420,6 +1448,16 @@ extern "C" AM_API void am_destroy(am_handle* h) {
     for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
+}
+
+extern "C" AM_API int am_periodic_info(am_handle* h, double* params, long long* sizes) {
+    if (!h) return AM_ERR_ARG;
+    if (!box_set(h->cfg)) return set_err(h, AM_ERR_ARG, "am_periodic_info: the handle has no periodic box");
+    const int rc = check_handle(h, "am_periodic_info", true);
+    if (rc) return rc;
+    if (!h->per) return set_err(h, AM_ERR_ARG, "am_periodic_info: no bodies set");
+    am::periodic_info(h, params, sizes);
+    return AM_OK;
 }
 
 extern "C" AM_API const char* am_last_error(const am_handle* h) {

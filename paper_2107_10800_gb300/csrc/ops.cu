@@ -910,6 +910,7 @@ void launch_geometry(am_handle* h) {
         sb_rhs(h);
         return;
     }
+    if (h->per) h->per_status = periodic_bin(h);
     steric_apply(h);
 }
 
@@ -927,8 +928,9 @@ static void mobility_partial(am_handle* h, const double* lam, int mode, const in
     timing_mark(h);
     launch_items(h, lam, mode, active);
     timing_mark(h);
-    long long pairs = 0;
-    for (const auto& r : h->sys) pairs += (long long)r.Nb * r.Nb;
+    long long pairs = h->per_nnz;  // periodic: the real-space pairs
+    if (!h->per)
+        for (const auto& r : h->sys) pairs += (long long)r.Nb * r.Nb;
     h->pairs += pairs;
 }
 

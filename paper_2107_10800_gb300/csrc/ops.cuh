@@ -49,6 +49,16 @@ int df_resident_grid(bool wall);
 void launch_items_df(am_handle* h, const double* lam);
 void launch_sum_items(am_handle* h, double* u);
 int mobility_autotune(am_handle* h);
+// Periodic box (periodic.cu): parameters and buffers for the handle's box,
+// tolerance and blob count; cell list and real-space pair blocks of the
+// current pose (host-synchronising); the product u = M_per lam into d_mv;
+// the chosen parameters (xi, r_c, sigma, hx, hy, hz; Mx, My, Mz, P,
+// real-space pairs, cells).
+int periodic_setup(am_handle* h);
+void periodic_free(am_handle* h);
+int periodic_bin(am_handle* h);
+void launch_periodic(am_handle* h, const double* lam);
+void periodic_info(const am_handle* h, double* d6, long long* i6);
 // Per system, x <- xp + beta_s (x - xp) with beta_s minimising the
 // residual |b - A x| on that line (operator in the handle's precision);
 // returns how many systems have beta_s > 0.  Uses d_w, d_rir, d_z, d_part

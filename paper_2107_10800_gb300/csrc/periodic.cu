@@ -1,0 +1,836 @@
+// Periodic blob mobility: u = M_per lambda for the free-space RPY tensor
+// (Sec. 2.3, Eq. RPY: the Oseen tensor averaged over both blob surfaces)
+// periodised over a box Lx x Ly x Lz with zero mean flow, the periodic
+// boundary conditions of the suspension runs of Sec. 5.3, by spectral Ewald
+// summation in O(N log N) instead of the O(N^2) all-pairs sum.
+//
+// In Fourier space the periodic mobility is sinc^2(ka) (I - khat khat) /
+// (eta k^2) over the nonzero wave vectors of the box.  Ewald's split with
+// Hasimoto's function H(k) = (1 + k^2/(4 xi^2)) exp(-k^2/(4 xi^2)):
+//  - real space: M_RPY(d) - W(d) over pairs closer than r_c (minimum image),
+//    W the R^3 inverse transform of the wave multiplier, W(r) = (A I +
+//    B rhat rhat) / eta with the radial integrals
+//        A = 1/(2 pi^2) int H sinc^2(ka) [(2/3) j0(kr) - j2(kr)/3] dk,
+//        B = 1/(2 pi^2) int H sinc^2(ka) j2(kr) dk,
+//    tabulated in s = r^2 (A and B/s are smooth functions of s) by
+//    Gauss-Legendre quadrature; M_RPY in closed form (rpy_pair.cuh).  The
+//    pair blocks depend on the pose only, so they are formed once per pose
+//    into a sparse block matrix (CSR over the blobs in cell order, 6
+//    doubles per pair) that every product reads;
+//  - wave space: the forces are spread onto a uniform grid with a Gaussian
+//    of width sigma truncated to P x P x P points, transformed (cuFFT, the
+//    three components batched), multiplied by sinc^2(ka) H(k) e^{sigma^2
+//    k^2} (I - khat khat) / (eta k^2) (the Gaussian's transform divided
+//    out twice), transformed back and interpolated at the blobs with the
+//    same Gaussian.  The spreading adds into the grid with FP64 atomics, so
+//    the last bits of the wave part depend on the order of arrival.
+//
+// Parameters from the relative tolerance eps (lg = ln(1/eps)): support
+// P = ceil(0.7 lg + 1.5), sigma / h = 0.3 + 0.055 P, grid spacing h =
+// pi / (2 xi sqrt(lg + ln(1 + lg))) (the wave multiplier below eps beyond
+// the grid's Nyquist wave number), r_c = 2a + sqrt(0.8 lg) / xi (the real
+// part below eps mu0 beyond it); xi minimises a cost model of the product
+// (real-space pairs read against grid points transformed) subject to r_c <=
+// min(L)/3 (three cells per side).  These rules were calibrated against the
+// Ewald sum evaluated to rounding.
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "am_internal.cuh"
+#include "ops.cuh"
+#include "rpy_pair.cuh"
+
+namespace am {
+
+struct PeriodicPlan {
+    double L[3] = {0, 0, 0}, hgrid[3] = {0, 0, 0};
+    double xi = 0, rc = 0, sigma = 0, tol = 0;
+    int Mg[3] = {0, 0, 0}, P = 0, G = 16;  // grid, support, lanes per blob
+    int nc[3] = {0, 0, 0}, ncell = 0;      // cells per side (side >= r_c)
+    int ntab = 0;
+    double ds = 0;                          // table step in s = r^2
+    long long ngrid = 0, nhat = 0;          // real points, half-spectrum points
+    int Nb = 0;
+    // device
+    double2* d_tab = nullptr;               // (A(s), B(s)/s)
+    int* d_cell_start = nullptr;            // ncell + 1
+    int* d_cell_fill = nullptr;             // ncell
+    int* d_cell_of = nullptr;               // Nb
+    int* d_order = nullptr;                 // sorted position -> blob
+    double4_32a* d_spos = nullptr;          // sorted wrapped positions
+    float4* d_sposf = nullptr;              // the same in FP32 (cut test)
+    long long* d_row = nullptr;             // Nb + 1 CSR offsets
+    int* d_nbr = nullptr;                   // neighbour blob indices
+    double* d_blk = nullptr;                // 6 x cap pair blocks (SoA)
+    long long cap = 0, nnz = 0;
+    long long* d_scan = nullptr;            // scan scratch
+    double* d_grid = nullptr;               // 3 x ngrid
+    cufftDoubleComplex* d_hat = nullptr;    // 3 x nhat
+    double2* d_kfac = nullptr;              // (fac, fac / k^2) per half-spectrum point
+    cufftHandle fwd = 0, inv = 0;
+    bool planned = false;
+    bool valid = false;  // pair blocks of the current pose are in place
+};
+
+namespace {
+
+constexpr int kTab = 16384;  // table nodes over [0, r_c^2]
+constexpr int kScanBlock = 1024;
+
+// ---- radial functions of the wave part (own series and closed forms) ----
+// j2(x) / x^2 = sum_n (-x^2/2)^n / (n! (2n+5)!!)
+__device__ __forceinline__ double j2_over_x2(double x) {
+    if (x < 1.0) {
+        const double y = -0.5 * x * x;
+        double term = 1.0 / 15.0, sum = term;
+        for (int n = 1; n < 10; ++n) {
+            term *= y / ((double)n * (double)(2 * n + 5));
+            sum += term;
+        }
+        return sum;
+    }
+    double s, c;
+    sincos(x, &s, &c);
+    const double xi = 1.0 / x;
+    return ((3.0 * xi * xi - 1.0) * s * xi - 3.0 * c * xi * xi) * xi * xi;
+}
+
+__device__ __forceinline__ double j0f(double x) {
+    if (x < 1e-3) return 1.0 - x * x / 6.0 + x * x * x * x / 120.0;
+    return sin(x) / x;
+}
+
+// Table node t: s = t ds; A(s) and B(s)/s by the quadrature rule (nodes k_q,
+// weights already times H(k_q) sinc^2(k_q a) / (2 pi^2)).
+__global__ void k_per_table(int ntab, double ds, const double* __restrict__ kq, const double* __restrict__ wq,
+                            int nq, double2* __restrict__ tab) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntab) return;
+    const double r = sqrt(t * ds);
+    double A = 0.0, Bs = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        const double k = kq[q], x = k * r;
+        const double q2 = j2_over_x2(x);
+        const double j2 = x * x * q2;
+        A = fma(wq[q], (2.0 / 3.0) * j0f(x) - j2 / 3.0, A);
+        Bs = fma(wq[q] * k * k, q2, Bs);
+    }
+    tab[t] = make_double2(A, Bs);
+}
+
+// cubic Lagrange interpolation of the table at s (4 nodes around s)
+__device__ __forceinline__ double2 tab_at(const double2* __restrict__ tab, int ntab, double inv_ds, double s) {
+    const double u = s * inv_ds;
+    int i = (int)u - 1;
+    i = max(0, min(i, ntab - 4));
+    const double t = u - (double)i;  // in [0, 3] up to the ends
+    const double w0 = -(t - 1.0) * (t - 2.0) * (t - 3.0) / 6.0;
+    const double w1 = t * (t - 2.0) * (t - 3.0) / 2.0;
+    const double w2 = -t * (t - 1.0) * (t - 3.0) / 2.0;
+    const double w3 = t * (t - 1.0) * (t - 2.0) / 6.0;
+    const double2 a = tab[i], b = tab[i + 1], c = tab[i + 2], d = tab[i + 3];
+    return make_double2(w0 * a.x + w1 * b.x + w2 * c.x + w3 * d.x, w0 * a.y + w1 * b.y + w2 * c.y + w3 * d.y);
+}
+
+// Wave multiplier per half-spectrum point (cuFFT D2Z layout of a Mz x My x
+// Mx grid: index (iz My + iy)(Mx/2 + 1) + ix), with the normalisation of the
+// spread -> forward -> inverse -> interpolate chain, hx hy hz / (Mx My Mz),
+// and zero at k = 0 and on the Nyquist planes of even sizes.
+__global__ void k_per_kfac(int Mx, int My, int Mz, double Lx, double Ly, double Lz, double a, double eta,
+                           double xi, double sigma, double2* __restrict__ kfac) {
+    const long long Mxh = Mx / 2 + 1;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= Mxh * My * Mz) return;
+    const int ix = (int)(q % Mxh), iy = (int)((q / Mxh) % My), iz = (int)(q / (Mxh * My));
+    const int mx = ix, my = iy <= My / 2 ? iy : iy - My, mz = iz <= Mz / 2 ? iz : iz - Mz;
+    const bool nyq = (Mx % 2 == 0 && 2 * ix == Mx) || (My % 2 == 0 && 2 * iy == My) || (Mz % 2 == 0 && 2 * iz == Mz);
+    const double kx = 2.0 * kPi * mx / Lx, ky = 2.0 * kPi * my / Ly, kz = 2.0 * kPi * mz / Lz;
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    if (k2 == 0.0 || nyq) {
+        kfac[q] = make_double2(0.0, 0.0);
+        return;
+    }
+    const double k = sqrt(k2), ka = k * a;
+    const double sinc = ka < 1e-4 ? 1.0 - ka * ka / 6.0 : sin(ka) / ka;
+    const double x = k2 / (4.0 * xi * xi);
+    const double norm = (Lx / Mx) * (Ly / My) * (Lz / Mz) / ((double)Mx * (double)My * (double)Mz);
+    const double fac = norm / eta * sinc * sinc * (1.0 + x) * exp(-x + sigma * sigma * k2) / k2;
+    kfac[q] = make_double2(fac, fac / k2);
+}
+
+// ---- cell list ------------------------------------------------------------
+__device__ __forceinline__ double wrap1(double x, double L) {
+    double w = x - L * floor(x / L);
+    if (w >= L) w -= L;
+    if (w < 0.0) w = 0.0;
+    return w;
+}
+
+__global__ void k_per_cell(int Nb, const double4_32a* __restrict__ r4, double Lx, double Ly, double Lz, int ncx,
+                           int ncy, int ncz, int* __restrict__ cell_of, int* __restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nb) return;
+    const double4_32a p = r4[i];
+    const double x = wrap1(p.x, Lx), y = wrap1(p.y, Ly), z = wrap1(p.z, Lz);
+    const int cx = min((int)(x / Lx * ncx), ncx - 1);
+    const int cy = min((int)(y / Ly * ncy), ncy - 1);
+    const int cz = min((int)(z / Lz * ncz), ncz - 1);
+    const int c = (cz * ncy + cy) * ncx + cx;
+    cell_of[i] = c;
+    atomicAdd(&cnt[c], 1);
+}
+
+// exclusive scan of n counts (int or long long) into out (long long or int),
+// three passes: block sums, a one-block scan of them, block offsets
+template <class Tin>
+__global__ void k_scan_blocks(const Tin* __restrict__ in, int n, long long* __restrict__ bsum) {
+    __shared__ long long sh[32];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    long long v = i < n ? (long long)in[i] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        long long w = sh[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = w;
+    }
+}
+
+__global__ void k_scan_sums(long long* __restrict__ bsum, int nb) {
+    // one block of kScanBlock threads; nb block sums, exclusive in place
+    __shared__ long long sh[kScanBlock];
+    long long carry = 0;
+    for (int base = 0; base < nb; base += kScanBlock) {
+        const int i = base + threadIdx.x;
+        const long long v = i < nb ? bsum[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < kScanBlock; o <<= 1) {
+            const long long add = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        carry += sh[kScanBlock - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+template <class Tin, class Tout>
+__global__ void k_scan_apply(const Tin* __restrict__ in, int n, const long long* __restrict__ bsum,
+                             Tout* __restrict__ out) {
+    __shared__ long long sh[kScanBlock];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    const long long v = i < n ? (long long)in[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kScanBlock; o <<= 1) {
+        const long long add = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += add;
+        __syncthreads();
+    }
+    if (i < n) out[i] = (Tout)(bsum[blockIdx.x] + sh[threadIdx.x] - v);
+    if (i == n - 1) out[n] = (Tout)(bsum[blockIdx.x] + sh[threadIdx.x]);
+}
+
+// out[0..n] = exclusive scan of in[0..n) with the total in out[n]
+template <class Tin, class Tout>
+void exclusive_scan(const Tin* in, int n, Tout* out, long long* scratch, cudaStream_t s) {
+    const int nb = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_blocks<Tin><<<nb, kScanBlock, 0, s>>>(in, n, scratch);
+    k_scan_sums<<<1, kScanBlock, 0, s>>>(scratch, nb);
+    k_scan_apply<Tin, Tout><<<nb, kScanBlock, 0, s>>>(in, n, scratch, out);
+    count_launch(3);
+}
+
+__global__ void k_per_fill(int Nb, const int* __restrict__ cell_of, const int* __restrict__ start,
+                           int* __restrict__ fill, int* __restrict__ order) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nb) return;
+    const int c = cell_of[i];
+    order[start[c] + atomicAdd(&fill[c], 1)] = i;
+}
+
+// blobs of each cell in index order (the fill order depends on arrival), and
+// the sorted wrapped positions
+__global__ void k_per_sort_cells(int ncell, const int* __restrict__ start, int* __restrict__ order) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int b = start[c], e = start[c + 1];
+    for (int i = b + 1; i < e; ++i) {
+        const int v = order[i];
+        int j = i - 1;
+        while (j >= b && order[j] > v) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = v;
+    }
+}
+
+__global__ void k_per_gather_pos(int Nb, const int* __restrict__ order, const double4_32a* __restrict__ r4,
+                                 double Lx, double Ly, double Lz, double4_32a* __restrict__ spos,
+                                 float4* __restrict__ sposf) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Nb) return;
+    const double4_32a r = r4[order[p]];
+    double4_32a w;
+    w.x = wrap1(r.x, Lx); w.y = wrap1(r.y, Ly); w.z = wrap1(r.z, Lz); w.w = 0.0;
+    spos[p] = w;
+    sposf[p] = make_float4((float)w.x, (float)w.y, (float)w.z, 0.f);
+}
+
+// Neighbour cell k (0..26) of the cell of (x, y, z): its index and the shift
+// that brings its blobs next to the target (target - shift is compared).
+struct CellGeom {
+    int nc[3];
+    double L[3];
+};
+
+__device__ __forceinline__ int neighbour_cell(const CellGeom& g, int cx, int cy, int cz, int k, double& sx,
+                                              double& sy, double& sz) {
+    int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+    int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+    sx = sy = sz = 0.0;
+    if (nx < 0) { nx += g.nc[0]; sx = -g.L[0]; } else if (nx >= g.nc[0]) { nx -= g.nc[0]; sx = g.L[0]; }
+    if (ny < 0) { ny += g.nc[1]; sy = -g.L[1]; } else if (ny >= g.nc[1]) { ny -= g.nc[1]; sy = g.L[1]; }
+    if (nz < 0) { nz += g.nc[2]; sz = -g.L[2]; } else if (nz >= g.nc[2]) { nz -= g.nc[2]; sz = g.L[2]; }
+    return (nz * g.nc[1] + ny) * g.nc[0] + nx;
+}
+
+__device__ __forceinline__ void cell_coords(const CellGeom& g, double x, double y, double z, int& cx, int& cy,
+                                            int& cz) {
+    cx = min((int)(x / g.L[0] * g.nc[0]), g.nc[0] - 1);
+    cy = min((int)(y / g.L[1] * g.nc[1]), g.nc[1] - 1);
+    cz = min((int)(z / g.L[2] * g.nc[2]), g.nc[2] - 1);
+}
+
+// Pairs of sorted target p within r_c (FP32 test, the same in both passes):
+// count, or write the neighbour blob indices and FP64 pair blocks
+// M_RPY(d) - W(d) = alpha I + beta d d^T in the order of the 27 cells.
+template <bool WRITE>
+__global__ void k_per_pairs(int Nb, CellGeom g, const double4_32a* __restrict__ spos,
+                            const float4* __restrict__ sposf, const int* __restrict__ start,
+                            const int* __restrict__ order, float rc2f, long long* __restrict__ row,
+                            int* __restrict__ nbr, double* __restrict__ blk, long long cap,
+                            const double2* __restrict__ tab, int ntab, double inv_ds, RpyK<double> k,
+                            double inv_eta) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Nb) return;
+    const double4_32a x = spos[p];
+    const float4 xf = sposf[p];
+    int cx, cy, cz;
+    cell_coords(g, x.x, x.y, x.z, cx, cy, cz);
+    long long out = WRITE ? row[p] : 0;
+    int count = 0;
+    for (int kc = 0; kc < 27; ++kc) {
+        double sx, sy, sz;
+        const int c = neighbour_cell(g, cx, cy, cz, kc, sx, sy, sz);
+        const float tx = xf.x - (float)sx, ty = xf.y - (float)sy, tz = xf.z - (float)sz;
+        for (int q = start[c]; q < start[c + 1]; ++q) {
+            const float4 yf = sposf[q];
+            const float dxf = tx - yf.x, dyf = ty - yf.y, dzf = tz - yf.z;
+            if (fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf)) >= rc2f) continue;
+            if (!WRITE) {
+                ++count;
+                continue;
+            }
+            if (out >= cap) continue;  // guarded: cap is the counted total
+            const double4_32a y = spos[q];
+            const double dx = (x.x - sx) - y.x, dy = (x.y - sy) - y.y, dz = (x.z - sz) - y.z;
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            double c1, c2;
+            free_coefs<double>(r2, k, c1, c2);
+            const double2 w = tab_at(tab, ntab, inv_ds, r2);
+            const double al = k.A1 * c1 - w.x * inv_eta;
+            const double be = k.A1 * c2 - w.y * inv_eta;
+            nbr[out] = order[q];
+            blk[out] = fma(be, dx * dx, al);
+            blk[cap + out] = be * dx * dy;
+            blk[2 * cap + out] = be * dx * dz;
+            blk[3 * cap + out] = fma(be, dy * dy, al);
+            blk[4 * cap + out] = be * dy * dz;
+            blk[5 * cap + out] = fma(be, dz * dz, al);
+            ++out;
+        }
+    }
+    if (!WRITE) row[p] = count;
+}
+
+__global__ void k_per_zero(double* __restrict__ g, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        g[i] = 0.0;
+}
+
+// Gaussian weights of lane l (< P) along one axis: grid index i0 + l and
+// exp(-t^2 / (2 sigma^2)) (2 pi sigma^2)^(-1/2), t = (i0 + l) h - x
+struct SpreadGeom {
+    int M[3], P;
+    double h[3], inv2s2, c1;
+};
+
+__device__ __forceinline__ void axis_weight(double x, int d, const SpreadGeom& g, int lane, int& idx, double& w) {
+    const int i0 = (int)ceil(x / g.h[d] - 0.5 * g.P);
+    int i = i0 + lane;
+    const double t = (double)i * g.h[d] - x;
+    w = g.c1 * exp(-t * t * g.inv2s2);
+    if (i < 0) i += g.M[d]; else if (i >= g.M[d]) i -= g.M[d];
+    idx = i;
+}
+
+// Spread: a group of G lanes per blob (sorted order); lane l owns the grid
+// column x = i0x + l and walks the P x P (y, z) points.
+__global__ void __launch_bounds__(256)
+k_per_spread(int Nb, SpreadGeom g, int G, const double4_32a* __restrict__ spos, const int* __restrict__ order,
+             const double* __restrict__ lam, double* __restrict__ grid, long long ngrid) {
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int lane = threadIdx.x % G;
+    const bool live = gid < Nb;
+    const int p = live ? gid : Nb - 1;
+    const double4_32a x = spos[p];
+    const int i = order[p];
+    const double lx = lam[3 * (size_t)i], ly = lam[3 * (size_t)i + 1], lz = lam[3 * (size_t)i + 2];
+    int ix = 0, iy = 0, iz = 0;
+    double wx = 0.0, wy = 0.0, wz = 0.0;
+    if (lane < g.P) {
+        axis_weight(x.x, 0, g, lane, ix, wx);
+        axis_weight(x.y, 1, g, lane, iy, wy);
+        axis_weight(x.z, 2, g, lane, iz, wz);
+    }
+    const unsigned mask = 0xffffffffu;
+    for (int pz = 0; pz < g.P; ++pz) {
+        const double wzz = __shfl_sync(mask, wz, pz, G);
+        const int zz = __shfl_sync(mask, iz, pz, G);
+        for (int py = 0; py < g.P; ++py) {
+            const double wyz = __shfl_sync(mask, wy, py, G) * wzz;
+            const int yy = __shfl_sync(mask, iy, py, G);
+            if (live && lane < g.P) {
+                const double w = wx * wyz;
+                const long long idx = ((long long)zz * g.M[1] + yy) * g.M[0] + ix;
+                atomicAdd(grid + idx, w * lx);
+                atomicAdd(grid + ngrid + idx, w * ly);
+                atomicAdd(grid + 2 * ngrid + idx, w * lz);
+            }
+        }
+    }
+}
+
+// f_hat <- fac (f_hat - k (k . f_hat) / k^2) on the half spectrum
+__global__ void k_per_kmul(int Mx, int My, int Mz, double Lx, double Ly, double Lz,
+                           const double2* __restrict__ kfac, cufftDoubleComplex* __restrict__ hat, long long nhat) {
+    const long long Mxh = Mx / 2 + 1;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= nhat) return;
+    const double2 f = kfac[q];
+    cufftDoubleComplex* h0 = hat + q;
+    cufftDoubleComplex* h1 = hat + nhat + q;
+    cufftDoubleComplex* h2 = hat + 2 * nhat + q;
+    if (f.x == 0.0) {
+        *h0 = make_double2(0.0, 0.0); *h1 = make_double2(0.0, 0.0); *h2 = make_double2(0.0, 0.0);
+        return;
+    }
+    const int ix = (int)(q % Mxh), iy = (int)((q / Mxh) % My), iz = (int)(q / (Mxh * My));
+    const int mx = ix, my = iy <= My / 2 ? iy : iy - My, mz = iz <= Mz / 2 ? iz : iz - Mz;
+    const double kx = 2.0 * kPi * mx / Lx, ky = 2.0 * kPi * my / Ly, kz = 2.0 * kPi * mz / Lz;
+    const cufftDoubleComplex a = *h0, b = *h1, c = *h2;
+    const double dr = kx * a.x + ky * b.x + kz * c.x, di = kx * a.y + ky * b.y + kz * c.y;
+    *h0 = make_double2(f.x * a.x - f.y * kx * dr, f.x * a.y - f.y * kx * di);
+    *h1 = make_double2(f.x * b.x - f.y * ky * dr, f.x * b.y - f.y * ky * di);
+    *h2 = make_double2(f.x * c.x - f.y * kz * dr, f.x * c.y - f.y * kz * di);
+}
+
+// u_i = sum over its CSR row of the pair blocks times lambda_j (real space)
+// + the Gaussian interpolation of the wave-space field at r_i; a group of G
+// lanes per blob, sums in a fixed order (lane-strided rows, then a shuffle
+// tree).
+__global__ void __launch_bounds__(256)
+k_per_gather(int Nb, SpreadGeom g, int G, const double4_32a* __restrict__ spos, const int* __restrict__ order,
+             const long long* __restrict__ row, const int* __restrict__ nbr, const double* __restrict__ blk,
+             long long cap, const double* __restrict__ lam, const double* __restrict__ grid, long long ngrid,
+             double* __restrict__ out) {
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int lane = threadIdx.x % G;
+    const bool live = gid < Nb;
+    const int p = live ? gid : Nb - 1;
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    if (live) {
+        for (long long e = row[p] + lane; e < row[p + 1]; e += G) {
+            const int j = nbr[e];
+            const double lx = lam[3 * (size_t)j], ly = lam[3 * (size_t)j + 1], lz = lam[3 * (size_t)j + 2];
+            const double m00 = blk[e], m01 = blk[cap + e], m02 = blk[2 * cap + e];
+            const double m11 = blk[3 * cap + e], m12 = blk[4 * cap + e], m22 = blk[5 * cap + e];
+            ux = fma(m00, lx, fma(m01, ly, fma(m02, lz, ux)));
+            uy = fma(m01, lx, fma(m11, ly, fma(m12, lz, uy)));
+            uz = fma(m02, lx, fma(m12, ly, fma(m22, lz, uz)));
+        }
+    }
+    const double4_32a x = spos[p];
+    int ix = 0, iy = 0, iz = 0;
+    double wx = 0.0, wy = 0.0, wz = 0.0;
+    if (lane < g.P) {
+        axis_weight(x.x, 0, g, lane, ix, wx);
+        axis_weight(x.y, 1, g, lane, iy, wy);
+        axis_weight(x.z, 2, g, lane, iz, wz);
+    }
+    const unsigned mask = 0xffffffffu;
+    double vx = 0.0, vy = 0.0, vz = 0.0;
+    for (int pz = 0; pz < g.P; ++pz) {
+        const double wzz = __shfl_sync(mask, wz, pz, G);
+        const int zz = __shfl_sync(mask, iz, pz, G);
+        for (int py = 0; py < g.P; ++py) {
+            const double wyz = __shfl_sync(mask, wy, py, G) * wzz;
+            const int yy = __shfl_sync(mask, iy, py, G);
+            if (lane < g.P) {
+                const long long idx = ((long long)zz * g.M[1] + yy) * g.M[0] + ix;
+                const double w = wx * wyz;
+                vx = fma(w, __ldg(grid + idx), vx);
+                vy = fma(w, __ldg(grid + ngrid + idx), vy);
+                vz = fma(w, __ldg(grid + 2 * ngrid + idx), vz);
+            }
+        }
+    }
+    ux += vx; uy += vy; uz += vz;
+    for (int o = G / 2; o > 0; o >>= 1) {
+        ux += __shfl_xor_sync(mask, ux, o, G);
+        uy += __shfl_xor_sync(mask, uy, o, G);
+        uz += __shfl_xor_sync(mask, uz, o, G);
+    }
+    if (live && lane == 0) {
+        const int i = order[p];
+        out[3 * (size_t)i] = ux;
+        out[3 * (size_t)i + 1] = uy;
+        out[3 * (size_t)i + 2] = uz;
+    }
+}
+
+// ---- host ------------------------------------------------------------------
+int fft_size(int n) {  // smallest 2-3-5-7-smooth size >= n
+    for (;; ++n) {
+        int m = n;
+        for (int f : {2, 3, 5, 7})
+            while (m % f == 0) m /= f;
+        if (m == 1) return n;
+    }
+}
+
+// 20-point Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_20)
+void gauss_legendre20(double* x, double* w) {
+    const int n = 20;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+void free_plan(PeriodicPlan* p) {
+    if (!p) return;
+    if (p->planned) {
+        cufftDestroy(p->fwd);
+        cufftDestroy(p->inv);
+    }
+    void* ptrs[] = {p->d_tab, p->d_cell_start, p->d_cell_fill, p->d_cell_of, p->d_order, p->d_spos,
+                    p->d_sposf, p->d_row, p->d_nbr, p->d_blk, p->d_scan, p->d_grid, p->d_hat, p->d_kfac};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+template <class T>
+bool dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T)) == cudaSuccess;
+}
+
+SpreadGeom spread_geom(const PeriodicPlan* p) {
+    SpreadGeom g;
+    for (int d = 0; d < 3; ++d) {
+        g.M[d] = p->Mg[d];
+        g.h[d] = p->hgrid[d];
+    }
+    g.P = p->P;
+    g.inv2s2 = 1.0 / (2.0 * p->sigma * p->sigma);
+    g.c1 = std::pow(2.0 * kPi * p->sigma * p->sigma, -0.5);
+    return g;
+}
+
+CellGeom cell_geom(const PeriodicPlan* p) {
+    CellGeom g;
+    for (int d = 0; d < 3; ++d) {
+        g.nc[d] = p->nc[d];
+        g.L[d] = p->L[d];
+    }
+    return g;
+}
+
+}  // namespace
+
+void periodic_free(am_handle* h) {
+    free_plan(h->per);
+    h->per = nullptr;
+    h->per_nnz = 0;
+}
+
+// Parameters and buffers for the handle's box, tolerance and blob count.
+int periodic_setup(am_handle* h) {
+    periodic_free(h);
+    const double a = h->cfg.blob_radius, eta = h->cfg.eta;
+    const double tol = h->cfg.ewald_tol > 0.0 ? h->cfg.ewald_tol : 1e-10;
+    const int Nb = h->Nb;
+    PeriodicPlan* p = new PeriodicPlan();
+    h->per = p;
+    p->Nb = Nb;
+    p->tol = tol;
+    for (int d = 0; d < 3; ++d) p->L[d] = h->cfg.box[d];
+    const double lg = std::log(1.0 / tol);
+    p->P = std::min(32, std::max(4, (int)std::ceil(0.7 * lg + 1.5)));
+    p->G = p->P <= 16 ? 16 : 32;
+    const double xN = lg + std::log1p(lg), crc = std::sqrt(0.8 * lg);
+    const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
+    if (!(Lmin / 3.0 > 2.0 * a * 1.01)) {
+        h->err = "periodic box: every side must exceed 6 blob radii";
+        return AM_ERR_ARG;
+    }
+    const double xi_lo = crc / (Lmin / 3.0 - 2.0 * a);
+    const double V = p->L[0] * p->L[1] * p->L[2], dens = Nb / V;
+    auto grid_for = [&](double xi, int* M) {
+        const double hmax = kPi / (2.0 * xi * std::sqrt(xN));
+        long long tot = 1;
+        for (int d = 0; d < 3; ++d) {
+            M[d] = fft_size(std::max(p->P + 1, (int)std::ceil(p->L[d] / hmax)));
+            tot *= M[d];
+        }
+        return tot;
+    };
+    double xi = h->cfg.ewald_xi;
+    if (xi > 0.0) {
+        if (xi < xi_lo) {
+            h->err = "periodic box: ewald_xi too small for the box (r_c would exceed a third of a side)";
+            return AM_ERR_ARG;
+        }
+    } else {
+        // cost per product: real-space pairs (52 bytes each) against grid
+        // points (about 340 bytes of transform traffic each)
+        double best = 1e300;
+        for (int t = 0; t < 96; ++t) {
+            const double x = xi_lo * std::pow(2.0, t / 8.0);
+            int M[3];
+            const long long tot = grid_for(x, M);
+            if (tot > (1LL << 31)) break;
+            const double rc = 2.0 * a + crc / x;
+            const double pairs = (double)Nb * (1.0 + dens * 4.0 / 3.0 * kPi * rc * rc * rc);
+            const double cost = 52.0 * pairs + 340.0 * (double)tot;
+            if (cost < best) {
+                best = cost;
+                xi = x;
+            }
+        }
+        if (!(xi > 0.0)) {
+            h->err = "periodic box: no grid fits (box too large for the blob radius and tolerance)";
+            return AM_ERR_ARG;
+        }
+    }
+    p->xi = xi;
+    p->rc = 2.0 * a + crc / xi;
+    p->ngrid = grid_for(xi, p->Mg);
+    for (int d = 0; d < 3; ++d) p->hgrid[d] = p->L[d] / p->Mg[d];
+    p->nhat = (long long)(p->Mg[0] / 2 + 1) * p->Mg[1] * p->Mg[2];
+    const double hmin = std::min(p->hgrid[0], std::min(p->hgrid[1], p->hgrid[2]));
+    p->sigma = (0.3 + 0.055 * p->P) * hmin;
+    if (p->sigma * xi >= 0.5) p->sigma = 0.49 / xi;  // keep e^{sigma^2 k^2 - k^2/(4 xi^2)} decaying
+    for (int d = 0; d < 3; ++d) p->nc[d] = std::max(3, (int)std::floor(p->L[d] / p->rc));
+    p->ncell = p->nc[0] * p->nc[1] * p->nc[2];
+    p->ntab = kTab;
+    p->ds = p->rc * p->rc * 1.001 / (kTab - 3);
+
+    const int nscan = (std::max(Nb, p->ncell) + kScanBlock - 1) / kScanBlock + 1;
+    bool ok = dalloc(&p->d_tab, p->ntab) && dalloc(&p->d_cell_start, p->ncell + 1) &&
+              dalloc(&p->d_cell_fill, p->ncell) && dalloc(&p->d_cell_of, Nb) && dalloc(&p->d_order, Nb) &&
+              dalloc(&p->d_spos, Nb) && dalloc(&p->d_sposf, Nb) && dalloc(&p->d_row, Nb + 1) &&
+              dalloc(&p->d_scan, nscan) && dalloc(&p->d_grid, 3 * (size_t)p->ngrid) &&
+              dalloc(&p->d_hat, 3 * (size_t)p->nhat) && dalloc(&p->d_kfac, p->nhat);
+    if (!ok) {
+        cudaGetLastError();
+        h->err = "periodic mobility: device allocation failed";
+        return AM_ERR_CUDA;
+    }
+    int n3[3] = {p->Mg[2], p->Mg[1], p->Mg[0]};
+    if (cufftPlanMany(&p->fwd, 3, n3, nullptr, 1, 0, nullptr, 1, 0, CUFFT_D2Z, 3) != CUFFT_SUCCESS) {
+        h->err = "periodic mobility: cuFFT plan failed";
+        return AM_ERR_CUDA;
+    }
+    if (cufftPlanMany(&p->inv, 3, n3, nullptr, 1, 0, nullptr, 1, 0, CUFFT_Z2D, 3) != CUFFT_SUCCESS) {
+        cufftDestroy(p->fwd);
+        h->err = "periodic mobility: cuFFT plan failed";
+        return AM_ERR_CUDA;
+    }
+    p->planned = true;
+    cufftSetStream(p->fwd, h->stream);
+    cufftSetStream(p->inv, h->stream);
+
+    // quadrature of the wave part's radial integrals: 20-point panels, four
+    // per oscillation period of the integrand, up to k = 2 xi sqrt(50)
+    double gx[20], gw[20];
+    gauss_legendre20(gx, gw);
+    const double kmax = 2.0 * xi * std::sqrt(50.0);
+    const double span = std::max(p->rc * 1.001, 2.0 * a);
+    const int panels = std::max(64, (int)std::ceil(4.0 * kmax * span / (2.0 * kPi)));
+    std::vector<double> kq, wq;
+    kq.reserve(20 * panels);
+    wq.reserve(20 * panels);
+    for (int pn = 0; pn < panels; ++pn) {
+        const double k0 = kmax * pn / panels, k1 = kmax * (pn + 1) / panels;
+        const double mid = 0.5 * (k0 + k1), half = 0.5 * (k1 - k0);
+        for (int i = 0; i < 20; ++i) {
+            const double k = mid + half * gx[i];
+            const double x = k * k / (4.0 * xi * xi);
+            const double ka = k * a;
+            const double sinc = ka < 1e-4 ? 1.0 - ka * ka / 6.0 : std::sin(ka) / ka;
+            kq.push_back(k);
+            wq.push_back(half * gw[i] * (1.0 + x) * std::exp(-x) * sinc * sinc / (2.0 * kPi * kPi));
+        }
+    }
+    double *d_kq = nullptr, *d_wq = nullptr;
+    cudaStream_t s = h->stream;
+    if (!dalloc(&d_kq, kq.size()) || !dalloc(&d_wq, wq.size())) {
+        if (d_kq) cudaFree(d_kq);
+        h->err = "periodic mobility: device allocation failed";
+        return AM_ERR_CUDA;
+    }
+    cudaMemcpyAsync(d_kq, kq.data(), kq.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_wq, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    k_per_table<<<(p->ntab + 127) / 128, 128, 0, s>>>(p->ntab, p->ds, d_kq, d_wq, (int)kq.size(), p->d_tab);
+    k_per_kfac<<<(int)((p->nhat + 255) / 256), 256, 0, s>>>(p->Mg[0], p->Mg[1], p->Mg[2], p->L[0], p->L[1],
+                                                            p->L[2], a, eta, xi, p->sigma, p->d_kfac);
+    count_launch(2);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(d_kq);
+    cudaFree(d_wq);
+    if (e != cudaSuccess) {
+        h->err = "periodic mobility: setup kernels failed";
+        return AM_ERR_CUDA;
+    }
+    return AM_OK;
+}
+
+// Cell list and real-space pair blocks at the current blob positions
+// (h->d_r4); called with every pose (launch_geometry).
+int periodic_bin(am_handle* h) {
+    PeriodicPlan* p = h->per;
+    if (!p) return AM_ERR_ARG;
+    cudaStream_t s = h->stream;
+    const int Nb = p->Nb;
+    const int nbk = (Nb + 255) / 256;
+    p->valid = false;
+    cudaMemsetAsync(p->d_cell_fill, 0, p->ncell * sizeof(int), s);
+    k_per_cell<<<nbk, 256, 0, s>>>(Nb, h->d_r4, p->L[0], p->L[1], p->L[2], p->nc[0], p->nc[1], p->nc[2],
+                                   p->d_cell_of, p->d_cell_fill);
+    count_launch();
+    exclusive_scan<int, int>(p->d_cell_fill, p->ncell, p->d_cell_start, p->d_scan, s);
+    cudaMemsetAsync(p->d_cell_fill, 0, p->ncell * sizeof(int), s);
+    k_per_fill<<<nbk, 256, 0, s>>>(Nb, p->d_cell_of, p->d_cell_start, p->d_cell_fill, p->d_order);
+    k_per_sort_cells<<<(p->ncell + 127) / 128, 128, 0, s>>>(p->ncell, p->d_cell_start, p->d_order);
+    k_per_gather_pos<<<nbk, 256, 0, s>>>(Nb, p->d_order, h->d_r4, p->L[0], p->L[1], p->L[2], p->d_spos,
+                                         p->d_sposf);
+    count_launch(3);
+    const CellGeom cg = cell_geom(p);
+    const RpyK<double> k = rpy_consts<double>(h->prm);
+    const float rc2f = (float)(p->rc * p->rc);
+    // count, scan, then write the pair blocks
+    k_per_pairs<false><<<nbk, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_sposf, p->d_cell_start, p->d_order, rc2f,
+                                           p->d_row, nullptr, nullptr, 0, p->d_tab, p->ntab, 1.0 / p->ds, k,
+                                           1.0 / h->cfg.eta);
+    count_launch();
+    exclusive_scan<long long, long long>(p->d_row, Nb, p->d_row, p->d_scan, s);
+    long long nnz = 0;
+    cudaMemcpyAsync(&nnz, p->d_row + Nb, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        h->err = "periodic mobility: cell list failed";
+        return AM_ERR_CUDA;
+    }
+    if (nnz > p->cap) {
+        if (p->d_nbr) cudaFree(p->d_nbr);
+        if (p->d_blk) cudaFree(p->d_blk);
+        p->d_nbr = nullptr;
+        p->d_blk = nullptr;
+        const long long cap = nnz + nnz / 4 + 1024;
+        if (!dalloc(&p->d_nbr, cap) || !dalloc(&p->d_blk, 6 * (size_t)cap)) {
+            cudaGetLastError();
+            p->cap = 0;
+            h->err = "periodic mobility: device allocation of the real-space pairs failed";
+            return AM_ERR_CUDA;
+        }
+        p->cap = cap;
+    }
+    k_per_pairs<true><<<nbk, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_sposf, p->d_cell_start, p->d_order, rc2f,
+                                          p->d_row, p->d_nbr, p->d_blk, p->cap, p->d_tab, p->ntab, 1.0 / p->ds, k,
+                                          1.0 / h->cfg.eta);
+    count_launch();
+    p->nnz = nnz;
+    h->per_nnz = nnz;
+    if (cudaGetLastError() != cudaSuccess) {
+        h->err = "periodic mobility: pair kernels failed";
+        return AM_ERR_CUDA;
+    }
+    p->valid = true;
+    return AM_OK;
+}
+
+// u = M_per lam (3 Nb each, blob order) into h->d_mv.  Stream-ordered; no
+// host synchronisation, so it can be captured into a graph.
+void launch_periodic(am_handle* h, const double* lam) {
+    PeriodicPlan* p = h->per;
+    cudaStream_t s = h->stream;
+    const int Nb = p->Nb;
+    if (!p->valid) {  // binning failed (reported by the caller): no launch on stale pairs
+        cudaMemsetAsync(h->d_mv, 0, 3 * (size_t)Nb * sizeof(double), s);
+        return;
+    }
+    const SpreadGeom g = spread_geom(p);
+    k_per_zero<<<8 * num_sms(), 256, 0, s>>>(p->d_grid, 3 * p->ngrid);
+    const int per_block = 256 / p->G;
+    const int nblk_g = (Nb + per_block - 1) / per_block;
+    k_per_spread<<<nblk_g, 256, 0, s>>>(Nb, g, p->G, p->d_spos, p->d_order, lam, p->d_grid, p->ngrid);
+    cufftExecD2Z(p->fwd, p->d_grid, p->d_hat);
+    k_per_kmul<<<(int)((p->nhat + 255) / 256), 256, 0, s>>>(p->Mg[0], p->Mg[1], p->Mg[2], p->L[0], p->L[1],
+                                                            p->L[2], p->d_kfac, p->d_hat, p->nhat);
+    cufftExecZ2D(p->inv, p->d_hat, p->d_grid);
+    k_per_gather<<<nblk_g, 256, 0, s>>>(Nb, g, p->G, p->d_spos, p->d_order, p->d_row, p->d_nbr, p->d_blk, p->cap,
+                                        lam, p->d_grid, p->ngrid, h->d_mv);
+    count_launch(4);
+}
+
+// xi, r_c, sigma, hx, hy, hz; Mx, My, Mz, P, real-space pairs, cells
+void periodic_info(const am_handle* h, double* d6, long long* i6) {
+    const PeriodicPlan* p = h->per;
+    if (d6) {
+        d6[0] = p->xi; d6[1] = p->rc; d6[2] = p->sigma;
+        d6[3] = p->hgrid[0]; d6[4] = p->hgrid[1]; d6[5] = p->hgrid[2];
+    }
+    if (i6) {
+        i6[0] = p->Mg[0]; i6[1] = p->Mg[1]; i6[2] = p->Mg[2];
+        i6[3] = p->P; i6[4] = p->nnz; i6[5] = p->ncell;
+    }
+}
+
+}  // namespace am

@@ -824,6 +824,7 @@ static int resident_grid(F kernel) {
 int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup) {
     const int S = h->S;
     if (h->cfg.precision != AM_MIXED) tpt = 1;
+    if (h->per) chunk = std::max(1, h->Nb);  // the periodic product writes u in one piece
     // targets per item: a block's targets, or (one target per thread) 32 or
     // 64 of them so that small systems spread over more SMs
     if (tpt == 2 || tgroup <= 0 || tgroup > kThreads || tgroup % 32) tgroup = kThreads * tpt;
@@ -900,6 +901,10 @@ int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup) {
 // The partial sums of u = M lambda for all systems (mode: the handle's
 // precision, FP64 or double-float).
 void launch_items(am_handle* h, const double* lam, int mode, const int* active) {
+    if (h->per) {  // FP64 only (checked by the callers)
+        launch_periodic(h, lam);
+        return;
+    }
     if (mode == kOpDF) {
         launch_items_df(h, lam);
         return;
@@ -944,6 +949,10 @@ void launch_sum_items(am_handle* h, double* u) {
 // Autotuner: times the handle's product for candidate (targets per thread,
 // source chunk) pairs on the current positions and keeps the fastest.
 int mobility_autotune(am_handle* h) {
+    if (h->per) {  // the periodic product has no item layout to tune
+        h->mv_tuned = true;
+        return 0;
+    }
     struct Cand { int tpt, chunk, tgroup; };
     std::vector<Cand> cand;
     const bool mixed = h->cfg.precision == AM_MIXED;

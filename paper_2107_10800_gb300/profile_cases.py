@@ -6,6 +6,7 @@ one kernel (-k, -c) ends quickly.  Nothing here is timed.
     python -m paper_2107_10800_gb300.profile_cases colony --precision fp64|mixed [--steps 3] [--host-steps]
     python -m paper_2107_10800_gb300.profile_cases batched [--steps 1] [--host-steps]
     python -m paper_2107_10800_gb300.profile_cases mlp [--rows 65536] [--calls 3]
+    python -m paper_2107_10800_gb300.profile_cases periodic [--lattice 10 10 10] [--tol 1e-8] [--calls 3]
 
 product: the all-pairs wall product u = M lambda on the first N blobs of the
 1,000-bacteria suspension above a wall (each blob its own body, so the
@@ -19,6 +20,9 @@ batched: steps of the 256 free-space chain suspensions in one handle
 (mixed precision); --host-steps as for colony.
 mlp: BF16 predictions of the learned-guess network (random weights) for
 `--rows` feature rows: four tcgen05 layer launches per call.
+periodic: spectral Ewald products of the bacteria in a periodic box (one
+bacterium per lattice site, 360 blobs each; 10 x 10 x 10 is 360,000 blobs),
+relative tolerance `--tol`, `--calls` products after the pose's pair blocks.
 """
 import argparse
 import os
@@ -80,9 +84,20 @@ def mlp(rows, calls):
     net.close()
 
 
+def periodic(lattice, tol, calls):
+    w = W.bacteria_periodic(5, lattice=tuple(lattice))
+    s = binding.Solver.from_workload(w, ewald_tol=tol)
+    lam = np.random.default_rng(6).standard_normal((s.Nb, 3))
+    for _ in range(calls):
+        s.apply_mobility(lam)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["product", "colony", "batched", "mlp"])
+    ap.add_argument("case", choices=["product", "colony", "batched", "mlp", "periodic"])
+    ap.add_argument("--lattice", type=int, nargs=3, default=[10, 10, 10])
+    ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--rows", type=int, default=65536)
     ap.add_argument("--blobs", type=int, default=60000)
     ap.add_argument("--arith", default="mixed", choices=["mixed", "fp64", "df64"])
@@ -98,6 +113,8 @@ def main():
         colony(a.precision, a.steps, a.host_steps)
     elif a.case == "batched":
         batched(a.steps, a.host_steps)
+    elif a.case == "periodic":
+        periodic(a.lattice, a.tol, a.calls)
     else:
         mlp(a.rows, a.calls)
 

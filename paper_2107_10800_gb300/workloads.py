@@ -293,6 +293,83 @@ def bacteria_wall(seed, n_bact=1000, a=0.05, box=250.0, hmin=1.0, hmax=5.0,
                 joints=np.array(joints), dl=None)
 
 
+def _quat_axis_angle(axis, ang):
+    axis = np.asarray(axis, dtype=np.float64)
+    axis = axis / np.linalg.norm(axis)
+    return np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * axis])
+
+
+def _quat_mul(q2, q1):
+    s2, p2, s1, p1 = q2[0], q2[1:], q1[0], q1[1:]
+    return np.concatenate([[s2 * s1 - p2 @ p1], s2 * p1 + s1 * p2 + np.cross(p2, p1)])
+
+
+def _quat_rot(q):
+    s, p = q[0], q[1:]
+    return 2.0 * (np.outer(p, p) + s * np.array([[0, -p[2], p[1]], [p[2], 0, -p[0]], [-p[1], p[0], 0]])
+                  + (s * s - 0.5) * np.eye(3))
+
+
+def bacteria_periodic(seed, lattice=(10, 10, 10), spacing=(15.0, 3.0, 3.0), tilt=0.1, a=0.05,
+                      motor_torque=1.0, eta=1.0, **tmpl_kw):
+    """Bacteria in a triply periodic box (the periodic suspensions of Sec.
+    5.3, here without the wall): one bacterium per site of a lattice with
+    the given spacing (box = lattice x spacing), its head centre jittered by
+    a tenth of the spacing, long axis along x tilted by up to ``tilt``
+    radians about a random perpendicular axis and spun by a random angle
+    about itself (an aligned suspension whose bodies do not overlap).
+    Motor torques as in bacteria_wall.  With the defaults: 1,000 bacteria,
+    360,000 blobs in a 150 x 30 x 30 box.  Returns the workload dict with
+    ``box``."""
+    rng = np.random.default_rng(np.random.Philox(seed))
+    bodies, hinge, seg_joints = bacterium_template(a=a, **tmpl_kw)
+    centroids = [b.mean(axis=0) for b in bodies]
+    nb = len(bodies)
+    box = np.array(lattice, dtype=np.float64) * np.array(spacing, dtype=np.float64)
+    q, theta, rho, F, assembly = [], [], [], [], []
+    body_p, body_q, joints = [], [], []
+    offs = [0]
+    b = 0
+    for ix in range(lattice[0]):
+        for iy in range(lattice[1]):
+            for iz in range(lattice[2]):
+                origin = (np.array([ix, iy, iz]) + 0.5 + rng.uniform(-0.1, 0.1, 3)) * np.array(spacing)
+                spin = _quat_axis_angle([1.0, 0.0, 0.0], rng.uniform(0.0, 2 * math.pi))
+                phi = rng.uniform(0.0, 2 * math.pi)
+                tq = _quat_axis_angle([0.0, math.cos(phi), math.sin(phi)], rng.uniform(0.0, tilt))
+                qq = _quat_mul(tq, spin)
+                R = _quat_rot(qq)
+                base = len(q)
+                axis = R @ np.array([1.0, 0.0, 0.0])
+                for k in range(nb):
+                    q.append(origin + R @ centroids[k])
+                    theta.append(qq.copy())
+                    rho.append(bodies[k] - centroids[k])
+                    offs.append(offs[-1] + len(bodies[k]))
+                    assembly.append(b)
+                    f = np.zeros(6)
+                    if k == 0:
+                        f[3:] = motor_torque * axis
+                    elif k == 1:
+                        f[3:] = -motor_torque * axis
+                    F.append(f)
+                for hpt in hinge:
+                    body_p.append(base); body_q.append(base + 1)
+                    joints.append(origin + R @ hpt)
+                for i, jp in enumerate(seg_joints):
+                    body_p.append(base + 1 + i); body_q.append(base + 2 + i)
+                    joints.append(origin + R @ jp)
+                b += 1
+    return dict(name="bacteria_periodic", eta=eta, a=a, wall=0, box=box,
+                q=np.array(q), theta=np.array(theta),
+                blob_offset=np.array(offs, dtype=np.int64),
+                rho=np.concatenate(rho), F=np.array(F),
+                assembly=np.array(assembly, dtype=np.int64),
+                body_p=np.array(body_p, dtype=np.int64),
+                body_q=np.array(body_q, dtype=np.int64),
+                joints=np.array(joints), dl=None)
+
+
 def random_blobs(seed, n, box=None, a=0.1, wall=0, hmin=None, hmax=None):
     """Loose blobs for matvec tests: uniform in a cube whose side keeps the
     number density of ``n`` blobs moderate; above a wall the heights are

@@ -1,0 +1,176 @@
+"""Periodic box (spectral Ewald product, csrc/periodic.cu) through the C ABI
+against the oracle's Ewald sum (oracle/periodic.py, pinned by its own
+tests).
+
+Bar: the product within 10 x the requested relative tolerance (ewald_tol)
+of the oracle, max-abs difference over max-abs value; the rules that pick
+the grid, support and cutoff from the tolerance were calibrated to meet the
+tolerance itself, so 10 x leaves room for configurations other than the
+calibration's.  Solves: the GPU solve of the periodic problem against the
+oracle's dense solve with the periodic mobility, within 1e-8 at
+ewald_tol = 1e-12 (the dense solve amplifies the product error by the
+condition number of A).  At 360,000 blobs, where the oracle's Ewald sum is
+out of reach, properties that hold at any size: independence of the split
+parameter and of a translation of every body, within the same bar."""
+import numpy as np
+import pytest
+
+from paper_2107_10800_gb300 import build, binding, workloads as W
+from oracle import periodic as op
+from oracle.system import System
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    binding.lib()
+
+
+def rel(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def loose(r, a, box, tol, eta=1.0, xi=0.0):
+    n = len(r)
+    s = binding.Solver(eta=eta, a=a, box=box, ewald_tol=tol, ewald_xi=xi)
+    s.set_bodies(r, np.tile([1.0, 0, 0, 0], (n, 1)), np.arange(n + 1), np.zeros((n, 3)),
+                 np.zeros((n, 6)), np.arange(n))
+    return s
+
+
+def edge_blobs(seed, n, box, a):
+    """Random blobs in the box plus the edge cases: an overlapping pair
+    across a face, a pair at contact, a centre on a face, centres several
+    box lengths outside."""
+    rng = np.random.default_rng(seed)
+    box = np.asarray(box, float)
+    r = rng.random((n, 3)) * box
+    lam = rng.standard_normal((n, 3))
+    if n >= 6:
+        r[0] = [0.01 * box[0], 0.5 * box[1], 0.5 * box[2]]
+        r[1] = [box[0] - 0.03, 0.5 * box[1] + 0.02, 0.5 * box[2]]  # overlaps r[0] through x = 0
+        r[2] = r[3] + [2.0 * a, 0.0, 0.0]
+        r[4] = [0.0, box[1], 0.3 * box[2]]
+        r[5] += box * np.array([3.0, -2.0, 5.0])
+    return r, lam
+
+
+@pytest.mark.parametrize("n", [1, 2, 50, 257])
+def test_periodic_product_matches_oracle(n):
+    box, a = np.array([1.0, 1.2, 0.9]), 0.1
+    r, lam = edge_blobs(n, n, box, a)
+    s = loose(r, a, box, 1e-10, eta=1.3)
+    u = s.apply_mobility(lam)
+    ref = op.periodic_mobility_matvec(r, lam, a, 1.3, box)
+    assert rel(u, ref) <= 1e-9
+    info = s.periodic_info()
+    assert info["real_pairs"] >= n  # every blob pairs with itself
+    assert info["r_c"] <= box.min() / 3.0 + 1e-12
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-6, 1e-8, 1e-10, 1e-12])
+def test_periodic_error_follows_tolerance(tol):
+    box, a = np.array([2.0, 2.0, 2.5]), 0.1
+    r, lam = edge_blobs(7, 120, box, a)
+    s = loose(r, a, box, tol)
+    u = s.apply_mobility(lam)
+    ref = op.periodic_mobility_matvec(r, lam, a, 1.0, box)
+    assert rel(u, ref) <= 10.0 * tol
+
+
+def test_periodic_split_parameter_and_cubic_box():
+    box, a = np.array([3.0, 3.0, 3.0]), 0.15
+    r, lam = edge_blobs(11, 200, box, a)
+    ref = op.periodic_mobility_matvec(r, lam, a, 1.0, box)
+    s0 = loose(r, a, box, 1e-10)
+    xi0 = s0.periodic_info()["xi"]
+    for xi in (xi0, 1.7 * xi0, 3.0 * xi0):
+        u = loose(r, a, box, 1e-10, xi=xi).apply_mobility(lam)
+        assert rel(u, ref) <= 1e-9
+
+
+def test_periodic_self_mobility_hasimoto():
+    # one blob in a cube: mu0 (1 - 2.837297 a/L + (4 pi/3) (a/L)^3)
+    a, eta = 0.1, 1.0
+    for L in (0.7, 1.0, 2.0):
+        s = loose(np.array([[0.3, 0.2, 0.1]]), a, [L, L, L], 1e-12)
+        u = s.apply_mobility(np.array([[1.0, 0.0, 0.0]]))
+        mu0 = 1.0 / (6.0 * np.pi * eta * a)
+        x = a / L
+        expect = mu0 * (1.0 - 2.8372974794806 * x + 4.0 * np.pi / 3.0 * x ** 3)
+        assert abs(u[0, 0] - expect) <= 1e-11 * mu0
+        assert abs(u[0, 1]) <= 1e-11 * mu0 and abs(u[0, 2]) <= 1e-11 * mu0
+
+
+def periodic_chains(seed, box):
+    w = W.chains_free_space(seed, n_chains=2, bodies_per_chain=4, box=box[0])
+    w["box"] = np.asarray(box, float)
+    return w
+
+
+def test_periodic_solve_matches_dense_solution():
+    box = np.array([4.0, 4.0, 4.0])
+    w = periodic_chains(3, box)
+    s = binding.Solver.from_workload(w, tol=1e-12, ewald_tol=1e-12)
+    U, phi, lam, st = s.solve()
+    assert st["rel_residual"] <= 1e-12
+    S = System(w)
+    S._M = op.periodic_mobility_dense(S.r, S.a, S.eta, box)
+    lo, uo, po = S.split(S.solve_dense())
+    assert rel(U.ravel(), uo) <= 1e-8
+    assert rel(lam.ravel(), lo) <= 1e-8
+    C = S.C_dense()
+    assert rel(C.T @ phi.ravel(), C.T @ po) <= 1e-8
+
+
+def test_periodic_step_solves_then_moves():
+    box = np.array([4.0, 4.0, 4.0])
+    w = periodic_chains(4, box)
+    s = binding.Solver.from_workload(w, tol=1e-10)
+    U0, _, _, _ = s.solve()
+    q0, _ = s.bodies()
+    U1, _, _, st = s.step(0.0, 0.01)
+    assert rel(U1, U0) <= 1e-8  # the step's solve is the same problem
+    assert st["g2_after"] < 1e-10
+    q1, _ = s.bodies()
+    assert np.abs(q1 - q0).max() > 1e-4 * np.abs(U0[:, :3]).max()
+
+
+def test_periodic_full_size_properties():
+    # 1,000 bacteria, 360,000 blobs in a 150 x 30 x 30 box: the split
+    # parameter and a common translation change the product by rounding
+    # and the Ewald truncation only
+    w = W.bacteria_periodic(5)
+    lam = np.random.default_rng(6).standard_normal((360_000, 3))
+    s = binding.Solver.from_workload(w, ewald_tol=1e-8)
+    info = s.periodic_info()
+    u0 = s.apply_mobility(lam)
+    s1 = binding.Solver.from_workload(w, ewald_tol=1e-8, ewald_xi=1.5 * info["xi"])
+    assert rel(s1.apply_mobility(lam), u0) <= 1e-7
+    w2 = dict(w)
+    w2["q"] = w["q"] + np.array([7.3, -11.1, 2.9])
+    w2["joints"] = w["joints"] + np.array([7.3, -11.1, 2.9])
+    s2 = binding.Solver.from_workload(w2, ewald_tol=1e-8)
+    assert rel(s2.apply_mobility(lam), u0) <= 1e-7
+
+
+def test_periodic_rejects():
+    with pytest.raises(binding.AmError):
+        binding.Solver(a=0.1, wall=1, box=[2, 2, 2])
+    with pytest.raises(binding.AmError):
+        binding.Solver(a=0.1, precision="mixed", box=[2, 2, 2])
+    with pytest.raises(binding.AmError):
+        binding.Solver(a=0.1, n_systems=2, box=[2, 2, 2])
+    with pytest.raises(binding.AmError):
+        binding.Solver(a=0.1, box=[2, 0, 2])
+    with pytest.raises(binding.AmError):  # a side below 6a
+        loose(np.zeros((2, 3)) + 0.1, 0.1, [0.5, 2.0, 2.0], 1e-8)
+    s = loose(np.random.default_rng(0).random((10, 3)), 0.1, [1.0, 1.0, 1.0], 1e-8)
+    with pytest.raises(binding.AmError):
+        s.apply_mobility_ex(np.zeros((10, 3)), "mixed")
+    with pytest.raises(binding.AmError):
+        s.set_repulsion(1.0, 0.1, 0.3)
