@@ -596,6 +596,52 @@ def bacteria_step(torch, binding, W, stream, dt=1e-3, rows=4096):
             "mixed_vs_fp64_product_rows": {"rows": rows, "max_rel_diff": err}}
 
 
+def periodic_form(torch, binding, W, stream, products=5):
+    """Fast summation: the 1,000 bacteria in a triply periodic 150 x 30 x 30
+    box (360,000 blobs, aligned on a jittered lattice), FP64 spectral Ewald
+    product (csrc/periodic.cu).  Per tolerance 1e-8 and 1e-10: the product's
+    device time (CUDA events around each product launch, am_mobility_timing,
+    after the pose's pair blocks) and its parameters; then one solve at
+    relative residual 1e-8 with the 1e-10 product (pose, pair blocks,
+    preconditioner build, GMRES) and one Euler step after it, CUDA events on
+    the solver's stream."""
+    w = W.bacteria_periodic(5)
+    lam = np.random.default_rng(6).standard_normal((int(w["blob_offset"][-1]), 3))
+    out = {"workload": "1,000 bacteria (360 blobs each, a=0.05) on a jittered 10 x 10 x 10 lattice in a "
+                       "triply periodic 150 x 30 x 30 box, 360,000 blobs; FP64 spectral Ewald product"}
+    for tol in (1e-8, 1e-10):
+        s = binding.Solver.from_workload(w, ewald_tol=tol, stream=stream.cuda_stream)
+        s.apply_mobility(lam)  # pair blocks of the pose
+        s.mobility_timing(True)
+        for _ in range(products):
+            s.apply_mobility(lam)
+        ms, k = s.mobility_timing(False)
+        info = s.periodic_info()
+        s.close()
+        out["product_tol_%g" % tol] = {"ms": ms / max(k, 1), "grid": list(info["grid"]),
+                                       "window_points": info["support"], "xi": info["xi"], "r_c": info["r_c"],
+                                       "real_space_pairs": info["real_pairs"]}
+    s = binding.Solver.from_workload(w, tol=1e-8, ewald_tol=1e-10, stream=stream.cuda_stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, _, _, st = s.solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    e0.record(stream)
+    _, _, _, st2 = s.step(0.0, 1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1)
+    s.close()
+    out.update({"solve_ms": solve_ms, "gmres_iterations": st["iterations"], "rel_residual": st["rel_residual"],
+                "ms_precond": st["ms_precond"], "ms_gmres": st["ms_gmres"], "step_ms": step_ms,
+                "step_gmres_iterations": st2["iterations"], "step_rel_residual": st2["rel_residual"]})
+    return out
+
+
 def combine_ranks(torch, total_s, pairs, e2e_ms_mean, steps, device):
     """Whole-job figures over the ranks of the process group: the timed
     region is the slowest rank's, the pairs are all ranks' (independent
@@ -732,6 +778,7 @@ def run_ours(args):
     guess_res = guess_form(binding, W) if world == 1 else None
     sb_res = single_blob_form(binding, W) if world == 1 else None
     chains_res = chains_solve(torch, binding, W, stream) if world == 1 else None
+    periodic_res = periodic_form(torch, binding, W, stream) if world == 1 else None
     bact_res = bacteria_step(torch, binding, W, stream) if world == 1 else None
     fpp = binding.flops_per_pair(1)
     avg_launch_s = (mob_ms * 1e-3) / max(mob_launches, 1)
@@ -786,7 +833,8 @@ def run_ours(args):
             "gpu_launches": int(launches), "clocks": clocks,
             "rk2_form": rk2_res, "guess_form": guess_res, "steric": steric, "single_blob_form": sb_res,
             "products_compared": compared, "matvec_at_scale": at_scale, "chains_solve": chains_res,
-            "learned_form": learned_res, "batched_form": batched, "bacteria_step": bact_res}
+            "learned_form": learned_res, "batched_form": batched, "periodic_form": periodic_res,
+            "bacteria_step": bact_res}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -17,22 +17,27 @@
 //    pair blocks depend on the pose only, so they are formed once per pose
 //    into a sparse block matrix (CSR over the blobs in cell order, 6
 //    doubles per pair) that every product reads;
-//  - wave space: the forces are spread onto a uniform grid with a Gaussian
-//    of width sigma truncated to P x P x P points, transformed (cuFFT, the
-//    three components batched), multiplied by sinc^2(ka) H(k) e^{sigma^2
-//    k^2} (I - khat khat) / (eta k^2) (the Gaussian's transform divided
-//    out twice), transformed back and interpolated at the blobs with the
-//    same Gaussian.  The spreading adds into the grid with FP64 atomics, so
-//    the last bits of the wave part depend on the order of arrival.
+//  - wave space: the forces are spread onto a uniform grid with the
+//    "exponential of semicircle" window phi(z) = exp(beta (sqrt(1 - z^2) -
+//    1)), z = t / (w h / 2), over w x w x w points (the window of Barnett,
+//    Magland and af Klinteberg's non-uniform FFT), transformed (cuFFT, the
+//    three components batched), multiplied by sinc^2(ka) H(k) (I - khat
+//    khat) / (eta k^2) / Phi(k)^2 (Phi the window's transform, computed by
+//    quadrature; the division undoes the spreading and the interpolation),
+//    transformed back and interpolated at the blobs with the same window.
+//    The spreading adds into the grid with FP64 atomics, so the last bits of
+//    the wave part depend on the order of arrival.
 //
-// Parameters from the relative tolerance eps (lg = ln(1/eps)): support
-// P = ceil(0.7 lg + 1.5), sigma / h = 0.3 + 0.055 P, grid spacing h =
-// pi / (2 xi sqrt(lg + ln(1 + lg))) (the wave multiplier below eps beyond
-// the grid's Nyquist wave number), r_c = 2a + sqrt(0.8 lg) / xi (the real
-// part below eps mu0 beyond it); xi minimises a cost model of the product
-// (real-space pairs read against grid points transformed) subject to r_c <=
-// min(L)/3 (three cells per side).  These rules were calibrated against the
-// Ewald sum evaluated to rounding.
+// Parameters from the relative tolerance eps (lg = ln(1/eps)): grid spacing
+// h = pi / (2 xi sqrt(lg + ln(1 + lg))) (the wave multiplier below eps
+// beyond the grid's Nyquist wave number; wave vectors beyond that radius are
+// dropped), window width w = ceil(log10(1/eps)) + 1 points with beta = 2.6 w,
+// r_c = 2a + sqrt(0.8 lg) / xi (the real part below eps mu0 beyond it); xi
+// minimises a cost model of the product (real-space pairs read against grid
+// points transformed, weights measured on GB300) subject to r_c <= min(L)/3
+// (three cells per side).
+// These rules were calibrated against the Ewald sum evaluated to rounding
+// (width 9 gives 7e-10 relative, 11 gives 2e-11).
 #include <cufft.h>
 
 #include <algorithm>
@@ -47,8 +52,8 @@ namespace am {
 
 struct PeriodicPlan {
     double L[3] = {0, 0, 0}, hgrid[3] = {0, 0, 0};
-    double xi = 0, rc = 0, sigma = 0, tol = 0;
-    int Mg[3] = {0, 0, 0}, P = 0, G = 16;  // grid, support, lanes per blob
+    double xi = 0, rc = 0, beta = 0, kcut = 0, tol = 0;
+    int Mg[3] = {0, 0, 0}, P = 0;          // grid, window width w
     int nc[3] = {0, 0, 0}, ncell = 0;      // cells per side (side >= r_c)
     int ntab = 0;
     double ds = 0;                          // table step in s = r^2
@@ -67,6 +72,9 @@ struct PeriodicPlan {
     double* d_blk = nullptr;                // 6 x cap pair blocks (SoA)
     long long cap = 0, nnz = 0;
     long long* d_scan = nullptr;            // scan scratch
+    int* d_code = nullptr;                  // per pair: source sorted index << 5 | neighbour cell
+    double4_32a* d_rprev = nullptr;         // positions of the last binning
+    int* d_moved = nullptr;                 // set when a blob moved since d_rprev
     double* d_grid = nullptr;               // 3 x ngrid
     cufftDoubleComplex* d_hat = nullptr;    // 3 x nhat
     double2* d_kfac = nullptr;              // (fac, fac / k^2) per half-spectrum point
@@ -104,21 +112,27 @@ __device__ __forceinline__ double j0f(double x) {
 }
 
 // Table node t: s = t ds; A(s) and B(s)/s by the quadrature rule (nodes k_q,
-// weights already times H(k_q) sinc^2(k_q a) / (2 pi^2)).
+// weights already times H(k_q) sinc^2(k_q a) / (2 pi^2)); one warp per node,
+// lanes over the quadrature nodes, a shuffle tree for the sums.
 __global__ void k_per_table(int ntab, double ds, const double* __restrict__ kq, const double* __restrict__ wq,
                             int nq, double2* __restrict__ tab) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (t >= ntab) return;
     const double r = sqrt(t * ds);
     double A = 0.0, Bs = 0.0;
-    for (int q = 0; q < nq; ++q) {
+    for (int q = lane; q < nq; q += 32) {
         const double k = kq[q], x = k * r;
         const double q2 = j2_over_x2(x);
         const double j2 = x * x * q2;
         A = fma(wq[q], (2.0 / 3.0) * j0f(x) - j2 / 3.0, A);
         Bs = fma(wq[q] * k * k, q2, Bs);
     }
-    tab[t] = make_double2(A, Bs);
+    for (int o = 16; o > 0; o >>= 1) {
+        A += __shfl_xor_sync(0xffffffffu, A, o);
+        Bs += __shfl_xor_sync(0xffffffffu, Bs, o);
+    }
+    if (lane == 0) tab[t] = make_double2(A, Bs);
 }
 
 // cubic Lagrange interpolation of the table at s (4 nodes around s)
@@ -138,9 +152,12 @@ __device__ __forceinline__ double2 tab_at(const double2* __restrict__ tab, int n
 // Wave multiplier per half-spectrum point (cuFFT D2Z layout of a Mz x My x
 // Mx grid: index (iz My + iy)(Mx/2 + 1) + ix), with the normalisation of the
 // spread -> forward -> inverse -> interpolate chain, hx hy hz / (Mx My Mz),
-// and zero at k = 0 and on the Nyquist planes of even sizes.
+// divided by the window's transform squared (phx[|mx|] phy[|my|] phz[|mz|]
+// per axis), and zero at k = 0, beyond |k| = kcut and on the Nyquist planes
+// of even sizes.
 __global__ void k_per_kfac(int Mx, int My, int Mz, double Lx, double Ly, double Lz, double a, double eta,
-                           double xi, double sigma, double2* __restrict__ kfac) {
+                           double xi, double kcut, const double* __restrict__ phx, const double* __restrict__ phy,
+                           const double* __restrict__ phz, double2* __restrict__ kfac) {
     const long long Mxh = Mx / 2 + 1;
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= Mxh * My * Mz) return;
@@ -149,7 +166,7 @@ __global__ void k_per_kfac(int Mx, int My, int Mz, double Lx, double Ly, double 
     const bool nyq = (Mx % 2 == 0 && 2 * ix == Mx) || (My % 2 == 0 && 2 * iy == My) || (Mz % 2 == 0 && 2 * iz == Mz);
     const double kx = 2.0 * kPi * mx / Lx, ky = 2.0 * kPi * my / Ly, kz = 2.0 * kPi * mz / Lz;
     const double k2 = kx * kx + ky * ky + kz * kz;
-    if (k2 == 0.0 || nyq) {
+    if (k2 == 0.0 || nyq || k2 > kcut * kcut) {
         kfac[q] = make_double2(0.0, 0.0);
         return;
     }
@@ -157,7 +174,8 @@ __global__ void k_per_kfac(int Mx, int My, int Mz, double Lx, double Ly, double 
     const double sinc = ka < 1e-4 ? 1.0 - ka * ka / 6.0 : sin(ka) / ka;
     const double x = k2 / (4.0 * xi * xi);
     const double norm = (Lx / Mx) * (Ly / My) * (Lz / Mz) / ((double)Mx * (double)My * (double)Mz);
-    const double fac = norm / eta * sinc * sinc * (1.0 + x) * exp(-x + sigma * sigma * k2) / k2;
+    const double ph = phx[ix] * phy[iy <= My / 2 ? iy : My - iy] * phz[iz <= Mz / 2 ? iz : Mz - iz];
+    const double fac = norm / eta * sinc * sinc * (1.0 + x) * exp(-x) / (k2 * ph * ph);
     kfac[q] = make_double2(fac, fac / k2);
 }
 
@@ -313,16 +331,13 @@ __device__ __forceinline__ void cell_coords(const CellGeom& g, double x, double 
     cz = min((int)(z / g.L[2] * g.nc[2]), g.nc[2] - 1);
 }
 
-// Pairs of sorted target p within r_c (FP32 test, the same in both passes):
-// count, or write the neighbour blob indices and FP64 pair blocks
-// M_RPY(d) - W(d) = alpha I + beta d d^T in the order of the 27 cells.
+// Pairs of sorted target p within r_c, by an FP32 distance test that is the
+// same in both passes: count them, or list them (source sorted index << 5 |
+// neighbour cell 0..26) in the order of the 27 cells.
 template <bool WRITE>
 __global__ void k_per_pairs(int Nb, CellGeom g, const double4_32a* __restrict__ spos,
-                            const float4* __restrict__ sposf, const int* __restrict__ start,
-                            const int* __restrict__ order, float rc2f, long long* __restrict__ row,
-                            int* __restrict__ nbr, double* __restrict__ blk, long long cap,
-                            const double2* __restrict__ tab, int ntab, double inv_ds, RpyK<double> k,
-                            double inv_eta) {
+                            const float4* __restrict__ sposf, const int* __restrict__ start, float rc2f,
+                            long long* __restrict__ row, int* __restrict__ code, long long cap) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= Nb) return;
     const double4_32a x = spos[p];
@@ -339,30 +354,67 @@ __global__ void k_per_pairs(int Nb, CellGeom g, const double4_32a* __restrict__ 
             const float4 yf = sposf[q];
             const float dxf = tx - yf.x, dyf = ty - yf.y, dzf = tz - yf.z;
             if (fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf)) >= rc2f) continue;
-            if (!WRITE) {
+            if (WRITE) {
+                if (out < cap) code[out] = (q << 5) | kc;  // cap is the counted total
+                ++out;
+            } else {
                 ++count;
-                continue;
             }
-            if (out >= cap) continue;  // guarded: cap is the counted total
-            const double4_32a y = spos[q];
-            const double dx = (x.x - sx) - y.x, dy = (x.y - sy) - y.y, dz = (x.z - sz) - y.z;
-            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            double c1, c2;
-            free_coefs<double>(r2, k, c1, c2);
-            const double2 w = tab_at(tab, ntab, inv_ds, r2);
-            const double al = k.A1 * c1 - w.x * inv_eta;
-            const double be = k.A1 * c2 - w.y * inv_eta;
-            nbr[out] = order[q];
-            blk[out] = fma(be, dx * dx, al);
-            blk[cap + out] = be * dx * dy;
-            blk[2 * cap + out] = be * dx * dz;
-            blk[3 * cap + out] = fma(be, dy * dy, al);
-            blk[4 * cap + out] = be * dy * dz;
-            blk[5 * cap + out] = fma(be, dz * dz, al);
-            ++out;
         }
     }
     if (!WRITE) row[p] = count;
+}
+
+// FP64 pair blocks M_RPY(d) - W(d) = alpha I + beta d d^T of the listed
+// pairs, one warp per target row (lanes over its pairs), and the source's
+// blob index for the products.
+__global__ void __launch_bounds__(256)
+k_per_blocks(int Nb, CellGeom g, const double4_32a* __restrict__ spos, const int* __restrict__ order,
+             const long long* __restrict__ row, const int* __restrict__ code, int* __restrict__ nbr,
+             double* __restrict__ blk, long long cap, const double2* __restrict__ tab, int ntab, double inv_ds,
+             RpyK<double> k, double inv_eta) {
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= Nb) return;
+    const double4_32a x = spos[p];
+    int cx, cy, cz;
+    cell_coords(g, x.x, x.y, x.z, cx, cy, cz);
+    const long long e1 = min(row[p + 1], cap);
+    for (long long e = row[p] + lane; e < e1; e += 32) {
+        const int cd = code[e];
+        const int q = cd >> 5;
+        if (q < 0 || q >= Nb) {  // never listed (the two FP32 passes agree): a zero block, in bounds
+            nbr[e] = 0;
+            for (int j = 0; j < 6; ++j) blk[j * cap + e] = 0.0;
+            continue;
+        }
+        double sx, sy, sz;
+        neighbour_cell(g, cx, cy, cz, cd & 31, sx, sy, sz);
+        const double4_32a y = spos[q];
+        const double dx = (x.x - sx) - y.x, dy = (x.y - sy) - y.y, dz = (x.z - sz) - y.z;
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        double c1, c2;
+        free_coefs<double>(r2, k, c1, c2);
+        const double2 w = tab_at(tab, ntab, inv_ds, r2);
+        const double al = k.A1 * c1 - w.x * inv_eta;
+        const double be = k.A1 * c2 - w.y * inv_eta;
+        nbr[e] = order[q];
+        blk[e] = fma(be, dx * dx, al);
+        blk[cap + e] = be * dx * dy;
+        blk[2 * cap + e] = be * dx * dz;
+        blk[3 * cap + e] = fma(be, dy * dy, al);
+        blk[4 * cap + e] = be * dy * dz;
+        blk[5 * cap + e] = fma(be, dz * dz, al);
+    }
+}
+
+// *moved = 1 if any blob moved since the last binning (x, y, z compared)
+__global__ void k_per_moved(int Nb, const double4_32a* __restrict__ r4, const double4_32a* __restrict__ prev,
+                            int* __restrict__ moved) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nb) return;
+    const double4_32a a = r4[i], b = prev[i];
+    if (a.x != b.x || a.y != b.y || a.z != b.z) *moved = 1;
 }
 
 __global__ void k_per_zero(double* __restrict__ g, long long n) {
@@ -371,49 +423,71 @@ __global__ void k_per_zero(double* __restrict__ g, long long n) {
         g[i] = 0.0;
 }
 
-// Gaussian weights of lane l (< P) along one axis: grid index i0 + l and
-// exp(-t^2 / (2 sigma^2)) (2 pi sigma^2)^(-1/2), t = (i0 + l) h - x
+// Window weight of lane l (< w = P) along one axis: grid index i0 + l (the
+// w points nearest x) and exp(beta (sqrt(1 - z^2) - 1)), z = ((i0 + l) h -
+// x) / (w h / 2)
 struct SpreadGeom {
     int M[3], P;
-    double h[3], inv2s2, c1;
+    double h[3], inv_half[3], beta;
 };
 
 __device__ __forceinline__ void axis_weight(double x, int d, const SpreadGeom& g, int lane, int& idx, double& w) {
     const int i0 = (int)ceil(x / g.h[d] - 0.5 * g.P);
     int i = i0 + lane;
-    const double t = (double)i * g.h[d] - x;
-    w = g.c1 * exp(-t * t * g.inv2s2);
+    const double z = ((double)i * g.h[d] - x) * g.inv_half[d];
+    w = exp(g.beta * (sqrt(fmax(0.0, 1.0 - z * z)) - 1.0));
     if (i < 0) i += g.M[d]; else if (i >= g.M[d]) i -= g.M[d];
     idx = i;
 }
 
-// Spread: a group of G lanes per blob (sorted order); lane l owns the grid
-// column x = i0x + l and walks the P x P (y, z) points.
+// Lanes of a warp: floor(32 / w) blobs side by side, w lanes each (sorted
+// blob order); lane l of a blob owns the grid column x = i0x + l and walks
+// the w x w (y, z) points.  Lanes past the last group only take part in the
+// shuffles.
+struct LaneMap {
+    int sub, lp, base;  // blob slot in the warp, lane within the blob, first lane of the blob
+    bool live;          // a lane of a blob that exists
+    int p;              // the blob (sorted position), clamped into range
+};
+
+__device__ __forceinline__ LaneMap lane_map(int Nb, int P) {
+    LaneMap m;
+    const int per = 32 / P;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    m.sub = lane / P;
+    m.lp = lane - m.sub * P;
+    const bool slot = m.sub < per;
+    if (!slot) { m.sub = 0; m.lp = lane; }
+    m.base = m.sub * P;
+    const int gid = warp * per + m.sub;
+    m.live = slot && gid < Nb;
+    m.p = min(gid, Nb - 1);
+    return m;
+}
+
 __global__ void __launch_bounds__(256)
-k_per_spread(int Nb, SpreadGeom g, int G, const double4_32a* __restrict__ spos, const int* __restrict__ order,
+k_per_spread(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const int* __restrict__ order,
              const double* __restrict__ lam, double* __restrict__ grid, long long ngrid) {
-    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int lane = threadIdx.x % G;
-    const bool live = gid < Nb;
-    const int p = live ? gid : Nb - 1;
-    const double4_32a x = spos[p];
-    const int i = order[p];
+    const LaneMap m = lane_map(Nb, g.P);
+    const double4_32a x = spos[m.p];
+    const int i = order[m.p];
     const double lx = lam[3 * (size_t)i], ly = lam[3 * (size_t)i + 1], lz = lam[3 * (size_t)i + 2];
     int ix = 0, iy = 0, iz = 0;
     double wx = 0.0, wy = 0.0, wz = 0.0;
-    if (lane < g.P) {
-        axis_weight(x.x, 0, g, lane, ix, wx);
-        axis_weight(x.y, 1, g, lane, iy, wy);
-        axis_weight(x.z, 2, g, lane, iz, wz);
+    if (m.lp < g.P) {
+        axis_weight(x.x, 0, g, m.lp, ix, wx);
+        axis_weight(x.y, 1, g, m.lp, iy, wy);
+        axis_weight(x.z, 2, g, m.lp, iz, wz);
     }
     const unsigned mask = 0xffffffffu;
     for (int pz = 0; pz < g.P; ++pz) {
-        const double wzz = __shfl_sync(mask, wz, pz, G);
-        const int zz = __shfl_sync(mask, iz, pz, G);
+        const double wzz = __shfl_sync(mask, wz, m.base + pz);
+        const int zz = __shfl_sync(mask, iz, m.base + pz);
         for (int py = 0; py < g.P; ++py) {
-            const double wyz = __shfl_sync(mask, wy, py, G) * wzz;
-            const int yy = __shfl_sync(mask, iy, py, G);
-            if (live && lane < g.P) {
+            const double wyz = __shfl_sync(mask, wy, m.base + py) * wzz;
+            const int yy = __shfl_sync(mask, iy, m.base + py);
+            if (m.live) {
                 const double w = wx * wyz;
                 const long long idx = ((long long)zz * g.M[1] + yy) * g.M[0] + ix;
                 atomicAdd(grid + idx, w * lx);
@@ -449,21 +523,19 @@ __global__ void k_per_kmul(int Mx, int My, int Mz, double Lx, double Ly, double 
 }
 
 // u_i = sum over its CSR row of the pair blocks times lambda_j (real space)
-// + the Gaussian interpolation of the wave-space field at r_i; a group of G
-// lanes per blob, sums in a fixed order (lane-strided rows, then a shuffle
-// tree).
+// + the interpolation of the wave-space field at r_i with the window; the
+// lanes of lane_map, sums in a fixed order (lane-strided rows, the lanes of
+// a blob added in lane order through shared memory).
 __global__ void __launch_bounds__(256)
-k_per_gather(int Nb, SpreadGeom g, int G, const double4_32a* __restrict__ spos, const int* __restrict__ order,
+k_per_gather(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const int* __restrict__ order,
              const long long* __restrict__ row, const int* __restrict__ nbr, const double* __restrict__ blk,
              long long cap, const double* __restrict__ lam, const double* __restrict__ grid, long long ngrid,
              double* __restrict__ out) {
-    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int lane = threadIdx.x % G;
-    const bool live = gid < Nb;
-    const int p = live ? gid : Nb - 1;
+    __shared__ double part[256][3];
+    const LaneMap m = lane_map(Nb, g.P);
     double ux = 0.0, uy = 0.0, uz = 0.0;
-    if (live) {
-        for (long long e = row[p] + lane; e < row[p + 1]; e += G) {
+    if (m.live) {
+        for (long long e = row[m.p] + m.lp; e < row[m.p + 1]; e += g.P) {
             const int j = nbr[e];
             const double lx = lam[3 * (size_t)j], ly = lam[3 * (size_t)j + 1], lz = lam[3 * (size_t)j + 2];
             const double m00 = blk[e], m01 = blk[cap + e], m02 = blk[2 * cap + e];
@@ -473,23 +545,23 @@ k_per_gather(int Nb, SpreadGeom g, int G, const double4_32a* __restrict__ spos, 
             uz = fma(m02, lx, fma(m12, ly, fma(m22, lz, uz)));
         }
     }
-    const double4_32a x = spos[p];
+    const double4_32a x = spos[m.p];
     int ix = 0, iy = 0, iz = 0;
     double wx = 0.0, wy = 0.0, wz = 0.0;
-    if (lane < g.P) {
-        axis_weight(x.x, 0, g, lane, ix, wx);
-        axis_weight(x.y, 1, g, lane, iy, wy);
-        axis_weight(x.z, 2, g, lane, iz, wz);
+    if (m.lp < g.P) {
+        axis_weight(x.x, 0, g, m.lp, ix, wx);
+        axis_weight(x.y, 1, g, m.lp, iy, wy);
+        axis_weight(x.z, 2, g, m.lp, iz, wz);
     }
     const unsigned mask = 0xffffffffu;
     double vx = 0.0, vy = 0.0, vz = 0.0;
     for (int pz = 0; pz < g.P; ++pz) {
-        const double wzz = __shfl_sync(mask, wz, pz, G);
-        const int zz = __shfl_sync(mask, iz, pz, G);
+        const double wzz = __shfl_sync(mask, wz, m.base + pz);
+        const int zz = __shfl_sync(mask, iz, m.base + pz);
         for (int py = 0; py < g.P; ++py) {
-            const double wyz = __shfl_sync(mask, wy, py, G) * wzz;
-            const int yy = __shfl_sync(mask, iy, py, G);
-            if (lane < g.P) {
+            const double wyz = __shfl_sync(mask, wy, m.base + py) * wzz;
+            const int yy = __shfl_sync(mask, iy, m.base + py);
+            if (m.live) {
                 const long long idx = ((long long)zz * g.M[1] + yy) * g.M[0] + ix;
                 const double w = wx * wyz;
                 vx = fma(w, __ldg(grid + idx), vx);
@@ -498,25 +570,30 @@ k_per_gather(int Nb, SpreadGeom g, int G, const double4_32a* __restrict__ spos, 
             }
         }
     }
-    ux += vx; uy += vy; uz += vz;
-    for (int o = G / 2; o > 0; o >>= 1) {
-        ux += __shfl_xor_sync(mask, ux, o, G);
-        uy += __shfl_xor_sync(mask, uy, o, G);
-        uz += __shfl_xor_sync(mask, uz, o, G);
-    }
-    if (live && lane == 0) {
-        const int i = order[p];
-        out[3 * (size_t)i] = ux;
-        out[3 * (size_t)i + 1] = uy;
-        out[3 * (size_t)i + 2] = uz;
+    part[threadIdx.x][0] = ux + vx;
+    part[threadIdx.x][1] = uy + vy;
+    part[threadIdx.x][2] = uz + vz;
+    __syncwarp();
+    if (m.live && m.lp == 0) {
+        const int t0 = threadIdx.x;  // the blob's first lane
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int l = 0; l < g.P; ++l) {
+            sx += part[t0 + l][0];
+            sy += part[t0 + l][1];
+            sz += part[t0 + l][2];
+        }
+        const int i = order[m.p];
+        out[3 * (size_t)i] = sx;
+        out[3 * (size_t)i + 1] = sy;
+        out[3 * (size_t)i + 2] = sz;
     }
 }
 
 // ---- host ------------------------------------------------------------------
-int fft_size(int n) {  // smallest 2-3-5-7-smooth size >= n
+int fft_size(int n) {  // smallest 2-3-5-smooth size >= n (cuFFT's fast radices)
     for (;; ++n) {
         int m = n;
-        for (int f : {2, 3, 5, 7})
+        for (int f : {2, 3, 5})
             while (m % f == 0) m /= f;
         if (m == 1) return n;
     }
@@ -550,8 +627,9 @@ void free_plan(PeriodicPlan* p) {
         cufftDestroy(p->fwd);
         cufftDestroy(p->inv);
     }
-    void* ptrs[] = {p->d_tab, p->d_cell_start, p->d_cell_fill, p->d_cell_of, p->d_order, p->d_spos,
-                    p->d_sposf, p->d_row, p->d_nbr, p->d_blk, p->d_scan, p->d_grid, p->d_hat, p->d_kfac};
+    void* ptrs[] = {p->d_tab,  p->d_cell_start, p->d_cell_fill, p->d_cell_of, p->d_order, p->d_spos,
+                    p->d_sposf, p->d_row,     p->d_nbr,       p->d_blk,     p->d_scan,  p->d_grid,
+                    p->d_hat,  p->d_kfac,     p->d_code,      p->d_rprev,   p->d_moved};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -569,8 +647,8 @@ SpreadGeom spread_geom(const PeriodicPlan* p) {
         g.h[d] = p->hgrid[d];
     }
     g.P = p->P;
-    g.inv2s2 = 1.0 / (2.0 * p->sigma * p->sigma);
-    g.c1 = std::pow(2.0 * kPi * p->sigma * p->sigma, -0.5);
+    for (int d = 0; d < 3; ++d) g.inv_half[d] = 2.0 / (p->P * p->hgrid[d]);
+    g.beta = p->beta;
     return g;
 }
 
@@ -597,14 +675,18 @@ int periodic_setup(am_handle* h) {
     const double a = h->cfg.blob_radius, eta = h->cfg.eta;
     const double tol = h->cfg.ewald_tol > 0.0 ? h->cfg.ewald_tol : 1e-10;
     const int Nb = h->Nb;
+    if (Nb <= 0 || Nb >= (1 << 26)) {
+        h->err = "periodic box: the blob count must be in 1 .. 2^26 - 1";
+        return AM_ERR_ARG;
+    }
     PeriodicPlan* p = new PeriodicPlan();
     h->per = p;
     p->Nb = Nb;
     p->tol = tol;
     for (int d = 0; d < 3; ++d) p->L[d] = h->cfg.box[d];
     const double lg = std::log(1.0 / tol);
-    p->P = std::min(32, std::max(4, (int)std::ceil(0.7 * lg + 1.5)));
-    p->G = p->P <= 16 ? 16 : 32;
+    p->P = std::min(32, std::max(4, (int)std::ceil(std::log10(1.0 / tol)) + 1));
+    p->beta = 2.6 * p->P;
     const double xN = lg + std::log1p(lg), crc = std::sqrt(0.8 * lg);
     const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
     if (!(Lmin / 3.0 > 2.0 * a * 1.01)) {
@@ -629,8 +711,11 @@ int periodic_setup(am_handle* h) {
             return AM_ERR_ARG;
         }
     } else {
-        // cost per product: real-space pairs (52 bytes each) against grid
-        // points (about 340 bytes of transform traffic each)
+        // time per product, measured on GB300: about 20 ps per real-space
+        // pair (its 52 bytes read, plus its share of the per-pose block
+        // build over a solve) against 700 ps per grid point (the three
+        // FP64 transforms each way, bound by the FP64 rate); the spreading
+        // and interpolation do not depend on xi
         double best = 1e300;
         for (int t = 0; t < 96; ++t) {
             const double x = xi_lo * std::pow(2.0, t / 8.0);
@@ -639,7 +724,7 @@ int periodic_setup(am_handle* h) {
             if (tot > (1LL << 31)) break;
             const double rc = 2.0 * a + crc / x;
             const double pairs = (double)Nb * (1.0 + dens * 4.0 / 3.0 * kPi * rc * rc * rc);
-            const double cost = 52.0 * pairs + 340.0 * (double)tot;
+            const double cost = 20.0 * pairs + 700.0 * (double)tot;
             if (cost < best) {
                 best = cost;
                 xi = x;
@@ -655,9 +740,7 @@ int periodic_setup(am_handle* h) {
     p->ngrid = grid_for(xi, p->Mg);
     for (int d = 0; d < 3; ++d) p->hgrid[d] = p->L[d] / p->Mg[d];
     p->nhat = (long long)(p->Mg[0] / 2 + 1) * p->Mg[1] * p->Mg[2];
-    const double hmin = std::min(p->hgrid[0], std::min(p->hgrid[1], p->hgrid[2]));
-    p->sigma = (0.3 + 0.055 * p->P) * hmin;
-    if (p->sigma * xi >= 0.5) p->sigma = 0.49 / xi;  // keep e^{sigma^2 k^2 - k^2/(4 xi^2)} decaying
+    p->kcut = 2.0 * xi * std::sqrt(xN);
     for (int d = 0; d < 3; ++d) p->nc[d] = std::max(3, (int)std::floor(p->L[d] / p->rc));
     p->ncell = p->nc[0] * p->nc[1] * p->nc[2];
     p->ntab = kTab;
@@ -668,7 +751,8 @@ int periodic_setup(am_handle* h) {
               dalloc(&p->d_cell_fill, p->ncell) && dalloc(&p->d_cell_of, Nb) && dalloc(&p->d_order, Nb) &&
               dalloc(&p->d_spos, Nb) && dalloc(&p->d_sposf, Nb) && dalloc(&p->d_row, Nb + 1) &&
               dalloc(&p->d_scan, nscan) && dalloc(&p->d_grid, 3 * (size_t)p->ngrid) &&
-              dalloc(&p->d_hat, 3 * (size_t)p->nhat) && dalloc(&p->d_kfac, p->nhat);
+              dalloc(&p->d_hat, 3 * (size_t)p->nhat) && dalloc(&p->d_kfac, p->nhat) &&
+              dalloc(&p->d_rprev, Nb) && dalloc(&p->d_moved, 1);
     if (!ok) {
         cudaGetLastError();
         h->err = "periodic mobility: device allocation failed";
@@ -719,13 +803,45 @@ int periodic_setup(am_handle* h) {
     }
     cudaMemcpyAsync(d_kq, kq.data(), kq.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_wq, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice, s);
-    k_per_table<<<(p->ntab + 127) / 128, 128, 0, s>>>(p->ntab, p->ds, d_kq, d_wq, (int)kq.size(), p->d_tab);
+    // window transforms per axis at k = 2 pi m / L, m = 0 .. M/2:
+    // Phi(k) = (w h / 2) int_{-1}^{1} exp(beta (sqrt(1 - z^2) - 1)) cos(k w h z / 2) dz
+    // (composite 20-point Gauss-Legendre, 16 panels)
+    std::vector<double> ph;
+    int ph_off[4] = {0, 0, 0, 0};
+    for (int d = 0; d < 3; ++d) {
+        const double half = 0.5 * p->P * p->hgrid[d];
+        for (int m = 0; m <= p->Mg[d] / 2; ++m) {
+            const double k = 2.0 * kPi * m / p->L[d];
+            double acc = 0.0;
+            for (int pn = 0; pn < 16; ++pn) {
+                const double z0 = -1.0 + 2.0 * pn / 16.0, zh = 1.0 / 16.0;
+                for (int i = 0; i < 20; ++i) {
+                    const double z = z0 + zh * (1.0 + gx[i]);
+                    acc += zh * gw[i] * std::exp(p->beta * (std::sqrt(std::max(0.0, 1.0 - z * z)) - 1.0)) *
+                           std::cos(k * half * z);
+                }
+            }
+            ph.push_back(half * acc);
+        }
+        ph_off[d + 1] = (int)ph.size();
+    }
+    double* d_ph = nullptr;
+    if (!dalloc(&d_ph, ph.size())) {
+        cudaFree(d_kq);
+        cudaFree(d_wq);
+        h->err = "periodic mobility: device allocation failed";
+        return AM_ERR_CUDA;
+    }
+    cudaMemcpyAsync(d_ph, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    k_per_table<<<(p->ntab * 32 + 255) / 256, 256, 0, s>>>(p->ntab, p->ds, d_kq, d_wq, (int)kq.size(), p->d_tab);
     k_per_kfac<<<(int)((p->nhat + 255) / 256), 256, 0, s>>>(p->Mg[0], p->Mg[1], p->Mg[2], p->L[0], p->L[1],
-                                                            p->L[2], a, eta, xi, p->sigma, p->d_kfac);
+                                                            p->L[2], a, eta, xi, p->kcut, d_ph + ph_off[0],
+                                                            d_ph + ph_off[1], d_ph + ph_off[2], p->d_kfac);
     count_launch(2);
     const cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(d_kq);
     cudaFree(d_wq);
+    cudaFree(d_ph);
     if (e != cudaSuccess) {
         h->err = "periodic mobility: setup kernels failed";
         return AM_ERR_CUDA;
@@ -741,6 +857,19 @@ int periodic_bin(am_handle* h) {
     cudaStream_t s = h->stream;
     const int Nb = p->Nb;
     const int nbk = (Nb + 255) / 256;
+    if (p->valid) {  // the same positions as at the last binning: nothing to redo
+        int moved = 1;
+        cudaMemsetAsync(p->d_moved, 0, sizeof(int), s);
+        k_per_moved<<<nbk, 256, 0, s>>>(Nb, h->d_r4, p->d_rprev, p->d_moved);
+        count_launch();
+        cudaMemcpyAsync(&moved, p->d_moved, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            h->err = "periodic mobility: position check failed";
+            p->valid = false;
+            return AM_ERR_CUDA;
+        }
+        if (!moved) return AM_OK;
+    }
     p->valid = false;
     cudaMemsetAsync(p->d_cell_fill, 0, p->ncell * sizeof(int), s);
     k_per_cell<<<nbk, 256, 0, s>>>(Nb, h->d_r4, p->L[0], p->L[1], p->L[2], p->nc[0], p->nc[1], p->nc[2],
@@ -756,10 +885,9 @@ int periodic_bin(am_handle* h) {
     const CellGeom cg = cell_geom(p);
     const RpyK<double> k = rpy_consts<double>(h->prm);
     const float rc2f = (float)(p->rc * p->rc);
-    // count, scan, then write the pair blocks
-    k_per_pairs<false><<<nbk, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_sposf, p->d_cell_start, p->d_order, rc2f,
-                                           p->d_row, nullptr, nullptr, 0, p->d_tab, p->ntab, 1.0 / p->ds, k,
-                                           1.0 / h->cfg.eta);
+    // count, scan, list, then the FP64 blocks
+    k_per_pairs<false><<<nbk, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_sposf, p->d_cell_start, rc2f, p->d_row,
+                                           nullptr, 0);
     count_launch();
     exclusive_scan<long long, long long>(p->d_row, Nb, p->d_row, p->d_scan, s);
     long long nnz = 0;
@@ -771,10 +899,12 @@ int periodic_bin(am_handle* h) {
     if (nnz > p->cap) {
         if (p->d_nbr) cudaFree(p->d_nbr);
         if (p->d_blk) cudaFree(p->d_blk);
+        if (p->d_code) cudaFree(p->d_code);
         p->d_nbr = nullptr;
         p->d_blk = nullptr;
+        p->d_code = nullptr;
         const long long cap = nnz + nnz / 4 + 1024;
-        if (!dalloc(&p->d_nbr, cap) || !dalloc(&p->d_blk, 6 * (size_t)cap)) {
+        if (!dalloc(&p->d_nbr, cap) || !dalloc(&p->d_blk, 6 * (size_t)cap) || !dalloc(&p->d_code, cap)) {
             cudaGetLastError();
             p->cap = 0;
             h->err = "periodic mobility: device allocation of the real-space pairs failed";
@@ -782,10 +912,13 @@ int periodic_bin(am_handle* h) {
         }
         p->cap = cap;
     }
-    k_per_pairs<true><<<nbk, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_sposf, p->d_cell_start, p->d_order, rc2f,
-                                          p->d_row, p->d_nbr, p->d_blk, p->cap, p->d_tab, p->ntab, 1.0 / p->ds, k,
-                                          1.0 / h->cfg.eta);
-    count_launch();
+    k_per_pairs<true><<<nbk, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_sposf, p->d_cell_start, rc2f, p->d_row,
+                                          p->d_code, p->cap);
+    k_per_blocks<<<(int)(((long long)Nb * 32 + 255) / 256), 256, 0, s>>>(
+        Nb, cg, p->d_spos, p->d_order, p->d_row, p->d_code, p->d_nbr, p->d_blk, p->cap, p->d_tab, p->ntab,
+        1.0 / p->ds, k, 1.0 / h->cfg.eta);
+    cudaMemcpyAsync(p->d_rprev, h->d_r4, Nb * sizeof(double4_32a), cudaMemcpyDeviceToDevice, s);
+    count_launch(2);
     p->nnz = nnz;
     h->per_nnz = nnz;
     if (cudaGetLastError() != cudaSuccess) {
@@ -808,23 +941,23 @@ void launch_periodic(am_handle* h, const double* lam) {
     }
     const SpreadGeom g = spread_geom(p);
     k_per_zero<<<8 * num_sms(), 256, 0, s>>>(p->d_grid, 3 * p->ngrid);
-    const int per_block = 256 / p->G;
+    const int per_block = 8 * (32 / p->P);  // blobs per 256-thread block (lane_map)
     const int nblk_g = (Nb + per_block - 1) / per_block;
-    k_per_spread<<<nblk_g, 256, 0, s>>>(Nb, g, p->G, p->d_spos, p->d_order, lam, p->d_grid, p->ngrid);
+    k_per_spread<<<nblk_g, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, lam, p->d_grid, p->ngrid);
     cufftExecD2Z(p->fwd, p->d_grid, p->d_hat);
     k_per_kmul<<<(int)((p->nhat + 255) / 256), 256, 0, s>>>(p->Mg[0], p->Mg[1], p->Mg[2], p->L[0], p->L[1],
                                                             p->L[2], p->d_kfac, p->d_hat, p->nhat);
     cufftExecZ2D(p->inv, p->d_hat, p->d_grid);
-    k_per_gather<<<nblk_g, 256, 0, s>>>(Nb, g, p->G, p->d_spos, p->d_order, p->d_row, p->d_nbr, p->d_blk, p->cap,
-                                        lam, p->d_grid, p->ngrid, h->d_mv);
+    k_per_gather<<<nblk_g, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, p->d_row, p->d_nbr, p->d_blk, p->cap, lam,
+                                        p->d_grid, p->ngrid, h->d_mv);
     count_launch(4);
 }
 
-// xi, r_c, sigma, hx, hy, hz; Mx, My, Mz, P, real-space pairs, cells
+// xi, r_c, beta, hx, hy, hz; Mx, My, Mz, w, real-space pairs, cells
 void periodic_info(const am_handle* h, double* d6, long long* i6) {
     const PeriodicPlan* p = h->per;
     if (d6) {
-        d6[0] = p->xi; d6[1] = p->rc; d6[2] = p->sigma;
+        d6[0] = p->xi; d6[1] = p->rc; d6[2] = p->beta;
         d6[3] = p->hgrid[0]; d6[4] = p->hgrid[1]; d6[5] = p->hgrid[2];
     }
     if (i6) {
