@@ -72,7 +72,7 @@ struct PeriodicPlan {
     double* d_blk = nullptr;                // 6 x cap pair blocks (SoA)
     long long cap = 0, nnz = 0;
     long long* d_scan = nullptr;            // scan scratch
-    int* d_code = nullptr;                  // per pair: source sorted index << 5 | neighbour cell
+    int* d_code = nullptr;                  // per pair: neighbour cell << 26 | source sorted index
     double4_32a* d_rprev = nullptr;         // positions of the last binning
     int* d_moved = nullptr;                 // set when a blob moved since d_rprev
     double* d_grid = nullptr;               // 3 x ngrid
@@ -277,23 +277,8 @@ __global__ void k_per_fill(int Nb, const int* __restrict__ cell_of, const int* _
     order[start[c] + atomicAdd(&fill[c], 1)] = i;
 }
 
-// blobs of each cell in index order (the fill order depends on arrival), and
-// the sorted wrapped positions
-__global__ void k_per_sort_cells(int ncell, const int* __restrict__ start, int* __restrict__ order) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int b = start[c], e = start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        const int v = order[i];
-        int j = i - 1;
-        while (j >= b && order[j] > v) {
-            order[j + 1] = order[j];
-            --j;
-        }
-        order[j + 1] = v;
-    }
-}
-
+// the sorted wrapped positions (blobs of a cell in the order of arrival at
+// k_per_fill, which only changes the order of the sums)
 __global__ void k_per_gather_pos(int Nb, const int* __restrict__ order, const double4_32a* __restrict__ r4,
                                  double Lx, double Ly, double Lz, double4_32a* __restrict__ spos,
                                  float4* __restrict__ sposf) {
@@ -332,8 +317,9 @@ __device__ __forceinline__ void cell_coords(const CellGeom& g, double x, double 
 }
 
 // Pairs of sorted target p within r_c, by an FP32 distance test that is the
-// same in both passes: count them, or list them (source sorted index << 5 |
-// neighbour cell 0..26) in the order of the 27 cells.
+// same in both passes: count them, or list them as codes (neighbour cell
+// 0..26) << 26 | source sorted index, ascending within a row (cells in
+// order, sources in sorted order within a cell).
 template <bool WRITE>
 __global__ void k_per_pairs(int Nb, CellGeom g, const double4_32a* __restrict__ spos,
                             const float4* __restrict__ sposf, const int* __restrict__ start, float rc2f,
@@ -355,7 +341,7 @@ __global__ void k_per_pairs(int Nb, CellGeom g, const double4_32a* __restrict__ 
             const float dxf = tx - yf.x, dyf = ty - yf.y, dzf = tz - yf.z;
             if (fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf)) >= rc2f) continue;
             if (WRITE) {
-                if (out < cap) code[out] = (q << 5) | kc;  // cap is the counted total
+                if (out < cap) code[out] = (kc << 26) | q;  // cap is the counted total
                 ++out;
             } else {
                 ++count;
@@ -365,9 +351,38 @@ __global__ void k_per_pairs(int Nb, CellGeom g, const double4_32a* __restrict__ 
     if (!WRITE) row[p] = count;
 }
 
-// FP64 pair blocks M_RPY(d) - W(d) = alpha I + beta d d^T of the listed
-// pairs, one warp per target row (lanes over its pairs), and the source's
-// blob index for the products.
+// FP64 pair block M_RPY(d) - W(d) = alpha I + beta d d^T of target p and
+// listed source q in neighbour cell kc (the six distinct entries)
+__device__ __forceinline__ void pair_block(const CellGeom& g, int cx, int cy, int cz, const double4_32a& x,
+                                           const double4_32a* __restrict__ spos, int q, int kc,
+                                           const double2* __restrict__ tab, int ntab, double inv_ds,
+                                           const RpyK<double>& k, double inv_eta, double* m) {
+    double sx, sy, sz;
+    neighbour_cell(g, cx, cy, cz, kc, sx, sy, sz);
+    const double4_32a y = spos[q];
+    const double dx = (x.x - sx) - y.x, dy = (x.y - sy) - y.y, dz = (x.z - sz) - y.z;
+    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    double c1, c2;
+    free_coefs<double>(r2, k, c1, c2);
+    const double2 w = tab_at(tab, ntab, inv_ds, r2);
+    const double al = k.A1 * c1 - w.x * inv_eta;
+    const double be = k.A1 * c2 - w.y * inv_eta;
+    m[0] = fma(be, dx * dx, al);
+    m[1] = be * dx * dy;
+    m[2] = be * dx * dz;
+    m[3] = fma(be, dy * dy, al);
+    m[4] = be * dy * dz;
+    m[5] = fma(be, dz * dz, al);
+}
+
+// Blocks of the listed pairs, one warp per target row (lanes over its
+// pairs), and the source's blob index for the products.  MIRROR = false:
+// the pairs with q >= p, in FP64; MIRROR = true: the pairs with q < p,
+// copied from the entry (q -> p) of row q, which sits at code
+// (26 - kc) << 26 | p (the opposite neighbour cell) and is found by binary
+// search (the block is even in d); computed in FP64 when the FP32 cut
+// listed only one direction.
+template <bool MIRROR>
 __global__ void __launch_bounds__(256)
 k_per_blocks(int Nb, CellGeom g, const double4_32a* __restrict__ spos, const int* __restrict__ order,
              const long long* __restrict__ row, const int* __restrict__ code, int* __restrict__ nbr,
@@ -382,29 +397,32 @@ k_per_blocks(int Nb, CellGeom g, const double4_32a* __restrict__ spos, const int
     const long long e1 = min(row[p + 1], cap);
     for (long long e = row[p] + lane; e < e1; e += 32) {
         const int cd = code[e];
-        const int q = cd >> 5;
-        if (q < 0 || q >= Nb) {  // never listed (the two FP32 passes agree): a zero block, in bounds
+        const int q = cd & ((1 << 26) - 1), kc = cd >> 26;
+        if (q >= Nb || kc < 0 || kc > 26) {  // never listed (the two FP32 passes agree): a zero block, in bounds
             nbr[e] = 0;
             for (int j = 0; j < 6; ++j) blk[j * cap + e] = 0.0;
             continue;
         }
-        double sx, sy, sz;
-        neighbour_cell(g, cx, cy, cz, cd & 31, sx, sy, sz);
-        const double4_32a y = spos[q];
-        const double dx = (x.x - sx) - y.x, dy = (x.y - sy) - y.y, dz = (x.z - sz) - y.z;
-        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        double c1, c2;
-        free_coefs<double>(r2, k, c1, c2);
-        const double2 w = tab_at(tab, ntab, inv_ds, r2);
-        const double al = k.A1 * c1 - w.x * inv_eta;
-        const double be = k.A1 * c2 - w.y * inv_eta;
+        if ((q < p) != MIRROR) continue;
         nbr[e] = order[q];
-        blk[e] = fma(be, dx * dx, al);
-        blk[cap + e] = be * dx * dy;
-        blk[2 * cap + e] = be * dx * dz;
-        blk[3 * cap + e] = fma(be, dy * dy, al);
-        blk[4 * cap + e] = be * dy * dz;
-        blk[5 * cap + e] = fma(be, dz * dz, al);
+        double m[6];
+        bool have = false;
+        if (MIRROR) {
+            const int want = ((26 - kc) << 26) | p;
+            long long lo = row[q], hi = min(row[q + 1], cap) - 1;
+            while (lo <= hi) {
+                const long long mid = (lo + hi) >> 1;
+                const int v = code[mid];
+                if (v == want) {
+                    for (int j = 0; j < 6; ++j) m[j] = blk[j * cap + mid];
+                    have = true;
+                    break;
+                }
+                if (v < want) lo = mid + 1; else hi = mid - 1;
+            }
+        }
+        if (!have) pair_block(g, cx, cy, cz, x, spos, q, kc, tab, ntab, inv_ds, k, inv_eta, m);
+        for (int j = 0; j < 6; ++j) blk[j * cap + e] = m[j];
     }
 }
 
@@ -671,10 +689,14 @@ void periodic_free(am_handle* h) {
 
 // Parameters and buffers for the handle's box, tolerance and blob count.
 int periodic_setup(am_handle* h) {
-    periodic_free(h);
     const double a = h->cfg.blob_radius, eta = h->cfg.eta;
     const double tol = h->cfg.ewald_tol > 0.0 ? h->cfg.ewald_tol : 1e-10;
     const int Nb = h->Nb;
+    if (h->per && h->per->Nb == Nb) {  // the same box, tolerance and blob count: keep the plan
+        h->per->valid = false;         // (bin again at the next pose)
+        return AM_OK;
+    }
+    periodic_free(h);
     if (Nb <= 0 || Nb >= (1 << 26)) {
         h->err = "periodic box: the blob count must be in 1 .. 2^26 - 1";
         return AM_ERR_ARG;
@@ -878,10 +900,9 @@ int periodic_bin(am_handle* h) {
     exclusive_scan<int, int>(p->d_cell_fill, p->ncell, p->d_cell_start, p->d_scan, s);
     cudaMemsetAsync(p->d_cell_fill, 0, p->ncell * sizeof(int), s);
     k_per_fill<<<nbk, 256, 0, s>>>(Nb, p->d_cell_of, p->d_cell_start, p->d_cell_fill, p->d_order);
-    k_per_sort_cells<<<(p->ncell + 127) / 128, 128, 0, s>>>(p->ncell, p->d_cell_start, p->d_order);
     k_per_gather_pos<<<nbk, 256, 0, s>>>(Nb, p->d_order, h->d_r4, p->L[0], p->L[1], p->L[2], p->d_spos,
                                          p->d_sposf);
-    count_launch(3);
+    count_launch(2);
     const CellGeom cg = cell_geom(p);
     const RpyK<double> k = rpy_consts<double>(h->prm);
     const float rc2f = (float)(p->rc * p->rc);
@@ -914,11 +935,13 @@ int periodic_bin(am_handle* h) {
     }
     k_per_pairs<true><<<nbk, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_sposf, p->d_cell_start, rc2f, p->d_row,
                                           p->d_code, p->cap);
-    k_per_blocks<<<(int)(((long long)Nb * 32 + 255) / 256), 256, 0, s>>>(
-        Nb, cg, p->d_spos, p->d_order, p->d_row, p->d_code, p->d_nbr, p->d_blk, p->cap, p->d_tab, p->ntab,
-        1.0 / p->ds, k, 1.0 / h->cfg.eta);
+    const int nbw = (int)(((long long)Nb * 32 + 255) / 256);
+    k_per_blocks<false><<<nbw, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_order, p->d_row, p->d_code, p->d_nbr, p->d_blk,
+                                            p->cap, p->d_tab, p->ntab, 1.0 / p->ds, k, 1.0 / h->cfg.eta);
+    k_per_blocks<true><<<nbw, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_order, p->d_row, p->d_code, p->d_nbr, p->d_blk,
+                                           p->cap, p->d_tab, p->ntab, 1.0 / p->ds, k, 1.0 / h->cfg.eta);
     cudaMemcpyAsync(p->d_rprev, h->d_r4, Nb * sizeof(double4_32a), cudaMemcpyDeviceToDevice, s);
-    count_launch(2);
+    count_launch(3);
     p->nnz = nnz;
     h->per_nnz = nnz;
     if (cudaGetLastError() != cudaSuccess) {

@@ -96,3 +96,40 @@ def test_rank8_correction_ceiling():
     assert it_rank8 >= it_block - 1, (it_block, it_rank8)
     assert it_velocity >= it_block - 1, (it_block, it_velocity)
     assert it_exact <= it_block // 2, (it_block, it_exact)
+
+
+def test_global_rank8_deflation_ceiling():
+    # The other form a rank-8 term can take: a global coarse correction.  Its
+    # ceiling moves the 8 eigenvalues of A P~^-1 nearest zero (the null
+    # directions of the redundant links left out) to 1 exactly: with right
+    # eigenvectors V and left ones W (W^T V = I), P^-1 = P~^-1 (I + V
+    # (L^-1 - I) W^T).  On two bacteria the spectrum has a cluster of 15
+    # eigenvalues per bacterium near 0.36, so deflating 8 gains nothing
+    # (measured here 16 -> 16; 4 bacteria 16 -> 17; the 32-body diatom
+    # colony 39 -> 38, rank 32: 35).
+    w = learned.bacteria_at_density(20000, 2)
+    S = System(w)
+    A = S.A_dense()
+    S.build_preconditioner()
+    b = S.rhs()
+    n = S.n
+    Pinv = np.column_stack([S.apply_preconditioner(e) for e in np.eye(n)])
+    lam, V = np.linalg.eig(A @ Pinv)
+    Wt = np.linalg.inv(V)
+    order = np.argsort(np.abs(lam))
+    order = order[np.abs(lam[order]) > 1e-8]
+    assert np.sum(np.abs(lam[order]) < 0.4) >= 15 * 2  # the cluster
+    sel = set(order[:8].tolist())
+    for i in list(sel):  # conjugate partners keep the correction real
+        if abs(lam[i].imag) > 0:
+            sel.add(int(np.argmin(np.abs(lam - np.conj(lam[i])))))
+    idx = np.array(sorted(sel))
+    corr = ((V[:, idx] * (1.0 / lam[idx] - 1.0)) @ Wt[idx, :]).real
+
+    def iterations(P):
+        return gmres_right(lambda y: A @ y, P, b, tol=1e-8, restart=50, max_iter=500)[1]
+
+    it_plain = iterations(S.apply_preconditioner)
+    it_defl = iterations(lambda r: Pinv @ (r + corr @ r))
+    assert it_plain >= 12
+    assert it_defl >= it_plain - 1, (it_plain, it_defl)
