@@ -738,6 +738,12 @@ int periodic_setup(am_handle* h) {
         // build over a solve) against 700 ps per grid point (the three
         // FP64 transforms each way, bound by the FP64 rate); the spreading
         // and interpolation do not depend on xi
+        // memory: the real-space pairs (60 bytes each with the listing
+        // codes; estimated from the mean density, so with a margin of two
+        // for clustered blobs) within a quarter of the free device memory
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)16 << 30;
+        const double pair_budget = 0.25 * (double)free_b / (2.0 * 60.0);
         double best = 1e300;
         for (int t = 0; t < 96; ++t) {
             const double x = xi_lo * std::pow(2.0, t / 8.0);
@@ -746,6 +752,7 @@ int periodic_setup(am_handle* h) {
             if (tot > (1LL << 31)) break;
             const double rc = 2.0 * a + crc / x;
             const double pairs = (double)Nb * (1.0 + dens * 4.0 / 3.0 * kPi * rc * rc * rc);
+            if (pairs > pair_budget) continue;
             const double cost = 20.0 * pairs + 700.0 * (double)tot;
             if (cost < best) {
                 best = cost;
