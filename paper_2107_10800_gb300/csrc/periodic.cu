@@ -484,34 +484,54 @@ __device__ __forceinline__ LaneMap lane_map(int Nb, int P) {
     return m;
 }
 
+// The lanes of a blob compute one window weight per axis each (their own
+// grid column, row and layer); before the loops every lane collects the w
+// weights and indices of the y and z axes into registers (4 w shuffles per
+// blob instead of two per inner iteration).
+template <int P>
+__device__ __forceinline__ void window_axes(const SpreadGeom& g, const LaneMap& m, const double4_32a& x, int& ix,
+                                            double& wx, int* iy, double* wy, int* iz, double* wz) {
+    int jy = 0, jz = 0;
+    double vy = 0.0, vz = 0.0;
+    ix = 0;
+    wx = 0.0;
+    if (m.lp < P) {
+        axis_weight(x.x, 0, g, m.lp, ix, wx);
+        axis_weight(x.y, 1, g, m.lp, jy, vy);
+        axis_weight(x.z, 2, g, m.lp, jz, vz);
+    }
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+        wy[t] = __shfl_sync(0xffffffffu, vy, m.base + t);
+        iy[t] = __shfl_sync(0xffffffffu, jy, m.base + t);
+        wz[t] = __shfl_sync(0xffffffffu, vz, m.base + t);
+        iz[t] = __shfl_sync(0xffffffffu, jz, m.base + t);
+    }
+}
+
+template <int P>
 __global__ void __launch_bounds__(256)
 k_per_spread(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const int* __restrict__ order,
              const double* __restrict__ lam, double* __restrict__ grid, long long ngrid) {
-    const LaneMap m = lane_map(Nb, g.P);
+    const LaneMap m = lane_map(Nb, P);
     const double4_32a x = spos[m.p];
     const int i = order[m.p];
     const double lx = lam[3 * (size_t)i], ly = lam[3 * (size_t)i + 1], lz = lam[3 * (size_t)i + 2];
-    int ix = 0, iy = 0, iz = 0;
-    double wx = 0.0, wy = 0.0, wz = 0.0;
-    if (m.lp < g.P) {
-        axis_weight(x.x, 0, g, m.lp, ix, wx);
-        axis_weight(x.y, 1, g, m.lp, iy, wy);
-        axis_weight(x.z, 2, g, m.lp, iz, wz);
-    }
-    const unsigned mask = 0xffffffffu;
-    for (int pz = 0; pz < g.P; ++pz) {
-        const double wzz = __shfl_sync(mask, wz, m.base + pz);
-        const int zz = __shfl_sync(mask, iz, m.base + pz);
-        for (int py = 0; py < g.P; ++py) {
-            const double wyz = __shfl_sync(mask, wy, m.base + py) * wzz;
-            const int yy = __shfl_sync(mask, iy, m.base + py);
-            if (m.live) {
-                const double w = wx * wyz;
-                const long long idx = ((long long)zz * g.M[1] + yy) * g.M[0] + ix;
-                atomicAdd(grid + idx, w * lx);
-                atomicAdd(grid + ngrid + idx, w * ly);
-                atomicAdd(grid + 2 * ngrid + idx, w * lz);
-            }
+    int ix, iy[P], iz[P];
+    double wx, wy[P], wz[P];
+    window_axes<P>(g, m, x, ix, wx, iy, wy, iz, wz);
+    if (!m.live) return;
+    const double ax = wx * lx, ay = wx * ly, az = wx * lz;
+#pragma unroll 1
+    for (int pz = 0; pz < P; ++pz) {
+        const long long zrow = (long long)iz[pz] * g.M[1];
+#pragma unroll
+        for (int py = 0; py < P; ++py) {
+            const double w = wy[py] * wz[pz];
+            const long long idx = (zrow + iy[py]) * g.M[0] + ix;
+            atomicAdd(grid + idx, w * ax);
+            atomicAdd(grid + ngrid + idx, w * ay);
+            atomicAdd(grid + 2 * ngrid + idx, w * az);
         }
     }
 }
@@ -544,16 +564,17 @@ __global__ void k_per_kmul(int Mx, int My, int Mz, double Lx, double Ly, double 
 // + the interpolation of the wave-space field at r_i with the window; the
 // lanes of lane_map, sums in a fixed order (lane-strided rows, the lanes of
 // a blob added in lane order through shared memory).
+template <int P>
 __global__ void __launch_bounds__(256)
 k_per_gather(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const int* __restrict__ order,
              const long long* __restrict__ row, const int* __restrict__ nbr, const double* __restrict__ blk,
              long long cap, const double* __restrict__ lam, const double* __restrict__ grid, long long ngrid,
              double* __restrict__ out) {
     __shared__ double part[256][3];
-    const LaneMap m = lane_map(Nb, g.P);
+    const LaneMap m = lane_map(Nb, P);
     double ux = 0.0, uy = 0.0, uz = 0.0;
     if (m.live) {
-        for (long long e = row[m.p] + m.lp; e < row[m.p + 1]; e += g.P) {
+        for (long long e = row[m.p] + m.lp; e < row[m.p + 1]; e += P) {
             const int j = nbr[e];
             const double lx = lam[3 * (size_t)j], ly = lam[3 * (size_t)j + 1], lz = lam[3 * (size_t)j + 2];
             const double m00 = blk[e], m01 = blk[cap + e], m02 = blk[2 * cap + e];
@@ -564,38 +585,32 @@ k_per_gather(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const i
         }
     }
     const double4_32a x = spos[m.p];
-    int ix = 0, iy = 0, iz = 0;
-    double wx = 0.0, wy = 0.0, wz = 0.0;
-    if (m.lp < g.P) {
-        axis_weight(x.x, 0, g, m.lp, ix, wx);
-        axis_weight(x.y, 1, g, m.lp, iy, wy);
-        axis_weight(x.z, 2, g, m.lp, iz, wz);
-    }
-    const unsigned mask = 0xffffffffu;
+    int ix, iy[P], iz[P];
+    double wx, wy[P], wz[P];
+    window_axes<P>(g, m, x, ix, wx, iy, wy, iz, wz);
     double vx = 0.0, vy = 0.0, vz = 0.0;
-    for (int pz = 0; pz < g.P; ++pz) {
-        const double wzz = __shfl_sync(mask, wz, m.base + pz);
-        const int zz = __shfl_sync(mask, iz, m.base + pz);
-        for (int py = 0; py < g.P; ++py) {
-            const double wyz = __shfl_sync(mask, wy, m.base + py) * wzz;
-            const int yy = __shfl_sync(mask, iy, m.base + py);
-            if (m.live) {
-                const long long idx = ((long long)zz * g.M[1] + yy) * g.M[0] + ix;
-                const double w = wx * wyz;
+    if (m.live) {
+#pragma unroll 1
+        for (int pz = 0; pz < P; ++pz) {
+            const long long zrow = (long long)iz[pz] * g.M[1];
+#pragma unroll
+            for (int py = 0; py < P; ++py) {
+                const long long idx = (zrow + iy[py]) * g.M[0] + ix;
+                const double w = wy[py] * wz[pz];
                 vx = fma(w, __ldg(grid + idx), vx);
                 vy = fma(w, __ldg(grid + ngrid + idx), vy);
                 vz = fma(w, __ldg(grid + 2 * ngrid + idx), vz);
             }
         }
     }
-    part[threadIdx.x][0] = ux + vx;
-    part[threadIdx.x][1] = uy + vy;
-    part[threadIdx.x][2] = uz + vz;
+    part[threadIdx.x][0] = fma(wx, vx, ux);
+    part[threadIdx.x][1] = fma(wx, vy, uy);
+    part[threadIdx.x][2] = fma(wx, vz, uz);
     __syncwarp();
     if (m.live && m.lp == 0) {
         const int t0 = threadIdx.x;  // the blob's first lane
         double sx = 0.0, sy = 0.0, sz = 0.0;
-        for (int l = 0; l < g.P; ++l) {
+        for (int l = 0; l < P; ++l) {
             sx += part[t0 + l][0];
             sy += part[t0 + l][1];
             sz += part[t0 + l][2];
@@ -604,6 +619,38 @@ k_per_gather(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const i
         out[3 * (size_t)i] = sx;
         out[3 * (size_t)i + 1] = sy;
         out[3 * (size_t)i + 2] = sz;
+    }
+}
+
+template <int P>
+void launch_window(int Nb, const SpreadGeom& g, const PeriodicPlan* p, const double* lam, double* out,
+                   bool spread, cudaStream_t s) {
+    const int per_block = 8 * (32 / P);  // blobs per 256-thread block (lane_map)
+    const int nb = (Nb + per_block - 1) / per_block;
+    if (spread)
+        k_per_spread<P><<<nb, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, lam, p->d_grid, p->ngrid);
+    else
+        k_per_gather<P><<<nb, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, p->d_row, p->d_nbr, p->d_blk, p->cap, lam,
+                                           p->d_grid, p->ngrid, out);
+}
+
+// window widths 4 .. 16 (tolerances 1e-3 .. 1e-15)
+void launch_window_any(int Nb, const SpreadGeom& g, const PeriodicPlan* p, const double* lam, double* out,
+                       bool spread, cudaStream_t s) {
+    switch (p->P) {
+        case 4: launch_window<4>(Nb, g, p, lam, out, spread, s); break;
+        case 5: launch_window<5>(Nb, g, p, lam, out, spread, s); break;
+        case 6: launch_window<6>(Nb, g, p, lam, out, spread, s); break;
+        case 7: launch_window<7>(Nb, g, p, lam, out, spread, s); break;
+        case 8: launch_window<8>(Nb, g, p, lam, out, spread, s); break;
+        case 9: launch_window<9>(Nb, g, p, lam, out, spread, s); break;
+        case 10: launch_window<10>(Nb, g, p, lam, out, spread, s); break;
+        case 11: launch_window<11>(Nb, g, p, lam, out, spread, s); break;
+        case 12: launch_window<12>(Nb, g, p, lam, out, spread, s); break;
+        case 13: launch_window<13>(Nb, g, p, lam, out, spread, s); break;
+        case 14: launch_window<14>(Nb, g, p, lam, out, spread, s); break;
+        case 15: launch_window<15>(Nb, g, p, lam, out, spread, s); break;
+        default: launch_window<16>(Nb, g, p, lam, out, spread, s); break;
     }
 }
 
@@ -707,7 +754,7 @@ int periodic_setup(am_handle* h) {
     p->tol = tol;
     for (int d = 0; d < 3; ++d) p->L[d] = h->cfg.box[d];
     const double lg = std::log(1.0 / tol);
-    p->P = std::min(32, std::max(4, (int)std::ceil(std::log10(1.0 / tol)) + 1));
+    p->P = std::min(16, std::max(4, (int)std::ceil(std::log10(1.0 / tol)) + 1));
     p->beta = 2.6 * p->P;
     const double xN = lg + std::log1p(lg), crc = std::sqrt(0.8 * lg);
     const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
@@ -971,15 +1018,12 @@ void launch_periodic(am_handle* h, const double* lam) {
     }
     const SpreadGeom g = spread_geom(p);
     k_per_zero<<<8 * num_sms(), 256, 0, s>>>(p->d_grid, 3 * p->ngrid);
-    const int per_block = 8 * (32 / p->P);  // blobs per 256-thread block (lane_map)
-    const int nblk_g = (Nb + per_block - 1) / per_block;
-    k_per_spread<<<nblk_g, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, lam, p->d_grid, p->ngrid);
+    launch_window_any(Nb, g, p, lam, h->d_mv, true, s);
     cufftExecD2Z(p->fwd, p->d_grid, p->d_hat);
     k_per_kmul<<<(int)((p->nhat + 255) / 256), 256, 0, s>>>(p->Mg[0], p->Mg[1], p->Mg[2], p->L[0], p->L[1],
                                                             p->L[2], p->d_kfac, p->d_hat, p->nhat);
     cufftExecZ2D(p->inv, p->d_hat, p->d_grid);
-    k_per_gather<<<nblk_g, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, p->d_row, p->d_nbr, p->d_blk, p->cap, lam,
-                                        p->d_grid, p->ngrid, h->d_mv);
+    launch_window_any(Nb, g, p, lam, h->d_mv, false, s);
     count_launch(4);
 }
 
