@@ -37,10 +37,13 @@ WORKLOAD = ("diatom colony above a no-slip wall: 32 rods of 2x40 blobs (2,560 bl
             "62 sliding links, dt=1e-3, FP64, GMRES relative residual 1e-8")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DRAM bytes (read + write) of one launch of the FP64 wall product on this
-# colony, from an ncu capture of the bench's own timed steps
+# colony (the symmetric kernel, rpy_sym_f64), from an ncu capture of the
+# colony's steps (profile_cases colony --host-steps)
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where no capture of
 # the kernel as it now stands exists
-TRAFFIC_BYTES = {"fp64": 196864, "mixed": None}
+TRAFFIC_BYTES = {"fp64": 218368, "mixed": None}
+# flop per unordered pair of the symmetric FP64 wall product (see run_ours)
+SYM_WALL_FLOP_PER_UNORDERED_PAIR = 126
 
 
 def parse():
@@ -783,12 +786,26 @@ def run_ours(args):
     fpp = binding.flops_per_pair(1)
     avg_launch_s = (mob_ms * 1e-3) / max(mob_launches, 1)
     achieved = nb * nb * fpp / avg_launch_s
+    layout = solver.mobility_layout()
+    if layout[3] > 0:
+        # symmetric FP64 product: each unordered pair evaluated once and applied
+        # both ways, 126 flop per unordered pair (FMA = 2, rsqrt = 1, counted
+        # from pair_wall_sym and the pair's distances) against 2 x 119
+        kname = "rpy_sym_f64<wall, tile %d>" % layout[3]
+        executed = nb * (nb + 1) / 2 * SYM_WALL_FLOP_PER_UNORDERED_PAIR / avg_launch_s
+    else:
+        kname = "rpy_items_%s<wall>" % ("f64" if args.precision == "fp64" else "mixed")
+        executed = achieved
     peak = fp64_peak if args.precision == "fp64" else fp32_peak
     clocks = clk.summary()
     roofline = {"bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_BYTES[args.precision],
-                "kernel": "rpy_items_%s<wall>" % ("f64" if args.precision == "fp64" else "mixed"),
+                "traffic": TRAFFIC_BYTES[args.precision] if layout[3] > 0 or args.precision != "fp64" else None,
+                "kernel": kname, "layout": list(layout),
+                "executed_tflops": executed / 1e12, "executed_frac": executed / peak,
+                "algorithmic_vs_executed": "achieved counts N^2 pairs x 119 flop per launch; the symmetric "
+                                           "kernel executes N(N+1)/2 x 126, so frac can exceed the FP64 "
+                                           "pipe's busy fraction" if layout[3] > 0 else None,
                 "flop_per_pair": fpp, "pairs_per_launch": nb * nb,
                 "launch_ms": avg_launch_s * 1e3, "launches": mob_launches,
                 "launch_timing": "CUDA events around each launch in %d further steps "

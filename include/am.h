@@ -294,6 +294,17 @@ AM_API int am_steric_forces(am_handle* h, double* f);
  * bodies, values out of range), AM_ERR_CUDA. */
 AM_API int am_set_mobility_layout(am_handle* h, int targets_per_thread, int source_chunk);
 
+/* The layout of the all-pairs product in use (after the autotuning of the
+ * first product): layout[0] targets per thread, [1] source chunk (blobs),
+ * [2] targets per work item, [3] tile of the symmetric FP64 product (32,
+ * 64 or 128 blobs; 0 when the one-direction kernel runs).  The symmetric
+ * product (FP64 handles) evaluates each unordered pair of blobs once and
+ * applies it in both directions (M_ji = M_ij^T); the autotuner takes it when
+ * it is faster and its partial sums (one slot per tile) fit in 1 GiB.  A
+ * measurement aid, not in the paper.  Errors: AM_ERR_ARG (NULL, no
+ * bodies). */
+AM_API int am_get_mobility_layout(am_handle* h, int* layout);
+
 /* y -> A y for the full operator of Eq. linear_system at the current pose
  * (y and Ay: 3Nb + 6M + 3P, ordered (lambda, U, phi)). */
 AM_API int am_apply_operator(am_handle* h, const double* y, double* Ay);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "am_apply_mobility": (ctypes.c_int, [_vp, _dp, _dp]),
     "am_apply_mobility_ex": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int]),
     "am_set_mobility_layout": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "am_get_mobility_layout": (ctypes.c_int, [_vp, _ip]),
     "am_set_repulsion": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double]),
     "am_steric_forces": (ctypes.c_int, [_vp, _dp]),
@@ -331,6 +332,13 @@ class Solver:
         return {"xi": d[0], "r_c": d[1], "sigma": d[2], "h": tuple(d[3:6]),
                 "grid": tuple(int(v) for v in i[0:3]), "support": int(i[3]),
                 "real_pairs": int(i[4]), "cells": int(i[5])}
+
+    def mobility_layout(self):
+        """(targets per thread, source chunk, targets per item, symmetric
+        tile or 0) of the all-pairs product in use (am_get_mobility_layout)."""
+        a = np.zeros(4, np.int32)
+        self._check(lib().am_get_mobility_layout(self.h, a.ctypes.data_as(_ip)))
+        return tuple(int(v) for v in a)
 
     def set_repulsion(self, eps, range_, cutoff, eps_wall=0.0, range_wall=1.0):
         """Steric repulsion between articulated bodies and with the wall."""

@@ -185,6 +185,9 @@ struct am_handle {
     int mv_tpt = 1, mv_chunk = 0, mv_tgroup = 0, mv_grid = 0, mv_grid64 = 0, mv_griddf = 0;
     long long mv_part_total = 0;
     bool mv_tuned = false;
+    // tile-pair items of the symmetric FP64 product (tiles of 32 sym_nsub blobs)
+    void* d_sym_items = nullptr;
+    int n_sym = 0, sym_nsub = 0, mv_gridsym = 0;
 
     // host structure
     std::vector<int> blob_off, asm_of_body, bp, bq;

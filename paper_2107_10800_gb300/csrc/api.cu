@@ -162,6 +162,9 @@ void free_solver(am_handle* h) {
     if (h->d_items) cudaFree(h->d_items);
     h->d_items = nullptr;
     h->n_items = 0;
+    if (h->d_sym_items) cudaFree(h->d_sym_items);
+    h->d_sym_items = nullptr;
+    h->n_sym = 0;
 }
 
 int alloc_solver(am_handle* h) {
@@ -1362,6 +1365,18 @@ extern "C" AM_API int am_set_mobility_layout(am_handle* h, int targets_per_threa
     if (am::mobility_layout(h, targets_per_thread, source_chunk))
         return set_err(h, AM_ERR_CUDA, "am_set_mobility_layout: device allocation failed");
     h->mv_tuned = true;
+    return AM_OK;
+}
+
+extern "C" AM_API int am_get_mobility_layout(am_handle* h, int* layout) {
+    if (!h) return AM_ERR_ARG;
+    if (!layout) return set_err(h, AM_ERR_ARG, "am_get_mobility_layout: NULL array");
+    const int rc = check_handle(h, "am_get_mobility_layout", true);
+    if (rc) return rc;
+    layout[0] = h->mv_tpt;
+    layout[1] = h->mv_chunk;
+    layout[2] = h->mv_tgroup;
+    layout[3] = h->n_sym > 0 ? 32 * h->sym_nsub : 0;
     return AM_OK;
 }
 

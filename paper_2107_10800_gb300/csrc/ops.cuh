@@ -43,7 +43,7 @@ int advance(am_handle* h, double dt, am_step_stats* st);
 // Block-diagonal mobility product of all systems (rpy.cu): work items for
 // tpt targets per thread and source chunks (0 = automatic), their launch,
 // the sum of the partials, and the autotuner that picks (tpt, chunk).
-int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup = 0);
+int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup = 0, int sym = 0);
 void launch_items(am_handle* h, const double* lam, int mode, const int* active = nullptr);
 int df_resident_grid(bool wall);
 void launch_items_df(am_handle* h, const double* lam);

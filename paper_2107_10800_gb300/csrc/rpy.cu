@@ -516,6 +516,142 @@ rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam
     item_queue_done(counter);
 }
 
+// One item of the symmetric FP64 product: tiles I (targets) and J (sources)
+// of T = 32 NSUB blobs of one system with I <= J; the pairs between them are
+// evaluated once and give the rows of I (slot J) and the columns of J (slot
+// I); the diagonal item (I = J) takes each unordered pair of its tile once
+// and writes rows and columns together.
+struct SymItem {
+    int i0, ni, j0, nj;     // first blob and count of tile I and of tile J
+    int tbase, sys;         // first blob of the system, system
+    int ti, tj;             // tile indices within the system (partial-sum slots)
+    long long poff;         // the system's partial-sum offset
+    int n3, pad;            // 3 N_s
+};
+
+// Symmetric FP64 product (the mobility is symmetric: M_ji = M_ij^T).  Per
+// item the block stages both tiles; its warps take the item's NSUB x NSUB
+// warp tiles (32 targets x 32 sources) in turn.  In a warp tile lane l
+// holds target l and, at step t, meets source (l + t) mod 32: u_l gathers
+// M lambda_source, and the source's column sum v (M^T mu_l) is carried
+// from lane to lane (lane l hands it to lane l - 1), so after 32 steps it
+// is back on the source's lane with the sum over the 32 targets.  On the
+// diagonal of a diagonal item the steps 1..15, and 16 on lanes 0..15, take
+// every unordered pair once (step 0: the self term).  Warp-tile sums go to
+// shared memory and are added in a fixed order: the result does not
+// depend on scheduling.
+template <bool WALL, int NSUB>
+__global__ void __launch_bounds__(NSUB == 1 ? 32 : 128)
+rpy_sym_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam, double* __restrict__ part,
+            const SymItem* __restrict__ items, int n_items, int* __restrict__ counter, RpyK<double> k,
+            const int* __restrict__ active) {
+    constexpr int T = 32 * NSUB;
+    constexpr int NW = NSUB == 1 ? 1 : 4;
+    constexpr int NWT = NSUB * NSUB;
+    __shared__ double4_32a sI[T], sJ[T];
+    __shared__ double lI[3 * T], lJ[3 * T];
+    __shared__ double up[NWT][32][3], vp[NWT][32][3];
+    __shared__ int s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int round = 0;; ++round) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(counter, 1);
+        __syncthreads();
+        const int itn = s_item;
+        if (itn >= n_items) break;
+        const SymItem m = items[itn];
+        const bool diag = m.ti == m.tj;
+        double* rowo = part + m.poff + (long long)m.tj * m.n3 + 3 * (long long)(m.i0 - m.tbase);
+        double* colo = part + m.poff + (long long)m.ti * m.n3 + 3 * (long long)(m.j0 - m.tbase);
+        if (active && !active[m.sys]) {  // a stopped system: zero partial sums
+            for (int q = threadIdx.x; q < 3 * m.ni; q += blockDim.x) rowo[q] = 0.0;
+            if (!diag)
+                for (int q = threadIdx.x; q < 3 * m.nj; q += blockDim.x) colo[q] = 0.0;
+            continue;
+        }
+        for (int q = threadIdx.x; q < T; q += blockDim.x) {
+            double4_32a a = q < m.ni ? r4[m.i0 + q] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
+            a.w = 2.0 * a.z;
+            sI[q] = a;
+            double4_32a b = q < m.nj ? r4[m.j0 + q] : make_double4_32a(0.0, 0.0, 1.0, 0.0);
+            b.w = 2.0 * b.z;
+            sJ[q] = b;
+        }
+        for (int q = threadIdx.x; q < 3 * T; q += blockDim.x) {
+            lI[q] = q < 3 * m.ni ? lam[3 * (size_t)m.i0 + q] : 0.0;
+            lJ[q] = q < 3 * m.nj ? lam[3 * (size_t)m.j0 + q] : 0.0;
+        }
+        __syncthreads();
+        for (int wt = warp; wt < NWT; wt += NW) {
+            const int a = wt / NSUB, b = wt % NSUB;
+            double ux = 0.0, uy = 0.0, uz = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
+            if (!(diag && b < a)) {  // below the diagonal of a diagonal item: taken by (b, a)
+                const bool self_tile = diag && a == b;
+                const int t = 32 * a + lane;
+                const double4_32a xi = sI[t];
+                const double mx = lI[3 * t], my = lI[3 * t + 1], mz = lI[3 * t + 2];
+                const double nx3 = -xi.z;
+                const bool ti_ok = t < m.ni;
+#pragma unroll 1
+                for (int step = 0; step < 32; ++step) {
+                    const int q = 32 * b + ((lane + step) & 31);
+                    const bool pair_ok = ti_ok && q < m.nj &&
+                                         (!self_tile || (step >= 1 && (step < 16 || (step == 16 && lane < 16))));
+                    if (pair_ok) {
+                        const double4_32a xj = sJ[q];
+                        const double lx = lJ[3 * q], ly = lJ[3 * q + 1], lz = lJ[3 * q + 2];
+                        const double dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+                        if (WALL) {
+                            const double rxy2 = fma(dx, dx, dy * dy);
+                            pair_wall_sym<double>(dx, dy, dz, rxy2, fma(dz, dz, rxy2), xi.z + xj.z, xj.w, nx3, lx,
+                                                  ly, lz, mx, my, mz, k, ux, uy, uz, vx, vy, vz);
+                        } else {
+                            pair_free_sym<double>(dx, dy, dz, fma(dx, dx, fma(dy, dy, dz * dz)), lx, ly, lz, mx,
+                                                  my, mz, k, ux, uy, uz, vx, vy, vz);
+                        }
+                    } else if (self_tile && step == 0 && ti_ok) {  // the self term
+                        if (WALL)
+                            pair_wall_r2<double>(0.0, 0.0, 0.0, 0.0, 0.0, 2.0 * xi.z, xi.w, nx3, mx, my, mz, k, ux,
+                                                 uy, uz);
+                        else
+                            pair_free<double>(0.0, 0.0, 0.0, mx, my, mz, k, ux, uy, uz);
+                    }
+                    // hand the column sum to the lane that meets this source next
+                    const int src = (lane + 1) & 31;
+                    vx = __shfl_sync(0xffffffffu, vx, src);
+                    vy = __shfl_sync(0xffffffffu, vy, src);
+                    vz = __shfl_sync(0xffffffffu, vz, src);
+                }
+            }
+            up[wt][lane][0] = ux; up[wt][lane][1] = uy; up[wt][lane][2] = uz;
+            vp[wt][lane][0] = vx; vp[wt][lane][1] = vy; vp[wt][lane][2] = vz;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            const int a = t >> 5, l = t & 31;
+            if (t < m.ni) {
+                double sx = 0.0, sy = 0.0, sz = 0.0;
+                for (int b = 0; b < NSUB; ++b) {
+                    sx += up[a * NSUB + b][l][0]; sy += up[a * NSUB + b][l][1]; sz += up[a * NSUB + b][l][2];
+                }
+                if (diag)
+                    for (int a2 = 0; a2 < NSUB; ++a2) {
+                        sx += vp[a2 * NSUB + a][l][0]; sy += vp[a2 * NSUB + a][l][1]; sz += vp[a2 * NSUB + a][l][2];
+                    }
+                rowo[3 * t] = k.A1 * sx; rowo[3 * t + 1] = k.A1 * sy; rowo[3 * t + 2] = k.A1 * sz;
+            }
+            if (!diag && t < m.nj) {
+                double sx = 0.0, sy = 0.0, sz = 0.0;
+                for (int a2 = 0; a2 < NSUB; ++a2) {
+                    sx += vp[a2 * NSUB + a][l][0]; sy += vp[a2 * NSUB + a][l][1]; sz += vp[a2 * NSUB + a][l][2];
+                }
+                colo[3 * t] = k.A1 * sx; colo[3 * t + 1] = k.A1 * sy; colo[3 * t + 2] = k.A1 * sz;
+            }
+        }
+    }
+    item_queue_done(counter);
+}
+
 template <bool WALL, int TPT>
 __global__ void __launch_bounds__(kThreads, 4)
 rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
@@ -812,19 +948,37 @@ __global__ void k_sum_items(int Nb, const double* __restrict__ part, const int* 
 }
 
 template <class F>
-static int resident_grid(F kernel) {
+static int resident_grid(F kernel, int threads = kThreads) {
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0) != cudaSuccess || per <= 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess || per <= 0)
         per = 4;
     return per * num_sms();
 }
 
+// resident blocks of the symmetric FP64 kernel for nsub (1, 2, 4)
+static int sym_grid(bool wall, int nsub) {
+    const int th = nsub == 1 ? 32 : 128;
+    if (wall) {
+        if (nsub == 1) return resident_grid(rpy_sym_f64<true, 1>, th);
+        if (nsub == 2) return resident_grid(rpy_sym_f64<true, 2>, th);
+        return resident_grid(rpy_sym_f64<true, 4>, th);
+    }
+    if (nsub == 1) return resident_grid(rpy_sym_f64<false, 1>, th);
+    if (nsub == 2) return resident_grid(rpy_sym_f64<false, 2>, th);
+    return resident_grid(rpy_sym_f64<false, 4>, th);
+}
+
 // Work items for tpt targets per thread and source chunks of `chunk` blobs
-// (0: choose so that the items fill the GPU).  Returns 0 on success.
-int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup) {
+// (0: choose so that the items fill the GPU); with sym = nsub > 0 (FP64
+// handles) also the tile-pair items of the symmetric FP64 product on tiles
+// of 32 nsub blobs, whose partial-sum slots are the source chunks of that
+// length.  Returns 0 on success.
+int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup, int sym) {
     const int S = h->S;
     if (h->cfg.precision != AM_MIXED) tpt = 1;
     if (h->per) chunk = std::max(1, h->Nb);  // the periodic product writes u in one piece
+    if (h->per || h->cfg.precision != AM_FP64) sym = 0;
+    if (sym) chunk = 32 * sym;
     // targets per item: a block's targets, or (one target per thread) 32 or
     // 64 of them so that small systems spread over more SMs
     if (tpt == 2 || tgroup <= 0 || tgroup > kThreads || tgroup % 32) tgroup = kThreads * tpt;
@@ -860,7 +1014,36 @@ int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup) {
     std::stable_sort(items.begin(), items.end(), [](const MvItem& a, const MvItem& b) {
         return (long long)(a.t1 - a.t0) * (a.j1 - a.j0) > (long long)(b.t1 - b.t0) * (b.j1 - b.j0);
     });
+    std::vector<SymItem> sitems;
+    if (sym) {
+        const int T = 32 * sym;
+        for (int s = 0; s < S; ++s) {
+            const int nb = h->sys[s].Nb, b0 = h->sys_blob0[s];
+            const int nt = (nb + T - 1) / T;
+            for (int a = 0; a < nt; ++a)
+                for (int b = a; b < nt; ++b) {
+                    SymItem it;
+                    it.i0 = b0 + a * T; it.ni = std::min(T, nb - a * T);
+                    it.j0 = b0 + b * T; it.nj = std::min(T, nb - b * T);
+                    it.tbase = b0; it.sys = s; it.ti = a; it.tj = b;
+                    it.poff = poff[s]; it.n3 = 3 * nb; it.pad = 0;
+                    sitems.push_back(it);
+                }
+        }
+    }
     cudaStream_t st = h->stream;
+    if (h->d_sym_items) cudaFree(h->d_sym_items);
+    h->d_sym_items = nullptr;
+    h->n_sym = 0;
+    if (!sitems.empty()) {
+        if (cudaMalloc(&h->d_sym_items, sitems.size() * sizeof(SymItem)) != cudaSuccess ||
+            cudaMemcpyAsync(h->d_sym_items, sitems.data(), sitems.size() * sizeof(SymItem), cudaMemcpyHostToDevice,
+                            st) != cudaSuccess)
+            return 1;
+        h->n_sym = (int)sitems.size();
+        h->sym_nsub = sym;
+        h->mv_gridsym = std::min(sym_grid(h->cfg.wall != 0, sym), h->n_sym);
+    }
     if (h->d_items) cudaFree(h->d_items);
     h->d_items = nullptr;
     if (h->d_mv) cudaFree(h->d_mv);
@@ -912,7 +1095,20 @@ void launch_items(am_handle* h, const double* lam, int mode, const int* active) 
     const bool fp64 = mode == kOpFP64 || (mode == kOpHandle && h->cfg.precision == AM_FP64);
     cudaStream_t st = h->stream;  // the queue counter is zero (reset by the last launch's last block)
     const MvItem* items = static_cast<const MvItem*>(h->d_items);
-    if (fp64) {
+    if (fp64 && h->n_sym > 0) {
+        const RpyK<double> k = rpy_consts<double>(h->prm);
+        const SymItem* si = static_cast<const SymItem*>(h->d_sym_items);
+        const int th = h->sym_nsub == 1 ? 32 : 128;
+#define AM_SYM(W, N)                                                                                      \
+    rpy_sym_f64<W, N><<<h->mv_gridsym, th, 0, st>>>(h->d_r4, lam, h->d_mv, si, h->n_sym, h->d_item_counter, \
+                                                    k, active)
+        if (h->cfg.wall) {
+            if (h->sym_nsub == 1) AM_SYM(true, 1); else if (h->sym_nsub == 2) AM_SYM(true, 2); else AM_SYM(true, 4);
+        } else {
+            if (h->sym_nsub == 1) AM_SYM(false, 1); else if (h->sym_nsub == 2) AM_SYM(false, 2); else AM_SYM(false, 4);
+        }
+#undef AM_SYM
+    } else if (fp64) {
         const RpyK<double> k = rpy_consts<double>(h->prm);
         if (h->cfg.wall)
             rpy_items_f64<true><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,
@@ -953,14 +1149,14 @@ int mobility_autotune(am_handle* h) {
         h->mv_tuned = true;
         return 0;
     }
-    struct Cand { int tpt, chunk, tgroup; };
+    struct Cand { int tpt, chunk, tgroup, sym; };
     std::vector<Cand> cand;
     const bool mixed = h->cfg.precision == AM_MIXED;
     long long maxnb = 0;
     for (const auto& r : h->sys) maxnb = std::max<long long>(maxnb, r.Nb);
     for (int tpt : (mixed ? std::vector<int>{1, 2} : std::vector<int>{1}))
         for (int chunk : {0, 512, 1024, 2048, 4096, 8192})
-            if (chunk == 0 || chunk <= 2 * maxnb) cand.push_back({tpt, chunk, 0});
+            if (chunk == 0 || chunk <= 2 * maxnb) cand.push_back({tpt, chunk, 0, 0});
     // One system of modest size: the items all start at once, so the
     // slowest SM sets the time; chunks that make the item count a multiple
     // of the SM count (k = 1..6 items per SM) balance the last wave.  Small
@@ -976,10 +1172,19 @@ int mobility_autotune(am_handle* h) {
                 for (int k = 1; k <= 6; ++k) {
                     const long long c = ((long long)k * num_sms() + ntb - 1) / ntb;  // chunks per system
                     const long long chunk = (maxnb + c - 1) / c;
-                    if (chunk >= 32) cand.push_back({tpt, (int)chunk, tg == kThreads * tpt ? 0 : tg});
+                    if (chunk >= 32) cand.push_back({tpt, (int)chunk, tg == kThreads * tpt ? 0 : tg, 0});
                 }
-                if (tg != kThreads * tpt) cand.push_back({tpt, 32, tg});
+                if (tg != kThreads * tpt) cand.push_back({tpt, 32, tg, 0});
             }
+        }
+    }
+    // FP64: the symmetric product on tiles of 32, 64 and 128 blobs, while its
+    // partial sums (one slot per tile of the system) stay within 1 GiB
+    if (h->cfg.precision == AM_FP64) {
+        for (int nsub : {1, 2, 4}) {
+            long long slots = 0;
+            for (const auto& r : h->sys) slots += (long long)((r.Nb + 32 * nsub - 1) / (32 * nsub)) * 3 * r.Nb;
+            if (slots * 8 <= (1LL << 30)) cand.push_back({1, 32 * nsub, 0, nsub});
         }
     }
     cudaStream_t st = h->stream;
@@ -994,7 +1199,7 @@ int mobility_autotune(am_handle* h) {
     const bool timing = h->timing;
     h->timing = false;
     for (auto c : cand) {
-        if (mobility_layout(h, c.tpt, c.chunk, c.tgroup)) continue;
+        if (mobility_layout(h, c.tpt, c.chunk, c.tgroup, c.sym)) continue;
         launch_items(h, lam, false);  // warm-up
         cudaEventRecord(e0, st);
         launch_items(h, lam, false);
@@ -1011,7 +1216,7 @@ int mobility_autotune(am_handle* h) {
     cudaFree(lam);
     cudaGetLastError();
     h->mv_tuned = true;
-    return mobility_layout(h, pick.tpt, pick.chunk, pick.tgroup);
+    return mobility_layout(h, pick.tpt, pick.chunk, pick.tgroup, pick.sym);
 }
 
 }  // namespace am

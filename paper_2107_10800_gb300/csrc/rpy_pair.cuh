@@ -182,6 +182,82 @@ __device__ __forceinline__ void pair_wall_r2(T dx, T dy, T dz, T rxy2, T r2, T R
     uz = fma(cc, lz, fma(sdl, dz, fma(P, Rz, uz + Q)));
 }
 
+// Both directions of one pair from one evaluation (the mobility is
+// symmetric: M_ji = M_ij^T).  u/A1 += M_ij lambda_j at the target as
+// pair_wall_r2 (same arguments: d = x_i - x_j, Rz = z_i + z_j, h2 = 2 z_j,
+// nx3 = -z_i) and v/A1 += M_ij^T mu_i at the source, the velocity that
+// target i's force mu causes there.  Written as a tensor applied to lambda,
+// pair_wall_r2 is
+//   cc I + c2f d d^T + s^3 cRR R R^T + s^3 g R e3^T
+//        + s^3 e3 (h2 d^T - (20/3) a^4 w^2 Rz R^T) + s^3 phi e3 e3^T,
+// g = Rz inner + h2, phi = w (c2-term of Q), so the transpose multiplies mu
+// with the d, R and e3 coefficients
+//   c2f (d . mu) + s^3 h2 mu_3,  s^3 cRR (R . mu) - (20/3) s^3 a^4 w^2 Rz mu_3,
+//   s^3 g (R . mu) + s^3 phi mu_3.
+// The coefficients are shared; the second direction costs about 20
+// operations against about 60 for a separate evaluation.
+template <class T>
+__device__ __forceinline__ void pair_wall_sym(T dx, T dy, T dz, T rxy2, T r2, T Rz, T h2, T nx3, T lx, T ly,
+                                              T lz, T mx, T my, T mz, const RpyK<T>& k, T& ux, T& uy, T& uz,
+                                              T& vx, T& vy, T& vz) {
+    const T Rz2 = Rz * Rz;
+    T c1f, c2f;
+    free_coefs<T>(r2, k, c1f, c2f);
+    const T s = rsq(rxy2 + Rz2);
+    const T w = s * s, s3 = s * w, w2 = w * w;
+    const T c1 = fma(h2, nx3, k.wc1);
+    const T c2 = fma(Rz2, k.w2a2, k.wc2);
+    const T c3 = Rz2 * k.wc3;
+    const T x1 = fma(w, c3, c2);
+    const T cI = fma(w, fma(w, x1, c1), (T)-1);
+    const T y = fma(w, c3, x1);                 // c2 + 2 w c3
+    const T yz = fma(w, c3, y);                 // c2 + 3 w c3
+    const T cRR = fma(w2 * y, (T)-2, fma(cI, (T)-3, (T)-4));
+    const T A4w2n = w2 * -k.wa4;                // -20/3 a^4 w^2
+    const T cc = fma(s, cI, c1f);
+    const T g = fma(Rz, fma(cRR, (T)-2, fma(A4w2n, (T)-1, (T)-2)), h2);
+    const T s3cRR = s3 * cRR, s3g = s3 * g, s3h2 = s3 * h2;
+    const T s3A = s3 * (A4w2n * Rz), s3phi = s3 * (w * fma(yz, (T)-2, k.wi2));
+    {   // u += M_ij lambda
+        const T dlxy = fma(dx, lx, dy * ly);
+        const T Df = fma(dz, lz, dlxy), Di = fma(Rz, lz, dlxy);
+        const T sdl = c2f * Df;
+        const T P = fma(s3cRR, Di, s3g * lz);
+        const T Q = fma(s3h2, Df, fma(s3A, Di, s3phi * lz));
+        const T pp = sdl + P;
+        ux = fma(cc, lx, fma(pp, dx, ux));
+        uy = fma(cc, ly, fma(pp, dy, uy));
+        uz = fma(cc, lz, fma(sdl, dz, fma(P, Rz, uz + Q)));
+    }
+    {   // v += M_ij^T mu
+        const T dmxy = fma(dx, mx, dy * my);
+        const T Df = fma(dz, mz, dmxy), Di = fma(Rz, mz, dmxy);
+        const T cd = fma(c2f, Df, s3h2 * mz);
+        const T P = fma(s3cRR, Di, s3A * mz);
+        const T Q = fma(s3g, Di, s3phi * mz);
+        const T pp = cd + P;
+        vx = fma(cc, mx, fma(pp, dx, vx));
+        vy = fma(cc, my, fma(pp, dy, vy));
+        vz = fma(cc, mz, fma(cd, dz, fma(P, Rz, vz + Q)));
+    }
+}
+
+// Free space: the RPY tensor is symmetric in the pair and even in d
+template <class T>
+__device__ __forceinline__ void pair_free_sym(T dx, T dy, T dz, T r2, T lx, T ly, T lz, T mx, T my, T mz,
+                                              const RpyK<T>& k, T& ux, T& uy, T& uz, T& vx, T& vy, T& vz) {
+    T c1, c2;
+    free_coefs<T>(r2, k, c1, c2);
+    const T sl = c2 * fma(dx, lx, fma(dy, ly, dz * lz));
+    const T sm = c2 * fma(dx, mx, fma(dy, my, dz * mz));
+    ux = fma(c1, lx, fma(sl, dx, ux));
+    uy = fma(c1, ly, fma(sl, dy, uy));
+    uz = fma(c1, lz, fma(sl, dz, uz));
+    vx = fma(c1, mx, fma(sm, dx, vx));
+    vy = fma(c1, my, fma(sm, dy, vy));
+    vz = fma(c1, mz, fma(sm, dz, vz));
+}
+
 // Full 3x3 tensor T (row-major, T[3a+b]: velocity a at x from force b at y),
 // FP64, including the 1/(8 pi eta) factor.
 __device__ __forceinline__ void pair_tensor_f64(double4_32a x, double4_32a y, const RpyK<double>& k,
