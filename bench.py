@@ -222,8 +222,8 @@ def matvec_at_scale(torch, binding, W, stream, fp32_peak, fp64_peak):
     """The solver's all-pairs wall product at the bacteria-suspension scale
     (1,000 bacteria, 360,000 blobs, a = 0.05): the mixed work-queue kernel
     with two targets per thread in paired FP32 lanes and 4,096-source chunks
-    on all blobs, the FP64 kernel on the first 40,000 (an FP64 product on
-    all blobs takes about 20 s).  The blobs are single-blob bodies of one
+    on all blobs, the FP64 kernels (one-direction and symmetric, tiles of
+    128) on the first 40,000 (an FP64 product on all blobs takes about 20 s).  The blobs are single-blob bodies of one
     handle; kernel time from CUDA events around each launch
     (am_mobility_timing), after a warm-up product."""
     w = W.bacteria_wall(1)
@@ -233,7 +233,9 @@ def matvec_at_scale(torch, binding, W, stream, fp32_peak, fp64_peak):
     out = {"workload": "bacteria above a wall: 1,000 x (200-blob head + 16 x 10-blob flagellum), "
                        "360,000 blobs, a=0.05"}
     fpp = binding.flops_per_pair(1)
-    for prec, n, layout, peak in (("mixed", len(R), (2, 4096), fp32_peak), ("fp64", 40_000, (1, 0), fp64_peak)):
+    for key, prec, n, layout, peak in (("mixed", "mixed", len(R), (2, 4096), fp32_peak),
+                                       ("fp64", "fp64", 40_000, (1, 0), fp64_peak),
+                                       ("fp64_symmetric", "fp64", 40_000, (3, 128), fp64_peak)):
         r = R[:n]
         s = binding.Solver(eta=w["eta"], a=w["a"], wall=1, precision=prec)
         s.set_bodies(r, np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)), np.arange(n + 1), np.zeros((n, 3)),
@@ -248,9 +250,10 @@ def matvec_at_scale(torch, binding, W, stream, fp32_peak, fp64_peak):
         s.close()
         t = ms * 1e-3 / max(launches, 1)
         pairs = float(n) * n
-        out[prec] = {"blobs": n, "ms": t * 1e3, "pairs_per_s": pairs / t,
-                     "tflops": pairs * fpp / t / 1e12, "frac_of_fma_peak": pairs * fpp / t / peak,
-                     "kernel": "rpy_items_mixed_x2<wall>" if prec == "mixed" else "rpy_items_f64<wall>"}
+        out[key] = {"blobs": n, "ms": t * 1e3, "pairs_per_s": pairs / t,
+                    "tflops": pairs * fpp / t / 1e12, "frac_of_fma_peak": pairs * fpp / t / peak,
+                    "kernel": {"mixed": "rpy_items_mixed_x2<wall>", "fp64": "rpy_items_f64<wall>",
+                               "fp64_symmetric": "rpy_sym_f64<wall, tile 128>"}[key]}
     return out
 
 

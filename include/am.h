@@ -288,7 +288,9 @@ AM_API int am_steric_forces(am_handle* h, double* f);
  * items of 128 x targets_per_thread targets (2: two targets per thread in
  * paired FP32 lanes; mixed precision only, FP64 handles use 1) against
  * source chunks of source_chunk blobs (0: a default that fills the GPU).
- * targets_per_thread = 0 restores autotuning before the next product.  The
+ * targets_per_thread = 0 restores autotuning before the next product;
+ * targets_per_thread = 3 selects the symmetric FP64 product (FP64 handles
+ * without a box) on tiles of source_chunk = 32, 64 or 128 blobs.  The
  * layout is rebuilt (and autotuned) whenever the bodies change.  A
  * measurement and testing aid, not in the paper.  Errors: AM_ERR_ARG (no
  * bodies, values out of range), AM_ERR_CUDA. */

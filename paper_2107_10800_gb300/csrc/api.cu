@@ -1355,11 +1355,21 @@ extern "C" AM_API int am_set_mobility_layout(am_handle* h, int targets_per_threa
     if (!h) return AM_ERR_ARG;
     int rc = check_handle(h, "am_set_mobility_layout", true);
     if (rc) return rc;
-    if (targets_per_thread < 0 || targets_per_thread > 2 || source_chunk < 0)
-        return set_err(h, AM_ERR_ARG, "am_set_mobility_layout: targets_per_thread must be 0, 1 or 2 and "
+    if (targets_per_thread < 0 || targets_per_thread > 3 || source_chunk < 0)
+        return set_err(h, AM_ERR_ARG, "am_set_mobility_layout: targets_per_thread must be 0 .. 3 and "
                                       "source_chunk >= 0");
     if (targets_per_thread == 0) {
         h->mv_tuned = false;  // tuned again before the next product
+        return AM_OK;
+    }
+    if (targets_per_thread == 3) {  // the symmetric FP64 product on tiles of source_chunk blobs
+        if (h->cfg.precision != AM_FP64 || box_set(h->cfg) || h->sb ||
+            (source_chunk != 32 && source_chunk != 64 && source_chunk != 128))
+            return set_err(h, AM_ERR_ARG, "am_set_mobility_layout: the symmetric product needs an FP64 handle "
+                                          "(no box, multi-blob bodies) and tiles of 32, 64 or 128 blobs");
+        if (am::mobility_layout(h, 1, source_chunk, 0, source_chunk / 32))
+            return set_err(h, AM_ERR_CUDA, "am_set_mobility_layout: device allocation failed");
+        h->mv_tuned = true;
         return AM_OK;
     }
     if (am::mobility_layout(h, targets_per_thread, source_chunk))

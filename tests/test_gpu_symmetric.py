@@ -1,0 +1,83 @@
+"""The symmetric FP64 all-pairs product (each unordered pair evaluated once
+and applied in both directions, M_ji = M_ij^T; rpy_sym_f64 in csrc/rpy.cu)
+through the C ABI, forced on every tile size: against the oracle's product
+at the FP64 bar (1e-12, max-abs over max-abs) and against the one-direction
+kernel, on sizes that leave ragged tiles, free space and above a wall; and a
+batched FP64 solve on the symmetric layout, whose systems stop at different
+iterations (stopped systems write zero partial sums), against the oracle's
+dense solves at 1e-10."""
+import numpy as np
+import pytest
+
+from paper_2107_10800_gb300 import build, binding, workloads as W
+from oracle import mobility as om
+from oracle.system import System
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    binding.lib()
+
+
+def rel(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def loose(r, a, wall):
+    n = len(r)
+    s = binding.Solver(eta=1.0, a=a, wall=wall, precision="fp64")
+    s.set_bodies(r, np.tile([1.0, 0, 0, 0], (n, 1)), np.arange(n + 1), np.zeros((n, 3)), np.zeros((n, 6)),
+                 np.arange(n))
+    return s
+
+
+@pytest.mark.parametrize("tile", [32, 64, 128])
+@pytest.mark.parametrize("n", [1, 2, 33, 65, 129, 300, 1000])
+@pytest.mark.parametrize("wall", [0, 1])
+def test_symmetric_product_matches_oracle(tile, n, wall):
+    r, lam = W.random_blobs(300 + n, n, a=0.1, wall=wall)
+    if n >= 4:  # an overlapping pair and a pair at contact
+        r[1] = r[0] + [0.05, 0.1, 0.0]
+        r[3] = r[2] + [0.2, 0.0, 0.0]
+    s = loose(r, 0.1, wall)
+    s.set_mobility_layout(3, tile)
+    assert s.mobility_layout()[3] == tile
+    u = s.apply_mobility(lam)
+    ref = om.mobility_matvec(r, lam, 0.1, 1.0, wall)
+    assert rel(u, ref) <= 1e-12
+    s.set_mobility_layout(1, 0)
+    assert s.mobility_layout()[3] == 0
+    assert rel(s.apply_mobility(lam), u) <= 1e-13
+
+
+def test_symmetric_layout_rejected_where_it_does_not_apply():
+    s = binding.Solver(a=0.1, precision="mixed")
+    r, _ = W.random_blobs(1, 10, a=0.1)
+    s.set_bodies(r, np.tile([1.0, 0, 0, 0], (10, 1)), np.arange(11), np.zeros((10, 3)), np.zeros((10, 6)),
+                 np.arange(10))
+    with pytest.raises(binding.AmError):
+        s.set_mobility_layout(3, 64)
+    s64 = loose(r, 0.1, 0)
+    with pytest.raises(binding.AmError):
+        s64.set_mobility_layout(3, 48)
+
+
+def test_batched_solve_on_symmetric_layout():
+    ws = [W.chains_free_space(400 + k, n_chains=1, bodies_per_chain=2 + k % 4) for k in range(40)]
+    s = binding.Solver.from_workloads(ws, tol=1e-13, precision="fp64", max_iter=2000)
+    s.set_mobility_layout(3, 32)
+    U, phi, lam, st = s.solve()
+    assert s.mobility_layout()[3] == 32
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-13
+    for k, (w, (Us, ps, ls)) in enumerate(zip(ws, s.split(U, phi, lam))):
+        if k % 5:
+            continue
+        S = System(w)
+        lo, uo, po = S.split(S.solve_dense())
+        assert rel(Us.ravel(), uo) <= 1e-10, k
+        assert rel(ls.ravel(), lo) <= 1e-10, k
