@@ -610,7 +610,8 @@ def periodic_form(torch, binding, W, stream, products=5):
     after the pose's pair blocks) and its parameters; then one solve at
     relative residual 1e-8 with the 1e-10 product (pose, pair blocks,
     preconditioner build, GMRES) and one Euler step after it, CUDA events on
-    the solver's stream."""
+    the solver's stream; then the mixed form (FP32 products inside, FP64
+    outer residuals): its FP32 product and one solve at 1e-8."""
     w = W.bacteria_periodic(5)
     lam = np.random.default_rng(6).standard_normal((int(w["blob_offset"][-1]), 3))
     out = {"workload": "1,000 bacteria (360 blobs each, a=0.05) on a jittered 10 x 10 x 10 lattice in a "
@@ -645,6 +646,22 @@ def periodic_form(torch, binding, W, stream, products=5):
     out.update({"solve_ms": solve_ms, "gmres_iterations": st["iterations"], "rel_residual": st["rel_residual"],
                 "ms_precond": st["ms_precond"], "ms_gmres": st["ms_gmres"], "step_ms": step_ms,
                 "step_gmres_iterations": st2["iterations"], "step_rel_residual": st2["rel_residual"]})
+    # mixed: FP32 wave part and blocks inside, FP64 product for the outer residuals
+    s = binding.Solver.from_workload(w, tol=1e-8, ewald_tol=1e-10, precision="mixed", stream=stream.cuda_stream)
+    s.apply_mobility(lam)
+    s.mobility_timing(True)
+    for _ in range(products):
+        s.apply_mobility_ex(lam, "mixed")
+    ms32, k32 = s.mobility_timing(False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, _, _, st3 = s.solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s.close()
+    out["mixed"] = {"product_ms": ms32 / max(k32, 1), "solve_ms": e0.elapsed_time(e1),
+                    "gmres_iterations": st3["iterations"], "rel_residual": st3["rel_residual"],
+                    "ms_precond": st3["ms_precond"], "ms_gmres": st3["ms_gmres"]}
     return out
 
 

@@ -96,9 +96,12 @@ typedef struct {
                             suspensions of Sec. 5.3; here without the
                             wall): the blob mobility is the RPY tensor
                             periodised by spectral Ewald summation
-                            (O(N log N)); needs wall = 0, AM_FP64, one
-                            system, multi-blob bodies and every side
-                            longer than 6 a.  Bodies are not wrapped: q
+                            (O(N log N)); needs wall = 0, one system,
+                            multi-blob bodies and every side longer than
+                            6 a.  AM_MIXED: FP32 wave part and blocks for
+                            the inner products (tolerance max(ewald_tol,
+                            1e-6)), the FP64 product for the outer
+                            residuals.  Bodies are not wrapped: q
                             stays continuous, the product wraps blob
                             centres into the box                         */
     double ewald_tol;    /* relative accuracy of the periodic product

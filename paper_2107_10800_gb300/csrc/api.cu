@@ -512,11 +512,11 @@ extern "C" AM_API int am_create(const am_config* cfg, am_handle** out) {
         (c.single_blob && (c.wall || c.precision != AM_FP64)))
         return AM_ERR_ARG;
     if (box_set(c)) {
-        // periodic box: every side positive and finite; free space, FP64,
-        // one system of multi-blob bodies
+        // periodic box: every side positive and finite; free space, one
+        // system of multi-blob bodies
         for (int d = 0; d < 3; ++d)
             if (!(c.box[d] > 0.0) || !std::isfinite(c.box[d])) return AM_ERR_ARG;
-        if (c.wall || c.single_blob || c.precision != AM_FP64 || c.n_systems != 1) return AM_ERR_ARG;
+        if (c.wall || c.single_blob || c.n_systems != 1) return AM_ERR_ARG;
         if (c.ewald_tol == 0.0) c.ewald_tol = 1e-10;
         if (!(c.ewald_tol >= 1e-14 && c.ewald_tol <= 1e-3) || !(c.ewald_xi >= 0.0) || !std::isfinite(c.ewald_xi))
             return AM_ERR_ARG;
@@ -1297,8 +1297,11 @@ extern "C" AM_API int am_apply_mobility_ex(am_handle* h, const double* lam, doub
         case AM_DF64: mode = am::kOpDF; break;
         default: return set_err(h, AM_ERR_ARG, "am_apply_mobility_ex: unknown arithmetic");
     }
-    if (box_set(h->cfg) && arithmetic != AM_FP64)
-        return set_err(h, AM_ERR_ARG, "am_apply_mobility_ex: a periodic box has the FP64 product only");
+    if (box_set(h->cfg)) {  // periodic: FP64 (also for double-float requests) or, on mixed handles, FP32
+        if (arithmetic == AM_MIXED && h->cfg.precision != AM_MIXED)
+            return set_err(h, AM_ERR_ARG, "am_apply_mobility_ex: the FP32 periodic product needs a mixed handle");
+        if (arithmetic == AM_DF64) mode = am::kOpFP64;
+    }
     cudaStream_t s = h->stream;
     am::launch_geometry(h);
     rc = device_flags_to_status(h, "am_apply_mobility_ex");

@@ -57,7 +57,7 @@ int mobility_autotune(am_handle* h);
 int periodic_setup(am_handle* h);
 void periodic_free(am_handle* h);
 int periodic_bin(am_handle* h);
-void launch_periodic(am_handle* h, const double* lam);
+void launch_periodic(am_handle* h, const double* lam, bool fp32);
 void periodic_info(const am_handle* h, double* d6, long long* i6);
 // Per system, x <- xp + beta_s (x - xp) with beta_s minimising the
 // residual |b - A x| on that line (operator in the handle's precision);

@@ -50,15 +50,29 @@
 
 namespace am {
 
+// The wave-space part at one precision (T = double for the FP64 product,
+// float for the mixed one): window, grid, its half spectra, the multiplier
+// and the cuFFT plans.
+struct Wave {
+    int P = 0, M[3] = {0, 0, 0};            // window width w, grid points per side
+    double beta = 0, kcut = 0, h[3] = {0, 0, 0};
+    long long ngrid = 0, nhat = 0;          // real points, half-spectrum points
+    void* grid = nullptr;                   // 3 x ngrid T
+    void* hat = nullptr;                    // 3 x nhat complex T
+    void* kfac = nullptr;                   // (fac, fac / k^2) per half-spectrum point, T
+    cufftHandle fwd = 0, inv = 0;
+    bool planned = false;
+};
+
 struct PeriodicPlan {
-    double L[3] = {0, 0, 0}, hgrid[3] = {0, 0, 0};
-    double xi = 0, rc = 0, beta = 0, kcut = 0, tol = 0;
-    int Mg[3] = {0, 0, 0}, P = 0;          // grid, window width w
+    double L[3] = {0, 0, 0};
+    double xi = 0, rc = 0, tol = 0;
     int nc[3] = {0, 0, 0}, ncell = 0;      // cells per side (side >= r_c)
     int ntab = 0;
     double ds = 0;                          // table step in s = r^2
-    long long ngrid = 0, nhat = 0;          // real points, half-spectrum points
     int Nb = 0;
+    Wave w64, w32;                          // FP64 wave part; FP32 one for mixed handles
+    bool has32 = false;
     // device
     double2* d_tab = nullptr;               // (A(s), B(s)/s)
     int* d_cell_start = nullptr;            // ncell + 1
@@ -70,20 +84,23 @@ struct PeriodicPlan {
     long long* d_row = nullptr;             // Nb + 1 CSR offsets
     int* d_nbr = nullptr;                   // neighbour blob indices
     double* d_blk = nullptr;                // 6 x cap pair blocks (SoA)
+    float* d_blk32 = nullptr;               // the same in FP32 (mixed handles)
     long long cap = 0, nnz = 0;
     long long* d_scan = nullptr;            // scan scratch
     int* d_code = nullptr;                  // per pair: neighbour cell << 26 | source sorted index
     double4_32a* d_rprev = nullptr;         // positions of the last binning
     int* d_moved = nullptr;                 // set when a blob moved since d_rprev
-    double* d_grid = nullptr;               // 3 x ngrid
-    cufftDoubleComplex* d_hat = nullptr;    // 3 x nhat
-    double2* d_kfac = nullptr;              // (fac, fac / k^2) per half-spectrum point
-    cufftHandle fwd = 0, inv = 0;
-    bool planned = false;
     bool valid = false;  // pair blocks of the current pose are in place
 };
 
 namespace {
+
+template <class T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+template <class T> using vec2_t = typename Vec2<T>::type;
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
 
 constexpr int kTab = 16384;  // table nodes over [0, r_c^2]
 constexpr int kScanBlock = 1024;
@@ -155,9 +172,10 @@ __device__ __forceinline__ double2 tab_at(const double2* __restrict__ tab, int n
 // divided by the window's transform squared (phx[|mx|] phy[|my|] phz[|mz|]
 // per axis), and zero at k = 0, beyond |k| = kcut and on the Nyquist planes
 // of even sizes.
+template <class T>
 __global__ void k_per_kfac(int Mx, int My, int Mz, double Lx, double Ly, double Lz, double a, double eta,
                            double xi, double kcut, const double* __restrict__ phx, const double* __restrict__ phy,
-                           const double* __restrict__ phz, double2* __restrict__ kfac) {
+                           const double* __restrict__ phz, vec2_t<T>* __restrict__ kfac) {
     const long long Mxh = Mx / 2 + 1;
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= Mxh * My * Mz) return;
@@ -167,7 +185,7 @@ __global__ void k_per_kfac(int Mx, int My, int Mz, double Lx, double Ly, double 
     const double kx = 2.0 * kPi * mx / Lx, ky = 2.0 * kPi * my / Ly, kz = 2.0 * kPi * mz / Lz;
     const double k2 = kx * kx + ky * ky + kz * kz;
     if (k2 == 0.0 || nyq || k2 > kcut * kcut) {
-        kfac[q] = make_double2(0.0, 0.0);
+        kfac[q] = mk2((T)0, (T)0);
         return;
     }
     const double k = sqrt(k2), ka = k * a;
@@ -176,7 +194,7 @@ __global__ void k_per_kfac(int Mx, int My, int Mz, double Lx, double Ly, double 
     const double norm = (Lx / Mx) * (Ly / My) * (Lz / Mz) / ((double)Mx * (double)My * (double)Mz);
     const double ph = phx[ix] * phy[iy <= My / 2 ? iy : My - iy] * phz[iz <= Mz / 2 ? iz : Mz - iz];
     const double fac = norm / eta * sinc * sinc * (1.0 + x) * exp(-x) / (k2 * ph * ph);
-    kfac[q] = make_double2(fac, fac / k2);
+    kfac[q] = mk2((T)fac, (T)(fac / k2));
 }
 
 // ---- cell list ------------------------------------------------------------
@@ -435,10 +453,11 @@ __global__ void k_per_moved(int Nb, const double4_32a* __restrict__ r4, const do
     if (a.x != b.x || a.y != b.y || a.z != b.z) *moved = 1;
 }
 
-__global__ void k_per_zero(double* __restrict__ g, long long n) {
+template <class T>
+__global__ void k_per_zero(T* __restrict__ g, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        g[i] = 0.0;
+        g[i] = (T)0;
 }
 
 // Window weight of lane l (< w = P) along one axis: grid index i0 + l (the
@@ -449,11 +468,17 @@ struct SpreadGeom {
     double h[3], inv_half[3], beta;
 };
 
-__device__ __forceinline__ void axis_weight(double x, int d, const SpreadGeom& g, int lane, int& idx, double& w) {
+template <class T>
+__device__ __forceinline__ void axis_weight(double x, int d, const SpreadGeom& g, int lane, int& idx, T& w) {
     const int i0 = (int)ceil(x / g.h[d] - 0.5 * g.P);
     int i = i0 + lane;
-    const double z = ((double)i * g.h[d] - x) * g.inv_half[d];
-    w = exp(g.beta * (sqrt(fmax(0.0, 1.0 - z * z)) - 1.0));
+    const double z = ((double)i * g.h[d] - x) * g.inv_half[d];  // in FP64: positions far from the origin
+    if constexpr (sizeof(T) == 8) {
+        w = exp(g.beta * (sqrt(fmax(0.0, 1.0 - z * z)) - 1.0));
+    } else {
+        const float zf = (float)z;
+        w = expf((float)g.beta * (sqrtf(fmaxf(0.f, 1.f - zf * zf)) - 1.f));
+    }
     if (i < 0) i += g.M[d]; else if (i >= g.M[d]) i -= g.M[d];
     idx = i;
 }
@@ -488,13 +513,13 @@ __device__ __forceinline__ LaneMap lane_map(int Nb, int P) {
 // grid column, row and layer); before the loops every lane collects the w
 // weights and indices of the y and z axes into registers (4 w shuffles per
 // blob instead of two per inner iteration).
-template <int P>
+template <class T, int P>
 __device__ __forceinline__ void window_axes(const SpreadGeom& g, const LaneMap& m, const double4_32a& x, int& ix,
-                                            double& wx, int* iy, double* wy, int* iz, double* wz) {
+                                            T& wx, int* iy, T* wy, int* iz, T* wz) {
     int jy = 0, jz = 0;
-    double vy = 0.0, vz = 0.0;
+    T vy = (T)0, vz = (T)0;
     ix = 0;
-    wx = 0.0;
+    wx = (T)0;
     if (m.lp < P) {
         axis_weight(x.x, 0, g, m.lp, ix, wx);
         axis_weight(x.y, 1, g, m.lp, jy, vy);
@@ -509,25 +534,25 @@ __device__ __forceinline__ void window_axes(const SpreadGeom& g, const LaneMap& 
     }
 }
 
-template <int P>
+template <class T, int P>
 __global__ void __launch_bounds__(256)
 k_per_spread(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const int* __restrict__ order,
-             const double* __restrict__ lam, double* __restrict__ grid, long long ngrid) {
+             const double* __restrict__ lam, T* __restrict__ grid, long long ngrid) {
     const LaneMap m = lane_map(Nb, P);
     const double4_32a x = spos[m.p];
     const int i = order[m.p];
-    const double lx = lam[3 * (size_t)i], ly = lam[3 * (size_t)i + 1], lz = lam[3 * (size_t)i + 2];
+    const T lx = (T)lam[3 * (size_t)i], ly = (T)lam[3 * (size_t)i + 1], lz = (T)lam[3 * (size_t)i + 2];
     int ix, iy[P], iz[P];
-    double wx, wy[P], wz[P];
-    window_axes<P>(g, m, x, ix, wx, iy, wy, iz, wz);
+    T wx, wy[P], wz[P];
+    window_axes<T, P>(g, m, x, ix, wx, iy, wy, iz, wz);
     if (!m.live) return;
-    const double ax = wx * lx, ay = wx * ly, az = wx * lz;
+    const T ax = wx * lx, ay = wx * ly, az = wx * lz;
 #pragma unroll 1
     for (int pz = 0; pz < P; ++pz) {
         const long long zrow = (long long)iz[pz] * g.M[1];
 #pragma unroll
         for (int py = 0; py < P; ++py) {
-            const double w = wy[py] * wz[pz];
+            const T w = wy[py] * wz[pz];
             const long long idx = (zrow + iy[py]) * g.M[0] + ix;
             atomicAdd(grid + idx, w * ax);
             atomicAdd(grid + ngrid + idx, w * ay);
@@ -537,48 +562,50 @@ k_per_spread(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const i
 }
 
 // f_hat <- fac (f_hat - k (k . f_hat) / k^2) on the half spectrum
+template <class T>
 __global__ void k_per_kmul(int Mx, int My, int Mz, double Lx, double Ly, double Lz,
-                           const double2* __restrict__ kfac, cufftDoubleComplex* __restrict__ hat, long long nhat) {
+                           const vec2_t<T>* __restrict__ kfac, vec2_t<T>* __restrict__ hat, long long nhat) {
+    using C = vec2_t<T>;
     const long long Mxh = Mx / 2 + 1;
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= nhat) return;
-    const double2 f = kfac[q];
-    cufftDoubleComplex* h0 = hat + q;
-    cufftDoubleComplex* h1 = hat + nhat + q;
-    cufftDoubleComplex* h2 = hat + 2 * nhat + q;
-    if (f.x == 0.0) {
-        *h0 = make_double2(0.0, 0.0); *h1 = make_double2(0.0, 0.0); *h2 = make_double2(0.0, 0.0);
+    const C f = kfac[q];
+    C* h0 = hat + q;
+    C* h1 = hat + nhat + q;
+    C* h2 = hat + 2 * nhat + q;
+    if (f.x == (T)0) {
+        *h0 = mk2((T)0, (T)0); *h1 = mk2((T)0, (T)0); *h2 = mk2((T)0, (T)0);
         return;
     }
     const int ix = (int)(q % Mxh), iy = (int)((q / Mxh) % My), iz = (int)(q / (Mxh * My));
     const int mx = ix, my = iy <= My / 2 ? iy : iy - My, mz = iz <= Mz / 2 ? iz : iz - Mz;
-    const double kx = 2.0 * kPi * mx / Lx, ky = 2.0 * kPi * my / Ly, kz = 2.0 * kPi * mz / Lz;
-    const cufftDoubleComplex a = *h0, b = *h1, c = *h2;
-    const double dr = kx * a.x + ky * b.x + kz * c.x, di = kx * a.y + ky * b.y + kz * c.y;
-    *h0 = make_double2(f.x * a.x - f.y * kx * dr, f.x * a.y - f.y * kx * di);
-    *h1 = make_double2(f.x * b.x - f.y * ky * dr, f.x * b.y - f.y * ky * di);
-    *h2 = make_double2(f.x * c.x - f.y * kz * dr, f.x * c.y - f.y * kz * di);
+    const T kx = (T)(2.0 * kPi * mx / Lx), ky = (T)(2.0 * kPi * my / Ly), kz = (T)(2.0 * kPi * mz / Lz);
+    const C a = *h0, b = *h1, c = *h2;
+    const T dr = kx * a.x + ky * b.x + kz * c.x, di = kx * a.y + ky * b.y + kz * c.y;
+    *h0 = mk2(f.x * a.x - f.y * kx * dr, f.x * a.y - f.y * kx * di);
+    *h1 = mk2(f.x * b.x - f.y * ky * dr, f.x * b.y - f.y * ky * di);
+    *h2 = mk2(f.x * c.x - f.y * kz * dr, f.x * c.y - f.y * kz * di);
 }
 
 // u_i = sum over its CSR row of the pair blocks times lambda_j (real space)
 // + the interpolation of the wave-space field at r_i with the window; the
 // lanes of lane_map, sums in a fixed order (lane-strided rows, the lanes of
 // a blob added in lane order through shared memory).
-template <int P>
+template <class T, int P>
 __global__ void __launch_bounds__(256)
 k_per_gather(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const int* __restrict__ order,
-             const long long* __restrict__ row, const int* __restrict__ nbr, const double* __restrict__ blk,
-             long long cap, const double* __restrict__ lam, const double* __restrict__ grid, long long ngrid,
+             const long long* __restrict__ row, const int* __restrict__ nbr, const T* __restrict__ blk,
+             long long cap, const double* __restrict__ lam, const T* __restrict__ grid, long long ngrid,
              double* __restrict__ out) {
     __shared__ double part[256][3];
     const LaneMap m = lane_map(Nb, P);
-    double ux = 0.0, uy = 0.0, uz = 0.0;
+    T ux = (T)0, uy = (T)0, uz = (T)0;
     if (m.live) {
         for (long long e = row[m.p] + m.lp; e < row[m.p + 1]; e += P) {
             const int j = nbr[e];
-            const double lx = lam[3 * (size_t)j], ly = lam[3 * (size_t)j + 1], lz = lam[3 * (size_t)j + 2];
-            const double m00 = blk[e], m01 = blk[cap + e], m02 = blk[2 * cap + e];
-            const double m11 = blk[3 * cap + e], m12 = blk[4 * cap + e], m22 = blk[5 * cap + e];
+            const T lx = (T)lam[3 * (size_t)j], ly = (T)lam[3 * (size_t)j + 1], lz = (T)lam[3 * (size_t)j + 2];
+            const T m00 = blk[e], m01 = blk[cap + e], m02 = blk[2 * cap + e];
+            const T m11 = blk[3 * cap + e], m12 = blk[4 * cap + e], m22 = blk[5 * cap + e];
             ux = fma(m00, lx, fma(m01, ly, fma(m02, lz, ux)));
             uy = fma(m01, lx, fma(m11, ly, fma(m12, lz, uy)));
             uz = fma(m02, lx, fma(m12, ly, fma(m22, lz, uz)));
@@ -586,9 +613,9 @@ k_per_gather(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const i
     }
     const double4_32a x = spos[m.p];
     int ix, iy[P], iz[P];
-    double wx, wy[P], wz[P];
-    window_axes<P>(g, m, x, ix, wx, iy, wy, iz, wz);
-    double vx = 0.0, vy = 0.0, vz = 0.0;
+    T wx, wy[P], wz[P];
+    window_axes<T, P>(g, m, x, ix, wx, iy, wy, iz, wz);
+    T vx = (T)0, vy = (T)0, vz = (T)0;
     if (m.live) {
 #pragma unroll 1
         for (int pz = 0; pz < P; ++pz) {
@@ -596,16 +623,16 @@ k_per_gather(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const i
 #pragma unroll
             for (int py = 0; py < P; ++py) {
                 const long long idx = (zrow + iy[py]) * g.M[0] + ix;
-                const double w = wy[py] * wz[pz];
+                const T w = wy[py] * wz[pz];
                 vx = fma(w, __ldg(grid + idx), vx);
                 vy = fma(w, __ldg(grid + ngrid + idx), vy);
                 vz = fma(w, __ldg(grid + 2 * ngrid + idx), vz);
             }
         }
     }
-    part[threadIdx.x][0] = fma(wx, vx, ux);
-    part[threadIdx.x][1] = fma(wx, vy, uy);
-    part[threadIdx.x][2] = fma(wx, vz, uz);
+    part[threadIdx.x][0] = (double)fma(wx, vx, ux);
+    part[threadIdx.x][1] = (double)fma(wx, vy, uy);
+    part[threadIdx.x][2] = (double)fma(wx, vz, uz);
     __syncwarp();
     if (m.live && m.lp == 0) {
         const int t0 = threadIdx.x;  // the blob's first lane
@@ -622,36 +649,45 @@ k_per_gather(int Nb, SpreadGeom g, const double4_32a* __restrict__ spos, const i
     }
 }
 
-template <int P>
-void launch_window(int Nb, const SpreadGeom& g, const PeriodicPlan* p, const double* lam, double* out,
-                   bool spread, cudaStream_t s) {
+template <class T, int P>
+void launch_window(int Nb, const SpreadGeom& g, const PeriodicPlan* p, const Wave& w, const T* blk,
+                   const double* lam, double* out, bool spread, cudaStream_t s) {
     const int per_block = 8 * (32 / P);  // blobs per 256-thread block (lane_map)
     const int nb = (Nb + per_block - 1) / per_block;
+    T* grid = static_cast<T*>(w.grid);
     if (spread)
-        k_per_spread<P><<<nb, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, lam, p->d_grid, p->ngrid);
+        k_per_spread<T, P><<<nb, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, lam, grid, w.ngrid);
     else
-        k_per_gather<P><<<nb, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, p->d_row, p->d_nbr, p->d_blk, p->cap, lam,
-                                           p->d_grid, p->ngrid, out);
+        k_per_gather<T, P><<<nb, 256, 0, s>>>(Nb, g, p->d_spos, p->d_order, p->d_row, p->d_nbr, blk, p->cap, lam,
+                                              grid, w.ngrid, out);
 }
 
 // window widths 4 .. 16 (tolerances 1e-3 .. 1e-15)
-void launch_window_any(int Nb, const SpreadGeom& g, const PeriodicPlan* p, const double* lam, double* out,
-                       bool spread, cudaStream_t s) {
-    switch (p->P) {
-        case 4: launch_window<4>(Nb, g, p, lam, out, spread, s); break;
-        case 5: launch_window<5>(Nb, g, p, lam, out, spread, s); break;
-        case 6: launch_window<6>(Nb, g, p, lam, out, spread, s); break;
-        case 7: launch_window<7>(Nb, g, p, lam, out, spread, s); break;
-        case 8: launch_window<8>(Nb, g, p, lam, out, spread, s); break;
-        case 9: launch_window<9>(Nb, g, p, lam, out, spread, s); break;
-        case 10: launch_window<10>(Nb, g, p, lam, out, spread, s); break;
-        case 11: launch_window<11>(Nb, g, p, lam, out, spread, s); break;
-        case 12: launch_window<12>(Nb, g, p, lam, out, spread, s); break;
-        case 13: launch_window<13>(Nb, g, p, lam, out, spread, s); break;
-        case 14: launch_window<14>(Nb, g, p, lam, out, spread, s); break;
-        case 15: launch_window<15>(Nb, g, p, lam, out, spread, s); break;
-        default: launch_window<16>(Nb, g, p, lam, out, spread, s); break;
+template <class T>
+void launch_window_any(int Nb, const SpreadGeom& g, const PeriodicPlan* p, const Wave& w, const T* blk,
+                       const double* lam, double* out, bool spread, cudaStream_t s) {
+    switch (w.P) {
+        case 4: launch_window<T, 4>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 5: launch_window<T, 5>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 6: launch_window<T, 6>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 7: launch_window<T, 7>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 8: launch_window<T, 8>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 9: launch_window<T, 9>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 10: launch_window<T, 10>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 11: launch_window<T, 11>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 12: launch_window<T, 12>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 13: launch_window<T, 13>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 14: launch_window<T, 14>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        case 15: launch_window<T, 15>(Nb, g, p, w, blk, lam, out, spread, s); break;
+        default: launch_window<T, 16>(Nb, g, p, w, blk, lam, out, spread, s); break;
     }
+}
+
+// FP32 copy of the pair blocks (6 x cap, SoA) for the mixed product
+__global__ void k_per_blk32(const double* __restrict__ blk, float* __restrict__ blk32, long long cap, long long nnz) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz;
+         e += (long long)gridDim.x * blockDim.x)
+        for (int j = 0; j < 6; ++j) blk32[j * cap + e] = (float)blk[j * cap + e];
 }
 
 // ---- host ------------------------------------------------------------------
@@ -686,15 +722,24 @@ void gauss_legendre20(double* x, double* w) {
     }
 }
 
+void free_wave(Wave& w) {
+    if (w.planned) {
+        cufftDestroy(w.fwd);
+        cufftDestroy(w.inv);
+    }
+    void* ptrs[] = {w.grid, w.hat, w.kfac};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    w = Wave();
+}
+
 void free_plan(PeriodicPlan* p) {
     if (!p) return;
-    if (p->planned) {
-        cufftDestroy(p->fwd);
-        cufftDestroy(p->inv);
-    }
+    free_wave(p->w64);
+    free_wave(p->w32);
     void* ptrs[] = {p->d_tab,  p->d_cell_start, p->d_cell_fill, p->d_cell_of, p->d_order, p->d_spos,
-                    p->d_sposf, p->d_row,     p->d_nbr,       p->d_blk,     p->d_scan,  p->d_grid,
-                    p->d_hat,  p->d_kfac,     p->d_code,      p->d_rprev,   p->d_moved};
+                    p->d_sposf, p->d_row,     p->d_nbr,       p->d_blk,     p->d_scan,  p->d_code,
+                    p->d_rprev, p->d_moved,   p->d_blk32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -705,16 +750,109 @@ bool dalloc(T** p, size_t count) {
     return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T)) == cudaSuccess;
 }
 
-SpreadGeom spread_geom(const PeriodicPlan* p) {
+SpreadGeom spread_geom(const Wave& w) {
     SpreadGeom g;
     for (int d = 0; d < 3; ++d) {
-        g.M[d] = p->Mg[d];
-        g.h[d] = p->hgrid[d];
+        g.M[d] = w.M[d];
+        g.h[d] = w.h[d];
+        g.inv_half[d] = 2.0 / (w.P * w.h[d]);
     }
-    g.P = p->P;
-    for (int d = 0; d < 3; ++d) g.inv_half[d] = 2.0 / (p->P * p->hgrid[d]);
-    g.beta = p->beta;
+    g.P = w.P;
+    g.beta = w.beta;
     return g;
+}
+
+// Grid of the wave part for tolerance tol at splitting xi: the Nyquist wave
+// number where the wave multiplier falls below tol, 2-3-5-smooth sizes.
+long long wave_grid(const PeriodicPlan* p, double xi, double tol, int P, int* M) {
+    const double lg = std::log(1.0 / tol), xN = lg + std::log1p(lg);
+    const double hmax = kPi / (2.0 * xi * std::sqrt(xN));
+    long long tot = 1;
+    for (int d = 0; d < 3; ++d) {
+        M[d] = fft_size(std::max(P + 1, (int)std::ceil(p->L[d] / hmax)));
+        tot *= M[d];
+    }
+    return tot;
+}
+
+int window_width(double tol) { return std::min(16, std::max(4, (int)std::ceil(std::log10(1.0 / tol)) + 1)); }
+
+// Buffers, cuFFT plans and multiplier of the wave part at precision T for
+// tolerance tol (gx, gw: 20-point Gauss-Legendre rule).
+template <class T>
+int wave_setup(PeriodicPlan* p, Wave& w, double tol, double a, double eta, cudaStream_t s, const double* gx,
+               const double* gw, std::string& err) {
+    const double lg = std::log(1.0 / tol), xN = lg + std::log1p(lg);
+    w.P = window_width(tol);
+    w.beta = 2.6 * w.P;
+    w.ngrid = wave_grid(p, p->xi, tol, w.P, w.M);
+    for (int d = 0; d < 3; ++d) w.h[d] = p->L[d] / w.M[d];
+    w.nhat = (long long)(w.M[0] / 2 + 1) * w.M[1] * w.M[2];
+    w.kcut = 2.0 * p->xi * std::sqrt(xN);
+    using C = vec2_t<T>;
+    if (cudaMalloc(&w.grid, 3 * (size_t)w.ngrid * sizeof(T)) != cudaSuccess ||
+        cudaMalloc(&w.hat, 3 * (size_t)w.nhat * sizeof(C)) != cudaSuccess ||
+        cudaMalloc(&w.kfac, (size_t)w.nhat * sizeof(C)) != cudaSuccess) {
+        cudaGetLastError();
+        err = "periodic mobility: device allocation failed";
+        return AM_ERR_CUDA;
+    }
+    int n3[3] = {w.M[2], w.M[1], w.M[0]};
+    const bool f64 = sizeof(T) == 8;
+    if (cufftPlanMany(&w.fwd, 3, n3, nullptr, 1, 0, nullptr, 1, 0, f64 ? CUFFT_D2Z : CUFFT_R2C, 3) !=
+        CUFFT_SUCCESS) {
+        err = "periodic mobility: cuFFT plan failed";
+        return AM_ERR_CUDA;
+    }
+    if (cufftPlanMany(&w.inv, 3, n3, nullptr, 1, 0, nullptr, 1, 0, f64 ? CUFFT_Z2D : CUFFT_C2R, 3) !=
+        CUFFT_SUCCESS) {
+        cufftDestroy(w.fwd);
+        err = "periodic mobility: cuFFT plan failed";
+        return AM_ERR_CUDA;
+    }
+    w.planned = true;
+    cufftSetStream(w.fwd, s);
+    cufftSetStream(w.inv, s);
+    // window transforms per axis at k = 2 pi m / L, m = 0 .. M/2:
+    // Phi(k) = (w h / 2) int_{-1}^{1} exp(beta (sqrt(1 - z^2) - 1)) cos(k w h z / 2) dz
+    // (composite 20-point Gauss-Legendre, 16 panels)
+    std::vector<double> ph;
+    int ph_off[4] = {0, 0, 0, 0};
+    for (int d = 0; d < 3; ++d) {
+        const double half = 0.5 * w.P * w.h[d];
+        for (int m = 0; m <= w.M[d] / 2; ++m) {
+            const double k = 2.0 * kPi * m / p->L[d];
+            double acc = 0.0;
+            for (int pn = 0; pn < 16; ++pn) {
+                const double z0 = -1.0 + 2.0 * pn / 16.0, zh = 1.0 / 16.0;
+                for (int i = 0; i < 20; ++i) {
+                    const double z = z0 + zh * (1.0 + gx[i]);
+                    acc += zh * gw[i] * std::exp(w.beta * (std::sqrt(std::max(0.0, 1.0 - z * z)) - 1.0)) *
+                           std::cos(k * half * z);
+                }
+            }
+            ph.push_back(half * acc);
+        }
+        ph_off[d + 1] = (int)ph.size();
+    }
+    double* d_ph = nullptr;
+    if (!dalloc(&d_ph, ph.size())) {
+        err = "periodic mobility: device allocation failed";
+        return AM_ERR_CUDA;
+    }
+    cudaMemcpyAsync(d_ph, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    k_per_kfac<T><<<(int)((w.nhat + 255) / 256), 256, 0, s>>>(w.M[0], w.M[1], w.M[2], p->L[0], p->L[1], p->L[2],
+                                                              a, eta, p->xi, w.kcut, d_ph + ph_off[0],
+                                                              d_ph + ph_off[1], d_ph + ph_off[2],
+                                                              static_cast<C*>(w.kfac));
+    count_launch();
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(d_ph);
+    if (e != cudaSuccess) {
+        err = "periodic mobility: setup kernels failed";
+        return AM_ERR_CUDA;
+    }
+    return AM_OK;
 }
 
 CellGeom cell_geom(const PeriodicPlan* p) {
@@ -734,7 +872,9 @@ void periodic_free(am_handle* h) {
     h->per_nnz = 0;
 }
 
-// Parameters and buffers for the handle's box, tolerance and blob count.
+// Parameters and buffers for the handle's box, tolerance and blob count
+// (the FP64 wave part, and the FP32 one at tolerance max(ewald_tol, 1e-6)
+// for mixed handles; both share xi and the real-space pairs).
 int periodic_setup(am_handle* h) {
     const double a = h->cfg.blob_radius, eta = h->cfg.eta;
     const double tol = h->cfg.ewald_tol > 0.0 ? h->cfg.ewald_tol : 1e-10;
@@ -753,10 +893,8 @@ int periodic_setup(am_handle* h) {
     p->Nb = Nb;
     p->tol = tol;
     for (int d = 0; d < 3; ++d) p->L[d] = h->cfg.box[d];
-    const double lg = std::log(1.0 / tol);
-    p->P = std::min(16, std::max(4, (int)std::ceil(std::log10(1.0 / tol)) + 1));
-    p->beta = 2.6 * p->P;
-    const double xN = lg + std::log1p(lg), crc = std::sqrt(0.8 * lg);
+    const double lg = std::log(1.0 / tol), crc = std::sqrt(0.8 * lg);
+    const int P = window_width(tol);
     const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
     if (!(Lmin / 3.0 > 2.0 * a * 1.01)) {
         h->err = "periodic box: every side must exceed 6 blob radii";
@@ -764,15 +902,6 @@ int periodic_setup(am_handle* h) {
     }
     const double xi_lo = crc / (Lmin / 3.0 - 2.0 * a);
     const double V = p->L[0] * p->L[1] * p->L[2], dens = Nb / V;
-    auto grid_for = [&](double xi, int* M) {
-        const double hmax = kPi / (2.0 * xi * std::sqrt(xN));
-        long long tot = 1;
-        for (int d = 0; d < 3; ++d) {
-            M[d] = fft_size(std::max(p->P + 1, (int)std::ceil(p->L[d] / hmax)));
-            tot *= M[d];
-        }
-        return tot;
-    };
     double xi = h->cfg.ewald_xi;
     if (xi > 0.0) {
         if (xi < xi_lo) {
@@ -795,7 +924,7 @@ int periodic_setup(am_handle* h) {
         for (int t = 0; t < 96; ++t) {
             const double x = xi_lo * std::pow(2.0, t / 8.0);
             int M[3];
-            const long long tot = grid_for(x, M);
+            const long long tot = wave_grid(p, x, tol, P, M);
             if (tot > (1LL << 31)) break;
             const double rc = 2.0 * a + crc / x;
             const double pairs = (double)Nb * (1.0 + dens * 4.0 / 3.0 * kPi * rc * rc * rc);
@@ -813,10 +942,6 @@ int periodic_setup(am_handle* h) {
     }
     p->xi = xi;
     p->rc = 2.0 * a + crc / xi;
-    p->ngrid = grid_for(xi, p->Mg);
-    for (int d = 0; d < 3; ++d) p->hgrid[d] = p->L[d] / p->Mg[d];
-    p->nhat = (long long)(p->Mg[0] / 2 + 1) * p->Mg[1] * p->Mg[2];
-    p->kcut = 2.0 * xi * std::sqrt(xN);
     for (int d = 0; d < 3; ++d) p->nc[d] = std::max(3, (int)std::floor(p->L[d] / p->rc));
     p->ncell = p->nc[0] * p->nc[1] * p->nc[2];
     p->ntab = kTab;
@@ -826,32 +951,25 @@ int periodic_setup(am_handle* h) {
     bool ok = dalloc(&p->d_tab, p->ntab) && dalloc(&p->d_cell_start, p->ncell + 1) &&
               dalloc(&p->d_cell_fill, p->ncell) && dalloc(&p->d_cell_of, Nb) && dalloc(&p->d_order, Nb) &&
               dalloc(&p->d_spos, Nb) && dalloc(&p->d_sposf, Nb) && dalloc(&p->d_row, Nb + 1) &&
-              dalloc(&p->d_scan, nscan) && dalloc(&p->d_grid, 3 * (size_t)p->ngrid) &&
-              dalloc(&p->d_hat, 3 * (size_t)p->nhat) && dalloc(&p->d_kfac, p->nhat) &&
-              dalloc(&p->d_rprev, Nb) && dalloc(&p->d_moved, 1);
+              dalloc(&p->d_scan, nscan) && dalloc(&p->d_rprev, Nb) && dalloc(&p->d_moved, 1);
     if (!ok) {
         cudaGetLastError();
         h->err = "periodic mobility: device allocation failed";
         return AM_ERR_CUDA;
     }
-    int n3[3] = {p->Mg[2], p->Mg[1], p->Mg[0]};
-    if (cufftPlanMany(&p->fwd, 3, n3, nullptr, 1, 0, nullptr, 1, 0, CUFFT_D2Z, 3) != CUFFT_SUCCESS) {
-        h->err = "periodic mobility: cuFFT plan failed";
-        return AM_ERR_CUDA;
+    cudaStream_t s = h->stream;
+    double gx[20], gw[20];
+    gauss_legendre20(gx, gw);
+    int rc = wave_setup<double>(p, p->w64, tol, a, eta, s, gx, gw, h->err);
+    if (rc) return rc;
+    if (h->cfg.precision == AM_MIXED) {
+        rc = wave_setup<float>(p, p->w32, std::max(tol, 1e-6), a, eta, s, gx, gw, h->err);
+        if (rc) return rc;
+        p->has32 = true;
     }
-    if (cufftPlanMany(&p->inv, 3, n3, nullptr, 1, 0, nullptr, 1, 0, CUFFT_Z2D, 3) != CUFFT_SUCCESS) {
-        cufftDestroy(p->fwd);
-        h->err = "periodic mobility: cuFFT plan failed";
-        return AM_ERR_CUDA;
-    }
-    p->planned = true;
-    cufftSetStream(p->fwd, h->stream);
-    cufftSetStream(p->inv, h->stream);
 
     // quadrature of the wave part's radial integrals: 20-point panels, four
     // per oscillation period of the integrand, up to k = 2 xi sqrt(50)
-    double gx[20], gw[20];
-    gauss_legendre20(gx, gw);
     const double kmax = 2.0 * xi * std::sqrt(50.0);
     const double span = std::max(p->rc * 1.001, 2.0 * a);
     const int panels = std::max(64, (int)std::ceil(4.0 * kmax * span / (2.0 * kPi)));
@@ -871,7 +989,6 @@ int periodic_setup(am_handle* h) {
         }
     }
     double *d_kq = nullptr, *d_wq = nullptr;
-    cudaStream_t s = h->stream;
     if (!dalloc(&d_kq, kq.size()) || !dalloc(&d_wq, wq.size())) {
         if (d_kq) cudaFree(d_kq);
         h->err = "periodic mobility: device allocation failed";
@@ -879,45 +996,11 @@ int periodic_setup(am_handle* h) {
     }
     cudaMemcpyAsync(d_kq, kq.data(), kq.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_wq, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice, s);
-    // window transforms per axis at k = 2 pi m / L, m = 0 .. M/2:
-    // Phi(k) = (w h / 2) int_{-1}^{1} exp(beta (sqrt(1 - z^2) - 1)) cos(k w h z / 2) dz
-    // (composite 20-point Gauss-Legendre, 16 panels)
-    std::vector<double> ph;
-    int ph_off[4] = {0, 0, 0, 0};
-    for (int d = 0; d < 3; ++d) {
-        const double half = 0.5 * p->P * p->hgrid[d];
-        for (int m = 0; m <= p->Mg[d] / 2; ++m) {
-            const double k = 2.0 * kPi * m / p->L[d];
-            double acc = 0.0;
-            for (int pn = 0; pn < 16; ++pn) {
-                const double z0 = -1.0 + 2.0 * pn / 16.0, zh = 1.0 / 16.0;
-                for (int i = 0; i < 20; ++i) {
-                    const double z = z0 + zh * (1.0 + gx[i]);
-                    acc += zh * gw[i] * std::exp(p->beta * (std::sqrt(std::max(0.0, 1.0 - z * z)) - 1.0)) *
-                           std::cos(k * half * z);
-                }
-            }
-            ph.push_back(half * acc);
-        }
-        ph_off[d + 1] = (int)ph.size();
-    }
-    double* d_ph = nullptr;
-    if (!dalloc(&d_ph, ph.size())) {
-        cudaFree(d_kq);
-        cudaFree(d_wq);
-        h->err = "periodic mobility: device allocation failed";
-        return AM_ERR_CUDA;
-    }
-    cudaMemcpyAsync(d_ph, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     k_per_table<<<(p->ntab * 32 + 255) / 256, 256, 0, s>>>(p->ntab, p->ds, d_kq, d_wq, (int)kq.size(), p->d_tab);
-    k_per_kfac<<<(int)((p->nhat + 255) / 256), 256, 0, s>>>(p->Mg[0], p->Mg[1], p->Mg[2], p->L[0], p->L[1],
-                                                            p->L[2], a, eta, xi, p->kcut, d_ph + ph_off[0],
-                                                            d_ph + ph_off[1], d_ph + ph_off[2], p->d_kfac);
-    count_launch(2);
+    count_launch();
     const cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(d_kq);
     cudaFree(d_wq);
-    cudaFree(d_ph);
     if (e != cudaSuccess) {
         h->err = "periodic mobility: setup kernels failed";
         return AM_ERR_CUDA;
@@ -975,11 +1058,14 @@ int periodic_bin(am_handle* h) {
         if (p->d_nbr) cudaFree(p->d_nbr);
         if (p->d_blk) cudaFree(p->d_blk);
         if (p->d_code) cudaFree(p->d_code);
+        if (p->d_blk32) cudaFree(p->d_blk32);
         p->d_nbr = nullptr;
         p->d_blk = nullptr;
         p->d_code = nullptr;
+        p->d_blk32 = nullptr;
         const long long cap = nnz + nnz / 4 + 1024;
-        if (!dalloc(&p->d_nbr, cap) || !dalloc(&p->d_blk, 6 * (size_t)cap) || !dalloc(&p->d_code, cap)) {
+        if (!dalloc(&p->d_nbr, cap) || !dalloc(&p->d_blk, 6 * (size_t)cap) || !dalloc(&p->d_code, cap) ||
+            (p->has32 && !dalloc(&p->d_blk32, 6 * (size_t)cap))) {
             cudaGetLastError();
             p->cap = 0;
             h->err = "periodic mobility: device allocation of the real-space pairs failed";
@@ -994,6 +1080,10 @@ int periodic_bin(am_handle* h) {
                                             p->cap, p->d_tab, p->ntab, 1.0 / p->ds, k, 1.0 / h->cfg.eta);
     k_per_blocks<true><<<nbw, 256, 0, s>>>(Nb, cg, p->d_spos, p->d_order, p->d_row, p->d_code, p->d_nbr, p->d_blk,
                                            p->cap, p->d_tab, p->ntab, 1.0 / p->ds, k, 1.0 / h->cfg.eta);
+    if (p->has32) {
+        k_per_blk32<<<8 * num_sms(), 256, 0, s>>>(p->d_blk, p->d_blk32, p->cap, nnz);
+        count_launch();
+    }
     cudaMemcpyAsync(p->d_rprev, h->d_r4, Nb * sizeof(double4_32a), cudaMemcpyDeviceToDevice, s);
     count_launch(3);
     p->nnz = nnz;
@@ -1006,37 +1096,54 @@ int periodic_bin(am_handle* h) {
     return AM_OK;
 }
 
-// u = M_per lam (3 Nb each, blob order) into h->d_mv.  Stream-ordered; no
-// host synchronisation, so it can be captured into a graph.
-void launch_periodic(am_handle* h, const double* lam) {
+// u = M_per lam (3 Nb each, blob order) into h->d_mv, with the FP64 wave
+// part and blocks, or (fp32, mixed handles) the FP32 ones.  Stream-ordered;
+// no host synchronisation, so it can be captured into a graph.
+template <class T>
+void launch_wave(am_handle* h, const Wave& w, const T* blk, const double* lam) {
     PeriodicPlan* p = h->per;
     cudaStream_t s = h->stream;
-    const int Nb = p->Nb;
+    const SpreadGeom g = spread_geom(w);
+    T* grid = static_cast<T*>(w.grid);
+    k_per_zero<T><<<8 * num_sms(), 256, 0, s>>>(grid, 3 * w.ngrid);
+    launch_window_any<T>(p->Nb, g, p, w, blk, lam, h->d_mv, true, s);
+    if constexpr (sizeof(T) == 8)
+        cufftExecD2Z(w.fwd, static_cast<double*>(w.grid), static_cast<cufftDoubleComplex*>(w.hat));
+    else
+        cufftExecR2C(w.fwd, static_cast<float*>(w.grid), static_cast<cufftComplex*>(w.hat));
+    k_per_kmul<T><<<(int)((w.nhat + 255) / 256), 256, 0, s>>>(w.M[0], w.M[1], w.M[2], p->L[0], p->L[1], p->L[2],
+                                                              static_cast<const vec2_t<T>*>(w.kfac),
+                                                              static_cast<vec2_t<T>*>(w.hat), w.nhat);
+    if constexpr (sizeof(T) == 8)
+        cufftExecZ2D(w.inv, static_cast<cufftDoubleComplex*>(w.hat), static_cast<double*>(w.grid));
+    else
+        cufftExecC2R(w.inv, static_cast<cufftComplex*>(w.hat), static_cast<float*>(w.grid));
+    launch_window_any<T>(p->Nb, g, p, w, blk, lam, h->d_mv, false, s);
+    count_launch(4);
+}
+
+void launch_periodic(am_handle* h, const double* lam, bool fp32) {
+    PeriodicPlan* p = h->per;
     if (!p->valid) {  // binning failed (reported by the caller): no launch on stale pairs
-        cudaMemsetAsync(h->d_mv, 0, 3 * (size_t)Nb * sizeof(double), s);
+        cudaMemsetAsync(h->d_mv, 0, 3 * (size_t)p->Nb * sizeof(double), h->stream);
         return;
     }
-    const SpreadGeom g = spread_geom(p);
-    k_per_zero<<<8 * num_sms(), 256, 0, s>>>(p->d_grid, 3 * p->ngrid);
-    launch_window_any(Nb, g, p, lam, h->d_mv, true, s);
-    cufftExecD2Z(p->fwd, p->d_grid, p->d_hat);
-    k_per_kmul<<<(int)((p->nhat + 255) / 256), 256, 0, s>>>(p->Mg[0], p->Mg[1], p->Mg[2], p->L[0], p->L[1],
-                                                            p->L[2], p->d_kfac, p->d_hat, p->nhat);
-    cufftExecZ2D(p->inv, p->d_hat, p->d_grid);
-    launch_window_any(Nb, g, p, lam, h->d_mv, false, s);
-    count_launch(4);
+    if (fp32 && p->has32)
+        launch_wave<float>(h, p->w32, p->d_blk32, lam);
+    else
+        launch_wave<double>(h, p->w64, p->d_blk, lam);
 }
 
 // xi, r_c, beta, hx, hy, hz; Mx, My, Mz, w, real-space pairs, cells
 void periodic_info(const am_handle* h, double* d6, long long* i6) {
     const PeriodicPlan* p = h->per;
     if (d6) {
-        d6[0] = p->xi; d6[1] = p->rc; d6[2] = p->beta;
-        d6[3] = p->hgrid[0]; d6[4] = p->hgrid[1]; d6[5] = p->hgrid[2];
+        d6[0] = p->xi; d6[1] = p->rc; d6[2] = p->w64.beta;
+        d6[3] = p->w64.h[0]; d6[4] = p->w64.h[1]; d6[5] = p->w64.h[2];
     }
     if (i6) {
-        i6[0] = p->Mg[0]; i6[1] = p->Mg[1]; i6[2] = p->Mg[2];
-        i6[3] = p->P; i6[4] = p->nnz; i6[5] = p->ncell;
+        i6[0] = p->w64.M[0]; i6[1] = p->w64.M[1]; i6[2] = p->w64.M[2];
+        i6[3] = p->w64.P; i6[4] = p->nnz; i6[5] = p->ncell;
     }
 }
 

@@ -1084,8 +1084,8 @@ int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup, int sym) {
 // The partial sums of u = M lambda for all systems (mode: the handle's
 // precision, FP64 or double-float).
 void launch_items(am_handle* h, const double* lam, int mode, const int* active) {
-    if (h->per) {  // FP64 only (checked by the callers)
-        launch_periodic(h, lam);
+    if (h->per) {  // FP32 wave part for the mixed operator; FP64 for FP64 and double-float requests
+        launch_periodic(h, lam, mode == kOpMixed || (mode == kOpHandle && h->cfg.precision == AM_MIXED));
         return;
     }
     if (mode == kOpDF) {
@@ -1142,8 +1142,8 @@ void launch_sum_items(am_handle* h, double* u) {
     count_launch();
 }
 
-// Autotuner: times the handle's product for candidate (targets per thread,
-// source chunk) pairs on the current positions and keeps the fastest.
+// Autotuner: times the handle's product and the sum of its partials for
+// candidate layouts on the current positions and keeps the fastest.
 int mobility_autotune(am_handle* h) {
     if (h->per) {  // the periodic product has no item layout to tune
         h->mv_tuned = true;
@@ -1189,8 +1189,9 @@ int mobility_autotune(am_handle* h) {
     }
     cudaStream_t st = h->stream;
     double* lam = nullptr;
-    if (cudaMalloc(&lam, 3 * (size_t)std::max(h->Nb, 1) * sizeof(double)) != cudaSuccess) return 1;
-    cudaMemsetAsync(lam, 0, 3 * (size_t)h->Nb * sizeof(double), st);
+    if (cudaMalloc(&lam, 6 * (size_t)std::max(h->Nb, 1) * sizeof(double)) != cudaSuccess) return 1;
+    cudaMemsetAsync(lam, 0, 6 * (size_t)h->Nb * sizeof(double), st);
+    double* usum = lam + 3 * (size_t)std::max(h->Nb, 1);  // the sum of the partials: its cost grows with them
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1202,8 +1203,10 @@ int mobility_autotune(am_handle* h) {
         if (mobility_layout(h, c.tpt, c.chunk, c.tgroup, c.sym)) continue;
         launch_items(h, lam, false);  // warm-up
         cudaEventRecord(e0, st);
-        launch_items(h, lam, false);
-        launch_items(h, lam, false);
+        for (int rep = 0; rep < 2; ++rep) {
+            launch_items(h, lam, false);
+            launch_sum_items(h, usum);
+        }
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) continue;
         float ms = 0.f;

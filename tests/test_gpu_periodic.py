@@ -11,7 +11,10 @@ oracle's dense solve with the periodic mobility, within 1e-8 at
 ewald_tol = 1e-12 (the dense solve amplifies the product error by the
 condition number of A).  At 360,000 blobs, where the oracle's Ewald sum is
 out of reach, properties that hold at any size: independence of the split
-parameter and of a translation of every body, within the same bar."""
+parameter and of a translation of every body, within the same bar.  Mixed
+handles: the FP32 product (FP32 window, grid, transforms and real-space
+blocks at tolerance max(ewald_tol, 1e-6)) within 1e-5 of the oracle, the
+mixed solve (FP64 outer residuals) against the dense solution as above."""
 import numpy as np
 import pytest
 
@@ -34,9 +37,9 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def loose(r, a, box, tol, eta=1.0, xi=0.0):
+def loose(r, a, box, tol, eta=1.0, xi=0.0, precision="fp64"):
     n = len(r)
-    s = binding.Solver(eta=eta, a=a, box=box, ewald_tol=tol, ewald_xi=xi)
+    s = binding.Solver(eta=eta, a=a, box=box, ewald_tol=tol, ewald_xi=xi, precision=precision)
     s.set_bodies(r, np.tile([1.0, 0, 0, 0], (n, 1)), np.arange(n + 1), np.zeros((n, 3)),
                  np.zeros((n, 6)), np.arange(n))
     return s
@@ -162,15 +165,45 @@ def test_periodic_rejects():
     with pytest.raises(binding.AmError):
         binding.Solver(a=0.1, wall=1, box=[2, 2, 2])
     with pytest.raises(binding.AmError):
-        binding.Solver(a=0.1, precision="mixed", box=[2, 2, 2])
-    with pytest.raises(binding.AmError):
         binding.Solver(a=0.1, n_systems=2, box=[2, 2, 2])
     with pytest.raises(binding.AmError):
         binding.Solver(a=0.1, box=[2, 0, 2])
     with pytest.raises(binding.AmError):  # a side below 6a
         loose(np.zeros((2, 3)) + 0.1, 0.1, [0.5, 2.0, 2.0], 1e-8)
     s = loose(np.random.default_rng(0).random((10, 3)), 0.1, [1.0, 1.0, 1.0], 1e-8)
-    with pytest.raises(binding.AmError):
+    with pytest.raises(binding.AmError):  # the FP32 product needs a mixed handle
         s.apply_mobility_ex(np.zeros((10, 3)), "mixed")
     with pytest.raises(binding.AmError):
         s.set_repulsion(1.0, 0.1, 0.3)
+
+
+@pytest.mark.parametrize("n", [2, 50, 257])
+def test_periodic_mixed_product(n):
+    box, a = np.array([1.0, 1.2, 0.9]), 0.1
+    r, lam = edge_blobs(n, n, box, a)
+    s = loose(r, a, box, 1e-10, eta=1.3, precision="mixed")
+    ref = op.periodic_mobility_matvec(r, lam, a, 1.3, box)
+    assert rel(s.apply_mobility_ex(lam, "mixed"), ref) <= 1e-5
+    assert rel(s.apply_mobility_ex(lam, "fp64"), ref) <= 1e-9
+    assert rel(s.apply_mobility_ex(lam, "df64"), ref) <= 1e-9
+
+
+def test_periodic_mixed_solve_matches_dense_solution():
+    box = np.array([4.0, 4.0, 4.0])
+    w = periodic_chains(3, box)
+    s = binding.Solver.from_workload(w, tol=1e-11, ewald_tol=1e-12, precision="mixed")
+    U, phi, lam, st = s.solve()
+    assert st["rel_residual"] <= 1e-11
+    S = System(w)
+    S._M = op.periodic_mobility_dense(S.r, S.a, S.eta, box)
+    lo, uo, po = S.split(S.solve_dense())
+    assert rel(U.ravel(), uo) <= 1e-8
+    assert rel(lam.ravel(), lo) <= 1e-8
+
+
+def test_periodic_mixed_full_size_product():
+    # FP32 wave part and blocks against the FP64 product on 360,000 blobs
+    w = W.bacteria_periodic(5)
+    lam = np.random.default_rng(7).standard_normal((360_000, 3))
+    s = binding.Solver.from_workload(w, ewald_tol=1e-10, precision="mixed")
+    assert rel(s.apply_mobility_ex(lam, "mixed"), s.apply_mobility_ex(lam, "fp64")) <= 1e-5
