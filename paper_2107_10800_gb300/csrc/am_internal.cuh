@@ -187,7 +187,7 @@ struct am_handle {
     bool mv_tuned = false;
     // tile-pair items of the symmetric FP64 product (tiles of 32 sym_nsub blobs)
     void* d_sym_items = nullptr;
-    int n_sym = 0, sym_nsub = 0, mv_gridsym = 0;
+    int n_sym = 0, sym_nsub = 0, mv_gridsym = 0, mv_gridsym32 = 0;
 
     // host structure
     std::vector<int> blob_off, asm_of_body, bp, bq;

@@ -827,6 +827,226 @@ __device__ __forceinline__ void pair2(float2 dx, float2 dy, float2 dz, float2 rx
     uz = fma2(cc, lz, fma2(sdl, dz, fma2(P, Rz, add2(uz, Q))));
 }
 
+// Both directions of a pair in paired FP32 lanes: u += M lambda_src for two
+// targets (the lanes), and v += M^T mu for the source from each target (v.x
+// from the first, v.y from the second; the caller adds them).  The
+// operations of pair_wall_sym (rpy_pair.cuh) on the lanes of pair2.
+template <bool WALL>
+__device__ __forceinline__ void pair2_sym(float2 dx, float2 dy, float2 dz, float2 rxy2, float2 r2, float2 Rz,
+                                          float2 h2, float2 nx3, float2 lx, float2 ly, float2 lz, float2 mx,
+                                          float2 my, float2 mz, const RpyK<float>& k, float2& ux, float2& uy,
+                                          float2& uz, float2& vx, float2& vy, float2& vz) {
+    const float2 one = bc2(1.f);
+    float2 c1f, c2f;
+    if (r2.x < k.four_a2 || r2.y < k.four_a2) {
+        free_coefs<float>(r2.x, k, c1f.x, c2f.x);
+        free_coefs<float>(r2.y, k, c1f.y, c2f.y);
+    } else {
+        const float2 ri = rsq2(r2);
+        const float2 ri2 = mul2(ri, ri);
+        c1f = mul2(ri, fma2(bc2(k.kf2), ri2, one));
+        c2f = mul2(mul2(ri, ri2), fma2(bc2(-k.kf3), ri2, one));
+    }
+    const float2 dlxy = fma2(dx, lx, mul2(dy, ly));
+    const float2 Df = fma2(dz, lz, dlxy);
+    const float2 dmxy = fma2(dx, mx, mul2(dy, my));
+    const float2 Dfm = fma2(dz, mz, dmxy);
+    if (!WALL) {
+        const float2 sl = mul2(c2f, Df), sm = mul2(c2f, Dfm);
+        ux = fma2(c1f, lx, fma2(sl, dx, ux));
+        uy = fma2(c1f, ly, fma2(sl, dy, uy));
+        uz = fma2(c1f, lz, fma2(sl, dz, uz));
+        vx = fma2(c1f, mx, fma2(sm, dx, vx));
+        vy = fma2(c1f, my, fma2(sm, dy, vy));
+        vz = fma2(c1f, mz, fma2(sm, dz, vz));
+        return;
+    }
+    const float2 Rz2 = mul2(Rz, Rz);
+    const float2 s = rsq2(add2(rxy2, Rz2));
+    const float2 w = mul2(s, s), s3 = mul2(s, w), w2 = mul2(w, w);
+    const float2 c1 = fma2(h2, nx3, bc2(k.wc1));
+    const float2 c2 = fma2(Rz2, bc2(k.w2a2), bc2(k.wc2));
+    const float2 c3 = mul2(Rz2, bc2(k.wc3));
+    const float2 x1 = fma2(w, c3, c2);
+    const float2 cI = fma2(w, fma2(w, x1, c1), bc2(-1.f));
+    const float2 y = fma2(w, c3, x1);
+    const float2 yz = fma2(w, c3, y);
+    const float2 cRR = fma2(mul2(w2, y), bc2(-2.f), fma2(cI, bc2(-3.f), bc2(-4.f)));
+    const float2 A4w2n = mul2(w2, bc2(-k.wa4));
+    const float2 cc = fma2(s, cI, c1f);
+    const float2 g = fma2(Rz, fma2(cRR, bc2(-2.f), fma2(A4w2n, bc2(-1.f), bc2(-2.f))), h2);
+    const float2 s3cRR = mul2(s3, cRR), s3g = mul2(s3, g), s3h2 = mul2(s3, h2);
+    const float2 s3A = mul2(s3, mul2(A4w2n, Rz)), s3phi = mul2(s3, mul2(w, fma2(yz, bc2(-2.f), bc2(k.wi2))));
+    {
+        const float2 Di = fma2(Rz, lz, dlxy);
+        const float2 sdl = mul2(c2f, Df);
+        const float2 P = fma2(s3cRR, Di, mul2(s3g, lz));
+        const float2 Q = fma2(s3h2, Df, fma2(s3A, Di, mul2(s3phi, lz)));
+        const float2 pp = add2(sdl, P);
+        ux = fma2(cc, lx, fma2(pp, dx, ux));
+        uy = fma2(cc, ly, fma2(pp, dy, uy));
+        uz = fma2(cc, lz, fma2(sdl, dz, fma2(P, Rz, add2(uz, Q))));
+    }
+    {
+        const float2 Di = fma2(Rz, mz, dmxy);
+        const float2 cd = fma2(c2f, Dfm, mul2(s3h2, mz));
+        const float2 P = fma2(s3cRR, Di, mul2(s3A, mz));
+        const float2 Q = fma2(s3g, Di, mul2(s3phi, mz));
+        const float2 pp = add2(cd, P);
+        vx = fma2(cc, mx, fma2(pp, dx, vx));
+        vy = fma2(cc, my, fma2(pp, dy, vy));
+        vz = fma2(cc, mz, fma2(cd, dz, fma2(P, Rz, add2(vz, Q))));
+    }
+}
+
+// Symmetric mixed product on tile pairs of 128 blobs (the SymItem list of
+// the handle, tiles of 128): warp w holds 64 targets of tile I, two per lane
+// in the lanes of float2 registers (targets 64 (w & 1) + l and + 32), and
+// takes source sub-tiles 2 (w >> 1) and 2 (w >> 1) + 1 of tile J (32
+// sources each).  At step t lane l meets source (l + t) mod 32 of the
+// sub-tile with both targets; the source's column sum (the two targets'
+// contributions added) moves one lane per step as in rpy_sym_f64.
+// Differences from the hi parts, with the lo parts added within a quarter
+// of the target's largest coordinate (as rpy_items_mixed_x2).  FP32 sums over
+// at most 64 terms (a warp's sources for u, its targets for v), added in
+// FP64 across warps in a fixed order.  Diagonal items (I = J) take every
+// ordered pair in one direction (the self term included), no column sums.
+template <bool WALL>
+__global__ void __launch_bounds__(kThreads, 4)
+rpy_sym_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo, const double* __restrict__ lam,
+                 double* __restrict__ part, const SymItem* __restrict__ items, int n_items, int* __restrict__ counter,
+                 RpyK<float> k, const int* __restrict__ active) {
+    constexpr int T = 128;
+    __shared__ float4 sq[3][T];   // sources: (-hx, -hx, -hy, -hy), (2hz, 2hz, lz, lz), (lx, lx, ly, ly)
+    __shared__ float4 so[T];      // (-ox, -ox, -oy, -oy)
+    __shared__ float2 soz[T];     // (-oz, -oz)
+    __shared__ double up[4][64][3];     // row sums of each warp's 64 targets
+    __shared__ double vp[4][2][32][3];  // column sums of each warp's two sub-tiles
+    __shared__ int s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int th = warp & 1;            // target half of tile I
+    const int sb0 = 2 * (warp >> 1);    // the warp's first source sub-tile
+    for (int round = 0;; ++round) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(counter, 1);
+        __syncthreads();
+        const int itn = s_item;
+        if (itn >= n_items) break;
+        const SymItem m = items[itn];
+        const bool diag = m.ti == m.tj;
+        double* rowo = part + m.poff + (long long)m.tj * m.n3 + 3 * (long long)(m.i0 - m.tbase);
+        double* colo = part + m.poff + (long long)m.ti * m.n3 + 3 * (long long)(m.j0 - m.tbase);
+        if (active && !active[m.sys]) {
+            for (int q = threadIdx.x; q < 3 * m.ni; q += blockDim.x) rowo[q] = 0.0;
+            if (!diag)
+                for (int q = threadIdx.x; q < 3 * m.nj; q += blockDim.x) colo[q] = 0.0;
+            continue;
+        }
+        {   // stage the sources of tile J (one per thread)
+            const int q = threadIdx.x;
+            const bool ok = q < m.nj;
+            const float4 h = ok ? hi[m.j0 + q] : make_float4(0.f, 0.f, 1.f, 0.f);
+            const float4 o = ok ? lo[m.j0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float lx = ok ? (float)lam[3 * (size_t)(m.j0 + q)] : 0.f;
+            const float ly = ok ? (float)lam[3 * (size_t)(m.j0 + q) + 1] : 0.f;
+            const float lz = ok ? (float)lam[3 * (size_t)(m.j0 + q) + 2] : 0.f;
+            sq[0][q] = make_float4(-h.x, -h.x, -h.y, -h.y);
+            sq[1][q] = make_float4(2.f * h.z, 2.f * h.z, lz, lz);
+            sq[2][q] = make_float4(lx, lx, ly, ly);
+            so[q] = make_float4(-o.x, -o.x, -o.y, -o.y);
+            soz[q] = make_float2(-o.z, -o.z);
+        }
+        __syncthreads();
+        const int t0 = 64 * th + lane, t1 = t0 + 32;
+        const bool ok0 = t0 < m.ni, ok1 = t1 < m.ni;
+        const float4 h0 = ok0 ? hi[m.i0 + t0] : make_float4(0.f, 0.f, 1.f, 0.f);
+        const float4 h1 = ok1 ? hi[m.i0 + t1] : make_float4(0.f, 0.f, 1.f, 0.f);
+        const float4 l0 = ok0 ? lo[m.i0 + t0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 l1 = ok1 ? lo[m.i0 + t1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 HX = make_float2(h0.x, h1.x), HY = make_float2(h0.y, h1.y), HZ = make_float2(h0.z, h1.z);
+        const float2 LX = make_float2(l0.x, l1.x), LY = make_float2(l0.y, l1.y), LZ = make_float2(l0.z, l1.z);
+        const float2 NX3 = make_float2(-h0.z, -h1.z);
+        const float n0 = 0.25f * fmaxf(fabsf(h0.x), fmaxf(fabsf(h0.y), fabsf(h0.z)));
+        const float n1 = 0.25f * fmaxf(fabsf(h1.x), fmaxf(fabsf(h1.y), fabsf(h1.z)));
+        const float near2x = n0 * n0, near2y = n1 * n1;
+        // the targets' forces for the column sums (zero for missing targets)
+        float2 MX = bc2(0.f), MY = bc2(0.f), MZ = bc2(0.f);
+        if (ok0) {
+            MX.x = (float)lam[3 * (size_t)(m.i0 + t0)];
+            MY.x = (float)lam[3 * (size_t)(m.i0 + t0) + 1];
+            MZ.x = (float)lam[3 * (size_t)(m.i0 + t0) + 2];
+        }
+        if (ok1) {
+            MX.y = (float)lam[3 * (size_t)(m.i0 + t1)];
+            MY.y = (float)lam[3 * (size_t)(m.i0 + t1) + 1];
+            MZ.y = (float)lam[3 * (size_t)(m.i0 + t1) + 2];
+        }
+        float2 ux = bc2(0.f), uy = bc2(0.f), uz = bc2(0.f);
+        for (int sbi = 0; sbi < 2; ++sbi) {
+            const int sb = sb0 + sbi;
+            float vx = 0.f, vy = 0.f, vz = 0.f;  // column sum of source 32 sb + ((lane + t) & 31)
+#pragma unroll 2
+            for (int t = 0; t < 32; ++t) {
+                const int q = 32 * sb + (diag ? t : ((lane + t) & 31));
+                const float4 v0 = sq[0][q], v1 = sq[1][q], v2 = sq[2][q];
+                const float2 h2 = make_float2(v1.x, v1.y);
+                float2 dx = add2(HX, make_float2(v0.x, v0.y));
+                float2 dy = add2(HY, make_float2(v0.z, v0.w));
+                float2 dz = fma2(h2, bc2(-0.5f), HZ);
+                const float2 Rz = fma2(h2, bc2(0.5f), HZ);
+                float2 rxy2 = fma2(dx, dx, mul2(dy, dy));
+                float2 r2 = fma2(dz, dz, rxy2);
+                if (r2.x < near2x || r2.y < near2y) {
+                    const float4 o = so[q];
+                    dx = add2(dx, add2(LX, make_float2(o.x, o.y)));
+                    dy = add2(dy, add2(LY, make_float2(o.z, o.w)));
+                    dz = add2(dz, add2(LZ, soz[q]));
+                    rxy2 = fma2(dx, dx, mul2(dy, dy));
+                    r2 = fma2(dz, dz, rxy2);
+                }
+                const float2 lxs = make_float2(v2.x, v2.y), lys = make_float2(v2.z, v2.w),
+                             lzs = make_float2(v1.z, v1.w);
+                if (diag) {
+                    pair2<WALL>(dx, dy, dz, rxy2, r2, Rz, h2, NX3, lxs, lys, lzs, k, ux, uy, uz);
+                } else {
+                    float2 cx = bc2(0.f), cy = bc2(0.f), cz = bc2(0.f);
+                    pair2_sym<WALL>(dx, dy, dz, rxy2, r2, Rz, h2, NX3, lxs, lys, lzs, MX, MY, MZ, k, ux, uy, uz,
+                                    cx, cy, cz);
+                    vx += cx.x + cx.y;
+                    vy += cy.x + cy.y;
+                    vz += cz.x + cz.y;
+                    const int src = (lane + 1) & 31;
+                    vx = __shfl_sync(0xffffffffu, vx, src);
+                    vy = __shfl_sync(0xffffffffu, vy, src);
+                    vz = __shfl_sync(0xffffffffu, vz, src);
+                }
+            }
+            vp[warp][sbi][lane][0] = vx;
+            vp[warp][sbi][lane][1] = vy;
+            vp[warp][sbi][lane][2] = vz;
+        }
+        up[warp][lane][0] = ux.x; up[warp][lane][1] = uy.x; up[warp][lane][2] = uz.x;
+        up[warp][32 + lane][0] = ux.y; up[warp][32 + lane][1] = uy.y; up[warp][32 + lane][2] = uz.y;
+        __syncthreads();
+        {
+            const int t = threadIdx.x;
+            if (t < m.ni) {  // target t: half t >> 6, row t & 63 of warps th and th + 2
+                const int hh = t >> 6, j = t & 63;
+                rowo[3 * t] = k.A1 * (up[hh][j][0] + up[hh + 2][j][0]);
+                rowo[3 * t + 1] = k.A1 * (up[hh][j][1] + up[hh + 2][j][1]);
+                rowo[3 * t + 2] = k.A1 * (up[hh][j][2] + up[hh + 2][j][2]);
+            }
+            if (!diag && t < m.nj) {  // source t: sub-tile sb = t >> 5 of warps 2 (sb >> 1) and + 1
+                const int sb = t >> 5, l = t & 31, wa = 2 * (sb >> 1), si = sb & 1;
+                colo[3 * t] = k.A1 * (vp[wa][si][l][0] + vp[wa + 1][si][l][0]);
+                colo[3 * t + 1] = k.A1 * (vp[wa][si][l][1] + vp[wa + 1][si][l][1]);
+                colo[3 * t + 2] = k.A1 * (vp[wa][si][l][2] + vp[wa + 1][si][l][2]);
+            }
+        }
+    }
+    item_queue_done(counter);
+}
+
 // The mixed product with two targets per thread (items of 256 targets):
 // target t0 + threadIdx.x in lane x, t0 + 128 + threadIdx.x in lane y.
 // Differences are formed from the hi parts; within a quarter of the
@@ -977,7 +1197,7 @@ int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup, int sym) {
     const int S = h->S;
     if (h->cfg.precision != AM_MIXED) tpt = 1;
     if (h->per) chunk = std::max(1, h->Nb);  // the periodic product writes u in one piece
-    if (h->per || h->cfg.precision != AM_FP64) sym = 0;
+    if (h->per || (h->cfg.precision == AM_MIXED && sym != 4)) sym = 0;  // mixed: tiles of 128 only
     if (sym) chunk = 32 * sym;
     // targets per item: a block's targets, or (one target per thread) 32 or
     // 64 of them so that small systems spread over more SMs
@@ -1043,6 +1263,9 @@ int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup, int sym) {
         h->n_sym = (int)sitems.size();
         h->sym_nsub = sym;
         h->mv_gridsym = std::min(sym_grid(h->cfg.wall != 0, sym), h->n_sym);
+        h->mv_gridsym32 = std::min(h->cfg.wall ? resident_grid(rpy_sym_mixed_x2<true>)
+                                               : resident_grid(rpy_sym_mixed_x2<false>),
+                                   h->n_sym);
     }
     if (h->d_items) cudaFree(h->d_items);
     h->d_items = nullptr;
@@ -1116,6 +1339,15 @@ void launch_items(am_handle* h, const double* lam, int mode, const int* active) 
         else
             rpy_items_f64<false><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,
                                                                    h->d_item_counter, k, active);
+    } else if (h->n_sym > 0) {
+        const RpyK<float> k = rpy_consts<float>(h->prm);
+        const SymItem* si = static_cast<const SymItem*>(h->d_sym_items);
+        if (h->cfg.wall)
+            rpy_sym_mixed_x2<true><<<h->mv_gridsym32, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, si,
+                                                                         h->n_sym, h->d_item_counter, k, active);
+        else
+            rpy_sym_mixed_x2<false><<<h->mv_gridsym32, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, si,
+                                                                          h->n_sym, h->d_item_counter, k, active);
     } else {
         const RpyK<float> k = rpy_consts<float>(h->prm);
 #define AM_MIXED_ITEMS(W, T)                                                                             \
@@ -1178,14 +1410,22 @@ int mobility_autotune(am_handle* h) {
             }
         }
     }
-    // FP64: the symmetric product on tiles of 32, 64 and 128 blobs, while its
-    // partial sums (one slot per tile of the system) stay within 1 GiB
+    // The symmetric product: FP64 on tiles of 32, 64 and 128 blobs while
+    // its partial sums (one slot per tile of the system) stay within 1 GiB;
+    // mixed on tiles of 128 while they stay within a quarter of the free
+    // device memory (24 GB for 360,000 blobs)
     if (h->cfg.precision == AM_FP64) {
         for (int nsub : {1, 2, 4}) {
             long long slots = 0;
             for (const auto& r : h->sys) slots += (long long)((r.Nb + 32 * nsub - 1) / (32 * nsub)) * 3 * r.Nb;
             if (slots * 8 <= (1LL << 30)) cand.push_back({1, 32 * nsub, 0, nsub});
         }
+    } else if (!h->per) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        long long slots = 0;
+        for (const auto& r : h->sys) slots += (long long)((r.Nb + 127) / 128) * 3 * r.Nb;
+        if ((double)slots * 8.0 <= 0.25 * (double)free_b) cand.push_back({2, 128, 0, 4});
     }
     cudaStream_t st = h->stream;
     double* lam = nullptr;

@@ -5,7 +5,10 @@ at the FP64 bar (1e-12, max-abs over max-abs) and against the one-direction
 kernel, on sizes that leave ragged tiles, free space and above a wall; and a
 batched FP64 solve on the symmetric layout, whose systems stop at different
 iterations (stopped systems write zero partial sums), against the oracle's
-dense solves at 1e-10."""
+dense solves at 1e-10.  The symmetric mixed product (FP32 pair terms in
+paired lanes, rpy_sym_mixed_x2) against the oracle at the mixed bar 1e-5,
+with the FP64 and double-float products on the same layout, and a batched
+mixed solve on it."""
 import numpy as np
 import pytest
 
@@ -28,9 +31,9 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def loose(r, a, wall):
+def loose(r, a, wall, precision="fp64"):
     n = len(r)
-    s = binding.Solver(eta=1.0, a=a, wall=wall, precision="fp64")
+    s = binding.Solver(eta=1.0, a=a, wall=wall, precision=precision)
     s.set_bodies(r, np.tile([1.0, 0, 0, 0], (n, 1)), np.arange(n + 1), np.zeros((n, 3)), np.zeros((n, 6)),
                  np.arange(n))
     return s
@@ -56,15 +59,49 @@ def test_symmetric_product_matches_oracle(tile, n, wall):
 
 
 def test_symmetric_layout_rejected_where_it_does_not_apply():
-    s = binding.Solver(a=0.1, precision="mixed")
     r, _ = W.random_blobs(1, 10, a=0.1)
-    s.set_bodies(r, np.tile([1.0, 0, 0, 0], (10, 1)), np.arange(11), np.zeros((10, 3)), np.zeros((10, 6)),
-                 np.arange(10))
-    with pytest.raises(binding.AmError):
+    s = loose(r, 0.1, 0, "mixed")
+    with pytest.raises(binding.AmError):  # mixed: tiles of 128 only
         s.set_mobility_layout(3, 64)
     s64 = loose(r, 0.1, 0)
     with pytest.raises(binding.AmError):
         s64.set_mobility_layout(3, 48)
+
+
+@pytest.mark.parametrize("n", [1, 2, 129, 300, 1000])
+@pytest.mark.parametrize("wall", [0, 1])
+def test_symmetric_mixed_product_matches_oracle(n, wall):
+    # FP32 pair terms in paired lanes, both directions per evaluation; the
+    # mixed bar 1e-5, and far from the origin so that the hi/lo positions
+    # of near pairs matter
+    r, lam = W.random_blobs(500 + n, n, a=0.1, wall=wall)
+    if n >= 4:
+        r[1] = r[0] + [0.05, 0.1, 0.0]
+        r[3] = r[2] + [0.2, 0.0, 0.0]
+    r = r + np.array([250.0, -125.0, 0.0])
+    s = loose(r, 0.1, wall, "mixed")
+    s.set_mobility_layout(3, 128)
+    assert s.mobility_layout()[3] == 128
+    u = s.apply_mobility(lam)
+    ref = om.mobility_matvec(r, lam, 0.1, 1.0, wall)
+    assert rel(u, ref) <= 1e-5
+    # FP64 and double-float products on the same (symmetric) layout
+    assert rel(s.apply_mobility_ex(lam, "fp64"), ref) <= 1e-12
+    assert rel(s.apply_mobility_ex(lam, "df64"), ref) <= 1e-11
+
+
+def test_batched_mixed_solve_on_symmetric_layout():
+    ws = [W.chains_free_space(600 + k, n_chains=1 + k % 3, bodies_per_chain=4) for k in range(20)]
+    s = binding.Solver.from_workloads(ws, tol=1e-8, precision="mixed", max_iter=2000)
+    s.set_mobility_layout(3, 128)
+    U, phi, lam, st = s.solve()
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-8
+    for k, (w, (Us, ps, ls)) in enumerate(zip(ws, s.split(U, phi, lam))):
+        if k % 4:
+            continue
+        S = System(w)
+        lo, uo, po = S.split(S.solve_dense())
+        assert rel(Us.ravel(), uo) <= 1e-5, k
 
 
 def test_batched_solve_on_symmetric_layout():
