@@ -2,7 +2,7 @@
 piece of the solver's hot path a few times and exits, so that a capture of
 one kernel (-k, -c) ends quickly.  Nothing here is timed.
 
-    python -m paper_2107_10800_gb300.profile_cases product --blobs 60000 [--arith mixed|fp64|df64]
+    python -m paper_2107_10800_gb300.profile_cases product --blobs 60000 [--arith mixed|fp64|df64] [--symmetric]
     python -m paper_2107_10800_gb300.profile_cases colony --precision fp64|mixed [--steps 3] [--host-steps]
     python -m paper_2107_10800_gb300.profile_cases batched [--steps 1] [--host-steps]
     python -m paper_2107_10800_gb300.profile_cases mlp [--rows 65536] [--calls 3]
@@ -11,7 +11,8 @@ one kernel (-k, -c) ends quickly.  Nothing here is timed.
 product: the all-pairs wall product u = M lambda on the first N blobs of the
 1,000-bacteria suspension above a wall (each blob its own body, so the
 product is the solver's work-queue kernel on one system), two targets per
-thread and 4,096-source chunks for the mixed arithmetic; `--calls` products.
+thread and 4,096-source chunks for the mixed arithmetic, or with
+--symmetric the symmetric product on tile pairs of 128; `--calls` products.
 colony: Euler steps of the diatom colony (2,560 blobs, 62 sliding links,
 dt = 1e-3, relative residual 1e-8); with --host-steps the Arnoldi steps are
 launched from the host (per-launch timing of the product on) instead of
@@ -37,7 +38,7 @@ if ROOT not in sys.path:
 from paper_2107_10800_gb300 import build, binding, workloads as W  # noqa: E402
 
 
-def product(blobs, arith, calls):
+def product(blobs, arith, calls, symmetric=False):
     w = W.bacteria_wall(1)
     s = binding.Solver.from_workload(w, precision="mixed")
     r = s.blobs()[:blobs]
@@ -46,7 +47,10 @@ def product(blobs, arith, calls):
     s = binding.Solver(eta=w["eta"], a=w["a"], wall=1, precision="mixed")
     s.set_bodies(r, np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)), np.arange(n + 1), np.zeros((n, 3)),
                  np.zeros((n, 6)), np.arange(n))
-    s.set_mobility_layout(2 if arith == "mixed" else 1, 4096 if arith == "mixed" else 0)
+    if symmetric:
+        s.set_mobility_layout(3, 128)
+    else:
+        s.set_mobility_layout(2 if arith == "mixed" else 1, 4096 if arith == "mixed" else 0)
     lam = np.random.default_rng(0).standard_normal(r.shape)
     for _ in range(calls):
         s.apply_mobility_ex(lam, arith)
@@ -105,10 +109,11 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--host-steps", action="store_true")
+    ap.add_argument("--symmetric", action="store_true")
     a = ap.parse_args()
     build.build()
     if a.case == "product":
-        product(a.blobs, a.arith, a.calls)
+        product(a.blobs, a.arith, a.calls, a.symmetric)
     elif a.case == "colony":
         colony(a.precision, a.steps, a.host_steps)
     elif a.case == "batched":
