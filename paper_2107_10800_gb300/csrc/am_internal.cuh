@@ -77,6 +77,19 @@ struct MvItem {
     int sys, pad;     // system index
 };
 
+// One item of the symmetric products: tiles I (targets) and J (sources)
+// of T = 32 NSUB blobs of one system with I <= J; the pairs between them are
+// evaluated once and give the rows of I (slot J) and the columns of J (slot
+// I); the diagonal item (I = J) takes each unordered pair of its tile once
+// and writes rows and columns together.
+struct SymItem {
+    int i0, ni, j0, nj;     // first blob and count of tile I and of tile J
+    int tbase, sys;         // first blob of the system, system
+    int ti, tj;             // tile indices within the system (partial-sum slots)
+    long long poff;         // the system's partial-sum offset
+    int n3, pad;            // 3 N_s
+};
+
 // ---- device helpers -----------------------------------------------------
 // End of a work-queue kernel (counter[0]: next item, counter[1]: blocks
 // finished): the last block to finish zeroes both for the next launch.
@@ -187,7 +200,7 @@ struct am_handle {
     bool mv_tuned = false;
     // tile-pair items of the symmetric FP64 product (tiles of 32 sym_nsub blobs)
     void* d_sym_items = nullptr;
-    int n_sym = 0, sym_nsub = 0, mv_gridsym = 0, mv_gridsym32 = 0;
+    int n_sym = 0, sym_nsub = 0, mv_gridsym = 0, mv_gridsym32 = 0, mv_gridsymdf = 0;
 
     // host structure
     std::vector<int> blob_off, asm_of_body, bp, bq;

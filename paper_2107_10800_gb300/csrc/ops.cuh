@@ -46,6 +46,7 @@ int advance(am_handle* h, double dt, am_step_stats* st);
 int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup = 0, int sym = 0);
 void launch_items(am_handle* h, const double* lam, int mode, const int* active = nullptr);
 int df_resident_grid(bool wall);
+int sym_df_resident_grid(bool wall);
 void launch_items_df(am_handle* h, const double* lam);
 void launch_sum_items(am_handle* h, double* u);
 int mobility_autotune(am_handle* h);

@@ -516,19 +516,6 @@ rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam
     item_queue_done(counter);
 }
 
-// One item of the symmetric FP64 product: tiles I (targets) and J (sources)
-// of T = 32 NSUB blobs of one system with I <= J; the pairs between them are
-// evaluated once and give the rows of I (slot J) and the columns of J (slot
-// I); the diagonal item (I = J) takes each unordered pair of its tile once
-// and writes rows and columns together.
-struct SymItem {
-    int i0, ni, j0, nj;     // first blob and count of tile I and of tile J
-    int tbase, sys;         // first blob of the system, system
-    int ti, tj;             // tile indices within the system (partial-sum slots)
-    long long poff;         // the system's partial-sum offset
-    int n3, pad;            // 3 N_s
-};
-
 // Symmetric FP64 product (the mobility is symmetric: M_ji = M_ij^T).  Per
 // item the block stages both tiles; its warps take the item's NSUB x NSUB
 // warp tiles (32 targets x 32 sources) in turn.  In a warp tile lane l
@@ -1266,6 +1253,7 @@ int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup, int sym) {
         h->mv_gridsym32 = std::min(h->cfg.wall ? resident_grid(rpy_sym_mixed_x2<true>)
                                                : resident_grid(rpy_sym_mixed_x2<false>),
                                    h->n_sym);
+        h->mv_gridsymdf = std::min(sym_df_resident_grid(h->cfg.wall != 0), h->n_sym);
     }
     if (h->d_items) cudaFree(h->d_items);
     h->d_items = nullptr;
