@@ -310,14 +310,17 @@ def _quat_rot(q):
                   + (s * s - 0.5) * np.eye(3))
 
 
-def bacteria_periodic(seed, lattice=(10, 10, 10), spacing=(15.0, 3.0, 3.0), tilt=0.1, a=0.05,
-                      motor_torque=1.0, eta=1.0, **tmpl_kw):
+def bacteria_periodic(seed, lattice=(10, 10, 10), spacing=(15.0, 3.0, 3.0), tilt=0.02, a=0.05,
+                      motor_torque=1.0, eta=1.0, jitter=(0.02, 0.05, 0.05), **tmpl_kw):
     """Bacteria in a triply periodic box (the periodic suspensions of Sec.
     5.3, here without the wall): one bacterium per site of a lattice with
     the given spacing (box = lattice x spacing), its head centre jittered by
-    a tenth of the spacing, long axis along x tilted by up to ``tilt``
-    radians about a random perpendicular axis and spun by a random angle
-    about itself (an aligned suspension whose bodies do not overlap).
+    up to ``jitter`` x spacing per axis, long axis along x tilted by up to
+    ``tilt`` radians about a random perpendicular axis and spun by a random
+    angle about itself: an aligned suspension.  With the defaults the bodies
+    cannot overlap: a bacterium spans 13.5 along x and at most 0.55 + 0.24
+    (head radius plus the tilt over its length) across, so neighbouring
+    bacteria stay at least 0.95 apart along x and 1.1 across.
     Motor torques as in bacteria_wall.  With the defaults: 1,000 bacteria,
     360,000 blobs in a 150 x 30 x 30 box.  Returns the workload dict with
     ``box``."""
@@ -333,7 +336,8 @@ def bacteria_periodic(seed, lattice=(10, 10, 10), spacing=(15.0, 3.0, 3.0), tilt
     for ix in range(lattice[0]):
         for iy in range(lattice[1]):
             for iz in range(lattice[2]):
-                origin = (np.array([ix, iy, iz]) + 0.5 + rng.uniform(-0.1, 0.1, 3)) * np.array(spacing)
+                origin = (np.array([ix, iy, iz]) + 0.5 +
+                          rng.uniform(-1.0, 1.0, 3) * np.asarray(jitter)) * np.array(spacing)
                 spin = _quat_axis_angle([1.0, 0.0, 0.0], rng.uniform(0.0, 2 * math.pi))
                 phi = rng.uniform(0.0, 2 * math.pi)
                 tq = _quat_axis_angle([0.0, math.cos(phi), math.sin(phi)], rng.uniform(0.0, tilt))

@@ -97,3 +97,26 @@ def test_learned_argument_checks(L):
     assert L.am_mlp_get_params(None, None) == binding.AM_ERR_ARG
     assert L.am_mlp_train(None, None, None, 0, 1, 1, 1e-3, 0, None) == binding.AM_ERR_ARG
     L.am_mlp_destroy(None)
+
+
+def _struct_fields(name):
+    """Field names of a typedef struct in include/am.h, in order."""
+    text = open(os.path.join(ROOT, "include", "am.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", text).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            m = re.search(r"(\w+)\s*(\[\s*\d+\s*\])?\s*$", part.strip())
+            names.append(m.group(1))
+    return names
+
+
+def test_binding_structs_mirror_the_header():
+    # the ctypes mirrors of am_config and am_step_stats list the header's
+    # fields in the header's order (a mismatch would shift every later field)
+    assert [f for f, _ in binding.Config._fields_] == _struct_fields("am_config")
+    assert [f for f, _ in binding.StepStats._fields_] == _struct_fields("am_step_stats")
