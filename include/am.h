@@ -506,19 +506,20 @@ AM_API int am_set_initial_guess(am_handle* h, int order);
 /* Destroy a handle and free its device memory (NULL is a no-op). */
 AM_API void am_destroy(am_handle* h);
 
-/* Message of the last error of h, or of the calling thread's last stateless
- * call when h is NULL; never NULL. */
 /* Parameters of a periodic handle's product (after am_set_bodies):
- * params (6): xi (Ewald splitting), r_c (real-space cutoff), sigma (width
- *             of the Gaussian of the grid transfer), hx, hy, hz (grid
+ * params (6): xi (Ewald splitting), r_c (real-space cutoff), beta (shape
+ *             of the exponential-of-semicircle window of the grid
+ *             transfer, exp(beta (sqrt(1 - z^2) - 1))), hx, hy, hz (grid
  *             spacings);
- * sizes (6):  Mx, My, Mz (grid points per side), P (Gaussian support in
+ * sizes (6):  Mx, My, Mz (grid points per side), w (window width in
  *             points per side), real-space pairs within r_c at the current
  *             pose (the target itself included), cells of the cell list.
  * Either pointer may be NULL.  Errors: AM_ERR_ARG for a handle without a
  * box or without bodies. */
 AM_API int am_periodic_info(am_handle* h, double* params, long long* sizes);
 
+/* Message of the last error of h, or of the calling thread's last stateless
+ * call when h is NULL; never NULL. */
 AM_API const char* am_last_error(const am_handle* h);
 
 #ifdef __cplusplus

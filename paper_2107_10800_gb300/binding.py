@@ -329,7 +329,7 @@ class Solver:
         i = np.empty(6, np.int64)
         self._check(lib().am_periodic_info(self.h, d.ctypes.data_as(_dp),
                                            i.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))))
-        return {"xi": d[0], "r_c": d[1], "sigma": d[2], "h": tuple(d[3:6]),
+        return {"xi": d[0], "r_c": d[1], "beta": d[2], "h": tuple(d[3:6]),
                 "grid": tuple(int(v) for v in i[0:3]), "support": int(i[3]),
                 "real_pairs": int(i[4]), "cells": int(i[5])}
 
