@@ -1427,18 +1427,31 @@ int mobility_autotune(am_handle* h) {
     Cand pick = cand[0];
     const bool timing = h->timing;
     h->timing = false;
+    // per candidate: a warm-up product and sum, timed; a candidate whose
+    // warm-up is already 50 % slower than the best (per product) stops there,
+    // and products of more than 20 ms are taken from the warm-up alone (large
+    // systems, where the candidates cost seconds)
     for (auto c : cand) {
         if (mobility_layout(h, c.tpt, c.chunk, c.tgroup, c.sym)) continue;
-        launch_items(h, lam, false);  // warm-up
         cudaEventRecord(e0, st);
-        for (int rep = 0; rep < 2; ++rep) {
-            launch_items(h, lam, false);
-            launch_sum_items(h, usum);
-        }
+        launch_items(h, lam, false);  // warm-up
+        launch_sum_items(h, usum);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) continue;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        float warm = 0.f;
+        cudaEventElapsedTime(&warm, e0, e1);
+        float ms = warm;
+        if (warm < 1.5f * best && warm <= 20.f) {
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 2; ++rep) {
+                launch_items(h, lam, false);
+                launch_sum_items(h, usum);
+            }
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms *= 0.5f;
+        }
         if (ms < best) { best = ms; pick = c; }
     }
     h->timing = timing;
