@@ -46,9 +46,6 @@ RpyDf rpy_df_consts(const RpyParams& q) {
     return k;
 }
 
-__device__ __forceinline__ df dfc(double c) { return df_from(c); }
-__device__ __forceinline__ df one_plus(df x) { return df_add(df{1.0f, 0.0f}, x); }
-
 // the free-space coefficients c1, c2 at squared distance r2 (rpy_pair.cuh)
 __device__ __forceinline__ void free_coefs_df(df r2, const RpyDf& k, df& c1, df& c2) {
     const df one{1.0f, 0.0f};
