@@ -40,7 +40,7 @@ def loose(r, a, wall, precision="fp64"):
 
 
 @pytest.mark.parametrize("tile", [32, 64, 128])
-@pytest.mark.parametrize("n", [1, 2, 33, 65, 129, 300, 1000])
+@pytest.mark.parametrize("n", [1, 2, 33, 64, 65, 128, 129, 256, 300, 1000])
 @pytest.mark.parametrize("wall", [0, 1])
 def test_symmetric_product_matches_oracle(tile, n, wall):
     r, lam = W.random_blobs(300 + n, n, a=0.1, wall=wall)
@@ -68,7 +68,7 @@ def test_symmetric_layout_rejected_where_it_does_not_apply():
         s64.set_mobility_layout(3, 48)
 
 
-@pytest.mark.parametrize("n", [1, 2, 129, 300, 1000])
+@pytest.mark.parametrize("n", [1, 2, 128, 129, 256, 300, 1000])
 @pytest.mark.parametrize("wall", [0, 1])
 def test_symmetric_mixed_product_matches_oracle(n, wall):
     # FP32 pair terms in paired lanes, both directions per evaluation; the
