@@ -293,8 +293,9 @@ AM_API int am_steric_forces(am_handle* h, double* f);
  * source chunks of source_chunk blobs (0: a default that fills the GPU).
  * targets_per_thread = 0 restores autotuning before the next product;
  * targets_per_thread = 3 selects the symmetric product (handles without a
- * box) on tiles of source_chunk = 32, 64 or 128 blobs (mixed handles: 128).
- * The
+ * box) on tiles of source_chunk = 32, 64 or 128 blobs (mixed handles: two
+ * targets per thread in paired FP32 lanes on tiles of 128, one target per
+ * thread on tiles of 32 and 64).  The
  * layout is rebuilt (and autotuned) whenever the bodies change.  A
  * measurement and testing aid, not in the paper.  Errors: AM_ERR_ARG (no
  * bodies, values out of range), AM_ERR_CUDA. */
@@ -302,12 +303,12 @@ AM_API int am_set_mobility_layout(am_handle* h, int targets_per_thread, int sour
 
 /* The layout of the all-pairs product in use (after the autotuning of the
  * first product): layout[0] targets per thread, [1] source chunk (blobs),
- * [2] targets per work item, [3] tile of the symmetric FP64 product (32,
- * 64 or 128 blobs; 0 when the one-direction kernel runs).  The symmetric
+ * [2] targets per work item, [3] tile of the symmetric product (32, 64 or
+ * 128 blobs; 0 when the one-direction kernel runs).  The symmetric
  * product evaluates each unordered pair of blobs once and applies it in both
  * directions (M_ji = M_ij^T); the autotuner takes it when it is faster and
- * its partial sums (one slot per tile) fit (FP64: 1 GiB; mixed, tiles of
- * 128: a quarter of the free device memory).  A
+ * its partial sums (one slot per tile) fit (1 GiB; mixed in paired lanes,
+ * tiles of 128: a quarter of the free device memory).  A
  * measurement aid, not in the paper.  Errors: AM_ERR_ARG (NULL, no
  * bodies). */
 AM_API int am_get_mobility_layout(am_handle* h, int* layout);

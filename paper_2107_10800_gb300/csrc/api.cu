@@ -1367,12 +1367,11 @@ extern "C" AM_API int am_set_mobility_layout(am_handle* h, int targets_per_threa
     }
     if (targets_per_thread == 3) {  // the symmetric product on tiles of source_chunk blobs
         const bool mixed = h->cfg.precision == AM_MIXED;
-        if (box_set(h->cfg) || h->sb ||
-            (mixed ? source_chunk != 128 : (source_chunk != 32 && source_chunk != 64 && source_chunk != 128)))
+        if (box_set(h->cfg) || h->sb || (source_chunk != 32 && source_chunk != 64 && source_chunk != 128))
             return set_err(h, AM_ERR_ARG, "am_set_mobility_layout: the symmetric product needs a handle without "
-                                          "a box, multi-blob bodies, and tiles of 32, 64 or 128 blobs (mixed: "
-                                          "128)");
-        if (am::mobility_layout(h, mixed ? 2 : 1, source_chunk, 0, source_chunk / 32))
+                                          "a box, multi-blob bodies, and tiles of 32, 64 or 128 blobs");
+        // mixed handles: paired FP32 lanes on tiles of 128, one target per lane on smaller tiles
+        if (am::mobility_layout(h, mixed && source_chunk == 128 ? 2 : 1, source_chunk, 0, source_chunk / 32))
             return set_err(h, AM_ERR_CUDA, "am_set_mobility_layout: device allocation failed");
         h->mv_tuned = true;
         return AM_OK;

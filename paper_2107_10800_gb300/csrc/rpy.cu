@@ -1034,6 +1034,140 @@ rpy_sym_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo, c
     item_queue_done(counter);
 }
 
+// Symmetric mixed product on tiles of 32 NSUB blobs, one target per lane:
+// the scheme of rpy_sym_f64 (each unordered pair of a tile pair evaluated
+// once and applied in both directions, the column sums carried from lane
+// to lane, the diagonal warp tile on steps 1..16) with FP32 pair terms.
+// Differences are formed from the hi parts of the positions; within a
+// quarter of the target's largest coordinate the lo parts are added, as in
+// rpy_items_mixed.  A lane sums the 32 terms of a warp tile in FP32; the
+// warp-tile sums are added in FP64 in a fixed order.  Small tiles spread
+// systems of a few thousand blobs over every SM.
+template <bool WALL, int NSUB>
+__global__ void __launch_bounds__(NSUB == 1 ? 32 : 128)
+rpy_sym_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo, const double* __restrict__ lam,
+              double* __restrict__ part, const SymItem* __restrict__ items, int n_items, int* __restrict__ counter,
+              RpyK<float> k, const int* __restrict__ active) {
+    constexpr int T = 32 * NSUB;
+    constexpr int NW = NSUB == 1 ? 1 : 4;
+    constexpr int NWT = NSUB * NSUB;
+    __shared__ float4 hI[T], hJ[T];  // hi parts, .w = twice the height
+    __shared__ float4 oI[T], oJ[T];  // lo parts
+    __shared__ float4 lI[T], lJ[T];  // forces
+    __shared__ double up[NWT][32][3], vp[NWT][32][3];
+    __shared__ int s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int round = 0;; ++round) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(counter, 1);
+        __syncthreads();
+        const int itn = s_item;
+        if (itn >= n_items) break;
+        const SymItem m = items[itn];
+        const bool diag = m.ti == m.tj;
+        double* rowo = part + m.poff + (long long)m.tj * m.n3 + 3 * (long long)(m.i0 - m.tbase);
+        double* colo = part + m.poff + (long long)m.ti * m.n3 + 3 * (long long)(m.j0 - m.tbase);
+        if (active && !active[m.sys]) {  // a stopped system: zero partial sums
+            for (int q = threadIdx.x; q < 3 * m.ni; q += blockDim.x) rowo[q] = 0.0;
+            if (!diag)
+                for (int q = threadIdx.x; q < 3 * m.nj; q += blockDim.x) colo[q] = 0.0;
+            continue;
+        }
+        for (int q = threadIdx.x; q < T; q += blockDim.x) {
+            const bool oi = q < m.ni, oj = q < m.nj;
+            float4 a = oi ? hi[m.i0 + q] : make_float4(0.f, 0.f, 1.f, 0.f);
+            a.w = 2.f * a.z;
+            hI[q] = a;
+            oI[q] = oi ? lo[m.i0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            lI[q] = oi ? make_float4((float)lam[3 * (size_t)(m.i0 + q)], (float)lam[3 * (size_t)(m.i0 + q) + 1],
+                                     (float)lam[3 * (size_t)(m.i0 + q) + 2], 0.f)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 b = oj ? hi[m.j0 + q] : make_float4(0.f, 0.f, 1.f, 0.f);
+            b.w = 2.f * b.z;
+            hJ[q] = b;
+            oJ[q] = oj ? lo[m.j0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            lJ[q] = oj ? make_float4((float)lam[3 * (size_t)(m.j0 + q)], (float)lam[3 * (size_t)(m.j0 + q) + 1],
+                                     (float)lam[3 * (size_t)(m.j0 + q) + 2], 0.f)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        for (int wt = warp; wt < NWT; wt += NW) {
+            const int a = wt / NSUB, b = wt % NSUB;
+            float ux = 0.f, uy = 0.f, uz = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+            if (!(diag && b < a)) {  // below the diagonal of a diagonal item: taken by (b, a)
+                const bool self_tile = diag && a == b;
+                const int t = 32 * a + lane;
+                const float4 xi = hI[t], xo = oI[t], mu = lI[t];
+                const float nr = 0.25f * fmaxf(fabsf(xi.x), fmaxf(fabsf(xi.y), fabsf(xi.z)));
+                const float near2 = nr * nr;
+                const bool ti_ok = t < m.ni;
+#pragma unroll 1
+                for (int step = 0; step < 32; ++step) {
+                    const int q = 32 * b + ((lane + step) & 31);
+                    const bool pair_ok = ti_ok && q < m.nj &&
+                                         (!self_tile || (step >= 1 && (step < 16 || (step == 16 && lane < 16))));
+                    if (pair_ok) {
+                        const float4 xj = hJ[q], l = lJ[q];
+                        float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+                        float rxy2 = fmaf(dx, dx, dy * dy);
+                        float r2 = fmaf(dz, dz, rxy2);
+                        if (r2 < near2) {
+                            const float4 o = oJ[q];
+                            dx += xo.x - o.x;
+                            dy += xo.y - o.y;
+                            dz += xo.z - o.z;
+                            rxy2 = fmaf(dx, dx, dy * dy);
+                            r2 = fmaf(dz, dz, rxy2);
+                        }
+                        if (WALL)
+                            pair_wall_sym<float>(dx, dy, dz, rxy2, r2, xi.z + xj.z, xj.w, -xi.z, l.x, l.y, l.z, mu.x,
+                                                 mu.y, mu.z, k, ux, uy, uz, vx, vy, vz);
+                        else
+                            pair_free_sym<float>(dx, dy, dz, r2, l.x, l.y, l.z, mu.x, mu.y, mu.z, k, ux, uy, uz, vx,
+                                                 vy, vz);
+                    } else if (self_tile && step == 0 && ti_ok) {  // the self term
+                        if (WALL)
+                            pair_wall_r2<float>(0.f, 0.f, 0.f, 0.f, 0.f, xi.w, xi.w, -xi.z, mu.x, mu.y, mu.z, k, ux,
+                                                uy, uz);
+                        else
+                            pair_free<float>(0.f, 0.f, 0.f, mu.x, mu.y, mu.z, k, ux, uy, uz);
+                    }
+                    // hand the column sum to the lane that meets this source next
+                    const int src = (lane + 1) & 31;
+                    vx = __shfl_sync(0xffffffffu, vx, src);
+                    vy = __shfl_sync(0xffffffffu, vy, src);
+                    vz = __shfl_sync(0xffffffffu, vz, src);
+                }
+            }
+            up[wt][lane][0] = ux; up[wt][lane][1] = uy; up[wt][lane][2] = uz;
+            vp[wt][lane][0] = vx; vp[wt][lane][1] = vy; vp[wt][lane][2] = vz;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            const int a = t >> 5, l = t & 31;
+            if (t < m.ni) {
+                double sx = 0.0, sy = 0.0, sz = 0.0;
+                for (int b = 0; b < NSUB; ++b) {
+                    sx += up[a * NSUB + b][l][0]; sy += up[a * NSUB + b][l][1]; sz += up[a * NSUB + b][l][2];
+                }
+                if (diag)
+                    for (int a2 = 0; a2 < NSUB; ++a2) {
+                        sx += vp[a2 * NSUB + a][l][0]; sy += vp[a2 * NSUB + a][l][1]; sz += vp[a2 * NSUB + a][l][2];
+                    }
+                rowo[3 * t] = k.A1 * sx; rowo[3 * t + 1] = k.A1 * sy; rowo[3 * t + 2] = k.A1 * sz;
+            }
+            if (!diag && t < m.nj) {
+                double sx = 0.0, sy = 0.0, sz = 0.0;
+                for (int a2 = 0; a2 < NSUB; ++a2) {
+                    sx += vp[a2 * NSUB + a][l][0]; sy += vp[a2 * NSUB + a][l][1]; sz += vp[a2 * NSUB + a][l][2];
+                }
+                colo[3 * t] = k.A1 * sx; colo[3 * t + 1] = k.A1 * sy; colo[3 * t + 2] = k.A1 * sz;
+            }
+        }
+    }
+    item_queue_done(counter);
+}
+
 // The mixed product with two targets per thread (items of 256 targets):
 // target t0 + threadIdx.x in lane x, t0 + 128 + threadIdx.x in lane y.
 // Differences are formed from the hi parts; within a quarter of the
@@ -1175,16 +1309,32 @@ static int sym_grid(bool wall, int nsub) {
     return resident_grid(rpy_sym_f64<false, 4>, th);
 }
 
+// resident blocks of the symmetric mixed kernel: paired lanes (tpt 2,
+// tiles of 128) or one target per lane (tiles of 32 nsub)
+static int sym_mixed_grid(bool wall, int tpt, int nsub) {
+    if (tpt == 2) return wall ? resident_grid(rpy_sym_mixed_x2<true>) : resident_grid(rpy_sym_mixed_x2<false>);
+    const int th = nsub == 1 ? 32 : 128;
+    if (wall) {
+        if (nsub == 1) return resident_grid(rpy_sym_mixed<true, 1>, th);
+        if (nsub == 2) return resident_grid(rpy_sym_mixed<true, 2>, th);
+        return resident_grid(rpy_sym_mixed<true, 4>, th);
+    }
+    if (nsub == 1) return resident_grid(rpy_sym_mixed<false, 1>, th);
+    if (nsub == 2) return resident_grid(rpy_sym_mixed<false, 2>, th);
+    return resident_grid(rpy_sym_mixed<false, 4>, th);
+}
+
 // Work items for tpt targets per thread and source chunks of `chunk` blobs
-// (0: choose so that the items fill the GPU); with sym = nsub > 0 (FP64
-// handles) also the tile-pair items of the symmetric FP64 product on tiles
-// of 32 nsub blobs, whose partial-sum slots are the source chunks of that
-// length.  Returns 0 on success.
+// (0: choose so that the items fill the GPU); with sym = nsub > 0 also the
+// tile-pair items of the symmetric product on tiles of 32 nsub blobs, whose
+// partial-sum slots are the source chunks of that length (mixed handles:
+// paired lanes with tpt = 2 on tiles of 128, one target per lane with
+// tpt = 1).  Returns 0 on success.
 int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup, int sym) {
     const int S = h->S;
     if (h->cfg.precision != AM_MIXED) tpt = 1;
     if (h->per) chunk = std::max(1, h->Nb);  // the periodic product writes u in one piece
-    if (h->per || (h->cfg.precision == AM_MIXED && sym != 4)) sym = 0;  // mixed: tiles of 128 only
+    if (h->per || (tpt == 2 && sym != 4)) sym = 0;  // paired lanes: tiles of 128 only
     if (sym) chunk = 32 * sym;
     // targets per item: a block's targets, or (one target per thread) 32 or
     // 64 of them so that small systems spread over more SMs
@@ -1250,9 +1400,7 @@ int mobility_layout(am_handle* h, int tpt, int chunk, int tgroup, int sym) {
         h->n_sym = (int)sitems.size();
         h->sym_nsub = sym;
         h->mv_gridsym = std::min(sym_grid(h->cfg.wall != 0, sym), h->n_sym);
-        h->mv_gridsym32 = std::min(h->cfg.wall ? resident_grid(rpy_sym_mixed_x2<true>)
-                                               : resident_grid(rpy_sym_mixed_x2<false>),
-                                   h->n_sym);
+        h->mv_gridsym32 = std::min(sym_mixed_grid(h->cfg.wall != 0, tpt, sym), h->n_sym);
         h->mv_gridsymdf = std::min(sym_df_resident_grid(h->cfg.wall != 0), h->n_sym);
     }
     if (h->d_items) cudaFree(h->d_items);
@@ -1330,12 +1478,26 @@ void launch_items(am_handle* h, const double* lam, int mode, const int* active) 
     } else if (h->n_sym > 0) {
         const RpyK<float> k = rpy_consts<float>(h->prm);
         const SymItem* si = static_cast<const SymItem*>(h->d_sym_items);
-        if (h->cfg.wall)
-            rpy_sym_mixed_x2<true><<<h->mv_gridsym32, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, si,
-                                                                         h->n_sym, h->d_item_counter, k, active);
-        else
-            rpy_sym_mixed_x2<false><<<h->mv_gridsym32, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, si,
-                                                                          h->n_sym, h->d_item_counter, k, active);
+        const int th = h->mv_tpt == 2 || h->sym_nsub > 1 ? kThreads : 32;
+#define AM_SYM32(W, N)                                                                                   \
+    rpy_sym_mixed<W, N><<<h->mv_gridsym32, th, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, si, h->n_sym, \
+                                                        h->d_item_counter, k, active)
+#define AM_SYM32X2(W)                                                                                        \
+    rpy_sym_mixed_x2<W><<<h->mv_gridsym32, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, si, h->n_sym, \
+                                                              h->d_item_counter, k, active)
+        if (h->cfg.wall) {
+            if (h->mv_tpt == 2) AM_SYM32X2(true);
+            else if (h->sym_nsub == 1) AM_SYM32(true, 1);
+            else if (h->sym_nsub == 2) AM_SYM32(true, 2);
+            else AM_SYM32(true, 4);
+        } else {
+            if (h->mv_tpt == 2) AM_SYM32X2(false);
+            else if (h->sym_nsub == 1) AM_SYM32(false, 1);
+            else if (h->sym_nsub == 2) AM_SYM32(false, 2);
+            else AM_SYM32(false, 4);
+        }
+#undef AM_SYM32X2
+#undef AM_SYM32
     } else {
         const RpyK<float> k = rpy_consts<float>(h->prm);
 #define AM_MIXED_ITEMS(W, T)                                                                             \
@@ -1398,17 +1560,17 @@ int mobility_autotune(am_handle* h) {
             }
         }
     }
-    // The symmetric product: FP64 on tiles of 32, 64 and 128 blobs while
-    // its partial sums (one slot per tile of the system) stay within 1 GiB;
-    // mixed on tiles of 128 while they stay within a quarter of the free
-    // device memory (24 GB for 360,000 blobs)
-    if (h->cfg.precision == AM_FP64) {
-        for (int nsub : {1, 2, 4}) {
-            long long slots = 0;
-            for (const auto& r : h->sys) slots += (long long)((r.Nb + 32 * nsub - 1) / (32 * nsub)) * 3 * r.Nb;
-            if (slots * 8 <= (1LL << 30)) cand.push_back({1, 32 * nsub, 0, nsub});
-        }
-    } else if (!h->per) {
+    // The symmetric product: on tiles of 32, 64 and 128 blobs while its
+    // partial sums (one slot per tile of the system) stay within 1 GiB (FP64,
+    // and mixed with one target per lane); mixed in paired lanes on tiles
+    // of 128 while they stay within a quarter of the free device memory
+    // (24 GB for 360,000 blobs)
+    for (int nsub : {1, 2, 4}) {
+        long long slots = 0;
+        for (const auto& r : h->sys) slots += (long long)((r.Nb + 32 * nsub - 1) / (32 * nsub)) * 3 * r.Nb;
+        if (slots * 8 <= (1LL << 30)) cand.push_back({1, 32 * nsub, 0, nsub});
+    }
+    if (mixed) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
         long long slots = 0;

@@ -8,7 +8,9 @@ iterations (stopped systems write zero partial sums), against the oracle's
 dense solves at 1e-10.  The symmetric mixed product (FP32 pair terms in
 paired lanes, rpy_sym_mixed_x2) against the oracle at the mixed bar 1e-5,
 with the FP64 and double-float products on the same layout, and a batched
-mixed solve on it."""
+mixed solve on it; the symmetric mixed product with one target per lane
+(rpy_sym_mixed) on tiles of 32 and 64 blobs, against the oracle at 1e-5 and
+against the paired-lane kernel, and a batched mixed solve on it."""
 import numpy as np
 import pytest
 
@@ -60,12 +62,11 @@ def test_symmetric_product_matches_oracle(tile, n, wall):
 
 def test_symmetric_layout_rejected_where_it_does_not_apply():
     r, _ = W.random_blobs(1, 10, a=0.1)
-    s = loose(r, 0.1, 0, "mixed")
-    with pytest.raises(binding.AmError):  # mixed: tiles of 128 only
-        s.set_mobility_layout(3, 64)
-    s64 = loose(r, 0.1, 0)
-    with pytest.raises(binding.AmError):
-        s64.set_mobility_layout(3, 48)
+    for prec in ("mixed", "fp64"):
+        s = loose(r, 0.1, 0, prec)
+        for tile in (48, 256, 16):
+            with pytest.raises(binding.AmError):
+                s.set_mobility_layout(3, tile)
 
 
 @pytest.mark.parametrize("n", [1, 2, 128, 129, 256, 300, 1000])
@@ -88,6 +89,56 @@ def test_symmetric_mixed_product_matches_oracle(n, wall):
     # FP64 and double-float products on the same (symmetric) layout
     assert rel(s.apply_mobility_ex(lam, "fp64"), ref) <= 1e-12
     assert rel(s.apply_mobility_ex(lam, "df64"), ref) <= 1e-11
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+@pytest.mark.parametrize("n", [1, 2, 33, 64, 65, 129, 300, 1000])
+@pytest.mark.parametrize("wall", [0, 1])
+def test_symmetric_mixed_small_tiles_match_oracle(tile, n, wall):
+    # one target per lane (rpy_sym_mixed) on tiles of 32 and 64 blobs, far
+    # from the origin so that the hi/lo positions of near pairs matter
+    r, lam = W.random_blobs(700 + n, n, a=0.1, wall=wall)
+    if n >= 4:
+        r[1] = r[0] + [0.05, 0.1, 0.0]
+        r[3] = r[2] + [0.2, 0.0, 0.0]
+    r = r + np.array([250.0, -125.0, 0.0])
+    s = loose(r, 0.1, wall, "mixed")
+    s.set_mobility_layout(3, tile)
+    lay = s.mobility_layout()
+    assert lay[3] == tile and lay[0] == 1
+    u = s.apply_mobility(lam)
+    ref = om.mobility_matvec(r, lam, 0.1, 1.0, wall)
+    assert rel(u, ref) <= 1e-5
+    # the FP64 and double-float products on the same partial-sum slots
+    assert rel(s.apply_mobility_ex(lam, "fp64"), ref) <= 1e-12
+    assert rel(s.apply_mobility_ex(lam, "df64"), ref) <= 1e-11
+
+
+def test_symmetric_mixed_small_tiles_agree_with_paired_lanes():
+    # the two symmetric mixed kernels against each other at 3,000 wall blobs
+    r, lam = W.random_blobs(17, 3000, a=0.1, wall=1)
+    s = loose(r, 0.1, 1, "mixed")
+    s.set_mobility_layout(3, 128)
+    u128 = s.apply_mobility(lam)
+    for tile in (32, 64):
+        s.set_mobility_layout(3, tile)
+        assert rel(s.apply_mobility(lam), u128) <= 2e-6
+
+
+def test_batched_mixed_solve_on_small_symmetric_tiles():
+    # systems that stop at different iterations write zero partial sums
+    ws = [W.chains_free_space(900 + k, n_chains=1 + k % 3, bodies_per_chain=3) for k in range(12)]
+    s = binding.Solver.from_workloads(ws, tol=1e-8, precision="mixed", max_iter=2000)
+    s.set_mobility_layout(3, 32)
+    U, phi, lam, st = s.solve()
+    assert s.mobility_layout()[3] == 32
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-8
+    for k, (w, (Us, ps, ls)) in enumerate(zip(ws, s.split(U, phi, lam))):
+        if k % 3:
+            continue
+        S = System(w)
+        lo, uo, po = S.split(S.solve_dense())
+        assert rel(Us.ravel(), uo) <= 1e-5, k
 
 
 def test_batched_mixed_solve_on_symmetric_layout():
