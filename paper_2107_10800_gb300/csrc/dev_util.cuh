@@ -116,18 +116,31 @@ __device__ __forceinline__ void tile_load(T (*S)[kNB + 1], const T* G, int ld, i
     }
 }
 
-// acc[e] for entry (r, c) = (idx / 32, idx % 32), idx = threadIdx.x + e * blockDim.x:
-// sum_k A[r][k] B[c][k] (nt) or sum_k A[r][k] B[k][c] (nn)
+// The accumulators of a 32 x 32 tile: each of the 256 threads holds a 2 x 2
+// block, acc[e] (e = 0..3) the entry (acc_row(e), acc_col(e)) with rows
+// 2 (t / 16) + e / 2 and columns 2 (t % 16) + e % 2, t = threadIdx.x; per k a
+// thread loads two entries of each operand for four multiply-adds.
+static_assert(kNB == 32 && kPcThreads == 256, "2 x 2 accumulator blocks of 256 threads cover a 32 x 32 tile");
+__device__ __forceinline__ int acc_row(int e) { return 2 * ((int)threadIdx.x >> 4) + (e >> 1); }
+__device__ __forceinline__ int acc_col(int e) { return 2 * ((int)threadIdx.x & 15) + (e & 1); }
+
+// acc[e] += sum_k A[r][k] B[c][k] (nt) or sum_k A[r][k] B[k][c] (nn) for the
+// thread's entries (r, c), each sum in the order k = 0, 1, ..
 template <class T, bool NT>
 __device__ __forceinline__ void tile_mac(const T (*A)[kNB + 1], const T (*B)[kNB + 1], T* acc) {
-#pragma unroll
-    for (int e = 0; e < kNB * kNB / kPcThreads; ++e) {
-        const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
-        T s = acc[e];
+    const int r = acc_row(0), c = acc_col(0);
+    T s00 = acc[0], s01 = acc[1], s10 = acc[2], s11 = acc[3];
 #pragma unroll 8
-        for (int k = 0; k < kNB; ++k) s = fma(A[r][k], NT ? B[c][k] : B[k][c], s);
-        acc[e] = s;
+    for (int k = 0; k < kNB; ++k) {
+        const T a0 = A[r][k], a1 = A[r + 1][k];
+        const T b0 = NT ? B[c][k] : B[k][c];
+        const T b1 = NT ? B[c + 1][k] : B[k][c + 1];
+        s00 = fma(a0, b0, s00);
+        s01 = fma(a0, b1, s01);
+        s10 = fma(a1, b0, s10);
+        s11 = fma(a1, b1, s11);
     }
+    acc[0] = s00; acc[1] = s01; acc[2] = s10; acc[3] = s11;
 }
 
 // In place: the lower Cholesky factor of the leading kw x kw part of the
@@ -227,7 +240,7 @@ __device__ void blocked_cholesky(T* L, int n, int ld, PcTiles<T>& s, int* bad, c
             __syncthreads();
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
+                const int r = acc_row(e), c = acc_col(e);
                 if (r0 + r < n && c < kw) L[(size_t)(r0 + r) * ld + k0 + c] = acc[e];
             }
             __syncthreads();
@@ -254,7 +267,7 @@ __device__ void blocked_cholesky(T* L, int n, int ld, PcTiles<T>& s, int* bad, c
                 tile_mac<T, true>(s.a, s.b, acc);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
+                    const int r = acc_row(e), c = acc_col(e);
                     if (i0 + r < n && j0 + c < n) L[(size_t)(i0 + r) * ld + j0 + c] -= acc[e];
                 }
                 __syncthreads();
@@ -309,7 +322,7 @@ __device__ void blocked_chol_inverse(const T* L, T* X, T* A, int n, int ld, PcTi
                 T acc[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
+                    const int r = acc_row(e), c = acc_col(e);
                     acc[e] = (I0 + r < n && J0 + c < n) ? -X[(size_t)(I0 + r) * ld + J0 + c] : (T)0;
                 }
                 tile_mac<T, false>(s.a, s.b, acc);  // acc = -(B_IJ - L_IK X_KJ)
@@ -317,8 +330,7 @@ __device__ void blocked_chol_inverse(const T* L, T* X, T* A, int n, int ld, PcTi
                     __syncthreads();
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        const int idx = threadIdx.x + e * kPcThreads;
-                        s.c[idx / kNB][idx % kNB] = acc[e];
+                        s.c[acc_row(e)][acc_col(e)] = acc[e];
                     }
                     tile_load(s.a, X, ld, n, I0, I0, false);  // X_II
                     __syncthreads();
@@ -328,7 +340,7 @@ __device__ void blocked_chol_inverse(const T* L, T* X, T* A, int n, int ld, PcTi
                 }
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
+                    const int r = acc_row(e), c = acc_col(e);
                     if (I0 + r < n && J0 + c < n) X[(size_t)(I0 + r) * ld + J0 + c] = -acc[e];
                 }
             }
@@ -352,7 +364,7 @@ __device__ void blocked_chol_inverse(const T* L, T* X, T* A, int n, int ld, PcTi
             }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int idx = threadIdx.x + e * kPcThreads, r = idx / kNB, c = idx % kNB;
+                const int r = acc_row(e), c = acc_col(e);
                 const int i = i0 + r, j = j0 + c;
                 if (i < n && j < n && j <= i) {
                     A[(size_t)i * ld + j] = acc[e];

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kPcThreads)
 k_pcb_build(const int* __restrict__ body_list, const int* __restrict__ blob_off,
             const double4_32a* __restrict__ r4, const double4_32a* __restrict__ d4,
             const long long* __restrict__ moff, T* __restrict__ minv, T* __restrict__ work,
-            T* __restrict__ Y, double* __restrict__ Nt, RpyK<double> prm, int wall, int* flags) {
+            T* __restrict__ Y, double* __restrict__ Nt, RpyK<T> prm, int wall, int* flags) {
     __shared__ double sh[64];
     __shared__ PcTiles<T> tiles;
     __shared__ int s_bad;
@@ -55,12 +55,17 @@ k_pcb_build(const int* __restrict__ body_list, const int* __restrict__ blob_off,
     T* A = minv + moff[b];
     T* L = work + 2 * moff[b];
     T* X = L + (size_t)m * m;
+    // the lower triangle of M^(pp) (blob pairs ti >= sj, the factorisation
+    // reads no entry above the diagonal), pair tensors in the storage
+    // precision from FP64 differences
     for (int idx = threadIdx.x + tr * blockDim.x; idx < nbl * nbl; idx += blockDim.x * ts) {
         const int ti = idx / nbl, sj = idx % nbl;
-        double Tt[9];
-        pair_tensor_f64(r4[i0 + ti], r4[i0 + sj], prm, wall, Tt);
+        if (sj > ti) continue;
+        const double4_32a x = r4[i0 + ti], y = r4[i0 + sj];
+        T Tt[9];
+        pair_tensor<T>((T)(x.x - y.x), (T)(x.y - y.y), (T)(x.z - y.z), (T)x.z, (T)y.z, prm, wall, Tt);
         for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 3; ++c) L[(size_t)(3 * ti + a) * m + 3 * sj + c] = (T)Tt[3 * a + c];
+            for (int c = 0; c < 3; ++c) L[(size_t)(3 * ti + a) * m + 3 * sj + c] = Tt[3 * a + c];
     }
     team.sync();
     // (M^(pp))^-1 by blocked Cholesky, triangular inverse and X^T X
@@ -313,7 +318,7 @@ k_pca_build(const int* __restrict__ asm_list, const int* __restrict__ asm_link_o
                 tile_mac<T, true>(tiles.a, tiles.b, acc);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const int idx = threadIdx.x + e * kPcThreads, rr = idx / kNB, c = idx % kNB;
+                    const int rr = acc_row(e), c = acc_col(e);
                     if (i0 + rr < m && j0 + c < m) H[(size_t)(i0 + rr) * m + j0 + c] -= acc[e];
                 }
                 __syncthreads();
@@ -589,13 +594,13 @@ static void pc_build_t(am_handle* h, double tol) {
     const int n_one = h->pcb_cs > 1 ? h->n_pcb_small : h->M;
     launch_team(k_pcb_build<T, CtaTeam>, n_one, 1, 0, s, (const int*)h->d_pcb_list, (const int*)h->d_blob_off,
                 (const double4_32a*)h->d_r4, (const double4_32a*)h->d_d4, (const long long*)h->d_minv_off,
-                (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt, rpy_consts<double>(h->prm), h->cfg.wall,
+                (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt, rpy_consts<T>(h->prm), h->cfg.wall,
                 h->d_flags);
     if (h->pcb_cs > 1)
         launch_team(k_pcb_build<T, ClusterTeam>, h->M - h->n_pcb_small, h->pcb_cs, 0, s,
                     (const int*)(h->d_pcb_list + h->n_pcb_small), (const int*)h->d_blob_off,
                     (const double4_32a*)h->d_r4, (const double4_32a*)h->d_d4, (const long long*)h->d_minv_off,
-                    (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt, rpy_consts<double>(h->prm),
+                    (T*)h->d_minv, (T*)h->d_pcwork, (T*)h->d_Y, h->d_Nt, rpy_consts<T>(h->prm),
                     h->cfg.wall, h->d_flags);
     if (h->P) pca_build_t<T>(h, tol);
 }

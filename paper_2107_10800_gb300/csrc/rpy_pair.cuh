@@ -103,9 +103,16 @@ __device__ __forceinline__ void pair_free(T dx, T dy, T dz, T lx, T ly, T lz, co
     pair_free_r2<T>(dx, dy, dz, fma(dx, dx, fma(dy, dy, dz * dz)), lx, ly, lz, k, ux, uy, uz);
 }
 
+// The image coefficients of one pair (see the header): s = 1/|R|, the
+// direction Rh = (rx, ry, ez) and cI, cRR, cRz, czR, czz
 template <class T>
-__device__ __forceinline__ void pair_image(T Rx, T Ry, T Rz, T x3, T h, T lx, T ly, T lz,
-                                           const RpyK<T>& k, T& ux, T& uy, T& uz) {
+struct ImageCoefs {
+    T s, rx, ry, ez, cI, cRR, cRz, czR, czz;
+};
+
+template <class T>
+__device__ __forceinline__ ImageCoefs<T> image_coefs(T Rx, T Ry, T Rz, T x3, T h, const RpyK<T>& k) {
+    ImageCoefs<T> c;
     const T s = rsq(fma(Rx, Rx, fma(Ry, Ry, Rz * Rz)));
     const T s2 = s * s;
     const T hs = h * s;
@@ -116,19 +123,29 @@ __device__ __forceinline__ void pair_image(T Rx, T Ry, T Rz, T x3, T h, T lx, T 
     const T A2 = A * A;
     const T t1 = A * ez2;
     const T t2 = A2 * ez2;
-    const T cI = fma((T)(-10.0 / 3.0), t2, fma((T)(2.0 / 3.0), A2, fma((T)2, t1, fma((T)(-2.0 / 3.0), A, fma((T)-2, u, (T)-1)))));
-    const T cRR = fma((T)(70.0 / 3.0), t2, fma((T)(-10.0 / 3.0), A2, fma((T)-10, t1, fma((T)2, A, fma((T)6, u, (T)-1)))));
-    const T inner = fma((T)(20.0 / 3.0), A2, fma((T)-2, cRR, (T)-2));
+    c.cI = fma((T)(-10.0 / 3.0), t2, fma((T)(2.0 / 3.0), A2, fma((T)2, t1, fma((T)(-2.0 / 3.0), A, fma((T)-2, u, (T)-1)))));
+    c.cRR = fma((T)(70.0 / 3.0), t2, fma((T)(-10.0 / 3.0), A2, fma((T)-10, t1, fma((T)2, A, fma((T)6, u, (T)-1)))));
+    const T inner = fma((T)(20.0 / 3.0), A2, fma((T)-2, c.cRR, (T)-2));
     const T hs2 = (T)2 * hs;
-    const T cRz = fma(ez, inner, hs2);
-    const T czR = fma((T)(-20.0 / 3.0) * A2, ez, hs2);
-    const T czz = fma((T)-4, hs * hs, fma((T)20, t2, fma((T)(-8.0 / 3.0), A2, (T)-4 * t1)));
-    const T rx = Rx * s, ry = Ry * s;
-    const T dotR = fma(rx, lx, fma(ry, ly, ez * lz));
-    const T t = fma(cRR, dotR, cRz * lz);
-    ux = fma(s, fma(cI, lx, t * rx), ux);
-    uy = fma(s, fma(cI, ly, t * ry), uy);
-    uz = fma(s, fma(cI, lz, fma(t, ez, fma(czR, dotR, czz * lz))), uz);
+    c.cRz = fma(ez, inner, hs2);
+    c.czR = fma((T)(-20.0 / 3.0) * A2, ez, hs2);
+    c.czz = fma((T)-4, hs * hs, fma((T)20, t2, fma((T)(-8.0 / 3.0), A2, (T)-4 * t1)));
+    c.s = s;
+    c.rx = Rx * s;
+    c.ry = Ry * s;
+    c.ez = ez;
+    return c;
+}
+
+template <class T>
+__device__ __forceinline__ void pair_image(T Rx, T Ry, T Rz, T x3, T h, T lx, T ly, T lz,
+                                           const RpyK<T>& k, T& ux, T& uy, T& uz) {
+    const ImageCoefs<T> c = image_coefs<T>(Rx, Ry, Rz, x3, h, k);
+    const T dotR = fma(c.rx, lx, fma(c.ry, ly, c.ez * lz));
+    const T t = fma(c.cRR, dotR, c.cRz * lz);
+    ux = fma(c.s, fma(c.cI, lx, t * c.rx), ux);
+    uy = fma(c.s, fma(c.cI, ly, t * c.ry), uy);
+    uz = fma(c.s, fma(c.cI, lz, fma(t, c.ez, fma(c.czR, dotR, c.czz * lz))), uz);
 }
 
 // Free-space pair plus wall image of one source, fused (the sum of
@@ -258,19 +275,43 @@ __device__ __forceinline__ void pair_free_sym(T dx, T dy, T dz, T r2, T lx, T ly
     vz = fma(c1, mz, fma(sm, dz, vz));
 }
 
-// Full 3x3 tensor T (row-major, T[3a+b]: velocity a at x from force b at y),
-// FP64, including the 1/(8 pi eta) factor.
-__device__ __forceinline__ void pair_tensor_f64(double4_32a x, double4_32a y, const RpyK<double>& k,
-                                                int wall, double* Tt) {
-    for (int b = 0; b < 3; ++b) {
-        double l[3] = {0.0, 0.0, 0.0};
-        l[b] = 1.0;
-        double ux = 0.0, uy = 0.0, uz = 0.0;
-        pair_free<double>(x.x - y.x, x.y - y.y, x.z - y.z, l[0], l[1], l[2], k, ux, uy, uz);
-        if (wall)
-            pair_image<double>(x.x - y.x, x.y - y.y, x.z + y.z, x.z, y.z, l[0], l[1], l[2], k, ux, uy, uz);
-        Tt[b] = k.A1 * ux; Tt[3 + b] = k.A1 * uy; Tt[6 + b] = k.A1 * uz;
+// Full 3 x 3 tensor Tt (row-major, Tt[3a + b]: velocity a at x from force b
+// at y), including the 1/(8 pi eta) factor, for d = x - y and the heights
+// xz, yz of x and y: the operators of pair_free_r2 and pair_image written
+// out, c1 I + c2 d d^T and (wall) s (cI I + cRR Rh Rh^T + cRz Rh e3^T +
+// czR e3 Rh^T + czz e3 e3^T).
+template <class T>
+__device__ __forceinline__ void pair_tensor(T dx, T dy, T dz, T xz, T yz, const RpyK<T>& k, int wall, T* Tt) {
+    T c1, c2;
+    free_coefs<T>(fma(dx, dx, fma(dy, dy, dz * dz)), k, c1, c2);
+    const T d[3] = {dx, dy, dz};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Tt[3 * a + b] = (a == b ? c1 : (T)0) + c2 * d[a] * d[b];
+    if (wall) {
+        const ImageCoefs<T> c = image_coefs<T>(dx, dy, xz + yz, xz, yz, k);
+        const T Rh[3] = {c.rx, c.ry, c.ez};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                T v = c.cRR * Rh[a] * Rh[b] + (a == b ? c.cI : (T)0);
+                if (b == 2) v += c.cRz * Rh[a];
+                if (a == 2) v += c.czR * Rh[b];
+                if (a == 2 && b == 2) v += c.czz;
+                Tt[3 * a + b] += c.s * v;
+            }
     }
+    const T A1 = (T)k.A1;
+    for (int q = 0; q < 9; ++q) Tt[q] *= A1;
+}
+
+// the constants in another precision
+template <class T>
+__device__ __host__ inline RpyK<T> rpy_cast(const RpyK<double>& q) {
+    RpyK<T> k;
+    k.a2 = (T)q.a2; k.four_a2 = (T)q.four_a2; k.kf2 = (T)q.kf2; k.kf3 = (T)q.kf3;
+    k.kn0 = (T)q.kn0; k.kn1 = (T)q.kn1; k.kn2 = (T)q.kn2;
+    k.wc1 = (T)q.wc1; k.w2a2 = (T)q.w2a2; k.wc2 = (T)q.wc2; k.wc3 = (T)q.wc3; k.wa4 = (T)q.wa4; k.wi2 = (T)q.wi2;
+    k.A1 = q.A1;
+    return k;
 }
 
 }  // namespace am

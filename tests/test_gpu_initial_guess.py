@@ -122,20 +122,25 @@ def test_extrapolated_midpoint_steps_match_oracle():
 
 def test_repeated_time_falls_back_to_the_previous_solution():
     # every step given t = 0: the history times coincide, so the guess is the
-    # previous solution and the steps are those of order 1
+    # previous solution and the steps are those of order 1.  The product's
+    # layout is fixed (the autotuner's pick, and with it the rounding of the
+    # sums, may differ between handles), so the runs are the same
+    # computation: a second order-1 run repeats the first exactly.
     w = W.diatom_colony(5, n_rods=4, nx=8)
     dt = 1e-2
     out = {}
-    for order in (1, 3):
+    for key, order in (("1", 1), ("1 again", 1), ("3", 3)):
         s = binding.Solver.from_workload(w, t=0.0, tol=1e-12, max_iter=2000)
+        s.set_mobility_layout(1, 0)
         s.set_initial_guess(order)
         r0 = []
         for k in range(4):
             U, phi, lam, st = s.step(0.0, dt)
             r0.append(st["rel_residual0"])
-        out[order] = (s.bodies(), r0)
-    (q1, th1), r01 = out[1]
-    (q3, th3), r03 = out[3]
+        out[key] = (s.bodies(), r0)
+    (q1, th1), r01 = out["1"]
+    (q3, th3), r03 = out["3"]
+    assert out["1 again"][1] == r01
     assert rel(q3, q1) <= FP64_SOLVE and rel(th3, th1) <= FP64_SOLVE
     assert np.allclose(r03, r01, rtol=1e-6, atol=0.0)
 
