@@ -749,7 +749,7 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsq(a.x), rsq(a.y)); }
 
 // (hi, lo) += t exactly in each lane (Knuth's TwoSum of hi and t, the
 // rounding error added to lo): the compensated accumulation of the tile sums

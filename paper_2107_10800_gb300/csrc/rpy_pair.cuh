@@ -66,7 +66,15 @@ inline RpyK<T> rpy_consts(const RpyParams& q) {
     return k;
 }
 
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// FP32: the hardware estimate (PTX rsqrt.approx, relative error below
+// 2^-22.9) without the subnormal path, which no argument here needs: they
+// are squared distances of at least (2a)^2 or squared image distances of
+// at least the squared sum of two heights above the wall
+__device__ __forceinline__ float rsq(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float sqt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqt(double x) { return sqrt(x); }

@@ -3,7 +3,7 @@ piece of the solver's hot path a few times and exits, so that a capture of
 one kernel (-k, -c) ends quickly.  Nothing here is timed.
 
     python -m paper_2107_10800_gb300.profile_cases product --blobs 60000 [--arith mixed|fp64|df64] [--symmetric]
-    python -m paper_2107_10800_gb300.profile_cases colony --precision fp64|mixed [--steps 3] [--host-steps]
+    python -m paper_2107_10800_gb300.profile_cases colony --precision fp64|mixed [--steps 3] [--host-steps] [--tile 64]
     python -m paper_2107_10800_gb300.profile_cases batched [--steps 1] [--host-steps]
     python -m paper_2107_10800_gb300.profile_cases mlp [--rows 65536] [--calls 3]
     python -m paper_2107_10800_gb300.profile_cases periodic [--lattice 10 10 10] [--tol 1e-8] [--calls 3]
@@ -16,7 +16,9 @@ thread and 4,096-source chunks for the mixed arithmetic, or with
 colony: Euler steps of the diatom colony (2,560 blobs, 62 sliding links,
 dt = 1e-3, relative residual 1e-8); with --host-steps the Arnoldi steps are
 launched from the host (per-launch timing of the product on) instead of
-from the CUDA-graph loop, whose kernels profilers do not capture.
+from the CUDA-graph loop, whose kernels profilers do not capture; --tile
+fixes the symmetric product on tiles of that many blobs (the autotuner's
+timings mean nothing under a profiler).
 batched: steps of the 256 free-space chain suspensions in one handle
 (mixed precision); --host-steps as for colony.
 mlp: BF16 predictions of the learned-guess network (random weights) for
@@ -57,9 +59,11 @@ def product(blobs, arith, calls, symmetric=False):
     s.close()
 
 
-def colony(precision, steps, host_steps=False):
+def colony(precision, steps, host_steps=False, tile=0):
     w = W.diatom_colony(1)
     s = binding.Solver.from_workload(w, t=0.0, tol=1e-8, precision=precision)
+    if tile:
+        s.set_mobility_layout(3, tile)
     if host_steps:
         s.mobility_timing(True)
     for k in range(steps):
@@ -110,12 +114,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--host-steps", action="store_true")
     ap.add_argument("--symmetric", action="store_true")
+    ap.add_argument("--tile", type=int, default=0)
     a = ap.parse_args()
     build.build()
     if a.case == "product":
         product(a.blobs, a.arith, a.calls, a.symmetric)
     elif a.case == "colony":
-        colony(a.precision, a.steps, a.host_steps)
+        colony(a.precision, a.steps, a.host_steps, a.tile)
     elif a.case == "batched":
         batched(a.steps, a.host_steps)
     elif a.case == "periodic":
