@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "am.h"
@@ -91,6 +92,28 @@ struct SymItem {
 };
 
 // ---- device helpers -----------------------------------------------------
+// Programmatic dependent launch: a kernel launched by launch_dep may be
+// scheduled while its predecessor in the stream drains; it calls dep_wait
+// before its first global memory access, which returns once the
+// predecessor has completed and its writes are visible (a no-op for a
+// kernel launched without the attribute).
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class K, class... Args>
+inline cudaError_t launch_dep(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, kernel, std::forward<Args>(args)...);
+}
+
 // End of a work-queue kernel (counter[0]: next item, counter[1]: blocks
 // finished): the last block to finish zeroes both for the next launch.
 // Every block has taken its last item before it counts itself finished, so

@@ -85,6 +85,7 @@ __global__ void k_op_epilogue(int Nb, int M, int P, int nblob_blocks, int nbody_
                               const int* __restrict__ bl_idx, const double* __restrict__ lp,
                               const double* __restrict__ lq, const int* __restrict__ bp,
                               const int* __restrict__ bq) {
+    dep_wait();
     const double* lam = y;
     const double* U = y + 3 * (size_t)Nb;
     const double* phi = U + 6 * (size_t)M;
@@ -784,6 +785,7 @@ k_arn_dots(const double* __restrict__ V, size_t ldv, const double* __restrict__ 
            const int* __restrict__ ce, const int* __restrict__ sys_of, const int* __restrict__ coff,
            double* __restrict__ part, int nchunks, int m1, double* __restrict__ coef, double* __restrict__ hcol,
            int* __restrict__ cnt, const ArnoldiCtrl* __restrict__ c) {
+    dep_wait();
     const int j = c->j, b = blockIdx.x, c0 = cs[b], c1 = ce[b], s = sys_of[c0];
     double* zc = Z + (size_t)j * ldv;
     for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) zc[i] = z[i];
@@ -797,6 +799,7 @@ k_arn_orth_dots(const double* __restrict__ V, size_t ldv, double* __restrict__ w
                 const int* __restrict__ ce, const int* __restrict__ sys_of, const int* __restrict__ coff, int clen,
                 double* __restrict__ part, int nchunks, int m1, double* __restrict__ coef,
                 double* __restrict__ hcol, int* __restrict__ cnt, const ArnoldiCtrl* __restrict__ c) {
+    dep_wait();
     __shared__ double sh[256];
     const int j = c->j, b = blockIdx.x, c0 = cs[b], c1 = ce[b], s = sys_of[c0];
     chunk_orth(V, ldv, w, c0, c1, j, coef + (size_t)s * m1, clen, sh);
@@ -815,6 +818,7 @@ k_arn_orth_finish(const double* __restrict__ V, size_t ldv, double* __restrict__
                   double* __restrict__ csv, double* __restrict__ snv, double* __restrict__ g,
                   int* __restrict__ active, int* __restrict__ kdone, const double* __restrict__ tol_s,
                   double* __restrict__ inv, ArnoldiCtrl* c, cudaGraphConditionalHandle hc, int in_graph) {
+    dep_wait();
     __shared__ double sh[256];
     const int j = c->j, b = blockIdx.x, c0 = cs[b], c1 = ce[b], s = sys_of[c0];
     double a = chunk_orth(V, ldv, w, c0, c1, j, coef + (size_t)s * m1, clen, sh);
@@ -835,6 +839,7 @@ k_arn_orth_finish(const double* __restrict__ V, size_t ldv, double* __restrict__
 __global__ void k_next_basis(const double* __restrict__ w, double* __restrict__ V, size_t ldv, int n,
                              const int* __restrict__ sys_of, const double* __restrict__ inv,
                              const ArnoldiCtrl* __restrict__ c, double* __restrict__ vj, int j_ahead) {
+    dep_wait();
     double* v = V + (size_t)(c->j + (j_ahead ? 0 : 1)) * ldv;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double t = inv[sys_of[i]] * w[i];
@@ -946,10 +951,10 @@ void op_apply(am_handle* h, const double* y, double* out, int mode, const int* a
     }
     mobility_partial(h, y, mode, active);
     const int nbb = nblk(h->Nb, 128), nbody = nblk(h->M, 4), nlink = nblk(h->P, 128);
-    k_op_epilogue<<<nbb + nbody + nlink, 128, 0, h->stream>>>(
-        h->Nb, h->M, h->P, nbb, nbody, h->d_mv, h->d_sys_of_blob, h->d_sys_blob0, h->d_sys_nb,
-        h->d_sys_nch, h->d_sys_poff, y, out, h->d_body_of_blob, h->d_blob_off, h->d_d4,
-        h->d_body_link_off, h->d_body_link_idx, h->d_lp, h->d_lq, h->d_bp, h->d_bq);
+    launch_dep(k_op_epilogue, dim3(nbb + nbody + nlink), dim3(128), 0, h->stream, h->Nb, h->M, h->P, nbb, nbody,
+               h->d_mv, h->d_sys_of_blob, h->d_sys_blob0, h->d_sys_nb, h->d_sys_nch, h->d_sys_poff, y, out,
+               h->d_body_of_blob, h->d_blob_off, h->d_d4, h->d_body_link_off, h->d_body_link_idx, h->d_lp, h->d_lq,
+               h->d_bp, h->d_bq);
     count_launch();
 }
 
@@ -1074,19 +1079,19 @@ static void issue_arnoldi_step(am_handle* h, bool fp64, cudaGraphConditionalHand
     pc_apply(h, h->d_vj, h->d_zj);  // vj = V[j], written with V[j]
     // the input of a stopped system is zero: its product skips the pairs
     op_apply(h, h->d_zj, h->d_w, fp64, S > 1 ? h->d_active : nullptr);
-    k_arn_dots<<<nch, ct, 0, s>>>(h->d_V, ldv, h->d_w, h->d_zj, h->d_Z, h->d_chunk_start, h->d_chunk_end,
-                                   h->d_sys_of_elem, h->d_sys_chunk_off, h->d_part, nch, m1, h->d_coefs,
-                                   h->d_hcols, h->d_arn_cnt, h->d_ctrl);
-    k_arn_orth_dots<<<nch, ct, 0, s>>>(h->d_V, ldv, h->d_w, h->d_chunk_start, h->d_chunk_end, h->d_sys_of_elem,
-                                        h->d_sys_chunk_off, h->chunk_len, h->d_part, nch, m1, h->d_coefs, h->d_hcols,
-                                        h->d_arn_cnt, h->d_ctrl);
-    k_arn_orth_finish<<<nch, ct, 0, s>>>(h->d_V, ldv, h->d_w, h->d_chunk_start, h->d_chunk_end,
-                                          h->d_sys_of_elem, h->d_sys_chunk_off, h->chunk_len, h->d_npart, m1, h->d_coefs,
-                                          h->d_hcols, h->d_arn_cnt, S, m, h->d_Hs, h->d_css, h->d_sns, h->d_gs,
-                                          h->d_active, h->d_kdone, h->d_tol_s, h->d_inv_s, h->d_ctrl, hc,
-                                          in_graph ? 1 : 0);
+    launch_dep(k_arn_dots, dim3(nch), dim3(ct), 0, s, h->d_V, ldv, h->d_w, h->d_zj, h->d_Z, h->d_chunk_start,
+               h->d_chunk_end, h->d_sys_of_elem, h->d_sys_chunk_off, h->d_part, nch, m1, h->d_coefs, h->d_hcols,
+               h->d_arn_cnt, h->d_ctrl);
+    launch_dep(k_arn_orth_dots, dim3(nch), dim3(ct), 0, s, h->d_V, ldv, h->d_w, h->d_chunk_start, h->d_chunk_end,
+               h->d_sys_of_elem, h->d_sys_chunk_off, h->chunk_len, h->d_part, nch, m1, h->d_coefs, h->d_hcols,
+               h->d_arn_cnt, h->d_ctrl);
+    launch_dep(k_arn_orth_finish, dim3(nch), dim3(ct), 0, s, h->d_V, ldv, h->d_w, h->d_chunk_start, h->d_chunk_end,
+               h->d_sys_of_elem, h->d_sys_chunk_off, h->chunk_len, h->d_npart, m1, h->d_coefs, h->d_hcols,
+               h->d_arn_cnt, S, m, h->d_Hs, h->d_css, h->d_sns, h->d_gs, h->d_active, h->d_kdone, h->d_tol_s,
+               h->d_inv_s, h->d_ctrl, hc, in_graph ? 1 : 0);
     // j has advanced: V[j] = w / |w_s| and the next step's input
-    k_next_basis<<<nb, 256, 0, s>>>(h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s, h->d_ctrl, h->d_vj, 1);
+    launch_dep(k_next_basis, dim3(nb), dim3(256), 0, s, h->d_w, h->d_V, ldv, n, h->d_sys_of_elem, h->d_inv_s,
+               h->d_ctrl, h->d_vj, 1);
     count_launch(4);
 }
 

@@ -347,6 +347,7 @@ k_pc_ap1(const int* __restrict__ pcw_body, const int* __restrict__ pcw_chunk,
          const long long* __restrict__ moff, const T* __restrict__ Y, const double* __restrict__ r,
          double* __restrict__ w, double* __restrict__ ytp, int Nb, const int* __restrict__ pcw_off,
          const double* __restrict__ Nt, double* __restrict__ Uhat, int* __restrict__ body_cnt) {
+    dep_wait();
     __shared__ double red[4][kRows];
     __shared__ double yred[4][6];
     const int it = blockIdx.x;
@@ -440,6 +441,7 @@ k_pc_ap2(int Nb, int M, const int* __restrict__ pca_asm, const int* __restrict__
          double* __restrict__ z, const int* __restrict__ bp, const int* __restrict__ bq,
          const double* __restrict__ lp, const double* __restrict__ lq, const double* __restrict__ Uhat,
          const double* __restrict__ r) {
+    dep_wait();
     constexpr int kStage = 1024;  // entries of c staged in shared memory at a time
     __shared__ double red[4][kRows];
     __shared__ double cs[kStage];
@@ -499,6 +501,7 @@ k_pc_ap3(int Nb, int M, const int* __restrict__ pcw_body, const int* __restrict_
          const double* __restrict__ w, const double* __restrict__ Uhat,
          const int* __restrict__ bl_off, const int* __restrict__ bl_idx,
          const double* __restrict__ lp, const double* __restrict__ lq, double* __restrict__ z) {
+    dep_wait();
     __shared__ double sU[6];
     const int it = blockIdx.x;
     const int b = pcw_body[it];
@@ -643,20 +646,20 @@ template <class T>
 static void pc_apply_t(am_handle* h, const double* r, double* z) {
     cudaStream_t s = h->stream;
     // w and Y^T r1 per (body, chunk) item; the body's last item forms U^
-    k_pc_ap1<T><<<h->n_pcw, 128, 0, s>>>(h->d_pcw_body, h->d_pcw_chunk, h->d_blob_off, (const T*)h->d_minv,
-                                          h->d_minv_off, (const T*)h->d_Y, r, h->d_pc_w, h->d_ytp, h->Nb,
-                                          h->d_pcw_off, h->d_Nt, h->d_pc_Uhat, h->d_pcb_cnt);
+    launch_dep(k_pc_ap1<T>, dim3(h->n_pcw), dim3(128), 0, s, h->d_pcw_body, h->d_pcw_chunk, h->d_blob_off,
+               (const T*)h->d_minv, h->d_minv_off, (const T*)h->d_Y, r, h->d_pc_w, h->d_ytp, h->Nb, h->d_pcw_off,
+               h->d_Nt, h->d_pc_Uhat, h->d_pcb_cnt);
     count_launch();
     if (h->P) {
         // phi = G~ (r3 - C U^), c formed per staged entry
-        k_pc_ap2<T, true><<<h->n_pca, 128, 0, s>>>(h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk, h->d_asm_link_off,
-                                                    h->d_asm_link_idx, (const T*)h->d_G, h->d_G_off, nullptr, z,
-                                                    h->d_bp, h->d_bq, h->d_lp, h->d_lq, h->d_pc_Uhat, r);
+        launch_dep(k_pc_ap2<T, true>, dim3(h->n_pca), dim3(128), 0, s, h->Nb, h->M, h->d_pca_asm, h->d_pca_chunk,
+                   h->d_asm_link_off, h->d_asm_link_idx, (const T*)h->d_G, h->d_G_off, nullptr, z, h->d_bp, h->d_bq,
+                   h->d_lp, h->d_lq, h->d_pc_Uhat, r);
         count_launch();
     }
-    k_pc_ap3<T><<<h->n_pcw, 128, 0, s>>>(h->Nb, h->M, h->d_pcw_body, h->d_pcw_chunk, h->d_blob_off,
-                                          (const T*)h->d_Y, h->d_Nt, h->d_pc_w, h->d_pc_Uhat,
-                                          h->d_body_link_off, h->d_body_link_idx, h->d_lp, h->d_lq, z);
+    launch_dep(k_pc_ap3<T>, dim3(h->n_pcw), dim3(128), 0, s, h->Nb, h->M, h->d_pcw_body, h->d_pcw_chunk,
+               h->d_blob_off, (const T*)h->d_Y, h->d_Nt, h->d_pc_w, h->d_pc_Uhat, h->d_body_link_off,
+               h->d_body_link_idx, h->d_lp, h->d_lq, z);
     count_launch();
 }
 

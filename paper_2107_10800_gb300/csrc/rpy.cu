@@ -460,6 +460,7 @@ __global__ void __launch_bounds__(kThreads)
 rpy_items_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam,
               double* __restrict__ part, const MvItem* __restrict__ items, int n_items,
               int* __restrict__ counter, RpyK<double> k, const int* __restrict__ active) {
+    dep_wait();
     __shared__ double4_32a sr[kTile];
     __shared__ double sl[3 * kTile];
     __shared__ int s_item;
@@ -532,6 +533,7 @@ __global__ void __launch_bounds__(NSUB == 1 ? 32 : 128)
 rpy_sym_f64(const double4_32a* __restrict__ r4, const double* __restrict__ lam, double* __restrict__ part,
             const SymItem* __restrict__ items, int n_items, int* __restrict__ counter, RpyK<double> k,
             const int* __restrict__ active) {
+    dep_wait();
     constexpr int T = 32 * NSUB;
     constexpr int NW = NSUB == 1 ? 1 : 4;
     constexpr int NWT = NSUB * NSUB;
@@ -645,6 +647,7 @@ rpy_items_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo,
                 const double* __restrict__ lam, double* __restrict__ part,
                 const MvItem* __restrict__ items, int n_items, int* __restrict__ counter,
                 RpyK<float> k, const int* __restrict__ active) {
+    dep_wait();
     __shared__ float4 sh[kTile];
     __shared__ float4 so[kTile];
     __shared__ float4 sl[kTile];
@@ -903,6 +906,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 rpy_sym_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo, const double* __restrict__ lam,
                  double* __restrict__ part, const SymItem* __restrict__ items, int n_items, int* __restrict__ counter,
                  RpyK<float> k, const int* __restrict__ active) {
+    dep_wait();
     constexpr int T = 128;
     __shared__ float4 sq[3][T];   // sources: (-hx, -hx, -hy, -hy), (2hz, 2hz, lz, lz), (lx, lx, ly, ly)
     __shared__ float4 so[T];      // (-ox, -ox, -oy, -oy)
@@ -1048,6 +1052,7 @@ __global__ void __launch_bounds__(NSUB == 1 ? 32 : 128)
 rpy_sym_mixed(const float4* __restrict__ hi, const float4* __restrict__ lo, const double* __restrict__ lam,
               double* __restrict__ part, const SymItem* __restrict__ items, int n_items, int* __restrict__ counter,
               RpyK<float> k, const int* __restrict__ active) {
+    dep_wait();
     constexpr int T = 32 * NSUB;
     constexpr int NW = NSUB == 1 ? 1 : 4;
     constexpr int NWT = NSUB * NSUB;
@@ -1183,6 +1188,7 @@ rpy_items_mixed_x2(const float4* __restrict__ hi, const float4* __restrict__ lo,
                    const double* __restrict__ lam, double* __restrict__ part,
                    const MvItem* __restrict__ items, int n_items, int* __restrict__ counter,
                    RpyK<float> k, const int* __restrict__ active) {
+    dep_wait();
     __shared__ float4 sq[3][kTile];
     __shared__ float4 so[kTile];
     __shared__ float2 soz[kTile];
@@ -1459,8 +1465,8 @@ void launch_items(am_handle* h, const double* lam, int mode, const int* active) 
         const SymItem* si = static_cast<const SymItem*>(h->d_sym_items);
         const int th = h->sym_nsub == 1 ? 32 : 128;
 #define AM_SYM(W, N)                                                                                      \
-    rpy_sym_f64<W, N><<<h->mv_gridsym, th, 0, st>>>(h->d_r4, lam, h->d_mv, si, h->n_sym, h->d_item_counter, \
-                                                    k, active)
+    launch_dep(rpy_sym_f64<W, N>, dim3(h->mv_gridsym), dim3(th), 0, st, h->d_r4, lam, h->d_mv, si, h->n_sym, \
+               h->d_item_counter, k, active)
         if (h->cfg.wall) {
             if (h->sym_nsub == 1) AM_SYM(true, 1); else if (h->sym_nsub == 2) AM_SYM(true, 2); else AM_SYM(true, 4);
         } else {
@@ -1470,21 +1476,21 @@ void launch_items(am_handle* h, const double* lam, int mode, const int* active) 
     } else if (fp64) {
         const RpyK<double> k = rpy_consts<double>(h->prm);
         if (h->cfg.wall)
-            rpy_items_f64<true><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,
-                                                                  h->d_item_counter, k, active);
+            launch_dep(rpy_items_f64<true>, dim3(h->mv_grid64), dim3(kThreads), 0, st, h->d_r4, lam, h->d_mv, items,
+                       h->n_items, h->d_item_counter, k, active);
         else
-            rpy_items_f64<false><<<h->mv_grid64, kThreads, 0, st>>>(h->d_r4, lam, h->d_mv, items, h->n_items,
-                                                                   h->d_item_counter, k, active);
+            launch_dep(rpy_items_f64<false>, dim3(h->mv_grid64), dim3(kThreads), 0, st, h->d_r4, lam, h->d_mv, items,
+                       h->n_items, h->d_item_counter, k, active);
     } else if (h->n_sym > 0) {
         const RpyK<float> k = rpy_consts<float>(h->prm);
         const SymItem* si = static_cast<const SymItem*>(h->d_sym_items);
         const int th = h->mv_tpt == 2 || h->sym_nsub > 1 ? kThreads : 32;
-#define AM_SYM32(W, N)                                                                                   \
-    rpy_sym_mixed<W, N><<<h->mv_gridsym32, th, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, si, h->n_sym, \
-                                                        h->d_item_counter, k, active)
-#define AM_SYM32X2(W)                                                                                        \
-    rpy_sym_mixed_x2<W><<<h->mv_gridsym32, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, si, h->n_sym, \
-                                                              h->d_item_counter, k, active)
+#define AM_SYM32(W, N)                                                                                      \
+    launch_dep(rpy_sym_mixed<W, N>, dim3(h->mv_gridsym32), dim3(th), 0, st, h->d_rhi, h->d_rlo, lam, h->d_mv, si, \
+               h->n_sym, h->d_item_counter, k, active)
+#define AM_SYM32X2(W)                                                                                         \
+    launch_dep(rpy_sym_mixed_x2<W>, dim3(h->mv_gridsym32), dim3(kThreads), 0, st, h->d_rhi, h->d_rlo, lam, h->d_mv, \
+               si, h->n_sym, h->d_item_counter, k, active)
         if (h->cfg.wall) {
             if (h->mv_tpt == 2) AM_SYM32X2(true);
             else if (h->sym_nsub == 1) AM_SYM32(true, 1);
@@ -1500,12 +1506,12 @@ void launch_items(am_handle* h, const double* lam, int mode, const int* active) 
 #undef AM_SYM32
     } else {
         const RpyK<float> k = rpy_consts<float>(h->prm);
-#define AM_MIXED_ITEMS(W, T)                                                                             \
-    rpy_items_mixed<W, T><<<h->mv_grid, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items, \
-                                                           h->n_items, h->d_item_counter, k, active)
-#define AM_MIXED_X2(W)                                                                               \
-    rpy_items_mixed_x2<W><<<h->mv_grid, kThreads, 0, st>>>(h->d_rhi, h->d_rlo, lam, h->d_mv, items,  \
-                                                           h->n_items, h->d_item_counter, k, active)
+#define AM_MIXED_ITEMS(W, T)                                                                                 \
+    launch_dep(rpy_items_mixed<W, T>, dim3(h->mv_grid), dim3(kThreads), 0, st, h->d_rhi, h->d_rlo, lam, h->d_mv, \
+               items, h->n_items, h->d_item_counter, k, active)
+#define AM_MIXED_X2(W)                                                                                      \
+    launch_dep(rpy_items_mixed_x2<W>, dim3(h->mv_grid), dim3(kThreads), 0, st, h->d_rhi, h->d_rlo, lam, h->d_mv, \
+               items, h->n_items, h->d_item_counter, k, active)
         if (h->cfg.wall) {
             if (h->mv_tpt == 2) AM_MIXED_X2(true); else AM_MIXED_ITEMS(true, 1);
         } else {
