@@ -36,12 +36,12 @@ TOL = 1e-8
 WORKLOAD = ("diatom colony above a no-slip wall: 32 rods of 2x40 blobs (2,560 blobs, a=0.1), "
             "62 sliding links, dt=1e-3, FP64, GMRES relative residual 1e-8")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
-# DRAM bytes (read + write) of one launch of the FP64 wall product on this
-# colony (the symmetric kernel, rpy_sym_f64), from an ncu capture of the
-# colony's steps (profile_cases colony --host-steps)
-# (dram__bytes_read.sum + dram__bytes_write.sum); None where no capture of
+# DRAM bytes (read + write) of one launch of the wall product on this colony
+# per (precision, symmetric tile), from ncu captures of the colony's steps
+# with the tile fixed (profile_cases colony --host-steps --tile T;
+# dram__bytes_read.sum + dram__bytes_write.sum); absent where no capture of
 # the kernel as it now stands exists
-TRAFFIC_BYTES = {"fp64": 218368, "mixed": None}
+TRAFFIC_BYTES = {("fp64", 32): 337152, ("fp64", 64): 219648}
 # flop per unordered pair of the symmetric FP64 wall product (see run_ours)
 SYM_WALL_FLOP_PER_UNORDERED_PAIR = 126
 
@@ -821,7 +821,7 @@ def run_ours(args):
     clocks = clk.summary()
     roofline = {"bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_BYTES[args.precision] if layout[3] > 0 or args.precision != "fp64" else None,
+                "traffic": TRAFFIC_BYTES.get((args.precision, layout[3])),
                 "kernel": kname, "layout": list(layout),
                 "executed_tflops": executed / 1e12, "executed_frac": executed / peak,
                 "algorithmic_vs_executed": "achieved counts N^2 pairs x 119 flop per launch; the symmetric "
